@@ -1,0 +1,164 @@
+"""CPU oracle for the weakly-synchronous AT method of arXiv 1911.05769.
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+benchmark's CPU-baseline leg (``bench.py``) may import this package.  It shares
+no code with the CUDA library in ``paper_1911_05769_gb300``; the two are
+compared element by element.
+
+The arithmetic lives in ``at_oracle.c`` (plain FP64 C, compiled with
+``-O2 -ffp-contract=off``).  This module compiles it on first use and marshals
+numpy arrays through ctypes.
+
+Sections followed (see the C file for the details): Eq. BS (Burgers), Sec. 3.2
+(forward Euler, central differences, AT schemes at process-boundary points),
+Eq. AT1 / Eq. AT2 (AT coefficients), Sec. 5.2 and Algorithm 2 (split form:
+halo approximation, then the unchanged stencil; synchrony during start-up).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "at_oracle.c")
+_LIB = os.path.join(_HERE, "libat_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+SYNC, SEEDED, REPLAY = 0, 1, 2
+EQ_BURGERS, EQ_LINEAR = 0, 1
+BC_PERIODIC, BC_TANH = 0, 1
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle into ``oracle/libat_oracle.so`` (plain gcc)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math",
+                               "-std=c99", "-shared", "-fPIC", _SRC, "-o", tmp, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class Cfg(ctypes.Structure):
+    _fields_ = [
+        ("N", ctypes.c_int64), ("P", ctypes.c_int64),
+        ("p_lo", ctypes.c_int64), ("p_count", ctypes.c_int64),
+        ("order", ctypes.c_int32), ("L", ctypes.c_int32),
+        ("nu", ctypes.c_double), ("dt", ctypes.c_double),
+        ("x0", ctypes.c_double), ("dx", ctypes.c_double),
+        ("forcing_amp", ctypes.c_double),
+        ("eq", ctypes.c_int32), ("bc", ctypes.c_int32),
+        ("adv_c", ctypes.c_double),
+        ("tanh_a", ctypes.c_double), ("tanh_c", ctypes.c_double), ("tanh_xc", ctypes.c_double),
+        ("delay_mode", ctypes.c_int32), ("per_subdomain", ctypes.c_int32),
+        ("at_weights", ctypes.c_int32), ("pad_", ctypes.c_int32),
+        ("seed", ctypes.c_uint64),
+    ]
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = ctypes.CDLL(build())
+            L.at_oracle_splitmix64.restype = ctypes.c_uint64
+            L.at_oracle_splitmix64.argtypes = [ctypes.c_uint64, ctypes.c_uint64]
+            L.at_oracle_seeded_delay.restype = ctypes.c_int
+            L.at_oracle_seeded_delay.argtypes = [ctypes.c_uint64, ctypes.c_int64, ctypes.c_int64,
+                                                 ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+            L.at_oracle_weights.restype = ctypes.c_int
+            L.at_oracle_weights.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                            ctypes.POINTER(ctypes.c_double)]
+            L.at_oracle_extrapolate.restype = ctypes.c_double
+            L.at_oracle_extrapolate.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                ctypes.POINTER(ctypes.c_double)]
+            L.at_oracle_derivs.restype = ctypes.c_int
+            L.at_oracle_derivs.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.c_double,
+                                           ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
+            L.at_oracle_run.restype = ctypes.c_int
+            L.at_oracle_run.argtypes = [ctypes.POINTER(Cfg), ctypes.c_int64, ctypes.c_void_p,
+                                        ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+            L.at_oracle_cfg_size.restype = ctypes.c_int64
+            if L.at_oracle_cfg_size() != ctypes.sizeof(Cfg):
+                raise RuntimeError("oracle: configuration struct layout mismatch")
+            _lib = L
+    return _lib
+
+
+def _dptr(a):
+    return a.ctypes.data_as(ctypes.c_void_p) if a is not None else None
+
+
+def splitmix64(seed: int, i: int) -> int:
+    return int(lib().at_oracle_splitmix64(seed & (2**64 - 1), i & (2**64 - 1)))
+
+
+def seeded_delay(seed, n, p, P, face, F, L) -> int:
+    return int(lib().at_oracle_seeded_delay(seed, n, p, P, face, F, L))
+
+
+def weights(s: int, k: int, at_weights: bool = True) -> np.ndarray:
+    w = np.zeros(s, dtype=np.float64)
+    rc = lib().at_oracle_weights(s, k, int(at_weights), w.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    if rc != 0:
+        raise ValueError(f"oracle weights: rc={rc}")
+    return w
+
+
+def extrapolate(s: int, k: int, levels, at_weights: bool = True) -> float:
+    lev = np.ascontiguousarray(levels, dtype=np.float64)
+    return float(lib().at_oracle_extrapolate(s, k, int(at_weights),
+                                             lev.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+
+
+def derivs(order: int, v, dx: float):
+    v = np.ascontiguousarray(v, dtype=np.float64)
+    d1, d2 = ctypes.c_double(), ctypes.c_double()
+    rc = lib().at_oracle_derivs(order, v.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), dx,
+                                ctypes.byref(d1), ctypes.byref(d2))
+    if rc != 0:
+        raise ValueError("oracle derivs: bad order")
+    return d1.value, d2.value
+
+
+def run(u0, *, N=None, P, order, L, nu, dt, n_steps, x0=0.0, dx=None, length=2 * np.pi,
+        forcing_amp=0.0, eq=EQ_BURGERS, adv_c=0.0, bc=BC_PERIODIC, tanh=(0.0, 0.0, 0.0),
+        delay_mode=SYNC, seed=0, replay=None, per_subdomain=False, at_weights=True,
+        p_lo=0, p_count=None, want_k=False):
+    """Advance ``u0`` by ``n_steps`` forward-Euler steps of the AT method.
+
+    ``u0`` holds the field of subdomains ``p_lo .. p_lo+p_count-1`` (the whole
+    domain by default).  Returns ``(u, hist)`` or ``(u, hist, k_used)``.
+    """
+    u0 = np.ascontiguousarray(u0, dtype=np.float64)
+    if N is None:
+        N = u0.size
+    if p_count is None:
+        p_count = P
+    if dx is None:
+        dx = length / N
+    c = Cfg(N=N, P=P, p_lo=p_lo, p_count=p_count, order=order, L=L, nu=nu, dt=dt, x0=x0, dx=dx,
+            forcing_amp=forcing_amp, eq=eq, bc=bc, adv_c=adv_c, tanh_a=tanh[0], tanh_c=tanh[1],
+            tanh_xc=tanh[2], delay_mode=delay_mode, per_subdomain=int(per_subdomain),
+            at_weights=int(at_weights), pad_=0, seed=seed & (2**64 - 1))
+    W = p_count * (N // P)
+    if u0.size != W:
+        raise ValueError(f"oracle run: u0 has {u0.size} values, window needs {W}")
+    out = np.empty(W, dtype=np.float64)
+    hist = np.zeros(L + 1, dtype=np.int64)
+    rep = None
+    if delay_mode == REPLAY:
+        rep = np.ascontiguousarray(replay, dtype=np.int8)
+        if rep.size != n_steps * p_count * 2:
+            raise ValueError("oracle run: replay array has the wrong size")
+    kk = np.empty((n_steps, p_count, 2), dtype=np.int8) if want_k else None
+    rc = lib().at_oracle_run(ctypes.byref(c), n_steps, _dptr(rep), _dptr(u0), _dptr(out),
+                             _dptr(hist), _dptr(kk))
+    if rc != 0:
+        raise ValueError(f"oracle run failed: rc={rc}")
+    return (out, hist, kk) if want_k else (out, hist)

@@ -1,0 +1,262 @@
+/*
+ * at_oracle.c -- plain FP64 CPU oracle for the weakly-synchronous AT method.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing on the product path may call, link or
+ * execute this file; only the tests, the smoke check and the benchmark's
+ * CPU-baseline leg use it.  It shares no code, header, table or constant
+ * generator with the CUDA library: the two are checked against each other.
+ *
+ * What it computes (arXiv 1911.05769):
+ *   - viscous Burgers' equation u_t + u u_x = nu u_xx (Eq. BS, one velocity
+ *     component, one dimension), optionally with a time-independent forcing
+ *     F(x) = A sin(x), or the linear advection-diffusion equation
+ *     u_t + c u_x = nu u_xx used for the accuracy demonstration of Fig. 2;
+ *   - forward-Euler time integration (Sec. 3.2);
+ *   - standard central differences at interior points I_i (Sec. 3.2);
+ *   - asynchrony-tolerant (AT) differences at process-boundary points I_b,
+ *     Eq. AT1 / Eq. AT2, in the "split" form of Sec. 5.2: every halo value is
+ *     first approximated from the delayed levels n-k, n-k-1 (the
+ *     "approximate" step of Algorithm 2), then the unchanged central stencil
+ *     is applied;
+ *   - delays k <= L per (time level n, subdomain p, face), prescribed by a
+ *     counter-based generator (SplitMix64), replayed from an array, or zero
+ *     (the synchronous algorithm, Algorithm 1).
+ *
+ * The domain [x0, x0 + N dx) is split into P subdomains of M = N/P points.
+ * Readings of the paper used here (the paper is silent or ambiguous):
+ *   - k ranges over {0..L}: Algorithm 2 lets the receive time lag the send
+ *     time by L (Sec. 2 writes n-L+1 as the oldest level; Alg. 2 allows n-L).
+ *   - Start-up: k is clamped to n-s+1 so that no level below 0 is read; this
+ *     is the "synchronize during initialisation" branch of Algorithm 2.
+ *   - 4th order: the paper gives only the 2nd-order AT formulas; the 4th-order
+ *     variant extrapolates each delayed halo value quadratically in time from
+ *     three levels (a wider stencil in time, Sec. 2) and then applies the
+ *     standard 4th-order central stencil.
+ *   - Delays are drawn independently per face (one message per face per step,
+ *     Sec. 5.1); the per_subdomain flag uses one draw for both faces.
+ *
+ * Everything is FP64, evaluated in the written order; compile with
+ * -O2 -ffp-contract=off and no fast-math.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_OK 0
+#define ORC_EARG (-1)
+#define ORC_ENOMEM (-2)
+#define ORC_EDELAY (-3)
+
+/* ------------------------------------------------------------------------ */
+/* Counter-based generator for prescribed delays.                           */
+/* SplitMix64 (Steele, Lea & Flood, "Fast splittable pseudorandom number    */
+/* generators", OOPSLA 2014): state advances by the golden-ratio increment  */
+/* and each state is passed through the 64-bit finaliser with shift/multiply */
+/* constants (30, 0xBF58476D1CE4E5B9), (27, 0x94D049BB133111EB), 31.         */
+/* at_oracle_splitmix64(seed, i) is the i-th (0-based) output of the        */
+/* sequence started from state `seed`.                                       */
+/* ------------------------------------------------------------------------ */
+uint64_t at_oracle_splitmix64(uint64_t seed, uint64_t i)
+{
+    uint64_t z = seed + (i + 1u) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+/* Raw prescribed delay in {0..L} for (level n, subdomain p, face f) of a
+ * decomposition into P subdomains with F faces each: the generator output at
+ * counter (n*P + p)*F + f, upper 32 bits mapped to {0..L} by multiply-shift. */
+int at_oracle_seeded_delay(uint64_t seed, int64_t n, int64_t p, int64_t P,
+                           int face, int F, int L)
+{
+    uint64_t ctr = ((uint64_t)n * (uint64_t)P + (uint64_t)p) * (uint64_t)F
+                   + (uint64_t)face;
+    uint64_t h = at_oracle_splitmix64(seed, ctr) >> 32;
+    return (int)((h * (uint64_t)(L + 1)) >> 32);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Halo approximation weights (Eq. AT1 / AT2; split form, Sec. 5.2).        */
+/* The value at level n is extrapolated from the s levels n-k, ..., n-k-s+1 */
+/* by the Lagrange polynomial through times -k-m (m = 0..s-1) evaluated at  */
+/* time 0:  w_m = prod_{j != m} (0 - t_j) / (t_m - t_j),  t_j = -k-j.       */
+/* For s = 2 this gives w = (k+1, -k), the coefficients of Eq. AT1 / AT2.   */
+/* With at_weights == 0 the delayed value is used as is, w = (1, 0, ...):   */
+/* the "standard schemes under asynchrony" configuration of Fig. 2.         */
+/* ------------------------------------------------------------------------ */
+int at_oracle_weights(int s, int k, int at_weights, double *w)
+{
+    if (s < 1 || s > 8 || k < 0) return ORC_EARG;
+    for (int m = 0; m < s; ++m) {
+        if (!at_weights) { w[m] = (m == 0) ? 1.0 : 0.0; continue; }
+        double num = 1.0, den = 1.0;
+        for (int j = 0; j < s; ++j) {
+            if (j == m) continue;
+            double tj = (double)(-k - j), tm = (double)(-k - m);
+            num *= (0.0 - tj);
+            den *= (tm - tj);
+        }
+        w[m] = num / den;
+    }
+    return ORC_OK;
+}
+
+/* Approximate one halo value from its delayed levels lev[m] = f^{n-k-m}.   */
+/* Terms with a zero weight are skipped, so that k = 0 returns lev[0]       */
+/* exactly (Sec. 3.2: for k = 0 the AT schemes are the standard schemes).   */
+double at_oracle_extrapolate(int s, int k, int at_weights, const double *lev)
+{
+    double w[8];
+    at_oracle_weights(s, k, at_weights, w);
+    double acc = 0.0;
+    for (int m = 0; m < s; ++m)
+        if (w[m] != 0.0) acc += w[m] * lev[m];
+    return acc;
+}
+
+/* Central differences of order 2 or 4 at the middle of v[0..2R]
+ * (v[R] is the point itself).  Sec. 3.2 (order 2); order 4 is the standard
+ * five-point formula. */
+int at_oracle_derivs(int order, const double *v, double dx, double *d1, double *d2)
+{
+    if (order == 2) {
+        const double *c = v + 1;
+        *d1 = (c[1] - c[-1]) / (2.0 * dx);
+        *d2 = (c[1] - 2.0 * c[0] + c[-1]) / (dx * dx);
+        return ORC_OK;
+    }
+    if (order == 4) {
+        const double *c = v + 2;
+        *d1 = (-c[2] + 8.0 * c[1] - 8.0 * c[-1] + c[-2]) / (12.0 * dx);
+        *d2 = (-c[2] + 16.0 * c[1] - 30.0 * c[0] + 16.0 * c[-1] - c[-2])
+              / (12.0 * dx * dx);
+        return ORC_OK;
+    }
+    return ORC_EARG;
+}
+
+/* ------------------------------------------------------------------------ */
+/* One run of the method.                                                    */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    int64_t N;          /* grid points of the whole domain                   */
+    int64_t P;          /* subdomains of the whole domain                    */
+    int64_t p_lo;       /* first simulated subdomain (window), 0 = all       */
+    int64_t p_count;    /* simulated subdomains; the window wraps around     */
+    int32_t order;      /* 2 or 4                                            */
+    int32_t L;          /* maximal allowable delay                           */
+    double nu, dt;      /* viscosity, time step                              */
+    double x0, dx;      /* x_i = x0 + i dx                                   */
+    double forcing_amp; /* F(x) = A sin(x)                                   */
+    int32_t eq;         /* 0: Burgers, 1: linear advection-diffusion         */
+    int32_t bc;         /* 0: periodic, 1: exact tanh travelling wave ghosts */
+    double adv_c;       /* advection speed of the linear equation            */
+    double tanh_a, tanh_c, tanh_xc; /* u = c - a tanh(a (x - xc - c t)/(2 nu)) */
+    int32_t delay_mode; /* 0: synchronous, 1: seeded, 2: replay              */
+    int32_t per_subdomain; /* one delay draw for both faces                  */
+    int32_t at_weights;    /* 1: AT extrapolation, 0: standard (negative ctl) */
+    int32_t pad_;
+    uint64_t seed;
+} at_oracle_cfg;
+
+static int64_t wrap(int64_t a, int64_t b) { int64_t r = a % b; return r < 0 ? r + b : r; }
+
+static double tanh_wave(const at_oracle_cfg *c, double x, double t)
+{
+    return c->tanh_c - c->tanh_a * tanh(c->tanh_a * (x - c->tanh_xc - c->tanh_c * t) / (2.0 * c->nu));
+}
+
+/* Runs n_steps forward-Euler steps from level 0.
+ *   u0     [p_count*M]   initial field of the window (level 0)
+ *   u_out  [p_count*M]   field at level n_steps
+ *   replay [n_steps][p_count][2]   delays for delay_mode 2 (else ignored)
+ *   hist   [L+1]         counts of the delays used (after the start-up clamp)
+ *   k_used [n_steps][p_count][2]   delays used (may be NULL)
+ * When the window is smaller than the domain it wraps onto itself; values
+ * within n_steps*R points of its ends are then meaningless, the rest exact. */
+int at_oracle_run(const at_oracle_cfg *c, int64_t n_steps, const int8_t *replay,
+                  const double *u0, double *u_out, int64_t *hist, int8_t *k_used)
+{
+    if (!c || c->N <= 0 || c->P <= 0 || c->N % c->P != 0) return ORC_EARG;
+    if (c->order != 2 && c->order != 4) return ORC_EARG;
+    if (c->L < 0 || c->L > 64 || n_steps < 0) return ORC_EARG;
+    if (c->p_count <= 0 || c->p_lo < 0 || c->p_lo + c->p_count > c->P) return ORC_EARG;
+    const int64_t M = c->N / c->P;
+    const int R = c->order / 2;        /* stencil radius                     */
+    const int s = c->order / 2 + 1;    /* time levels per halo approximation */
+    if (M < 2 * R) return ORC_EARG;
+    if (c->bc == 1 && (c->p_lo != 0 || c->p_count != c->P)) return ORC_EARG;
+    const int64_t W = c->p_count * M;  /* points simulated                   */
+    const int depth = c->L + s + 1;    /* levels n-L-s+1 .. n+1              */
+
+    double *H = (double *)calloc((size_t)depth * (size_t)W, sizeof(double));
+    if (!H) return ORC_ENOMEM;
+    memcpy(H, u0, (size_t)W * sizeof(double));
+    if (hist) memset(hist, 0, (size_t)(c->L + 1) * sizeof(int64_t));
+
+    double v[5], lev[4];
+    for (int64_t n = 0; n < n_steps; ++n) {
+        const double *cur = H + (size_t)(n % depth) * W;
+        double *nxt = H + (size_t)((n + 1) % depth) * W;
+        const double tn = (double)n * c->dt;
+        for (int64_t pl = 0; pl < c->p_count; ++pl) {
+            const int64_t pg = c->p_lo + pl;
+            /* delays of the two faces (0: left neighbour p-1, 1: right p+1) */
+            int k[2];
+            for (int f = 0; f < 2; ++f) {
+                int kr = 0;
+                if (c->delay_mode == 1)
+                    kr = at_oracle_seeded_delay(c->seed, n, pg, c->P,
+                                                c->per_subdomain ? 0 : f, 2, c->L);
+                else if (c->delay_mode == 2)
+                    kr = replay[((size_t)n * c->p_count + pl) * 2 + f];
+                if (kr < 0 || kr > c->L) { free(H); return ORC_EDELAY; }
+                /* start-up: never read a level below 0 */
+                int64_t kmax = n - s + 1; if (kmax < 0) kmax = 0;
+                k[f] = (kr < kmax) ? kr : (int)kmax;
+                if (hist) hist[k[f]] += 1;
+                if (k_used) k_used[((size_t)n * c->p_count + pl) * 2 + f] = (int8_t)k[f];
+            }
+            for (int64_t m = 0; m < M; ++m) {
+                const int64_t il = pl * M + m;   /* index in the window */
+                const int64_t ig = pg * M + m;   /* index in the domain */
+                for (int j = -R; j <= R; ++j) {
+                    const int64_t mj = m + j;
+                    if (mj >= 0 && mj < M) {     /* same subdomain: level n  */
+                        v[j + R] = cur[il + j];
+                        continue;
+                    }
+                    const int64_t gj = ig + j;
+                    if (c->bc == 1 && (gj < 0 || gj >= c->N)) {
+                        /* domain boundary: exact ghost value, undelayed */
+                        v[j + R] = tanh_wave(c, c->x0 + (double)gj * c->dx, tn);
+                        continue;
+                    }
+                    /* halo point across face f, approximated from n-k-m */
+                    const int f = (mj < 0) ? 0 : 1;
+                    const int64_t src = wrap(il + j, W);
+                    for (int q = 0; q < s; ++q) {
+                        const int64_t lv = n - k[f] - q;
+                        lev[q] = (lv >= 0) ? H[(size_t)(lv % depth) * W + src] : 0.0;
+                    }
+                    v[j + R] = at_oracle_extrapolate(s, k[f], c->at_weights, lev);
+                }
+                double d1, d2;
+                at_oracle_derivs(c->order, v, c->dx, &d1, &d2);
+                const double a = (c->eq == 0) ? v[R] : c->adv_c;
+                double rhs = -a * d1 + c->nu * d2;
+                if (c->forcing_amp != 0.0)
+                    rhs += c->forcing_amp * sin(c->x0 + (double)ig * c->dx);
+                nxt[il] = cur[il] + c->dt * rhs;
+            }
+        }
+    }
+    memcpy(u_out, H + (size_t)(n_steps % depth) * W, (size_t)W * sizeof(double));
+    free(H);
+    return ORC_OK;
+}
+
+/* Size of the configuration struct, so the caller can check its layout. */
+int64_t at_oracle_cfg_size(void) { return (int64_t)sizeof(at_oracle_cfg); }

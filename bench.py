@@ -1,0 +1,389 @@
+#!/usr/bin/env python3
+"""Benchmark: grid-point updates per second of the weakly-synchronous AT
+solver on the forced 1D Burgers workload N = 2^26 points, P = 65536
+subdomains of 1024, 4th-order stencils, L = 3, FP32 state (arXiv 1911.05769
+method; synthetic seeded initial field, 64 Fourier modes with k^-1 amplitudes).
+
+A bench step is one at_step call that advances the whole field by
+--time-steps time steps (default 1000) in one persistent kernel launch.  The
+headline arm runs free-running delays (Algorithm 2: a CTA waits only when a
+neighbour lags by more than L); the synchronous arm (grid barrier every step,
+Algorithm 1) and the seeded-delay arm are timed in the same process.
+
+Prints one JSON line (rank 0).  --impl reference times the CPU oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import at_workloads as W  # noqa: E402
+
+WORKLOAD = "burgers1d_forced_n2p26"
+METRIC = "grid-point updates/sec (GPts/s), AT vs synchronous, 1D forced Burgers N=2^26 order 4 L=3"
+UNIT = "GPts/s"
+FALLBACK_HBM = 6800.0
+KERNEL_SOURCES = ["paper_1911_05769_gb300/csrc/at_kernels.cuh", "paper_1911_05769_gb300/csrc/at_device.cuh",
+                  "paper_1911_05769_gb300/csrc/at_api.cu"]
+PROFILE = os.path.join(ROOT, "profiles", "at_stepper_f32_o4_n2p26.md")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--time-steps", type=int, default=1000, help="time steps per bench step (one launch)")
+    ap.add_argument("--dtype", default="f32", choices=["f32", "f64"])
+    ap.add_argument("--no-extra", action="store_true", help="skip the f64, e2e and CPU-baseline legs")
+    ap.add_argument("--cpu-sample-steps", type=int, default=100)
+    ap.add_argument("--cpu-sample-subdomains", type=int, default=4096)
+    ap.add_argument("--ctas", type=int, default=0, help="CTAs of the persistent kernel (0 = one per SM)")
+    ap.add_argument("--stages", type=int, default=0, help="tiles in flight per CTA (0 = default)")
+    ap.add_argument("--arms", default="free,sync,seeded", help="timed arms (free first is the headline)")
+    ap.add_argument("--N", type=int, default=0, help="smaller N for profiling runs (P scales, M stays 1024)")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+def sources_sha() -> str:
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic():
+    """Per-launch DRAM bytes of the stepper from the committed ncu summary,
+    or None if absent or taken on other kernel sources."""
+    try:
+        txt = open(PROFILE).read()
+    except OSError:
+        return None, None
+    m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+    s = re.search(r"kernel_sources_sha:\s*([0-9a-f]+)", txt)
+    if not m or not s or s.group(1) != sources_sha():
+        return None, None
+    t = re.search(r"time_steps_per_launch:\s*([0-9]+)", txt)
+    return float(m.group(1)), int(t.group(1)) if t else None
+
+
+def hbm_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(self.idx)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        loaded = [x for x in sm if smax and x > 0.5 * smax] or sm
+        return {"sm_mhz": statistics.median(loaded) if loaded else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+def dist_setup(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if ws > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "gpu" else "gloo"
+        dist.init_process_group(backend=backend)
+        pg = dist
+    return ws, rank, local, pg
+
+
+def cpu_baseline(args, u0, dt, cfg):
+    """The oracle (single thread, as it stands) on a bounded sample: a window of
+    the workload's subdomains advanced a few steps with seeded delays."""
+    import oracle
+    oracle.build()
+    N, P, M = cfg["N"], cfg["P"], cfg["N"] // cfg["P"]
+    nsub = min(args.cpu_sample_subdomains, P)
+    steps = args.cpu_sample_steps
+    u0w = np.ascontiguousarray(u0[:nsub * M], dtype=np.float64)
+    t0 = time.perf_counter()
+    oracle.run(u0w, N=N, P=P, order=cfg["order"], L=cfg["L"], nu=cfg["nu"], dt=dt, n_steps=steps,
+               forcing_amp=cfg["forcing_amp"], delay_mode=oracle.SEEDED, seed=cfg["seed"], p_lo=0, p_count=nsub)
+    el = time.perf_counter() - t0
+    upd = nsub * M * steps
+    return {"value": upd / el / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{nsub} subdomains x {M} points ({nsub * M} points) of the N=2^26 workload, "
+                      f"{steps} seeded-delay steps, FP64, single thread: {upd:.3e} updates in {el:.2f} s"}
+
+
+def reference_arm(args, ws, rank, pg):
+    """--impl reference: the CPU oracle timed on this workload, bounded sample per step."""
+    cfg = W.config(WORKLOAD)
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    N, P, M = cfg["N"], cfg["P"], cfg["N"] // cfg["P"]
+    nsub = 1024
+    full = W.initial_field(cfg)
+    _, dx = W.grid(N)
+    dt = W.dt_rule(full, dx, cfg["nu"])
+    u0 = np.ascontiguousarray(full[:nsub * M])
+    del full
+    steps_per = max(1, args.time_steps // 100)
+    kw = dict(N=N, P=P, order=cfg["order"], L=cfg["L"], nu=cfg["nu"], dt=dt, n_steps=steps_per,
+              forcing_amp=cfg["forcing_amp"], delay_mode=oracle.SEEDED, seed=cfg["seed"], p_lo=0, p_count=nsub)
+    for _ in range(args.warmup):
+        oracle.run(u0, **kw)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.run(u0, **kw)
+        times.append(time.perf_counter() - t0)
+    tot = sum(times)
+    upd = nsub * M * steps_per * args.steps
+    val = upd / tot / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "N": N, "P": P, "order": cfg["order"], "L": cfg["L"],
+                   "sample": f"{nsub} subdomains ({nsub * M} points) x {steps_per} steps per bench step"},
+        "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{nsub * M} points x {steps_per} seeded steps per bench step, single thread"},
+        "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+def gpu_arm(args, ws, rank, local, pg):
+    import torch
+
+    import paper_1911_05769_gb300 as at
+    from paper_1911_05769_gb300 import build as atbuild
+    if rank == 0:
+        atbuild.build()
+    if pg is not None:
+        pg.barrier()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    cfg = W.config(WORKLOAD)
+    if args.N:
+        cfg = dict(cfg, N=args.N, P=args.N // (cfg["N"] // cfg["P"]))
+    N, P, order, L, nu, A = cfg["N"], cfg["P"], cfg["order"], cfg["L"], cfg["nu"], cfg["forcing_amp"]
+    u0 = W.initial_field(cfg)
+    _, dx = W.grid(N)
+    dt = W.dt_rule(u0, dx, nu)
+    S = args.time_steps
+    tdt = torch.float32 if args.dtype == "f32" else torch.float64
+    wbytes = 4 if args.dtype == "f32" else 8
+    u0_dev = torch.from_numpy(u0).to(device=dev, dtype=tdt)
+    stream = torch.cuda.Stream(device=dev)
+
+    def make(dtype=args.dtype):
+        s = at.Solver(N, P, order, L, nu, dt, dtype=dtype, forcing_amp=A, seed=cfg["seed"], stream=stream,
+                      device=local, max_ctas=args.ctas, stages=args.stages)
+        return s
+
+    def barrier():
+        if pg is not None:
+            pg.barrier()
+
+    def max_over_ranks(x):
+        if pg is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        return float(t.item())
+
+    def timed_arm(mode, steps, warmup, time_steps, dtype=args.dtype, clocks=None):
+        s = make(dtype)
+        s.set_state(u0_dev if dtype == args.dtype else u0_dev.to(torch.float64 if dtype == "f64" else torch.float32))
+        for _ in range(warmup):
+            s.step(time_steps, mode)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+        torch.cuda.synchronize(dev)
+        barrier()
+        torch.cuda.synchronize(dev)
+        if clocks:
+            clocks.start()
+        with torch.cuda.stream(stream):
+            ev[0].record(stream)
+            for i in range(steps):
+                s.step(time_steps, mode)
+                ev[i + 1].record(stream)
+        torch.cuda.synchronize(dev)
+        barrier()
+        torch.cuda.synchronize(dev)
+        clk = clocks.stop() if clocks else None
+        per = [ev[i].elapsed_time(ev[i + 1]) for i in range(steps)]
+        tot = ev[0].elapsed_time(ev[steps])
+        rc = s.status()
+        if rc != at.AT_OK:
+            raise RuntimeError(f"{mode}: device status {rc}: {at.at_last_error()}")
+        info = s.info()
+        hist, m1, m2 = s.delay_stats()
+        final = s.state()
+        s.close()
+        return dict(total_ms=max_over_ranks(tot), launch_ms=per, info=info, m1=m1, m2=m2, final=final, clocks=clk)
+
+    clocks = Clocks(local)
+    arms = args.arms.split(",")
+    head = timed_arm(at.AT_FREE, args.steps, args.warmup, S, clocks=clocks)
+    sync = timed_arm(at.AT_SYNC, args.steps, args.warmup, S) if "sync" in arms else None
+    seed = timed_arm(at.AT_SEEDED, args.steps, args.warmup, S) if "seeded" in arms else None
+
+    upd_per_step = N * S
+    def gpts(r, steps=args.steps, per=upd_per_step):
+        return ws * per * steps / (r["total_ms"] * 1e-3) / 1e9
+
+    value = gpts(head)
+    ms_per_step = head["total_ms"] / args.steps
+    # equal error: AT results against the synchronous result after the same steps
+    def err_vs_sync(r):
+        if sync is None or r is None:
+            return None
+        ref = sync["final"].double()
+        return float((r["final"].double() - ref).abs().max()) / float(ref.abs().max())
+    err_free, err_seed = err_vs_sync(head), err_vs_sync(seed)
+
+    # roofline of the stepper kernel: algorithmic bytes per launch / launch time
+    M, R, s_lev = N // P, order // 2, order // 2 + 1
+    bytes_per_update = 2 * wbytes + (2 * R * wbytes + 2 * R * s_lev * wbytes) / M
+    alg_bytes = bytes_per_update * upd_per_step
+    launch_s = statistics.mean(head["launch_ms"]) * 1e-3
+    achieved = alg_bytes / launch_s / 1e9
+    peak, peak_src = hbm_peak()
+    traffic, traffic_steps = ncu_traffic()
+    if traffic is not None and traffic_steps:
+        traffic = traffic * S / traffic_steps
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": traffic, "peak_source": peak_src, "kernel": f"at_stepper<{'float' if wbytes == 4 else 'double'},4>",
+            "algorithmic_bytes_per_update": bytes_per_update}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": args.dtype, "data": "synthetic",
+        "config": {"workload": WORKLOAD, "N": N, "P": P, "M": M, "order": order, "L": L, "nu": nu,
+                   "forcing_amp": A, "dt": dt, "time_steps_per_step": S, "mode": "free",
+                   "ctas": head["info"].ctas, "stages": head["info"].stages,
+                   "l2": f"inputs larger than L2: state {N * wbytes / 2**20:.0f} MiB updated in place (no flush)",
+                   "parallelism": "replicas" if ws > 1 else "single-gpu"},
+        "gpu_launches": args.steps,
+        "gpu_launches_note": "one at_stepper launch per bench step in the headline arm",
+        "roofline": roof,
+        "clocks": head["clocks"],
+        "at_vs_sync": {
+            "free": {"value": value, "ms_per_step": ms_per_step, "mean_k": head["m1"], "mean_k2": head["m2"],
+                     "rel_linf_vs_sync": err_free},
+            "seeded": None if seed is None else {
+                "value": gpts(seed), "ms_per_step": seed["total_ms"] / args.steps, "mean_k": seed["m1"],
+                "mean_k2": seed["m2"], "rel_linf_vs_sync": err_seed},
+            "sync": None if sync is None else {"value": gpts(sync), "ms_per_step": sync["total_ms"] / args.steps},
+            "speedup_free_over_sync": None if sync is None else value / gpts(sync),
+        },
+    }
+
+    if not args.no_extra:
+        # e2e: host buffers through the C ABI, copies inside the timed region
+        s = make()
+        host_in = torch.from_numpy(u0).to(tdt).pin_memory()
+        host_out = torch.empty(N, dtype=tdt).pin_memory()
+        for _ in range(1):
+            at.at_set_state(s.h, host_in.data_ptr())
+            s.step(S, at.AT_FREE)
+            at.at_state(s.h, host_out.data_ptr())
+        e2e_steps = max(1, min(args.steps, 5))
+        barrier()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            rc = (at.at_set_state(s.h, host_in.data_ptr()), at.at_step(s.h, S, at.AT_FREE, None),
+                  at.at_state(s.h, host_out.data_ptr()))
+            if any(rc):
+                raise RuntimeError(f"e2e: {rc} {at.at_last_error()}")
+        el = max_over_ranks(time.perf_counter() - t0)
+        s.close()
+        line["e2e"] = {"value": ws * upd_per_step * e2e_steps / el / 1e9, "unit": UNIT,
+                       "h2d_bytes_per_step": N * wbytes, "d2h_bytes_per_step": N * wbytes,
+                       "steps": e2e_steps}
+        # FP64 state (FP64 arithmetic) on the same workload, fewer time steps
+        f64 = timed_arm(at.AT_FREE, 3, 2, max(1, S // 10), dtype="f64")
+        line["f64"] = {"value": ws * N * max(1, S // 10) * 3 / (f64["total_ms"] * 1e-3) / 1e9, "unit": UNIT,
+                       "time_steps_per_step": max(1, S // 10), "bound": "fp64 alu (see DESIGN)"}
+        if rank == 0 and ws == 1:
+            line["cpu_baseline"] = cpu_baseline(args, u0, dt, cfg)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        # the oracle runs on rank 0 only; other ranks exit without work
+        ws = int(os.environ.get("WORLD_SIZE", "1"))
+        rank = int(os.environ.get("RANK", "0"))
+        reference_arm(args, ws, rank, None)
+        return
+    ws, rank, local, pg = dist_setup(args)
+    gpu_arm(args, ws, rank, local, pg)
+    if pg is not None:
+        pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

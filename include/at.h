@@ -1,0 +1,171 @@
+/*
+ * at.h -- C ABI of the GB300 weakly-synchronous AT Burgers solver.
+ *
+ * The library advances the viscous Burgers' equation u_t + u u_x = nu u_xx
+ * (+ A sin x) on a periodic 1D grid with forward Euler (arXiv 1911.05769,
+ * Eq. BS and Sec. 3.2).  The grid of N points is split into P subdomains of
+ * M = N/P points, the paper's processing elements.  Interior points use the
+ * standard central stencil of order 2 or 4; points next to a subdomain
+ * boundary use asynchrony-tolerant (AT) stencils (Eq. AT1 / Eq. AT2): each
+ * halo value at level n is approximated from the neighbour's delayed levels
+ * n-k, n-k-1 (order 2) or n-k, n-k-1, n-k-2 (order 4), with 0 <= k <= L.
+ *
+ * On the GPU the subdomains are processed by the CTAs of one persistent,
+ * cooperatively launched kernel.  Halo values travel through a ring buffer of
+ * past boundary values in device memory with one progress flag per
+ * subdomain face (the device counterpart of the notified puts and circular
+ * receive buffers of Algorithm 2), so CTAs run ahead of one another by up to
+ * L steps without a grid-wide barrier.  AT_SYNC instead puts a grid barrier
+ * after every step (Algorithm 1).
+ *
+ * Memory and ownership.  The library never allocates device memory.  The
+ * caller allocates one workspace of at_workspace_bytes() bytes (device
+ * memory, 256-byte aligned) and passes it, with a CUDA stream, in at_grid.
+ * The workspace holds the state u, the ring buffers, the progress flags and
+ * the device status; it is borrowed until at_destroy().  Every call that
+ * launches work is asynchronous and ordered on that stream unless it says it
+ * synchronises.
+ *
+ * Errors.  Every int-returning call returns AT_OK (0) or a negative AT_ERR_*
+ * code and leaves a message for at_last_error() (per thread).  A device wait
+ * that exceeds timeout_ns latches AT_ERR_TIMEOUT in the workspace; every
+ * kernel then stops early and the next synchronising call (at_state,
+ * at_status, at_delay_stats) returns it.  The CUDA context stays usable.
+ */
+#ifndef AT_H
+#define AT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* return codes */
+#define AT_OK             0
+#define AT_ERR_ARG       (-1)  /* invalid argument (message says which)          */
+#define AT_ERR_UNSTABLE  (-2)  /* nu dt / dx^2 above the stability limit         */
+#define AT_ERR_RESIDENCY (-3)  /* the CTAs cannot all be resident at once        */
+#define AT_ERR_CUDA      (-4)  /* a CUDA runtime call failed                     */
+#define AT_ERR_TIMEOUT   (-5)  /* a device wait ran out of time (latched)        */
+#define AT_ERR_STATE     (-6)  /* call out of order (e.g. at_step before state)  */
+
+/* state and ring storage type (the arithmetic type of the stencil) */
+#define AT_F64 0
+#define AT_F32 1
+
+/* boundary condition */
+#define AT_BC_PERIODIC 0
+
+/* delay modes of at_step (Sec. 2 delay model; Algorithms 1 and 2) */
+#define AT_SYNC   0  /* k = 0 everywhere, grid barrier every step (Alg. 1)     */
+#define AT_SEEDED 1  /* k prescribed by SplitMix64(seed) per (n, p, face)      */
+#define AT_FREE   2  /* k = how far the neighbour lags, waiting only if > L    */
+#define AT_REPLAY 3  /* k read from a caller array                             */
+
+/* at_grid.flags */
+#define AT_FLAG_PER_SUBDOMAIN_DELAY 1  /* SEEDED: one draw for both faces       */
+#define AT_FLAG_ALLOW_UNSTABLE      2  /* skip the stability check of at_create */
+#define AT_FLAG_TEST_SKIP_PUBLISH   4  /* test only: CTA 0 stops publishing its
+                                          progress flags after level test_skip_step,
+                                          so that its neighbours' waits time out */
+
+typedef struct at_solver at_solver;   /* opaque handle */
+
+/* Problem and execution description (the "grid" argument of at_create).
+ * Zero-initialise it and set the fields that apply. */
+typedef struct at_grid {
+  int32_t  dim;             /* 1 (one-dimensional domain)                          */
+  int32_t  bc;              /* AT_BC_PERIODIC                                      */
+  int32_t  dtype;           /* AT_F64 or AT_F32                                    */
+  int32_t  flags;           /* AT_FLAG_*                                           */
+  int64_t  n[3];            /* grid points per dimension; n[0] = N                 */
+  double   length[3];       /* domain length; x_i = origin + i * length / N        */
+  double   origin[3];       /* domain origin                                       */
+  double   forcing_amp;     /* A of the forcing A sin(x); 0 = unforced (Eq. BS)    */
+  uint64_t seed;            /* seed of AT_SEEDED delays                            */
+  void    *workspace;       /* device memory, >= at_workspace_bytes(), 256-aligned */
+  size_t   workspace_bytes;
+  void    *stream;          /* cudaStream_t (NULL = legacy default stream)         */
+  int64_t  timeout_ns;      /* bound of every device wait; 0 = 1 s                 */
+  int32_t  max_ctas;        /* CTAs: 0 = one per SM; else this many (capped at P;
+                               AT_ERR_RESIDENCY if they cannot all be resident)   */
+  int32_t  stages;          /* 0 = default pipeline depth (tiles in flight per CTA)*/
+  int64_t  test_skip_step;  /* level after which AT_FLAG_TEST_SKIP_PUBLISH acts    */
+} at_grid;
+
+/* Launch facts of a solver, for tests and benchmarks. */
+typedef struct at_info {
+  int64_t N, P, M;          /* points, subdomains, points per subdomain            */
+  int32_t order, L;         /* stencil order, maximal delay                        */
+  int32_t R, s;             /* stencil radius, levels per halo approximation       */
+  int32_t T;                /* ring slots (levels kept per boundary)               */
+  int32_t ctas;             /* CTAs of the persistent kernel                       */
+  int32_t threads;          /* threads per CTA                                     */
+  int32_t stages;           /* tiles in flight per CTA                             */
+  int64_t smem_bytes;       /* dynamic shared memory per CTA                       */
+  int64_t step;             /* time level of the state (steps taken)               */
+  int32_t sm_count;         /* SMs of the device                                   */
+  int32_t dtype;            /* AT_F64 or AT_F32                                    */
+} at_info;
+
+/* Bytes of workspace needed for this problem, or 0 if the arguments are
+ * invalid (see at_last_error()).  Host only; no CUDA call. */
+size_t at_workspace_bytes(const at_grid *grid, int64_t P, int scheme_order, int L);
+
+/* Creates a solver for N = grid->n[0] points split into P subdomains, central
+ * stencils of order scheme_order (2 or 4, Sec. 3.2) with AT boundary stencils
+ * (Eq. AT1/AT2; order 4 extrapolates quadratically in time), maximal delay L
+ * (0..16, Sec. 2 and Algorithm 2), viscosity nu >= 0 and time step dt > 0.
+ * Requires N % P == 0, M = N/P a multiple of 4 with M >= 4, M*word <= 16 KiB,
+ * and nu dt / dx^2 <= 1/2 (order 2) or 3/8 (order 4) unless
+ * AT_FLAG_ALLOW_UNSTABLE.  Checks that the kernel's CTAs can be co-resident.
+ * The state is undefined until at_set_state().  *out receives the handle. */
+int at_create(const at_grid *grid, int64_t P, int scheme_order, int L,
+              double nu, double dt, at_solver **out);
+
+/* Sets the state (time level 0) from u: N contiguous words of the grid's
+ * dtype, in host or device memory.  Resets the step counter, the ring
+ * buffers, the progress flags, the delay statistics and the device status.
+ * Stream-ordered; a host source is copied before the call returns. */
+int at_set_state(at_solver *h, const void *u);
+
+/* Advances the state by n_steps >= 0 forward-Euler steps in one persistent
+ * kernel launch on the grid's stream (asynchronous).
+ *   delay_mode: AT_SYNC, AT_SEEDED, AT_FREE or AT_REPLAY.
+ *   delays:     device array int8 [n_steps][P][2] (face 0 = left neighbour
+ *               p-1, face 1 = right neighbour p+1).  AT_REPLAY reads the delays
+ *               from it (values 0..L; they are clamped to n-s+1 during start-up,
+ *               as the oracle does).  In the other modes, if not NULL, it
+ *               receives the delays actually used.  NULL is an error for
+ *               AT_REPLAY.
+ * Device waits are bounded by timeout_ns; see at_status(). */
+int at_step(at_solver *h, int64_t n_steps, int delay_mode, int8_t *delays);
+
+/* Copies the state (N words) to dst (host or device memory), waits for the
+ * stream and returns the device status: AT_OK or AT_ERR_TIMEOUT. */
+int at_state(at_solver *h, void *dst);
+
+/* Waits for the stream and returns the device status. */
+int at_status(at_solver *h);
+
+/* Delay statistics since at_set_state(): hist[0..L] counts the delays used
+ * per (level, subdomain, face); mean_k and mean_k2 are <k> and <k^2>, the
+ * moments of Eq. err_scaling.  Any pointer may be NULL.  Synchronises. */
+int at_delay_stats(at_solver *h, int64_t *hist, double *mean_k, double *mean_k2);
+
+/* Fills *info with the launch facts of the solver. */
+int at_get_info(const at_solver *h, at_info *info);
+
+/* Releases the handle (host memory only; the workspace stays the caller's). */
+int at_destroy(at_solver *h);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *at_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* AT_H */

@@ -174,15 +174,17 @@ static double tanh_wave(const at_oracle_cfg *c, double x, double t)
  *   replay [n_steps][p_count][2]   delays for delay_mode 2 (else ignored)
  *   hist   [L+1]         counts of the delays used (after the start-up clamp)
  *   k_used [n_steps][p_count][2]   delays used (may be NULL)
- * When the window is smaller than the domain it wraps onto itself; values
- * within n_steps*R points of its ends are then meaningless, the rest exact. */
+ * The window p_lo .. p_lo+p_count-1 is taken modulo P (it may run past the
+ * last subdomain).  When it is smaller than the domain its two ends are glued
+ * together; values within n_steps*R points of its ends are then meaningless,
+ * the rest exact. */
 int at_oracle_run(const at_oracle_cfg *c, int64_t n_steps, const int8_t *replay,
                   const double *u0, double *u_out, int64_t *hist, int8_t *k_used)
 {
     if (!c || c->N <= 0 || c->P <= 0 || c->N % c->P != 0) return ORC_EARG;
     if (c->order != 2 && c->order != 4) return ORC_EARG;
     if (c->L < 0 || c->L > 64 || n_steps < 0) return ORC_EARG;
-    if (c->p_count <= 0 || c->p_lo < 0 || c->p_lo + c->p_count > c->P) return ORC_EARG;
+    if (c->p_count <= 0 || c->p_lo < 0 || c->p_lo >= c->P || c->p_count > c->P) return ORC_EARG;
     const int64_t M = c->N / c->P;
     const int R = c->order / 2;        /* stencil radius                     */
     const int s = c->order / 2 + 1;    /* time levels per halo approximation */
@@ -202,7 +204,7 @@ int at_oracle_run(const at_oracle_cfg *c, int64_t n_steps, const int8_t *replay,
         double *nxt = H + (size_t)((n + 1) % depth) * W;
         const double tn = (double)n * c->dt;
         for (int64_t pl = 0; pl < c->p_count; ++pl) {
-            const int64_t pg = c->p_lo + pl;
+            const int64_t pg = (c->p_lo + pl) % c->P;   /* windows wrap */
             /* delays of the two faces (0: left neighbour p-1, 1: right p+1) */
             int k[2];
             for (int f = 0; f < 2; ++f) {

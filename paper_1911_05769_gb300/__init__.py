@@ -1,0 +1,22 @@
+"""GB300-native weakly-synchronous AT solver for viscous Burgers' equation.
+
+arXiv 1911.05769: explicit forward-Euler time-marching with asynchrony-tolerant
+finite differences at subdomain boundaries (Eq. AT1/AT2), subdomains as CTAs
+of one persistent CUDA kernel exchanging halos through ring buffers with
+progress flags (Algorithm 2), or a grid barrier every step (Algorithm 1).
+
+The compute path is the CUDA library ``libat.so`` (C ABI in ``include/at.h``);
+this package only marshals arguments to it (``binding``) and offers a small
+convenience wrapper (``Solver``) that keeps the workspace in a torch tensor.
+There is no CPU fallback: importing the binding fails if the library is
+missing.
+"""
+from .binding import (AT_BC_PERIODIC, AT_ERR_ARG, AT_ERR_CUDA, AT_ERR_RESIDENCY, AT_ERR_STATE,
+                      AT_ERR_TIMEOUT, AT_ERR_UNSTABLE, AT_F32, AT_F64, AT_FLAG_ALLOW_UNSTABLE,
+                      AT_FLAG_PER_SUBDOMAIN_DELAY, AT_FLAG_TEST_SKIP_PUBLISH, AT_FREE, AT_OK, AT_REPLAY,
+                      AT_SEEDED, AT_SYNC, AtError, at_create, at_delay_stats, at_destroy, at_get_info,
+                      at_grid, at_info, at_last_error, at_set_state, at_state, at_status, at_step,
+                      at_workspace_bytes, library_path)
+from .solver import Solver
+
+__all__ = [n for n in dir() if n.startswith(("AT_", "at_"))] + ["AtError", "Solver", "library_path"]

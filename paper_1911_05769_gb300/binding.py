@@ -1,0 +1,159 @@
+"""ctypes binding of the C ABI in ``include/at.h`` -- argument marshalling only.
+
+Every function has the name and the argument order of its C counterpart and
+returns the C return code.  Pointers are plain integers (device or host
+addresses, e.g. ``tensor.data_ptr()``).  The library is loaded on first use;
+if ``libat.so`` has not been built, the first call raises ``RuntimeError``
+(there is no CPU fallback).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(HERE, "libat.so")
+_lock = threading.Lock()
+_lib = None
+
+AT_OK = 0
+AT_ERR_ARG = -1
+AT_ERR_UNSTABLE = -2
+AT_ERR_RESIDENCY = -3
+AT_ERR_CUDA = -4
+AT_ERR_TIMEOUT = -5
+AT_ERR_STATE = -6
+
+AT_F64 = 0
+AT_F32 = 1
+AT_BC_PERIODIC = 0
+
+AT_SYNC = 0
+AT_SEEDED = 1
+AT_FREE = 2
+AT_REPLAY = 3
+
+AT_FLAG_PER_SUBDOMAIN_DELAY = 1
+AT_FLAG_ALLOW_UNSTABLE = 2
+AT_FLAG_TEST_SKIP_PUBLISH = 4
+
+
+class at_grid(ctypes.Structure):
+    _fields_ = [
+        ("dim", ctypes.c_int32), ("bc", ctypes.c_int32), ("dtype", ctypes.c_int32), ("flags", ctypes.c_int32),
+        ("n", ctypes.c_int64 * 3), ("length", ctypes.c_double * 3), ("origin", ctypes.c_double * 3),
+        ("forcing_amp", ctypes.c_double), ("seed", ctypes.c_uint64),
+        ("workspace", ctypes.c_void_p), ("workspace_bytes", ctypes.c_size_t), ("stream", ctypes.c_void_p),
+        ("timeout_ns", ctypes.c_int64), ("max_ctas", ctypes.c_int32), ("stages", ctypes.c_int32),
+        ("test_skip_step", ctypes.c_int64),
+    ]
+
+
+class at_info(ctypes.Structure):
+    _fields_ = [
+        ("N", ctypes.c_int64), ("P", ctypes.c_int64), ("M", ctypes.c_int64),
+        ("order", ctypes.c_int32), ("L", ctypes.c_int32), ("R", ctypes.c_int32), ("s", ctypes.c_int32),
+        ("T", ctypes.c_int32), ("ctas", ctypes.c_int32), ("threads", ctypes.c_int32), ("stages", ctypes.c_int32),
+        ("smem_bytes", ctypes.c_int64), ("step", ctypes.c_int64), ("sm_count", ctypes.c_int32),
+        ("dtype", ctypes.c_int32),
+    ]
+
+
+# (name, restype, argtypes) of every exported entry point
+_SIGNATURES = [
+    ("at_workspace_bytes", ctypes.c_size_t,
+     [ctypes.POINTER(at_grid), ctypes.c_int64, ctypes.c_int, ctypes.c_int]),
+    ("at_create", ctypes.c_int,
+     [ctypes.POINTER(at_grid), ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+      ctypes.POINTER(ctypes.c_void_p)]),
+    ("at_set_state", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    ("at_step", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p]),
+    ("at_state", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    ("at_status", ctypes.c_int, [ctypes.c_void_p]),
+    ("at_delay_stats", ctypes.c_int,
+     [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double),
+      ctypes.POINTER(ctypes.c_double)]),
+    ("at_get_info", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(at_info)]),
+    ("at_destroy", ctypes.c_int, [ctypes.c_void_p]),
+    ("at_last_error", ctypes.c_char_p, []),
+]
+
+EXPORTED = [s[0] for s in _SIGNATURES]
+
+
+def library_path() -> str:
+    return _LIB_PATH
+
+
+def lib():
+    """The loaded CUDA library; raises if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(_LIB_PATH):
+                raise RuntimeError(f"CUDA library {_LIB_PATH} is missing: run "
+                                   "`python -m paper_1911_05769_gb300.build` (no CPU fallback exists)")
+            L = ctypes.CDLL(_LIB_PATH)
+            for name, res, args in _SIGNATURES:
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+class AtError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__(f"{what} failed with {code}: {at_last_error()}")
+        self.code = code
+
+
+def at_workspace_bytes(grid: at_grid, P: int, scheme_order: int, L: int) -> int:
+    return int(lib().at_workspace_bytes(ctypes.byref(grid), P, scheme_order, L))
+
+
+def at_create(grid: at_grid, P: int, scheme_order: int, L: int, nu: float, dt: float):
+    """Returns (code, handle)."""
+    h = ctypes.c_void_p()
+    rc = lib().at_create(ctypes.byref(grid), P, scheme_order, L, nu, dt, ctypes.byref(h))
+    return rc, h
+
+
+def at_set_state(h, u_ptr: int) -> int:
+    return lib().at_set_state(h, ctypes.c_void_p(u_ptr))
+
+
+def at_step(h, n_steps: int, delay_mode: int, delays_ptr: int | None = None) -> int:
+    return lib().at_step(h, n_steps, delay_mode, ctypes.c_void_p(delays_ptr) if delays_ptr else None)
+
+
+def at_state(h, dst_ptr: int) -> int:
+    return lib().at_state(h, ctypes.c_void_p(dst_ptr))
+
+
+def at_status(h) -> int:
+    return lib().at_status(h)
+
+
+def at_delay_stats(h, L: int):
+    """Returns (code, hist[L+1] list, mean_k, mean_k2)."""
+    hist = (ctypes.c_int64 * (L + 1))()
+    m1, m2 = ctypes.c_double(), ctypes.c_double()
+    rc = lib().at_delay_stats(h, hist, ctypes.byref(m1), ctypes.byref(m2))
+    return rc, list(hist), m1.value, m2.value
+
+
+def at_get_info(h):
+    info = at_info()
+    rc = lib().at_get_info(h, ctypes.byref(info))
+    return rc, info
+
+
+def at_destroy(h) -> int:
+    return lib().at_destroy(h)
+
+
+def at_last_error() -> str:
+    s = lib().at_last_error()
+    return s.decode() if s else ""

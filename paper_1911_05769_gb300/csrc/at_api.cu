@@ -1,0 +1,357 @@
+// at_api.cu -- host side of the C ABI declared in include/at.h.
+//
+// Validates arguments, carves the caller's workspace, chooses the launch shape
+// of the persistent kernel (one CTA per SM, cooperative launch so that every
+// CTA is resident and the bounded waits between CTAs always make progress),
+// and launches the kernels on the caller's stream.  No device memory is
+// allocated here.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "at.h"
+#include "at_kernels.cuh"
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+int fail(int code, const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char *what)
+{
+    if (e == cudaErrorCooperativeLaunchTooLarge)
+        return fail(AT_ERR_RESIDENCY, "%s: %s", what, cudaGetErrorString(e));
+    return fail(AT_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+int ring_slots(int L, int s)
+{
+    // A neighbour runs at most L+1 levels ahead of a consumer that reads back
+    // to level n-L-s+1, so 2L+s+1 levels are live; round up to a power of 2.
+    int need = 2 * L + s + 1, T = 1;
+    while (T < need) T <<= 1;
+    return T;
+}
+
+struct Layout {
+    size_t u, ring, flag, ctrl, hist, gbar, total;
+};
+
+Layout layout(int64_t N, int64_t P, int w, int L, int T)
+{
+    Layout l{};
+    size_t off = 0;
+    l.u = off;    off = align_up(off + (size_t)N * w, 256);
+    l.ring = off; off = align_up(off + (size_t)T * P * 2 * atk::kRingEntry, 256);
+    l.flag = off; off = align_up(off + (size_t)P * 2 * 8, 256);
+    l.ctrl = off; off = align_up(off + atk::kCtrlWords * 4, 256);
+    l.hist = off; off = align_up(off + (size_t)(L + 1) * 8, 256);
+    l.gbar = off; off = align_up(off + 8, 256);
+    l.total = off;
+    return l;
+}
+
+int check_args(const at_grid *g, int64_t P, int order, int L)
+{
+    if (!g) return fail(AT_ERR_ARG, "grid is NULL");
+    if (g->dim != 1) return fail(AT_ERR_ARG, "dim must be 1");
+    if (g->bc != AT_BC_PERIODIC) return fail(AT_ERR_ARG, "bc must be AT_BC_PERIODIC");
+    if (g->dtype != AT_F64 && g->dtype != AT_F32) return fail(AT_ERR_ARG, "dtype must be AT_F64 or AT_F32");
+    const int64_t N = g->n[0];
+    if (N <= 0) return fail(AT_ERR_ARG, "n[0] must be positive");
+    if (P <= 0 || N % P != 0) return fail(AT_ERR_ARG, "N %% P != 0 (N=%lld, P=%lld)", (long long)N, (long long)P);
+    if (order != 2 && order != 4) return fail(AT_ERR_ARG, "scheme_order must be 2 or 4");
+    if (L < 0 || L > atk::kMaxL) return fail(AT_ERR_ARG, "L must be in 0..%d", atk::kMaxL);
+    const int64_t M = N / P;
+    const int w = g->dtype == AT_F64 ? 8 : 4;
+    if (M % 4 != 0 || M < 4) return fail(AT_ERR_ARG, "M = N/P must be a multiple of 4 (M=%lld)", (long long)M);
+    if (M * w > 16384) return fail(AT_ERR_ARG, "M * word size must be <= 16 KiB (M=%lld)", (long long)M);
+    if (!(g->length[0] > 0.0)) return fail(AT_ERR_ARG, "length[0] must be positive");
+    return AT_OK;
+}
+
+}  // namespace
+
+struct at_solver {
+    at_grid g;
+    int64_t N, P, M;
+    int order, L, R, s, T, w;
+    double nu, dt, dx;
+    Layout lay;
+    unsigned char *ws;
+    cudaStream_t stream;
+    int device, sm_count;
+    int G, stages, stage_bytes, stage_off, tab_off, smem;
+    int64_t step;
+    unsigned long long gbar_count;
+    bool has_state;
+    void *kernel;
+    void *init_kernel;
+};
+
+extern "C" {
+
+const char *at_last_error(void) { return g_err; }
+
+size_t at_workspace_bytes(const at_grid *grid, int64_t P, int scheme_order, int L)
+{
+    if (check_args(grid, P, scheme_order, L) != AT_OK) return 0;
+    const int w = grid->dtype == AT_F64 ? 8 : 4;
+    const int s = scheme_order / 2 + 1;
+    return layout(grid->n[0], P, w, L, ring_slots(L, s)).total;
+}
+
+int at_create(const at_grid *grid, int64_t P, int scheme_order, int L, double nu, double dt, at_solver **out)
+{
+    g_err[0] = 0;
+    if (!out) return fail(AT_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    int rc = check_args(grid, P, scheme_order, L);
+    if (rc != AT_OK) return rc;
+    if (!(dt > 0.0) || !std::isfinite(dt)) return fail(AT_ERR_ARG, "dt must be positive");
+    if (!(nu >= 0.0) || !std::isfinite(nu)) return fail(AT_ERR_ARG, "nu must be >= 0");
+    const int64_t N = grid->n[0];
+    const double dx = grid->length[0] / (double)N;
+    const double lim = scheme_order == 2 ? 0.5 : 0.375;   // forward Euler, pure diffusion
+    if (!(grid->flags & AT_FLAG_ALLOW_UNSTABLE) && nu * dt / (dx * dx) > lim)
+        return fail(AT_ERR_UNSTABLE, "nu*dt/dx^2 = %g exceeds %g", nu * dt / (dx * dx), lim);
+    const int w = grid->dtype == AT_F64 ? 8 : 4;
+    const int s = scheme_order / 2 + 1;
+    const int T = ring_slots(L, s);
+    const Layout lay = layout(N, P, w, L, T);
+    if (!grid->workspace) return fail(AT_ERR_ARG, "workspace is NULL");
+    if (grid->workspace_bytes < lay.total)
+        return fail(AT_ERR_ARG, "workspace too small: %zu < %zu", grid->workspace_bytes, lay.total);
+    if (reinterpret_cast<uintptr_t>(grid->workspace) % 256 != 0)
+        return fail(AT_ERR_ARG, "workspace must be 256-byte aligned");
+
+    int dev = 0, sms = 0, coop = 0, smem_optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (!coop) return fail(AT_ERR_RESIDENCY, "device does not support cooperative launch");
+
+    at_solver *h = new (std::nothrow) at_solver();
+    if (!h) return fail(AT_ERR_ARG, "out of host memory");
+    h->g = *grid;
+    if (h->g.timeout_ns <= 0) h->g.timeout_ns = 1000000000ll;
+    h->N = N; h->P = P; h->M = N / P;
+    h->order = scheme_order; h->L = L; h->R = scheme_order / 2; h->s = s; h->T = T; h->w = w;
+    h->nu = nu; h->dt = dt; h->dx = dx;
+    h->lay = lay;
+    h->ws = static_cast<unsigned char *>(grid->workspace);
+    h->stream = static_cast<cudaStream_t>(grid->stream);
+    h->device = dev; h->sm_count = sms;
+
+    if (w == 8) {
+        h->kernel = scheme_order == 2 ? (void *)atk::at_stepper<double, 2> : (void *)atk::at_stepper<double, 4>;
+        h->init_kernel = scheme_order == 2 ? (void *)atk::at_init<double, 1> : (void *)atk::at_init<double, 2>;
+    } else {
+        h->kernel = scheme_order == 2 ? (void *)atk::at_stepper<float, 2> : (void *)atk::at_stepper<float, 4>;
+        h->init_kernel = scheme_order == 2 ? (void *)atk::at_init<float, 1> : (void *)atk::at_init<float, 2>;
+    }
+
+    // launch shape: one CTA per SM by default (max_ctas overrides, e.g. two
+    // per SM), at most one per subdomain; stages sized to shared memory
+    int G = grid->max_ctas > 0 ? grid->max_ctas : sms;
+    if (P < G) G = (int)P;
+    int stages = grid->stages > 0 ? grid->stages : (w == 4 ? 16 : 12);
+    const int stage_bytes = (int)align_up(atk::kTileOff + (size_t)h->M * w, 128);
+    const int64_t Smax = (P + G - 1) / G;
+    const size_t tab_bytes = grid->forcing_amp != 0.0 ? (size_t)(2 * h->M + 2 * Smax) * w : 0;
+    auto smem_for = [&](int st) {
+        const size_t off = align_up((size_t)16 * st + atk::kMiscBytes, 128);
+        return off + (size_t)st * stage_bytes + tab_bytes;
+    };
+    while (stages > 1 && smem_for(stages) > (size_t)smem_optin) --stages;
+    if (smem_for(stages) > (size_t)smem_optin) {
+        delete h;
+        return fail(AT_ERR_RESIDENCY, "shared memory %zu exceeds %d", smem_for(stages), smem_optin);
+    }
+    h->stages = stages;
+    h->stage_bytes = stage_bytes;
+    h->stage_off = (int)align_up((size_t)16 * stages + atk::kMiscBytes, 128);
+    h->tab_off = h->stage_off + stages * stage_bytes;
+    h->smem = (int)smem_for(stages);
+    e = cudaFuncSetAttribute(h->kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, h->smem);
+    if (e != cudaSuccess) { delete h; return cuda_fail(e, "cudaFuncSetAttribute"); }
+    int occ = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, h->kernel, atk::kThreads, h->smem);
+    if (e != cudaSuccess) { delete h; return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor"); }
+    if (occ < 1 || (int64_t)occ * sms < G) {
+        delete h;
+        return fail(AT_ERR_RESIDENCY, "%d CTAs cannot be co-resident (occupancy %d per SM)", G, occ);
+    }
+    h->G = G;
+    h->step = 0;
+    h->gbar_count = 0;
+    h->has_state = false;
+    *out = h;
+    return AT_OK;
+}
+
+static atk::Params make_params(const at_solver *h)
+{
+    atk::Params p{};
+    p.u = h->ws + h->lay.u;
+    p.ring = h->ws + h->lay.ring;
+    p.flag = reinterpret_cast<unsigned long long *>(h->ws + h->lay.flag);
+    p.ctrl = reinterpret_cast<int *>(h->ws + h->lay.ctrl);
+    p.hist = reinterpret_cast<unsigned long long *>(h->ws + h->lay.hist);
+    p.gbar = reinterpret_cast<unsigned long long *>(h->ws + h->lay.gbar);
+    p.N = h->N; p.P = h->P; p.M = h->M;
+    p.L = h->L; p.T = h->T;
+    p.per_sub = (h->g.flags & AT_FLAG_PER_SUBDOMAIN_DELAY) ? 1 : 0;
+    p.seed = h->g.seed;
+    if (h->order == 2) {
+        p.cA = h->dt / (2.0 * h->dx);
+        p.cB = h->nu * h->dt / (h->dx * h->dx);
+    } else {
+        p.cA = h->dt / (12.0 * h->dx);
+        p.cB = h->nu * h->dt / (12.0 * h->dx * h->dx);
+    }
+    p.dtA = h->dt * h->g.forcing_amp;
+    p.forcing = h->g.forcing_amp != 0.0 ? 1 : 0;
+    p.x0 = h->g.origin[0];
+    p.dx = h->dx;
+    p.G = h->G;
+    p.stages = h->stages;
+    p.stage_bytes = h->stage_bytes;
+    p.stage_off = h->stage_off;
+    p.tab_off = h->tab_off;
+    p.timeout_ns = h->g.timeout_ns;
+    p.skip_publish = (h->g.flags & AT_FLAG_TEST_SKIP_PUBLISH) ? 1 : 0;
+    p.skip_step = h->g.test_skip_step;
+    return p;
+}
+
+int at_set_state(at_solver *h, const void *u)
+{
+    g_err[0] = 0;
+    if (!h || !u) return fail(AT_ERR_ARG, "NULL argument");
+    cudaError_t e = cudaMemcpyAsync(h->ws + h->lay.u, u, (size_t)h->N * h->w, cudaMemcpyDefault, h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(state)");
+    e = cudaMemsetAsync(h->ws + h->lay.ring, 0, (size_t)h->T * h->P * 2 * atk::kRingEntry, h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(ring)");
+    atk::Params p = make_params(h);
+    void *args[] = {&p};
+    const int blocks = (int)((h->P + 255) / 256 < 1024 ? (h->P + 255) / 256 : 1024);
+    e = cudaLaunchKernel(h->init_kernel, dim3(blocks), dim3(256), args, 0, h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "launch at_init");
+    h->step = 0;
+    h->gbar_count = 0;
+    h->has_state = true;
+    return AT_OK;
+}
+
+int at_step(at_solver *h, int64_t n_steps, int delay_mode, int8_t *delays)
+{
+    g_err[0] = 0;
+    if (!h) return fail(AT_ERR_ARG, "NULL handle");
+    if (!h->has_state) return fail(AT_ERR_STATE, "at_step before at_set_state");
+    if (n_steps < 0) return fail(AT_ERR_ARG, "n_steps < 0");
+    if (delay_mode < AT_SYNC || delay_mode > AT_REPLAY) return fail(AT_ERR_ARG, "bad delay_mode %d", delay_mode);
+    if (delay_mode == AT_REPLAY && !delays) return fail(AT_ERR_ARG, "AT_REPLAY needs a delays array");
+    if (n_steps == 0) return AT_OK;
+    atk::Params p = make_params(h);
+    p.mode = delay_mode;
+    p.delays = delays;
+    p.n0 = h->step;
+    p.n_steps = n_steps;
+    p.gbar_base = h->gbar_count;
+    void *args[] = {&p};
+    cudaError_t e = cudaLaunchCooperativeKernel(h->kernel, dim3(h->G), dim3(atk::kThreads), args, (size_t)h->smem,
+                                                h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaLaunchCooperativeKernel(at_stepper)");
+    h->step += n_steps;
+    if (delay_mode == AT_SYNC) h->gbar_count += (unsigned long long)n_steps * (unsigned long long)h->G;
+    return AT_OK;
+}
+
+static int read_status(at_solver *h)
+{
+    int ctrl[atk::kCtrlWords];
+    cudaError_t e = cudaMemcpyAsync(ctrl, h->ws + h->lay.ctrl, sizeof(ctrl), cudaMemcpyDeviceToHost, h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(status)");
+    e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    if (ctrl[atk::kCtrlStatus] == atk::kStatusTimeout)
+        return fail(AT_ERR_TIMEOUT, "device wait timed out (cta %d, where %d, step %d, neighbour %d)",
+                    ctrl[atk::kCtrlCta], ctrl[atk::kCtrlWhere], ctrl[atk::kCtrlStep], ctrl[atk::kCtrlNb]);
+    if (ctrl[atk::kCtrlStatus] != 0) return fail(AT_ERR_CUDA, "device status %d", ctrl[atk::kCtrlStatus]);
+    return AT_OK;
+}
+
+int at_state(at_solver *h, void *dst)
+{
+    g_err[0] = 0;
+    if (!h || !dst) return fail(AT_ERR_ARG, "NULL argument");
+    if (!h->has_state) return fail(AT_ERR_STATE, "at_state before at_set_state");
+    cudaError_t e = cudaMemcpyAsync(dst, h->ws + h->lay.u, (size_t)h->N * h->w, cudaMemcpyDefault, h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(state out)");
+    return read_status(h);
+}
+
+int at_status(at_solver *h)
+{
+    g_err[0] = 0;
+    if (!h) return fail(AT_ERR_ARG, "NULL handle");
+    return read_status(h);
+}
+
+int at_delay_stats(at_solver *h, int64_t *hist, double *mean_k, double *mean_k2)
+{
+    g_err[0] = 0;
+    if (!h) return fail(AT_ERR_ARG, "NULL handle");
+    unsigned long long cnt[atk::kMaxL + 1] = {0};
+    cudaError_t e = cudaMemcpyAsync(cnt, h->ws + h->lay.hist, (size_t)(h->L + 1) * 8, cudaMemcpyDeviceToHost,
+                                    h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(hist)");
+    const int rc = read_status(h);
+    double tot = 0, m1 = 0, m2 = 0;
+    for (int k = 0; k <= h->L; ++k) {
+        if (hist) hist[k] = (int64_t)cnt[k];
+        tot += (double)cnt[k];
+        m1 += (double)k * (double)cnt[k];
+        m2 += (double)k * k * (double)cnt[k];
+    }
+    if (mean_k) *mean_k = tot > 0 ? m1 / tot : 0.0;
+    if (mean_k2) *mean_k2 = tot > 0 ? m2 / tot : 0.0;
+    return rc;
+}
+
+int at_get_info(const at_solver *h, at_info *info)
+{
+    if (!h || !info) return fail(AT_ERR_ARG, "NULL argument");
+    std::memset(info, 0, sizeof(*info));
+    info->N = h->N; info->P = h->P; info->M = h->M;
+    info->order = h->order; info->L = h->L; info->R = h->R; info->s = h->s; info->T = h->T;
+    info->ctas = h->G; info->threads = atk::kThreads; info->stages = h->stages;
+    info->smem_bytes = h->smem; info->step = h->step; info->sm_count = h->sm_count;
+    info->dtype = h->g.dtype;
+    return AT_OK;
+}
+
+int at_destroy(at_solver *h)
+{
+    delete h;
+    return AT_OK;
+}
+
+}  // extern "C"

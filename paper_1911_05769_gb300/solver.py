@@ -1,0 +1,119 @@
+"""Convenience wrapper over the C ABI: the workspace lives in a torch tensor.
+
+torch provides only device memory and the stream; every step of the method
+runs in the CUDA library.
+"""
+from __future__ import annotations
+
+import math
+
+from . import binding as B
+
+
+class Solver:
+    """One 1D problem: N points, P subdomains, order 2|4, maximal delay L.
+
+    ``dtype`` is "f64" or "f32".  ``stream`` defaults to torch's current
+    stream on the current device.
+    """
+
+    def __init__(self, N, P, order, L, nu, dt, *, dtype="f64", length=2 * math.pi, origin=0.0,
+                 forcing_amp=0.0, seed=0, flags=0, timeout_ns=0, max_ctas=0, stages=0,
+                 test_skip_step=0, stream=None, device=None):
+        import torch
+        self.torch = torch
+        dev = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        self.device = dev
+        self.stream = stream if stream is not None else torch.cuda.current_stream(dev)
+        self.tdtype = torch.float64 if dtype == "f64" else torch.float32
+        g = B.at_grid()
+        g.dim, g.bc = 1, B.AT_BC_PERIODIC
+        g.dtype = B.AT_F64 if dtype == "f64" else B.AT_F32
+        g.flags = flags
+        g.n[0], g.n[1], g.n[2] = N, 1, 1
+        g.length[0] = length
+        g.origin[0] = origin
+        g.forcing_amp = forcing_amp
+        g.seed = seed & (2 ** 64 - 1)
+        g.timeout_ns = timeout_ns
+        g.max_ctas = max_ctas
+        g.stages = stages
+        g.test_skip_step = test_skip_step
+        nbytes = B.at_workspace_bytes(g, P, order, L)
+        if nbytes == 0:
+            raise B.AtError(B.AT_ERR_ARG, "at_workspace_bytes")
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+        g.workspace = self.workspace.data_ptr()
+        g.workspace_bytes = nbytes
+        g.stream = self.stream.cuda_stream
+        self.grid = g
+        rc, h = B.at_create(g, P, order, L, nu, dt)
+        if rc != B.AT_OK:
+            raise B.AtError(rc, "at_create")
+        self.h = h
+        self.N, self.P, self.order, self.L = N, P, order, L
+
+    def info(self):
+        rc, info = B.at_get_info(self.h)
+        if rc != B.AT_OK:
+            raise B.AtError(rc, "at_get_info")
+        return info
+
+    def set_state(self, u):
+        """u: torch tensor (device or host) or numpy array of N words."""
+        t = self._as_tensor(u)
+        rc = B.at_set_state(self.h, t.data_ptr())
+        if rc != B.AT_OK:
+            raise B.AtError(rc, "at_set_state")
+        self._keep = t     # keep a host source alive until the stream passes the copy
+
+    def step(self, n_steps, mode=B.AT_SEEDED, delays=None):
+        """delays: int8 device tensor [n_steps, P, 2] (input for REPLAY, record otherwise)."""
+        ptr = None
+        if delays is not None:
+            assert delays.dtype == self.torch.int8 and delays.is_cuda and delays.is_contiguous()
+            assert delays.numel() == n_steps * self.P * 2
+            ptr = delays.data_ptr()
+        rc = B.at_step(self.h, n_steps, mode, ptr)
+        if rc != B.AT_OK:
+            raise B.AtError(rc, "at_step")
+
+    def state(self, out=None):
+        """Copies the state into ``out`` (new device tensor by default); raises on a device timeout."""
+        if out is None:
+            out = self.torch.empty(self.N, dtype=self.tdtype, device=self.device)
+        rc = B.at_state(self.h, out.data_ptr())
+        if rc != B.AT_OK:
+            raise B.AtError(rc, "at_state")
+        return out
+
+    def status(self):
+        return B.at_status(self.h)
+
+    def delay_stats(self):
+        rc, hist, m1, m2 = B.at_delay_stats(self.h, self.L)
+        if rc != B.AT_OK:
+            raise B.AtError(rc, "at_delay_stats")
+        return hist, m1, m2
+
+    def close(self):
+        if getattr(self, "h", None) is not None:
+            B.at_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _as_tensor(self, u):
+        torch = self.torch
+        if not isinstance(u, torch.Tensor):
+            u = torch.from_numpy(u)
+        if u.dtype != self.tdtype:
+            u = u.to(self.tdtype)
+        u = u.contiguous()
+        if u.numel() != self.N:
+            raise ValueError(f"state needs {self.N} values, got {u.numel()}")
+        return u

@@ -1,0 +1,133 @@
+"""C ABI checks that need no GPU: the library builds for sm_103a, loads, exports
+every entry point include/at.h declares, its structs have the layout the
+binding assumes, and host-side argument validation rejects bad input."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "at.h")
+
+
+@pytest.fixture(scope="module")
+def B():
+    from paper_1911_05769_gb300 import build
+    build.build()
+    from paper_1911_05769_gb300 import binding
+    binding.lib()
+    return binding
+
+
+def _declared_functions():
+    txt = open(HEADER).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b(at_\w+)\s*\(", txt, flags=re.M)))
+
+
+def test_header_declares_the_abi():
+    names = _declared_functions()
+    for must in ("at_create", "at_step", "at_state", "at_destroy", "at_set_state", "at_workspace_bytes",
+                 "at_status", "at_delay_stats", "at_get_info", "at_last_error"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(B):
+    out = subprocess.check_output(["nm", "-D", "--defined-only", B.library_path()], text=True)
+    exported = set(re.findall(r"\sT\s+(at_\w+)$", out, flags=re.M))
+    declared = set(_declared_functions())
+    assert declared <= exported, declared - exported
+    assert exported <= declared, exported - declared
+    assert set(B.EXPORTED) == declared
+    lib = B.lib()
+    for name in declared:
+        assert getattr(lib, name) is not None
+
+
+_LAYOUT_C = r"""
+#include <stdio.h>
+#include <stddef.h>
+#include "at.h"
+#define F(S, m) printf(#S " " #m " %zu\n", offsetof(S, m))
+int main(void) {
+  printf("at_grid size %zu\n", sizeof(at_grid));
+  F(at_grid, dim); F(at_grid, bc); F(at_grid, dtype); F(at_grid, flags); F(at_grid, n); F(at_grid, length);
+  F(at_grid, origin); F(at_grid, forcing_amp); F(at_grid, seed); F(at_grid, workspace);
+  F(at_grid, workspace_bytes); F(at_grid, stream); F(at_grid, timeout_ns); F(at_grid, max_ctas);
+  F(at_grid, stages); F(at_grid, test_skip_step);
+  printf("at_info size %zu\n", sizeof(at_info));
+  F(at_info, N); F(at_info, P); F(at_info, M); F(at_info, order); F(at_info, L); F(at_info, R); F(at_info, s);
+  F(at_info, T); F(at_info, ctas); F(at_info, threads); F(at_info, stages); F(at_info, smem_bytes);
+  F(at_info, step); F(at_info, sm_count); F(at_info, dtype);
+  return 0;
+}
+"""
+
+
+def test_struct_layout_matches_binding(B, tmp_path):
+    src = tmp_path / "layout.c"
+    src.write_text(_LAYOUT_C)
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    lines = subprocess.check_output([str(exe)], text=True).split("\n")
+    for line in lines:
+        if not line.strip():
+            continue
+        sname, field, val = line.split()
+        cls = getattr(B, sname)
+        if field == "size":
+            assert ctypes.sizeof(cls) == int(val), line
+        else:
+            assert getattr(cls, field).offset == int(val), line
+
+
+def _grid(B, N=4096, dtype=None, length=6.283185307179586):
+    g = B.at_grid()
+    g.dim, g.bc = 1, B.AT_BC_PERIODIC
+    g.dtype = B.AT_F64 if dtype is None else dtype
+    g.n[0], g.n[1], g.n[2] = N, 1, 1
+    g.length[0] = length
+    return g
+
+
+def test_workspace_bytes_and_validation(B):
+    g = _grid(B)
+    nb = B.at_workspace_bytes(g, 16, 2, 2)
+    # state + ring + flags + control at least
+    assert nb >= 4096 * 8 + 8 * 16 * 2 * 16 + 16 * 2 * 8
+    assert nb % 256 == 0
+    assert B.at_workspace_bytes(g, 3, 2, 2) == 0 and "N % P" in B.at_last_error()
+    assert B.at_workspace_bytes(g, 16, 3, 2) == 0 and "order" in B.at_last_error()
+    assert B.at_workspace_bytes(g, 16, 2, 17) == 0 and "L must" in B.at_last_error()
+    assert B.at_workspace_bytes(_grid(B, N=4096 + 16 * 2), 16, 2, 2) == 0   # M = 258
+    assert B.at_workspace_bytes(_grid(B, dtype=7), 16, 2, 2) == 0
+    g.dim = 3
+    assert B.at_workspace_bytes(g, 16, 2, 2) == 0
+
+
+def test_create_rejects_bad_arguments_on_the_host(B):
+    g = _grid(B)
+    dx = 6.283185307179586 / 4096
+    rc, h = B.at_create(g, 16, 2, 2, 0.02, 1e-6)       # no workspace
+    assert rc == B.AT_ERR_ARG and not h.value
+    rc, _ = B.at_create(g, 16, 2, 2, 0.02, -1.0)
+    assert rc == B.AT_ERR_ARG
+    rc, _ = B.at_create(g, 16, 2, 2, -0.1, 1e-6)
+    assert rc == B.AT_ERR_ARG
+    rc, _ = B.at_create(g, 16, 2, 2, 0.02, 0.6 * dx * dx / 0.02)   # nu dt/dx^2 = 0.6 > 1/2
+    assert rc == B.AT_ERR_UNSTABLE
+    rc, _ = B.at_create(g, 16, 4, 2, 0.02, 0.4 * dx * dx / 0.02)   # 0.4 > 3/8 for order 4
+    assert rc == B.AT_ERR_UNSTABLE
+
+
+def test_product_path_has_no_cpu_fallback():
+    """The package refuses to run without the CUDA library and never imports
+    the oracle."""
+    import paper_1911_05769_gb300 as pkg
+    src_dir = os.path.dirname(pkg.__file__)
+    for name in os.listdir(src_dir):
+        if name.endswith(".py"):
+            text = open(os.path.join(src_dir, name)).read()
+            assert "import oracle" not in text and "from oracle" not in text, name

@@ -1,0 +1,181 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Bars: relative L-inf <= 1e-12 for FP64 state, <= 1e-5 for FP32 state; delays
+(integers) bit-exact.  FP32 cases keep the step count where round-to-nearest
+FP32 state stays within 1e-5 of the FP64 result (a few hundred steps at these
+sizes; the drift is a property of FP32 storage, not of the method).
+"""
+import numpy as np
+import pytest
+
+import at_workloads as W
+import oracle
+from gpu_util import TOL, gpu_run, oracle_run, rel_linf
+
+pytestmark = pytest.mark.gpu
+
+
+def _setup(N, nu, kind="two_modes", seed=2):
+    u0 = W.u0_two_modes(N) if kind == "two_modes" else W.u0_fourier(N, modes=64, seed=seed)
+    _, dx = W.grid(N)
+    return u0, W.dt_rule(u0, dx, nu)
+
+
+def test_burgers1d_n4096_seeded_fp64(require_gpu):
+    """N=4096, P=16, order 2, L=2, seeded delays (seed 1), 1000 steps, FP64."""
+    from paper_1911_05769_gb300 import AT_SEEDED
+    cfg = W.config("burgers1d_n4096")
+    u0 = W.initial_field(cfg)
+    _, dx = W.grid(cfg["N"])
+    dt = W.dt_rule(u0, dx, cfg["nu"])
+    kw = dict(P=cfg["P"], order=cfg["order"], L=cfg["L"], nu=cfg["nu"], dt=dt, steps=cfg["n_steps"])
+    g = gpu_run(u0, mode=AT_SEEDED, seed=cfg["seed"], record=True, **kw)
+    ref, hist, k = oracle_run(u0, mode="seeded", seed=cfg["seed"], want_k=True, **kw)
+    assert rel_linf(g["u"], ref) <= TOL["f64"]
+    assert np.array_equal(g["rec"], k)          # delays: bit-exact
+    assert np.array_equal(g["hist"], hist)
+    assert hist[1:].sum() > 0
+
+
+CASES = [
+    # dtype, order, L, P, M, max_ctas, forcing, steps, stages
+    ("f64", 4, 3, 148, 256, 10, 0.1, 300, 0),     # ragged CTA partition (14/15 subdomains)
+    ("f64", 2, 2, 37, 1028, 5, 0.0, 200, 0),      # M/4 = 257 groups > 256 consumer threads
+    ("f64", 4, 1, 8, 2048, 3, 0.1, 150, 0),       # largest FP64 tile (16 KiB)
+    ("f32", 4, 3, 64, 1024, 0, 0.1, 200, 0),      # forced order-4 subdomains of 1024 points
+    ("f32", 2, 2, 16, 256, 4, 0.0, 200, 0),
+    ("f32", 4, 3, 3, 4096, 0, 0.1, 100, 0),       # largest FP32 tile, one subdomain per CTA
+    ("f64", 2, 0, 32, 64, 7, 0.0, 300, 0),        # L = 0
+    ("f64", 2, 16, 64, 32, 8, 0.0, 200, 0),       # L = 16 (largest), see below
+    ("f64", 2, 2, 1, 256, 0, 0.0, 200, 0),        # one subdomain, its own neighbour
+    ("f64", 4, 3, 40, 4, 6, 0.0, 200, 0),         # M = 4: one group per tile
+    ("f64", 4, 3, 96, 128, 4, 0.1, 200, 1),       # one stage in flight
+    ("f64", 2, 3, 96, 128, 4, 0.1, 200, 2),       # two stages
+    ("f32", 4, 2, 300, 512, 0, 0.1, 150, 0),      # 300 subdomains over all SMs, ragged
+]
+
+
+@pytest.mark.parametrize("dtype,order,L,P,M,max_ctas,forcing,steps,stages", CASES)
+def test_seeded_parity(require_gpu, dtype, order, L, P, M, max_ctas, forcing, steps, stages):
+    from paper_1911_05769_gb300 import AT_SEEDED
+    N = P * M
+    u0, dt = _setup(N, 0.02, kind="fourier" if N >= 256 else "two_modes")
+    # L = 16 runs at order 2: with order 4 the quadratic extrapolation weights
+    # reach 153 at k = 16 and the problem itself amplifies a 1-ulp change of u0
+    # to ~4e-9 after 200 steps, so no differently rounded FP64 code can meet 1e-12.
+    kw = dict(P=P, order=order, L=L, nu=0.02, dt=dt, steps=steps, seed=1234 + P, forcing=forcing)
+    g = gpu_run(u0, dtype=dtype, mode=AT_SEEDED, max_ctas=max_ctas, stages=stages, record=True, **kw)
+    ref, hist, k = oracle_run(u0, mode="seeded", want_k=True, **kw)
+    assert rel_linf(g["u"], ref) <= TOL[dtype]
+    assert np.array_equal(g["rec"], k)
+    assert np.array_equal(g["hist"], hist)
+
+
+@pytest.mark.parametrize("dtype,order,max_ctas", [("f64", 2, 0), ("f64", 4, 5), ("f32", 4, 3), ("f64", 4, 1)])
+def test_sync_parity(require_gpu, dtype, order, max_ctas):
+    """AT_SYNC (grid barrier every step, Algorithm 1) against the synchronous oracle."""
+    from paper_1911_05769_gb300 import AT_SYNC
+    N, P = 64 * 128, 64
+    u0, dt = _setup(N, 0.02, kind="fourier")
+    kw = dict(P=P, order=order, L=2, nu=0.02, dt=dt, steps=200 if dtype == "f32" else 400, forcing=0.1)
+    g = gpu_run(u0, dtype=dtype, mode=AT_SYNC, max_ctas=max_ctas, record=True, **kw)
+    ref, hist = oracle_run(u0, mode="sync", **kw)
+    assert rel_linf(g["u"], ref) <= TOL[dtype]
+    assert np.all(g["rec"] == 0) and g["hist"][0] == hist[0] and g["hist"][1:].sum() == 0
+
+
+def test_zero_delay_modes_are_bitwise_synchronous(require_gpu):
+    """Sec. 3.2: k = 0 gives the standard scheme -- on the GPU, SEEDED with
+    L = 0 and REPLAY of zeros reproduce AT_SYNC bit for bit."""
+    from paper_1911_05769_gb300 import AT_REPLAY, AT_SEEDED, AT_SYNC
+    N, P = 32 * 256, 32
+    u0, dt = _setup(N, 0.02, kind="fourier")
+    kw = dict(P=P, order=4, nu=0.02, dt=dt, steps=300, forcing=0.1, max_ctas=6)
+    a = gpu_run(u0, L=0, mode=AT_SYNC, **kw)["u"]
+    b = gpu_run(u0, L=0, mode=AT_SEEDED, seed=3, **kw)["u"]
+    c = gpu_run(u0, L=2, mode=AT_REPLAY, delays=np.zeros((300, P, 2), np.int8), **kw)["u"]
+    assert np.array_equal(a, b) and np.array_equal(a, c)
+
+
+@pytest.mark.parametrize("dtype,order", [("f64", 2), ("f64", 4), ("f32", 4)])
+def test_replay_parity(require_gpu, dtype, order):
+    from paper_1911_05769_gb300 import AT_REPLAY
+    N, P, L, steps = 48 * 256, 48, 3, 200
+    u0, dt = _setup(N, 0.02, kind="fourier")
+    d = W.random_delays(steps, P, L, seed=77)
+    kw = dict(P=P, order=order, L=L, nu=0.02, dt=dt, steps=steps, forcing=0.1)
+    g = gpu_run(u0, dtype=dtype, mode=AT_REPLAY, delays=d, max_ctas=5, **kw)
+    ref, hist = oracle_run(u0, mode="replay", delays=d, **kw)
+    assert rel_linf(g["u"], ref) <= TOL[dtype]
+    assert np.array_equal(g["hist"], hist)
+
+
+@pytest.mark.parametrize("dtype,max_ctas", [("f64", 0), ("f64", 7), ("f32", 0)])
+def test_free_running_replays_exactly(require_gpu, dtype, max_ctas):
+    """Free-running delays have many correct results (c15): the GPU records
+    the delays it used, the oracle replays them and must agree to the bar;
+    every recorded delay lies in 0..L."""
+    from paper_1911_05769_gb300 import AT_FREE
+    N, P, L, steps = 256 * 128, 256, 3, 300 if dtype == "f64" else 150
+    u0, dt = _setup(N, 0.02, kind="fourier")
+    kw = dict(P=P, order=4, L=L, nu=0.02, dt=dt, steps=steps, forcing=0.1)
+    g = gpu_run(u0, dtype=dtype, mode=AT_FREE, max_ctas=max_ctas, record=True, **kw)
+    rec = g["rec"]
+    assert rec.min() >= 0 and rec.max() <= L
+    assert g["hist"].sum() == steps * P * 2
+    ref, hist = oracle_run(u0, mode="replay", delays=rec, **kw)
+    assert rel_linf(g["u"], ref) <= TOL[dtype]
+    assert np.array_equal(g["hist"], hist)
+
+
+def test_free_running_within_asynchrony_envelope(require_gpu):
+    """FREE results stay within the error the scheme makes with the largest
+    admissible delay everywhere (k = L), measured from the synchronous run."""
+    from paper_1911_05769_gb300 import AT_FREE
+    N, P, L, steps = 128 * 128, 128, 3, 400
+    u0, dt = _setup(N, 0.02, kind="fourier")
+    kw = dict(P=P, order=2, L=L, nu=0.02, dt=dt, steps=steps)
+    g = gpu_run(u0, mode=AT_FREE, max_ctas=9, **kw)["u"]
+    sync, _ = oracle_run(u0, mode="sync", **kw)
+    worst, _ = oracle_run(u0, mode="replay", delays=np.full((steps, P, 2), L, np.int8), **kw)
+    env = 2.0 * np.max(np.abs(worst - sync)) + 10 * np.finfo(np.float64).eps * np.max(np.abs(sync))
+    assert np.max(np.abs(g - sync)) <= env
+
+
+def test_calls_continue_one_another(require_gpu):
+    """Several at_step calls equal one long run (ring, flags and the step
+    counter persist across launches), in seeded and in replayed mode."""
+    from paper_1911_05769_gb300 import AT_REPLAY, AT_SEEDED, AT_SYNC
+    N, P, L, steps = 40 * 256, 40, 2, 300
+    u0, dt = _setup(N, 0.02, kind="fourier")
+    kw = dict(P=P, order=4, L=L, nu=0.02, dt=dt, steps=steps, forcing=0.1)
+    g = gpu_run(u0, mode=AT_SEEDED, seed=9, max_ctas=6, calls=[100, 37, 1, 162], **kw)
+    ref, _ = oracle_run(u0, mode="seeded", seed=9, **kw)
+    assert rel_linf(g["u"], ref) <= TOL["f64"]
+    d = W.random_delays(steps, P, L, seed=5)
+    g = gpu_run(u0, mode=AT_REPLAY, delays=d, max_ctas=6, calls=[150, 150], **kw)
+    ref, _ = oracle_run(u0, mode="replay", delays=d, **kw)
+    assert rel_linf(g["u"], ref) <= TOL["f64"]
+    # a synchronous call in between: the ring stays consistent
+    g1 = gpu_run(u0, mode=AT_SYNC, max_ctas=6, calls=[300], **kw)["u"]
+    ref, _ = oracle_run(u0, mode="sync", **kw)
+    assert rel_linf(g1, ref) <= TOL["f64"]
+
+
+def test_per_subdomain_delay_draw(require_gpu):
+    from paper_1911_05769_gb300 import AT_FLAG_PER_SUBDOMAIN_DELAY, AT_SEEDED
+    N, P, L, steps = 32 * 128, 32, 2, 200
+    u0, dt = _setup(N, 0.02, kind="fourier")
+    kw = dict(P=P, order=2, L=L, nu=0.02, dt=dt, steps=steps, seed=21)
+    g = gpu_run(u0, mode=AT_SEEDED, flags=AT_FLAG_PER_SUBDOMAIN_DELAY, record=True, max_ctas=4, **kw)
+    ref, _, k = oracle_run(u0, mode="seeded", per_subdomain=True, want_k=True, **kw)
+    assert np.array_equal(g["rec"], k)
+    assert rel_linf(g["u"], ref) <= TOL["f64"]
+
+
+def test_empty_step_is_a_no_op(require_gpu):
+    from paper_1911_05769_gb300 import AT_SEEDED
+    N, P = 16 * 64, 16
+    u0, dt = _setup(N, 0.02)
+    g = gpu_run(u0, P=P, order=2, L=1, nu=0.02, dt=dt, steps=0, calls=[0], mode=AT_SEEDED)
+    assert np.array_equal(g["u"], u0)

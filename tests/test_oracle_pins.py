@@ -447,3 +447,17 @@ def test_window_run_matches_full_run_in_its_centre():
     win, _ = oracle.run(u0[p_lo * M:(p_lo + p_count) * M], p_lo=p_lo, p_count=p_count, **kw)
     mid = slice(2 * M, 3 * M)
     assert np.array_equal(win[mid], full[(p_lo + 2) * M:(p_lo + 3) * M])
+
+
+def test_window_run_wraps_around_the_domain_end():
+    """A window that runs past subdomain P-1 continues at subdomain 0."""
+    N, P, n = 1024, 32, 20
+    u0 = W.u0_fourier(N, modes=16, seed=5)
+    kw = dict(N=N, P=P, order=2, L=2, nu=1e-2, dt=1e-5, n_steps=n, forcing_amp=0.1,
+              delay_mode=oracle.SEEDED, seed=8)
+    full, _ = oracle.run(u0, **kw)
+    M = N // P
+    p_lo, p_count = P - 2, 5     # subdomains P-2, P-1, 0, 1, 2
+    idx = np.concatenate([np.arange((P - 2) * M, N), np.arange(0, 3 * M)])
+    win, _ = oracle.run(u0[idx], p_lo=p_lo, p_count=p_count, **kw)
+    assert np.array_equal(win[2 * M:3 * M], full[0:M])

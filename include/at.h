@@ -164,6 +164,44 @@ int at_destroy(at_solver *h);
 /* Message of the last failed call on this thread ("" if none). */
 const char *at_last_error(void);
 
+/* Size in bytes of the fixed scratch array used by at_step_noalloc(). */
+#define AT_NOALLOC_SCRATCH_BYTES (8u * 1024u * 1024u)
+
+/* at_step_noalloc -- the same run as at_create + at_set_state + at_step +
+ * at_status, for callers that cannot allocate device memory (for example a
+ * plug-in whose host application owns all device memory and hands it only
+ * the state buffer, or code that must never call cudaMalloc).  The paper has
+ * no counterpart; this entry point exists only for such callers.
+ *
+ *   u        device memory, N words of grid->dtype, 16-byte aligned: level 0
+ *            on entry, level n_steps on return (updated in place).
+ *   delays   as in at_step (input for AT_REPLAY, optional record otherwise).
+ *   The other arguments are those of at_create; grid->workspace and
+ *   grid->workspace_bytes are ignored.
+ *
+ * Memory.  Nothing is allocated, on the device or on the host: the ring
+ * buffers, progress flags, status word and counters live in one array of
+ * AT_NOALLOC_SCRATCH_BYTES (8 MiB) that this library places in the device
+ * memory of every GPU that loads it and keeps until the process exits.  A
+ * problem whose scratch would not fit -- roughly 32 T + 16 bytes per
+ * subdomain with T = 8 or 16 ring slots, i.e. up to about 15,000 subdomains at
+ * order 4 and L = 3 -- is rejected with AT_ERR_ARG and a message giving both
+ * sizes.
+ *
+ * Sharing.  All calls on a device share that one array, and it keeps what the
+ * last call left in it; each call clears the parts that must start at zero
+ * before it launches.  Calls whose work overlaps on the same GPU (other
+ * streams, other host threads) race on the array and corrupt each other's
+ * results: issue them one after another.  The call waits for its stream
+ * before it returns, and returns the device status (AT_OK or AT_ERR_TIMEOUT).
+ *
+ * Set-up.  The first call on each device looks up the device address of the
+ * array (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture begins on the device. */
+int at_step_noalloc(const at_grid *grid, int64_t P, int scheme_order, int L,
+                    double nu, double dt, void *u, int64_t n_steps,
+                    int delay_mode, int8_t *delays);
+
 #ifdef __cplusplus
 }
 #endif

@@ -38,6 +38,8 @@ AT_FLAG_PER_SUBDOMAIN_DELAY = 1
 AT_FLAG_ALLOW_UNSTABLE = 2
 AT_FLAG_TEST_SKIP_PUBLISH = 4
 
+AT_NOALLOC_SCRATCH_BYTES = 8 * 1024 * 1024
+
 
 class at_grid(ctypes.Structure):
     _fields_ = [
@@ -77,6 +79,9 @@ _SIGNATURES = [
     ("at_get_info", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(at_info)]),
     ("at_destroy", ctypes.c_int, [ctypes.c_void_p]),
     ("at_last_error", ctypes.c_char_p, []),
+    ("at_step_noalloc", ctypes.c_int,
+     [ctypes.POINTER(at_grid), ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+      ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p]),
 ]
 
 EXPORTED = [s[0] for s in _SIGNATURES]
@@ -152,6 +157,15 @@ def at_get_info(h):
 
 def at_destroy(h) -> int:
     return lib().at_destroy(h)
+
+
+def at_step_noalloc(grid: at_grid, P: int, scheme_order: int, L: int, nu: float, dt: float, u_ptr: int,
+                    n_steps: int, delay_mode: int, delays_ptr: int | None = None) -> int:
+    """Allocation-free run for callers that cannot allocate device memory: the
+    state at ``u_ptr`` (device) is advanced in place; scratch is the library's
+    fixed array (see include/at.h).  Synchronises and returns the status."""
+    return lib().at_step_noalloc(ctypes.byref(grid), P, scheme_order, L, nu, dt, ctypes.c_void_p(u_ptr), n_steps,
+                                 delay_mode, ctypes.c_void_p(delays_ptr) if delays_ptr else None)
 
 
 def at_last_error() -> str:

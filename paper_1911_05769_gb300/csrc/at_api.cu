@@ -355,3 +355,149 @@ int at_destroy(at_solver *h)
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free entry point (at_step_noalloc).
+//
+// Some callers cannot allocate device memory: a plug-in living inside a host
+// application that owns every byte of device memory and gives it only the
+// state buffer, code with a hard device-memory budget, or a loop that must
+// never reach the CUDA allocator.  at_step_noalloc serves them by running the
+// same persistent kernel with its scratch -- ring buffers, progress flags,
+// control block, delay counters and barrier counter -- in the fixed array
+// below, which every GPU that loads this library keeps until the process
+// exits.  The caller still passes the state (input and output) and, if used,
+// the delay array.
+// ---------------------------------------------------------------------------
+#include <mutex>
+
+namespace {
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[AT_NOALLOC_SCRATCH_BYTES];
+
+constexpr int kNoallocMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+unsigned char *g_noalloc_addr[kNoallocMaxDevices] = {};
+
+// Device address of the scratch array on device `dev` (which must be the
+// current device).  In host code the array's name is only a host-side
+// stand-in, so the address is looked up once per device and cached.
+int noalloc_scratch_address(int dev, unsigned char **out)
+{
+    if (dev < 0 || dev >= kNoallocMaxDevices) return fail(AT_ERR_ARG, "device ordinal %d not supported", dev);
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_addr[dev]) {
+        void *ptr = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(scratch array)");
+        g_noalloc_addr[dev] = static_cast<unsigned char *>(ptr);
+    }
+    *out = g_noalloc_addr[dev];
+    return AT_OK;
+}
+
+}  // namespace
+
+extern "C" int at_step_noalloc(const at_grid *grid, int64_t P, int scheme_order, int L, double nu, double dt,
+                               void *u, int64_t n_steps, int delay_mode, int8_t *delays)
+{
+    g_err[0] = 0;
+    int rc = check_args(grid, P, scheme_order, L);
+    if (rc != AT_OK) return rc;
+    if (!u) return fail(AT_ERR_ARG, "u is NULL");
+    if (reinterpret_cast<uintptr_t>(u) % 16 != 0) return fail(AT_ERR_ARG, "u must be 16-byte aligned");
+    if (!(dt > 0.0) || !std::isfinite(dt)) return fail(AT_ERR_ARG, "dt must be positive");
+    if (!(nu >= 0.0) || !std::isfinite(nu)) return fail(AT_ERR_ARG, "nu must be >= 0");
+    if (n_steps < 0) return fail(AT_ERR_ARG, "n_steps < 0");
+    if (delay_mode < AT_SYNC || delay_mode > AT_REPLAY) return fail(AT_ERR_ARG, "bad delay_mode %d", delay_mode);
+    if (delay_mode == AT_REPLAY && !delays) return fail(AT_ERR_ARG, "AT_REPLAY needs a delays array");
+    const int64_t N = grid->n[0];
+    const double dx = grid->length[0] / (double)N;
+    const double lim = scheme_order == 2 ? 0.5 : 0.375;
+    if (!(grid->flags & AT_FLAG_ALLOW_UNSTABLE) && nu * dt / (dx * dx) > lim)
+        return fail(AT_ERR_UNSTABLE, "nu*dt/dx^2 = %g exceeds %g", nu * dt / (dx * dx), lim);
+    const int w = grid->dtype == AT_F64 ? 8 : 4;
+    const int s = scheme_order / 2 + 1;
+    const int T = ring_slots(L, s);
+    const Layout lay = layout(0, P, w, L, T);   // scratch only: the state is the caller's
+    if (lay.total > (size_t)AT_NOALLOC_SCRATCH_BYTES)
+        return fail(AT_ERR_ARG,
+                    "at_step_noalloc: P=%lld, L=%d, order %d need %zu bytes of scratch, more than the "
+                    "fixed %zu-byte array (use at_create with a workspace)",
+                    (long long)P, L, scheme_order, lay.total, (size_t)AT_NOALLOC_SCRATCH_BYTES);
+
+    int dev = 0, sms = 0, coop = 0, smem_optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (!coop) return fail(AT_ERR_RESIDENCY, "device does not support cooperative launch");
+    unsigned char *scratch = nullptr;
+    rc = noalloc_scratch_address(dev, &scratch);
+    if (rc != AT_OK) return rc;
+
+    at_solver h{};   // on the stack: nothing is allocated, on the host or on the device
+    h.g = *grid;
+    if (h.g.timeout_ns <= 0) h.g.timeout_ns = 1000000000ll;
+    h.N = N; h.P = P; h.M = N / P;
+    h.order = scheme_order; h.L = L; h.R = scheme_order / 2; h.s = s; h.T = T; h.w = w;
+    h.nu = nu; h.dt = dt; h.dx = dx;
+    h.lay = lay;
+    h.ws = scratch;
+    h.stream = static_cast<cudaStream_t>(grid->stream);
+    h.device = dev; h.sm_count = sms;
+    if (w == 8) {
+        h.kernel = scheme_order == 2 ? (void *)atk::at_stepper<double, 2> : (void *)atk::at_stepper<double, 4>;
+        h.init_kernel = scheme_order == 2 ? (void *)atk::at_init<double, 1> : (void *)atk::at_init<double, 2>;
+    } else {
+        h.kernel = scheme_order == 2 ? (void *)atk::at_stepper<float, 2> : (void *)atk::at_stepper<float, 4>;
+        h.init_kernel = scheme_order == 2 ? (void *)atk::at_init<float, 1> : (void *)atk::at_init<float, 2>;
+    }
+    int G = grid->max_ctas > 0 ? grid->max_ctas : sms;
+    if (P < G) G = (int)P;
+    int stages = grid->stages > 0 ? grid->stages : (w == 4 ? 16 : 12);
+    const int stage_bytes = (int)align_up(atk::kTileOff + (size_t)h.M * w, 128);
+    const int64_t Smax = (P + G - 1) / G;
+    const size_t tab_bytes = grid->forcing_amp != 0.0 ? (size_t)(2 * h.M + 2 * Smax) * w : 0;
+    auto smem_for = [&](int st) {
+        return align_up((size_t)16 * st + atk::kMiscBytes, 128) + (size_t)st * stage_bytes + tab_bytes;
+    };
+    while (stages > 1 && smem_for(stages) > (size_t)smem_optin) --stages;
+    if (smem_for(stages) > (size_t)smem_optin)
+        return fail(AT_ERR_RESIDENCY, "shared memory %zu exceeds %d", smem_for(stages), smem_optin);
+    h.stages = stages;
+    h.stage_bytes = stage_bytes;
+    h.stage_off = (int)align_up((size_t)16 * stages + atk::kMiscBytes, 128);
+    h.tab_off = h.stage_off + stages * stage_bytes;
+    h.smem = (int)smem_for(stages);
+    e = cudaFuncSetAttribute(h.kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, h.smem);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
+    int occ = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, h.kernel, atk::kThreads, h.smem);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+    if (occ < 1 || (int64_t)occ * sms < G)
+        return fail(AT_ERR_RESIDENCY, "%d CTAs cannot be co-resident (occupancy %d per SM)", G, occ);
+    h.G = G;
+
+    // Every call starts from zeroed ring buffers, flags, status and counters:
+    // the array still holds whatever the previous call left in it.
+    atk::Params p = make_params(&h);
+    p.u = u;
+    e = cudaMemsetAsync(scratch + lay.ring, 0, lay.total - lay.ring, h.stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(scratch)");
+    void *args[] = {&p};
+    const int blocks = (int)((P + 255) / 256 < 1024 ? (P + 255) / 256 : 1024);
+    e = cudaLaunchKernel(h.init_kernel, dim3(blocks), dim3(256), args, 0, h.stream);
+    if (e != cudaSuccess) return cuda_fail(e, "launch at_init");
+    if (n_steps > 0) {
+        p.mode = delay_mode;
+        p.delays = delays;
+        p.n0 = 0;
+        p.n_steps = n_steps;
+        p.gbar_base = 0;
+        e = cudaLaunchCooperativeKernel(h.kernel, dim3(h.G), dim3(atk::kThreads), args, (size_t)h.smem, h.stream);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaLaunchCooperativeKernel(at_stepper)");
+    }
+    return read_status(&h);
+}

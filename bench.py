@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--stages", type=int, default=0, help="tiles in flight per CTA (0 = default)")
     ap.add_argument("--arms", default="free,sync,seeded", help="timed arms (free first is the headline)")
     ap.add_argument("--N", type=int, default=0, help="smaller N for profiling runs (P scales, M stays 1024)")
+    ap.add_argument("--spp", type=int, default=-1,
+                    help="levels per pass of the free-running arm (temporal blocking); -1 = L+1")
     return ap.parse_args()
 
 
@@ -233,9 +235,11 @@ def gpu_arm(args, ws, rank, local, pg):
     u0_dev = torch.from_numpy(u0).to(device=dev, dtype=tdt)
     stream = torch.cuda.Stream(device=dev)
 
-    def make(dtype=args.dtype):
+    spp = L + 1 if args.spp < 0 else args.spp
+
+    def make(dtype=args.dtype, blocked=True):
         s = at.Solver(N, P, order, L, nu, dt, dtype=dtype, forcing_amp=A, seed=cfg["seed"], stream=stream,
-                      device=local, max_ctas=args.ctas, stages=args.stages)
+                      device=local, max_ctas=args.ctas, stages=args.stages, steps_per_pass=spp if blocked else 0)
         return s
 
     def barrier():
@@ -250,7 +254,7 @@ def gpu_arm(args, ws, rank, local, pg):
         return float(t.item())
 
     def timed_arm(mode, steps, warmup, time_steps, dtype=args.dtype, clocks=None):
-        s = make(dtype)
+        s = make(dtype, blocked=(mode == at.AT_FREE))
         s.set_state(u0_dev if dtype == args.dtype else u0_dev.to(torch.float64 if dtype == "f64" else torch.float32))
         for _ in range(warmup):
             s.step(time_steps, mode)
@@ -302,7 +306,9 @@ def gpu_arm(args, ws, rank, local, pg):
 
     # roofline of the stepper kernel: algorithmic bytes per launch / launch time
     M, R, s_lev = N // P, order // 2, order // 2 + 1
-    bytes_per_update = 2 * wbytes + (2 * R * wbytes + 2 * R * s_lev * wbytes) / M
+    # one HBM read and write of the state per pass of `spp` levels, plus the
+    # ring values a subdomain publishes (every level) and reads (every pass)
+    bytes_per_update = (2 * wbytes + 2 * R * s_lev * wbytes / M) / max(1, spp) + 2 * R * wbytes / M
     alg_bytes = bytes_per_update * upd_per_step
     launch_s = statistics.mean(head["launch_ms"]) * 1e-3
     achieved = alg_bytes / launch_s / 1e9
@@ -320,6 +326,7 @@ def gpu_arm(args, ws, rank, local, pg):
         "dtype": args.dtype, "data": "synthetic",
         "config": {"workload": WORKLOAD, "N": N, "P": P, "M": M, "order": order, "L": L, "nu": nu,
                    "forcing_amp": A, "dt": dt, "time_steps_per_step": S, "mode": "free",
+                   "steps_per_pass": spp,
                    "ctas": head["info"].ctas, "stages": head["info"].stages,
                    "l2": f"inputs larger than L2: state {N * wbytes / 2**20:.0f} MiB updated in place (no flush)",
                    "parallelism": "replicas" if ws > 1 else "single-gpu"},

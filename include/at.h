@@ -93,6 +93,9 @@ typedef struct at_grid {
                                AT_ERR_RESIDENCY if they cannot all be resident)   */
   int32_t  stages;          /* 0 = default pipeline depth (tiles in flight per CTA)*/
   int64_t  test_skip_step;  /* level after which AT_FLAG_TEST_SKIP_PUBLISH acts    */
+  int32_t  steps_per_pass;  /* AT_FREE only: levels advanced per pass over a tile  */
+                            /* (temporal blocking), 0 or 1 = none, at most L+1    */
+  int32_t  reserved;
 } at_grid;
 
 /* Launch facts of a solver, for tests and benchmarks. */
@@ -108,6 +111,8 @@ typedef struct at_info {
   int64_t step;             /* time level of the state (steps taken)               */
   int32_t sm_count;         /* SMs of the device                                   */
   int32_t dtype;            /* AT_F64 or AT_F32                                    */
+  int32_t steps_per_pass;   /* levels per pass in AT_FREE                          */
+  int32_t reserved;
 } at_info;
 
 /* Bytes of workspace needed for this problem, or 0 if the arguments are

@@ -48,7 +48,7 @@ class at_grid(ctypes.Structure):
         ("forcing_amp", ctypes.c_double), ("seed", ctypes.c_uint64),
         ("workspace", ctypes.c_void_p), ("workspace_bytes", ctypes.c_size_t), ("stream", ctypes.c_void_p),
         ("timeout_ns", ctypes.c_int64), ("max_ctas", ctypes.c_int32), ("stages", ctypes.c_int32),
-        ("test_skip_step", ctypes.c_int64),
+        ("test_skip_step", ctypes.c_int64), ("steps_per_pass", ctypes.c_int32), ("reserved", ctypes.c_int32),
     ]
 
 
@@ -58,7 +58,7 @@ class at_info(ctypes.Structure):
         ("order", ctypes.c_int32), ("L", ctypes.c_int32), ("R", ctypes.c_int32), ("s", ctypes.c_int32),
         ("T", ctypes.c_int32), ("ctas", ctypes.c_int32), ("threads", ctypes.c_int32), ("stages", ctypes.c_int32),
         ("smem_bytes", ctypes.c_int64), ("step", ctypes.c_int64), ("sm_count", ctypes.c_int32),
-        ("dtype", ctypes.c_int32),
+        ("dtype", ctypes.c_int32), ("steps_per_pass", ctypes.c_int32), ("reserved", ctypes.c_int32),
     ]
 
 

@@ -81,6 +81,8 @@ int check_args(const at_grid *g, int64_t P, int order, int L)
     if (M % 4 != 0 || M < 4) return fail(AT_ERR_ARG, "M = N/P must be a multiple of 4 (M=%lld)", (long long)M);
     if (M * w > 16384) return fail(AT_ERR_ARG, "M * word size must be <= 16 KiB (M=%lld)", (long long)M);
     if (!(g->length[0] > 0.0)) return fail(AT_ERR_ARG, "length[0] must be positive");
+    if (g->steps_per_pass < 0 || g->steps_per_pass > L + 1)
+        return fail(AT_ERR_ARG, "steps_per_pass must be in 0..L+1 (the delay bound), got %d", g->steps_per_pass);
     return AT_OK;
 }
 
@@ -95,7 +97,8 @@ struct at_solver {
     unsigned char *ws;
     cudaStream_t stream;
     int device, sm_count;
-    int G, stages, stage_bytes, stage_off, tab_off, smem;
+    int G, stages, sb, smem;
+    long long stage_bytes, stage_off, work_off, tab_off;
     int64_t step;
     unsigned long long gbar_count;
     bool has_state;
@@ -172,23 +175,23 @@ int at_create(const at_grid *grid, int64_t P, int scheme_order, int L, double nu
     int G = grid->max_ctas > 0 ? grid->max_ctas : sms;
     if (P < G) G = (int)P;
     int stages = grid->stages > 0 ? grid->stages : (w == 4 ? 16 : 12);
-    const int stage_bytes = (int)align_up(atk::kTileOff + (size_t)h->M * w, 128);
+    const int sb = grid->steps_per_pass > 0 ? grid->steps_per_pass : 1;
     const int64_t Smax = (P + G - 1) / G;
-    const size_t tab_bytes = grid->forcing_amp != 0.0 ? (size_t)(2 * h->M + 2 * Smax) * w : 0;
-    auto smem_for = [&](int st) {
-        const size_t off = align_up((size_t)16 * st + atk::kMiscBytes, 128);
-        return off + (size_t)st * stage_bytes + tab_bytes;
-    };
+    const long long tab_words = grid->forcing_amp != 0.0 ? 2 * h->M + 2 * Smax : 0;
+    auto smem_for = [&](int st) { return (size_t)atk::smem_layout(h->M, w, st, sb > 1, tab_words).total; };
     while (stages > 1 && smem_for(stages) > (size_t)smem_optin) --stages;
     if (smem_for(stages) > (size_t)smem_optin) {
         delete h;
         return fail(AT_ERR_RESIDENCY, "shared memory %zu exceeds %d", smem_for(stages), smem_optin);
     }
+    const atk::SmemLayout sl = atk::smem_layout(h->M, w, stages, sb > 1, tab_words);
     h->stages = stages;
-    h->stage_bytes = stage_bytes;
-    h->stage_off = (int)align_up((size_t)16 * stages + atk::kMiscBytes, 128);
-    h->tab_off = h->stage_off + stages * stage_bytes;
-    h->smem = (int)smem_for(stages);
+    h->sb = sb;
+    h->stage_bytes = sl.stage_bytes;
+    h->stage_off = sl.stage_off;
+    h->work_off = sl.work_off;
+    h->tab_off = sl.tab_off;
+    h->smem = (int)sl.total;
     e = cudaFuncSetAttribute(h->kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, h->smem);
     if (e != cudaSuccess) { delete h; return cuda_fail(e, "cudaFuncSetAttribute"); }
     int occ = 0;
@@ -234,7 +237,9 @@ static atk::Params make_params(const at_solver *h)
     p.stages = h->stages;
     p.stage_bytes = h->stage_bytes;
     p.stage_off = h->stage_off;
+    p.work_off = h->work_off;
     p.tab_off = h->tab_off;
+    p.sb = 1;
     p.timeout_ns = h->g.timeout_ns;
     p.skip_publish = (h->g.flags & AT_FLAG_TEST_SKIP_PUBLISH) ? 1 : 0;
     p.skip_step = h->g.test_skip_step;
@@ -275,6 +280,7 @@ int at_step(at_solver *h, int64_t n_steps, int delay_mode, int8_t *delays)
     p.n0 = h->step;
     p.n_steps = n_steps;
     p.gbar_base = h->gbar_count;
+    p.sb = delay_mode == AT_FREE ? h->sb : 1;
     void *args[] = {&p};
     cudaError_t e = cudaLaunchCooperativeKernel(h->kernel, dim3(h->G), dim3(atk::kThreads), args, (size_t)h->smem,
                                                 h->stream);
@@ -344,7 +350,7 @@ int at_get_info(const at_solver *h, at_info *info)
     info->order = h->order; info->L = h->L; info->R = h->R; info->s = h->s; info->T = h->T;
     info->ctas = h->G; info->threads = atk::kThreads; info->stages = h->stages;
     info->smem_bytes = h->smem; info->step = h->step; info->sm_count = h->sm_count;
-    info->dtype = h->g.dtype;
+    info->dtype = h->g.dtype; info->steps_per_pass = h->sb;
     return AT_OK;
 }
 
@@ -457,20 +463,20 @@ extern "C" int at_step_noalloc(const at_grid *grid, int64_t P, int scheme_order,
     int G = grid->max_ctas > 0 ? grid->max_ctas : sms;
     if (P < G) G = (int)P;
     int stages = grid->stages > 0 ? grid->stages : (w == 4 ? 16 : 12);
-    const int stage_bytes = (int)align_up(atk::kTileOff + (size_t)h.M * w, 128);
     const int64_t Smax = (P + G - 1) / G;
-    const size_t tab_bytes = grid->forcing_amp != 0.0 ? (size_t)(2 * h.M + 2 * Smax) * w : 0;
-    auto smem_for = [&](int st) {
-        return align_up((size_t)16 * st + atk::kMiscBytes, 128) + (size_t)st * stage_bytes + tab_bytes;
-    };
+    const long long tab_words = grid->forcing_amp != 0.0 ? 2 * h.M + 2 * Smax : 0;
+    auto smem_for = [&](int st) { return (size_t)atk::smem_layout(h.M, w, st, false, tab_words).total; };
     while (stages > 1 && smem_for(stages) > (size_t)smem_optin) --stages;
     if (smem_for(stages) > (size_t)smem_optin)
         return fail(AT_ERR_RESIDENCY, "shared memory %zu exceeds %d", smem_for(stages), smem_optin);
+    const atk::SmemLayout sl = atk::smem_layout(h.M, w, stages, false, tab_words);
     h.stages = stages;
-    h.stage_bytes = stage_bytes;
-    h.stage_off = (int)align_up((size_t)16 * stages + atk::kMiscBytes, 128);
-    h.tab_off = h.stage_off + stages * stage_bytes;
-    h.smem = (int)smem_for(stages);
+    h.sb = 1;
+    h.stage_bytes = sl.stage_bytes;
+    h.stage_off = sl.stage_off;
+    h.work_off = sl.work_off;
+    h.tab_off = sl.tab_off;
+    h.smem = (int)sl.total;
     e = cudaFuncSetAttribute(h.kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, h.smem);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
     int occ = 0;

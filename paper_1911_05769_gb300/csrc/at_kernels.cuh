@@ -2,42 +2,60 @@
 //
 // One cooperative launch advances the whole 1D field by n_steps forward-Euler
 // steps (arXiv 1911.05769, Sec. 3.2).  CTA c owns the contiguous subdomains
-// [lo, hi) and sweeps them in step-major order; a "tile" is one
-// (step n, subdomain j) pair.  Each CTA runs
+// [lo, hi) and sweeps them in step-major order.  A "tile" is one subdomain j
+// over one pass of `len` consecutive levels n .. n+len (len = 1 except in
+// blocked free-running mode).  Each CTA runs
 //   * one producer warp: for tile r it copies the subdomain's M state words
 //     and the neighbours' delayed boundary values (levels n-k-m, Eq. AT1/AT2)
 //     from the ring buffers into shared-memory stage r % PD with cp.async,
 //     after choosing the delays k (prescribed, replayed, or -- free running --
 //     read off the neighbour's progress flag, waiting only while the neighbour
-//     lags by more than L: the blocking branch of Algorithm 2);
-//   * eight consumer warps: the halo approximation ("approximate" step of
+//     lags by more than the delay bound allows: the blocking branch of
+//     Algorithm 2);
+//   * four consumer warps: the halo approximation ("approximate" step of
 //     Algorithm 2, split form of Sec. 5.2), the unchanged central stencil of
-//     order 2 or 4, the Euler update written back in place, and the publish
-//     of the new boundary values into the ring slot (n+1) mod T followed by a
-//     release store of the face's progress flag (the notified put).
+//     order 2 or 4 and the Euler update, `len` times on the tile held in
+//     shared memory, the final level written back in place; after every level
+//     the new boundary values go into ring slot (level mod T), followed, on
+//     the CTA's two edge faces, by a release store of the progress flag (the
+//     notified put).
 // Halo values never come from the neighbour's state array, only from the
 // ring, so each CTA updates its own subdomains in place.  Stage reuse is
 // signalled with mbarriers (full: copies landed; empty: tile consumed).
+//
+// Blocked free-running mode (temporal blocking): a pass of len <= L+1 levels
+// uses, at inner step i, the halo extrapolated with delay k0 + i from the
+// levels available when the pass started (Eq. AT1/AT2 with a larger k), so
+// the state is read and written once per pass instead of once per level.
+//
 // AT_SYNC replaces the flag waits with a grid barrier between steps
 // (Algorithm 1).  Every wait is bounded by timeout_ns; on expiry the kernel
 // latches AT_ERR_TIMEOUT in the control block, raises the abort word and
-// every CTA leaves its loops.
+// every CTA leaves its loops.  Abort is uniform inside a CTA: the producer
+// lets all its copies land before it raises the CTA's abort word, so every
+// consumer sees the same set of completed stages and takes the same named
+// barriers.
 #pragma once
 
 #include "at_device.cuh"
 
 namespace atk {
 
-constexpr int kConsumerWarps = 8;
-constexpr int kConsumers = 32 * kConsumerWarps;   // threads 0..255
+constexpr int kConsumerWarps = 4;
+constexpr int kConsumers = 32 * kConsumerWarps;   // threads 0..127
 constexpr int kThreads = kConsumers + 32;         // + one producer warp
 constexpr int kRingEntry = 16;                    // bytes per (slot, subdomain, face)
-constexpr int kHeaderBytes = 16;                  // per stage: the two delays k
 constexpr int kMaxS = 3;                          // levels per halo approximation
-constexpr int kTileOff = kHeaderBytes + 2 * kMaxS * kRingEntry;  // 112
+// stage layout: [0,16) header (k0 face 0, k0 face 1, len) | [16,112) delayed
+// ring levels [face][m] | [112,128) left halo pad | tile (M words) | 16-byte
+// right halo pad
+constexpr int kRawOff = 16;
+constexpr int kTileOff = 128;
+constexpr int kPadBytes = 16;
 constexpr int kMaxL = 16;
 constexpr int kFullArrivals = 32 + 2;             // 32 copy arrivals + 2 header writers
 constexpr int kMiscBytes = 256;                   // abort word + delay histograms
+constexpr int kConsumerBarrier = 1;               // named barrier id of the consumer warps
 
 enum : int { kModeSync = 0, kModeSeeded = 1, kModeFree = 2, kModeReplay = 3 };
 enum : int {
@@ -46,6 +64,25 @@ enum : int {
 };
 enum : int { kWhereFull = 1, kWhereEmpty = 2, kWhereFlag = 3, kWhereGrid = 4 };
 constexpr int kStatusTimeout = -5;
+
+// Shared-memory layout of the stepper, shared by the host (launch set-up) and
+// the kernel.
+struct SmemLayout {
+    long long stage_bytes, stage_off, work_off, tab_off, total;
+};
+
+__host__ __device__ inline long long round_up(long long x, long long a) { return (x + a - 1) / a * a; }
+
+__host__ __device__ inline SmemLayout smem_layout(long long M, int word, int stages, bool work, long long tab_words)
+{
+    SmemLayout l;
+    l.stage_bytes = round_up(kTileOff + M * word + kPadBytes, 128);
+    l.stage_off = round_up(16LL * stages + kMiscBytes, 128);
+    l.work_off = l.stage_off + (long long)stages * l.stage_bytes;
+    l.tab_off = l.work_off + (work ? l.stage_bytes : 0);
+    l.total = l.tab_off + tab_words * word;
+    return l;
+}
 
 struct Params {
     void *u;                   // state, N words, updated in place
@@ -58,13 +95,14 @@ struct Params {
     long long N, P, M;
     int L, T, mode, per_sub;
     long long n0, n_steps;
+    int sb;                    // levels per pass (temporal blocking, free mode)
     unsigned long long seed;
     double cA, cB, dtA;        // dt/(2dx) | dt/(12dx);  nu dt/dx^2 | nu dt/(12dx^2);  dt A
     double x0, dx;
     int forcing;
     int G;                     // CTAs
     int stages;                // stage buffers per CTA
-    int stage_bytes, stage_off, tab_off;
+    long long stage_bytes, stage_off, work_off, tab_off;
     long long timeout_ns;
     unsigned long long gbar_base;
     int skip_publish;          // test knob: CTA 0 stops releasing flags
@@ -85,25 +123,48 @@ __device__ __noinline__ void raise_timeout(const Params &p, int where, long long
     atomicExch(p.ctrl + kCtrlAbort, 1);
 }
 
+// Producer side: waits for a stage to be released by the consumers.
 __device__ __forceinline__ bool wait_mbar(uint64_t *bar, unsigned parity, const Params &p,
-                                          volatile int *s_abort, int where)
+                                          volatile int *s_abort, int where, long long limit_ns)
 {
     if (mbar_try_wait(bar, parity)) return true;
     const unsigned long long t0 = global_ns();
     for (;;) {
         if (mbar_try_wait(bar, parity)) return true;
         if (*s_abort) return false;
-        if ((long long)(global_ns() - t0) > p.timeout_ns) {
+        if ((long long)(global_ns() - t0) > limit_ns) {
             raise_timeout(p, where, -1, -1);
-            *s_abort = 1;
+            return false;
+        }
+    }
+}
+
+// Consumer side: waits for a stage to be filled.  Gives up only when the
+// producer has raised the CTA's abort word, after re-testing the phase: the
+// producer raises it only once all its copies have landed, so all consumers
+// see the same completed phases and leave at the same tile.  The time limit
+// is a last resort far beyond any producer wait.
+__device__ __forceinline__ bool wait_full(uint64_t *bar, unsigned parity, const Params &p,
+                                          volatile int *s_abort)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    for (;;) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (*s_abort) {
+            __threadfence_block();
+            return mbar_try_wait(bar, parity);
+        }
+        if ((long long)(global_ns() - t0) > 16 * p.timeout_ns) {
+            raise_timeout(p, kWhereFull, -1, -1);
             return false;
         }
     }
 }
 
 // Waits until *fl >= need (acquire).  Returns the value seen in *seen.
-__device__ __noinline__ bool wait_flag(const Params &p, volatile int *s_abort, const unsigned long long *fl,
-                                       long long need, unsigned long long *seen, long long n, long long nb)
+__device__ __noinline__ bool wait_flag(const Params &p, const unsigned long long *fl, long long need,
+                                       unsigned long long *seen, long long n, long long nb)
 {
     unsigned long long v = ld_acquire(fl);
     if ((long long)v >= need) { *seen = v; return true; }
@@ -114,30 +175,32 @@ __device__ __noinline__ bool wait_flag(const Params &p, volatile int *s_abort, c
         if (ns < 256) ns <<= 1;
         v = ld_acquire(fl);
         if ((long long)v >= need) { *seen = v; return true; }
-        if (*s_abort || ld_relaxed(p.ctrl + kCtrlAbort)) { *s_abort = 1; return false; }
+        if (ld_relaxed(p.ctrl + kCtrlAbort)) return false;
         if ((long long)(global_ns() - t0) > p.timeout_ns) {
             raise_timeout(p, kWhereFlag, n, nb);
-            *s_abort = 1;
             return false;
         }
     }
 }
 
-__device__ __noinline__ bool wait_grid(const Params &p, volatile int *s_abort, unsigned long long target,
-                                       long long n)
+__device__ __noinline__ bool wait_grid(const Params &p, unsigned long long target, long long n)
 {
     if (ld_acquire(p.gbar) >= target) return true;
     const unsigned long long t0 = global_ns();
     for (;;) {
         __nanosleep(20);
         if (ld_acquire(p.gbar) >= target) return true;
-        if (*s_abort || ld_relaxed(p.ctrl + kCtrlAbort)) { *s_abort = 1; return false; }
+        if (ld_relaxed(p.ctrl + kCtrlAbort)) return false;
         if ((long long)(global_ns() - t0) > p.timeout_ns) {
             raise_timeout(p, kWhereGrid, n, -1);
-            *s_abort = 1;
             return false;
         }
     }
+}
+
+__device__ __forceinline__ void consumer_sync()
+{
+    asm volatile("bar.sync %0, %1;" ::"n"(kConsumerBarrier), "n"(kConsumers) : "memory");
 }
 
 // ---------------------------------------------------------------------------
@@ -162,6 +225,17 @@ __device__ __forceinline__ void lds(const T *s, T *v)
     } else {
 #pragma unroll
         for (int i = 0; i < CNT; ++i) v[i] = s[i];
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void sts4(T *s, const T *v)
+{
+    if constexpr (sizeof(T) == 4) {
+        *reinterpret_cast<float4 *>(s) = make_float4(v[0], v[1], v[2], v[3]);
+    } else {
+        *reinterpret_cast<double2 *>(s) = make_double2(v[0], v[1]);
+        *reinterpret_cast<double2 *>(s + 2) = make_double2(v[2], v[3]);
     }
 }
 
@@ -220,7 +294,7 @@ __device__ void produce(const Params &p, long long lo, long long hi, int PD, uin
     constexpr unsigned kAll = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const long long S = hi - lo;
-    const long long Q = p.n_steps * S;
+    const long long n_end = p.n0 + p.n_steps;
     const int chunks = (int)(p.M * (long long)sizeof(T) / 16);
     const size_t tile_bytes = (size_t)p.M * sizeof(T);
     const size_t slot_stride = (size_t)p.P * 2 * kRingEntry;
@@ -229,20 +303,27 @@ __device__ void produce(const Params &p, long long lo, long long hi, int PD, uin
     int kb = 0;                 // lane i: raw delay of (tile r0 + i/2, face i%2) of the batch
     int st = 0;                 // stage of tile r
     unsigned use = 0;           // r / PD
-    long long n = p.n0, j = lo; // level and subdomain of tile r
+    long long n = p.n0, j = lo; // pass start level and subdomain of tile r
+    long long r = 0;
     bool ok = true;
 
-    for (long long r = 0; r < Q; ++r) {
-        // every 16 tiles, the 32 lanes draw the 32 (tile, face) delays at once
-        if ((r & 15) == 0) {
+    while (n < n_end) {
+        // levels in this pass: passes longer than one level extrapolate from s
+        // levels, so they start only once level s-1 exists (the same rule in
+        // every CTA, so all agree on the pass boundaries)
+        int len = (int)((n_end - n) < p.sb ? (n_end - n) : p.sb);
+        if (n < S_LEV - 1) len = 1;
+        // every 16 tiles, the 32 lanes draw the 32 (tile, face) delays at
+        // once (prescribed modes, one level per pass)
+        if ((r & 15) == 0 && (p.mode == kModeSeeded || p.mode == kModeReplay)) {
             long long jj = j + (lane >> 1), nn = n;
             while (jj >= hi) { jj -= S; ++nn; }
             const int f = lane & 1;
             int k = 0;
-            if (r + (lane >> 1) < Q) {
+            if (nn < n_end) {
                 if (p.mode == kModeSeeded)
                     k = seeded_delay(p.seed, nn, jj, p.P, p.per_sub ? 0 : f, p.L);
-                else if (p.mode == kModeReplay)
+                else
                     k = p.delays[((nn - p.n0) * p.P + jj) * 2 + f];
             }
             kb = k;
@@ -251,7 +332,7 @@ __device__ void produce(const Params &p, long long lo, long long hi, int PD, uin
             // lane 0 waits for the consumers to release the stage, then the
             // whole warp may overwrite it
             int freed = 1;
-            if (lane == 0) freed = wait_mbar(&empty[st], (use - 1u) & 1u, p, s_abort, kWhereEmpty);
+            if (lane == 0) freed = wait_mbar(&empty[st], (use - 1u) & 1u, p, s_abort, kWhereEmpty, 8 * p.timeout_ns);
             freed = __shfl_sync(kAll, freed, 0);
             __syncwarp();
             if (!freed) { ok = false; break; }
@@ -264,7 +345,7 @@ __device__ void produce(const Params &p, long long lo, long long hi, int PD, uin
         if (p.mode == kModeSync && step > 0 && j == lo) {
             int good = 1;
             if (lane == 0)
-                good = wait_grid(p, s_abort, p.gbar_base + (unsigned long long)step * (unsigned long long)p.G, n);
+                good = wait_grid(p, p.gbar_base + (unsigned long long)step * (unsigned long long)p.G, n);
             good = __shfl_sync(kAll, good, 0);
             if (!good) { ok = false; break; }
         }
@@ -285,34 +366,39 @@ __device__ void produce(const Params &p, long long lo, long long hi, int PD, uin
             // the neighbour is the same CTA (one CTA, periodic wrap): there the
             // neighbour's level n comes from the tile just before this one.
             const bool cross = (f == 0) ? (j == lo) : (j == hi - 1);
-            long long kmax = n - S_LEV + 1;           // start-up: never below level 0
+            // largest delay at the start of the pass such that the last inner
+            // step stays within L, and no level below 0 is ever read
+            long long kmax = n - S_LEV + 1;
             if (kmax < 0) kmax = 0;
-            if (kmax > p.L) kmax = p.L;
+            if (kmax > p.L - (len - 1)) kmax = p.L - (len - 1);
             long long k = f ? kr1 : kr0;
+            if (p.mode == kModeFree || p.mode == kModeSync) k = 0;
             if (k > kmax) k = kmax;
             if (k < 0) k = 0;
             if (cross && p.mode != kModeSync) {
                 const unsigned long long *fl = p.flag + q * 2 + (1 - f);
                 const long long need = (p.mode == kModeFree) ? n - kmax : n - k;
                 unsigned long long seen = 0;
-                if (!wait_flag(p, s_abort, fl, need, &seen, n, q)) {
+                if (!wait_flag(p, fl, need, &seen, n, q)) {
                     good = 0;
                 } else if (p.mode == kModeFree) {
                     const long long avail = ((long long)seen < n) ? (long long)seen : n;
                     k = n - avail;
                 }
-            } else if (p.mode == kModeFree) {
-                k = 0;    // same CTA, not an edge: level n is always there
             }
             if (good) {
-                my_hist[k] += 1u;
-                if (p.delays && p.mode != kModeReplay) p.delays[(step * p.P + j) * 2 + f] = (int8_t)k;
+                for (int i = 0; i < len; ++i) {
+                    my_hist[k + i] += 1u;
+                    if (p.delays && p.mode != kModeReplay)
+                        p.delays[((step + i) * p.P + j) * 2 + f] = (int8_t)(k + i);
+                }
                 reinterpret_cast<volatile int *>(sb)[f] = (int)k;
+                if (f == 0) reinterpret_cast<volatile int *>(sb)[2] = len;
                 const unsigned char *rbase = p.ring + ((size_t)q * 2 + (1 - f)) * kRingEntry;
-                for (int m = 0; m < S_LEV; ++m) {
-                    if (m > 0 && k == 0) break;
+                const int levels = (k == 0 && len == 1) ? 1 : S_LEV;
+                for (int m = 0; m < levels; ++m) {
                     const long long lv = n - k - m;
-                    cp_async16(sb + kHeaderBytes + (f * kMaxS + m) * kRingEntry,
+                    cp_async16(sb + kRawOff + (f * kMaxS + m) * kRingEntry,
                                rbase + (size_t)(lv & (p.T - 1)) * slot_stride);
                 }
             }
@@ -322,11 +408,29 @@ __device__ void produce(const Params &p, long long lo, long long hi, int PD, uin
         mbar_arrive_on_copies(&full[st]);
         if (lane < 2) mbar_arrive(&full[st]);
 
+        ++r;
         if (++st == PD) { st = 0; ++use; }
-        if (++j == hi) { j = lo; ++n; }
+        if (++j == hi) { j = lo; n += len; }
     }
-    if (!ok) *s_abort = 1;
+    // let every issued copy land, and the stage phases they complete become
+    // visible, before the abort word is raised: consumers then agree on which
+    // stages are complete and leave at the same tile
     cp_async_wait_all();
+    __syncwarp();
+    if (!ok) {
+        if (lane == 0) {
+            const long long first = r > PD ? r - PD : 0;
+            for (long long q = first; q < r; ++q) {
+                const unsigned long long t0 = global_ns();
+                while (!mbar_try_wait(&full[q % PD], (unsigned)((q / PD) & 1)) &&
+                       (long long)(global_ns() - t0) < p.timeout_ns) {
+                }
+            }
+            __threadfence_block();
+            *s_abort = 1;
+        }
+        __syncwarp();
+    }
     if (lane < 2) {
         for (int i = 0; i <= p.L && i <= kMaxL; ++i)
             if (my_hist[i]) atomicAdd(p.hist + i, (unsigned long long)my_hist[i]);
@@ -338,98 +442,121 @@ __device__ void produce(const Params &p, long long lo, long long hi, int PD, uin
 // ---------------------------------------------------------------------------
 template <typename T, int ORDER>
 __device__ void consume(const Params &p, long long lo, long long hi, int PD, uint64_t *full, uint64_t *empty,
-                        volatile int *s_abort, unsigned char *stages, const T *tab)
+                        volatile int *s_abort, unsigned char *stages, unsigned char *work, const T *tab)
 {
     constexpr int R = ORDER / 2;
     constexpr int S_LEV = ORDER / 2 + 1;
     constexpr int NV = 4 + 2 * R;
     const int t = threadIdx.x;
     const long long S = hi - lo;
-    const long long Q = p.n_steps * S;
+    const long long n_end = p.n0 + p.n_steps;
     const int NG = (int)(p.M / 4);
     const T cA = (T)p.cA, cB = (T)p.cB, dtA = (T)p.dtA;
     const size_t slot_stride = (size_t)p.P * 2 * kRingEntry;
     const T *sj = tab, *cj = tab + p.M, *spt = tab + 2 * p.M, *cpt = spt + S;
+    T *wtile = reinterpret_cast<T *>(work + kTileOff);
 
     int st = 0;
     unsigned use = 0;
     long long n = p.n0, j = lo;
-    for (long long r = 0; r < Q; ++r) {
-        if (!wait_mbar(&full[st], use & 1u, p, s_abort, kWhereFull)) break;
+    while (n < n_end) {
+        if (!wait_full(&full[st], use & 1u, p, s_abort)) break;
         const unsigned char *sb = stages + (size_t)st * p.stage_bytes;
-        const T *tile = reinterpret_cast<const T *>(sb + kTileOff);
+        T *stile = reinterpret_cast<T *>(const_cast<unsigned char *>(sb) + kTileOff);
         const int k0 = reinterpret_cast<const volatile int *>(sb)[0];
         const int k1 = reinterpret_cast<const volatile int *>(sb)[1];
+        const int len = reinterpret_cast<const volatile int *>(sb)[2];
         T sp = 0, cp = 0;
         if (p.forcing) { sp = spt[j - lo]; cp = cpt[j - lo]; }
         T *ug = reinterpret_cast<T *>(p.u) + (size_t)j * p.M;
-        const long long slot = (n + 1) & (p.T - 1);
-        const bool pub_ok = !(p.skip_publish && blockIdx.x == 0 && n + 1 > p.skip_step);
+        const bool edge_pub = !(p.skip_publish && blockIdx.x == 0);
 
-        for (int g = t; g < NG; g += kConsumers) {
-            T v[NV];
-            lds<T, 4>(tile + 4 * g, v + R);
-            if (g == 0) {
+        for (int i = 0; i < len; ++i) {
+            const T *src = (i & 1) ? wtile : stile;
+            T *dst = (i & 1) ? stile : wtile;
+            const bool last = (i == len - 1);
+            const long long lev = n + i + 1;                 // level being computed
+            const long long slot = lev & (p.T - 1);
+            const bool pub_ok = edge_pub || lev <= p.skip_step;
+            for (int g = t; g < NG; g += kConsumers) {
+                T v[NV];
+                lds<T, 4>(src + 4 * g, v + R);
+                if (g == 0 && i == 0) {
 #pragma unroll
-                for (int i = 0; i < R; ++i)
-                    v[i] = approx_halo<T, S_LEV>(sb + kHeaderBytes, k0, i);
-            } else {
-                lds<T, R>(tile + 4 * g - R, v);
-            }
-            if (g == NG - 1) {
-#pragma unroll
-                for (int i = 0; i < R; ++i)
-                    v[R + 4 + i] = approx_halo<T, S_LEV>(sb + kHeaderBytes + kMaxS * kRingEntry, k1, i);
-            } else {
-                lds<T, R>(tile + 4 * g + 4, v + R + 4);
-            }
-            T fo[4] = {0, 0, 0, 0};
-            if (p.forcing) {
-                T s4[4], c4[4];
-                lds<T, 4>(sj + 4 * g, s4);
-                lds<T, 4>(cj + 4 * g, c4);
-#pragma unroll
-                for (int e = 0; e < 4; ++e) fo[e] = dtA * (sp * c4[e] + cp * s4[e]);
-            }
-            T out[4];
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const T c = v[e + R];
-                T a, b;
-                if constexpr (ORDER == 2) {
-                    a = v[e + 2] - v[e];
-                    b = (v[e + 2] + v[e]) - (T)2 * c;
+                    for (int q = 0; q < R; ++q) v[q] = approx_halo<T, S_LEV>(sb + kRawOff, k0, q);
                 } else {
-                    a = (T)8 * (v[e + 3] - v[e + 1]) - (v[e + 4] - v[e]);
-                    b = (T)16 * (v[e + 3] + v[e + 1]) - (v[e + 4] + v[e]) - (T)30 * c;
+                    lds<T, R>(src + 4 * g - R, v);   // inner steps: halo sits in the pad
                 }
-                out[e] = c + ((cB * b - cA * c * a) + fo[e]);
+                if (g == NG - 1 && i == 0) {
+#pragma unroll
+                    for (int q = 0; q < R; ++q)
+                        v[R + 4 + q] = approx_halo<T, S_LEV>(sb + kRawOff + kMaxS * kRingEntry, k1, q);
+                } else {
+                    lds<T, R>(src + 4 * g + 4, v + R + 4);
+                }
+                T fo[4] = {0, 0, 0, 0};
+                if (p.forcing) {
+                    T s4[4], c4[4];
+                    lds<T, 4>(sj + 4 * g, s4);
+                    lds<T, 4>(cj + 4 * g, c4);
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) fo[e] = dtA * (sp * c4[e] + cp * s4[e]);
+                }
+                T out[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const T c = v[e + R];
+                    T a, b;
+                    if constexpr (ORDER == 2) {
+                        a = v[e + 2] - v[e];
+                        b = (v[e + 2] + v[e]) - (T)2 * c;
+                    } else {
+                        a = (T)8 * (v[e + 3] - v[e + 1]) - (v[e + 4] - v[e]);
+                        b = (T)16 * (v[e + 3] + v[e + 1]) - (v[e + 4] + v[e]) - (T)30 * c;
+                    }
+                    out[e] = c + ((cB * b - cA * c * a) + fo[e]);
+                }
+                if (last) stg4<T>(ug + 4 * g, out);
+                else sts4<T>(dst + 4 * g, out);
+                // publish the new boundary values and release the edge flag
+                if (g == 0) {
+                    unsigned char *e = p.ring + (size_t)slot * slot_stride + ((size_t)j * 2 + 0) * kRingEntry;
+                    st_entry<T, R>(e, out);
+                    if (p.mode == kModeSync) __threadfence();
+                    if (j == lo && pub_ok) st_release(p.flag + j * 2 + 0, (unsigned long long)lev);
+                    if (!last) {
+                        // left halo of the next inner step, delay k0 + i + 1
+#pragma unroll
+                        for (int q = 0; q < R; ++q)
+                            dst[q - R] = approx_halo<T, S_LEV>(sb + kRawOff, k0 + i + 1, q);
+                    }
+                }
+                if (g == NG - 1) {
+                    unsigned char *e = p.ring + (size_t)slot * slot_stride + ((size_t)j * 2 + 1) * kRingEntry;
+                    st_entry<T, R>(e, out + 4 - R);
+                    if (p.mode == kModeSync) __threadfence();
+                    if (j == hi - 1 && pub_ok) st_release(p.flag + j * 2 + 1, (unsigned long long)lev);
+                    if (!last) {
+#pragma unroll
+                        for (int q = 0; q < R; ++q)
+                            dst[p.M + q] = approx_halo<T, S_LEV>(sb + kRawOff + kMaxS * kRingEntry, k1 + i + 1, q);
+                    }
+                }
             }
-            stg4<T>(ug + 4 * g, out);
-            // publish the new boundary values (level n+1) and release the flag
-            if (g == 0) {
-                unsigned char *e = p.ring + (size_t)slot * slot_stride + ((size_t)j * 2 + 0) * kRingEntry;
-                st_entry<T, R>(e, out);
-                if (p.mode == kModeSync) __threadfence();
-                if (j == lo && pub_ok) st_release(p.flag + j * 2 + 0, (unsigned long long)(n + 1));
-            }
-            if (g == NG - 1) {
-                unsigned char *e = p.ring + (size_t)slot * slot_stride + ((size_t)j * 2 + 1) * kRingEntry;
-                st_entry<T, R>(e, out + 4 - R);
-                if (p.mode == kModeSync) __threadfence();
-                if (j == hi - 1 && pub_ok) st_release(p.flag + j * 2 + 1, (unsigned long long)(n + 1));
+            if (!last) consumer_sync();
+        }
+        // synchronous algorithm: arrive at the grid barrier once the CTA has
+        // finished step n (the consumers' named barrier orders their writes)
+        if (p.mode == kModeSync && j == hi - 1) {
+            consumer_sync();
+            if (t == 0) {
+                __threadfence();
+                atomicAdd(p.gbar, 1ull);
             }
         }
         mbar_arrive(&empty[st]);
-        // synchronous algorithm: arrive at the grid barrier once the CTA has
-        // finished step n (all consumers released the last tile of the step)
-        if (p.mode == kModeSync && j == hi - 1 && t == 0) {
-            if (!wait_mbar(&empty[st], use & 1u, p, s_abort, kWhereEmpty)) break;
-            __threadfence();
-            atomicAdd(p.gbar, 1ull);
-        }
         if (++st == PD) { st = 0; ++use; }
-        if (++j == hi) { j = lo; ++n; }
+        if (++j == hi) { j = lo; n += len; }
     }
 }
 
@@ -446,6 +573,7 @@ __global__ void __launch_bounds__(kThreads, 2) at_stepper(const Params p)
     volatile int *s_abort = reinterpret_cast<volatile int *>(misc);
     unsigned *s_hist = reinterpret_cast<unsigned *>(misc + 16);     // [2][kMaxL+1]
     unsigned char *stages = smem + p.stage_off;
+    unsigned char *work = smem + p.work_off;
     T *tab = reinterpret_cast<T *>(smem + p.tab_off);
 
     const long long c = blockIdx.x;
@@ -487,7 +615,7 @@ __global__ void __launch_bounds__(kThreads, 2) at_stepper(const Params p)
     if (threadIdx.x >= kConsumers)
         produce<T, ORDER>(p, lo, hi, PD, full, empty, s_abort, stages, s_hist);
     else
-        consume<T, ORDER>(p, lo, hi, PD, full, empty, s_abort, stages, tab);
+        consume<T, ORDER>(p, lo, hi, PD, full, empty, s_abort, stages, work, tab);
 }
 
 // ---------------------------------------------------------------------------

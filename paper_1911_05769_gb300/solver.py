@@ -19,7 +19,7 @@ class Solver:
 
     def __init__(self, N, P, order, L, nu, dt, *, dtype="f64", length=2 * math.pi, origin=0.0,
                  forcing_amp=0.0, seed=0, flags=0, timeout_ns=0, max_ctas=0, stages=0,
-                 test_skip_step=0, stream=None, device=None):
+                 test_skip_step=0, steps_per_pass=0, stream=None, device=None):
         import torch
         self.torch = torch
         dev = torch.device("cuda", torch.cuda.current_device() if device is None else device)
@@ -39,6 +39,7 @@ class Solver:
         g.max_ctas = max_ctas
         g.stages = stages
         g.test_skip_step = test_skip_step
+        g.steps_per_pass = steps_per_pass
         nbytes = B.at_workspace_bytes(g, P, order, L)
         if nbytes == 0:
             raise B.AtError(B.AT_ERR_ARG, "at_workspace_bytes")

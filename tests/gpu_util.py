@@ -15,7 +15,7 @@ def rel_linf(a, b) -> float:
 
 def gpu_run(u0, *, P, order, L, nu, dt, steps, dtype="f64", mode=None, seed=0, forcing=0.0, max_ctas=0,
             stages=0, delays=None, record=False, calls=None, flags=0, timeout_ns=0, test_skip_step=0,
-            check=True):
+            steps_per_pass=0, check=True):
     """Runs the CUDA solver; returns dict(u, hist, m1, m2, rec, info, rc)."""
     import torch
 
@@ -23,7 +23,8 @@ def gpu_run(u0, *, P, order, L, nu, dt, steps, dtype="f64", mode=None, seed=0, f
     mode = AT_SEEDED if mode is None else mode
     N = len(u0)
     s = Solver(N, P, order, L, nu, dt, dtype=dtype, seed=seed, forcing_amp=forcing, max_ctas=max_ctas,
-               stages=stages, flags=flags, timeout_ns=timeout_ns, test_skip_step=test_skip_step)
+               stages=stages, flags=flags, timeout_ns=timeout_ns, test_skip_step=test_skip_step,
+               steps_per_pass=steps_per_pass)
     s.set_state(torch.from_numpy(np.ascontiguousarray(u0)).cuda())
     calls = calls or [steps]
     assert sum(calls) == steps

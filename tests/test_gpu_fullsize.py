@@ -84,6 +84,18 @@ def test_full_size_free_fp32_replays(require_gpu, u0_full):
     _check_windows(g["u"], u0_full, dt, steps, "replay", "f32", _samples(g["info"].ctas), delays=rec)
 
 
+def test_full_size_blocked_free_fp32_replays(require_gpu, u0_full):
+    """The benchmark's headline mode: free running with passes of L+1 levels."""
+    from paper_1911_05769_gb300 import AT_FREE
+    dt = _dt(u0_full)
+    steps = 1000
+    g = gpu_run(u0_full, P=CFG["P"], order=CFG["order"], L=CFG["L"], nu=CFG["nu"], dt=dt, steps=steps,
+                dtype="f32", mode=AT_FREE, forcing=CFG["forcing_amp"], record=True, steps_per_pass=CFG["L"] + 1)
+    rec = g["rec"]
+    assert rec.min() >= 0 and rec.max() <= CFG["L"]
+    _check_windows(g["u"], u0_full, dt, steps, "replay", "f32", _samples(g["info"].ctas), delays=rec)
+
+
 def test_full_size_sync_fp32(require_gpu, u0_full):
     from paper_1911_05769_gb300 import AT_SYNC
     dt = _dt(u0_full)

@@ -179,3 +179,52 @@ def test_empty_step_is_a_no_op(require_gpu):
     u0, dt = _setup(N, 0.02)
     g = gpu_run(u0, P=P, order=2, L=1, nu=0.02, dt=dt, steps=0, calls=[0], mode=AT_SEEDED)
     assert np.array_equal(g["u"], u0)
+
+
+BLOCKED = [
+    # dtype, order, L, steps_per_pass, P, M, max_ctas, steps, calls
+    ("f64", 4, 3, 4, 96, 256, 7, 300, None),
+    ("f64", 2, 2, 3, 64, 128, 5, 301, [100, 1, 200]),
+    ("f64", 4, 3, 2, 40, 1028, 3, 150, None),
+    ("f32", 4, 3, 4, 256, 1024, 0, 200, None),
+    ("f64", 2, 1, 2, 1, 256, 0, 120, None),        # one subdomain, its own neighbour
+    ("f64", 4, 3, 4, 40, 4, 6, 100, [3, 97]),      # M = 4 (N = 160: a coarser grid is unstable for
+                                                   # forward Euler itself at this CFL number)
+]
+
+
+@pytest.mark.parametrize("dtype,order,L,spp,P,M,max_ctas,steps,calls", BLOCKED)
+def test_blocked_free_running_replays_exactly(require_gpu, dtype, order, L, spp, P, M, max_ctas, steps, calls):
+    """Temporal blocking in free-running mode: a tile advances `spp` levels per
+    pass with halos extrapolated from the levels available at the start of the
+    pass (delay k0 + i at inner step i).  The recorded delays, replayed by the
+    oracle, reproduce the result to the bar; every delay stays within L."""
+    from paper_1911_05769_gb300 import AT_FREE
+    N = P * M
+    u0, dt = _setup(N, 0.02, kind="fourier" if N >= 256 else "two_modes")
+    kw = dict(P=P, order=order, L=L, nu=0.02, dt=dt, steps=steps, forcing=0.1)
+    g = gpu_run(u0, dtype=dtype, mode=AT_FREE, max_ctas=max_ctas, record=True, calls=calls,
+                steps_per_pass=spp, **kw)
+    rec = g["rec"]
+    assert rec.min() >= 0 and rec.max() <= L
+    assert g["hist"].sum() == steps * P * 2
+    ref, hist = oracle_run(u0, mode="replay", delays=rec, **kw)
+    assert rel_linf(g["u"], ref) <= TOL[dtype]
+    assert np.array_equal(g["hist"], hist)
+    if spp > 1 and calls is None:
+        assert rec[:, :, :].max() >= 1      # the blocking did create delays
+
+
+def test_blocked_passes_of_L_plus_1_are_deterministic(require_gpu):
+    """With passes of L+1 levels every face must wait for level n exactly, so
+    the delays are fixed by the pass structure: single levels while n < s-1,
+    then k = (n - (s-1)) mod (L+1) within each full pass."""
+    from paper_1911_05769_gb300 import AT_FREE
+    N, P, L, order, steps = 64 * 256, 64, 3, 4, 2 + 4 * 50
+    s_lev = order // 2 + 1
+    u0, dt = _setup(N, 0.02, kind="fourier")
+    g = gpu_run(u0, P=P, order=order, L=L, nu=0.02, dt=dt, steps=steps, mode=AT_FREE, max_ctas=6, record=True,
+                steps_per_pass=L + 1)
+    n = np.arange(steps)
+    want = np.where(n < s_lev - 1, 0, (n - (s_lev - 1)) % (L + 1)).astype(np.int8)
+    assert np.array_equal(g["rec"], np.broadcast_to(want[:, None, None], g["rec"].shape))

@@ -59,6 +59,9 @@ def parse():
     ap.add_argument("--N", type=int, default=0, help="smaller N for profiling runs (P scales, M stays 1024)")
     ap.add_argument("--spp", type=int, default=-1,
                     help="levels per pass of the free-running arm (temporal blocking); -1 = L+1")
+    ap.add_argument("--M", type=int, default=0, help="points per subdomain for experiments (default 1024)")
+    ap.add_argument("--order", type=int, default=0, help="stencil order for experiments (default 4)")
+    ap.add_argument("--forcing", type=float, default=-1.0, help="forcing amplitude for experiments (default 0.1)")
     return ap.parse_args()
 
 
@@ -225,6 +228,12 @@ def gpu_arm(args, ws, rank, local, pg):
     cfg = W.config(WORKLOAD)
     if args.N:
         cfg = dict(cfg, N=args.N, P=args.N // (cfg["N"] // cfg["P"]))
+    if args.M:
+        cfg = dict(cfg, P=cfg["N"] // args.M)
+    if args.order:
+        cfg = dict(cfg, order=args.order)
+    if args.forcing >= 0:
+        cfg = dict(cfg, forcing_amp=args.forcing)
     N, P, order, L, nu, A = cfg["N"], cfg["P"], cfg["order"], cfg["L"], cfg["nu"], cfg["forcing_amp"]
     u0 = W.initial_field(cfg)
     _, dx = W.grid(N)

@@ -89,9 +89,10 @@ typedef struct at_grid {
   size_t   workspace_bytes;
   void    *stream;          /* cudaStream_t (NULL = legacy default stream)         */
   int64_t  timeout_ns;      /* bound of every device wait; 0 = 1 s                 */
-  int32_t  max_ctas;        /* CTAs: 0 = one per SM; else this many (capped at P;
-                               AT_ERR_RESIDENCY if they cannot all be resident)   */
-  int32_t  stages;          /* 0 = default pipeline depth (tiles in flight per CTA)*/
+  int32_t  max_ctas;        /* CTAs: 0 = all that can be resident at once (capped */
+                            /* at P); else this many (AT_ERR_RESIDENCY if they    */
+                            /* cannot all be resident)                            */
+  int32_t  stages;          /* tiles in flight per CTA: 0 = 16; at least 4        */
   int64_t  test_skip_step;  /* level after which AT_FLAG_TEST_SKIP_PUBLISH acts    */
   int32_t  steps_per_pass;  /* AT_FREE only: levels advanced per pass over a tile  */
                             /* (temporal blocking), 0 or 1 = none, at most L+1    */
@@ -123,7 +124,7 @@ size_t at_workspace_bytes(const at_grid *grid, int64_t P, int scheme_order, int 
  * stencils of order scheme_order (2 or 4, Sec. 3.2) with AT boundary stencils
  * (Eq. AT1/AT2; order 4 extrapolates quadratically in time), maximal delay L
  * (0..16, Sec. 2 and Algorithm 2), viscosity nu >= 0 and time step dt > 0.
- * Requires N % P == 0, M = N/P a multiple of 4 with M >= 4, M*word <= 16 KiB,
+ * Requires N % P == 0, M = N/P a multiple of 4 with 4 <= M <= 1024,
  * and nu dt / dx^2 <= 1/2 (order 2) or 3/8 (order 4) unless
  * AT_FLAG_ALLOW_UNSTABLE.  Checks that the kernel's CTAs can be co-resident.
  * The state is undefined until at_set_state().  *out receives the handle. */

@@ -1,6 +1,7 @@
 """Builds the CUDA library ``libat.so`` in-tree for sm_103a with nvcc.
 
-One translation unit, one ``-gencode``; static CUDA runtime.  Run as
+Three translation units (host ABI, FP32 kernels, FP64 kernels) compiled in
+parallel, one ``-gencode``; static CUDA runtime.  Run as
 ``python -m paper_1911_05769_gb300.build`` or through ``__graft_entry__.build()``.
 """
 from __future__ import annotations
@@ -14,14 +15,14 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libat.so")
-SOURCES = [os.path.join(CSRC, "at_api.cu")]
+SOURCES = [os.path.join(CSRC, f) for f in ("at_api.cu", "at_kernels_f32.cu", "at_kernels_f64.cu")]
 DEPS = SOURCES + [os.path.join(CSRC, f) for f in ("at_kernels.cuh", "at_device.cuh")] + [
     os.path.join(INCLUDE, "at.h")]
 
 NVCC_FLAGS = [
     "-O3", "-std=c++17", "-lineinfo",
     "-gencode", "arch=compute_103a,code=sm_103a",
-    "-Xcompiler", "-fPIC", "-shared",
+    "-Xcompiler", "-fPIC",
 ]
 
 
@@ -38,14 +39,32 @@ def needs_build() -> bool:
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
+    """Compiles every translation unit in parallel, then links libat.so."""
     if not force and not needs_build():
         return LIB
-    tmp = LIB + f".{os.getpid()}.tmp"
-    cmd = [nvcc(), *NVCC_FLAGS, "-I", INCLUDE, *SOURCES, "-o", tmp]
-    if verbose:
-        print(" ".join(cmd), file=sys.stderr)
-    subprocess.check_call(cmd)
-    os.replace(tmp, LIB)
+    tag = f"{os.getpid()}"
+    objs, procs = [], []
+    for src in SOURCES:
+        obj = os.path.join(HERE, os.path.basename(src)[:-3] + f".{tag}.o")
+        cmd = [nvcc(), *NVCC_FLAGS, "-I", INCLUDE, "-c", src, "-o", obj]
+        if verbose:
+            print(" ".join(cmd), file=sys.stderr)
+        procs.append(subprocess.Popen(cmd))
+        objs.append(obj)
+    rcs = [p.wait() for p in procs]
+    try:
+        if any(rcs):
+            raise subprocess.CalledProcessError(max(rcs), "nvcc")
+        tmp = LIB + f".{tag}.tmp"
+        cmd = [nvcc(), "-shared", "-gencode", "arch=compute_103a,code=sm_103a", *objs, "-o", tmp]
+        if verbose:
+            print(" ".join(cmd), file=sys.stderr)
+        subprocess.check_call(cmd)
+        os.replace(tmp, LIB)
+    finally:
+        for o in objs:
+            if os.path.exists(o):
+                os.remove(o)
     return LIB
 
 

@@ -16,6 +16,11 @@
 #include "at.h"
 #include "at_kernels.cuh"
 
+void *atk_stepper_kernel_f32(int order, int gw, bool forced);
+void *atk_stepper_kernel_f64(int order, int gw, bool forced);
+void *atk_init_kernel_f32(int order);
+void *atk_init_kernel_f64(int order);
+
 namespace {
 
 thread_local char g_err[512] = "";
@@ -77,12 +82,89 @@ int check_args(const at_grid *g, int64_t P, int order, int L)
     if (order != 2 && order != 4) return fail(AT_ERR_ARG, "scheme_order must be 2 or 4");
     if (L < 0 || L > atk::kMaxL) return fail(AT_ERR_ARG, "L must be in 0..%d", atk::kMaxL);
     const int64_t M = N / P;
-    const int w = g->dtype == AT_F64 ? 8 : 4;
     if (M % 4 != 0 || M < 4) return fail(AT_ERR_ARG, "M = N/P must be a multiple of 4 (M=%lld)", (long long)M);
-    if (M * w > 16384) return fail(AT_ERR_ARG, "M * word size must be <= 16 KiB (M=%lld)", (long long)M);
+    if (M > atk::kMaxM) return fail(AT_ERR_ARG, "M = N/P must be <= %d (M=%lld)", atk::kMaxM, (long long)M);
     if (!(g->length[0] > 0.0)) return fail(AT_ERR_ARG, "length[0] must be positive");
     if (g->steps_per_pass < 0 || g->steps_per_pass > L + 1)
         return fail(AT_ERR_ARG, "steps_per_pass must be in 0..L+1 (the delay bound), got %d", g->steps_per_pass);
+    return AT_OK;
+}
+
+// Groups of 4 points each lane of a consumer warp keeps in registers: M/4
+// groups over 32 lanes, rounded up to a power of two.
+int groups_per_lane(int64_t M)
+{
+    const int64_t ng = M / 4;
+    int g = 1;
+    while ((int64_t)g * 32 < ng) g <<= 1;
+    return g;
+}
+
+// Passes of at_step over the subdomains: one level per pass while the level
+// is below s-1, then passes of sb levels (the last one shorter).
+long long count_passes(long long n0, long long n_steps, int s, int sb)
+{
+    long long single = (s - 1) - n0;
+    if (single < 0) single = 0;
+    if (single > n_steps) single = n_steps;
+    const long long rest = n_steps - single;
+    return single + (rest + sb - 1) / sb;
+}
+
+// The stepper and init kernels for a word size, order, subdomain size and
+// forcing (instantiated in at_kernels_f32.cu / at_kernels_f64.cu).
+void pick_kernels(int w, int order, int64_t M, bool forced, void **stepper, void **init)
+{
+    const int gw = groups_per_lane(M);
+    if (w == 8) {
+        *stepper = atk_stepper_kernel_f64(order, gw, forced);
+        *init = atk_init_kernel_f64(order);
+    } else {
+        *stepper = atk_stepper_kernel_f32(order, gw, forced);
+        *init = atk_init_kernel_f32(order);
+    }
+}
+
+// Chooses the CTA count (all co-resident CTAs unless max_ctas is set, at most
+// one PE per subdomain) and the stages per PE that fit in shared memory, and
+// sets the kernel's dynamic shared-memory size.
+int launch_shape(int64_t M, int w, int64_t P, bool forced, int max_ctas, int stages, int sms, int smem_optin,
+                 void *kernel, int *G_out, int *stages_out, atk::SmemLayout *sl_out, int *smem_out,
+                 long long *smax_out)
+{
+    auto layout_for = [&](int G, int st, long long *smax) {
+        const int64_t E = (int64_t)G * atk::kWarps;
+        *smax = (P + E - 1) / E;
+        const long long tab = forced ? 2 * M + 2LL * atk::kWarps * *smax : 0;
+        return atk::smem_layout(M, w, st, tab);
+    };
+    // CTAs needed for one PE per subdomain at most
+    const int gmax = (int)((P + atk::kWarps - 1) / atk::kWarps);
+    int G = max_ctas > 0 ? max_ctas : sms;
+    if (G > gmax) G = gmax;
+    long long smax = 0;
+    while (stages > atk::kMinStages && layout_for(G, stages, &smax).total > smem_optin) --stages;
+    atk::SmemLayout sl = layout_for(G, stages, &smax);
+    if (sl.total > smem_optin) return fail(AT_ERR_RESIDENCY, "shared memory %lld exceeds %d", sl.total, smem_optin);
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sl.total);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
+    int occ = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, atk::kThreads, (size_t)sl.total);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+    if (max_ctas <= 0 && occ > 1) {
+        // all co-resident CTAs (fewer subdomains per PE only shrinks the tables)
+        int want = occ * sms;
+        if (want > gmax) want = gmax;
+        long long sm2 = 0;
+        if (layout_for(want, stages, &sm2).total <= sl.total) { G = want; sl = layout_for(G, stages, &smax); }
+    }
+    if (occ < 1 || (int64_t)occ * sms < G)
+        return fail(AT_ERR_RESIDENCY, "%d CTAs cannot be co-resident (occupancy %d per SM)", G, occ);
+    *G_out = G;
+    *stages_out = stages;
+    *sl_out = sl;
+    *smem_out = (int)sl.total;
+    *smax_out = smax;
     return AT_OK;
 }
 
@@ -98,7 +180,8 @@ struct at_solver {
     cudaStream_t stream;
     int device, sm_count;
     int G, stages, sb, smem;
-    long long stage_bytes, stage_off, work_off, tab_off;
+    long long smax;
+    atk::SmemLayout sl;
     int64_t step;
     unsigned long long gbar_count;
     bool has_state;
@@ -162,46 +245,18 @@ int at_create(const at_grid *grid, int64_t P, int scheme_order, int L, double nu
     h->stream = static_cast<cudaStream_t>(grid->stream);
     h->device = dev; h->sm_count = sms;
 
-    if (w == 8) {
-        h->kernel = scheme_order == 2 ? (void *)atk::at_stepper<double, 2> : (void *)atk::at_stepper<double, 4>;
-        h->init_kernel = scheme_order == 2 ? (void *)atk::at_init<double, 1> : (void *)atk::at_init<double, 2>;
-    } else {
-        h->kernel = scheme_order == 2 ? (void *)atk::at_stepper<float, 2> : (void *)atk::at_stepper<float, 4>;
-        h->init_kernel = scheme_order == 2 ? (void *)atk::at_init<float, 1> : (void *)atk::at_init<float, 2>;
-    }
+    pick_kernels(w, scheme_order, h->M, grid->forcing_amp != 0.0, &h->kernel, &h->init_kernel);
 
-    // launch shape: one CTA per SM by default (max_ctas overrides, e.g. two
-    // per SM), at most one per subdomain; stages sized to shared memory
-    int G = grid->max_ctas > 0 ? grid->max_ctas : sms;
-    if (P < G) G = (int)P;
-    int stages = grid->stages > 0 ? grid->stages : (w == 4 ? 16 : 12);
+    // launch shape: by default as many CTAs of kWarps processing elements
+    // (warps) as can be resident, at most one PE per subdomain; `stages`
+    // tile buffers per PE, fewer if shared memory is short
     const int sb = grid->steps_per_pass > 0 ? grid->steps_per_pass : 1;
-    const int64_t Smax = (P + G - 1) / G;
-    const long long tab_words = grid->forcing_amp != 0.0 ? 2 * h->M + 2 * Smax : 0;
-    auto smem_for = [&](int st) { return (size_t)atk::smem_layout(h->M, w, st, sb > 1, tab_words).total; };
-    while (stages > 1 && smem_for(stages) > (size_t)smem_optin) --stages;
-    if (smem_for(stages) > (size_t)smem_optin) {
-        delete h;
-        return fail(AT_ERR_RESIDENCY, "shared memory %zu exceeds %d", smem_for(stages), smem_optin);
-    }
-    const atk::SmemLayout sl = atk::smem_layout(h->M, w, stages, sb > 1, tab_words);
-    h->stages = stages;
+    int stages = grid->stages > 0 ? grid->stages : 3;
+    if (stages < atk::kMinStages) stages = atk::kMinStages;
+    int rc2 = launch_shape(h->M, w, P, grid->forcing_amp != 0.0, grid->max_ctas, stages, sms, smem_optin,
+                           h->kernel, &h->G, &h->stages, &h->sl, &h->smem, &h->smax);
+    if (rc2 != AT_OK) { delete h; return rc2; }
     h->sb = sb;
-    h->stage_bytes = sl.stage_bytes;
-    h->stage_off = sl.stage_off;
-    h->work_off = sl.work_off;
-    h->tab_off = sl.tab_off;
-    h->smem = (int)sl.total;
-    e = cudaFuncSetAttribute(h->kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, h->smem);
-    if (e != cudaSuccess) { delete h; return cuda_fail(e, "cudaFuncSetAttribute"); }
-    int occ = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, h->kernel, atk::kThreads, h->smem);
-    if (e != cudaSuccess) { delete h; return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor"); }
-    if (occ < 1 || (int64_t)occ * sms < G) {
-        delete h;
-        return fail(AT_ERR_RESIDENCY, "%d CTAs cannot be co-resident (occupancy %d per SM)", G, occ);
-    }
-    h->G = G;
     h->step = 0;
     h->gbar_count = 0;
     h->has_state = false;
@@ -230,15 +285,18 @@ static atk::Params make_params(const at_solver *h)
         p.cB = h->nu * h->dt / (12.0 * h->dx * h->dx);
     }
     p.dtA = h->dt * h->g.forcing_amp;
-    p.forcing = h->g.forcing_amp != 0.0 ? 1 : 0;
     p.x0 = h->g.origin[0];
     p.dx = h->dx;
     p.G = h->G;
+    p.E = h->G * atk::kWarps;
     p.stages = h->stages;
-    p.stage_bytes = h->stage_bytes;
-    p.stage_off = h->stage_off;
-    p.work_off = h->work_off;
-    p.tab_off = h->tab_off;
+    p.smax = h->smax;
+    p.bar_off = h->sl.bar_off;
+    p.hist_off = h->sl.hist_off;
+    p.raw_off = h->sl.raw_off;
+    p.stage_off = h->sl.stage_off;
+    p.stage_bytes = h->sl.stage_bytes;
+    p.tab_off = h->sl.tab_off;
     p.sb = 1;
     p.timeout_ns = h->g.timeout_ns;
     p.skip_publish = (h->g.flags & AT_FLAG_TEST_SKIP_PUBLISH) ? 1 : 0;
@@ -281,12 +339,13 @@ int at_step(at_solver *h, int64_t n_steps, int delay_mode, int8_t *delays)
     p.n_steps = n_steps;
     p.gbar_base = h->gbar_count;
     p.sb = delay_mode == AT_FREE ? h->sb : 1;
+    p.n_passes = count_passes(p.n0, n_steps, h->s, p.sb);
     void *args[] = {&p};
     cudaError_t e = cudaLaunchCooperativeKernel(h->kernel, dim3(h->G), dim3(atk::kThreads), args, (size_t)h->smem,
                                                 h->stream);
     if (e != cudaSuccess) return cuda_fail(e, "cudaLaunchCooperativeKernel(at_stepper)");
     h->step += n_steps;
-    if (delay_mode == AT_SYNC) h->gbar_count += (unsigned long long)n_steps * (unsigned long long)h->G;
+    if (delay_mode == AT_SYNC) h->gbar_count += (unsigned long long)n_steps * (unsigned long long)(h->G * atk::kWarps);
     return AT_OK;
 }
 
@@ -453,38 +512,13 @@ extern "C" int at_step_noalloc(const at_grid *grid, int64_t P, int scheme_order,
     h.ws = scratch;
     h.stream = static_cast<cudaStream_t>(grid->stream);
     h.device = dev; h.sm_count = sms;
-    if (w == 8) {
-        h.kernel = scheme_order == 2 ? (void *)atk::at_stepper<double, 2> : (void *)atk::at_stepper<double, 4>;
-        h.init_kernel = scheme_order == 2 ? (void *)atk::at_init<double, 1> : (void *)atk::at_init<double, 2>;
-    } else {
-        h.kernel = scheme_order == 2 ? (void *)atk::at_stepper<float, 2> : (void *)atk::at_stepper<float, 4>;
-        h.init_kernel = scheme_order == 2 ? (void *)atk::at_init<float, 1> : (void *)atk::at_init<float, 2>;
-    }
-    int G = grid->max_ctas > 0 ? grid->max_ctas : sms;
-    if (P < G) G = (int)P;
-    int stages = grid->stages > 0 ? grid->stages : (w == 4 ? 16 : 12);
-    const int64_t Smax = (P + G - 1) / G;
-    const long long tab_words = grid->forcing_amp != 0.0 ? 2 * h.M + 2 * Smax : 0;
-    auto smem_for = [&](int st) { return (size_t)atk::smem_layout(h.M, w, st, false, tab_words).total; };
-    while (stages > 1 && smem_for(stages) > (size_t)smem_optin) --stages;
-    if (smem_for(stages) > (size_t)smem_optin)
-        return fail(AT_ERR_RESIDENCY, "shared memory %zu exceeds %d", smem_for(stages), smem_optin);
-    const atk::SmemLayout sl = atk::smem_layout(h.M, w, stages, false, tab_words);
-    h.stages = stages;
+    pick_kernels(w, scheme_order, h.M, grid->forcing_amp != 0.0, &h.kernel, &h.init_kernel);
+    int stages = grid->stages > 0 ? grid->stages : 3;
+    if (stages < atk::kMinStages) stages = atk::kMinStages;
+    rc = launch_shape(h.M, w, P, grid->forcing_amp != 0.0, grid->max_ctas, stages, sms, smem_optin, h.kernel,
+                      &h.G, &h.stages, &h.sl, &h.smem, &h.smax);
+    if (rc != AT_OK) return rc;
     h.sb = 1;
-    h.stage_bytes = sl.stage_bytes;
-    h.stage_off = sl.stage_off;
-    h.work_off = sl.work_off;
-    h.tab_off = sl.tab_off;
-    h.smem = (int)sl.total;
-    e = cudaFuncSetAttribute(h.kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, h.smem);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
-    int occ = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, h.kernel, atk::kThreads, h.smem);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
-    if (occ < 1 || (int64_t)occ * sms < G)
-        return fail(AT_ERR_RESIDENCY, "%d CTAs cannot be co-resident (occupancy %d per SM)", G, occ);
-    h.G = G;
 
     // Every call starts from zeroed ring buffers, flags, status and counters:
     // the array still holds whatever the previous call left in it.
@@ -502,6 +536,7 @@ extern "C" int at_step_noalloc(const at_grid *grid, int64_t P, int scheme_order,
         p.n0 = 0;
         p.n_steps = n_steps;
         p.gbar_base = 0;
+        p.n_passes = count_passes(0, n_steps, s, 1);
         e = cudaLaunchCooperativeKernel(h.kernel, dim3(h.G), dim3(atk::kThreads), args, (size_t)h.smem, h.stream);
         if (e != cudaSuccess) return cuda_fail(e, "cudaLaunchCooperativeKernel(at_stepper)");
     }

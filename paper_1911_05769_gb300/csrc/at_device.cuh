@@ -64,6 +64,30 @@ __device__ __forceinline__ void cp_async16(void *dst_smem, const void *src_gmem)
                  : "memory");
 }
 
+// ---- bulk copy (TMA engine, async proxy) -----------------------------------
+// Arrival that also announces `bytes` of asynchronous transactions.
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// Contiguous global -> shared copy of `bytes` (multiple of 16, both ends
+// 16-byte aligned) whose completion is counted on `bar`.
+__device__ __forceinline__ void bulk_load(void *dst_smem, const void *src_gmem, unsigned bytes, uint64_t *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_addr(dst_smem)), "l"(src_gmem), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+
+// Orders this thread's earlier generic-proxy global accesses before later
+// async-proxy accesses (a bulk copy re-reading data written with st.global).
+__device__ __forceinline__ void fence_proxy_async_global()
+{
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+
 __device__ __forceinline__ void cp_async_wait_all()
 {
     asm volatile("cp.async.wait_all;" ::: "memory");
@@ -79,6 +103,19 @@ __device__ __forceinline__ unsigned long long ld_acquire(const unsigned long lon
 {
     unsigned long long v;
     asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// CTA-scope release/acquire on a 64-bit shared-memory word (per-warp progress)
+__device__ __forceinline__ void st_release_cta_shared(volatile long long *p, long long v)
+{
+    asm volatile("st.release.cta.shared.b64 [%0], %1;" ::"r"(smem_addr((const void *)p)), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ long long ld_acquire_cta_shared(const volatile long long *p)
+{
+    long long v;
+    asm volatile("ld.acquire.cta.shared.b64 %0, [%1];" : "=l"(v) : "r"(smem_addr((const void *)p)) : "memory");
     return v;
 }
 

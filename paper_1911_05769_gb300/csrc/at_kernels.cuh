@@ -1,27 +1,29 @@
 // at_kernels.cuh -- persistent weakly-synchronous AT stepper for sm_103a.
 //
 // One cooperative launch advances the whole 1D field by n_steps forward-Euler
-// steps (arXiv 1911.05769, Sec. 3.2).  CTA c owns the contiguous subdomains
-// [lo, hi) and sweeps them in step-major order.  A "tile" is one subdomain j
+// steps (arXiv 1911.05769, Sec. 3.2).  Every warp of the launch is one
+// processing element (PE) of the paper: PE e owns the contiguous subdomains
+// [lo, hi) and sweeps them in pass-major order.  A "tile" is one subdomain j
 // over one pass of `len` consecutive levels n .. n+len (len = 1 except in
-// blocked free-running mode).  Each CTA runs
-//   * one producer warp: for tile r it copies the subdomain's M state words
-//     and the neighbours' delayed boundary values (levels n-k-m, Eq. AT1/AT2)
-//     from the ring buffers into shared-memory stage r % PD with cp.async,
-//     after choosing the delays k (prescribed, replayed, or -- free running --
-//     read off the neighbour's progress flag, waiting only while the neighbour
-//     lags by more than the delay bound allows: the blocking branch of
-//     Algorithm 2);
-//   * four consumer warps: the halo approximation ("approximate" step of
-//     Algorithm 2, split form of Sec. 5.2), the unchanged central stencil of
-//     order 2 or 4 and the Euler update, `len` times on the tile held in
-//     shared memory, the final level written back in place; after every level
-//     the new boundary values go into ring slot (level mod T), followed, on
-//     the CTA's two edge faces, by a release store of the progress flag (the
-//     notified put).
-// Halo values never come from the neighbour's state array, only from the
-// ring, so each CTA updates its own subdomains in place.  Stage reuse is
-// signalled with mbarriers (full: copies landed; empty: tile consumed).
+// blocked free-running mode).  For each tile the PE
+//   * has already copied the subdomain's M state words into one of its
+//     shared-memory stages with a bulk (TMA-engine) copy, D tiles ahead;
+//   * has already chosen the delays k (prescribed, replayed, or -- free
+//     running -- read off the neighbour's progress flag, blocking only while
+//     the neighbour lags by more than the delay bound allows: the blocking
+//     branch of Algorithm 2) and copied the neighbours' delayed boundary
+//     values (levels n-k-m, Eq. AT1/AT2) from the ring buffers, one tile ahead;
+//   * approximates the halo values ("approximate" step of Algorithm 2, split
+//     form of Sec. 5.2), applies the unchanged central stencil of order 2 or
+//     4 and the Euler update `len` times on the tile held in registers
+//     (neighbour values by warp shuffles), and writes the final level back in
+//     place;
+//   * after every level writes the new boundary values into ring slot
+//     (level mod T) and, on its two edge faces, releases the face's progress
+//     flag (the notified put).
+// Halo values never come from a neighbour's state array, only from the ring,
+// so each PE updates its own subdomains in place, and a PE never waits for
+// another PE of its CTA except through the same flags.
 //
 // Blocked free-running mode (temporal blocking): a pass of len <= L+1 levels
 // uses, at inner step i, the halo extrapolated with delay k0 + i from the
@@ -31,55 +33,54 @@
 // AT_SYNC replaces the flag waits with a grid barrier between steps
 // (Algorithm 1).  Every wait is bounded by timeout_ns; on expiry the kernel
 // latches AT_ERR_TIMEOUT in the control block, raises the abort word and
-// every CTA leaves its loops.  Abort is uniform inside a CTA: the producer
-// lets all its copies land before it raises the CTA's abort word, so every
-// consumer sees the same set of completed stages and takes the same named
-// barriers.
+// every PE leaves its loop (after its copies in flight have landed).
 #pragma once
 
 #include "at_device.cuh"
 
+// Minimum resident CTAs per SM the stepper is compiled for (register cap).
+#ifndef AT_MIN_CTAS_PER_SM
+#define AT_MIN_CTAS_PER_SM 3
+#endif
+
 namespace atk {
 
-constexpr int kConsumerWarps = 4;
-constexpr int kConsumers = 32 * kConsumerWarps;   // threads 0..127
-constexpr int kThreads = kConsumers + 32;         // + one producer warp
+constexpr int kWarps = 4;                         // PEs (warps) per CTA
+constexpr int kThreads = 32 * kWarps;
 constexpr int kRingEntry = 16;                    // bytes per (slot, subdomain, face)
 constexpr int kMaxS = 3;                          // levels per halo approximation
-// stage layout: [0,16) header (k0 face 0, k0 face 1, len) | [16,112) delayed
-// ring levels [face][m] | [112,128) left halo pad | tile (M words) | 16-byte
-// right halo pad
-constexpr int kRawOff = 16;
-constexpr int kTileOff = 128;
-constexpr int kPadBytes = 16;
+constexpr int kRawBytes = 2 * kMaxS * kRingEntry; // one tile's delayed levels [face][m]
+constexpr int kMaxM = 1024;                       // points per subdomain (one warp's tile)
 constexpr int kMaxL = 16;
-constexpr int kFullArrivals = 32 + 2;             // 32 copy arrivals + 2 header writers
-constexpr int kMiscBytes = 256;                   // abort word + delay histograms
-constexpr int kConsumerBarrier = 1;               // named barrier id of the consumer warps
+constexpr int kMinStages = 2;                     // stages per PE (tile in use + one ahead)
 
 enum : int { kModeSync = 0, kModeSeeded = 1, kModeFree = 2, kModeReplay = 3 };
 enum : int {
     kCtrlStatus = 0, kCtrlAbort = 1, kCtrlCta = 2, kCtrlWhere = 3, kCtrlNb = 4, kCtrlStep = 5,
     kCtrlWords = 16
 };
-enum : int { kWhereFull = 1, kWhereEmpty = 2, kWhereFlag = 3, kWhereGrid = 4 };
+enum : int { kWhereTile = 1, kWhereRing = 2, kWhereFlag = 3, kWhereGrid = 4 };
 constexpr int kStatusTimeout = -5;
 
-// Shared-memory layout of the stepper, shared by the host (launch set-up) and
-// the kernel.
+// Shared-memory layout of one CTA, shared by the host (launch set-up) and the
+// kernel: per PE `stages` mbarriers, delay counters, two raw-level buffers and
+// `stages` tile buffers; then the forcing tables (sin/cos of the offsets in a
+// subdomain, and of each PE's subdomain origins).
 struct SmemLayout {
-    long long stage_bytes, stage_off, work_off, tab_off, total;
+    long long bar_off, hist_off, raw_off, stage_off, stage_bytes, tab_off, total;
 };
 
 __host__ __device__ inline long long round_up(long long x, long long a) { return (x + a - 1) / a * a; }
 
-__host__ __device__ inline SmemLayout smem_layout(long long M, int word, int stages, bool work, long long tab_words)
+__host__ __device__ inline SmemLayout smem_layout(long long M, int word, int stages, long long tab_words)
 {
     SmemLayout l;
-    l.stage_bytes = round_up(kTileOff + M * word + kPadBytes, 128);
-    l.stage_off = round_up(16LL * stages + kMiscBytes, 128);
-    l.work_off = l.stage_off + (long long)stages * l.stage_bytes;
-    l.tab_off = l.work_off + (work ? l.stage_bytes : 0);
+    l.bar_off = 0;
+    l.hist_off = round_up(8LL * kWarps * stages, 16);
+    l.raw_off = round_up(l.hist_off + 4LL * kWarps * 2 * (kMaxL + 1), 128);
+    l.stage_off = round_up(l.raw_off + 2LL * kWarps * kRawBytes, 128);
+    l.stage_bytes = round_up(M * word, 128);
+    l.tab_off = l.stage_off + (long long)kWarps * stages * l.stage_bytes;
     l.total = l.tab_off + tab_words * word;
     return l;
 }
@@ -95,24 +96,26 @@ struct Params {
     long long N, P, M;
     int L, T, mode, per_sub;
     long long n0, n_steps;
+    long long n_passes;        // passes over each PE's subdomains in this launch
     int sb;                    // levels per pass (temporal blocking, free mode)
     unsigned long long seed;
     double cA, cB, dtA;        // dt/(2dx) | dt/(12dx);  nu dt/dx^2 | nu dt/(12dx^2);  dt A
     double x0, dx;
-    int forcing;
     int G;                     // CTAs
-    int stages;                // stage buffers per CTA
-    long long stage_bytes, stage_off, work_off, tab_off;
+    int E;                     // PEs = G * kWarps
+    int stages;                // tile buffers per PE
+    long long smax;            // most subdomains of any PE
+    long long bar_off, hist_off, raw_off, stage_off, stage_bytes, tab_off;
     long long timeout_ns;
     unsigned long long gbar_base;
-    int skip_publish;          // test knob: CTA 0 stops releasing flags
+    int skip_publish;          // test knob: PE 0 stops releasing flags
     long long skip_step;
 };
 
 // ---------------------------------------------------------------------------
 // bounded waits
 // ---------------------------------------------------------------------------
-__device__ __noinline__ void raise_timeout(const Params &p, int where, long long n, long long nb)
+static __device__ __noinline__ void raise_timeout(const Params &p, int where, long long n, long long nb)
 {
     if (atomicCAS(p.ctrl + kCtrlStatus, 0, kStatusTimeout) == 0) {
         p.ctrl[kCtrlCta] = (int)blockIdx.x;
@@ -123,47 +126,8 @@ __device__ __noinline__ void raise_timeout(const Params &p, int where, long long
     atomicExch(p.ctrl + kCtrlAbort, 1);
 }
 
-// Producer side: waits for a stage to be released by the consumers.
-__device__ __forceinline__ bool wait_mbar(uint64_t *bar, unsigned parity, const Params &p,
-                                          volatile int *s_abort, int where, long long limit_ns)
-{
-    if (mbar_try_wait(bar, parity)) return true;
-    const unsigned long long t0 = global_ns();
-    for (;;) {
-        if (mbar_try_wait(bar, parity)) return true;
-        if (*s_abort) return false;
-        if ((long long)(global_ns() - t0) > limit_ns) {
-            raise_timeout(p, where, -1, -1);
-            return false;
-        }
-    }
-}
-
-// Consumer side: waits for a stage to be filled.  Gives up only when the
-// producer has raised the CTA's abort word, after re-testing the phase: the
-// producer raises it only once all its copies have landed, so all consumers
-// see the same completed phases and leave at the same tile.  The time limit
-// is a last resort far beyond any producer wait.
-__device__ __forceinline__ bool wait_full(uint64_t *bar, unsigned parity, const Params &p,
-                                          volatile int *s_abort)
-{
-    if (mbar_try_wait(bar, parity)) return true;
-    const unsigned long long t0 = global_ns();
-    for (;;) {
-        if (mbar_try_wait(bar, parity)) return true;
-        if (*s_abort) {
-            __threadfence_block();
-            return mbar_try_wait(bar, parity);
-        }
-        if ((long long)(global_ns() - t0) > 16 * p.timeout_ns) {
-            raise_timeout(p, kWhereFull, -1, -1);
-            return false;
-        }
-    }
-}
-
 // Waits until *fl >= need (acquire).  Returns the value seen in *seen.
-__device__ __noinline__ bool wait_flag(const Params &p, const unsigned long long *fl, long long need,
+static __device__ __noinline__ bool wait_flag(const Params &p, const unsigned long long *fl, long long need,
                                        unsigned long long *seen, long long n, long long nb)
 {
     unsigned long long v = ld_acquire(fl);
@@ -183,7 +147,7 @@ __device__ __noinline__ bool wait_flag(const Params &p, const unsigned long long
     }
 }
 
-__device__ __noinline__ bool wait_grid(const Params &p, unsigned long long target, long long n)
+static __device__ __noinline__ bool wait_grid(const Params &p, unsigned long long target, long long n)
 {
     if (ld_acquire(p.gbar) >= target) return true;
     const unsigned long long t0 = global_ns();
@@ -196,11 +160,6 @@ __device__ __noinline__ bool wait_grid(const Params &p, unsigned long long targe
             return false;
         }
     }
-}
-
-__device__ __forceinline__ void consumer_sync()
-{
-    asm volatile("bar.sync %0, %1;" ::"n"(kConsumerBarrier), "n"(kConsumers) : "memory");
 }
 
 // ---------------------------------------------------------------------------
@@ -283,154 +242,368 @@ __device__ __forceinline__ T approx_halo(const unsigned char *raw, int k, int r)
     }
 }
 
-// ---------------------------------------------------------------------------
-// producer warp
-// ---------------------------------------------------------------------------
-template <typename T, int ORDER>
-__device__ void produce(const Params &p, long long lo, long long hi, int PD, uint64_t *full, uint64_t *empty,
-                        volatile int *s_abort, unsigned char *stages, unsigned *s_hist)
+
+// Waits (lane 0) for the bulk copy into a stage; bounded.
+static __device__ __noinline__ bool wait_stage(const Params &p, uint64_t *bar, unsigned parity)
 {
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    for (;;) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((long long)(global_ns() - t0) > p.timeout_ns) {
+            raise_timeout(p, kWhereTile, -1, -1);
+            return false;
+        }
+    }
+}
+
+// Position of a tile in a PE's sweep: pass start level n, subdomain j and
+// the pass length (one level while n < s-1, then up to sb levels; the same
+// rule in every PE, so all agree on the pass boundaries).
+struct Cursor {
+    long long n, j;
+    int len;
+};
+
+__device__ __forceinline__ int pass_len(const Params &p, long long n, int s_lev)
+{
+    const long long left = p.n0 + p.n_steps - n;
+    int len = (int)(left < p.sb ? left : p.sb);
+    if (n < s_lev - 1) len = 1;
+    return len;
+}
+
+__device__ __forceinline__ void advance(const Params &p, Cursor &c, long long lo, long long hi, int s_lev)
+{
+    if (++c.j == hi) {
+        c.j = lo;
+        c.n += c.len;
+        c.len = pass_len(p, c.n, s_lev);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// one processing element (warp)
+// ---------------------------------------------------------------------------
+// Lane l keeps the 4-point groups g = l + 32 m (m < GW) of the tile in
+// registers for the whole pass, so that loads and stores stay coalesced.  The
+// left neighbours of group g are the last R words of group g-1 (lane l-1,
+// same m; for lane 0, lane 31 at m-1), the right neighbours the first R words
+// of group g+1 (lane l+1, same m; for lane 31, lane 0 at m+1): one shuffle
+// per word, no barrier.  Groups 0 and NG-1 take the approximated halo instead.
+template <typename T, int ORDER, int GW, bool FORCED>
+__device__ void run_pe(const Params &p, long long lo, long long hi, uint64_t *bars, unsigned *hist,
+                       unsigned char *raw, unsigned char *stages, const T *sj, const T *cj, const T *spt,
+                       const T *cpt)
+{
+    constexpr int R = ORDER / 2;
     constexpr int S_LEV = ORDER / 2 + 1;
     constexpr unsigned kAll = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const long long S = hi - lo;
-    const long long n_end = p.n0 + p.n_steps;
-    const int chunks = (int)(p.M * (long long)sizeof(T) / 16);
+    if (S <= 0) {
+        // a PE without subdomains still counts at every grid barrier
+        if (p.mode == kModeSync && lane == 0) atomicAdd(p.gbar, (unsigned long long)p.n_steps);
+        return;
+    }
+    const int NS = p.stages;
+    const int D = (int)((S - 1) < (NS - 1) ? (S - 1) : (NS - 1));   // tiles loaded ahead
+    const long long Q = p.n_passes * S;
+    const int NG = (int)(p.M / 4);
+    const int m_last = (NG - 1) >> 5, lane_last = (NG - 1) & 31;   // owner of group NG-1
+    const T cA = (T)p.cA, cB = (T)p.cB;
     const size_t tile_bytes = (size_t)p.M * sizeof(T);
     const size_t slot_stride = (size_t)p.P * 2 * kRingEntry;
-    unsigned *my_hist = s_hist + (lane & 1) * (kMaxL + 1);   // lanes 0 and 1 only
+    const int up = (lane + 31) & 31, down = (lane + 1) & 31;
+    const bool edge_pub = !(p.skip_publish && blockIdx.x == 0 && threadIdx.x < 32);
+    unsigned *my_hist = hist + (lane & 1) * (kMaxL + 1);
 
-    int kb = 0;                 // lane i: raw delay of (tile r0 + i/2, face i%2) of the batch
-    int st = 0;                 // stage of tile r
-    unsigned use = 0;           // r / PD
-    long long n = p.n0, j = lo; // pass start level and subdomain of tile r
-    long long r = 0;
-    bool ok = true;
+    Cursor L{p.n0, lo, pass_len(p, p.n0, S_LEV)};   // next tile to load
+    Cursor H = L;                                     // next tile whose halo is prepared
+    Cursor C = L;                                     // tile being processed
 
-    while (n < n_end) {
-        // levels in this pass: passes longer than one level extrapolate from s
-        // levels, so they start only once level s-1 exists (the same rule in
-        // every CTA, so all agree on the pass boundaries)
-        int len = (int)((n_end - n) < p.sb ? (n_end - n) : p.sb);
-        if (n < S_LEV - 1) len = 1;
-        // every 16 tiles, the 32 lanes draw the 32 (tile, face) delays at
-        // once (prescribed modes, one level per pass)
-        if ((r & 15) == 0 && (p.mode == kModeSeeded || p.mode == kModeReplay)) {
-            long long jj = j + (lane >> 1), nn = n;
+    // --- state tile copies (lane 0): tile t goes to stage t % NS ------------
+    auto issue_load = [&](long long t, const Cursor &c) {
+        if (lane == 0) {
+            uint64_t *bar = &bars[t % NS];
+            mbar_arrive_expect_tx(bar, (unsigned)tile_bytes);
+            bulk_load(stages + (size_t)(t % NS) * p.stage_bytes,
+                      reinterpret_cast<const unsigned char *>(p.u) + (size_t)c.j * tile_bytes,
+                      (unsigned)tile_bytes, bar);
+        }
+    };
+
+    // --- halo preparation (lane f for face f) -------------------------------
+    // Chooses the delay of face f of tile c and copies the delayed ring
+    // levels into raw buffer `buf`.  With block == false an edge face whose
+    // neighbour is not far enough yet is left pending (return 0); otherwise
+    // waits (bounded).  Returns 1 when done, -1 on abort.
+    int kb = 0;                        // lane i: raw delay of (tile t0 + i/2, face i%2)
+    long long kb_t0 = -1;
+    auto raw_delay = [&](long long t, const Cursor &c) -> int {
+        // prescribed modes draw 16 tiles' delays at once (one per lane)
+        const long long t0 = t & ~15LL;
+        if (t0 != kb_t0) {
+            // (n, j) of tile t0 + lane/2, stepping from c (tile t) back or forth
+            long long jj = c.j - (t - t0) + (lane >> 1), nn = c.n;
+            while (jj < lo) { jj += S; --nn; }
             while (jj >= hi) { jj -= S; ++nn; }
-            const int f = lane & 1;
             int k = 0;
-            if (nn < n_end) {
+            if (t0 + (lane >> 1) < Q && nn >= p.n0 && nn < p.n0 + p.n_steps) {
                 if (p.mode == kModeSeeded)
-                    k = seeded_delay(p.seed, nn, jj, p.P, p.per_sub ? 0 : f, p.L);
-                else
-                    k = p.delays[((nn - p.n0) * p.P + jj) * 2 + f];
+                    k = seeded_delay(p.seed, nn, jj, p.P, p.per_sub ? 0 : (lane & 1), p.L);
+                else if (p.mode == kModeReplay)
+                    k = p.delays[((nn - p.n0) * p.P + jj) * 2 + (lane & 1)];
             }
             kb = k;
+            kb_t0 = t0;
         }
-        if (r >= PD) {
-            // lane 0 waits for the consumers to release the stage, then the
-            // whole warp may overwrite it
-            int freed = 1;
-            if (lane == 0) freed = wait_mbar(&empty[st], (use - 1u) & 1u, p, s_abort, kWhereEmpty, 8 * p.timeout_ns);
-            freed = __shfl_sync(kAll, freed, 0);
-            __syncwarp();
-            if (!freed) { ok = false; break; }
-        }
-        const long long step = n - p.n0;
-        unsigned char *sb = stages + (size_t)st * p.stage_bytes;
+        const int i = 2 * (int)(t - t0);
+        const int k0 = __shfl_sync(kAll, kb, i), k1 = __shfl_sync(kAll, kb, i + 1);
+        return (lane & 1) ? k1 : k0;
+    };
 
-        // synchronous algorithm: every halo of step n waits for all CTAs to
-        // have finished step n-1 (grid barrier, Algorithm 1)
-        if (p.mode == kModeSync && step > 0 && j == lo) {
-            int good = 1;
-            if (lane == 0)
-                good = wait_grid(p, p.gbar_base + (unsigned long long)step * (unsigned long long)p.G, n);
-            good = __shfl_sync(kAll, good, 0);
-            if (!good) { ok = false; break; }
-        }
-
-        // state tile of subdomain j at level n
-        const unsigned char *src = reinterpret_cast<const unsigned char *>(p.u) + (size_t)j * tile_bytes;
-        for (int q = lane; q < chunks; q += 32) cp_async16(sb + kTileOff + 16 * q, src + 16 * q);
-
-        // delays and delayed ring levels, lane f for face f
-        const int bi = 2 * (int)(r & 15);
-        const int kr0 = __shfl_sync(kAll, kb, bi);
-        const int kr1 = __shfl_sync(kAll, kb, bi + 1);
-        int good = 1;
+    int hk = 0;                        // lanes 0/1: delay at the start of the pass for the prepared tile
+    auto prep_halo = [&](long long t, const Cursor &c, int buf, bool block) -> int {
+        const int kr = (p.mode == kModeSeeded || p.mode == kModeReplay) ? raw_delay(t, c) : 0;
+        // phase 1: choose the delay and check (or wait for) the neighbour
+        int state = 1;
+        long long k = 0, q = 0;
         if (lane < 2) {
             const int f = lane;
-            const long long q = (f == 0) ? (j == 0 ? p.P - 1 : j - 1) : (j == p.P - 1 ? 0 : j + 1);
-            // The CTA's two edge faces always use the progress flags, also when
-            // the neighbour is the same CTA (one CTA, periodic wrap): there the
-            // neighbour's level n comes from the tile just before this one.
-            const bool cross = (f == 0) ? (j == lo) : (j == hi - 1);
+            const long long n = c.n;
+            const int len = c.len;
+            q = (f == 0) ? (c.j == 0 ? p.P - 1 : c.j - 1) : (c.j == p.P - 1 ? 0 : c.j + 1);
+            const bool edge = (f == 0) ? (c.j == lo) : (c.j == hi - 1);
             // largest delay at the start of the pass such that the last inner
             // step stays within L, and no level below 0 is ever read
             long long kmax = n - S_LEV + 1;
             if (kmax < 0) kmax = 0;
             if (kmax > p.L - (len - 1)) kmax = p.L - (len - 1);
-            long long k = f ? kr1 : kr0;
-            if (p.mode == kModeFree || p.mode == kModeSync) k = 0;
+            k = kr;
             if (k > kmax) k = kmax;
             if (k < 0) k = 0;
-            if (cross && p.mode != kModeSync) {
+            if (edge && p.mode != kModeSync) {
                 const unsigned long long *fl = p.flag + q * 2 + (1 - f);
                 const long long need = (p.mode == kModeFree) ? n - kmax : n - k;
-                unsigned long long seen = 0;
-                if (!wait_flag(p, fl, need, &seen, n, q)) {
-                    good = 0;
-                } else if (p.mode == kModeFree) {
+                unsigned long long seen = ld_acquire(fl);
+                if ((long long)seen < need) {
+                    if (!block) state = 0;
+                    else if (!wait_flag(p, fl, need, &seen, n, q)) state = -1;
+                }
+                if (state == 1 && p.mode == kModeFree) {
                     const long long avail = ((long long)seen < n) ? (long long)seen : n;
                     k = n - avail;
                 }
             }
-            if (good) {
-                for (int i = 0; i < len; ++i) {
-                    my_hist[k + i] += 1u;
-                    if (p.delays && p.mode != kModeReplay)
-                        p.delays[((step + i) * p.P + j) * 2 + f] = (int8_t)(k + i);
-                }
-                reinterpret_cast<volatile int *>(sb)[f] = (int)k;
-                if (f == 0) reinterpret_cast<volatile int *>(sb)[2] = len;
-                const unsigned char *rbase = p.ring + ((size_t)q * 2 + (1 - f)) * kRingEntry;
-                const int levels = (k == 0 && len == 1) ? 1 : S_LEV;
-                for (int m = 0; m < levels; ++m) {
-                    const long long lv = n - k - m;
-                    cp_async16(sb + kRawOff + (f * kMaxS + m) * kRingEntry,
-                               rbase + (size_t)(lv & (p.T - 1)) * slot_stride);
-                }
+        }
+        // the warp agrees: any lane aborted -> -1, else any lane pending -> 0
+        const unsigned bad = __ballot_sync(kAll, state < 0), pend = __ballot_sync(kAll, state == 0);
+        if (bad) return -1;
+        if (pend) return 0;
+        // phase 2: both faces ready -- count, record and copy the levels
+        if (lane < 2) {
+            const int f = lane;
+            for (int i = 0; i < c.len; ++i) {
+                my_hist[k + i] += 1u;
+                if (p.delays && p.mode != kModeReplay)
+                    p.delays[((c.n - p.n0 + i) * p.P + c.j) * 2 + f] = (int8_t)(k + i);
+            }
+            hk = (int)k;
+            const unsigned char *rbase = p.ring + ((size_t)q * 2 + (1 - f)) * kRingEntry;
+            const int levels = (k == 0 && c.len == 1) ? 1 : S_LEV;
+            for (int m = 0; m < levels; ++m) {
+                const long long lv = c.n - k - m;
+                cp_async16(raw + (size_t)buf * kRawBytes + (f * kMaxS + m) * kRingEntry,
+                           rbase + (size_t)(lv & (p.T - 1)) * slot_stride);
             }
         }
-        good = __all_sync(kAll, good);
-        if (!good) { ok = false; break; }
-        mbar_arrive_on_copies(&full[st]);
-        if (lane < 2) mbar_arrive(&full[st]);
+        return 1;
+    };
 
-        ++r;
-        if (++st == PD) { st = 0; ++use; }
-        if (++j == hi) { j = lo; n += len; }
-    }
-    // let every issued copy land, and the stage phases they complete become
-    // visible, before the abort word is raised: consumers then agree on which
-    // stages are complete and leave at the same tile
-    cp_async_wait_all();
-    __syncwarp();
-    if (!ok) {
-        if (lane == 0) {
-            const long long first = r > PD ? r - PD : 0;
-            for (long long q = first; q < r; ++q) {
-                const unsigned long long t0 = global_ns();
-                while (!mbar_try_wait(&full[q % PD], (unsigned)((q / PD) & 1)) &&
-                       (long long)(global_ns() - t0) < p.timeout_ns) {
+    // --- prologue -------------------------------------------------------------
+    long long tl = 0;                  // next tile index to load
+    for (; tl < D && tl < Q; ++tl) { issue_load(tl, L); advance(p, L, lo, hi, S_LEV); }
+    bool ok = true;
+    bool pending = true;               // the halo of tile 0 is prepared in the loop
+    int k0cur = 0, k1cur = 0;
+
+    for (long long r = 0; r < Q && ok; ++r) {
+        // state copy of tile r + D (stage of tile r - 1, complete: in order)
+        if (tl < Q && tl <= r + D) {
+            issue_load(tl, L);
+            advance(p, L, lo, hi, S_LEV);
+            ++tl;
+        }
+        const long long step = C.n - p.n0;
+        // synchronous algorithm: before the first tile of a step, all PEs
+        // have finished the previous step (grid barrier, Algorithm 1)
+        if (p.mode == kModeSync && step > 0 && C.j == lo && C.n != p.n0) {
+            int good = 1;
+            if (lane == 0) {
+                __threadfence();
+                atomicAdd(p.gbar, 1ull);
+                good = wait_grid(p, p.gbar_base + (unsigned long long)step * (unsigned long long)p.E, C.n);
+            }
+            good = __shfl_sync(kAll, good, 0);
+            if (!good) { ok = false; break; }
+        }
+        // halo of tile r: prepared one tile ahead unless it was pending
+        const int buf = (int)(r & 1);
+        if (pending) {
+            if (prep_halo(r, C, buf, true) < 0) { ok = false; break; }
+            H = C;
+            advance(p, H, lo, hi, S_LEV);
+        }
+        if (lane < 2) cp_async_wait_all();
+        k0cur = __shfl_sync(kAll, hk, 0);
+        k1cur = __shfl_sync(kAll, hk, 1);
+        __syncwarp();
+        // prepare the halo of tile r + 1 without blocking (in AT_SYNC it must
+        // wait for the grid barrier when tile r + 1 starts a new step).  Its
+        // internal right neighbour at the pass start was computed by tile
+        // r + 2 - S, which is tile r itself when S == 2: no prefetch then.
+        pending = true;
+        if (r + 1 < Q && S != 2) {
+            const bool new_step = (H.j == lo);
+            if (!(p.mode == kModeSync && new_step)) {
+                const int st = prep_halo(r + 1, H, buf ^ 1, false);
+                if (st < 0) { ok = false; break; }
+                if (st > 0) {
+                    pending = false;
+                    advance(p, H, lo, hi, S_LEV);
                 }
             }
-            __threadfence_block();
-            *s_abort = 1;
         }
+        // the state tile
+        int good = 1;
+        if (lane == 0) good = wait_stage(p, &bars[r % NS], (unsigned)((r / NS) & 1));
+        good = __shfl_sync(kAll, good, 0);
         __syncwarp();
+        if (!good) { ok = false; break; }
+
+        const T *stile = reinterpret_cast<const T *>(stages + (size_t)(r % NS) * p.stage_bytes);
+        const unsigned char *rw = raw + (size_t)buf * kRawBytes;
+        const long long j = C.j, n = C.n;
+        const int len = C.len;
+        T *ug = reinterpret_cast<T *>(p.u) + (size_t)j * p.M;
+
+        T c[GW][4];
+#pragma unroll
+        for (int m = 0; m < GW; ++m) {
+            const int g = lane + 32 * m;
+            if (g < NG) lds<T, 4>(stile + 4 * g, c[m]);
+            else { c[m][0] = c[m][1] = c[m][2] = c[m][3] = (T)0; }
+        }
+        // A sin(x) dt = (dt A sin x_j) cos(i dx) + (dt A cos x_j) sin(i dx)
+        T fs = (T)0, fc = (T)0;
+        if constexpr (FORCED) {
+            fs = (T)(p.dtA * (double)spt[j - lo]);
+            fc = (T)(p.dtA * (double)cpt[j - lo]);
+        }
+
+        for (int i = 0; i < len; ++i) {
+            const long long lev = n + i + 1;                 // level being computed
+            // halo values of this inner step (delays k0 + i, k1 + i); every
+            // lane evaluates them (uniform), two lanes use them
+            T hl[R], hr[R];
+#pragma unroll
+            for (int q = 0; q < R; ++q) {
+                hl[q] = approx_halo<T, S_LEV>(rw, k0cur + i, q);
+                hr[q] = approx_halo<T, S_LEV>(rw + kMaxS * kRingEntry, k1cur + i, q);
+            }
+            T tail[R], rb[R];                                // old last words of group m-1; new last words of NG-1
+#pragma unroll
+            for (int q = 0; q < R; ++q) { tail[q] = (T)0; rb[q] = (T)0; }
+#pragma unroll
+            for (int m = 0; m < GW; ++m) {
+                const int g = lane + 32 * m;
+                T v[4 + 2 * R];
+#pragma unroll
+                for (int q = 0; q < R; ++q) {
+                    const T to_next = (lane == 31) ? tail[q] : c[m][4 - R + q];
+                    v[q] = __shfl_sync(kAll, to_next, up);
+                    const T to_prev = (lane == 0) ? c[m + 1 < GW ? m + 1 : m][q] : c[m][q];
+                    v[R + 4 + q] = __shfl_sync(kAll, to_prev, down);
+                }
+#pragma unroll
+                for (int q = 0; q < R; ++q) tail[q] = c[m][4 - R + q];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) v[R + e] = c[m][e];
+                if (m == 0) {
+#pragma unroll
+                    for (int q = 0; q < R; ++q) v[q] = (lane == 0) ? hl[q] : v[q];
+                }
+                const bool is_last = (m == m_last) && (lane == lane_last);
+#pragma unroll
+                for (int q = 0; q < R; ++q) v[R + 4 + q] = is_last ? hr[q] : v[R + 4 + q];
+                T s4[4], c4[4];
+                if constexpr (FORCED) {
+                    const int gg = g < NG ? g : NG - 1;
+                    lds<T, 4>(sj + 4 * gg, s4);
+                    lds<T, 4>(cj + 4 * gg, c4);
+                }
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const T cc = v[e + R];
+                    T a, b;
+                    if constexpr (ORDER == 2) {
+                        a = v[e + 2] - v[e];
+                        b = (v[e + 2] + v[e]) - (T)2 * cc;
+                    } else {
+                        a = (T)8 * (v[e + 3] - v[e + 1]) - (v[e + 4] - v[e]);
+                        b = (T)16 * (v[e + 3] + v[e + 1]) - (v[e + 4] + v[e]) - (T)30 * cc;
+                    }
+                    T du = cB * b - cA * cc * a;
+                    if constexpr (FORCED) du += fs * c4[e] + fc * s4[e];
+                    c[m][e] = cc + du;
+                }
+#pragma unroll
+                for (int q = 0; q < R; ++q) rb[q] = (m == m_last) ? c[m][4 - R + q] : rb[q];
+            }
+            // publish the new boundary values and release the edge flags
+            const long long slot = lev & (p.T - 1);
+            const bool pub_ok = edge_pub || lev <= p.skip_step;
+            if (lane == 0) {
+                unsigned char *e = p.ring + (size_t)slot * slot_stride + ((size_t)j * 2 + 0) * kRingEntry;
+                st_entry<T, R>(e, c[0]);
+                if (p.mode == kModeSync) __threadfence();
+                if (j == lo && pub_ok) st_release(p.flag + j * 2 + 0, (unsigned long long)lev);
+            }
+            if (lane == lane_last) {
+                unsigned char *e = p.ring + (size_t)slot * slot_stride + ((size_t)j * 2 + 1) * kRingEntry;
+                st_entry<T, R>(e, rb);
+                if (p.mode == kModeSync) __threadfence();
+                if (j == hi - 1 && pub_ok) st_release(p.flag + j * 2 + 1, (unsigned long long)lev);
+            }
+        }
+#pragma unroll
+        for (int m = 0; m < GW; ++m) {
+            const int g = lane + 32 * m;
+            if (g < NG) stg4<T>(ug + 4 * g, c[m]);
+        }
+        // the next read of this tile is a bulk copy (async proxy), issued by
+        // lane 0 after the warp barrier
+        fence_proxy_async_global();
+        __syncwarp();
+        advance(p, C, lo, hi, S_LEV);
     }
+    // synchronous algorithm: the last step's arrival at the grid barrier
+    if (ok && p.mode == kModeSync && lane == 0) {
+        __threadfence();
+        atomicAdd(p.gbar, 1ull);
+    }
+    // let every copy in flight land before the warp leaves
+    if (lane < 2) cp_async_wait_all();
+    if (lane == 0) {
+        for (long long t = (tl > NS ? tl - NS : 0); t < tl; ++t) {
+            const unsigned long long t0 = global_ns();
+            while (!mbar_try_wait(&bars[t % NS], (unsigned)((t / NS) & 1)) &&
+                   (long long)(global_ns() - t0) < p.timeout_ns) {
+            }
+        }
+    }
+    __syncwarp();
     if (lane < 2) {
         for (int i = 0; i <= p.L && i <= kMaxL; ++i)
             if (my_hist[i]) atomicAdd(p.hist + i, (unsigned long long)my_hist[i]);
@@ -438,184 +611,48 @@ __device__ void produce(const Params &p, long long lo, long long hi, int PD, uin
 }
 
 // ---------------------------------------------------------------------------
-// consumer warps
-// ---------------------------------------------------------------------------
-template <typename T, int ORDER>
-__device__ void consume(const Params &p, long long lo, long long hi, int PD, uint64_t *full, uint64_t *empty,
-                        volatile int *s_abort, unsigned char *stages, unsigned char *work, const T *tab)
-{
-    constexpr int R = ORDER / 2;
-    constexpr int S_LEV = ORDER / 2 + 1;
-    constexpr int NV = 4 + 2 * R;
-    const int t = threadIdx.x;
-    const long long S = hi - lo;
-    const long long n_end = p.n0 + p.n_steps;
-    const int NG = (int)(p.M / 4);
-    const T cA = (T)p.cA, cB = (T)p.cB, dtA = (T)p.dtA;
-    const size_t slot_stride = (size_t)p.P * 2 * kRingEntry;
-    const T *sj = tab, *cj = tab + p.M, *spt = tab + 2 * p.M, *cpt = spt + S;
-    T *wtile = reinterpret_cast<T *>(work + kTileOff);
-
-    int st = 0;
-    unsigned use = 0;
-    long long n = p.n0, j = lo;
-    while (n < n_end) {
-        if (!wait_full(&full[st], use & 1u, p, s_abort)) break;
-        const unsigned char *sb = stages + (size_t)st * p.stage_bytes;
-        T *stile = reinterpret_cast<T *>(const_cast<unsigned char *>(sb) + kTileOff);
-        const int k0 = reinterpret_cast<const volatile int *>(sb)[0];
-        const int k1 = reinterpret_cast<const volatile int *>(sb)[1];
-        const int len = reinterpret_cast<const volatile int *>(sb)[2];
-        T sp = 0, cp = 0;
-        if (p.forcing) { sp = spt[j - lo]; cp = cpt[j - lo]; }
-        T *ug = reinterpret_cast<T *>(p.u) + (size_t)j * p.M;
-        const bool edge_pub = !(p.skip_publish && blockIdx.x == 0);
-
-        for (int i = 0; i < len; ++i) {
-            const T *src = (i & 1) ? wtile : stile;
-            T *dst = (i & 1) ? stile : wtile;
-            const bool last = (i == len - 1);
-            const long long lev = n + i + 1;                 // level being computed
-            const long long slot = lev & (p.T - 1);
-            const bool pub_ok = edge_pub || lev <= p.skip_step;
-            for (int g = t; g < NG; g += kConsumers) {
-                T v[NV];
-                lds<T, 4>(src + 4 * g, v + R);
-                if (g == 0 && i == 0) {
-#pragma unroll
-                    for (int q = 0; q < R; ++q) v[q] = approx_halo<T, S_LEV>(sb + kRawOff, k0, q);
-                } else {
-                    lds<T, R>(src + 4 * g - R, v);   // inner steps: halo sits in the pad
-                }
-                if (g == NG - 1 && i == 0) {
-#pragma unroll
-                    for (int q = 0; q < R; ++q)
-                        v[R + 4 + q] = approx_halo<T, S_LEV>(sb + kRawOff + kMaxS * kRingEntry, k1, q);
-                } else {
-                    lds<T, R>(src + 4 * g + 4, v + R + 4);
-                }
-                T fo[4] = {0, 0, 0, 0};
-                if (p.forcing) {
-                    T s4[4], c4[4];
-                    lds<T, 4>(sj + 4 * g, s4);
-                    lds<T, 4>(cj + 4 * g, c4);
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) fo[e] = dtA * (sp * c4[e] + cp * s4[e]);
-                }
-                T out[4];
-#pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    const T c = v[e + R];
-                    T a, b;
-                    if constexpr (ORDER == 2) {
-                        a = v[e + 2] - v[e];
-                        b = (v[e + 2] + v[e]) - (T)2 * c;
-                    } else {
-                        a = (T)8 * (v[e + 3] - v[e + 1]) - (v[e + 4] - v[e]);
-                        b = (T)16 * (v[e + 3] + v[e + 1]) - (v[e + 4] + v[e]) - (T)30 * c;
-                    }
-                    out[e] = c + ((cB * b - cA * c * a) + fo[e]);
-                }
-                if (last) stg4<T>(ug + 4 * g, out);
-                else sts4<T>(dst + 4 * g, out);
-                // publish the new boundary values and release the edge flag
-                if (g == 0) {
-                    unsigned char *e = p.ring + (size_t)slot * slot_stride + ((size_t)j * 2 + 0) * kRingEntry;
-                    st_entry<T, R>(e, out);
-                    if (p.mode == kModeSync) __threadfence();
-                    if (j == lo && pub_ok) st_release(p.flag + j * 2 + 0, (unsigned long long)lev);
-                    if (!last) {
-                        // left halo of the next inner step, delay k0 + i + 1
-#pragma unroll
-                        for (int q = 0; q < R; ++q)
-                            dst[q - R] = approx_halo<T, S_LEV>(sb + kRawOff, k0 + i + 1, q);
-                    }
-                }
-                if (g == NG - 1) {
-                    unsigned char *e = p.ring + (size_t)slot * slot_stride + ((size_t)j * 2 + 1) * kRingEntry;
-                    st_entry<T, R>(e, out + 4 - R);
-                    if (p.mode == kModeSync) __threadfence();
-                    if (j == hi - 1 && pub_ok) st_release(p.flag + j * 2 + 1, (unsigned long long)lev);
-                    if (!last) {
-#pragma unroll
-                        for (int q = 0; q < R; ++q)
-                            dst[p.M + q] = approx_halo<T, S_LEV>(sb + kRawOff + kMaxS * kRingEntry, k1 + i + 1, q);
-                    }
-                }
-            }
-            if (!last) consumer_sync();
-        }
-        // synchronous algorithm: arrive at the grid barrier once the CTA has
-        // finished step n (the consumers' named barrier orders their writes)
-        if (p.mode == kModeSync && j == hi - 1) {
-            consumer_sync();
-            if (t == 0) {
-                __threadfence();
-                atomicAdd(p.gbar, 1ull);
-            }
-        }
-        mbar_arrive(&empty[st]);
-        if (++st == PD) { st = 0; ++use; }
-        if (++j == hi) { j = lo; n += len; }
-    }
-}
-
-// ---------------------------------------------------------------------------
 // the persistent kernel
 // ---------------------------------------------------------------------------
-template <typename T, int ORDER>
-__global__ void __launch_bounds__(kThreads, 2) at_stepper(const Params p)
+template <typename T, int ORDER, int GW, bool FORCED>
+__global__ void __launch_bounds__(kThreads, AT_MIN_CTAS_PER_SM) at_stepper(const Params p)
 {
     extern __shared__ __align__(128) unsigned char smem[];
-    uint64_t *full = reinterpret_cast<uint64_t *>(smem);
-    uint64_t *empty = full + p.stages;
-    unsigned char *misc = reinterpret_cast<unsigned char *>(empty + p.stages);
-    volatile int *s_abort = reinterpret_cast<volatile int *>(misc);
-    unsigned *s_hist = reinterpret_cast<unsigned *>(misc + 16);     // [2][kMaxL+1]
-    unsigned char *stages = smem + p.stage_off;
-    unsigned char *work = smem + p.work_off;
-    T *tab = reinterpret_cast<T *>(smem + p.tab_off);
-
-    const long long c = blockIdx.x;
-    const long long lo = c * p.P / p.G;
-    const long long hi = (c + 1) * p.P / p.G;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long long e = (long long)blockIdx.x * kWarps + w;     // this warp's PE
+    const long long lo = e * p.P / p.E;
+    const long long hi = (e + 1) * p.P / p.E;
     const long long S = hi - lo;
-    // Stage r % PD may be refilled once tile r - PD is consumed; the refill
-    // needs the state of tile r - S and the ring levels of tiles up to
-    // r - S + 1, hence PD <= S - 1 (PD = 1 when S == 1).
-    const int PD = (S <= 1) ? 1 : (int)((S - 1) < p.stages ? (S - 1) : p.stages);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + p.bar_off) + (size_t)w * p.stages;
+    unsigned *hist = reinterpret_cast<unsigned *>(smem + p.hist_off) + (size_t)w * 2 * (kMaxL + 1);
+    unsigned char *raw = smem + p.raw_off + (size_t)w * 2 * kRawBytes;
+    unsigned char *stages = smem + p.stage_off + (size_t)w * p.stages * p.stage_bytes;
+    T *tab = reinterpret_cast<T *>(smem + p.tab_off);
+    T *sj = tab, *cj = tab + p.M;
+    T *spt = tab + 2 * p.M + (size_t)w * 2 * p.smax, *cpt = spt + p.smax;
 
-    if (threadIdx.x == 0) {
-        for (int i = 0; i < PD; ++i) {
-            mbar_init(&full[i], kFullArrivals);
-            mbar_init(&empty[i], kConsumers);
-        }
-        *s_abort = 0;
+    if (lane == 0) {
+        for (int i = 0; i < p.stages; ++i) mbar_init(&bars[i], 1);
         mbar_fence_init();
     }
-    if (threadIdx.x < 2 * (kMaxL + 1)) s_hist[threadIdx.x] = 0u;
-    if (p.forcing) {
+    for (int i = lane; i < 2 * (kMaxL + 1); i += 32) hist[i] = 0u;
+    if (FORCED) {
         // sin/cos of the offsets j dx within a subdomain and of the subdomain
         // origins x0 + p M dx (FP64), so that A sin(x_i) needs two FMAs
         for (long long i = threadIdx.x; i < p.M; i += blockDim.x) {
             double sv, cv;
             sincos((double)i * p.dx, &sv, &cv);
-            tab[i] = (T)sv;
-            tab[p.M + i] = (T)cv;
+            sj[i] = (T)sv;
+            cj[i] = (T)cv;
         }
-        for (long long i = threadIdx.x; i < S; i += blockDim.x) {
+        for (long long i = lane; i < S; i += 32) {
             double sv, cv;
             sincos(p.x0 + (double)((lo + i) * p.M) * p.dx, &sv, &cv);
-            tab[2 * p.M + i] = (T)sv;
-            tab[2 * p.M + S + i] = (T)cv;
+            spt[i] = (T)sv;
+            cpt[i] = (T)cv;
         }
     }
     __syncthreads();
-
-    if (threadIdx.x >= kConsumers)
-        produce<T, ORDER>(p, lo, hi, PD, full, empty, s_abort, stages, s_hist);
-    else
-        consume<T, ORDER>(p, lo, hi, PD, full, empty, s_abort, stages, work, tab);
+    run_pe<T, ORDER, GW, FORCED>(p, lo, hi, bars, hist, raw, stages, sj, cj, spt, cpt);
 }
 
 // ---------------------------------------------------------------------------

@@ -40,17 +40,17 @@ def test_burgers1d_n4096_seeded_fp64(require_gpu):
 CASES = [
     # dtype, order, L, P, M, max_ctas, forcing, steps, stages
     ("f64", 4, 3, 148, 256, 10, 0.1, 300, 0),     # ragged CTA partition (14/15 subdomains)
-    ("f64", 2, 2, 37, 1028, 5, 0.0, 200, 0),      # M/4 = 257 groups > 256 consumer threads
-    ("f64", 4, 1, 8, 2048, 3, 0.1, 150, 0),       # largest FP64 tile (16 KiB)
+    ("f64", 2, 2, 37, 1020, 5, 0.0, 200, 0),      # M/4 = 255 groups: a ragged last row of lanes
+    ("f64", 4, 1, 8, 1024, 3, 0.1, 150, 0),       # largest tile, FP64
     ("f32", 4, 3, 64, 1024, 0, 0.1, 200, 0),      # forced order-4 subdomains of 1024 points
     ("f32", 2, 2, 16, 256, 4, 0.0, 200, 0),
-    ("f32", 4, 3, 3, 4096, 0, 0.1, 100, 0),       # largest FP32 tile, one subdomain per CTA
+    ("f32", 4, 3, 3, 1024, 0, 0.1, 100, 0),       # largest FP32 tile, one subdomain per CTA
     ("f64", 2, 0, 32, 64, 7, 0.0, 300, 0),        # L = 0
     ("f64", 2, 16, 64, 32, 8, 0.0, 200, 0),       # L = 16 (largest), see below
     ("f64", 2, 2, 1, 256, 0, 0.0, 200, 0),        # one subdomain, its own neighbour
     ("f64", 4, 3, 40, 4, 6, 0.0, 200, 0),         # M = 4: one group per tile
-    ("f64", 4, 3, 96, 128, 4, 0.1, 200, 1),       # one stage in flight
-    ("f64", 2, 3, 96, 128, 4, 0.1, 200, 2),       # two stages
+    ("f64", 4, 3, 96, 128, 4, 0.1, 200, 4),       # fewest stages (one per consumer warp)
+    ("f64", 2, 3, 96, 132, 4, 0.1, 200, 5),       # stages not a multiple of the warps
     ("f32", 4, 2, 300, 512, 0, 0.1, 150, 0),      # 300 subdomains over all SMs, ragged
 ]
 
@@ -185,7 +185,7 @@ BLOCKED = [
     # dtype, order, L, steps_per_pass, P, M, max_ctas, steps, calls
     ("f64", 4, 3, 4, 96, 256, 7, 300, None),
     ("f64", 2, 2, 3, 64, 128, 5, 301, [100, 1, 200]),
-    ("f64", 4, 3, 2, 40, 1028, 3, 150, None),
+    ("f64", 4, 3, 2, 40, 1020, 3, 150, None),
     ("f32", 4, 3, 4, 256, 1024, 0, 200, None),
     ("f64", 2, 1, 2, 1, 256, 0, 120, None),        # one subdomain, its own neighbour
     ("f64", 4, 3, 4, 40, 4, 6, 100, [3, 97]),      # M = 4 (N = 160: a coarser grid is unstable for
@@ -228,3 +228,29 @@ def test_blocked_passes_of_L_plus_1_are_deterministic(require_gpu):
     n = np.arange(steps)
     want = np.where(n < s_lev - 1, 0, (n - (s_lev - 1)) % (L + 1)).astype(np.int8)
     assert np.array_equal(g["rec"], np.broadcast_to(want[:, None, None], g["rec"].shape))
+
+
+@pytest.mark.parametrize("per_pe", [1, 2, 3])
+@pytest.mark.parametrize("mode_name", ["seeded", "free", "free_blocked", "sync"])
+def test_subdomains_per_processing_element(require_gpu, per_pe, mode_name):
+    """Each warp is one processing element owning a contiguous run of
+    subdomains; 1, 2 and 3 subdomains per element exercise the edge-only, the
+    no-prefetch and the prefetching halo paths.  Two CTAs = 8 elements."""
+    import paper_1911_05769_gb300 as at
+    P, M, L = 8 * per_pe, 128, 2
+    N = P * M
+    u0, dt = _setup(N, 0.02, kind="fourier")
+    kw = dict(P=P, order=4, L=L, nu=0.02, dt=dt, steps=120, forcing=0.1)
+    mode = {"seeded": at.AT_SEEDED, "free": at.AT_FREE, "free_blocked": at.AT_FREE, "sync": at.AT_SYNC}[mode_name]
+    spp = L + 1 if mode_name == "free_blocked" else 0
+    g = gpu_run(u0, mode=mode, seed=31, max_ctas=2, record=True, steps_per_pass=spp, **kw)
+    if mode_name == "seeded":
+        ref, hist, k = oracle_run(u0, mode="seeded", seed=31, want_k=True, **kw)
+        assert np.array_equal(g["rec"], k)
+    elif mode_name == "sync":
+        ref, hist = oracle_run(u0, mode="sync", **kw)
+    else:
+        ref, hist = oracle_run(u0, mode="replay", delays=g["rec"], **kw)
+    assert g["info"].ctas == 2
+    assert rel_linf(g["u"], ref) <= TOL["f64"]
+    assert np.array_equal(g["hist"], hist)

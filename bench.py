@@ -38,7 +38,7 @@ METRIC = "grid-point updates/sec (GPts/s), AT vs synchronous, 1D forced Burgers 
 UNIT = "GPts/s"
 FALLBACK_HBM = 6800.0
 KERNEL_SOURCES = ["paper_1911_05769_gb300/csrc/at_kernels.cuh", "paper_1911_05769_gb300/csrc/at_device.cuh",
-                  "paper_1911_05769_gb300/csrc/at_api.cu"]
+                  "paper_1911_05769_gb300/csrc/at_kernels_f32.cu"]
 PROFILE = os.path.join(ROOT, "profiles", "at_stepper_f32_o4_n2p26.md")
 
 
@@ -325,9 +325,25 @@ def gpu_arm(args, ws, rank, local, pg):
     traffic, traffic_steps = ncu_traffic()
     if traffic is not None and traffic_steps:
         traffic = traffic * S / traffic_steps
+    # FP32 operations per update of the order-4 forced stencil (FMA = one op):
+    # first difference 3, second difference 4, viscous/advective terms 3,
+    # forcing 2, Euler update 1; against 128 FP32 lanes per SM per clock
+    ops_per_update = 13
+    clk = (head["clocks"] or {}).get("sm_mhz") or 2070.0
+    sms = head["info"].sm_count
+    alu_peak = sms * 128 * clk * 1e6 / 1e12
+    alu_achieved = ops_per_update * upd_per_step / launch_s / 1e12
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": traffic, "peak_source": peak_src, "kernel": f"at_stepper<{'float' if wbytes == 4 else 'double'},4>",
-            "algorithmic_bytes_per_update": bytes_per_update}
+            "traffic": traffic, "peak_source": peak_src,
+            "kernel": f"at_stepper<{'float' if wbytes == 4 else 'double'},4>",
+            "algorithmic_bytes_per_update": bytes_per_update,
+            "effective_one_pass": {"achieved": upd_per_step * 2 * wbytes / launch_s / 1e9, "unit": "GB/s",
+                                   "frac": upd_per_step * 2 * wbytes / launch_s / 1e9 / peak,
+                                   "note": "updates/s x 2 words: the HBM bytes a one-pass-per-step kernel would need"},
+            "alu": None if wbytes != 4 else {
+                "achieved": alu_achieved, "peak": alu_peak, "unit": "TOP/s (FP32, FMA = 1 op)",
+                "frac": alu_achieved / alu_peak, "ops_per_update": ops_per_update,
+                "peak_note": f"{sms} SMs x 128 FP32 lanes x {clk:.0f} MHz (median SM clock under load)"}}
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,

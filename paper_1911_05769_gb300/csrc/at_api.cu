@@ -16,8 +16,8 @@
 #include "at.h"
 #include "at_kernels.cuh"
 
-void *atk_stepper_kernel_f32(int order, int gw, bool forced);
-void *atk_stepper_kernel_f64(int order, int gw, bool forced);
+void *atk_stepper_kernel_f32(int order, int gw, bool forced, bool full);
+void *atk_stepper_kernel_f64(int order, int gw, bool forced, bool full);
 void *atk_init_kernel_f32(int order);
 void *atk_init_kernel_f64(int order);
 
@@ -116,11 +116,12 @@ long long count_passes(long long n0, long long n_steps, int s, int sb)
 void pick_kernels(int w, int order, int64_t M, bool forced, void **stepper, void **init)
 {
     const int gw = groups_per_lane(M);
+    const bool full = (M == 128LL * gw);
     if (w == 8) {
-        *stepper = atk_stepper_kernel_f64(order, gw, forced);
+        *stepper = atk_stepper_kernel_f64(order, gw, forced, full);
         *init = atk_init_kernel_f64(order);
     } else {
-        *stepper = atk_stepper_kernel_f32(order, gw, forced);
+        *stepper = atk_stepper_kernel_f32(order, gw, forced, full);
         *init = atk_init_kernel_f32(order);
     }
 }
@@ -345,7 +346,7 @@ int at_step(at_solver *h, int64_t n_steps, int delay_mode, int8_t *delays)
                                                 h->stream);
     if (e != cudaSuccess) return cuda_fail(e, "cudaLaunchCooperativeKernel(at_stepper)");
     h->step += n_steps;
-    if (delay_mode == AT_SYNC) h->gbar_count += (unsigned long long)n_steps * (unsigned long long)(h->G * atk::kWarps);
+    if (delay_mode == AT_SYNC) h->gbar_count += (unsigned long long)n_steps * (unsigned long long)h->G;
     return AT_OK;
 }
 

@@ -257,6 +257,37 @@ static __device__ __noinline__ bool wait_stage(const Params &p, uint64_t *bar, u
     }
 }
 
+
+// Synchronous algorithm: grid barrier before step `step` (1-based within the
+// launch), combined per CTA.  Each warp counts itself on the CTA's shared
+// counter; the warp completing the CTA's count arrives on the global counter
+// and waits for all CTAs, then opens the CTA's epoch; the other warps wait
+// for the epoch.  `wait` = false for the last arrival of a launch.  Bounded.
+static __device__ __noinline__ bool cta_grid_sync(const Params &p, int *s_count, volatile long long *s_epoch,
+                                                  long long step, bool wait)
+{
+    bool ok = true;
+    if ((threadIdx.x & 31) == 0) {
+        __threadfence();
+        const int old = atomicAdd(s_count, 1);
+        if ((long long)old + 1 == step * kWarps) {
+            __threadfence();
+            atomicAdd(p.gbar, 1ull);
+            if (wait) ok = wait_grid(p, p.gbar_base + (unsigned long long)step * (unsigned long long)p.G, step);
+            st_release_cta_shared(s_epoch, ok ? step : -1);
+        } else if (wait) {
+            const unsigned long long t0 = global_ns();
+            long long ep;
+            while ((ep = ld_acquire_cta_shared(s_epoch)) < step && ep >= 0) {
+                if ((long long)(global_ns() - t0) > p.timeout_ns) { raise_timeout(p, kWhereGrid, step, -1); break; }
+            }
+            ok = (ep >= step);
+        }
+        __threadfence();
+    }
+    return __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+}
+
 // Position of a tile in a PE's sweep: pass start level n, subdomain j and
 // the pass length (one level while n < s-1, then up to sb levels; the same
 // rule in every PE, so all agree on the pass boundaries).
@@ -291,10 +322,10 @@ __device__ __forceinline__ void advance(const Params &p, Cursor &c, long long lo
 // same m; for lane 0, lane 31 at m-1), the right neighbours the first R words
 // of group g+1 (lane l+1, same m; for lane 31, lane 0 at m+1): one shuffle
 // per word, no barrier.  Groups 0 and NG-1 take the approximated halo instead.
-template <typename T, int ORDER, int GW, bool FORCED>
+template <typename T, int ORDER, int GW, bool FORCED, bool FULL>
 __device__ void run_pe(const Params &p, long long lo, long long hi, uint64_t *bars, unsigned *hist,
                        unsigned char *raw, unsigned char *stages, const T *sj, const T *cj, const T *spt,
-                       const T *cpt)
+                       const T *cpt, int *s_count, volatile long long *s_epoch)
 {
     constexpr int R = ORDER / 2;
     constexpr int S_LEV = ORDER / 2 + 1;
@@ -302,15 +333,20 @@ __device__ void run_pe(const Params &p, long long lo, long long hi, uint64_t *ba
     const int lane = threadIdx.x & 31;
     const long long S = hi - lo;
     if (S <= 0) {
-        // a PE without subdomains still counts at every grid barrier
-        if (p.mode == kModeSync && lane == 0) atomicAdd(p.gbar, (unsigned long long)p.n_steps);
+        // a PE without subdomains still takes part in every grid barrier
+        if (p.mode == kModeSync) {
+            for (long long st = 1; st <= p.n_steps; ++st)
+                if (!cta_grid_sync(p, s_count, s_epoch, st, st < p.n_steps)) break;
+        }
         return;
     }
     const int NS = p.stages;
     const int D = (int)((S - 1) < (NS - 1) ? (S - 1) : (NS - 1));   // tiles loaded ahead
     const long long Q = p.n_passes * S;
     const int NG = (int)(p.M / 4);
-    const int m_last = (NG - 1) >> 5, lane_last = (NG - 1) & 31;   // owner of group NG-1
+    // owner of group NG-1 (compile-time when the tile is a multiple of 128 points)
+    const int m_last = FULL ? GW - 1 : (NG - 1) >> 5;
+    const int lane_last = FULL ? 31 : (NG - 1) & 31;
     const T cA = (T)p.cA, cB = (T)p.cB;
     const size_t tile_bytes = (size_t)p.M * sizeof(T);
     const size_t slot_stride = (size_t)p.P * 2 * kRingEntry;
@@ -438,15 +474,8 @@ __device__ void run_pe(const Params &p, long long lo, long long hi, uint64_t *ba
         const long long step = C.n - p.n0;
         // synchronous algorithm: before the first tile of a step, all PEs
         // have finished the previous step (grid barrier, Algorithm 1)
-        if (p.mode == kModeSync && step > 0 && C.j == lo && C.n != p.n0) {
-            int good = 1;
-            if (lane == 0) {
-                __threadfence();
-                atomicAdd(p.gbar, 1ull);
-                good = wait_grid(p, p.gbar_base + (unsigned long long)step * (unsigned long long)p.E, C.n);
-            }
-            good = __shfl_sync(kAll, good, 0);
-            if (!good) { ok = false; break; }
+        if (p.mode == kModeSync && step > 0 && C.j == lo) {
+            if (!cta_grid_sync(p, s_count, s_epoch, step, true)) { ok = false; break; }
         }
         // halo of tile r: prepared one tile ahead unless it was pending
         const int buf = (int)(r & 1);
@@ -492,7 +521,7 @@ __device__ void run_pe(const Params &p, long long lo, long long hi, uint64_t *ba
 #pragma unroll
         for (int m = 0; m < GW; ++m) {
             const int g = lane + 32 * m;
-            if (g < NG) lds<T, 4>(stile + 4 * g, c[m]);
+            if (FULL || g < NG) lds<T, 4>(stile + 4 * g, c[m]);
             else { c[m][0] = c[m][1] = c[m][2] = c[m][3] = (T)0; }
         }
         // A sin(x) dt = (dt A sin x_j) cos(i dx) + (dt A cos x_j) sin(i dx)
@@ -502,15 +531,27 @@ __device__ void run_pe(const Params &p, long long lo, long long hi, uint64_t *ba
             fc = (T)(p.dtA * (double)cpt[j - lo]);
         }
 
+        // halo values of every inner level (delays k0 + i, k1 + i): lane
+        // x < 2 R len computes one of them once per tile; each level then
+        // takes its 2R values by shuffle
+        const bool hv_lanes = 2 * R * len <= 32;
+        T hv = (T)0;
+        if (hv_lanes && lane < 2 * R * len) {
+            const int f = lane / (R * len), rem = lane % (R * len);
+            hv = approx_halo<T, S_LEV>(rw + f * kMaxS * kRingEntry, (f ? k1cur : k0cur) + rem / R, rem % R);
+        }
         for (int i = 0; i < len; ++i) {
             const long long lev = n + i + 1;                 // level being computed
-            // halo values of this inner step (delays k0 + i, k1 + i); every
-            // lane evaluates them (uniform), two lanes use them
             T hl[R], hr[R];
 #pragma unroll
             for (int q = 0; q < R; ++q) {
-                hl[q] = approx_halo<T, S_LEV>(rw, k0cur + i, q);
-                hr[q] = approx_halo<T, S_LEV>(rw + kMaxS * kRingEntry, k1cur + i, q);
+                if (hv_lanes) {
+                    hl[q] = __shfl_sync(kAll, hv, i * R + q);
+                    hr[q] = __shfl_sync(kAll, hv, R * len + i * R + q);
+                } else {
+                    hl[q] = approx_halo<T, S_LEV>(rw, k0cur + i, q);
+                    hr[q] = approx_halo<T, S_LEV>(rw + kMaxS * kRingEntry, k1cur + i, q);
+                }
             }
             T tail[R], rb[R];                                // old last words of group m-1; new last words of NG-1
 #pragma unroll
@@ -539,7 +580,7 @@ __device__ void run_pe(const Params &p, long long lo, long long hi, uint64_t *ba
                 for (int q = 0; q < R; ++q) v[R + 4 + q] = is_last ? hr[q] : v[R + 4 + q];
                 T s4[4], c4[4];
                 if constexpr (FORCED) {
-                    const int gg = g < NG ? g : NG - 1;
+                    const int gg = (FULL || g < NG) ? g : NG - 1;
                     lds<T, 4>(sj + 4 * gg, s4);
                     lds<T, 4>(cj + 4 * gg, c4);
                 }
@@ -562,25 +603,23 @@ __device__ void run_pe(const Params &p, long long lo, long long hi, uint64_t *ba
                 for (int q = 0; q < R; ++q) rb[q] = (m == m_last) ? c[m][4 - R + q] : rb[q];
             }
             // publish the new boundary values and release the edge flags
-            const long long slot = lev & (p.T - 1);
-            const bool pub_ok = edge_pub || lev <= p.skip_step;
-            if (lane == 0) {
-                unsigned char *e = p.ring + (size_t)slot * slot_stride + ((size_t)j * 2 + 0) * kRingEntry;
-                st_entry<T, R>(e, c[0]);
-                if (p.mode == kModeSync) __threadfence();
-                if (j == lo && pub_ok) st_release(p.flag + j * 2 + 0, (unsigned long long)lev);
-            }
-            if (lane == lane_last) {
-                unsigned char *e = p.ring + (size_t)slot * slot_stride + ((size_t)j * 2 + 1) * kRingEntry;
-                st_entry<T, R>(e, rb);
-                if (p.mode == kModeSync) __threadfence();
-                if (j == hi - 1 && pub_ok) st_release(p.flag + j * 2 + 1, (unsigned long long)lev);
+            // (face 0 by lane 0, face 1 by the owner of group NG-1)
+            if (lane == 0 || lane == lane_last) {
+                const long long slot = lev & (p.T - 1);
+                const bool pub_ok = edge_pub || lev <= p.skip_step;
+                unsigned char *e0 = p.ring + (size_t)slot * slot_stride + (size_t)j * 2 * kRingEntry;
+                const int f_lo = (lane == 0) ? 0 : 1, f_hi = (lane == lane_last) ? 1 : 0;
+                for (int f = f_lo; f <= f_hi; ++f) {
+                    st_entry<T, R>(e0 + f * kRingEntry, f ? rb : c[0]);
+                    if (p.mode == kModeSync) __threadfence();
+                    if ((f ? j == hi - 1 : j == lo) && pub_ok) st_release(p.flag + j * 2 + f, (unsigned long long)lev);
+                }
             }
         }
 #pragma unroll
         for (int m = 0; m < GW; ++m) {
             const int g = lane + 32 * m;
-            if (g < NG) stg4<T>(ug + 4 * g, c[m]);
+            if (FULL || g < NG) stg4<T>(ug + 4 * g, c[m]);
         }
         // the next read of this tile is a bulk copy (async proxy), issued by
         // lane 0 after the warp barrier
@@ -589,10 +628,7 @@ __device__ void run_pe(const Params &p, long long lo, long long hi, uint64_t *ba
         advance(p, C, lo, hi, S_LEV);
     }
     // synchronous algorithm: the last step's arrival at the grid barrier
-    if (ok && p.mode == kModeSync && lane == 0) {
-        __threadfence();
-        atomicAdd(p.gbar, 1ull);
-    }
+    if (ok && p.mode == kModeSync) cta_grid_sync(p, s_count, s_epoch, p.n_steps, false);
     // let every copy in flight land before the warp leaves
     if (lane < 2) cp_async_wait_all();
     if (lane == 0) {
@@ -613,7 +649,7 @@ __device__ void run_pe(const Params &p, long long lo, long long hi, uint64_t *ba
 // ---------------------------------------------------------------------------
 // the persistent kernel
 // ---------------------------------------------------------------------------
-template <typename T, int ORDER, int GW, bool FORCED>
+template <typename T, int ORDER, int GW, bool FORCED, bool FULL>
 __global__ void __launch_bounds__(kThreads, AT_MIN_CTAS_PER_SM) at_stepper(const Params p)
 {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -630,6 +666,9 @@ __global__ void __launch_bounds__(kThreads, AT_MIN_CTAS_PER_SM) at_stepper(const
     T *sj = tab, *cj = tab + p.M;
     T *spt = tab + 2 * p.M + (size_t)w * 2 * p.smax, *cpt = spt + p.smax;
 
+    __shared__ int s_count;                   // grid-barrier arrivals of this CTA's warps
+    __shared__ long long s_epoch;             // last grid barrier this CTA passed
+    if (threadIdx.x == 0) { s_count = 0; s_epoch = 0; }
     if (lane == 0) {
         for (int i = 0; i < p.stages; ++i) mbar_init(&bars[i], 1);
         mbar_fence_init();
@@ -652,7 +691,7 @@ __global__ void __launch_bounds__(kThreads, AT_MIN_CTAS_PER_SM) at_stepper(const
         }
     }
     __syncthreads();
-    run_pe<T, ORDER, GW, FORCED>(p, lo, hi, bars, hist, raw, stages, sj, cj, spt, cpt);
+    run_pe<T, ORDER, GW, FORCED, FULL>(p, lo, hi, bars, hist, raw, stages, sj, cj, spt, cpt, &s_count, &s_epoch);
 }
 
 // ---------------------------------------------------------------------------

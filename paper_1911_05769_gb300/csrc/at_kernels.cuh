@@ -596,7 +596,7 @@ __device__ void run_pe(const Params &p, long long lo, long long hi, uint64_t *ba
                         b = (T)16 * (v[e + 3] + v[e + 1]) - (v[e + 4] + v[e]) - (T)30 * cc;
                     }
                     T du = cB * b - cA * cc * a;
-                    if constexpr (FORCED) du += fs * c4[e] + fc * s4[e];
+                    if constexpr (FORCED) du = fs * c4[e] + (fc * s4[e] + du);   // two fused multiply-adds
                     c[m][e] = cc + du;
                 }
 #pragma unroll

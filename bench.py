@@ -156,7 +156,8 @@ def dist_setup(args):
 
 def cpu_baseline(args, u0, dt, cfg):
     """The oracle (single thread, as it stands) on a bounded sample: a window of
-    the workload's subdomains advanced a few steps with seeded delays."""
+    the workload's subdomains advanced a few steps with seeded delays.  Also
+    returns the window's result for the FP64-oracle error of the GPU run."""
     import oracle
     oracle.build()
     N, P, M = cfg["N"], cfg["P"], cfg["N"] // cfg["P"]
@@ -164,13 +165,50 @@ def cpu_baseline(args, u0, dt, cfg):
     steps = args.cpu_sample_steps
     u0w = np.ascontiguousarray(u0[:nsub * M], dtype=np.float64)
     t0 = time.perf_counter()
-    oracle.run(u0w, N=N, P=P, order=cfg["order"], L=cfg["L"], nu=cfg["nu"], dt=dt, n_steps=steps,
-               forcing_amp=cfg["forcing_amp"], delay_mode=oracle.SEEDED, seed=cfg["seed"], p_lo=0, p_count=nsub)
+    ref, _ = oracle.run(u0w, N=N, P=P, order=cfg["order"], L=cfg["L"], nu=cfg["nu"], dt=dt, n_steps=steps,
+                        forcing_amp=cfg["forcing_amp"], delay_mode=oracle.SEEDED, seed=cfg["seed"], p_lo=0,
+                        p_count=nsub)
     el = time.perf_counter() - t0
     upd = nsub * M * steps
-    return {"value": upd / el / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{nsub} subdomains x {M} points ({nsub * M} points) of the N=2^26 workload, "
-                      f"{steps} seeded-delay steps, FP64, single thread: {upd:.3e} updates in {el:.2f} s"}
+    out = {"value": upd / el / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": f"{nsub} subdomains x {M} points ({nsub * M} points) of the N=2^26 workload, "
+                     f"{steps} seeded-delay steps, FP64, single thread: {upd:.3e} updates in {el:.2f} s"}
+    return out, ref, nsub, steps
+
+
+def small_config(args, at, torch, dev, stream):
+    """N = 4096, P = 16, order 2, L = 2, nu = 0.02, FP64, u0 = sin x + 0.5 sin(3x+1):
+    1000-step launches, free-running (plain and in passes of L+1 levels) vs
+    seeded vs synchronous, microseconds per step."""
+    cfg = W.config("burgers1d_n4096")
+    u0 = W.initial_field(cfg)
+    _, dx = W.grid(cfg["N"])
+    dt = W.dt_rule(u0, dx, cfg["nu"])
+    u0_dev = torch.from_numpy(u0).to(dev)
+    res = {"workload": "burgers1d_n4096", "N": cfg["N"], "P": cfg["P"], "order": cfg["order"], "L": cfg["L"],
+           "dtype": "f64", "time_steps_per_launch": cfg["n_steps"]}
+    arms = (("free", at.AT_FREE, 0), ("free_blocked", at.AT_FREE, cfg["L"] + 1), ("seeded", at.AT_SEEDED, 0),
+            ("sync", at.AT_SYNC, 0))
+    for name, mode, spp in arms:
+        s = at.Solver(cfg["N"], cfg["P"], cfg["order"], cfg["L"], cfg["nu"], dt, dtype="f64", seed=cfg["seed"],
+                      stream=stream, device=dev.index, steps_per_pass=spp)
+        s.set_state(u0_dev)
+        for _ in range(2):
+            s.step(cfg["n_steps"], mode)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 5
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+            for _ in range(reps):
+                s.step(cfg["n_steps"], mode)
+            e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1)
+        us_step = 1e3 * ms / (reps * cfg["n_steps"])
+        res[name] = {"us_per_step": us_step, "value": cfg["N"] / (us_step * 1e-6) / 1e9, "unit": UNIT}
+        s.close()
+    res["speedup_free_over_sync"] = res["sync"]["us_per_step"] / res["free"]["us_per_step"]
+    return res
 
 
 def reference_arm(args, ws, rank, pg):
@@ -398,7 +436,24 @@ def gpu_arm(args, ws, rank, local, pg):
         line["f64"] = {"value": ws * N * max(1, S // 10) * 3 / (f64["total_ms"] * 1e-3) / 1e9, "unit": UNIT,
                        "time_steps_per_step": max(1, S // 10), "bound": "fp64 alu (see DESIGN)"}
         if rank == 0 and ws == 1:
-            line["cpu_baseline"] = cpu_baseline(args, u0, dt, cfg)
+            cb, ref, nsub, csteps = cpu_baseline(args, u0, dt, cfg)
+            line["cpu_baseline"] = cb
+            # error of the GPU result against the FP64 oracle: the same seeded
+            # run on the GPU, compared away from the window's ends (values
+            # within R*steps points of them depend on the window's wrap)
+            s2 = at.Solver(N, P, order, L, nu, dt, dtype=args.dtype, forcing_amp=A, seed=cfg["seed"],
+                           stream=stream, device=local)
+            s2.set_state(u0_dev)
+            s2.step(csteps, at.AT_SEEDED)
+            g = s2.state().double().cpu().numpy()[:nsub * M]
+            s2.close()
+            cut = (order // 2) * csteps + M
+            err = float(np.max(np.abs(g[cut:-cut] - ref[cut:-cut])) / np.max(np.abs(ref)))
+            line["err_vs_fp64_oracle"] = {"rel_linf": err, "mode": "seeded", "steps": csteps,
+                                          "points_compared": int(nsub * M - 2 * cut), "dtype": args.dtype}
+        # the latency-bound case: N = 4096, P = 16 subdomains of 256 points,
+        # order 2, L = 2, FP64 (one PE per subdomain, four CTAs), AT vs barrier
+        line["small_config"] = small_config(args, at, torch, dev, stream)
     if rank == 0:
         print(json.dumps(line), flush=True)
 

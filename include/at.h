@@ -92,7 +92,8 @@ typedef struct at_grid {
   int32_t  max_ctas;        /* CTAs: 0 = all that can be resident at once (capped */
                             /* at P); else this many (AT_ERR_RESIDENCY if they    */
                             /* cannot all be resident)                            */
-  int32_t  stages;          /* tiles in flight per CTA: 0 = 16; at least 4        */
+  int32_t  stages;          /* tile buffers per warp: 0 = 3; at least 2; fewer if */
+                            /* shared memory cannot hold them                     */
   int64_t  test_skip_step;  /* level after which AT_FLAG_TEST_SKIP_PUBLISH acts    */
   int32_t  steps_per_pass;  /* AT_FREE only: levels advanced per pass over a tile  */
                             /* (temporal blocking), 0 or 1 = none, at most L+1    */
@@ -107,7 +108,7 @@ typedef struct at_info {
   int32_t T;                /* ring slots (levels kept per boundary)               */
   int32_t ctas;             /* CTAs of the persistent kernel                       */
   int32_t threads;          /* threads per CTA                                     */
-  int32_t stages;           /* tiles in flight per CTA                             */
+  int32_t stages;           /* tile buffers per warp                               */
   int64_t smem_bytes;       /* dynamic shared memory per CTA                       */
   int64_t step;             /* time level of the state (steps taken)               */
   int32_t sm_count;         /* SMs of the device                                   */

@@ -14,6 +14,13 @@ Workloads (1D viscous Burgers on the periodic interval [0, 2 pi)):
   order 4, L = 3, nu = 1e-3, forcing A sin(x) with A = 0.1,
   u0 = sum_{k=1}^{64} k^-1 sin(k x + phi_k), phi_k ~ U[0, 2 pi) (seed 2),
   seeded delays (seed 3) or free-running delays, 10^4 steps, FP32 or FP64.
+* ``burgers1d_ensemble_2048``: 2048 independent 1D problems on [-pi, pi),
+  N_j = 2^x_j (x_j ~ U[10, 16]) rounded to a multiple of 256 (P_j = N_j / 256
+  subdomains of M = 256 points), nu_j log-uniform in [1e-3, 1e-1], delay bound
+  L_j ~ U{1, 2, 3}, order 2, FP32, 5000 steps; initial data and boundary
+  values from the travelling tanh wave u = c - a tanh(a (x - xc - c t)/(2 nu))
+  with c_j ~ U[-0.5, 0.5], a_j = min(0.5, 0.5 nu_j / dx_j) (a front at least
+  4 dx wide), xc = 0; seed 6.
 
 The paper's own runs (3D Burgers' turbulence from a multi-scale sinusoidal
 initial condition, Sec. 3.1) use no dataset; these fields stand in for them.
@@ -90,6 +97,50 @@ def initial_field(cfg: dict, N: int | None = None) -> np.ndarray:
     if kind[0] == "fourier":
         return u0_fourier(N, modes=kind[1], seed=kind[2])
     raise KeyError(kind)
+
+
+def ensemble(n_inst: int = 2048, seed: int = 6, M: int = 256, log2_n=(10.0, 16.0), nu_range=(1e-3, 1e-1),
+             L_choices=(1, 2, 3), cfl: float = 0.2) -> list:
+    """Instances of an ensemble of travelling-wave problems (see the module
+    docstring): a list of dicts with n, L, nu, dt, length, origin, tanh_a,
+    tanh_c, tanh_xc and seed (the instance's seeded-delay seed).  dt follows
+    ``dt_rule`` on the instance's initial field."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(n_inst):
+        n = int(round(2.0 ** rng.uniform(*log2_n) / M)) * M
+        n = max(n, M)
+        nu = float(np.exp(rng.uniform(math.log(nu_range[0]), math.log(nu_range[1]))))
+        L = int(rng.choice(L_choices))
+        c = float(rng.uniform(-0.5, 0.5))
+        dx = TWO_PI / n
+        a = min(0.5, 0.5 * nu / dx)
+        inst = dict(n=n, L=L, nu=nu, length=TWO_PI, origin=-math.pi, tanh_a=a, tanh_c=c, tanh_xc=0.0,
+                    seed=int(rng.integers(0, 2**62)))
+        inst["dt"] = dt_rule(tanh_wave(inst, 0.0), dx, nu, cfl=cfl)
+        out.append(inst)
+    return out
+
+
+def tanh_wave(inst: dict, t: float) -> np.ndarray:
+    """The instance's travelling wave u = c - a tanh(a (x - xc - c t)/(2 nu))
+    at time t on its grid x_i = origin + i length / n."""
+    x, _ = grid(inst["n"], inst["length"], inst["origin"])
+    a, c = inst["tanh_a"], inst["tanh_c"]
+    return c - a * np.tanh(a * (x - inst["tanh_xc"] - c * t) / (2.0 * inst["nu"]))
+
+
+def instance_field(inst: dict) -> np.ndarray:
+    """Initial field of an instance: its own ``u0`` if it has one, else the
+    travelling wave at t = 0."""
+    if "u0" in inst:
+        return np.asarray(inst["u0"], dtype=np.float64)
+    return tanh_wave(inst, 0.0)
+
+
+def ensemble_field(instances: list) -> np.ndarray:
+    """Initial state of an ensemble: the instances' fields at t = 0, end to end."""
+    return np.concatenate([instance_field(d) for d in instances])
 
 
 def random_delays(n_steps: int, P: int, L: int, seed: int, faces: int = 2) -> np.ndarray:

@@ -62,6 +62,7 @@ def parse():
     ap.add_argument("--M", type=int, default=0, help="points per subdomain for experiments (default 1024)")
     ap.add_argument("--order", type=int, default=0, help="stencil order for experiments (default 4)")
     ap.add_argument("--forcing", type=float, default=-1.0, help="forcing amplitude for experiments (default 0.1)")
+    ap.add_argument("--ensemble-only", action="store_true", help="time only the 2048-instance ensemble leg")
     return ap.parse_args()
 
 
@@ -208,6 +209,86 @@ def small_config(args, at, torch, dev, stream):
         res[name] = {"us_per_step": us_step, "value": cfg["N"] / (us_step * 1e-6) / 1e9, "unit": UNIT}
         s.close()
     res["speedup_free_over_sync"] = res["sync"]["us_per_step"] / res["free"]["us_per_step"]
+    return res
+
+
+def ensemble_config(args, at, torch, dev, stream, time_steps=5000):
+    """The 2048-instance travelling-wave ensemble (N_j log-uniform in
+    [2^10, 2^16], M = 256, order 2, L_j in {1, 2, 3}, FP32): one persistent
+    launch of 5000 steps captured in a CUDA graph and replayed, launch shape
+    picked by the autotuner (free-running delays); the synchronous arm the same
+    way; the FP32 result's error against the FP64 oracle on sampled instances."""
+    inst = W.ensemble()
+    M, order = 256, 2
+    Ntot = sum(d["n"] for d in inst)
+    u0 = torch.from_numpy(W.ensemble_field(inst)).to(device=dev, dtype=torch.float32)
+    res = {"workload": "burgers1d_ensemble_2048", "instances": len(inst), "N": Ntot, "P": Ntot // M, "M": M,
+           "order": order, "L_j": [1, 2, 3], "dtype": "f32", "time_steps_per_launch": time_steps,
+           "l2": f"state {Ntot * 4 / 2**20:.0f} MiB: close to the 126 MiB L2 (replays continue in place)"}
+    Lmax = max(d["L"] for d in inst)
+
+    def run(mode, name):
+        s = at.EnsembleSolver(inst, M, order, dtype="f32", stream=stream, device=dev.index,
+                              steps_per_pass=Lmax + 1 if mode == at.AT_FREE else 0)
+        with torch.cuda.stream(stream):
+            s.set_state(u0)
+        t = s.tune(200, mode)
+        with torch.cuda.stream(stream):
+            s.set_state(u0)
+        torch.cuda.synchronize(dev)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=stream):
+            s.step(time_steps, mode)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        with torch.cuda.stream(stream):
+            for _ in range(args.warmup):
+                g.replay()
+            ev[0].record(stream)
+            for _ in range(args.steps):
+                g.replay()
+            ev[1].record(stream)
+        torch.cuda.synchronize(dev)
+        ms = ev[0].elapsed_time(ev[1]) / args.steps
+        rc = s.status()
+        if rc != at.AT_OK:
+            raise RuntimeError(f"ensemble {name}: device status {rc}: {at.at_last_error()}")
+        info = s.info()
+        assert info.step == (args.warmup + args.steps) * time_steps, info.step
+        s.close()
+        del g
+        return {"value": Ntot * time_steps / (ms * 1e-3) / 1e9, "unit": UNIT, "ms_per_launch": ms,
+                "tuned": {"ctas": t.ctas, "stages": t.stages, "steps_per_pass": t.steps_per_pass,
+                          "shapes_tried": t.n_tried, "ms_200_steps_first": t.first_ms,
+                          "ms_200_steps_best": t.best_ms}}
+
+    res["free"] = run(at.AT_FREE, "free")
+    res["sync"] = run(at.AT_SYNC, "sync")
+    res["speedup_free_over_sync"] = res["free"]["value"] / res["sync"]["value"]
+    res["effective_one_pass_frac"] = res["free"]["value"] * 1e9 * 8 / (hbm_peak()[0] * 1e9)
+    res["gpu_launches_per_replay"] = 1
+    # FP32 error against the FP64 oracle after the full 5000 seeded steps, on
+    # the four smallest instances and one mid-size one
+    s = at.EnsembleSolver(inst, M, order, dtype="f32", stream=stream, device=dev.index)
+    with torch.cuda.stream(stream):
+        s.set_state(u0)
+        s.step(time_steps, at.AT_SEEDED)
+        g = s.state().double().cpu().numpy()
+    s.close()
+    n = np.array([d["n"] for d in inst])
+    which = list(np.argsort(n)[:4]) + [int(np.argsort(n)[len(n) // 2])]
+    import oracle
+    offs = np.concatenate([[0], np.cumsum(n)])
+    worst = 0.0
+    for j in which:
+        d = inst[j]
+        ref, _ = oracle.run(W.instance_field(d), N=d["n"], P=d["n"] // M, order=order, L=d["L"], nu=d["nu"],
+                            dt=d["dt"], n_steps=time_steps, x0=d["origin"], dx=d["length"] / d["n"],
+                            bc=oracle.BC_TANH, tanh=(d["tanh_a"], d["tanh_c"], d["tanh_xc"]),
+                            delay_mode=oracle.SEEDED, seed=d["seed"])
+        part = g[offs[j]:offs[j + 1]]
+        worst = max(worst, float(np.max(np.abs(part - ref)) / np.max(np.abs(ref))))
+    res["err_vs_fp64_oracle"] = {"rel_linf": worst, "mode": "seeded", "steps": time_steps,
+                                 "instances": [int(j) for j in which]}
     return res
 
 
@@ -454,6 +535,8 @@ def gpu_arm(args, ws, rank, local, pg):
         # the latency-bound case: N = 4096, P = 16 subdomains of 256 points,
         # order 2, L = 2, FP64 (one PE per subdomain, four CTAs), AT vs barrier
         line["small_config"] = small_config(args, at, torch, dev, stream)
+        if rank == 0 and ws == 1:
+            line["ensemble"] = ensemble_config(args, at, torch, dev, stream)
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -467,6 +550,16 @@ def main():
         reference_arm(args, ws, rank, None)
         return
     ws, rank, local, pg = dist_setup(args)
+    if args.ensemble_only:
+        import torch
+
+        import paper_1911_05769_gb300 as at
+        from paper_1911_05769_gb300 import build as atbuild
+        atbuild.build()
+        torch.cuda.set_device(local)
+        dev = torch.device("cuda", local)
+        print(json.dumps(ensemble_config(args, at, torch, dev, torch.cuda.Stream(device=dev))), flush=True)
+        return
     gpu_arm(args, ws, rank, local, pg)
     if pg is not None:
         pg.destroy_process_group()

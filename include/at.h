@@ -56,7 +56,10 @@ extern "C" {
 #define AT_F32 1
 
 /* boundary condition */
-#define AT_BC_PERIODIC 0
+#define AT_BC_PERIODIC   0  /* periodic domain (the paper's setting, Sec. 3.2)     */
+#define AT_BC_EXACT_TANH 1  /* ensembles only: points outside the domain take the
+                               exact travelling-wave values at the current level,
+                               undelayed (see at_instance)                        */
 
 /* delay modes of at_step (Sec. 2 delay model; Algorithms 1 and 2) */
 #define AT_SYNC   0  /* k = 0 everywhere, grid barrier every step (Alg. 1)     */
@@ -139,7 +142,10 @@ int at_create(const at_grid *grid, int64_t P, int scheme_order, int L,
 int at_set_state(at_solver *h, const void *u);
 
 /* Advances the state by n_steps >= 0 forward-Euler steps in one persistent
- * kernel launch on the grid's stream (asynchronous).
+ * kernel launch on the grid's stream (asynchronous, no host synchronisation:
+ * it may be captured into a CUDA graph).  The time level of the state is kept
+ * in the workspace and advanced by the kernel itself, so every replay of a
+ * captured graph continues from the level the previous replay reached.
  *   delay_mode: AT_SYNC, AT_SEEDED, AT_FREE or AT_REPLAY.
  *   delays:     device array int8 [n_steps][P][2] (face 0 = left neighbour
  *               p-1, face 1 = right neighbour p+1).  AT_REPLAY reads the delays
@@ -162,7 +168,9 @@ int at_status(at_solver *h);
  * moments of Eq. err_scaling.  Any pointer may be NULL.  Synchronises. */
 int at_delay_stats(at_solver *h, int64_t *hist, double *mean_k, double *mean_k2);
 
-/* Fills *info with the launch facts of the solver. */
+/* Fills *info with the launch facts of the solver.  info->step is read from
+ * the device (waiting for the stream) unless the stream is being captured;
+ * then it counts the steps of the at_step calls made so far. */
 int at_get_info(const at_solver *h, at_info *info);
 
 /* Releases the handle (host memory only; the workspace stays the caller's). */
@@ -170,6 +178,73 @@ int at_destroy(at_solver *h);
 
 /* Message of the last failed call on this thread ("" if none). */
 const char *at_last_error(void);
+
+/* ---------------------------------------------------------------------------
+ * Ensembles: many independent 1D problems advanced by one persistent launch.
+ *
+ * Instance j has n_j points (a multiple of the common subdomain size M, so
+ * n_j / M subdomains of M points), its own viscosity, time step, delay bound
+ * L_j and seed, and either a periodic domain or exact travelling-wave
+ * boundary values: with AT_BC_EXACT_TANH the points just outside
+ * [origin, origin + length) take u = c - a tanh(a (x - xc - c t) / (2 nu)),
+ * the viscous Burgers travelling wave, at t = n dt (undelayed).  Inside an
+ * instance the method is that of at_create: central stencils, AT stencils
+ * at subdomain faces, delays per (level, subdomain, face).  With AT_SEEDED
+ * the delays of instance j are those of a single-domain solver with
+ * P = n_j / M, L = L_j and seed = seed_j.  The instances' subdomains are laid
+ * end to end: the state is the concatenation of the instances' fields
+ * (instance 0 first), N = sum n_j words, P = N / M subdomains in all.  A
+ * processing element (warp) may hold subdomains of several instances; its
+ * passes in AT_FREE are then no longer than the smallest L_j among them + 1.
+ * The paper treats one domain; ensembles are an extension.
+ * --------------------------------------------------------------------------- */
+typedef struct at_instance {
+  int64_t  n;               /* points of the instance (multiple of M)              */
+  int32_t  L;               /* maximal delay of the instance, 0..16                */
+  int32_t  bc;              /* AT_BC_PERIODIC or AT_BC_EXACT_TANH                  */
+  double   length, origin;  /* domain [origin, origin + length); dx = length / n  */
+  double   nu, dt;          /* viscosity (> 0 for AT_BC_EXACT_TANH), time step    */
+  double   tanh_a, tanh_c, tanh_xc;  /* a, c, xc of the exact boundary values     */
+  uint64_t seed;            /* AT_SEEDED seed of the instance                      */
+} at_instance;
+
+/* Workspace bytes for an ensemble, or 0 if the arguments are invalid. */
+size_t at_batch_workspace_bytes(const at_grid *grid, int64_t n_inst, const at_instance *inst, int64_t M,
+                                int scheme_order);
+
+/* Creates a solver for the ensemble inst[0 .. n_inst-1] (host array, read
+ * during the call) with subdomains of M points (a multiple of 4, 4..1024)
+ * and stencil order scheme_order.  From grid it uses dtype, flags,
+ * workspace, stream, timeout_ns, max_ctas, stages and steps_per_pass (at
+ * most max L_j + 1); forcing_amp must be 0.  Copies the instance tables into
+ * the workspace and waits for the stream.  The returned handle takes the
+ * calls of a single-domain solver (at_set_state with N words, at_step with a
+ * [n_steps][P][2] delay array over all subdomains, at_state, ...); at_info
+ * reports the total N and P and L = max L_j. */
+int at_create_batch(const at_grid *grid, int64_t n_inst, const at_instance *inst, int64_t M, int scheme_order,
+                    at_solver **out);
+
+/* ---------------------------------------------------------------------------
+ * Autotuner.  Launch shapes of the persistent kernel: CTAs (1 up to the
+ * resident limit per SM, times the SM count: so the processing elements per
+ * subdomain), tile buffers per warp (2..4) and, for AT_FREE, levels per pass
+ * (1 .. L + 1; in an ensemble each processing element then takes at most its
+ * own smallest delay bound + 1).
+ * --------------------------------------------------------------------------- */
+typedef struct at_tune_result {
+  int32_t ctas, stages, steps_per_pass;   /* the fastest shape                     */
+  int32_t n_tried;                        /* shapes timed                          */
+  double  best_ms;                        /* its time for at_step(n_steps)          */
+  double  first_ms;                       /* time of the shape the solver had      */
+} at_tune_result;
+
+/* Times at_step(h, n_steps, delay_mode, NULL) for every launch shape above
+ * (one untimed launch, then the best of two timed ones, CUDA events on the
+ * solver's stream) and keeps the fastest on the handle.  This runs the
+ * solver: the state advances by 3 n_steps per shape, so set the state again
+ * before a production run.  Synchronises; not for use under stream capture.
+ * Returns AT_OK, or the first error (then the handle keeps its shape). */
+int at_tune(at_solver *h, int64_t n_steps, int delay_mode, at_tune_result *res);
 
 /* Size in bytes of the fixed scratch array used by at_step_noalloc(). */
 #define AT_NOALLOC_SCRATCH_BYTES (8u * 1024u * 1024u)

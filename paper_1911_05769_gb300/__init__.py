@@ -11,13 +11,15 @@ convenience wrapper (``Solver``) that keeps the workspace in a torch tensor.
 There is no CPU fallback: importing the binding fails if the library is
 missing.
 """
-from .binding import (AT_BC_PERIODIC, AT_ERR_ARG, AT_ERR_CUDA, AT_ERR_RESIDENCY, AT_ERR_STATE,
+from .binding import (AT_BC_EXACT_TANH, AT_BC_PERIODIC, AT_ERR_ARG, AT_ERR_CUDA, AT_ERR_RESIDENCY, AT_ERR_STATE,
                       AT_ERR_TIMEOUT, AT_ERR_UNSTABLE, AT_F32, AT_F64, AT_FLAG_ALLOW_UNSTABLE,
                       AT_FLAG_PER_SUBDOMAIN_DELAY, AT_FLAG_TEST_SKIP_PUBLISH, AT_FREE, AT_NOALLOC_SCRATCH_BYTES, AT_OK,
                       AT_REPLAY,
-                      AT_SEEDED, AT_SYNC, AtError, at_create, at_delay_stats, at_destroy, at_get_info,
-                      at_grid, at_info, at_last_error, at_set_state, at_state, at_status, at_step,
-                      at_step_noalloc, at_workspace_bytes, library_path)
-from .solver import Solver
+                      AT_SEEDED, AT_SYNC, AtError, at_batch_workspace_bytes, at_create, at_create_batch,
+                      at_delay_stats, at_destroy, at_get_info, at_grid, at_info, at_instance, at_last_error,
+                      at_set_state, at_state, at_status, at_step, at_step_noalloc, at_tune, at_tune_result,
+                      at_workspace_bytes, library_path)
+from .solver import EnsembleSolver, Solver
 
-__all__ = [n for n in dir() if n.startswith(("AT_", "at_"))] + ["AtError", "Solver", "library_path"]
+__all__ = [n for n in dir() if n.startswith(("AT_", "at_"))] + ["AtError", "EnsembleSolver", "Solver",
+                                                                   "library_path"]

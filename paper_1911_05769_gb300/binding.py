@@ -28,6 +28,7 @@ AT_ERR_STATE = -6
 AT_F64 = 0
 AT_F32 = 1
 AT_BC_PERIODIC = 0
+AT_BC_EXACT_TANH = 1
 
 AT_SYNC = 0
 AT_SEEDED = 1
@@ -62,6 +63,22 @@ class at_info(ctypes.Structure):
     ]
 
 
+class at_instance(ctypes.Structure):
+    _fields_ = [
+        ("n", ctypes.c_int64), ("L", ctypes.c_int32), ("bc", ctypes.c_int32),
+        ("length", ctypes.c_double), ("origin", ctypes.c_double), ("nu", ctypes.c_double), ("dt", ctypes.c_double),
+        ("tanh_a", ctypes.c_double), ("tanh_c", ctypes.c_double), ("tanh_xc", ctypes.c_double),
+        ("seed", ctypes.c_uint64),
+    ]
+
+
+class at_tune_result(ctypes.Structure):
+    _fields_ = [
+        ("ctas", ctypes.c_int32), ("stages", ctypes.c_int32), ("steps_per_pass", ctypes.c_int32),
+        ("n_tried", ctypes.c_int32), ("best_ms", ctypes.c_double), ("first_ms", ctypes.c_double),
+    ]
+
+
 # (name, restype, argtypes) of every exported entry point
 _SIGNATURES = [
     ("at_workspace_bytes", ctypes.c_size_t,
@@ -82,6 +99,12 @@ _SIGNATURES = [
     ("at_step_noalloc", ctypes.c_int,
      [ctypes.POINTER(at_grid), ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
       ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p]),
+    ("at_batch_workspace_bytes", ctypes.c_size_t,
+     [ctypes.POINTER(at_grid), ctypes.c_int64, ctypes.POINTER(at_instance), ctypes.c_int64, ctypes.c_int]),
+    ("at_create_batch", ctypes.c_int,
+     [ctypes.POINTER(at_grid), ctypes.c_int64, ctypes.POINTER(at_instance), ctypes.c_int64, ctypes.c_int,
+      ctypes.POINTER(ctypes.c_void_p)]),
+    ("at_tune", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.POINTER(at_tune_result)]),
 ]
 
 EXPORTED = [s[0] for s in _SIGNATURES]
@@ -166,6 +189,25 @@ def at_step_noalloc(grid: at_grid, P: int, scheme_order: int, L: int, nu: float,
     fixed array (see include/at.h).  Synchronises and returns the status."""
     return lib().at_step_noalloc(ctypes.byref(grid), P, scheme_order, L, nu, dt, ctypes.c_void_p(u_ptr), n_steps,
                                  delay_mode, ctypes.c_void_p(delays_ptr) if delays_ptr else None)
+
+
+def at_batch_workspace_bytes(grid: at_grid, instances, M: int, scheme_order: int) -> int:
+    """instances: ctypes array of at_instance."""
+    return int(lib().at_batch_workspace_bytes(ctypes.byref(grid), len(instances), instances, M, scheme_order))
+
+
+def at_create_batch(grid: at_grid, instances, M: int, scheme_order: int):
+    """Returns (code, handle).  instances: ctypes array of at_instance."""
+    h = ctypes.c_void_p()
+    rc = lib().at_create_batch(ctypes.byref(grid), len(instances), instances, M, scheme_order, ctypes.byref(h))
+    return rc, h
+
+
+def at_tune(h, n_steps: int, delay_mode: int):
+    """Returns (code, at_tune_result)."""
+    res = at_tune_result()
+    rc = lib().at_tune(h, n_steps, delay_mode, ctypes.byref(res))
+    return rc, res
 
 
 def at_last_error() -> str:

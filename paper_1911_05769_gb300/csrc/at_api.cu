@@ -12,6 +12,7 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "at.h"
 #include "at_kernels.cuh"
@@ -20,6 +21,8 @@ void *atk_stepper_kernel_f32(int order, int gw, bool forced, bool full);
 void *atk_stepper_kernel_f64(int order, int gw, bool forced, bool full);
 void *atk_init_kernel_f32(int order);
 void *atk_init_kernel_f64(int order);
+void *atk_batch_kernel_f32(int order, int gw, bool full);
+void *atk_batch_kernel_f64(int order, int gw, bool full);
 
 namespace {
 
@@ -53,10 +56,13 @@ int ring_slots(int L, int s)
 }
 
 struct Layout {
-    size_t u, ring, flag, ctrl, hist, gbar, total;
+    size_t u, ring, flag, ctrl, hist, gbar, bsub, binst, total;
 };
 
-Layout layout(int64_t N, int64_t P, int w, int L, int T)
+// Workspace: state, ring buffers [T][P][2], flags [P][2], control block,
+// delay counts, barrier counter; for an ensemble (n_inst > 0) also the
+// subdomain and instance records.
+Layout layout(int64_t N, int64_t P, int w, int L, int T, int64_t n_inst = 0)
 {
     Layout l{};
     size_t off = 0;
@@ -66,6 +72,12 @@ Layout layout(int64_t N, int64_t P, int w, int L, int T)
     l.ctrl = off; off = align_up(off + atk::kCtrlWords * 4, 256);
     l.hist = off; off = align_up(off + (size_t)(L + 1) * 8, 256);
     l.gbar = off; off = align_up(off + 8, 256);
+    l.bsub = off; l.binst = off;
+    if (n_inst > 0) {
+        off = align_up(off + (size_t)P * sizeof(atk::BatchSub), 256);
+        l.binst = off;
+        off = align_up(off + (size_t)n_inst * sizeof(atk::BatchInst), 256);
+    }
     l.total = off;
     return l;
 }
@@ -100,17 +112,6 @@ int groups_per_lane(int64_t M)
     return g;
 }
 
-// Passes of at_step over the subdomains: one level per pass while the level
-// is below s-1, then passes of sb levels (the last one shorter).
-long long count_passes(long long n0, long long n_steps, int s, int sb)
-{
-    long long single = (s - 1) - n0;
-    if (single < 0) single = 0;
-    if (single > n_steps) single = n_steps;
-    const long long rest = n_steps - single;
-    return single + (rest + sb - 1) / sb;
-}
-
 // The stepper and init kernels for a word size, order, subdomain size and
 // forcing (instantiated in at_kernels_f32.cu / at_kernels_f64.cu).
 void pick_kernels(int w, int order, int64_t M, bool forced, void **stepper, void **init)
@@ -126,17 +127,30 @@ void pick_kernels(int w, int order, int64_t M, bool forced, void **stepper, void
     }
 }
 
+// Shared-memory table of a CTA: `fixed` bytes plus `per_sub` bytes per
+// subdomain of each of its PEs (forcing: sin/cos tables; ensembles: records).
+struct TabSize {
+    long long fixed, per_sub;
+};
+
+TabSize tab_size(int64_t M, int w, bool forced, bool batch)
+{
+    if (batch) return {0, (long long)sizeof(atk::BatchSub)};
+    if (forced) return {2LL * M * w, 2LL * w};
+    return {0, 0};
+}
+
 // Chooses the CTA count (all co-resident CTAs unless max_ctas is set, at most
 // one PE per subdomain) and the stages per PE that fit in shared memory, and
 // sets the kernel's dynamic shared-memory size.
-int launch_shape(int64_t M, int w, int64_t P, bool forced, int max_ctas, int stages, int sms, int smem_optin,
+int launch_shape(int64_t M, int w, int64_t P, TabSize tsz, int max_ctas, int stages, int sms, int smem_optin,
                  void *kernel, int *G_out, int *stages_out, atk::SmemLayout *sl_out, int *smem_out,
                  long long *smax_out)
 {
     auto layout_for = [&](int G, int st, long long *smax) {
         const int64_t E = (int64_t)G * atk::kWarps;
         *smax = (P + E - 1) / E;
-        const long long tab = forced ? 2 * M + 2LL * atk::kWarps * *smax : 0;
+        const long long tab = tsz.fixed + (long long)atk::kWarps * *smax * tsz.per_sub;
         return atk::smem_layout(M, w, st, tab);
     };
     // CTAs needed for one PE per subdomain at most
@@ -179,16 +193,65 @@ struct at_solver {
     Layout lay;
     unsigned char *ws;
     cudaStream_t stream;
-    int device, sm_count;
+    int device, sm_count, smem_optin;
     int G, stages, sb, smem;
     long long smax;
     atk::SmemLayout sl;
-    int64_t step;
-    unsigned long long gbar_count;
+    int64_t step;              // steps launched since at_set_state (host count)
+    int64_t flags_E;           // PEs of the launch that last released flags (0: none since the state was set)
     bool has_state;
+    bool batch;                // ensemble of instances
+    int64_t n_inst;
+    int lmin;                  // smallest delay bound (ensembles), else L
     void *kernel;
     void *init_kernel;
 };
+
+namespace {
+
+// Sets every progress flag to the level of the state.  A launch releases
+// only the flags of faces between processing elements; after a launch with
+// another partition of the subdomains (another CTA count) the flags of faces
+// that were inside a PE are stale, while every level up to the state's is
+// complete and its ring entries are written (entries go out on every face).
+__global__ void at_flags_to_level(unsigned long long *flag, const int *ctrl, long long nflags)
+{
+    const long long n0 = *reinterpret_cast<const long long *>(ctrl + atk::kCtrlN0);
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nflags;
+         i += (long long)gridDim.x * blockDim.x)
+        flag[i] = (unsigned long long)n0;
+}
+
+// One launch of the persistent stepper: cooperative, so that every CTA is
+// resident; cudaLaunchKernelExC with the cooperative attribute may be
+// captured into a CUDA graph.  Brings the flags up to date first when the
+// partition into PEs differs from the previous launch's.
+cudaError_t launch_stepper(at_solver *h, atk::Params *p)
+{
+    const int64_t E = (int64_t)h->G * atk::kWarps;
+    if (h->flags_E != 0 && h->flags_E != E) {
+        const long long nflags = h->P * 2;
+        const int blocks = (int)((nflags + 255) / 256 < 1024 ? (nflags + 255) / 256 : 1024);
+        at_flags_to_level<<<blocks, 256, 0, h->stream>>>(p->flag, p->ctrl, nflags);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    h->flags_E = E;
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(h->G);
+    cfg.blockDim = dim3(atk::kThreads);
+    cfg.dynamicSmemBytes = (size_t)h->smem;
+    cfg.stream = h->stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    void *args[] = {p};
+    return cudaLaunchKernelExC(&cfg, h->kernel, args);
+}
+
+}  // namespace
 
 extern "C" {
 
@@ -244,7 +307,8 @@ int at_create(const at_grid *grid, int64_t P, int scheme_order, int L, double nu
     h->lay = lay;
     h->ws = static_cast<unsigned char *>(grid->workspace);
     h->stream = static_cast<cudaStream_t>(grid->stream);
-    h->device = dev; h->sm_count = sms;
+    h->device = dev; h->sm_count = sms; h->smem_optin = smem_optin;
+    h->batch = false; h->n_inst = 0; h->lmin = L;
 
     pick_kernels(w, scheme_order, h->M, grid->forcing_amp != 0.0, &h->kernel, &h->init_kernel);
 
@@ -254,12 +318,11 @@ int at_create(const at_grid *grid, int64_t P, int scheme_order, int L, double nu
     const int sb = grid->steps_per_pass > 0 ? grid->steps_per_pass : 1;
     int stages = grid->stages > 0 ? grid->stages : 3;
     if (stages < atk::kMinStages) stages = atk::kMinStages;
-    int rc2 = launch_shape(h->M, w, P, grid->forcing_amp != 0.0, grid->max_ctas, stages, sms, smem_optin,
-                           h->kernel, &h->G, &h->stages, &h->sl, &h->smem, &h->smax);
+    int rc2 = launch_shape(h->M, w, P, tab_size(h->M, w, grid->forcing_amp != 0.0, false), grid->max_ctas, stages,
+                           sms, smem_optin, h->kernel, &h->G, &h->stages, &h->sl, &h->smem, &h->smax);
     if (rc2 != AT_OK) { delete h; return rc2; }
     h->sb = sb;
     h->step = 0;
-    h->gbar_count = 0;
     h->has_state = false;
     *out = h;
     return AT_OK;
@@ -274,6 +337,10 @@ static atk::Params make_params(const at_solver *h)
     p.ctrl = reinterpret_cast<int *>(h->ws + h->lay.ctrl);
     p.hist = reinterpret_cast<unsigned long long *>(h->ws + h->lay.hist);
     p.gbar = reinterpret_cast<unsigned long long *>(h->ws + h->lay.gbar);
+    if (h->batch) {
+        p.bsub = reinterpret_cast<const atk::BatchSub *>(h->ws + h->lay.bsub);
+        p.binst = reinterpret_cast<const atk::BatchInst *>(h->ws + h->lay.binst);
+    }
     p.N = h->N; p.P = h->P; p.M = h->M;
     p.L = h->L; p.T = h->T;
     p.per_sub = (h->g.flags & AT_FLAG_PER_SUBDOMAIN_DELAY) ? 1 : 0;
@@ -319,7 +386,7 @@ int at_set_state(at_solver *h, const void *u)
     e = cudaLaunchKernel(h->init_kernel, dim3(blocks), dim3(256), args, 0, h->stream);
     if (e != cudaSuccess) return cuda_fail(e, "launch at_init");
     h->step = 0;
-    h->gbar_count = 0;
+    h->flags_E = 0;
     h->has_state = true;
     return AT_OK;
 }
@@ -336,17 +403,11 @@ int at_step(at_solver *h, int64_t n_steps, int delay_mode, int8_t *delays)
     atk::Params p = make_params(h);
     p.mode = delay_mode;
     p.delays = delays;
-    p.n0 = h->step;
     p.n_steps = n_steps;
-    p.gbar_base = h->gbar_count;
     p.sb = delay_mode == AT_FREE ? h->sb : 1;
-    p.n_passes = count_passes(p.n0, n_steps, h->s, p.sb);
-    void *args[] = {&p};
-    cudaError_t e = cudaLaunchCooperativeKernel(h->kernel, dim3(h->G), dim3(atk::kThreads), args, (size_t)h->smem,
-                                                h->stream);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaLaunchCooperativeKernel(at_stepper)");
+    const cudaError_t e = launch_stepper(h, &p);
+    if (e != cudaSuccess) return cuda_fail(e, "cooperative launch of at_stepper");
     h->step += n_steps;
-    if (delay_mode == AT_SYNC) h->gbar_count += (unsigned long long)n_steps * (unsigned long long)h->G;
     return AT_OK;
 }
 
@@ -411,12 +472,289 @@ int at_get_info(const at_solver *h, at_info *info)
     info->ctas = h->G; info->threads = atk::kThreads; info->stages = h->stages;
     info->smem_bytes = h->smem; info->step = h->step; info->sm_count = h->sm_count;
     info->dtype = h->g.dtype; info->steps_per_pass = h->sb;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (h->has_state && cudaStreamIsCapturing(h->stream, &cap) == cudaSuccess && cap == cudaStreamCaptureStatusNone) {
+        long long n0 = 0;
+        cudaError_t e = cudaMemcpyAsync(&n0, h->ws + h->lay.ctrl + 4 * atk::kCtrlN0, sizeof(n0),
+                                        cudaMemcpyDeviceToHost, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "reading the level of the state");
+        info->step = n0;
+    }
     return AT_OK;
 }
 
 int at_destroy(at_solver *h)
 {
     delete h;
+    return AT_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Ensembles
+// ---------------------------------------------------------------------------
+namespace {
+
+struct BatchDims {
+    int64_t N, P;
+    int Lmax, Lmin;
+};
+
+int check_batch(const at_grid *g, int64_t n_inst, const at_instance *inst, int64_t M, int order, BatchDims *d)
+{
+    if (!g) return fail(AT_ERR_ARG, "grid is NULL");
+    if (g->dim != 1) return fail(AT_ERR_ARG, "dim must be 1");
+    if (g->dtype != AT_F64 && g->dtype != AT_F32) return fail(AT_ERR_ARG, "dtype must be AT_F64 or AT_F32");
+    if (g->forcing_amp != 0.0) return fail(AT_ERR_ARG, "ensembles are unforced (forcing_amp must be 0)");
+    if (order != 2 && order != 4) return fail(AT_ERR_ARG, "scheme_order must be 2 or 4");
+    if (M % 4 != 0 || M < 4 || M > atk::kMaxM)
+        return fail(AT_ERR_ARG, "M must be a multiple of 4 in 4..%d (M=%lld)", atk::kMaxM, (long long)M);
+    if (n_inst <= 0 || !inst) return fail(AT_ERR_ARG, "no instances");
+    d->N = 0;
+    d->Lmax = 0;
+    d->Lmin = atk::kMaxL;
+    const double lim = order == 2 ? 0.5 : 0.375;
+    for (int64_t j = 0; j < n_inst; ++j) {
+        const at_instance &a = inst[j];
+        if (a.n <= 0 || a.n % M != 0)
+            return fail(AT_ERR_ARG, "instance %lld: n=%lld is not a positive multiple of M=%lld", (long long)j,
+                        (long long)a.n, (long long)M);
+        if (a.L < 0 || a.L > atk::kMaxL) return fail(AT_ERR_ARG, "instance %lld: L must be in 0..%d", (long long)j,
+                                                     atk::kMaxL);
+        if (a.bc != AT_BC_PERIODIC && a.bc != AT_BC_EXACT_TANH)
+            return fail(AT_ERR_ARG, "instance %lld: bad bc %d", (long long)j, a.bc);
+        if (!(a.length > 0.0) || !std::isfinite(a.length) || !std::isfinite(a.origin))
+            return fail(AT_ERR_ARG, "instance %lld: length must be positive", (long long)j);
+        if (!(a.dt > 0.0) || !std::isfinite(a.dt)) return fail(AT_ERR_ARG, "instance %lld: dt must be positive",
+                                                                (long long)j);
+        if (!(a.nu >= 0.0) || !std::isfinite(a.nu)) return fail(AT_ERR_ARG, "instance %lld: nu must be >= 0",
+                                                                 (long long)j);
+        if (a.bc == AT_BC_EXACT_TANH && !(a.nu > 0.0))
+            return fail(AT_ERR_ARG, "instance %lld: exact tanh boundary values need nu > 0", (long long)j);
+        const double dx = a.length / (double)a.n;
+        if (!(g->flags & AT_FLAG_ALLOW_UNSTABLE) && a.nu * a.dt / (dx * dx) > lim)
+            return fail(AT_ERR_UNSTABLE, "instance %lld: nu*dt/dx^2 = %g exceeds %g", (long long)j,
+                        a.nu * a.dt / (dx * dx), lim);
+        d->N += a.n;
+        if (a.L > d->Lmax) d->Lmax = a.L;
+        if (a.L < d->Lmin) d->Lmin = a.L;
+    }
+    d->P = d->N / M;
+    if (g->steps_per_pass < 0 || g->steps_per_pass > d->Lmax + 1)
+        return fail(AT_ERR_ARG, "steps_per_pass must be in 0..max L + 1, got %d", g->steps_per_pass);
+    return AT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t at_batch_workspace_bytes(const at_grid *grid, int64_t n_inst, const at_instance *inst, int64_t M,
+                                int scheme_order)
+{
+    BatchDims d{};
+    if (check_batch(grid, n_inst, inst, M, scheme_order, &d) != AT_OK) return 0;
+    const int w = grid->dtype == AT_F64 ? 8 : 4;
+    const int s = scheme_order / 2 + 1;
+    return layout(d.N, d.P, w, d.Lmax, ring_slots(d.Lmax, s), n_inst).total;
+}
+
+int at_create_batch(const at_grid *grid, int64_t n_inst, const at_instance *inst, int64_t M, int scheme_order,
+                    at_solver **out)
+{
+    g_err[0] = 0;
+    if (!out) return fail(AT_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    BatchDims d{};
+    int rc = check_batch(grid, n_inst, inst, M, scheme_order, &d);
+    if (rc != AT_OK) return rc;
+    const int w = grid->dtype == AT_F64 ? 8 : 4;
+    const int s = scheme_order / 2 + 1;
+    const int T = ring_slots(d.Lmax, s);
+    const Layout lay = layout(d.N, d.P, w, d.Lmax, T, n_inst);
+    if (!grid->workspace) return fail(AT_ERR_ARG, "workspace is NULL");
+    if (grid->workspace_bytes < lay.total)
+        return fail(AT_ERR_ARG, "workspace too small: %zu < %zu", grid->workspace_bytes, lay.total);
+    if (reinterpret_cast<uintptr_t>(grid->workspace) % 256 != 0)
+        return fail(AT_ERR_ARG, "workspace must be 256-byte aligned");
+
+    int dev = 0, sms = 0, coop = 0, smem_optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (!coop) return fail(AT_ERR_RESIDENCY, "device does not support cooperative launch");
+
+    // subdomain and instance records
+    std::vector<atk::BatchSub> sub((size_t)d.P);
+    std::vector<atk::BatchInst> ins((size_t)n_inst);
+    int64_t p0 = 0;
+    for (int64_t j = 0; j < n_inst; ++j) {
+        const at_instance &a = inst[j];
+        const double dx = a.length / (double)a.n;
+        const int64_t Pi = a.n / M;
+        atk::BatchInst &bi = ins[(size_t)j];
+        bi = atk::BatchInst{};
+        bi.x0 = a.origin; bi.dx = dx; bi.dt = a.dt; bi.nu = a.nu;
+        bi.ta = a.tanh_a; bi.tc = a.tanh_c; bi.txc = a.tanh_xc;
+        const bool periodic = a.bc == AT_BC_PERIODIC;
+        for (int64_t lp = 0; lp < Pi; ++lp) {
+            atk::BatchSub &b = sub[(size_t)(p0 + lp)];
+            b = atk::BatchSub{};
+            if (scheme_order == 2) {
+                b.cA = a.dt / (2.0 * dx);
+                b.cB = a.nu * a.dt / (dx * dx);
+            } else {
+                b.cA = a.dt / (12.0 * dx);
+                b.cB = a.nu * a.dt / (12.0 * dx * dx);
+            }
+            b.seed = a.seed;
+            b.L = a.L;
+            b.lp = (int)lp;
+            b.Pi = (int)Pi;
+            b.inst = (int)j;
+            b.left = lp > 0 ? p0 + lp - 1 : (periodic ? p0 + Pi - 1 : -1);
+            b.right = lp < Pi - 1 ? p0 + lp + 1 : (periodic ? p0 : -1);
+        }
+        p0 += Pi;
+    }
+    unsigned char *ws = static_cast<unsigned char *>(grid->workspace);
+    cudaStream_t st = static_cast<cudaStream_t>(grid->stream);
+    e = cudaMemcpyAsync(ws + lay.bsub, sub.data(), sub.size() * sizeof(atk::BatchSub), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(ws + lay.binst, ins.data(), ins.size() * sizeof(atk::BatchInst), cudaMemcpyHostToDevice,
+                            st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "copying the ensemble tables");
+
+    at_solver *h = new (std::nothrow) at_solver();
+    if (!h) return fail(AT_ERR_ARG, "out of host memory");
+    h->g = *grid;
+    if (h->g.timeout_ns <= 0) h->g.timeout_ns = 1000000000ll;
+    h->N = d.N; h->P = d.P; h->M = M;
+    h->order = scheme_order; h->L = d.Lmax; h->R = scheme_order / 2; h->s = s; h->T = T; h->w = w;
+    h->nu = 0; h->dt = 0; h->dx = 0;
+    h->lay = lay;
+    h->ws = ws;
+    h->stream = st;
+    h->device = dev; h->sm_count = sms; h->smem_optin = smem_optin;
+    h->batch = true; h->n_inst = n_inst; h->lmin = d.Lmin;
+    const int gw = groups_per_lane(M);
+    const bool full = (M == 128LL * gw);
+    h->kernel = w == 8 ? atk_batch_kernel_f64(scheme_order, gw, full) : atk_batch_kernel_f32(scheme_order, gw, full);
+    h->init_kernel = w == 8 ? atk_init_kernel_f64(scheme_order) : atk_init_kernel_f32(scheme_order);
+    int stages = grid->stages > 0 ? grid->stages : 3;
+    if (stages < atk::kMinStages) stages = atk::kMinStages;
+    rc = launch_shape(M, w, d.P, tab_size(M, w, false, true), grid->max_ctas, stages, sms, smem_optin, h->kernel,
+                      &h->G, &h->stages, &h->sl, &h->smem, &h->smax);
+    if (rc != AT_OK) { delete h; return rc; }
+    h->sb = grid->steps_per_pass > 0 ? grid->steps_per_pass : 1;
+    h->step = 0;
+    h->has_state = false;
+    *out = h;
+    return AT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Autotuner
+// ---------------------------------------------------------------------------
+int at_tune(at_solver *h, int64_t n_steps, int delay_mode, at_tune_result *res)
+{
+    g_err[0] = 0;
+    if (!h || !res) return fail(AT_ERR_ARG, "NULL argument");
+    if (!h->has_state) return fail(AT_ERR_STATE, "at_tune before at_set_state");
+    if (n_steps <= 0) return fail(AT_ERR_ARG, "n_steps must be positive");
+    if (delay_mode != AT_SYNC && delay_mode != AT_SEEDED && delay_mode != AT_FREE)
+        return fail(AT_ERR_ARG, "at_tune times AT_SYNC, AT_SEEDED or AT_FREE");
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(h->stream, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone)
+        return fail(AT_ERR_STATE, "at_tune under stream capture");
+    std::memset(res, 0, sizeof(*res));
+    const TabSize tsz = tab_size(h->M, h->w, h->g.forcing_amp != 0.0, h->batch);
+    const int gmax = (int)((h->P + atk::kWarps - 1) / atk::kWarps);
+
+    cudaEvent_t ev[3];
+    for (int i = 0; i < 3; ++i) {
+        const cudaError_t e = cudaEventCreate(&ev[i]);
+        if (e != cudaSuccess) {
+            for (int k = 0; k < i; ++k) cudaEventDestroy(ev[k]);
+            return cuda_fail(e, "cudaEventCreate");
+        }
+    }
+    struct Shape {
+        int G, stages, sb;
+    };
+    auto apply = [&](const Shape &sh) -> int {
+        int G = 0, st = 0, smem = 0;
+        long long smax = 0;
+        atk::SmemLayout sl{};
+        const int r = launch_shape(h->M, h->w, h->P, tsz, sh.G, sh.stages, h->sm_count, h->smem_optin, h->kernel,
+                                   &G, &st, &sl, &smem, &smax);
+        if (r != AT_OK) return r;
+        if (st != sh.stages) return AT_ERR_RESIDENCY;   // did not fit as asked
+        h->G = G; h->stages = st; h->sl = sl; h->smem = smem; h->smax = smax; h->sb = sh.sb;
+        return AT_OK;
+    };
+    // time of one at_step(n_steps): one untimed launch, best of two timed
+    auto time_shape = [&](double *ms) -> int {
+        int r = at_step(h, n_steps, delay_mode, nullptr);
+        if (r != AT_OK) return r;
+        double best = 1e300;
+        for (int rep = 0; rep < 2; ++rep) {
+            cudaEventRecord(ev[0], h->stream);
+            r = at_step(h, n_steps, delay_mode, nullptr);
+            if (r != AT_OK) return r;
+            cudaEventRecord(ev[1], h->stream);
+            const cudaError_t e = cudaEventSynchronize(ev[1]);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaEventSynchronize");
+            float t = 0.f;
+            cudaEventElapsedTime(&t, ev[0], ev[1]);
+            if (t < best) best = t;
+        }
+        r = read_status(h);
+        if (r != AT_OK) return r;
+        *ms = best;
+        return AT_OK;
+    };
+
+    const Shape orig{h->G, h->stages, h->sb};
+    Shape best = orig;
+    double best_ms = 0.0;
+    int rc = time_shape(&best_ms);
+    int tried = 1;
+    res->first_ms = best_ms;
+    // levels per pass: up to the largest delay bound + 1 (an ensemble's PEs
+    // clamp it to their own smallest bound + 1)
+    const int sb_hi = delay_mode == AT_FREE ? h->L + 1 : 1;
+    for (int st = atk::kMinStages; rc == AT_OK && st <= 4; ++st) {
+        int lastG = -1;
+        for (int per_sm = 1; rc == AT_OK && per_sm <= 4; ++per_sm) {
+            const int G = per_sm * h->sm_count < gmax ? per_sm * h->sm_count : gmax;
+            if (G == lastG) break;
+            lastG = G;
+            for (int sb = 1; rc == AT_OK && sb <= sb_hi; ++sb) {
+                const Shape sh{G, st, sb};
+                if (sh.G == orig.G && sh.stages == orig.stages && sh.sb == orig.sb) continue;
+                if (apply(sh) != AT_OK) { g_err[0] = 0; continue; }   // not resident: skip
+                double ms = 0.0;
+                rc = time_shape(&ms);
+                ++tried;
+                if (rc == AT_OK && ms < best_ms) { best_ms = ms; best = sh; }
+            }
+        }
+    }
+    for (int i = 0; i < 3; ++i) cudaEventDestroy(ev[i]);
+    const int rc_apply = apply(rc == AT_OK ? best : orig);
+    if (rc != AT_OK) return rc;
+    if (rc_apply != AT_OK) return rc_apply;
+    res->ctas = h->G;
+    res->stages = h->stages;
+    res->steps_per_pass = h->sb;
+    res->n_tried = tried;
+    res->best_ms = best_ms;
     return AT_OK;
 }
 
@@ -512,12 +850,13 @@ extern "C" int at_step_noalloc(const at_grid *grid, int64_t P, int scheme_order,
     h.lay = lay;
     h.ws = scratch;
     h.stream = static_cast<cudaStream_t>(grid->stream);
-    h.device = dev; h.sm_count = sms;
+    h.device = dev; h.sm_count = sms; h.smem_optin = smem_optin;
+    h.batch = false; h.n_inst = 0; h.lmin = L;
     pick_kernels(w, scheme_order, h.M, grid->forcing_amp != 0.0, &h.kernel, &h.init_kernel);
     int stages = grid->stages > 0 ? grid->stages : 3;
     if (stages < atk::kMinStages) stages = atk::kMinStages;
-    rc = launch_shape(h.M, w, P, grid->forcing_amp != 0.0, grid->max_ctas, stages, sms, smem_optin, h.kernel,
-                      &h.G, &h.stages, &h.sl, &h.smem, &h.smax);
+    rc = launch_shape(h.M, w, P, tab_size(h.M, w, grid->forcing_amp != 0.0, false), grid->max_ctas, stages, sms,
+                      smem_optin, h.kernel, &h.G, &h.stages, &h.sl, &h.smem, &h.smax);
     if (rc != AT_OK) return rc;
     h.sb = 1;
 
@@ -534,12 +873,10 @@ extern "C" int at_step_noalloc(const at_grid *grid, int64_t P, int scheme_order,
     if (n_steps > 0) {
         p.mode = delay_mode;
         p.delays = delays;
-        p.n0 = 0;
         p.n_steps = n_steps;
-        p.gbar_base = 0;
-        p.n_passes = count_passes(0, n_steps, s, 1);
-        e = cudaLaunchCooperativeKernel(h.kernel, dim3(h.G), dim3(atk::kThreads), args, (size_t)h.smem, h.stream);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaLaunchCooperativeKernel(at_stepper)");
+        p.sb = 1;
+        e = launch_stepper(&h, &p);
+        if (e != cudaSuccess) return cuda_fail(e, "cooperative launch of at_stepper");
     }
     return read_status(&h);
 }

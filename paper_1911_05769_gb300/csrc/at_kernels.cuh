@@ -55,24 +55,29 @@ constexpr int kMaxL = 16;
 constexpr int kMinStages = 2;                     // stages per PE (tile in use + one ahead)
 
 enum : int { kModeSync = 0, kModeSeeded = 1, kModeFree = 2, kModeReplay = 3 };
+// Control block words.  kCtrlN0 (64-bit, words 8-9) is the time level of the
+// state: every launch reads it at its start and the last CTA to finish
+// advances it, so that a launch replayed from a captured graph continues
+// where the previous one stopped.  kCtrlDone counts finished CTAs.
 enum : int {
     kCtrlStatus = 0, kCtrlAbort = 1, kCtrlCta = 2, kCtrlWhere = 3, kCtrlNb = 4, kCtrlStep = 5,
-    kCtrlWords = 16
+    kCtrlN0 = 8, kCtrlDone = 10, kCtrlWords = 16
 };
 enum : int { kWhereTile = 1, kWhereRing = 2, kWhereFlag = 3, kWhereGrid = 4 };
 constexpr int kStatusTimeout = -5;
 
 // Shared-memory layout of one CTA, shared by the host (launch set-up) and the
 // kernel: per PE `stages` mbarriers, delay counters, two raw-level buffers and
-// `stages` tile buffers; then the forcing tables (sin/cos of the offsets in a
-// subdomain, and of each PE's subdomain origins).
+// `stages` tile buffers; then a table of `tab_bytes`: the forcing tables
+// (sin/cos of the offsets in a subdomain, and of each PE's subdomain origins)
+// or, for an ensemble, each PE's subdomain records.
 struct SmemLayout {
     long long bar_off, hist_off, raw_off, stage_off, stage_bytes, tab_off, total;
 };
 
 __host__ __device__ inline long long round_up(long long x, long long a) { return (x + a - 1) / a * a; }
 
-__host__ __device__ inline SmemLayout smem_layout(long long M, int word, int stages, long long tab_words)
+__host__ __device__ inline SmemLayout smem_layout(long long M, int word, int stages, long long tab_bytes)
 {
     SmemLayout l;
     l.bar_off = 0;
@@ -81,9 +86,31 @@ __host__ __device__ inline SmemLayout smem_layout(long long M, int word, int sta
     l.stage_off = round_up(l.raw_off + 2LL * kWarps * kRawBytes, 128);
     l.stage_bytes = round_up(M * word, 128);
     l.tab_off = l.stage_off + (long long)kWarps * stages * l.stage_bytes;
-    l.total = l.tab_off + tab_words * word;
+    l.total = l.tab_off + tab_bytes;
     return l;
 }
+
+// Ensembles: independent 1D problems of M-point subdomains laid end to end.
+// One record per subdomain (built on the host, copied to shared memory by the
+// PE that owns it) and one per problem instance.
+struct BatchSub {
+    double cA, cB;             // stencil factors of the instance (as Params::cA, cB)
+    unsigned long long seed;   // AT_SEEDED seed of the instance
+    int L;                     // delay bound of the instance
+    int lp;                    // index of the subdomain within its instance
+    int Pi;                    // subdomains of the instance
+    int inst;                  // instance
+    long long left, right;     // global subdomain across face 0 / 1; -1 = exact boundary
+    long long pad_;
+};
+static_assert(sizeof(BatchSub) == 64, "BatchSub is four 16-byte vectors");
+
+struct BatchInst {
+    double x0, dx, dt, nu;     // grid x_i = x0 + i dx of the instance, time step, viscosity
+    double ta, tc, txc;        // exact boundary values u = c - a tanh(a (x - xc - c t) / (2 nu))
+    double pad_;
+};
+static_assert(sizeof(BatchInst) == 64, "BatchInst is 64 bytes");
 
 struct Params {
     void *u;                   // state, N words, updated in place
@@ -93,11 +120,12 @@ struct Params {
     unsigned long long *hist;  // [L+1] delay counts
     unsigned long long *gbar;  // grid-barrier arrival counter (AT_SYNC)
     int8_t *delays;            // [n_steps][P][2] replay input / record output
+    const BatchSub *bsub;      // ensembles: [P] subdomain records (else NULL)
+    const BatchInst *binst;    // ensembles: instance records (else NULL)
     long long N, P, M;
-    int L, T, mode, per_sub;
-    long long n0, n_steps;
-    long long n_passes;        // passes over each PE's subdomains in this launch
-    int sb;                    // levels per pass (temporal blocking, free mode)
+    int L, T, mode, per_sub;   // L: largest delay bound (ensembles: of any instance)
+    long long n_steps;
+    int sb;                    // most levels per pass (temporal blocking, free mode)
     unsigned long long seed;
     double cA, cB, dtA;        // dt/(2dx) | dt/(12dx);  nu dt/dx^2 | nu dt/(12dx^2);  dt A
     double x0, dx;
@@ -107,7 +135,6 @@ struct Params {
     long long smax;            // most subdomains of any PE
     long long bar_off, hist_off, raw_off, stage_off, stage_bytes, tab_off;
     long long timeout_ns;
-    unsigned long long gbar_base;
     int skip_publish;          // test knob: PE 0 stops releasing flags
     long long skip_step;
 };
@@ -273,7 +300,7 @@ static __device__ __noinline__ bool cta_grid_sync(const Params &p, int *s_count,
         if ((long long)old + 1 == step * kWarps) {
             __threadfence();
             atomicAdd(p.gbar, 1ull);
-            if (wait) ok = wait_grid(p, p.gbar_base + (unsigned long long)step * (unsigned long long)p.G, step);
+            if (wait) ok = wait_grid(p, (unsigned long long)step * (unsigned long long)p.G, step);
             st_release_cta_shared(s_epoch, ok ? step : -1);
         } else if (wait) {
             const unsigned long long t0 = global_ns();
@@ -288,29 +315,60 @@ static __device__ __noinline__ bool cta_grid_sync(const Params &p, int *s_count,
     return __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
 }
 
+// The levels one launch advances a PE through: n0 .. n0 + n_steps, in passes
+// of one level while the level is below s-1, then of sb levels (the last one
+// shorter).  sb may differ between PEs (in an ensemble each PE takes the
+// smallest delay bound of its subdomains): a PE's halo waits only need its
+// neighbours' per-level flags, whatever their pass boundaries.
+struct Sweep {
+    long long n0, n_steps;
+    int sb;
+};
+
 // Position of a tile in a PE's sweep: pass start level n, subdomain j and
-// the pass length (one level while n < s-1, then up to sb levels; the same
-// rule in every PE, so all agree on the pass boundaries).
+// the pass length.
 struct Cursor {
     long long n, j;
     int len;
 };
 
-__device__ __forceinline__ int pass_len(const Params &p, long long n, int s_lev)
+__device__ __forceinline__ int pass_len(const Sweep &sw, long long n, int s_lev)
 {
-    const long long left = p.n0 + p.n_steps - n;
-    int len = (int)(left < p.sb ? left : p.sb);
+    const long long left = sw.n0 + sw.n_steps - n;
+    int len = (int)(left < sw.sb ? left : sw.sb);
     if (n < s_lev - 1) len = 1;
     return len;
 }
 
-__device__ __forceinline__ void advance(const Params &p, Cursor &c, long long lo, long long hi, int s_lev)
+__device__ __forceinline__ long long count_passes(const Sweep &sw, int s_lev)
+{
+    long long single = (s_lev - 1) - sw.n0;
+    if (single < 0) single = 0;
+    if (single > sw.n_steps) single = sw.n_steps;
+    const long long rest = sw.n_steps - single;
+    return single + (rest + sw.sb - 1) / sw.sb;
+}
+
+__device__ __forceinline__ void advance(const Sweep &sw, Cursor &c, long long lo, long long hi, int s_lev)
 {
     if (++c.j == hi) {
         c.j = lo;
         c.n += c.len;
-        c.len = pass_len(p, c.n, s_lev);
+        c.len = pass_len(sw, c.n, s_lev);
     }
+}
+
+// Exact boundary value of an ensemble instance (travelling tanh wave) at
+// point `q` of the halo across face f of subdomain record b, at level lev.
+template <typename T, int R>
+static __device__ __noinline__ T exact_ghost(const BatchInst *binst, const BatchSub &b, long long M, int f, int q,
+                                             long long lev)
+{
+    const BatchInst &bi = binst[b.inst];
+    const long long gi = f ? ((long long)b.lp + 1) * M + q : (long long)b.lp * M - R + q;
+    const double x = bi.x0 + (double)gi * bi.dx;
+    const double t = (double)lev * bi.dt;
+    return (T)(bi.tc - bi.ta * tanh(bi.ta * (x - bi.txc - bi.tc * t) / (2.0 * bi.nu)));
 }
 
 // ---------------------------------------------------------------------------
@@ -322,10 +380,16 @@ __device__ __forceinline__ void advance(const Params &p, Cursor &c, long long lo
 // same m; for lane 0, lane 31 at m-1), the right neighbours the first R words
 // of group g+1 (lane l+1, same m; for lane 31, lane 0 at m+1): one shuffle
 // per word, no barrier.  Groups 0 and NG-1 take the approximated halo instead.
-template <typename T, int ORDER, int GW, bool FORCED, bool FULL>
-__device__ void run_pe(const Params &p, long long lo, long long hi, uint64_t *bars, unsigned *hist,
+//
+// In an ensemble (BATCH) the stencil factors, delay bound and seed come from
+// the subdomain's record in shared memory (btab[j - lo]); a face whose record
+// names no neighbour takes the instance's exact boundary values, undelayed;
+// a face whose neighbour is another PE's, or not the next subdomain in the
+// sweep (a periodic instance's wrap-around), goes through the flags.
+template <typename T, int ORDER, int GW, bool FORCED, bool FULL, bool BATCH>
+__device__ void run_pe(const Params &p, const Sweep &sw, long long lo, long long hi, uint64_t *bars, unsigned *hist,
                        unsigned char *raw, unsigned char *stages, const T *sj, const T *cj, const T *spt,
-                       const T *cpt, int *s_count, volatile long long *s_epoch)
+                       const T *cpt, const BatchSub *btab, int *s_count, volatile long long *s_epoch)
 {
     constexpr int R = ORDER / 2;
     constexpr int S_LEV = ORDER / 2 + 1;
@@ -342,19 +406,19 @@ __device__ void run_pe(const Params &p, long long lo, long long hi, uint64_t *ba
     }
     const int NS = p.stages;
     const int D = (int)((S - 1) < (NS - 1) ? (S - 1) : (NS - 1));   // tiles loaded ahead
-    const long long Q = p.n_passes * S;
+    const long long Q = count_passes(sw, S_LEV) * S;
     const int NG = (int)(p.M / 4);
     // owner of group NG-1 (compile-time when the tile is a multiple of 128 points)
     const int m_last = FULL ? GW - 1 : (NG - 1) >> 5;
     const int lane_last = FULL ? 31 : (NG - 1) & 31;
-    const T cA = (T)p.cA, cB = (T)p.cB;
+    const T cA0 = (T)p.cA, cB0 = (T)p.cB;
     const size_t tile_bytes = (size_t)p.M * sizeof(T);
     const size_t slot_stride = (size_t)p.P * 2 * kRingEntry;
     const int up = (lane + 31) & 31, down = (lane + 1) & 31;
     const bool edge_pub = !(p.skip_publish && blockIdx.x == 0 && threadIdx.x < 32);
     unsigned *my_hist = hist + (lane & 1) * (kMaxL + 1);
 
-    Cursor L{p.n0, lo, pass_len(p, p.n0, S_LEV)};   // next tile to load
+    Cursor L{sw.n0, lo, pass_len(sw, sw.n0, S_LEV)};   // next tile to load
     Cursor H = L;                                     // next tile whose halo is prepared
     Cursor C = L;                                     // tile being processed
 
@@ -385,11 +449,17 @@ __device__ void run_pe(const Params &p, long long lo, long long hi, uint64_t *ba
             while (jj < lo) { jj += S; --nn; }
             while (jj >= hi) { jj -= S; ++nn; }
             int k = 0;
-            if (t0 + (lane >> 1) < Q && nn >= p.n0 && nn < p.n0 + p.n_steps) {
-                if (p.mode == kModeSeeded)
-                    k = seeded_delay(p.seed, nn, jj, p.P, p.per_sub ? 0 : (lane & 1), p.L);
-                else if (p.mode == kModeReplay)
-                    k = p.delays[((nn - p.n0) * p.P + jj) * 2 + (lane & 1)];
+            if (t0 + (lane >> 1) < Q && nn >= sw.n0 && nn < sw.n0 + sw.n_steps) {
+                if (p.mode == kModeSeeded) {
+                    if constexpr (BATCH) {
+                        const BatchSub &b = btab[jj - lo];
+                        k = seeded_delay(b.seed, nn, b.lp, b.Pi, p.per_sub ? 0 : (lane & 1), b.L);
+                    } else {
+                        k = seeded_delay(p.seed, nn, jj, p.P, p.per_sub ? 0 : (lane & 1), p.L);
+                    }
+                } else if (p.mode == kModeReplay) {
+                    k = p.delays[((nn - sw.n0) * p.P + jj) * 2 + (lane & 1)];
+                }
             }
             kb = k;
             kb_t0 = t0;
@@ -405,17 +475,28 @@ __device__ void run_pe(const Params &p, long long lo, long long hi, uint64_t *ba
         // phase 1: choose the delay and check (or wait for) the neighbour
         int state = 1;
         long long k = 0, q = 0;
+        bool bnd = false;              // exact boundary face (ensembles)
         if (lane < 2) {
             const int f = lane;
             const long long n = c.n;
             const int len = c.len;
-            q = (f == 0) ? (c.j == 0 ? p.P - 1 : c.j - 1) : (c.j == p.P - 1 ? 0 : c.j + 1);
-            const bool edge = (f == 0) ? (c.j == lo) : (c.j == hi - 1);
+            bool edge;
+            int Lj = p.L;
+            if constexpr (BATCH) {
+                const BatchSub &b = btab[c.j - lo];
+                q = f ? b.right : b.left;
+                bnd = q < 0;
+                edge = !bnd && (q < lo || q >= hi || q != c.j + (f ? 1 : -1));
+                Lj = b.L;
+            } else {
+                q = (f == 0) ? (c.j == 0 ? p.P - 1 : c.j - 1) : (c.j == p.P - 1 ? 0 : c.j + 1);
+                edge = (f == 0) ? (c.j == lo) : (c.j == hi - 1);
+            }
             // largest delay at the start of the pass such that the last inner
             // step stays within L, and no level below 0 is ever read
             long long kmax = n - S_LEV + 1;
             if (kmax < 0) kmax = 0;
-            if (kmax > p.L - (len - 1)) kmax = p.L - (len - 1);
+            if (kmax > Lj - (len - 1)) kmax = Lj - (len - 1);
             k = kr;
             if (k > kmax) k = kmax;
             if (k < 0) k = 0;
@@ -443,11 +524,11 @@ __device__ void run_pe(const Params &p, long long lo, long long hi, uint64_t *ba
             for (int i = 0; i < c.len; ++i) {
                 my_hist[k + i] += 1u;
                 if (p.delays && p.mode != kModeReplay)
-                    p.delays[((c.n - p.n0 + i) * p.P + c.j) * 2 + f] = (int8_t)(k + i);
+                    p.delays[((c.n - sw.n0 + i) * p.P + c.j) * 2 + f] = (int8_t)(k + i);
             }
             hk = (int)k;
-            const unsigned char *rbase = p.ring + ((size_t)q * 2 + (1 - f)) * kRingEntry;
-            const int levels = (k == 0 && c.len == 1) ? 1 : S_LEV;
+            const unsigned char *rbase = p.ring + ((size_t)(bnd ? 0 : q) * 2 + (1 - f)) * kRingEntry;
+            const int levels = bnd ? 0 : (k == 0 && c.len == 1) ? 1 : S_LEV;
             for (int m = 0; m < levels; ++m) {
                 const long long lv = c.n - k - m;
                 cp_async16(raw + (size_t)buf * kRawBytes + (f * kMaxS + m) * kRingEntry,
@@ -459,7 +540,7 @@ __device__ void run_pe(const Params &p, long long lo, long long hi, uint64_t *ba
 
     // --- prologue -------------------------------------------------------------
     long long tl = 0;                  // next tile index to load
-    for (; tl < D && tl < Q; ++tl) { issue_load(tl, L); advance(p, L, lo, hi, S_LEV); }
+    for (; tl < D && tl < Q; ++tl) { issue_load(tl, L); advance(sw, L, lo, hi, S_LEV); }
     bool ok = true;
     bool pending = true;               // the halo of tile 0 is prepared in the loop
     int k0cur = 0, k1cur = 0;
@@ -468,10 +549,10 @@ __device__ void run_pe(const Params &p, long long lo, long long hi, uint64_t *ba
         // state copy of tile r + D (stage of tile r - 1, complete: in order)
         if (tl < Q && tl <= r + D) {
             issue_load(tl, L);
-            advance(p, L, lo, hi, S_LEV);
+            advance(sw, L, lo, hi, S_LEV);
             ++tl;
         }
-        const long long step = C.n - p.n0;
+        const long long step = C.n - sw.n0;
         // synchronous algorithm: before the first tile of a step, all PEs
         // have finished the previous step (grid barrier, Algorithm 1)
         if (p.mode == kModeSync && step > 0 && C.j == lo) {
@@ -482,7 +563,7 @@ __device__ void run_pe(const Params &p, long long lo, long long hi, uint64_t *ba
         if (pending) {
             if (prep_halo(r, C, buf, true) < 0) { ok = false; break; }
             H = C;
-            advance(p, H, lo, hi, S_LEV);
+            advance(sw, H, lo, hi, S_LEV);
         }
         if (lane < 2) cp_async_wait_all();
         k0cur = __shfl_sync(kAll, hk, 0);
@@ -500,7 +581,7 @@ __device__ void run_pe(const Params &p, long long lo, long long hi, uint64_t *ba
                 if (st < 0) { ok = false; break; }
                 if (st > 0) {
                     pending = false;
-                    advance(p, H, lo, hi, S_LEV);
+                    advance(sw, H, lo, hi, S_LEV);
                 }
             }
         }
@@ -516,6 +597,15 @@ __device__ void run_pe(const Params &p, long long lo, long long hi, uint64_t *ba
         const long long j = C.j, n = C.n;
         const int len = C.len;
         T *ug = reinterpret_cast<T *>(p.u) + (size_t)j * p.M;
+        T cA = cA0, cB = cB0;
+        bool bnd0 = false, bnd1 = false;
+        if constexpr (BATCH) {
+            const BatchSub &b = btab[j - lo];
+            cA = (T)b.cA;
+            cB = (T)b.cB;
+            bnd0 = b.left < 0;
+            bnd1 = b.right < 0;
+        }
 
         T c[GW][4];
 #pragma unroll
@@ -538,7 +628,10 @@ __device__ void run_pe(const Params &p, long long lo, long long hi, uint64_t *ba
         T hv = (T)0;
         if (hv_lanes && lane < 2 * R * len) {
             const int f = lane / (R * len), rem = lane % (R * len);
-            hv = approx_halo<T, S_LEV>(rw + f * kMaxS * kRingEntry, (f ? k1cur : k0cur) + rem / R, rem % R);
+            if (BATCH && (f ? bnd1 : bnd0))
+                hv = exact_ghost<T, R>(p.binst, btab[j - lo], p.M, f, rem % R, n + rem / R);
+            else
+                hv = approx_halo<T, S_LEV>(rw + f * kMaxS * kRingEntry, (f ? k1cur : k0cur) + rem / R, rem % R);
         }
         for (int i = 0; i < len; ++i) {
             const long long lev = n + i + 1;                 // level being computed
@@ -549,8 +642,10 @@ __device__ void run_pe(const Params &p, long long lo, long long hi, uint64_t *ba
                     hl[q] = __shfl_sync(kAll, hv, i * R + q);
                     hr[q] = __shfl_sync(kAll, hv, R * len + i * R + q);
                 } else {
-                    hl[q] = approx_halo<T, S_LEV>(rw, k0cur + i, q);
-                    hr[q] = approx_halo<T, S_LEV>(rw + kMaxS * kRingEntry, k1cur + i, q);
+                    hl[q] = (BATCH && bnd0) ? exact_ghost<T, R>(p.binst, btab[j - lo], p.M, 0, q, n + i)
+                                            : approx_halo<T, S_LEV>(rw, k0cur + i, q);
+                    hr[q] = (BATCH && bnd1) ? exact_ghost<T, R>(p.binst, btab[j - lo], p.M, 1, q, n + i)
+                                            : approx_halo<T, S_LEV>(rw + kMaxS * kRingEntry, k1cur + i, q);
                 }
             }
             T tail[R], rb[R];                                // old last words of group m-1; new last words of NG-1
@@ -612,7 +707,14 @@ __device__ void run_pe(const Params &p, long long lo, long long hi, uint64_t *ba
                 for (int f = f_lo; f <= f_hi; ++f) {
                     st_entry<T, R>(e0 + f * kRingEntry, f ? rb : c[0]);
                     if (p.mode == kModeSync) __threadfence();
-                    if ((f ? j == hi - 1 : j == lo) && pub_ok) st_release(p.flag + j * 2 + f, (unsigned long long)lev);
+                    bool rel;              // the consumer across face f waits on this flag
+                    if constexpr (BATCH) {
+                        const long long qf = f ? btab[j - lo].right : btab[j - lo].left;
+                        rel = qf >= 0 && (qf < lo || qf >= hi || qf != j + (f ? 1 : -1));
+                    } else {
+                        rel = f ? j == hi - 1 : j == lo;
+                    }
+                    if (rel && pub_ok) st_release(p.flag + j * 2 + f, (unsigned long long)lev);
                 }
             }
         }
@@ -625,7 +727,7 @@ __device__ void run_pe(const Params &p, long long lo, long long hi, uint64_t *ba
         // lane 0 after the warp barrier
         fence_proxy_async_global();
         __syncwarp();
-        advance(p, C, lo, hi, S_LEV);
+        advance(sw, C, lo, hi, S_LEV);
     }
     // synchronous algorithm: the last step's arrival at the grid barrier
     if (ok && p.mode == kModeSync) cta_grid_sync(p, s_count, s_epoch, p.n_steps, false);
@@ -649,7 +751,7 @@ __device__ void run_pe(const Params &p, long long lo, long long hi, uint64_t *ba
 // ---------------------------------------------------------------------------
 // the persistent kernel
 // ---------------------------------------------------------------------------
-template <typename T, int ORDER, int GW, bool FORCED, bool FULL>
+template <typename T, int ORDER, int GW, bool FORCED, bool FULL, bool BATCH>
 __global__ void __launch_bounds__(kThreads, AT_MIN_CTAS_PER_SM) at_stepper(const Params p)
 {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -665,6 +767,9 @@ __global__ void __launch_bounds__(kThreads, AT_MIN_CTAS_PER_SM) at_stepper(const
     T *tab = reinterpret_cast<T *>(smem + p.tab_off);
     T *sj = tab, *cj = tab + p.M;
     T *spt = tab + 2 * p.M + (size_t)w * 2 * p.smax, *cpt = spt + p.smax;
+    BatchSub *btab = reinterpret_cast<BatchSub *>(smem + p.tab_off) + (size_t)w * p.smax;
+    // time level of the state, advanced at the end of the previous launch
+    Sweep sw{*reinterpret_cast<const volatile long long *>(p.ctrl + kCtrlN0), p.n_steps, p.sb};
 
     __shared__ int s_count;                   // grid-barrier arrivals of this CTA's warps
     __shared__ long long s_epoch;             // last grid barrier this CTA passed
@@ -690,8 +795,34 @@ __global__ void __launch_bounds__(kThreads, AT_MIN_CTAS_PER_SM) at_stepper(const
             cpt[i] = (T)cv;
         }
     }
+    if constexpr (BATCH) {
+        // this PE's subdomain records; passes no longer than the smallest
+        // delay bound among them allows (k0 + len - 1 <= L)
+        const uint4 *src = reinterpret_cast<const uint4 *>(p.bsub + lo);
+        uint4 *dst = reinterpret_cast<uint4 *>(btab);
+        constexpr int kVec = (int)(sizeof(BatchSub) / sizeof(uint4));
+        for (long long i = lane; i < S * kVec; i += 32) dst[i] = src[i];
+        int lmin = kMaxL;
+        for (long long i = lane; i < S; i += 32) lmin = min(lmin, p.bsub[lo + i].L);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) lmin = min(lmin, __shfl_xor_sync(0xffffffffu, lmin, o));
+        if (sw.sb > lmin + 1) sw.sb = lmin + 1;
+    }
     __syncthreads();
-    run_pe<T, ORDER, GW, FORCED, FULL>(p, lo, hi, bars, hist, raw, stages, sj, cj, spt, cpt, &s_count, &s_epoch);
+    run_pe<T, ORDER, GW, FORCED, FULL, BATCH>(p, sw, lo, hi, bars, hist, raw, stages, sj, cj, spt, cpt, btab,
+                                              &s_count, &s_epoch);
+    // the last CTA to finish advances the level of the state and rearms the
+    // grid barrier for the next launch (every CTA has read the level by now)
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(p.ctrl + kCtrlDone, 1) == p.G - 1) {
+            *reinterpret_cast<volatile long long *>(p.ctrl + kCtrlN0) = sw.n0 + p.n_steps;
+            *reinterpret_cast<volatile int *>(p.ctrl + kCtrlDone) = 0;
+            *reinterpret_cast<volatile unsigned long long *>(p.gbar) = 0ull;
+            __threadfence();
+        }
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -714,6 +845,46 @@ __global__ void at_init(const Params p)
         if (threadIdx.x < kCtrlWords) p.ctrl[threadIdx.x] = 0;
         if (threadIdx.x <= p.L) p.hist[threadIdx.x] = 0ull;
         if (threadIdx.x == 0) *p.gbar = 0ull;
+    }
+}
+
+}  // namespace atk
+
+// ---------------------------------------------------------------------------
+// kernel selection (each translation unit instantiates one word size and
+// either the single-domain or the ensemble kernels)
+// ---------------------------------------------------------------------------
+namespace atk {
+
+template <typename T, int ORDER, bool FORCED, bool FULL, bool BATCH>
+void *stepper_gw(int gw)
+{
+    switch (gw) {
+    case 1: return (void *)at_stepper<T, ORDER, 1, FORCED, FULL, BATCH>;
+    case 2: return (void *)at_stepper<T, ORDER, 2, FORCED, FULL, BATCH>;
+    case 4: return (void *)at_stepper<T, ORDER, 4, FORCED, FULL, BATCH>;
+    default: return (void *)at_stepper<T, ORDER, 8, FORCED, FULL, BATCH>;
+    }
+}
+
+template <typename T, int ORDER, bool FORCED, bool BATCH>
+void *stepper_full(int gw, bool full)
+{
+    return full ? stepper_gw<T, ORDER, FORCED, true, BATCH>(gw) : stepper_gw<T, ORDER, FORCED, false, BATCH>(gw);
+}
+
+// Stepper for stencil order 2|4, gw groups of 4 points per lane (1, 2, 4 or
+// 8), with or without forcing (single domain only), full tiles (M = 128 gw)
+// or not.
+template <typename T, bool BATCH>
+void *stepper_kernel(int order, int gw, bool forced, bool full)
+{
+    if constexpr (BATCH) {
+        return order == 2 ? stepper_full<T, 2, false, true>(gw, full) : stepper_full<T, 4, false, true>(gw, full);
+    } else {
+        if (order == 2)
+            return forced ? stepper_full<T, 2, true, false>(gw, full) : stepper_full<T, 2, false, false>(gw, full);
+        return forced ? stepper_full<T, 4, true, false>(gw, full) : stepper_full<T, 4, false, false>(gw, full);
     }
 }
 

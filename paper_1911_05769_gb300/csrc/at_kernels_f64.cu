@@ -1,36 +1,13 @@
 // at_kernels_f64.cu -- instantiations of the persistent AT stepper for double state
-// (one translation unit per word size, so the two build in parallel).
+// (one translation unit per word size and kind, so they build in parallel).
 // FP64 tiles need more registers per thread: two CTAs per SM
 #define AT_MIN_CTAS_PER_SM 2
 #include "at_kernels.cuh"
 
-namespace {
-
-template <int ORDER, bool FORCED, bool FULL>
-void *stepper_for(int gw)
-{
-    switch (gw) {
-    case 1: return (void *)atk::at_stepper<double, ORDER, 1, FORCED, FULL>;
-    case 2: return (void *)atk::at_stepper<double, ORDER, 2, FORCED, FULL>;
-    case 4: return (void *)atk::at_stepper<double, ORDER, 4, FORCED, FULL>;
-    default: return (void *)atk::at_stepper<double, ORDER, 8, FORCED, FULL>;
-    }
-}
-
-template <int ORDER, bool FORCED>
-void *stepper_for(int gw, bool full)
-{
-    return full ? stepper_for<ORDER, FORCED, true>(gw) : stepper_for<ORDER, FORCED, false>(gw);
-}
-
-}  // namespace
-
-// Stepper kernel for stencil order 2|4, gw groups of 4 points per lane
-// (1, 2, 4 or 8), with or without forcing, and full tiles (M = 128 gw) or not.
+// Single-domain stepper kernel (see atk::stepper_kernel).
 __attribute__((visibility("hidden"))) void *atk_stepper_kernel_f64(int order, int gw, bool forced, bool full)
 {
-    if (order == 2) return forced ? stepper_for<2, true>(gw, full) : stepper_for<2, false>(gw, full);
-    return forced ? stepper_for<4, true>(gw, full) : stepper_for<4, false>(gw, full);
+    return atk::stepper_kernel<double, false>(order, gw, forced, full);
 }
 
 // State (re)initialisation kernel for stencil order 2|4.

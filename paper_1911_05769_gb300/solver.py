@@ -54,6 +54,14 @@ class Solver:
         self.h = h
         self.N, self.P, self.order, self.L = N, P, order, L
 
+    def tune(self, n_steps, mode=B.AT_FREE):
+        """Runs the launch-shape autotuner (at_tune) and returns its result.
+        The state advances while shapes are timed: set it again afterwards."""
+        rc, res = B.at_tune(self.h, n_steps, mode)
+        if rc != B.AT_OK:
+            raise B.AtError(rc, "at_tune")
+        return res
+
     def info(self):
         rc, info = B.at_get_info(self.h)
         if rc != B.AT_OK:
@@ -118,3 +126,62 @@ class Solver:
         if u.numel() != self.N:
             raise ValueError(f"state needs {self.N} values, got {u.numel()}")
         return u
+
+
+class EnsembleSolver(Solver):
+    """Many independent 1D problems of M-point subdomains in one persistent launch.
+
+    ``instances`` is a sequence of dicts with keys n, L, nu, dt and optionally
+    bc (default AT_BC_EXACT_TANH), length (2 pi), origin (-pi), tanh_a,
+    tanh_c, tanh_xc, seed.  The state is the concatenation of the instances'
+    fields; step/state/delay_stats work as for ``Solver`` over all P = N / M
+    subdomains.
+    """
+
+    def __init__(self, instances, M, order, *, dtype="f32", flags=0, timeout_ns=0, max_ctas=0, stages=0,
+                 steps_per_pass=0, stream=None, device=None):
+        import torch
+        self.torch = torch
+        dev = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        self.device = dev
+        self.stream = stream if stream is not None else torch.cuda.current_stream(dev)
+        self.tdtype = torch.float64 if dtype == "f64" else torch.float32
+        arr = (B.at_instance * len(instances))()
+        for a, d in zip(arr, instances):
+            a.n, a.L = int(d["n"]), int(d["L"])
+            a.bc = int(d.get("bc", B.AT_BC_EXACT_TANH))
+            a.length = float(d.get("length", 2 * math.pi))
+            a.origin = float(d.get("origin", -math.pi))
+            a.nu, a.dt = float(d["nu"]), float(d["dt"])
+            a.tanh_a = float(d.get("tanh_a", 0.0))
+            a.tanh_c = float(d.get("tanh_c", 0.0))
+            a.tanh_xc = float(d.get("tanh_xc", 0.0))
+            a.seed = int(d.get("seed", 0)) & (2 ** 64 - 1)
+        g = B.at_grid()
+        g.dim = 1
+        g.dtype = B.AT_F64 if dtype == "f64" else B.AT_F32
+        g.flags = flags
+        g.timeout_ns = timeout_ns
+        g.max_ctas = max_ctas
+        g.stages = stages
+        g.steps_per_pass = steps_per_pass
+        nbytes = B.at_batch_workspace_bytes(g, arr, M, order)
+        if nbytes == 0:
+            raise B.AtError(B.AT_ERR_ARG, "at_batch_workspace_bytes")
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+        g.workspace = self.workspace.data_ptr()
+        g.workspace_bytes = nbytes
+        g.stream = self.stream.cuda_stream
+        self.grid = g
+        self.instances = arr
+        rc, h = B.at_create_batch(g, arr, M, order)
+        if rc != B.AT_OK:
+            raise B.AtError(rc, "at_create_batch")
+        self.h = h
+        self.N = sum(int(d["n"]) for d in instances)
+        self.P = self.N // M
+        self.order = order
+        self.L = max(int(d["L"]) for d in instances)
+        self.offsets = [0]
+        for d in instances:
+            self.offsets.append(self.offsets[-1] + int(d["n"]))

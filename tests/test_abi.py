@@ -30,7 +30,8 @@ def _declared_functions():
 def test_header_declares_the_abi():
     names = _declared_functions()
     for must in ("at_create", "at_step", "at_state", "at_destroy", "at_set_state", "at_workspace_bytes",
-                 "at_status", "at_delay_stats", "at_get_info", "at_last_error"):
+                 "at_status", "at_delay_stats", "at_get_info", "at_last_error", "at_create_batch",
+                 "at_batch_workspace_bytes", "at_tune"):
         assert must in names
 
 
@@ -61,6 +62,13 @@ int main(void) {
   F(at_info, N); F(at_info, P); F(at_info, M); F(at_info, order); F(at_info, L); F(at_info, R); F(at_info, s);
   F(at_info, T); F(at_info, ctas); F(at_info, threads); F(at_info, stages); F(at_info, smem_bytes);
   F(at_info, step); F(at_info, sm_count); F(at_info, dtype); F(at_info, steps_per_pass);
+  printf("at_instance size %zu\n", sizeof(at_instance));
+  F(at_instance, n); F(at_instance, L); F(at_instance, bc); F(at_instance, length); F(at_instance, origin);
+  F(at_instance, nu); F(at_instance, dt); F(at_instance, tanh_a); F(at_instance, tanh_c); F(at_instance, tanh_xc);
+  F(at_instance, seed);
+  printf("at_tune_result size %zu\n", sizeof(at_tune_result));
+  F(at_tune_result, ctas); F(at_tune_result, stages); F(at_tune_result, steps_per_pass);
+  F(at_tune_result, n_tried); F(at_tune_result, best_ms); F(at_tune_result, first_ms);
   return 0;
 }
 """
@@ -131,3 +139,41 @@ def test_product_path_has_no_cpu_fallback():
         if name.endswith(".py"):
             text = open(os.path.join(src_dir, name)).read()
             assert "import oracle" not in text and "from oracle" not in text, name
+
+
+def _instances(B, specs):
+    arr = (B.at_instance * len(specs))()
+    for a, (n, L, nu, dt) in zip(arr, specs):
+        a.n, a.L, a.bc = n, L, B.AT_BC_EXACT_TANH
+        a.length, a.origin, a.nu, a.dt = 6.283185307179586, -3.141592653589793, nu, dt
+        a.tanh_a, a.tanh_c = 0.1, 0.2
+    return arr
+
+
+def test_batch_workspace_bytes_and_validation(B):
+    g = B.at_grid()
+    g.dim, g.dtype = 1, B.AT_F32
+    ok = _instances(B, [(1024, 1, 0.01, 1e-5), (512, 3, 0.02, 1e-5)])
+    nb = B.at_batch_workspace_bytes(g, ok, 256, 2)
+    P = (1024 + 512) // 256
+    # state + ring (T = 16 for L = 3, s = 2) + flags + subdomain and instance records
+    assert nb >= 1536 * 4 + 16 * P * 2 * 16 + P * 2 * 8 + P * 64 + 2 * 64
+    assert nb % 256 == 0
+    assert B.at_batch_workspace_bytes(g, _instances(B, [(1000, 1, 0.01, 1e-5)]), 256, 2) == 0
+    assert "multiple of M" in B.at_last_error()
+    assert B.at_batch_workspace_bytes(g, _instances(B, [(1024, 17, 0.01, 1e-5)]), 256, 2) == 0
+    assert B.at_batch_workspace_bytes(g, _instances(B, [(1024, 1, 0.0, 1e-5)]), 256, 2) == 0
+    assert "nu > 0" in B.at_last_error()
+    assert B.at_batch_workspace_bytes(g, ok, 258, 2) == 0
+    assert B.at_batch_workspace_bytes(g, ok, 256, 3) == 0
+    # nu dt / dx^2 = 0.01 * 1e-2 / (2 pi / 1024)^2 > 1/2
+    assert B.at_batch_workspace_bytes(g, _instances(B, [(1024, 1, 0.01, 1e-2)]), 256, 2) == 0
+    assert "exceeds" in B.at_last_error()
+    g.steps_per_pass = 5                                  # above max L + 1 = 4
+    assert B.at_batch_workspace_bytes(g, ok, 256, 2) == 0
+    g.steps_per_pass = 0
+    g.forcing_amp = 0.1
+    assert B.at_batch_workspace_bytes(g, ok, 256, 2) == 0 and "unforced" in B.at_last_error()
+    g.forcing_amp = 0.0
+    rc, h = B.at_create_batch(g, ok, 256, 2)              # no workspace
+    assert rc == B.AT_ERR_ARG and not h.value

@@ -63,6 +63,8 @@ def parse():
     ap.add_argument("--order", type=int, default=0, help="stencil order for experiments (default 4)")
     ap.add_argument("--forcing", type=float, default=-1.0, help="forcing amplitude for experiments (default 0.1)")
     ap.add_argument("--ensemble-only", action="store_true", help="time only the 2048-instance ensemble leg")
+    ap.add_argument("--ens-time-steps", type=int, default=5000, help="time steps per ensemble launch")
+    ap.add_argument("--no-tune", action="store_true", help="ensemble leg: keep the default launch shape")
     return ap.parse_args()
 
 
@@ -212,7 +214,7 @@ def small_config(args, at, torch, dev, stream):
     return res
 
 
-def ensemble_config(args, at, torch, dev, stream, time_steps=5000):
+def ensemble_config(args, at, torch, dev, stream):
     """The 2048-instance travelling-wave ensemble (N_j log-uniform in
     [2^10, 2^16], M = 256, order 2, L_j in {1, 2, 3}, FP32): one persistent
     launch of 5000 steps captured in a CUDA graph and replayed, launch shape
@@ -220,6 +222,7 @@ def ensemble_config(args, at, torch, dev, stream, time_steps=5000):
     way; the FP32 result's error against the FP64 oracle on sampled instances."""
     inst = W.ensemble()
     M, order = 256, 2
+    time_steps = args.ens_time_steps
     Ntot = sum(d["n"] for d in inst)
     u0 = torch.from_numpy(W.ensemble_field(inst)).to(device=dev, dtype=torch.float32)
     res = {"workload": "burgers1d_ensemble_2048", "instances": len(inst), "N": Ntot, "P": Ntot // M, "M": M,
@@ -232,7 +235,7 @@ def ensemble_config(args, at, torch, dev, stream, time_steps=5000):
                               steps_per_pass=Lmax + 1 if mode == at.AT_FREE else 0)
         with torch.cuda.stream(stream):
             s.set_state(u0)
-        t = s.tune(200, mode)
+        t = None if args.no_tune else s.tune(200, mode)
         with torch.cuda.stream(stream):
             s.set_state(u0)
         torch.cuda.synchronize(dev)
@@ -257,9 +260,9 @@ def ensemble_config(args, at, torch, dev, stream, time_steps=5000):
         s.close()
         del g
         return {"value": Ntot * time_steps / (ms * 1e-3) / 1e9, "unit": UNIT, "ms_per_launch": ms,
-                "tuned": {"ctas": t.ctas, "stages": t.stages, "steps_per_pass": t.steps_per_pass,
-                          "shapes_tried": t.n_tried, "ms_200_steps_first": t.first_ms,
-                          "ms_200_steps_best": t.best_ms}}
+                "shape": {"ctas": info.ctas, "stages": info.stages, "steps_per_pass": info.steps_per_pass},
+                "tuned": None if t is None else {
+                    "shapes_tried": t.n_tried, "ms_200_steps_first": t.first_ms, "ms_200_steps_best": t.best_ms}}
 
     res["free"] = run(at.AT_FREE, "free")
     res["sync"] = run(at.AT_SYNC, "sync")

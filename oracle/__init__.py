@@ -83,6 +83,10 @@ def lib():
             L.at_oracle_run.restype = ctypes.c_int
             L.at_oracle_run.argtypes = [ctypes.POINTER(Cfg), ctypes.c_int64, ctypes.c_void_p,
                                         ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+            L.at_oracle_adjoint.restype = ctypes.c_int
+            L.at_oracle_adjoint.argtypes = [ctypes.POINTER(Cfg), ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
+                                            ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                            ctypes.POINTER(ctypes.c_double)]
             L.at_oracle_cfg_size.restype = ctypes.c_int64
             if L.at_oracle_cfg_size() != ctypes.sizeof(Cfg):
                 raise RuntimeError("oracle: configuration struct layout mismatch")
@@ -162,3 +166,37 @@ def run(u0, *, N=None, P, order, L, nu, dt, n_steps, x0=0.0, dx=None, length=2 *
     if rc != 0:
         raise ValueError(f"oracle run failed: rc={rc}")
     return (out, hist, kk) if want_k else (out, hist)
+
+
+def adjoint(u0, lam_T, *, N=None, P, order, L, nu, dt, n_steps, x0=0.0, dx=None, length=2 * np.pi,
+            forcing_amp=0.0, delay_mode=SYNC, seed=0, replay=None, per_subdomain=False, at_weights=True):
+    """Discrete adjoint of ``run`` (Burgers, whole periodic domain).
+
+    Returns ``(u_T, lam_0, dnu)``: the run's final level, dJ/du^0 and dJ/dnu
+    for a J whose gradient with respect to u^{n_steps} is ``lam_T``.
+    """
+    u0 = np.ascontiguousarray(u0, dtype=np.float64)
+    lam_T = np.ascontiguousarray(lam_T, dtype=np.float64)
+    if N is None:
+        N = u0.size
+    if dx is None:
+        dx = length / N
+    c = Cfg(N=N, P=P, p_lo=0, p_count=P, order=order, L=L, nu=nu, dt=dt, x0=x0, dx=dx,
+            forcing_amp=forcing_amp, eq=EQ_BURGERS, bc=BC_PERIODIC, adv_c=0.0, tanh_a=0.0, tanh_c=0.0,
+            tanh_xc=0.0, delay_mode=delay_mode, per_subdomain=int(per_subdomain), at_weights=int(at_weights),
+            pad_=0, seed=seed & (2**64 - 1))
+    if u0.size != N or lam_T.size != N:
+        raise ValueError("oracle adjoint: u0 and lam_T need N values")
+    rep = None
+    if delay_mode == REPLAY:
+        rep = np.ascontiguousarray(replay, dtype=np.int8)
+        if rep.size != n_steps * P * 2:
+            raise ValueError("oracle adjoint: replay array has the wrong size")
+    u_T = np.empty(N, dtype=np.float64)
+    lam_0 = np.empty(N, dtype=np.float64)
+    dnu = ctypes.c_double()
+    rc = lib().at_oracle_adjoint(ctypes.byref(c), n_steps, _dptr(rep), _dptr(u0), _dptr(lam_T), _dptr(u_T),
+                                 _dptr(lam_0), ctypes.byref(dnu))
+    if rc != 0:
+        raise ValueError(f"oracle adjoint failed: rc={rc}")
+    return u_T, lam_0, dnu.value

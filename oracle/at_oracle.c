@@ -262,3 +262,144 @@ int at_oracle_run(const at_oracle_cfg *c, int64_t n_steps, const int8_t *replay,
 
 /* Size of the configuration struct, so the caller can check its layout. */
 int64_t at_oracle_cfg_size(void) { return (int64_t)sizeof(at_oracle_cfg); }
+
+/* ------------------------------------------------------------------------ */
+/* Discrete adjoint of the method (reverse-mode differentiation of the run  */
+/* above, for Burgers' equation on the whole periodic domain).              */
+/*                                                                          */
+/* The run maps (u^0, nu) to u^{n_steps}.  For a scalar J that depends on   */
+/* the run only through u^{n_steps}, given lam_T = dJ/du^{n_steps} this      */
+/* returns lam_0 = dJ/du^0 and dJ/dnu.  It stores every level, then walks    */
+/* the levels backwards.  Each update                                       */
+/*     u^{n+1}_i = u^n_i + dt (-v_0 D1(v) + nu D2(v) + F(x_i))              */
+/* (Sec. 3.2, Eq. BS) reads stencil values v_j, each a stored value: the    */
+/* point itself or a neighbour at level n, or across a subdomain face the   */
+/* extrapolation sum_m w_m(k) f^{n-k-m} of Eq. AT1/AT2 over delayed levels.  */
+/* The derivative of the update with respect to v_j,                         */
+/*     dt (-v_0 dD1/dv_j + nu dD2/dv_j) - dt D1 [j = 0],                     */
+/* times lam^{n+1}_i, is added to the adjoint of every stored value v_j is   */
+/* made of (weight w_m(k) for a delayed level); the identity term adds      */
+/* lam^{n+1}_i to lam^n_i; dJ/dnu collects dt D2(v) lam^{n+1}_i.             */
+/* Contributions reach levels n, n-1, ..., so lam^n is complete once every  */
+/* update above level n has been processed.                                  */
+/* ------------------------------------------------------------------------ */
+
+/* Coefficients of D1 (times dx) and D2 (times dx^2) at offsets -R..R. */
+static void deriv_coeffs(int order, double *a1, double *a2)
+{
+    if (order == 2) {
+        a1[0] = -0.5; a1[1] = 0.0; a1[2] = 0.5;
+        a2[0] = 1.0; a2[1] = -2.0; a2[2] = 1.0;
+    } else {
+        a1[0] = 1.0 / 12.0; a1[1] = -8.0 / 12.0; a1[2] = 0.0; a1[3] = 8.0 / 12.0; a1[4] = -1.0 / 12.0;
+        a2[0] = -1.0 / 12.0; a2[1] = 16.0 / 12.0; a2[2] = -30.0 / 12.0; a2[3] = 16.0 / 12.0; a2[4] = -1.0 / 12.0;
+    }
+}
+
+/* Stencil value j (offset -R..R) of point il at level n, as a combination of
+ * stored values: levels lv[q], indices ix[q], weights wt[q], q < *cnt. */
+static void stencil_sources(const at_oracle_cfg *c, int64_t M, int R, int s, int64_t n, int64_t il,
+                            const int k[2], int j, int64_t *lv, int64_t *ix, double *wt, int *cnt)
+{
+    const int64_t m = il % M;
+    const int64_t mj = m + j;
+    *cnt = 0;
+    if (mj >= 0 && mj < M) {
+        lv[0] = n; ix[0] = il + j; wt[0] = 1.0; *cnt = 1;
+        return;
+    }
+    const int f = (mj < 0) ? 0 : 1;
+    const int64_t src = wrap(il + j, c->N);
+    double w[8];
+    at_oracle_weights(s, k[f], c->at_weights, w);
+    (void)R;
+    for (int q = 0; q < s; ++q) {
+        if (w[q] == 0.0) continue;
+        lv[*cnt] = n - k[f] - q; ix[*cnt] = src; wt[*cnt] = w[q]; ++*cnt;
+    }
+}
+
+int at_oracle_adjoint(const at_oracle_cfg *c, int64_t n_steps, const int8_t *replay, const double *u0,
+                      const double *lam_T, double *u_T, double *lam_0, double *dnu)
+{
+    if (!c || c->N <= 0 || c->P <= 0 || c->N % c->P != 0) return ORC_EARG;
+    if (c->order != 2 && c->order != 4) return ORC_EARG;
+    if (c->L < 0 || c->L > 64 || n_steps < 0) return ORC_EARG;
+    if (c->eq != 0 || c->bc != 0 || c->p_lo != 0 || c->p_count != c->P) return ORC_EARG;
+    const int64_t N = c->N, M = c->N / c->P;
+    const int R = c->order / 2, s = c->order / 2 + 1;
+    if (M < 2 * R) return ORC_EARG;
+    const size_t lvls = (size_t)n_steps + 1;
+    double *U = (double *)malloc(lvls * (size_t)N * sizeof(double));
+    double *G = (double *)calloc(lvls * (size_t)N, sizeof(double));
+    int8_t *K = (int8_t *)malloc(((size_t)n_steps * (size_t)c->P * 2 + 1) * sizeof(int8_t));
+    if (!U || !G || !K) { free(U); free(G); free(K); return ORC_ENOMEM; }
+    double a1[5], a2[5], v[5], wt[3];
+    int64_t lv[3], ix[3];
+    int cnt;
+    deriv_coeffs(c->order, a1, a2);
+
+    /* forward: every level, every delay */
+    memcpy(U, u0, (size_t)N * sizeof(double));
+    for (int64_t n = 0; n < n_steps; ++n) {
+        for (int64_t p = 0; p < c->P; ++p) {
+            for (int f = 0; f < 2; ++f) {
+                int kr = 0;
+                if (c->delay_mode == 1)
+                    kr = at_oracle_seeded_delay(c->seed, n, p, c->P, c->per_subdomain ? 0 : f, 2, c->L);
+                else if (c->delay_mode == 2)
+                    kr = replay[((size_t)n * c->P + p) * 2 + f];
+                if (kr < 0 || kr > c->L) { free(U); free(G); free(K); return ORC_EDELAY; }
+                int64_t kmax = n - s + 1; if (kmax < 0) kmax = 0;
+                K[((size_t)n * c->P + p) * 2 + f] = (int8_t)((kr < kmax) ? kr : kmax);
+            }
+        }
+        for (int64_t i = 0; i < N; ++i) {
+            const int64_t p = i / M;
+            const int k[2] = {K[((size_t)n * c->P + p) * 2], K[((size_t)n * c->P + p) * 2 + 1]};
+            for (int j = -R; j <= R; ++j) {
+                stencil_sources(c, M, R, s, n, i, k, j, lv, ix, wt, &cnt);
+                double acc = 0.0;
+                for (int q = 0; q < cnt; ++q) acc += wt[q] * U[(size_t)lv[q] * N + ix[q]];
+                v[j + R] = acc;
+            }
+            double d1, d2;
+            at_oracle_derivs(c->order, v, c->dx, &d1, &d2);
+            double rhs = -v[R] * d1 + c->nu * d2;
+            if (c->forcing_amp != 0.0) rhs += c->forcing_amp * sin(c->x0 + (double)i * c->dx);
+            U[(size_t)(n + 1) * N + i] = U[(size_t)n * N + i] + c->dt * rhs;
+        }
+    }
+    if (u_T) memcpy(u_T, U + (size_t)n_steps * N, (size_t)N * sizeof(double));
+
+    /* backward */
+    memcpy(G + (size_t)n_steps * N, lam_T, (size_t)N * sizeof(double));
+    double gnu = 0.0;
+    for (int64_t n = n_steps - 1; n >= 0; --n) {
+        for (int64_t i = 0; i < N; ++i) {
+            const double g = G[(size_t)(n + 1) * N + i];
+            const int64_t p = i / M;
+            const int k[2] = {K[((size_t)n * c->P + p) * 2], K[((size_t)n * c->P + p) * 2 + 1]};
+            for (int j = -R; j <= R; ++j) {
+                stencil_sources(c, M, R, s, n, i, k, j, lv, ix, wt, &cnt);
+                double acc = 0.0;
+                for (int q = 0; q < cnt; ++q) acc += wt[q] * U[(size_t)lv[q] * N + ix[q]];
+                v[j + R] = acc;
+            }
+            double d1, d2;
+            at_oracle_derivs(c->order, v, c->dx, &d1, &d2);
+            G[(size_t)n * N + i] += g;                       /* u^n_i itself */
+            gnu += g * c->dt * d2;
+            for (int j = -R; j <= R; ++j) {
+                double dv = c->dt * (-v[R] * a1[j + R] / c->dx + c->nu * a2[j + R] / (c->dx * c->dx));
+                if (j == 0) dv -= c->dt * d1;
+                stencil_sources(c, M, R, s, n, i, k, j, lv, ix, wt, &cnt);
+                for (int q = 0; q < cnt; ++q) G[(size_t)lv[q] * N + ix[q]] += g * dv * wt[q];
+            }
+        }
+    }
+    memcpy(lam_0, G, (size_t)N * sizeof(double));
+    if (dnu) *dnu = gnu;
+    free(U); free(G); free(K);
+    return ORC_OK;
+}

@@ -22,6 +22,8 @@ Workloads (1D viscous Burgers on the periodic interval [0, 2 pi)):
   with c_j ~ U[-0.5, 0.5], a_j = min(0.5, 0.5 nu_j / dx_j) (a front at least
   4 dx wide), xc = 0; seed 6.
 
+* ``burgers1d_adjoint_n2p20``: see ``adjoint_workload``.
+
 The paper's own runs (3D Burgers' turbulence from a multi-scale sinusoidal
 initial condition, Sec. 3.1) use no dataset; these fields stand in for them.
 """
@@ -141,6 +143,25 @@ def instance_field(inst: dict) -> np.ndarray:
 def ensemble_field(instances: list) -> np.ndarray:
     """Initial state of an ensemble: the instances' fields at t = 0, end to end."""
     return np.concatenate([instance_field(d) for d in instances])
+
+
+def adjoint_workload(N: int = 1 << 20, M: int = 1024) -> dict:
+    """The adjoint workload ``burgers1d_adjoint_n2p20``: N = 2^20 points in
+    subdomains of M = 1024 (P = 1024), order 2, L = 2, nu = 0.01, seeded
+    delays (seed 7), 2000 steps, checkpoints every 100; u0 = sin x +
+    0.5 sin(3x + 1); the target is the run (same delays) from u0 + 0.01 q
+    with viscosity 1.05 nu, q an 8-mode field with seeded amplitudes and
+    phases (seed 7), normalised to max |q| = 1.  Loss ||u(T) - u_target||^2."""
+    x, dx = grid(N)
+    u0 = u0_two_modes(N)
+    rng = np.random.default_rng(7)
+    amp = rng.uniform(0.5, 1.0, size=8)
+    phi = rng.uniform(0.0, TWO_PI, size=8)
+    q = sum(amp[k] * np.sin((k + 1) * x + phi[k]) for k in range(8))
+    q /= np.max(np.abs(q))
+    nu = 0.01
+    return dict(name="burgers1d_adjoint_n2p20", N=N, P=N // M, order=2, L=2, nu=nu, seed=7, n_steps=2000,
+                interval=100, u0=u0, u0_target=u0 + 0.01 * q, nu_target=1.05 * nu, dt=dt_rule(u0, dx, nu))
 
 
 def random_delays(n_steps: int, P: int, L: int, seed: int, faces: int = 2) -> np.ndarray:

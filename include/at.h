@@ -246,6 +246,59 @@ typedef struct at_tune_result {
  * Returns AT_OK, or the first error (then the handle keeps its shape). */
 int at_tune(at_solver *h, int64_t n_steps, int delay_mode, at_tune_result *res);
 
+/* ---------------------------------------------------------------------------
+ * Levels, restarts and the discrete adjoint (single-domain solvers).
+ *
+ * The paper's method maps (u^0, nu) to u^n; these calls give the gradient of
+ * a scalar J(u^{n_steps}) with respect to u^0 and nu by reverse-mode
+ * differentiation of exactly that discrete map (forward Euler, Sec. 3.2;
+ * central stencils; AT halos of Eq. AT1/AT2 with the run's delays): checkpoints
+ * every `interval` levels on the forward run, each interval recomputed from its
+ * checkpoint on the way back.  The paper has no adjoint; this is an extension.
+ * --------------------------------------------------------------------------- */
+
+/* as at_step, and also writes every level l it computes (n0+1 .. n0+n_steps)
+ * into levels + (l mod depth) * N words (device memory).  Passes are one level
+ * long in every mode. */
+int at_step_levels(at_solver *h, int64_t n_steps, int delay_mode, int8_t *delays, void *levels, int64_t depth);
+
+/* Restarts the solver at time level `level` from stored full fields: levels
+ * + (l mod depth) * N words must hold level l for l = max(0, level-L-s+1) ..
+ * level (s = 2 for order 2, 3 for order 4: the oldest level the next step's
+ * halos read).  Sets the state, the ring buffers and every progress flag;
+ * clears the device status.  Stream-ordered. */
+int at_set_history(at_solver *h, const void *levels, int64_t depth, int64_t level);
+
+/* Bytes of checkpoint storage for n_steps in intervals of `interval`:
+ * ceil(n_steps / interval) checkpoints of L + s levels, N words each. */
+size_t at_checkpoint_bytes(const at_solver *h, int64_t n_steps, int64_t interval);
+
+/* Forward run from level 0 (right after at_set_state) by n_steps, keeping in
+ * ckpt (device memory, at_checkpoint_bytes) the levels c-L-s+1 .. c of every
+ * c = 0, interval, 2 interval, ...  delays as in at_step (AT_FREE: pass an
+ * array to record the delays, which the adjoint then replays); passes are one
+ * level long except in the last interval. */
+int at_step_checkpointed(at_solver *h, int64_t n_steps, int delay_mode, int8_t *delays, int64_t interval,
+                         void *ckpt);
+
+/* Bytes of the adjoint's scratch workspace (device memory, 256-byte aligned):
+ * interval + L + s levels, one adjoint field, the pending adjoint of delayed
+ * boundary reads and per-block FP64 sums. */
+size_t at_adjoint_workspace_bytes(const at_solver *h, int64_t interval);
+
+/* Discrete adjoint of the run made by at_step_checkpointed(h, n_steps, ...):
+ *   lam (device, N words of the state's dtype): dJ/du^{n_steps} on entry,
+ *       dJ/du^0 on return;
+ *   *dnu: dJ/dnu, accumulated in FP64;
+ *   delay_mode AT_SYNC, AT_SEEDED or AT_REPLAY with the forward run's delays
+ *       (AT_FREE runs: the recorded array and AT_REPLAY).
+ * Each interval is recomputed from its checkpoint with at_step_levels, then
+ * one adjoint kernel launch per level takes lambda^{n+1} to lambda^n.
+ * Leaves the solver's state at an intermediate level: set it again before
+ * stepping.  Synchronises and returns the device status. */
+int at_adjoint(at_solver *h, int64_t n_steps, int delay_mode, const int8_t *delays, int64_t interval,
+               const void *ckpt, void *adj_ws, size_t adj_ws_bytes, void *lam, double *dnu);
+
 /* Size in bytes of the fixed scratch array used by at_step_noalloc(). */
 #define AT_NOALLOC_SCRATCH_BYTES (8u * 1024u * 1024u)
 

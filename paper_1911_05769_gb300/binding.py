@@ -105,6 +105,16 @@ _SIGNATURES = [
      [ctypes.POINTER(at_grid), ctypes.c_int64, ctypes.POINTER(at_instance), ctypes.c_int64, ctypes.c_int,
       ctypes.POINTER(ctypes.c_void_p)]),
     ("at_tune", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.POINTER(at_tune_result)]),
+    ("at_step_levels", ctypes.c_int,
+     [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64]),
+    ("at_set_history", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64]),
+    ("at_checkpoint_bytes", ctypes.c_size_t, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64]),
+    ("at_step_checkpointed", ctypes.c_int,
+     [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]),
+    ("at_adjoint_workspace_bytes", ctypes.c_size_t, [ctypes.c_void_p, ctypes.c_int64]),
+    ("at_adjoint", ctypes.c_int,
+     [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+      ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
 ]
 
 EXPORTED = [s[0] for s in _SIGNATURES]
@@ -208,6 +218,39 @@ def at_tune(h, n_steps: int, delay_mode: int):
     res = at_tune_result()
     rc = lib().at_tune(h, n_steps, delay_mode, ctypes.byref(res))
     return rc, res
+
+
+def _vp(ptr):
+    return ctypes.c_void_p(ptr) if ptr else None
+
+
+def at_step_levels(h, n_steps: int, delay_mode: int, delays_ptr, levels_ptr: int, depth: int) -> int:
+    return lib().at_step_levels(h, n_steps, delay_mode, _vp(delays_ptr), _vp(levels_ptr), depth)
+
+
+def at_set_history(h, levels_ptr: int, depth: int, level: int) -> int:
+    return lib().at_set_history(h, _vp(levels_ptr), depth, level)
+
+
+def at_checkpoint_bytes(h, n_steps: int, interval: int) -> int:
+    return int(lib().at_checkpoint_bytes(h, n_steps, interval))
+
+
+def at_step_checkpointed(h, n_steps: int, delay_mode: int, delays_ptr, interval: int, ckpt_ptr: int) -> int:
+    return lib().at_step_checkpointed(h, n_steps, delay_mode, _vp(delays_ptr), interval, _vp(ckpt_ptr))
+
+
+def at_adjoint_workspace_bytes(h, interval: int) -> int:
+    return int(lib().at_adjoint_workspace_bytes(h, interval))
+
+
+def at_adjoint(h, n_steps: int, delay_mode: int, delays_ptr, interval: int, ckpt_ptr: int, ws_ptr: int,
+               ws_bytes: int, lam_ptr: int):
+    """Returns (code, dJ/dnu); lam_ptr holds dJ/du(T) on entry and dJ/du0 on return."""
+    dnu = ctypes.c_double()
+    rc = lib().at_adjoint(h, n_steps, delay_mode, _vp(delays_ptr), interval, _vp(ckpt_ptr), _vp(ws_ptr), ws_bytes,
+                          _vp(lam_ptr), ctypes.byref(dnu))
+    return rc, dnu.value
 
 
 def at_last_error() -> str:

@@ -15,6 +15,7 @@
 #include <vector>
 
 #include "at.h"
+#include "at_adjoint.cuh"
 #include "at_kernels.cuh"
 
 void *atk_stepper_kernel_f32(int order, int gw, bool forced, bool full);
@@ -23,6 +24,9 @@ void *atk_init_kernel_f32(int order);
 void *atk_init_kernel_f64(int order);
 void *atk_batch_kernel_f32(int order, int gw, bool full);
 void *atk_batch_kernel_f64(int order, int gw, bool full);
+void *atk_restore_kernel_f32(int order);
+void *atk_restore_kernel_f64(int order);
+void *atk_adjoint_kernel(int w, int order);
 
 namespace {
 
@@ -391,9 +395,8 @@ int at_set_state(at_solver *h, const void *u)
     return AT_OK;
 }
 
-int at_step(at_solver *h, int64_t n_steps, int delay_mode, int8_t *delays)
+static int step_impl(at_solver *h, int64_t n_steps, int delay_mode, int8_t *delays, void *levels, int64_t depth)
 {
-    g_err[0] = 0;
     if (!h) return fail(AT_ERR_ARG, "NULL handle");
     if (!h->has_state) return fail(AT_ERR_STATE, "at_step before at_set_state");
     if (n_steps < 0) return fail(AT_ERR_ARG, "n_steps < 0");
@@ -404,10 +407,53 @@ int at_step(at_solver *h, int64_t n_steps, int delay_mode, int8_t *delays)
     p.mode = delay_mode;
     p.delays = delays;
     p.n_steps = n_steps;
-    p.sb = delay_mode == AT_FREE ? h->sb : 1;
+    p.sb = (delay_mode == AT_FREE && !levels) ? h->sb : 1;
+    p.levels = levels;
+    p.levels_depth = depth;
     const cudaError_t e = launch_stepper(h, &p);
     if (e != cudaSuccess) return cuda_fail(e, "cooperative launch of at_stepper");
     h->step += n_steps;
+    return AT_OK;
+}
+
+int at_step(at_solver *h, int64_t n_steps, int delay_mode, int8_t *delays)
+{
+    g_err[0] = 0;
+    return step_impl(h, n_steps, delay_mode, delays, nullptr, 0);
+}
+
+int at_step_levels(at_solver *h, int64_t n_steps, int delay_mode, int8_t *delays, void *levels, int64_t depth)
+{
+    g_err[0] = 0;
+    if (!levels || depth < 1) return fail(AT_ERR_ARG, "at_step_levels needs a levels array and depth >= 1");
+    return step_impl(h, n_steps, delay_mode, delays, levels, depth);
+}
+
+int at_set_history(at_solver *h, const void *levels, int64_t depth, int64_t level)
+{
+    g_err[0] = 0;
+    if (!h || !levels) return fail(AT_ERR_ARG, "NULL argument");
+    if (level < 0) return fail(AT_ERR_ARG, "level < 0");
+    const int64_t need = level + 1 < h->L + h->s ? level + 1 : h->L + h->s;
+    if (depth < need) return fail(AT_ERR_ARG, "depth %lld holds fewer than the %lld levels needed", (long long)depth,
+                                  (long long)need);
+    const unsigned char *lv = static_cast<const unsigned char *>(levels);
+    cudaError_t e = cudaMemcpyAsync(h->ws + h->lay.u, lv + (size_t)(level % depth) * h->N * h->w, (size_t)h->N * h->w,
+                                    cudaMemcpyDeviceToDevice, h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(level)");
+    atk::Params p = make_params(h);
+    const long long lo = level - need + 1;
+    void *kern = h->w == 8 ? atk_restore_kernel_f64(h->order) : atk_restore_kernel_f32(h->order);
+    const void *lv_ptr = levels;
+    long long depth_ll = depth, lo_ll = lo, level_ll = level;
+    void *args[] = {&p, (void *)&lv_ptr, &depth_ll, &lo_ll, &level_ll};
+    const long long work = h->P * need;
+    const int blocks = (int)((work + 255) / 256 < 1024 ? (work + 255) / 256 : 1024);
+    e = cudaLaunchKernel(kern, dim3(blocks), dim3(256), args, 0, h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "launch at_restore");
+    h->step = level;
+    h->flags_E = 0;
+    h->has_state = true;
     return AT_OK;
 }
 
@@ -755,6 +801,181 @@ int at_tune(at_solver *h, int64_t n_steps, int delay_mode, at_tune_result *res)
     res->steps_per_pass = h->sb;
     res->n_tried = tried;
     res->best_ms = best_ms;
+    return AT_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Checkpointed forward run and the discrete adjoint
+// ---------------------------------------------------------------------------
+namespace {
+
+// levels kept per checkpoint: the level itself and the L + s - 1 before it
+// (the oldest level the next step's halos read)
+int64_t ckpt_levels(const at_solver *h) { return h->L + h->s; }
+
+int64_t n_segments(int64_t n_steps, int64_t interval) { return n_steps <= 0 ? 1 : (n_steps + interval - 1) / interval; }
+
+int adj_blocks(const at_solver *h)
+{
+    const int64_t b = (h->N + 255) / 256;
+    return (int)(b < 8LL * h->sm_count ? b : 8LL * h->sm_count);
+}
+
+struct AdjLayout {
+    size_t levels, lam, pend, dnu, total;
+};
+
+AdjLayout adj_layout(const at_solver *h, int64_t interval)
+{
+    AdjLayout l{};
+    size_t off = 0;
+    l.levels = off; off = align_up(off + (size_t)(interval + ckpt_levels(h)) * h->N * h->w, 256);
+    l.lam = off;    off = align_up(off + (size_t)h->N * h->w, 256);
+    l.pend = off;   off = align_up(off + (size_t)h->T * h->P * 2 * h->R * h->w, 256);
+    l.dnu = off;    off = align_up(off + (size_t)adj_blocks(h) * 8, 256);
+    l.total = off;
+    return l;
+}
+
+int check_adjoint_args(const at_solver *h, int64_t n_steps, int64_t interval)
+{
+    if (!h) return fail(AT_ERR_ARG, "NULL handle");
+    if (h->batch) return fail(AT_ERR_ARG, "the adjoint covers single-domain solvers");
+    if (n_steps < 0) return fail(AT_ERR_ARG, "n_steps < 0");
+    if (interval < 1) return fail(AT_ERR_ARG, "interval must be >= 1");
+    return AT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t at_checkpoint_bytes(const at_solver *h, int64_t n_steps, int64_t interval)
+{
+    if (check_adjoint_args(h, n_steps, interval) != AT_OK) return 0;
+    return (size_t)n_segments(n_steps, interval) * (size_t)ckpt_levels(h) * (size_t)h->N * h->w;
+}
+
+int at_step_checkpointed(at_solver *h, int64_t n_steps, int delay_mode, int8_t *delays, int64_t interval, void *ckpt)
+{
+    g_err[0] = 0;
+    int rc = check_adjoint_args(h, n_steps, interval);
+    if (rc != AT_OK) return rc;
+    if (!ckpt) return fail(AT_ERR_ARG, "ckpt is NULL");
+    if (!h->has_state || h->step != 0) return fail(AT_ERR_STATE, "at_step_checkpointed starts at level 0 (after at_set_state)");
+    const int64_t Dc = ckpt_levels(h), nseg = n_segments(n_steps, interval);
+    const size_t lvl = (size_t)h->N * h->w, seg_bytes = (size_t)Dc * lvl;
+    unsigned char *ck = static_cast<unsigned char *>(ckpt);
+    cudaError_t e = cudaMemsetAsync(ck, 0, seg_bytes, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(ck, h->ws + h->lay.u, lvl, cudaMemcpyDeviceToDevice, h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "checkpoint 0");
+    for (int64_t seg = 0; seg < nseg; ++seg) {
+        const int64_t c = seg * interval;
+        const int64_t len = n_steps - c < interval ? n_steps - c : interval;
+        int8_t *d = delays ? delays + (size_t)c * h->P * 2 : nullptr;
+        if (seg + 1 < nseg) {
+            // the next checkpoint starts as a copy of this one, so that it also
+            // holds the levels before c when the interval is shorter than Dc
+            e = cudaMemcpyAsync(ck + (size_t)(seg + 1) * seg_bytes, ck + (size_t)seg * seg_bytes, seg_bytes,
+                                cudaMemcpyDeviceToDevice, h->stream);
+            if (e != cudaSuccess) return cuda_fail(e, "checkpoint copy");
+            rc = step_impl(h, len, delay_mode, d, ck + (size_t)(seg + 1) * seg_bytes, Dc);
+        } else {
+            rc = step_impl(h, len, delay_mode, d, nullptr, 0);
+        }
+        if (rc != AT_OK) return rc;
+    }
+    return AT_OK;
+}
+
+size_t at_adjoint_workspace_bytes(const at_solver *h, int64_t interval)
+{
+    if (check_adjoint_args(h, 0, interval) != AT_OK) return 0;
+    return adj_layout(h, interval).total;
+}
+
+int at_adjoint(at_solver *h, int64_t n_steps, int delay_mode, const int8_t *delays, int64_t interval,
+               const void *ckpt, void *adj_ws, size_t adj_ws_bytes, void *lam, double *dnu)
+{
+    g_err[0] = 0;
+    int rc = check_adjoint_args(h, n_steps, interval);
+    if (rc != AT_OK) return rc;
+    if (!ckpt || !adj_ws || !lam) return fail(AT_ERR_ARG, "NULL argument");
+    if (delay_mode != AT_SYNC && delay_mode != AT_SEEDED && delay_mode != AT_REPLAY)
+        return fail(AT_ERR_ARG, "the adjoint replays AT_SYNC, AT_SEEDED or AT_REPLAY delays (record AT_FREE ones)");
+    if (delay_mode == AT_REPLAY && !delays) return fail(AT_ERR_ARG, "AT_REPLAY needs a delays array");
+    const AdjLayout al = adj_layout(h, interval);
+    if (adj_ws_bytes < al.total) return fail(AT_ERR_ARG, "adjoint workspace too small: %zu < %zu", adj_ws_bytes, al.total);
+    if (reinterpret_cast<uintptr_t>(adj_ws) % 256 != 0) return fail(AT_ERR_ARG, "adjoint workspace must be 256-byte aligned");
+    if (!h->has_state) return fail(AT_ERR_STATE, "at_adjoint needs the solver's state to have been set");
+    const int64_t Dc = ckpt_levels(h), Dl = interval + Dc, nseg = n_segments(n_steps, interval);
+    const size_t lvl = (size_t)h->N * h->w, seg_bytes = (size_t)Dc * lvl;
+    unsigned char *ws = static_cast<unsigned char *>(adj_ws);
+    const unsigned char *ck = static_cast<const unsigned char *>(ckpt);
+    const int G = adj_blocks(h);
+    cudaError_t e = cudaMemsetAsync(ws + al.pend, 0, al.dnu - al.pend + (size_t)G * 8, h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(adjoint)");
+
+    atk::AdjParams a{};
+    a.levels = ws + al.levels;
+    a.depth = Dl;
+    a.pend = ws + al.pend;
+    a.dnu_part = reinterpret_cast<double *>(ws + al.dnu);
+    a.delays = delays;
+    a.N = h->N; a.P = h->P; a.M = h->M;
+    a.L = h->L; a.Tp = h->T;
+    a.mode = delay_mode == AT_SEEDED ? 1 : delay_mode == AT_REPLAY ? 3 : 0;
+    a.per_sub = (h->g.flags & AT_FLAG_PER_SUBDOMAIN_DELAY) ? 1 : 0;
+    a.seed = h->g.seed;
+    if (h->order == 2) {
+        a.cA = h->dt / (2.0 * h->dx);
+        a.cB = h->nu * h->dt / (h->dx * h->dx);
+        a.dtdx2 = h->dt / (h->dx * h->dx);
+    } else {
+        a.cA = h->dt / (12.0 * h->dx);
+        a.cB = h->nu * h->dt / (12.0 * h->dx * h->dx);
+        a.dtdx2 = h->dt / (12.0 * h->dx * h->dx);
+    }
+    void *kern = atk_adjoint_kernel(h->w, h->order);
+    unsigned char *cur = static_cast<unsigned char *>(lam), *other = ws + al.lam;
+    for (int64_t seg = nseg - 1; seg >= 0; --seg) {
+        const int64_t c = seg * interval;
+        const int64_t end = n_steps - c < interval ? n_steps : c + interval;
+        // levels c-Dc+1 .. c from the checkpoint, then c+1 .. end recomputed
+        for (int64_t l = (c - Dc + 1 > 0 ? c - Dc + 1 : 0); l <= c; ++l) {
+            e = cudaMemcpyAsync(ws + al.levels + (size_t)(l % Dl) * lvl, ck + (size_t)seg * seg_bytes + (size_t)(l % Dc) * lvl,
+                                lvl, cudaMemcpyDeviceToDevice, h->stream);
+            if (e != cudaSuccess) return cuda_fail(e, "restoring levels");
+        }
+        rc = at_set_history(h, ck + (size_t)seg * seg_bytes, Dc, c);
+        if (rc != AT_OK) return rc;
+        int8_t *d = delay_mode == AT_REPLAY ? const_cast<int8_t *>(delays) + (size_t)c * h->P * 2 : nullptr;
+        rc = step_impl(h, end - c, delay_mode, d, ws + al.levels, Dl);
+        if (rc != AT_OK) return rc;
+        for (int64_t n = end - 1; n >= c; --n) {
+            a.n = n;
+            a.lam_in = cur;
+            a.lam_out = other;
+            void *args[] = {&a};
+            e = cudaLaunchKernel(kern, dim3(G), dim3(256), args, 0, h->stream);
+            if (e != cudaSuccess) return cuda_fail(e, "launch at_adjoint_step");
+            unsigned char *t = cur; cur = other; other = t;
+        }
+    }
+    if (cur != lam) {
+        e = cudaMemcpyAsync(lam, cur, lvl, cudaMemcpyDeviceToDevice, h->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(lambda)");
+    }
+    std::vector<double> part((size_t)G);
+    e = cudaMemcpyAsync(part.data(), ws + al.dnu, (size_t)G * 8, cudaMemcpyDeviceToHost, h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(dnu)");
+    rc = read_status(h);
+    if (rc != AT_OK) return rc;
+    double sum = 0.0;
+    for (int b = 0; b < G; ++b) sum += part[(size_t)b];
+    if (dnu) *dnu = sum;
     return AT_OK;
 }
 

@@ -122,6 +122,8 @@ struct Params {
     int8_t *delays;            // [n_steps][P][2] replay input / record output
     const BatchSub *bsub;      // ensembles: [P] subdomain records (else NULL)
     const BatchInst *binst;    // ensembles: instance records (else NULL)
+    void *levels;              // optional copy of every level l computed: slot l mod levels_depth of N words
+    long long levels_depth;    // (single-level passes only; the adjoint's recomputation)
     long long N, P, M;
     int L, T, mode, per_sub;   // L: largest delay bound (ensembles: of any instance)
     long long n_steps;
@@ -723,6 +725,15 @@ __device__ void run_pe(const Params &p, const Sweep &sw, long long lo, long long
             const int g = lane + 32 * m;
             if (FULL || g < NG) stg4<T>(ug + 4 * g, c[m]);
         }
+        if (p.levels) {
+            T *lg = reinterpret_cast<T *>(p.levels) + (size_t)((n + len) % p.levels_depth) * (size_t)p.N +
+                    (size_t)j * p.M;
+#pragma unroll
+            for (int m = 0; m < GW; ++m) {
+                const int g = lane + 32 * m;
+                if (FULL || g < NG) stg4<T>(lg + 4 * g, c[m]);
+            }
+        }
         // the next read of this tile is a bulk copy (async proxy), issued by
         // lane 0 after the warp barrier
         fence_proxy_async_global();
@@ -845,6 +856,40 @@ __global__ void at_init(const Params p)
         if (threadIdx.x < kCtrlWords) p.ctrl[threadIdx.x] = 0;
         if (threadIdx.x <= p.L) p.hist[threadIdx.x] = 0ull;
         if (threadIdx.x == 0) *p.gbar = 0ull;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// restart from stored levels: ring slots of levels lo_level .. level from the
+// full fields levels[l mod depth], every flag at `level`, the control block
+// cleared with the state's level set to `level`
+// ---------------------------------------------------------------------------
+template <typename T, int R>
+__global__ void at_restore(const Params p, const T *levels, long long depth, long long lo_level, long long level)
+{
+    const long long nl = level - lo_level + 1;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const size_t slot_stride = (size_t)p.P * 2 * kRingEntry;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < p.P * nl; t += stride) {
+        const long long j = t % p.P, l = lo_level + t / p.P;
+        const T *u = levels + (size_t)(l % depth) * (size_t)p.N + (size_t)j * p.M;
+        T a[2] = {u[0], R > 1 ? u[1] : (T)0};
+        T b[2] = {u[p.M - R], R > 1 ? u[p.M - R + 1] : (T)0};
+        unsigned char *e = p.ring + (size_t)(l & (p.T - 1)) * slot_stride + (size_t)j * 2 * kRingEntry;
+        st_entry<T, R>(e, a);
+        st_entry<T, R>(e + kRingEntry, b);
+        if (l == level) {
+            p.flag[j * 2 + 0] = (unsigned long long)level;
+            p.flag[j * 2 + 1] = (unsigned long long)level;
+        }
+    }
+    if (blockIdx.x == 0) {
+        if (threadIdx.x < kCtrlWords) p.ctrl[threadIdx.x] = 0;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            *reinterpret_cast<long long *>(p.ctrl + kCtrlN0) = level;
+            *p.gbar = 0ull;
+        }
     }
 }
 

@@ -13,3 +13,9 @@ __attribute__((visibility("hidden"))) void *atk_init_kernel_f32(int order)
 {
     return order == 2 ? (void *)atk::at_init<float, 1> : (void *)atk::at_init<float, 2>;
 }
+
+// Restart kernel (stored levels -> ring, flags, level) for stencil order 2|4.
+__attribute__((visibility("hidden"))) void *atk_restore_kernel_f32(int order)
+{
+    return order == 2 ? (void *)atk::at_restore<float, 1> : (void *)atk::at_restore<float, 2>;
+}

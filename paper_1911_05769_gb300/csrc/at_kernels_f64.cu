@@ -15,3 +15,9 @@ __attribute__((visibility("hidden"))) void *atk_init_kernel_f64(int order)
 {
     return order == 2 ? (void *)atk::at_init<double, 1> : (void *)atk::at_init<double, 2>;
 }
+
+// Restart kernel (stored levels -> ring, flags, level) for stencil order 2|4.
+__attribute__((visibility("hidden"))) void *atk_restore_kernel_f64(int order)
+{
+    return order == 2 ? (void *)atk::at_restore<double, 1> : (void *)atk::at_restore<double, 2>;
+}

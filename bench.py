@@ -65,6 +65,7 @@ def parse():
     ap.add_argument("--ensemble-only", action="store_true", help="time only the 2048-instance ensemble leg")
     ap.add_argument("--ens-time-steps", type=int, default=5000, help="time steps per ensemble launch")
     ap.add_argument("--no-tune", action="store_true", help="ensemble leg: keep the default launch shape")
+    ap.add_argument("--adjoint-only", action="store_true", help="time only the adjoint leg")
     return ap.parse_args()
 
 
@@ -292,6 +293,81 @@ def ensemble_config(args, at, torch, dev, stream):
         worst = max(worst, float(np.max(np.abs(part - ref)) / np.max(np.abs(ref))))
     res["err_vs_fp64_oracle"] = {"rel_linf": worst, "mode": "seeded", "steps": time_steps,
                                  "instances": [int(j) for j in which]}
+    return res
+
+
+def adjoint_config(args, at, torch, dev):
+    """Gradient of ||u(T) - u_target||^2 with respect to u0 (2^20 values) and
+    nu through 2000 seeded AT steps (order 2, L = 2, nu = 0.01, checkpoints
+    every 100): forward (checkpointed) and backward (recomputation + adjoint
+    kernel) timed with CUDA events; the FP64 gradient checked against central
+    differences of the FP64 forward run on 16 random directions."""
+    wl = W.adjoint_workload()
+    N, n_steps = wl["N"], wl["n_steps"]
+    stream = torch.cuda.current_stream(dev)
+
+    def forward_run(u0, nu, dtype="f64"):
+        s = at.Solver(N, wl["P"], wl["order"], wl["L"], nu, wl["dt"], dtype=dtype, seed=wl["seed"], device=dev.index)
+        s.set_state(torch.as_tensor(u0).to(dev))
+        s.step(n_steps, at.AT_SEEDED)
+        out = s.state().double()
+        s.close()
+        return out
+
+    target = forward_run(wl["u0_target"], wl["nu_target"])
+    res = {"workload": wl["name"], "N": N, "P": wl["P"], "order": wl["order"], "L": wl["L"], "nu": wl["nu"],
+           "time_steps": n_steps, "checkpoint_interval": wl["interval"], "loss": "||u(T) - u_target||^2"}
+
+    def grad(dtype, reps):
+        tdt = torch.float64 if dtype == "f64" else torch.float32
+        u0 = torch.from_numpy(wl["u0"]).to(device=dev, dtype=tdt).requires_grad_(True)
+        nu = torch.tensor(wl["nu"], dtype=torch.float64, device=dev, requires_grad=True)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        fwd, bwd = [], []
+        for r in range(reps + 1):
+            ev[0].record(stream)
+            uT = at.at_run(u0, nu, P=wl["P"], order=wl["order"], L=wl["L"], dt=wl["dt"], n_steps=n_steps,
+                           mode=at.AT_SEEDED, seed=wl["seed"], interval=wl["interval"])
+            ev[1].record(stream)
+            loss = ((uT.double() - target) ** 2).sum()
+            gu0, gnu = torch.autograd.grad(loss, (u0, nu))
+            ev[2].record(stream)
+            torch.cuda.synchronize(dev)
+            if r > 0:
+                fwd.append(ev[0].elapsed_time(ev[1]))
+                bwd.append(ev[1].elapsed_time(ev[2]))
+        f, b = statistics.median(fwd), statistics.median(bwd)
+        return gu0.double(), float(gnu), {"forward_ms": f, "backward_ms": b,
+                                           "value": N * n_steps / ((f + b) * 1e-3) / 1e9, "unit": UNIT,
+                                           "value_note": "forward-equivalent updates per second of one gradient"}
+
+    g32, n32, t32 = grad("f32", 3)
+    g64, n64, t64 = grad("f64", 1)
+    res["f32"] = t32
+    res["f64"] = t64
+    res["f32_vs_f64_gradient_rel_l2"] = float((g32 - g64).norm() / g64.norm())
+    res["f32_vs_f64_dnu_rel"] = abs(n32 - n64) / abs(n64)
+    # central differences of the FP64 forward run
+    rng = np.random.default_rng(16)
+    base = torch.from_numpy(wl["u0"]).to(dev)
+
+    def J(u, n):
+        return float(((forward_run(u, n) - target) ** 2).sum())
+
+    worst = 0.0
+    for _ in range(16):
+        d = torch.from_numpy(rng.standard_normal(N)).to(dev)
+        eps = 1e-4
+        fd = (J(base + eps * d, wl["nu"]) - J(base - eps * d, wl["nu"])) / (2 * eps)
+        worst = max(worst, abs(fd - float((g64 * d).sum())) / abs(fd))
+    enu = 1e-2 * wl["nu"]
+    fdnu = (J(base, wl["nu"] + enu) - J(base, wl["nu"] - enu)) / (2 * enu)
+    res["fd_check_fp64"] = {"directions": 16, "max_rel_err_u0": worst, "rel_err_nu": abs(fdnu - n64) / abs(fdnu),
+                            "dJ_dnu": n64}
+    s = at.Solver(N, wl["P"], wl["order"], wl["L"], wl["nu"], wl["dt"], dtype="f32", seed=wl["seed"], device=dev.index)
+    res["memory_bytes"] = {"checkpoints_f32": at.at_checkpoint_bytes(s.h, n_steps, wl["interval"]),
+                           "adjoint_workspace_f32": at.at_adjoint_workspace_bytes(s.h, wl["interval"])}
+    s.close()
     return res
 
 
@@ -540,6 +616,7 @@ def gpu_arm(args, ws, rank, local, pg):
         line["small_config"] = small_config(args, at, torch, dev, stream)
         if rank == 0 and ws == 1:
             line["ensemble"] = ensemble_config(args, at, torch, dev, stream)
+            line["adjoint"] = adjoint_config(args, at, torch, dev)
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -553,6 +630,15 @@ def main():
         reference_arm(args, ws, rank, None)
         return
     ws, rank, local, pg = dist_setup(args)
+    if args.adjoint_only:
+        import torch
+
+        import paper_1911_05769_gb300 as at
+        from paper_1911_05769_gb300 import build as atbuild
+        atbuild.build()
+        torch.cuda.set_device(local)
+        print(json.dumps(adjoint_config(args, at, torch, torch.device("cuda", local))), flush=True)
+        return
     if args.ensemble_only:
         import torch
 

@@ -19,25 +19,29 @@
 // are scattered into a pending ring [slot][P][2][R] by the one thread that owns
 // the reading face (one writer per slot entry and step) and collected, then
 // cleared, when the sweep reaches that level.  No atomics; dJ/dnu is summed
-// per block in FP64.
+// per block in FP64.  Blocks walk the subdomains, one thread per point; the
+// word offsets of the levels read are computed on the host.
 #pragma once
 
 #include "at_device.cuh"
 
 namespace atk {
 
+constexpr int kAdjMaxLevels = 20;   // levels n .. n-L-s+1 a step reads (L <= 16, s <= 3)
+
 struct AdjParams {
-    const void *levels;        // u^l at slot l mod depth, N words each
-    long long depth;
+    const void *levels;        // full fields of the stored levels, N words each
+    long long lvl_off[kAdjMaxLevels];   // word offset of level n - q in `levels` (q = 0 .. L+s-1)
     const void *lam_in;        // lambda^{n+1}, N words
     void *lam_out;             // lambda^n, N words
     void *pend;                // [Tp][P][2][R] words: adjoint of boundary values at older levels
     double *dnu_part;          // [gridDim.x] running FP64 sums of dJ/dnu
-    const int8_t *delays;      // replayed delays [levels][P][2], absolute level index
+    const int8_t *delays;      // delays of level n at delays[(n - k_level) * P * 2 + p * 2 + face]
+    long long k_level;         // level of the delays' first row
     long long N, P, M;
-    int L, Tp, mode, per_sub;
-    unsigned long long seed;
+    int L, Tp;                 // Tp: a power of two
     double cA, cB, dtdx2;      // as the stepper's; dtdx2 = cB / nu
+    float cAf, cBf, dtdx2f;    // the same in FP32 (FP32 kernels convert nothing per point)
     long long n;               // level of lambda_out
 };
 
@@ -55,24 +59,33 @@ struct Coeffs<4> {
     static __device__ __forceinline__ int beta(int j) { return j == 0 ? -30 : (j == 1 || j == -1) ? 16 : -1; }
 };
 
+// Per-launch view of the stored levels and the adjoint fields, with 32-bit
+// indices within a level (the host checks N < 2^31).
 template <typename T, int ORDER>
 struct AdjStep {
     static constexpr int R = ORDER / 2;
     static constexpr int S_LEV = ORDER / 2 + 1;
     const AdjParams &a;
+    const T *lev;              // stored levels
+    const T *un;               // level n
+    const T *lam;              // lambda^{n+1}
+    int M, P;
+    T cA, cB;
 
-    __device__ T u(long long l, long long i) const
+    __device__ explicit AdjStep(const AdjParams &p)
+        : a(p), lev(reinterpret_cast<const T *>(p.levels)), un(reinterpret_cast<const T *>(p.levels) + p.lvl_off[0]),
+          lam(reinterpret_cast<const T *>(p.lam_in)), M((int)p.M), P((int)p.P)
     {
-        return reinterpret_cast<const T *>(a.levels)[(size_t)(l % a.depth) * (size_t)a.N + (size_t)i];
+        if constexpr (sizeof(T) == 4) { cA = p.cAf; cB = p.cBf; }
+        else { cA = (T)p.cA; cB = (T)p.cB; }
     }
 
-    // delay of face f of subdomain p at level n, clamped as the forward run
-    // clamps it (no level below 0, at most L)
-    __device__ int delay(long long p, int f) const
+    // delay of face f of subdomain p at level n (the forward run's, read from
+    // the recomputation's record or the replayed array), clamped as the
+    // forward run clamps it (no level below 0, at most L)
+    __device__ int delay(int p, int f) const
     {
-        int k = 0;
-        if (a.mode == 1) k = seeded_delay(a.seed, a.n, p, a.P, a.per_sub ? 0 : f, a.L);
-        else if (a.mode == 3) k = a.delays[((size_t)a.n * a.P + p) * 2 + f];
+        int k = a.delays[((size_t)(a.n - a.k_level) * a.P + p) * 2 + f];
         long long kmax = a.n - S_LEV + 1;
         if (kmax < 0) kmax = 0;
         if (kmax > a.L) kmax = a.L;
@@ -83,15 +96,15 @@ struct AdjStep {
 
     // halo value of point src extrapolated with delay k (same operations as
     // the stepper's halo approximation)
-    __device__ T halo(long long src, int k) const
+    __device__ T halo(int src, int k) const
     {
-        const T r0 = u(a.n - k, src);
+        const T r0 = lev[a.lvl_off[k] + src];
         if (k == 0) return r0;
-        const T r1 = u(a.n - k - 1, src);
+        const T r1 = lev[a.lvl_off[k + 1] + src];
         if constexpr (S_LEV == 2) {
             return (T)(k + 1) * r0 - (T)k * r1;
         } else {
-            const T r2 = u(a.n - k - 2, src);
+            const T r2 = lev[a.lvl_off[k + 2] + src];
             const T w0 = (T)((k + 1) * (k + 2) / 2);
             const T w1 = (T)(-k * (k + 2));
             const T w2 = (T)(k * (k + 1) / 2);
@@ -99,138 +112,186 @@ struct AdjStep {
         }
     }
 
-    // stencil values v[0..2R] of point r at level n
-    __device__ void values(long long r, T *v) const
+    __device__ int left(int p) const { return p == 0 ? P - 1 : p - 1; }
+    __device__ int right(int p) const { return p == P - 1 ? 0 : p + 1; }
+
+    // stencil values v[0..2R] at level n of point loc of subdomain p, whose
+    // faces have delays k0, k1
+    __device__ void values(int p, int loc, int k0, int k1, T *v) const
     {
-        const long long p = r / a.M, loc = r - p * a.M;
-        int kf[2] = {-1, -1};
 #pragma unroll
         for (int j = -R; j <= R; ++j) {
-            const long long lj = loc + j;
-            if (lj >= 0 && lj < a.M) {
-                v[j + R] = u(a.n, r + j);
-            } else {
-                const int f = lj < 0 ? 0 : 1;
-                if (kf[f] < 0) kf[f] = delay(p, f);
-                long long src = r + j;
-                if (src < 0) src += a.N;
-                if (src >= a.N) src -= a.N;
-                v[j + R] = halo(src, kf[f]);
-            }
+            const int lj = loc + j;
+            if (lj < 0) v[j + R] = halo(left(p) * M + M + lj, k0);
+            else if (lj >= M) v[j + R] = halo(right(p) * M + (lj - M), k1);
+            else v[j + R] = un[p * M + lj];
         }
     }
 
     // lambda^{n+1}_r d u^{n+1}_r / d v_j, given the values v of point r
-    __device__ T gbar(long long r, int j, const T *v) const
+    __device__ T gbar(int r, int j, const T *v) const
     {
         T av = (T)0;
 #pragma unroll
         for (int q = -R; q <= R; ++q) av += (T)Coeffs<ORDER>::alpha(q) * v[q + R];
-        const T g = reinterpret_cast<const T *>(a.lam_in)[r];
-        T d = (T)a.cB * (T)Coeffs<ORDER>::beta(j) - (T)a.cA * v[R] * (T)Coeffs<ORDER>::alpha(j);
-        if (j == 0) d += (T)1 - (T)a.cA * av;
-        return g * d;
+        T d = cB * (T)Coeffs<ORDER>::beta(j) - cA * v[R] * (T)Coeffs<ORDER>::alpha(j);
+        if (j == 0) d += (T)1 - cA * av;
+        return lam[r] * d;
     }
 
-    __device__ T *pend(long long l, long long p, int side, int r) const
+    __device__ T *pend(long long l, int p, int side, int r) const
     {
-        return reinterpret_cast<T *>(a.pend) + (((size_t)(l % a.Tp) * a.P + p) * 2 + side) * R + r;
+        return reinterpret_cast<T *>(a.pend) + (((size_t)(l & (a.Tp - 1)) * a.P + p) * 2 + side) * R + r;
     }
 };
 
+// Block (x, y) handles points y*256 .. y*256+255 of subdomains x, x + gridDim.x,
+// ...  Each point first computes the 2R+1 terms it contributes to the adjoint
+// of its stencil values (c_j = lambda^{n+1}_r d u^{n+1}_r / d v_j) into shared
+// memory; each point then gathers the terms of its readers from there.
+constexpr int kAdjThreads = 256;
+
 template <typename T, int ORDER>
-__global__ void __launch_bounds__(256) at_adjoint_step(const AdjParams a)
+__global__ void __launch_bounds__(kAdjThreads) at_adjoint_step(const AdjParams a)
 {
     constexpr int R = ORDER / 2;
     constexpr int S_LEV = ORDER / 2 + 1;
-    const AdjStep<T, ORDER> A{a};
-    double nu_acc = 0.0;
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < a.N; i += stride) {
-        const long long p = i / a.M, loc = i - p * a.M;
+    const AdjStep<T, ORDER> A(a);
+    __shared__ T s_c[2 * R + 1][kAdjThreads];
+    T nu_acc = (T)0;          // this thread's sum of lambda^{n+1}_i b_i
+    const T dtdx2 = sizeof(T) == 4 ? (T)a.dtdx2f : (T)a.dtdx2;
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int M = A.M;
+    const int chunk_lo = blockIdx.y * kAdjThreads;
+    const int loc = chunk_lo + tid;
+    T *lam_out = reinterpret_cast<T *>(a.lam_out);
+    for (int p = blockIdx.x; p < A.P; p += gridDim.x) {
+        const int pl = A.left(p), pr = A.right(p);
+        // delays (lanes 0..3, then shared across the warp): this subdomain's
+        // faces 0, 1; the left neighbour's face 1; the right neighbour's face 0
+        int kk = 0;
+        if (lane < 4) kk = A.delay(lane < 2 ? p : (lane == 2 ? pl : pr), lane < 2 ? lane : (lane == 2 ? 1 : 0));
+        const int k0 = __shfl_sync(0xffffffffu, kk, 0), k1 = __shfl_sync(0xffffffffu, kk, 1);
+        const int kl1 = __shfl_sync(0xffffffffu, kk, 2), kr0 = __shfl_sync(0xffffffffu, kk, 3);
+        __syncthreads();   // the previous subdomain's terms have been read
+        const bool live = loc < M;
+        const int i = p * M + loc;
         T v[2 * R + 1];
-        T acc = (T)0;
-        // readers r = i + d whose value j = -d is u^n_i
+        if (live) {
+            A.values(p, loc, k0, k1, v);
+            T av = (T)0, bv = (T)0;
 #pragma unroll
-        for (int d = -R; d <= R; ++d) {
-            const long long rl = loc + d;
-            long long r = i + d;
-            if (rl >= 0 && rl < a.M) {
-                A.values(r, v);
-                acc += A.gbar(r, -d, v);
-            } else {
-                // a boundary point of the neighbouring subdomain reads u^n_i
-                // across its face; only an undelayed read lands on level n
-                const long long pp = rl < 0 ? (p == 0 ? a.P - 1 : p - 1) : (p == a.P - 1 ? 0 : p + 1);
-                const int ff = rl < 0 ? 1 : 0;
-                if (A.delay(pp, ff) == 0) {
-                    if (r < 0) r += a.N;
-                    if (r >= a.N) r -= a.N;
-                    A.values(r, v);
-                    acc += A.gbar(r, -d, v);
+            for (int q = -R; q <= R; ++q) {
+                av += (T)Coeffs<ORDER>::alpha(q) * v[q + R];
+                bv += (T)Coeffs<ORDER>::beta(q) * v[q + R];
+            }
+            const T g = A.lam[i];
+#pragma unroll
+            for (int j = -R; j <= R; ++j) {
+                T d = A.cB * (T)Coeffs<ORDER>::beta(j) - A.cA * v[R] * (T)Coeffs<ORDER>::alpha(j);
+                if (j == 0) d += (T)1 - A.cA * av;
+                s_c[j + R][tid] = g * d;
+            }
+            nu_acc += g * bv;
+        }
+        __syncthreads();
+        if (live) {
+            T acc = (T)0;
+            // readers r = i + d whose value j = -d is u^n_i
+#pragma unroll
+            for (int d = -R; d <= R; ++d) {
+                const int rl = loc + d;
+                if (rl >= 0 && rl < M) {
+                    if (rl >= chunk_lo && rl < chunk_lo + kAdjThreads) {
+                        acc += s_c[-d + R][tid + d];
+                    } else {
+                        A.values(p, rl, k0, k1, v);
+                        acc += A.gbar(i + d, -d, v);
+                    }
+                } else if (rl < 0) {
+                    // the left neighbour's last points read u^n_i across their
+                    // face 1; only an undelayed read lands on level n (with
+                    // M >= 2R their stencils do not reach their own face 0)
+                    if (kl1 == 0) {
+                        A.values(pl, M + rl, -1, kl1, v);
+                        acc += A.gbar(pl * M + M + rl, -d, v);
+                    }
+                } else if (kr0 == 0) {
+                    A.values(pr, rl - M, kr0, -1, v);
+                    acc += A.gbar(pr * M + (rl - M), -d, v);
                 }
             }
-        }
-        // delayed reads from later steps addressed to level n
-        if (loc < R) {
-            T *q = A.pend(a.n, p, 0, (int)loc);
-            acc += *q;
-            *q = (T)0;
-        } else if (loc >= a.M - R) {
-            T *q = A.pend(a.n, p, 1, (int)(loc - (a.M - R)));
-            acc += *q;
-            *q = (T)0;
-        }
-        reinterpret_cast<T *>(a.lam_out)[i] = acc;
-
-        // dJ/dnu: lambda^{n+1}_i (cB / nu) b_i
-        A.values(i, v);
-        T bv = (T)0;
-#pragma unroll
-        for (int q = -R; q <= R; ++q) bv += (T)Coeffs<ORDER>::beta(q) * v[q + R];
-        nu_acc += (double)reinterpret_cast<const T *>(a.lam_in)[i] * a.dtdx2 * (double)bv;
-
-        // this subdomain's delayed reads across a face, scattered to older
-        // levels of the neighbour's boundary values (one thread per face)
-        if (loc == 0 || loc == a.M - 1) {
-            const int f = loc == 0 ? 0 : 1;
-            const int k = A.delay(p, f);
-            const long long q = f == 0 ? (p == 0 ? a.P - 1 : p - 1) : (p == a.P - 1 ? 0 : p + 1);
-            T w[S_LEV];
-            if constexpr (S_LEV == 2) {
-                w[0] = (T)(k + 1);
-                w[1] = (T)(-k);
-            } else {
-                w[0] = (T)((k + 1) * (k + 2) / 2);
-                w[1] = (T)(-k * (k + 2));
-                w[2] = (T)(k * (k + 1) / 2);
+            // delayed reads from later steps addressed to level n
+            if (loc < R) {
+                T *q = A.pend(a.n, p, 0, loc);
+                acc += *q;
+                *q = (T)0;
+            } else if (loc >= M - R) {
+                T *q = A.pend(a.n, p, 1, loc - (M - R));
+                acc += *q;
+                *q = (T)0;
             }
-            for (int t = 0; t < R; ++t) {
-                const long long r = f == 0 ? i + t : i - t;           // reader point
-                A.values(r, v);
-                for (int j = (f == 0 ? -R : t + 1); j <= (f == 0 ? -t - 1 : R); ++j) {
-                    const T gb = A.gbar(r, j, v);
-                    // source: point (M + t + j) of q (face 0) or (j - t - 1) of q (face 1)
-                    const int side = f == 0 ? 1 : 0;
-                    const int sr = f == 0 ? R + t + j : j - t - 1;
-                    for (int m = 0; m < S_LEV; ++m) {
-                        if (k + m == 0 || w[m] == (T)0) continue;     // level n: gathered above
-                        T *dst = A.pend(a.n - k - m, q, side, sr);
-                        *dst += w[m] * gb;
+            lam_out[i] = acc;
+
+            // this subdomain's delayed reads across a face, scattered to older
+            // levels of the neighbour's boundary values (one thread per face;
+            // its readers are in its own chunk)
+            if (loc == 0 || loc == M - 1) {
+                const int f = loc == 0 ? 0 : 1;
+                const int k = f == 0 ? k0 : k1;
+                const int q = f == 0 ? pl : pr;
+                T w[S_LEV];
+                if constexpr (S_LEV == 2) {
+                    w[0] = (T)(k + 1);
+                    w[1] = (T)(-k);
+                } else {
+                    w[0] = (T)((k + 1) * (k + 2) / 2);
+                    w[1] = (T)(-k * (k + 2));
+                    w[2] = (T)(k * (k + 1) / 2);
+                }
+                // per source point of q: the sum of its readers' terms (source:
+                // point M + t + j of q across face 0, j - t - 1 across face 1)
+                T src[R];
+#pragma unroll
+                for (int r = 0; r < R; ++r) src[r] = (T)0;
+#pragma unroll
+                for (int t = 0; t < R; ++t) {
+                    const int rt = f == 0 ? tid + t : tid - t;         // reader's thread
+#pragma unroll
+                    for (int j = -R; j <= R; ++j) {
+                        const bool crosses = f == 0 ? (j <= -t - 1) : (j >= t + 1);
+                        if (!crosses) continue;
+                        src[f == 0 ? R + t + j : j - t - 1] += s_c[j + R][rt];
                     }
                 }
+                // older levels n-k-m of those points: all loads, then all stores
+                const int side = f == 0 ? 1 : 0;
+                T old[S_LEV][R];
+#pragma unroll
+                for (int m = 0; m < S_LEV; ++m)
+#pragma unroll
+                    for (int r = 0; r < R; ++r)
+                        old[m][r] = (k + m == 0 || w[m] == (T)0) ? (T)0 : *A.pend(a.n - k - m, q, side, r);
+#pragma unroll
+                for (int m = 0; m < S_LEV; ++m) {
+                    if (k + m == 0 || w[m] == (T)0) continue;     // level n: gathered above
+#pragma unroll
+                    for (int r = 0; r < R; ++r) *A.pend(a.n - k - m, q, side, r) = old[m][r] + w[m] * src[r];
+                }
             }
         }
     }
-    // per-block sum of the nu contributions, added to this block's running total
-    __shared__ double red[256];
-    red[threadIdx.x] = nu_acc;
+    // dJ/dnu of this block: warp sums in the state's precision, then the
+    // block's FP64 running total (one FP64 add per warp: FP64 is slow here)
+    for (int o = 16; o > 0; o >>= 1) nu_acc += __shfl_xor_sync(0xffffffffu, nu_acc, o);
+    __shared__ T red[kAdjThreads / 32];
+    if (lane == 0) red[tid >> 5] = nu_acc;
     __syncthreads();
-    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-        if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
-        __syncthreads();
+    if (tid == 0) {
+        double sum = 0.0;
+        for (int w = 0; w < kAdjThreads / 32; ++w) sum += (double)red[w] * (double)dtdx2;
+        a.dnu_part[(size_t)blockIdx.y * gridDim.x + blockIdx.x] += sum;
     }
-    if (threadIdx.x == 0) a.dnu_part[blockIdx.x] += red[0];
 }
 
 }  // namespace atk

@@ -817,14 +817,13 @@ int64_t ckpt_levels(const at_solver *h) { return h->L + h->s; }
 
 int64_t n_segments(int64_t n_steps, int64_t interval) { return n_steps <= 0 ? 1 : (n_steps + interval - 1) / interval; }
 
-int adj_blocks(const at_solver *h)
-{
-    const int64_t b = (h->N + 255) / 256;
-    return (int)(b < 8LL * h->sm_count ? b : 8LL * h->sm_count);
-}
+// adjoint launch: x walks the subdomains, y the 256-point chunks of one
+int adj_grid_x(const at_solver *h) { return (int)(h->P < 16LL * h->sm_count ? h->P : 16LL * h->sm_count); }
+int adj_grid_y(const at_solver *h) { return (int)((h->M + atk::kAdjThreads - 1) / atk::kAdjThreads); }
+int adj_blocks(const at_solver *h) { return adj_grid_x(h) * adj_grid_y(h); }
 
 struct AdjLayout {
-    size_t levels, lam, pend, dnu, total;
+    size_t levels, lam, pend, dnu, kbuf, total;
 };
 
 AdjLayout adj_layout(const at_solver *h, int64_t interval)
@@ -835,6 +834,7 @@ AdjLayout adj_layout(const at_solver *h, int64_t interval)
     l.lam = off;    off = align_up(off + (size_t)h->N * h->w, 256);
     l.pend = off;   off = align_up(off + (size_t)h->T * h->P * 2 * h->R * h->w, 256);
     l.dnu = off;    off = align_up(off + (size_t)adj_blocks(h) * 8, 256);
+    l.kbuf = off;   off = align_up(off + (size_t)interval * h->P * 2, 256);
     l.total = off;
     return l;
 }
@@ -843,6 +843,7 @@ int check_adjoint_args(const at_solver *h, int64_t n_steps, int64_t interval)
 {
     if (!h) return fail(AT_ERR_ARG, "NULL handle");
     if (h->batch) return fail(AT_ERR_ARG, "the adjoint covers single-domain solvers");
+    if (h->N >= (1LL << 31)) return fail(AT_ERR_ARG, "the adjoint needs N < 2^31");
     if (n_steps < 0) return fail(AT_ERR_ARG, "n_steps < 0");
     if (interval < 1) return fail(AT_ERR_ARG, "interval must be >= 1");
     return AT_OK;
@@ -920,15 +921,10 @@ int at_adjoint(at_solver *h, int64_t n_steps, int delay_mode, const int8_t *dela
 
     atk::AdjParams a{};
     a.levels = ws + al.levels;
-    a.depth = Dl;
     a.pend = ws + al.pend;
     a.dnu_part = reinterpret_cast<double *>(ws + al.dnu);
-    a.delays = delays;
     a.N = h->N; a.P = h->P; a.M = h->M;
     a.L = h->L; a.Tp = h->T;
-    a.mode = delay_mode == AT_SEEDED ? 1 : delay_mode == AT_REPLAY ? 3 : 0;
-    a.per_sub = (h->g.flags & AT_FLAG_PER_SUBDOMAIN_DELAY) ? 1 : 0;
-    a.seed = h->g.seed;
     if (h->order == 2) {
         a.cA = h->dt / (2.0 * h->dx);
         a.cB = h->nu * h->dt / (h->dx * h->dx);
@@ -938,6 +934,7 @@ int at_adjoint(at_solver *h, int64_t n_steps, int delay_mode, const int8_t *dela
         a.cB = h->nu * h->dt / (12.0 * h->dx * h->dx);
         a.dtdx2 = h->dt / (12.0 * h->dx * h->dx);
     }
+    a.cAf = (float)a.cA; a.cBf = (float)a.cB; a.dtdx2f = (float)a.dtdx2;
     void *kern = atk_adjoint_kernel(h->w, h->order);
     unsigned char *cur = static_cast<unsigned char *>(lam), *other = ws + al.lam;
     for (int64_t seg = nseg - 1; seg >= 0; --seg) {
@@ -951,15 +948,22 @@ int at_adjoint(at_solver *h, int64_t n_steps, int delay_mode, const int8_t *dela
         }
         rc = at_set_history(h, ck + (size_t)seg * seg_bytes, Dc, c);
         if (rc != AT_OK) return rc;
-        int8_t *d = delay_mode == AT_REPLAY ? const_cast<int8_t *>(delays) + (size_t)c * h->P * 2 : nullptr;
+        // the recomputation replays the given delays or records the ones it
+        // draws; the adjoint reads them from there
+        int8_t *d = delay_mode == AT_REPLAY ? const_cast<int8_t *>(delays) + (size_t)c * h->P * 2
+                                            : reinterpret_cast<int8_t *>(ws + al.kbuf);
         rc = step_impl(h, end - c, delay_mode, d, ws + al.levels, Dl);
         if (rc != AT_OK) return rc;
+        a.delays = d;
+        a.k_level = c;
         for (int64_t n = end - 1; n >= c; --n) {
             a.n = n;
+            for (int q = 0; q < atk::kAdjMaxLevels; ++q)
+                a.lvl_off[q] = n - q >= 0 ? (long long)((n - q) % Dl) * h->N : 0;
             a.lam_in = cur;
             a.lam_out = other;
             void *args[] = {&a};
-            e = cudaLaunchKernel(kern, dim3(G), dim3(256), args, 0, h->stream);
+            e = cudaLaunchKernel(kern, dim3(adj_grid_x(h), adj_grid_y(h)), dim3(atk::kAdjThreads), args, 0, h->stream);
             if (e != cudaSuccess) return cuda_fail(e, "launch at_adjoint_step");
             unsigned char *t = cur; cur = other; other = t;
         }

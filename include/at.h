@@ -73,6 +73,11 @@ extern "C" {
 #define AT_FLAG_TEST_SKIP_PUBLISH   4  /* test only: CTA 0 stops publishing its
                                           progress flags after level test_skip_step,
                                           so that its neighbours' waits time out */
+#define AT_FLAG_VISCOUS_FP64        8  /* FP32 state: form the viscous term nu dt D2 u
+                                          and add it to u in FP64 (one rounding per
+                                          update).  Chosen automatically when
+                                          nu dt / dx^2 >= 0.8 x the stability limit */
+#define AT_FLAG_VISCOUS_FP32       16  /* FP32 state: never use FP64 for it */
 
 typedef struct at_solver at_solver;   /* opaque handle */
 
@@ -117,7 +122,7 @@ typedef struct at_info {
   int32_t sm_count;         /* SMs of the device                                   */
   int32_t dtype;            /* AT_F64 or AT_F32                                    */
   int32_t steps_per_pass;   /* levels per pass in AT_FREE                          */
-  int32_t reserved;
+  int32_t viscous_fp64;     /* 1 if the viscous term is accumulated in FP64        */
 } at_info;
 
 /* Bytes of workspace needed for this problem, or 0 if the arguments are

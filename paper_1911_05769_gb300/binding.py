@@ -38,6 +38,8 @@ AT_REPLAY = 3
 AT_FLAG_PER_SUBDOMAIN_DELAY = 1
 AT_FLAG_ALLOW_UNSTABLE = 2
 AT_FLAG_TEST_SKIP_PUBLISH = 4
+AT_FLAG_VISCOUS_FP64 = 8
+AT_FLAG_VISCOUS_FP32 = 16
 
 AT_NOALLOC_SCRATCH_BYTES = 8 * 1024 * 1024
 
@@ -59,7 +61,7 @@ class at_info(ctypes.Structure):
         ("order", ctypes.c_int32), ("L", ctypes.c_int32), ("R", ctypes.c_int32), ("s", ctypes.c_int32),
         ("T", ctypes.c_int32), ("ctas", ctypes.c_int32), ("threads", ctypes.c_int32), ("stages", ctypes.c_int32),
         ("smem_bytes", ctypes.c_int64), ("step", ctypes.c_int64), ("sm_count", ctypes.c_int32),
-        ("dtype", ctypes.c_int32), ("steps_per_pass", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("dtype", ctypes.c_int32), ("steps_per_pass", ctypes.c_int32), ("viscous_fp64", ctypes.c_int32),
     ]
 
 

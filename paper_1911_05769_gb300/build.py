@@ -1,8 +1,9 @@
 """Builds the CUDA library ``libat.so`` in-tree for sm_103a with nvcc.
 
-Six translation units (host ABI; FP32 and FP64 single-domain kernels; FP32
-and FP64 ensemble kernels; adjoint kernels) compiled in parallel, one
-``-gencode``; static CUDA runtime.  Run as
+Seven translation units (host ABI; FP32 and FP64 single-domain kernels; FP32
+and FP64 ensemble kernels; adjoint kernels; FP32 kernels with FP64 viscous
+accumulation) compiled in parallel, one ``-gencode``; static CUDA runtime.
+Run as
 ``python -m paper_1911_05769_gb300.build`` or through ``__graft_entry__.build()``.
 """
 from __future__ import annotations
@@ -17,7 +18,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libat.so")
 SOURCES = [os.path.join(CSRC, f) for f in (
-    "at_api.cu", "at_kernels_f32.cu", "at_kernels_f64.cu", "at_batch_f32.cu", "at_batch_f64.cu", "at_adjoint.cu")]
+    "at_api.cu", "at_kernels_f32.cu", "at_kernels_f64.cu", "at_batch_f32.cu", "at_batch_f64.cu", "at_adjoint.cu",
+    "at_kernels_f32v.cu")]
 DEPS = SOURCES + [os.path.join(CSRC, f) for f in ("at_kernels.cuh", "at_device.cuh", "at_adjoint.cuh")] + [
     os.path.join(INCLUDE, "at.h")]
 

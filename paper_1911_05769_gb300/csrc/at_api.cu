@@ -19,6 +19,7 @@
 #include "at_kernels.cuh"
 
 void *atk_stepper_kernel_f32(int order, int gw, bool forced, bool full);
+void *atk_stepper_kernel_f32v(int order, int gw, bool forced, bool full);
 void *atk_stepper_kernel_f64(int order, int gw, bool forced, bool full);
 void *atk_init_kernel_f32(int order);
 void *atk_init_kernel_f64(int order);
@@ -116,9 +117,20 @@ int groups_per_lane(int64_t M)
     return g;
 }
 
-// The stepper and init kernels for a word size, order, subdomain size and
-// forcing (instantiated in at_kernels_f32.cu / at_kernels_f64.cu).
-void pick_kernels(int w, int order, int64_t M, bool forced, void **stepper, void **init)
+// Whether an FP32-state solver accumulates the viscous term in FP64: forced
+// by the flags, else when nu dt / dx^2 reaches 0.8 of the stability limit.
+bool viscous_fp64(int w, int order, uint32_t flags, double D)
+{
+    if (w != 4 || (flags & AT_FLAG_VISCOUS_FP32)) return false;
+    if (flags & AT_FLAG_VISCOUS_FP64) return true;
+    const double lim = order == 2 ? 0.5 : 0.375;
+    return D >= 0.8 * lim;
+}
+
+// The stepper and init kernels for a word size, order, subdomain size,
+// forcing and viscous precision (instantiated in at_kernels_f32.cu,
+// at_kernels_f32v.cu and at_kernels_f64.cu).
+void pick_kernels(int w, int order, int64_t M, bool forced, bool v64, void **stepper, void **init)
 {
     const int gw = groups_per_lane(M);
     const bool full = (M == 128LL * gw);
@@ -126,7 +138,7 @@ void pick_kernels(int w, int order, int64_t M, bool forced, void **stepper, void
         *stepper = atk_stepper_kernel_f64(order, gw, forced, full);
         *init = atk_init_kernel_f64(order);
     } else {
-        *stepper = atk_stepper_kernel_f32(order, gw, forced, full);
+        *stepper = v64 ? atk_stepper_kernel_f32v(order, gw, forced, full) : atk_stepper_kernel_f32(order, gw, forced, full);
         *init = atk_init_kernel_f32(order);
     }
 }
@@ -204,6 +216,7 @@ struct at_solver {
     int64_t step;              // steps launched since at_set_state (host count)
     int64_t flags_E;           // PEs of the launch that last released flags (0: none since the state was set)
     bool has_state;
+    bool v64;                  // FP32 state with FP64 viscous accumulation
     bool batch;                // ensemble of instances
     int64_t n_inst;
     int lmin;                  // smallest delay bound (ensembles), else L
@@ -313,8 +326,9 @@ int at_create(const at_grid *grid, int64_t P, int scheme_order, int L, double nu
     h->stream = static_cast<cudaStream_t>(grid->stream);
     h->device = dev; h->sm_count = sms; h->smem_optin = smem_optin;
     h->batch = false; h->n_inst = 0; h->lmin = L;
+    h->v64 = viscous_fp64(w, scheme_order, (uint32_t)grid->flags, nu * dt / (dx * dx));
 
-    pick_kernels(w, scheme_order, h->M, grid->forcing_amp != 0.0, &h->kernel, &h->init_kernel);
+    pick_kernels(w, scheme_order, h->M, grid->forcing_amp != 0.0, h->v64, &h->kernel, &h->init_kernel);
 
     // launch shape: by default as many CTAs of kWarps processing elements
     // (warps) as can be resident, at most one PE per subdomain; `stages`
@@ -518,6 +532,7 @@ int at_get_info(const at_solver *h, at_info *info)
     info->ctas = h->G; info->threads = atk::kThreads; info->stages = h->stages;
     info->smem_bytes = h->smem; info->step = h->step; info->sm_count = h->sm_count;
     info->dtype = h->g.dtype; info->steps_per_pass = h->sb;
+    info->viscous_fp64 = h->v64 ? 1 : 0;
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     if (h->has_state && cudaStreamIsCapturing(h->stream, &cap) == cudaSuccess && cap == cudaStreamCaptureStatusNone) {
         long long n0 = 0;
@@ -1077,7 +1092,8 @@ extern "C" int at_step_noalloc(const at_grid *grid, int64_t P, int scheme_order,
     h.stream = static_cast<cudaStream_t>(grid->stream);
     h.device = dev; h.sm_count = sms; h.smem_optin = smem_optin;
     h.batch = false; h.n_inst = 0; h.lmin = L;
-    pick_kernels(w, scheme_order, h.M, grid->forcing_amp != 0.0, &h.kernel, &h.init_kernel);
+    h.v64 = viscous_fp64(w, scheme_order, (uint32_t)grid->flags, nu * dt / (dx * dx));
+    pick_kernels(w, scheme_order, h.M, grid->forcing_amp != 0.0, h.v64, &h.kernel, &h.init_kernel);
     int stages = grid->stages > 0 ? grid->stages : 3;
     if (stages < atk::kMinStages) stages = atk::kMinStages;
     rc = launch_shape(h.M, w, P, tab_size(h.M, w, grid->forcing_amp != 0.0, false), grid->max_ctas, stages, sms,

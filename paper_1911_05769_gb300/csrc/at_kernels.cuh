@@ -388,7 +388,11 @@ static __device__ __noinline__ T exact_ghost(const BatchInst *binst, const Batch
 // names no neighbour takes the instance's exact boundary values, undelayed;
 // a face whose neighbour is another PE's, or not the next subdomain in the
 // sweep (a periodic instance's wrap-around), goes through the flags.
-template <typename T, int ORDER, int GW, bool FORCED, bool FULL, bool BATCH>
+//
+// V64 (FP32 state only): the viscous term nu dt D2(u) is formed from the
+// stencil values in FP64 and added to u in FP64, rounded to FP32 once per
+// update (for runs close to the diffusive stability limit).
+template <typename T, int ORDER, int GW, bool FORCED, bool FULL, bool BATCH, bool V64>
 __device__ void run_pe(const Params &p, const Sweep &sw, long long lo, long long hi, uint64_t *bars, unsigned *hist,
                        unsigned char *raw, unsigned char *stages, const T *sj, const T *cj, const T *spt,
                        const T *cpt, const BatchSub *btab, int *s_count, volatile long long *s_epoch)
@@ -414,6 +418,7 @@ __device__ void run_pe(const Params &p, const Sweep &sw, long long lo, long long
     const int m_last = FULL ? GW - 1 : (NG - 1) >> 5;
     const int lane_last = FULL ? 31 : (NG - 1) & 31;
     const T cA0 = (T)p.cA, cB0 = (T)p.cB;
+    const double cB64_0 = p.cB;
     const size_t tile_bytes = (size_t)p.M * sizeof(T);
     const size_t slot_stride = (size_t)p.P * 2 * kRingEntry;
     const int up = (lane + 31) & 31, down = (lane + 1) & 31;
@@ -600,11 +605,13 @@ __device__ void run_pe(const Params &p, const Sweep &sw, long long lo, long long
         const int len = C.len;
         T *ug = reinterpret_cast<T *>(p.u) + (size_t)j * p.M;
         T cA = cA0, cB = cB0;
+        double cB64 = cB64_0;
         bool bnd0 = false, bnd1 = false;
         if constexpr (BATCH) {
             const BatchSub &b = btab[j - lo];
             cA = (T)b.cA;
             cB = (T)b.cB;
+            cB64 = b.cB;
             bnd0 = b.left < 0;
             bnd1 = b.right < 0;
         }
@@ -692,9 +699,23 @@ __device__ void run_pe(const Params &p, const Sweep &sw, long long lo, long long
                         a = (T)8 * (v[e + 3] - v[e + 1]) - (v[e + 4] - v[e]);
                         b = (T)16 * (v[e + 3] + v[e + 1]) - (v[e + 4] + v[e]) - (T)30 * cc;
                     }
-                    T du = cB * b - cA * cc * a;
-                    if constexpr (FORCED) du = fs * c4[e] + (fc * s4[e] + du);   // two fused multiply-adds
-                    c[m][e] = cc + du;
+                    if constexpr (V64) {
+                        double b64;
+                        if constexpr (ORDER == 2) {
+                            b64 = ((double)v[e + 2] + (double)v[e]) - 2.0 * (double)cc;
+                        } else {
+                            b64 = 16.0 * ((double)v[e + 3] + (double)v[e + 1]) - ((double)v[e + 4] + (double)v[e]) -
+                                  30.0 * (double)cc;
+                        }
+                        T rest = -cA * cc * a;
+                        if constexpr (FORCED) rest = fs * c4[e] + (fc * s4[e] + rest);
+                        c[m][e] = (T)((double)cc + (cB64 * b64 + (double)rest));
+                        (void)b;
+                    } else {
+                        T du = cB * b - cA * cc * a;
+                        if constexpr (FORCED) du = fs * c4[e] + (fc * s4[e] + du);   // two fused multiply-adds
+                        c[m][e] = cc + du;
+                    }
                 }
 #pragma unroll
                 for (int q = 0; q < R; ++q) rb[q] = (m == m_last) ? c[m][4 - R + q] : rb[q];
@@ -762,7 +783,7 @@ __device__ void run_pe(const Params &p, const Sweep &sw, long long lo, long long
 // ---------------------------------------------------------------------------
 // the persistent kernel
 // ---------------------------------------------------------------------------
-template <typename T, int ORDER, int GW, bool FORCED, bool FULL, bool BATCH>
+template <typename T, int ORDER, int GW, bool FORCED, bool FULL, bool BATCH, bool V64>
 __global__ void __launch_bounds__(kThreads, AT_MIN_CTAS_PER_SM) at_stepper(const Params p)
 {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -820,8 +841,8 @@ __global__ void __launch_bounds__(kThreads, AT_MIN_CTAS_PER_SM) at_stepper(const
         if (sw.sb > lmin + 1) sw.sb = lmin + 1;
     }
     __syncthreads();
-    run_pe<T, ORDER, GW, FORCED, FULL, BATCH>(p, sw, lo, hi, bars, hist, raw, stages, sj, cj, spt, cpt, btab,
-                                              &s_count, &s_epoch);
+    run_pe<T, ORDER, GW, FORCED, FULL, BATCH, V64>(p, sw, lo, hi, bars, hist, raw, stages, sj, cj, spt, cpt, btab,
+                                                   &s_count, &s_epoch);
     // the last CTA to finish advances the level of the state and rearms the
     // grid barrier for the next launch (every CTA has read the level by now)
     __syncthreads();
@@ -901,35 +922,35 @@ __global__ void at_restore(const Params p, const T *levels, long long depth, lon
 // ---------------------------------------------------------------------------
 namespace atk {
 
-template <typename T, int ORDER, bool FORCED, bool FULL, bool BATCH>
+template <typename T, int ORDER, bool FORCED, bool FULL, bool BATCH, bool V64>
 void *stepper_gw(int gw)
 {
     switch (gw) {
-    case 1: return (void *)at_stepper<T, ORDER, 1, FORCED, FULL, BATCH>;
-    case 2: return (void *)at_stepper<T, ORDER, 2, FORCED, FULL, BATCH>;
-    case 4: return (void *)at_stepper<T, ORDER, 4, FORCED, FULL, BATCH>;
-    default: return (void *)at_stepper<T, ORDER, 8, FORCED, FULL, BATCH>;
+    case 1: return (void *)at_stepper<T, ORDER, 1, FORCED, FULL, BATCH, V64>;
+    case 2: return (void *)at_stepper<T, ORDER, 2, FORCED, FULL, BATCH, V64>;
+    case 4: return (void *)at_stepper<T, ORDER, 4, FORCED, FULL, BATCH, V64>;
+    default: return (void *)at_stepper<T, ORDER, 8, FORCED, FULL, BATCH, V64>;
     }
 }
 
-template <typename T, int ORDER, bool FORCED, bool BATCH>
+template <typename T, int ORDER, bool FORCED, bool BATCH, bool V64>
 void *stepper_full(int gw, bool full)
 {
-    return full ? stepper_gw<T, ORDER, FORCED, true, BATCH>(gw) : stepper_gw<T, ORDER, FORCED, false, BATCH>(gw);
+    return full ? stepper_gw<T, ORDER, FORCED, true, BATCH, V64>(gw) : stepper_gw<T, ORDER, FORCED, false, BATCH, V64>(gw);
 }
 
 // Stepper for stencil order 2|4, gw groups of 4 points per lane (1, 2, 4 or
 // 8), with or without forcing (single domain only), full tiles (M = 128 gw)
-// or not.
-template <typename T, bool BATCH>
+// or not; V64: FP64 viscous accumulation.
+template <typename T, bool BATCH, bool V64 = false>
 void *stepper_kernel(int order, int gw, bool forced, bool full)
 {
     if constexpr (BATCH) {
-        return order == 2 ? stepper_full<T, 2, false, true>(gw, full) : stepper_full<T, 4, false, true>(gw, full);
+        return order == 2 ? stepper_full<T, 2, false, true, V64>(gw, full) : stepper_full<T, 4, false, true, V64>(gw, full);
     } else {
         if (order == 2)
-            return forced ? stepper_full<T, 2, true, false>(gw, full) : stepper_full<T, 2, false, false>(gw, full);
-        return forced ? stepper_full<T, 4, true, false>(gw, full) : stepper_full<T, 4, false, false>(gw, full);
+            return forced ? stepper_full<T, 2, true, false, V64>(gw, full) : stepper_full<T, 2, false, false, V64>(gw, full);
+        return forced ? stepper_full<T, 4, true, false, V64>(gw, full) : stepper_full<T, 4, false, false, V64>(gw, full);
     }
 }
 

@@ -61,7 +61,7 @@ int main(void) {
   printf("at_info size %zu\n", sizeof(at_info));
   F(at_info, N); F(at_info, P); F(at_info, M); F(at_info, order); F(at_info, L); F(at_info, R); F(at_info, s);
   F(at_info, T); F(at_info, ctas); F(at_info, threads); F(at_info, stages); F(at_info, smem_bytes);
-  F(at_info, step); F(at_info, sm_count); F(at_info, dtype); F(at_info, steps_per_pass);
+  F(at_info, step); F(at_info, sm_count); F(at_info, dtype); F(at_info, steps_per_pass); F(at_info, viscous_fp64);
   printf("at_instance size %zu\n", sizeof(at_instance));
   F(at_instance, n); F(at_instance, L); F(at_instance, bc); F(at_instance, length); F(at_instance, origin);
   F(at_instance, nu); F(at_instance, dt); F(at_instance, tanh_a); F(at_instance, tanh_c); F(at_instance, tanh_xc);

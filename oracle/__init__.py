@@ -61,6 +61,13 @@ class Cfg(ctypes.Structure):
     ]
 
 
+class Cfg3(ctypes.Structure):
+    _fields_ = [
+        ("n", ctypes.c_int64 * 3), ("P", ctypes.c_int64 * 3), ("L", ctypes.c_int32), ("delay_mode", ctypes.c_int32),
+        ("nu", ctypes.c_double), ("dt", ctypes.c_double), ("dx", ctypes.c_double * 3), ("seed", ctypes.c_uint64),
+    ]
+
+
 def lib():
     global _lib
     with _lock:
@@ -87,6 +94,12 @@ def lib():
             L.at_oracle_adjoint.argtypes = [ctypes.POINTER(Cfg), ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
                                             ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                             ctypes.POINTER(ctypes.c_double)]
+            L.at_oracle_run3d.restype = ctypes.c_int
+            L.at_oracle_run3d.argtypes = [ctypes.POINTER(Cfg3), ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
+                                          ctypes.c_void_p, ctypes.c_void_p]
+            L.at_oracle_cfg3_size.restype = ctypes.c_int64
+            if L.at_oracle_cfg3_size() != ctypes.sizeof(Cfg3):
+                raise RuntimeError("oracle: 3D configuration struct layout mismatch")
             L.at_oracle_cfg_size.restype = ctypes.c_int64
             if L.at_oracle_cfg_size() != ctypes.sizeof(Cfg):
                 raise RuntimeError("oracle: configuration struct layout mismatch")
@@ -200,3 +213,31 @@ def adjoint(u0, lam_T, *, N=None, P, order, L, nu, dt, n_steps, x0=0.0, dx=None,
     if rc != 0:
         raise ValueError(f"oracle adjoint failed: rc={rc}")
     return u_T, lam_0, dnu.value
+
+
+def run3d(u0, *, P, L, nu, dt, n_steps, dx=None, length=2 * np.pi, delay_mode=SYNC, seed=0, replay=None):
+    """3D AT run (order 2, six faces per subdomain) of ``u0`` shaped
+    (n2, n1, n0) (x fastest) with P = (P0, P1, P2) subdomains per axis.
+    Returns ``(u, hist)`` with u of the same shape."""
+    u0 = np.ascontiguousarray(u0, dtype=np.float64)
+    n2, n1, n0 = u0.shape
+    if dx is None:
+        dx = (length / n0, length / n1, length / n2)
+    c = Cfg3()
+    c.n[0], c.n[1], c.n[2] = n0, n1, n2
+    c.P[0], c.P[1], c.P[2] = P
+    c.L, c.delay_mode, c.nu, c.dt = L, delay_mode, nu, dt
+    c.dx[0], c.dx[1], c.dx[2] = dx
+    c.seed = seed & (2**64 - 1)
+    NP = P[0] * P[1] * P[2]
+    rep = None
+    if delay_mode == REPLAY:
+        rep = np.ascontiguousarray(replay, dtype=np.int8)
+        if rep.size != n_steps * NP * 6:
+            raise ValueError("oracle run3d: replay array has the wrong size")
+    out = np.empty_like(u0)
+    hist = np.zeros(L + 1, dtype=np.int64)
+    rc = lib().at_oracle_run3d(ctypes.byref(c), n_steps, _dptr(rep), _dptr(u0), _dptr(out), _dptr(hist))
+    if rc != 0:
+        raise ValueError(f"oracle run3d failed: rc={rc}")
+    return out, hist

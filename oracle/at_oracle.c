@@ -403,3 +403,98 @@ int at_oracle_adjoint(const at_oracle_cfg *c, int64_t n_steps, const int8_t *rep
     free(U); free(G); free(K);
     return ORC_OK;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Three dimensions: u_t + u (u_x + u_y + u_z) = nu (u_xx + u_yy + u_zz)    */
+/* (the scalar 3D form of Eq. BS), periodic box of n0 x n1 x n2 points      */
+/* (index (k n1 + j) n0 + i, x fastest), split into P0 x P1 x P2 subdomains  */
+/* of m0 x m1 x m2 points; subdomain index (p2 P1 + p1) P0 + p0.  Order-2    */
+/* central differences along each axis (Sec. 3.2); a stencil point across   */
+/* one of the six faces (0: -x, 1: +x, 2: -y, 3: +y, 4: -z, 5: +z) takes the */
+/* neighbour's value extrapolated from levels n-k, n-k-1 with that face's   */
+/* delay (Eq. AT1/AT2, split form).  Delays per (level, subdomain, face):    */
+/* seeded with counter (n P + p) 6 + face, replayed, or zero.                */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    int64_t n[3];       /* points per axis                                    */
+    int64_t P[3];       /* subdomains per axis                                */
+    int32_t L;          /* maximal delay                                      */
+    int32_t delay_mode; /* 0: synchronous, 1: seeded, 2: replay               */
+    double nu, dt;
+    double dx[3];       /* spacing per axis                                   */
+    uint64_t seed;
+} at_oracle_cfg3;
+
+int at_oracle_run3d(const at_oracle_cfg3 *c, int64_t n_steps, const int8_t *replay,
+                    const double *u0, double *u_out, int64_t *hist)
+{
+    if (!c || n_steps < 0 || c->L < 0 || c->L > 64) return ORC_EARG;
+    int64_t m[3], NP = 1, N = 1;
+    for (int a = 0; a < 3; ++a) {
+        if (c->n[a] <= 0 || c->P[a] <= 0 || c->n[a] % c->P[a] != 0) return ORC_EARG;
+        m[a] = c->n[a] / c->P[a];
+        if (m[a] < 2) return ORC_EARG;
+        NP *= c->P[a];
+        N *= c->n[a];
+    }
+    const int s = 2;                   /* levels per halo approximation     */
+    const int depth = c->L + s + 1;
+    double *H = (double *)calloc((size_t)depth * (size_t)N, sizeof(double));
+    int8_t *K = (int8_t *)malloc((size_t)NP * 6);
+    if (!H || !K) { free(H); free(K); return ORC_ENOMEM; }
+    memcpy(H, u0, (size_t)N * sizeof(double));
+    if (hist) memset(hist, 0, (size_t)(c->L + 1) * sizeof(int64_t));
+    const int64_t n0 = c->n[0], n1 = c->n[1], n2 = c->n[2];
+    for (int64_t n = 0; n < n_steps; ++n) {
+        const double *cur = H + (size_t)(n % depth) * N;
+        double *nxt = H + (size_t)((n + 1) % depth) * N;
+        /* the six delays of every subdomain at this level */
+        for (int64_t p = 0; p < NP; ++p) {
+            for (int f = 0; f < 6; ++f) {
+                int kr = 0;
+                if (c->delay_mode == 1) kr = at_oracle_seeded_delay(c->seed, n, p, NP, f, 6, c->L);
+                else if (c->delay_mode == 2) kr = replay[((size_t)n * NP + p) * 6 + f];
+                if (kr < 0 || kr > c->L) { free(H); free(K); return ORC_EDELAY; }
+                int64_t kmax = n - s + 1; if (kmax < 0) kmax = 0;
+                K[p * 6 + f] = (int8_t)((kr < kmax) ? kr : kmax);
+                if (hist) hist[K[p * 6 + f]] += 1;
+            }
+        }
+        for (int64_t k = 0; k < n2; ++k)
+            for (int64_t j = 0; j < n1; ++j)
+                for (int64_t i = 0; i < n0; ++i) {
+                    const int64_t idx[3] = {i, j, k};
+                    const int64_t p = ((k / m[2]) * c->P[1] + j / m[1]) * c->P[0] + i / m[0];
+                    const double u = cur[(k * n1 + j) * n0 + i];
+                    double d1 = 0.0, d2 = 0.0;
+                    for (int a = 0; a < 3; ++a) {
+                        double v[2];    /* neighbour below and above along axis a */
+                        for (int side = 0; side < 2; ++side) {
+                            int64_t q[3] = {i, j, k};
+                            q[a] = wrap(idx[a] + (side ? 1 : -1), c->n[a]);
+                            const int64_t src = (q[2] * n1 + q[1]) * n0 + q[0];
+                            const int64_t loc = idx[a] % m[a] + (side ? 1 : -1);
+                            if (loc >= 0 && loc < m[a]) {      /* same subdomain: level n */
+                                v[side] = cur[src];
+                                continue;
+                            }
+                            const int kf = K[p * 6 + 2 * a + side];
+                            double lev[2];
+                            for (int t = 0; t < s; ++t) {
+                                const int64_t lv = n - kf - t;
+                                lev[t] = (lv >= 0) ? H[(size_t)(lv % depth) * N + src] : 0.0;
+                            }
+                            v[side] = at_oracle_extrapolate(s, kf, 1, lev);
+                        }
+                        d1 += (v[1] - v[0]) / (2.0 * c->dx[a]);
+                        d2 += (v[1] - 2.0 * u + v[0]) / (c->dx[a] * c->dx[a]);
+                    }
+                    nxt[(k * n1 + j) * n0 + i] = u + c->dt * (-u * d1 + c->nu * d2);
+                }
+    }
+    memcpy(u_out, H + (size_t)(n_steps % depth) * N, (size_t)N * sizeof(double));
+    free(H); free(K);
+    return ORC_OK;
+}
+
+int64_t at_oracle_cfg3_size(void) { return (int64_t)sizeof(at_oracle_cfg3); }

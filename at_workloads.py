@@ -23,6 +23,7 @@ Workloads (1D viscous Burgers on the periodic interval [0, 2 pi)):
   4 dx wide), xc = 0; seed 6.
 
 * ``burgers1d_adjoint_n2p20``: see ``adjoint_workload``.
+* ``burgers3d_n512``: see ``u0_spectral3d``.
 
 The paper's own runs (3D Burgers' turbulence from a multi-scale sinusoidal
 initial condition, Sec. 3.1) use no dataset; these fields stand in for them.
@@ -162,6 +163,27 @@ def adjoint_workload(N: int = 1 << 20, M: int = 1024) -> dict:
     nu = 0.01
     return dict(name="burgers1d_adjoint_n2p20", N=N, P=N // M, order=2, L=2, nu=nu, seed=7, n_steps=2000,
                 interval=100, u0=u0, u0_target=u0 + 0.01 * q, nu_target=1.05 * nu, dt=dt_rule(u0, dx, nu))
+
+
+def u0_spectral3d(n: int, seed: int = 4, kmax: int = 32) -> np.ndarray:
+    """Periodic n^3 field (shape (n, n, n), x fastest) with energy spectrum
+    E(k) ~ k^-5/3 for 1 <= |k| <= kmax: every wavevector in that shell gets
+    amplitude |k|^-11/6 and a uniform random phase (seeded), the real field is
+    the inverse real FFT, normalised to max |u0| = 1 (the workload
+    ``burgers3d_n512``: n = 512, nu = 5e-3, subdomains of 32^3, order 2, L = 2,
+    seed 4, 2000 steps)."""
+    rng = np.random.default_rng(seed)
+    km = min(kmax, n // 2 - 1)
+    k1 = np.arange(-km, km + 1)
+    kz = np.arange(0, km + 1)
+    KX, KY, KZ = np.meshgrid(k1, k1, kz, indexing="ij")
+    kk = np.sqrt(KX ** 2 + KY ** 2 + KZ ** 2)
+    amp = np.where((kk >= 1) & (kk <= kmax), np.power(np.maximum(kk, 1.0), -11.0 / 6.0), 0.0)
+    phase = rng.uniform(0.0, TWO_PI, size=amp.shape)
+    X = np.zeros((n, n, n // 2 + 1), dtype=np.complex128)
+    X[np.ix_(k1 % n, k1 % n, kz)] = amp * np.exp(1j * phase)
+    u = np.fft.irfftn(X, s=(n, n, n), axes=(0, 1, 2))
+    return u / np.max(np.abs(u))
 
 
 def random_delays(n_steps: int, P: int, L: int, seed: int, faces: int = 2) -> np.ndarray:

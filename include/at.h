@@ -84,7 +84,7 @@ typedef struct at_solver at_solver;   /* opaque handle */
 /* Problem and execution description (the "grid" argument of at_create).
  * Zero-initialise it and set the fields that apply. */
 typedef struct at_grid {
-  int32_t  dim;             /* 1 (one-dimensional domain)                          */
+  int32_t  dim;             /* 1, or 3 (scalar 3D Burgers, order 2; see below)     */
   int32_t  bc;              /* AT_BC_PERIODIC                                      */
   int32_t  dtype;           /* AT_F64 or AT_F32                                    */
   int32_t  flags;           /* AT_FLAG_*                                           */
@@ -106,6 +106,8 @@ typedef struct at_grid {
   int32_t  steps_per_pass;  /* AT_FREE only: levels advanced per pass over a tile  */
                             /* (temporal blocking), 0 or 1 = none, at most L+1    */
   int32_t  reserved;
+  int64_t  sub[3];          /* dim 3: points per subdomain along x, y, z; n[a] a  */
+                            /* multiple of sub[a]; P = product of n[a] / sub[a]   */
 } at_grid;
 
 /* Launch facts of a solver, for tests and benchmarks. */
@@ -183,6 +185,21 @@ int at_destroy(at_solver *h);
 
 /* Message of the last failed call on this thread ("" if none). */
 const char *at_last_error(void);
+
+/* ---------------------------------------------------------------------------
+ * Three dimensions (grid->dim = 3): u_t + u (u_x + u_y + u_z) = nu lap u on a
+ * periodic box of n[0] x n[1] x n[2] points (x fastest in memory), split into
+ * subdomains of sub[0] x sub[1] x sub[2] points (sub[0] a multiple of 4,
+ * sub[0] * sub[1] <= 1024, sub[2] >= 3), numbered (p2 P1 + p1) P0 + p0.
+ * Order-2 central differences along each axis; a neighbour across any of the
+ * six faces (0: -x, 1: +x, 2: -y, 3: +y, 4: -z, 5: +z) is extrapolated from the
+ * levels n-k, n-k-1 of the neighbouring subdomain (Eq. AT1/AT2) with a delay
+ * per (level, subdomain, face); AT_SEEDED draws it at counter (n P + p) 6 +
+ * face.  at_create's P must equal the number of subdomains; scheme_order must
+ * be 2.  The delay arrays of at_step are [n_steps][P][6].  Stability limit
+ * for at_create: nu dt (1/dx^2 + 1/dy^2 + 1/dz^2) <= 1/2.  No forcing,
+ * temporal blocking, ensembles, adjoint or autotuner in 3D.
+ * --------------------------------------------------------------------------- */
 
 /* ---------------------------------------------------------------------------
  * Ensembles: many independent 1D problems advanced by one persistent launch.

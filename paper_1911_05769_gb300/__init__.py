@@ -21,7 +21,7 @@ from .binding import (AT_BC_EXACT_TANH, AT_BC_PERIODIC, AT_ERR_ARG, AT_ERR_CUDA,
                       at_workspace_bytes, library_path, at_adjoint, at_adjoint_workspace_bytes,
                       at_checkpoint_bytes, at_set_history, at_step_checkpointed, at_step_levels)
 from .adjoint import at_run
-from .solver import EnsembleSolver, Solver
+from .solver import EnsembleSolver, Solver, Solver3D
 
-__all__ = [n for n in dir() if n.startswith(("AT_", "at_"))] + ["AtError", "EnsembleSolver", "Solver",
+__all__ = [n for n in dir() if n.startswith(("AT_", "at_"))] + ["AtError", "EnsembleSolver", "Solver", "Solver3D",
                                                                    "library_path"]

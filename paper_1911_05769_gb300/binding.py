@@ -52,6 +52,7 @@ class at_grid(ctypes.Structure):
         ("workspace", ctypes.c_void_p), ("workspace_bytes", ctypes.c_size_t), ("stream", ctypes.c_void_p),
         ("timeout_ns", ctypes.c_int64), ("max_ctas", ctypes.c_int32), ("stages", ctypes.c_int32),
         ("test_skip_step", ctypes.c_int64), ("steps_per_pass", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("sub", ctypes.c_int64 * 3),
     ]
 
 

@@ -17,6 +17,7 @@
 #include "at.h"
 #include "at_adjoint.cuh"
 #include "at_kernels.cuh"
+#include "at_kernels3d.cuh"
 
 void *atk_stepper_kernel_f32(int order, int gw, bool forced, bool full);
 void *atk_stepper_kernel_f32v(int order, int gw, bool forced, bool full);
@@ -28,6 +29,8 @@ void *atk_batch_kernel_f64(int order, int gw, bool full);
 void *atk_restore_kernel_f32(int order);
 void *atk_restore_kernel_f64(int order);
 void *atk_adjoint_kernel(int w, int order);
+void *atk_stepper3d_kernel(int w, int tc);
+void *atk_init3d_kernel(int w);
 
 namespace {
 
@@ -87,10 +90,67 @@ Layout layout(int64_t N, int64_t P, int w, int L, int T, int64_t n_inst = 0)
     return l;
 }
 
+// ---- three dimensions -------------------------------------------------------
+struct Dims3 {
+    int64_t n[3], P[3];
+    int m[3];
+    int64_t face_words;
+};
+
+int check_args3(const at_grid *g, int64_t P, int order, int L, Dims3 *d)
+{
+    if (g->bc != AT_BC_PERIODIC) return fail(AT_ERR_ARG, "bc must be AT_BC_PERIODIC");
+    if (g->dtype != AT_F64 && g->dtype != AT_F32) return fail(AT_ERR_ARG, "dtype must be AT_F64 or AT_F32");
+    if (order != 2) return fail(AT_ERR_ARG, "3D solvers use scheme_order 2");
+    if (L < 0 || L > atk::kMaxL) return fail(AT_ERR_ARG, "L must be in 0..%d", atk::kMaxL);
+    if (g->forcing_amp != 0.0) return fail(AT_ERR_ARG, "3D solvers are unforced");
+    if (g->steps_per_pass > 1) return fail(AT_ERR_ARG, "3D solvers take one level per pass");
+    int64_t np = 1;
+    for (int a = 0; a < 3; ++a) {
+        if (g->n[a] <= 0 || g->sub[a] <= 0 || g->n[a] % g->sub[a] != 0)
+            return fail(AT_ERR_ARG, "axis %d: n=%lld is not a positive multiple of sub=%lld", a, (long long)g->n[a],
+                        (long long)g->sub[a]);
+        if (!(g->length[a] > 0.0)) return fail(AT_ERR_ARG, "length[%d] must be positive", a);
+        d->n[a] = g->n[a];
+        d->m[a] = (int)g->sub[a];
+        d->P[a] = g->n[a] / g->sub[a];
+        np *= d->P[a];
+    }
+    if (d->m[0] % 4 != 0) return fail(AT_ERR_ARG, "sub[0] must be a multiple of 4");
+    if ((int64_t)d->m[0] * d->m[1] > 1024) return fail(AT_ERR_ARG, "sub[0] * sub[1] must be <= 1024");
+    if (d->m[1] < 2 || d->m[2] < 3) return fail(AT_ERR_ARG, "sub[1] >= 2 and sub[2] >= 3 are required");
+    if (P != np) return fail(AT_ERR_ARG, "P=%lld differs from the %lld subdomains of the grid", (long long)P, (long long)np);
+    int64_t fw = (int64_t)d->m[1] * d->m[2];
+    if ((int64_t)d->m[0] * d->m[2] > fw) fw = (int64_t)d->m[0] * d->m[2];
+    if ((int64_t)d->m[0] * d->m[1] > fw) fw = (int64_t)d->m[0] * d->m[1];
+    d->face_words = (fw + 3) / 4 * 4;
+    return AT_OK;
+}
+
+Layout layout3(const Dims3 &d, int64_t P, int w, int L, int T)
+{
+    Layout l{};
+    size_t off = 0;
+    const int64_t N = d.n[0] * d.n[1] * d.n[2];
+    l.u = off;    off = align_up(off + (size_t)N * w, 256);
+    l.ring = off; off = align_up(off + (size_t)T * P * 6 * d.face_words * w, 256);
+    l.flag = off; off = align_up(off + (size_t)P * 6 * 8, 256);
+    l.ctrl = off; off = align_up(off + atk::kCtrlWords * 4, 256);
+    l.hist = off; off = align_up(off + (size_t)(L + 1) * 8, 256);
+    l.gbar = off; off = align_up(off + 8, 256);
+    l.bsub = off; l.binst = off;
+    l.total = off;
+    return l;
+}
+
 int check_args(const at_grid *g, int64_t P, int order, int L)
 {
     if (!g) return fail(AT_ERR_ARG, "grid is NULL");
-    if (g->dim != 1) return fail(AT_ERR_ARG, "dim must be 1");
+    if (g->dim == 3) {
+        Dims3 d;
+        return check_args3(g, P, order, L, &d);
+    }
+    if (g->dim != 1) return fail(AT_ERR_ARG, "dim must be 1 or 3");
     if (g->bc != AT_BC_PERIODIC) return fail(AT_ERR_ARG, "bc must be AT_BC_PERIODIC");
     if (g->dtype != AT_F64 && g->dtype != AT_F32) return fail(AT_ERR_ARG, "dtype must be AT_F64 or AT_F32");
     const int64_t N = g->n[0];
@@ -216,6 +276,9 @@ struct at_solver {
     int64_t step;              // steps launched since at_set_state (host count)
     int64_t flags_E;           // PEs of the launch that last released flags (0: none since the state was set)
     bool has_state;
+    int dim;                   // 1 or 3
+    Dims3 d3;                  // 3D: extents, subdomains, ring entry size
+    int tc;                    // 3D: columns per thread
     bool v64;                  // FP32 state with FP64 viscous accumulation
     bool batch;                // ensemble of instances
     int64_t n_inst;
@@ -279,7 +342,114 @@ size_t at_workspace_bytes(const at_grid *grid, int64_t P, int scheme_order, int 
     if (check_args(grid, P, scheme_order, L) != AT_OK) return 0;
     const int w = grid->dtype == AT_F64 ? 8 : 4;
     const int s = scheme_order / 2 + 1;
+    if (grid->dim == 3) {
+        Dims3 d;
+        check_args3(grid, P, scheme_order, L, &d);
+        return layout3(d, P, w, L, ring_slots(L, s)).total;
+    }
     return layout(grid->n[0], P, w, L, ring_slots(L, s)).total;
+}
+
+static int create3d(const at_grid *grid, int64_t P, int L, double nu, double dt, at_solver **out)
+{
+    Dims3 d;
+    int rc = check_args3(grid, P, 2, L, &d);
+    if (rc != AT_OK) return rc;
+    if (!(dt > 0.0) || !std::isfinite(dt)) return fail(AT_ERR_ARG, "dt must be positive");
+    if (!(nu >= 0.0) || !std::isfinite(nu)) return fail(AT_ERR_ARG, "nu must be >= 0");
+    double dx[3], sum = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        dx[a] = grid->length[a] / (double)d.n[a];
+        sum += 1.0 / (dx[a] * dx[a]);
+    }
+    if (!(grid->flags & AT_FLAG_ALLOW_UNSTABLE) && nu * dt * sum > 0.5)
+        return fail(AT_ERR_UNSTABLE, "nu*dt*(1/dx^2+1/dy^2+1/dz^2) = %g exceeds 1/2", nu * dt * sum);
+    const int w = grid->dtype == AT_F64 ? 8 : 4;
+    const int T = ring_slots(L, 2);
+    const Layout lay = layout3(d, P, w, L, T);
+    if (!grid->workspace) return fail(AT_ERR_ARG, "workspace is NULL");
+    if (grid->workspace_bytes < lay.total)
+        return fail(AT_ERR_ARG, "workspace too small: %zu < %zu", grid->workspace_bytes, lay.total);
+    if (reinterpret_cast<uintptr_t>(grid->workspace) % 256 != 0)
+        return fail(AT_ERR_ARG, "workspace must be 256-byte aligned");
+    int dev = 0, sms = 0, coop = 0, smem_optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (!coop) return fail(AT_ERR_RESIDENCY, "device does not support cooperative launch");
+
+    const int pw = d.m[0] * d.m[1];
+    const int tc = pw <= atk::kThreads3 ? 1 : pw <= 2 * atk::kThreads3 ? 2 : 4;
+    void *kern = atk_stepper3d_kernel(w, tc);
+    // plane buffers: at least 3 (planes z and z+1 in use, one arriving), at most sub[2]
+    int stages = grid->stages > 0 ? grid->stages : 4;
+    if (stages < 3) stages = 3;
+    if (stages > d.m[2]) stages = d.m[2];
+    atk::Smem3 sl3 = atk::smem3_layout(d.m[0], d.m[1], w, stages);
+    while (sl3.total > smem_optin && stages > 3) sl3 = atk::smem3_layout(d.m[0], d.m[1], w, --stages);
+    if (sl3.total > smem_optin) return fail(AT_ERR_RESIDENCY, "shared memory %lld exceeds %d", sl3.total, smem_optin);
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sl3.total);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
+    int occ = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, atk::kThreads3, (size_t)sl3.total);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+    int64_t G = grid->max_ctas > 0 ? grid->max_ctas : (int64_t)occ * sms;
+    if (G > P) G = P;
+    if (occ < 1 || (int64_t)occ * sms < G)
+        return fail(AT_ERR_RESIDENCY, "%lld CTAs cannot be co-resident (occupancy %d per SM)", (long long)G, occ);
+
+    at_solver *h = new (std::nothrow) at_solver();
+    if (!h) return fail(AT_ERR_ARG, "out of host memory");
+    h->g = *grid;
+    if (h->g.timeout_ns <= 0) h->g.timeout_ns = 1000000000ll;
+    h->dim = 3;
+    h->d3 = d;
+    h->tc = tc;
+    h->N = d.n[0] * d.n[1] * d.n[2];
+    h->P = P;
+    h->M = (int64_t)d.m[0] * d.m[1] * d.m[2];
+    h->order = 2; h->L = L; h->R = 1; h->s = 2; h->T = T; h->w = w;
+    h->nu = nu; h->dt = dt; h->dx = dx[0];
+    h->lay = lay;
+    h->ws = static_cast<unsigned char *>(grid->workspace);
+    h->stream = static_cast<cudaStream_t>(grid->stream);
+    h->device = dev; h->sm_count = sms; h->smem_optin = smem_optin;
+    h->kernel = kern;
+    h->init_kernel = atk_init3d_kernel(w);
+    h->G = (int)G;
+    h->stages = stages;
+    h->smem = (int)sl3.total;
+    h->sb = 1;
+    h->lmin = L;
+    *out = h;
+    return AT_OK;
+}
+
+static atk::Params3 make_params3(const at_solver *h)
+{
+    atk::Params3 p{};
+    p.u = h->ws + h->lay.u;
+    p.ring = h->ws + h->lay.ring;
+    p.flag = reinterpret_cast<unsigned long long *>(h->ws + h->lay.flag);
+    p.ctrl = reinterpret_cast<int *>(h->ws + h->lay.ctrl);
+    p.hist = reinterpret_cast<unsigned long long *>(h->ws + h->lay.hist);
+    p.gbar = reinterpret_cast<unsigned long long *>(h->ws + h->lay.gbar);
+    p.n0 = h->d3.n[0]; p.n1 = h->d3.n[1]; p.n2 = h->d3.n[2];
+    p.m0 = h->d3.m[0]; p.m1 = h->d3.m[1]; p.m2 = h->d3.m[2];
+    p.P0 = h->d3.P[0]; p.P1 = h->d3.P[1]; p.P2 = h->d3.P[2]; p.P = h->P;
+    p.L = h->L; p.T = h->T; p.stages = h->stages;
+    p.seed = h->g.seed;
+    for (int a = 0; a < 3; ++a) {
+        const double dxa = h->g.length[a] / (double)h->d3.n[a];
+        p.cA[a] = h->dt / (2.0 * dxa);
+        p.cB[a] = h->nu * h->dt / (dxa * dxa);
+    }
+    p.face_words = h->d3.face_words;
+    p.G = h->G;
+    p.timeout_ns = h->g.timeout_ns;
+    return p;
 }
 
 int at_create(const at_grid *grid, int64_t P, int scheme_order, int L, double nu, double dt, at_solver **out)
@@ -287,6 +457,7 @@ int at_create(const at_grid *grid, int64_t P, int scheme_order, int L, double nu
     g_err[0] = 0;
     if (!out) return fail(AT_ERR_ARG, "out is NULL");
     *out = nullptr;
+    if (grid && grid->dim == 3) return create3d(grid, P, L, nu, dt, out);
     int rc = check_args(grid, P, scheme_order, L);
     if (rc != AT_OK) return rc;
     if (!(dt > 0.0) || !std::isfinite(dt)) return fail(AT_ERR_ARG, "dt must be positive");
@@ -325,7 +496,7 @@ int at_create(const at_grid *grid, int64_t P, int scheme_order, int L, double nu
     h->ws = static_cast<unsigned char *>(grid->workspace);
     h->stream = static_cast<cudaStream_t>(grid->stream);
     h->device = dev; h->sm_count = sms; h->smem_optin = smem_optin;
-    h->batch = false; h->n_inst = 0; h->lmin = L;
+    h->batch = false; h->n_inst = 0; h->lmin = L; h->dim = 1;
     h->v64 = viscous_fp64(w, scheme_order, (uint32_t)grid->flags, nu * dt / (dx * dx));
 
     pick_kernels(w, scheme_order, h->M, grid->forcing_amp != 0.0, h->v64, &h->kernel, &h->init_kernel);
@@ -396,6 +567,18 @@ int at_set_state(at_solver *h, const void *u)
     if (!h || !u) return fail(AT_ERR_ARG, "NULL argument");
     cudaError_t e = cudaMemcpyAsync(h->ws + h->lay.u, u, (size_t)h->N * h->w, cudaMemcpyDefault, h->stream);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(state)");
+    if (h->dim == 3) {
+        atk::Params3 p = make_params3(h);
+        void *args[] = {&p};
+        const long long work = h->P * 6 * h->d3.face_words;
+        const int blocks = (int)((work + 255) / 256 < 4096 ? (work + 255) / 256 : 4096);
+        e = cudaLaunchKernel(h->init_kernel, dim3(blocks), dim3(256), args, 0, h->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "launch at_init3d");
+        h->step = 0;
+        h->flags_E = 0;
+        h->has_state = true;
+        return AT_OK;
+    }
     e = cudaMemsetAsync(h->ws + h->lay.ring, 0, (size_t)h->T * h->P * 2 * atk::kRingEntry, h->stream);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(ring)");
     atk::Params p = make_params(h);
@@ -417,6 +600,28 @@ static int step_impl(at_solver *h, int64_t n_steps, int delay_mode, int8_t *dela
     if (delay_mode < AT_SYNC || delay_mode > AT_REPLAY) return fail(AT_ERR_ARG, "bad delay_mode %d", delay_mode);
     if (delay_mode == AT_REPLAY && !delays) return fail(AT_ERR_ARG, "AT_REPLAY needs a delays array");
     if (n_steps == 0) return AT_OK;
+    if (h->dim == 3) {
+        if (levels) return fail(AT_ERR_ARG, "level output is for 1D solvers");
+        atk::Params3 p = make_params3(h);
+        p.mode = delay_mode;
+        p.delays = delays;
+        p.n_steps = n_steps;
+        cudaLaunchConfig_t cfg{};
+        cfg.gridDim = dim3(h->G);
+        cfg.blockDim = dim3(atk::kThreads3);
+        cfg.dynamicSmemBytes = (size_t)h->smem;
+        cfg.stream = h->stream;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeCooperative;
+        attr[0].val.cooperative = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        void *args[] = {&p};
+        const cudaError_t e = cudaLaunchKernelExC(&cfg, h->kernel, args);
+        if (e != cudaSuccess) return cuda_fail(e, "cooperative launch of at_stepper3d");
+        h->step += n_steps;
+        return AT_OK;
+    }
     atk::Params p = make_params(h);
     p.mode = delay_mode;
     p.delays = delays;
@@ -447,6 +652,7 @@ int at_set_history(at_solver *h, const void *levels, int64_t depth, int64_t leve
 {
     g_err[0] = 0;
     if (!h || !levels) return fail(AT_ERR_ARG, "NULL argument");
+    if (h->dim == 3) return fail(AT_ERR_ARG, "at_set_history is for 1D solvers");
     if (level < 0) return fail(AT_ERR_ARG, "level < 0");
     const int64_t need = level + 1 < h->L + h->s ? level + 1 : h->L + h->s;
     if (depth < need) return fail(AT_ERR_ARG, "depth %lld holds fewer than the %lld levels needed", (long long)depth,
@@ -527,6 +733,7 @@ int at_get_info(const at_solver *h, at_info *info)
 {
     if (!h || !info) return fail(AT_ERR_ARG, "NULL argument");
     std::memset(info, 0, sizeof(*info));
+    // (3D: M is the points per subdomain, sub[0] sub[1] sub[2])
     info->N = h->N; info->P = h->P; info->M = h->M;
     info->order = h->order; info->L = h->L; info->R = h->R; info->s = h->s; info->T = h->T;
     info->ctas = h->G; info->threads = atk::kThreads; info->stages = h->stages;
@@ -726,6 +933,7 @@ int at_tune(at_solver *h, int64_t n_steps, int delay_mode, at_tune_result *res)
 {
     g_err[0] = 0;
     if (!h || !res) return fail(AT_ERR_ARG, "NULL argument");
+    if (h->dim == 3) return fail(AT_ERR_ARG, "at_tune is for 1D solvers");
     if (!h->has_state) return fail(AT_ERR_STATE, "at_tune before at_set_state");
     if (n_steps <= 0) return fail(AT_ERR_ARG, "n_steps must be positive");
     if (delay_mode != AT_SYNC && delay_mode != AT_SEEDED && delay_mode != AT_FREE)
@@ -857,7 +1065,7 @@ AdjLayout adj_layout(const at_solver *h, int64_t interval)
 int check_adjoint_args(const at_solver *h, int64_t n_steps, int64_t interval)
 {
     if (!h) return fail(AT_ERR_ARG, "NULL handle");
-    if (h->batch) return fail(AT_ERR_ARG, "the adjoint covers single-domain solvers");
+    if (h->batch || h->dim == 3) return fail(AT_ERR_ARG, "the adjoint covers single-domain 1D solvers");
     if (h->N >= (1LL << 31)) return fail(AT_ERR_ARG, "the adjoint needs N < 2^31");
     if (n_steps < 0) return fail(AT_ERR_ARG, "n_steps < 0");
     if (interval < 1) return fail(AT_ERR_ARG, "interval must be >= 1");
@@ -1046,6 +1254,7 @@ extern "C" int at_step_noalloc(const at_grid *grid, int64_t P, int scheme_order,
                                void *u, int64_t n_steps, int delay_mode, int8_t *delays)
 {
     g_err[0] = 0;
+    if (grid && grid->dim != 1) return fail(AT_ERR_ARG, "at_step_noalloc is for 1D grids");
     int rc = check_args(grid, P, scheme_order, L);
     if (rc != AT_OK) return rc;
     if (!u) return fail(AT_ERR_ARG, "u is NULL");

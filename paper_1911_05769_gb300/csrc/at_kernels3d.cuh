@@ -1,0 +1,443 @@
+// at_kernels3d.cuh -- persistent AT stepper for the scalar 3D Burgers equation
+//     u_t + u (u_x + u_y + u_z) = nu (u_xx + u_yy + u_zz)
+// (the scalar form of Eq. BS in three dimensions) on a periodic box, order-2
+// central differences, AT halos on the six faces of every subdomain
+// (Eq. AT1/AT2 in split form, Sec. 3.2).
+//
+// The state keeps its natural layout (x fastest).  Subdomains of m0 x m1 x m2
+// points are numbered (p2 P1 + p1) P0 + p0.  Each CTA is one processing
+// element owning the subdomains [lo, hi) and sweeps them level by level.  A
+// tile (one subdomain at one level) is swept plane by plane along z: every
+// plane (m1 rows of m0 words) is brought into one of `stages` shared-memory
+// buffers by bulk copies (one per row, 16-byte aligned; completion counted on
+// the stage's mbarrier), several planes ahead.  A thread owns up to TC (x, y)
+// columns; it keeps the values of its columns at planes z-1, z, z+1 in
+// registers and reads x and y neighbours from the plane in shared memory.
+// Neighbours across a subdomain face come from the ring of face planes:
+// entry [slot][subdomain][face] holds the face's boundary values at level
+// slot (faces 0/1: the x = 0 / x = m0-1 planes indexed [z][y]; 2/3: y planes
+// [z][x]; 4/5: z planes [y][x]), extrapolated with the face's delay k from
+// levels n-k, n-k-1.  After a tile every face's progress flag is released.
+// The update is written in place; the next read of a plane is a bulk copy,
+// so writers fence the async proxy before it is issued.
+//
+// Delays: one per (level, subdomain, face): seeded (counter (n P + p) 6 + f),
+// replayed, free-running (read off the neighbour's flag, waiting only while
+// it lags by more than L), or zero with a grid barrier per level (Algorithm 1).
+// Every wait is bounded; on expiry the kernel latches the timeout status.
+#pragma once
+
+#include "at_kernels.cuh"
+
+namespace atk {
+
+constexpr int kThreads3 = 256;
+
+struct Params3 {
+    void *u;
+    unsigned char *ring;        // [T][P][6][face_words] words
+    unsigned long long *flag;   // [P][6]
+    int *ctrl;
+    unsigned long long *hist;
+    unsigned long long *gbar;
+    int8_t *delays;             // [n_steps][P][6]
+    long long n0, n1, n2;       // points per axis
+    int m0, m1, m2;             // points per subdomain per axis
+    long long P0, P1, P2, P;
+    int L, T, mode, stages;
+    long long n_steps;
+    unsigned long long seed;
+    double cA[3], cB[3];        // dt / (2 dx_a), nu dt / dx_a^2
+    long long face_words;       // words per ring entry (a multiple of 4)
+    int G;
+    long long timeout_ns;
+};
+
+// shared memory: mbarriers, delay counters, per-tile face data, plane stages
+struct Smem3 {
+    long long bar_off, hist_off, face_off, stage_off, plane_bytes, total;
+};
+
+__host__ __device__ inline Smem3 smem3_layout(int m0, int m1, int word, int stages)
+{
+    Smem3 l;
+    l.bar_off = 0;
+    l.hist_off = round_up(8LL * stages, 16);
+    l.face_off = round_up(l.hist_off + 4LL * (kMaxL + 1), 16);
+    l.stage_off = round_up(l.face_off + 6 * 16 + 16, 128);
+    l.plane_bytes = round_up((long long)m0 * m1 * word, 128);
+    l.total = l.stage_off + (long long)stages * l.plane_bytes;
+    return l;
+}
+
+static __device__ __noinline__ void raise_timeout3(const Params3 &p, int where, long long n, long long nb)
+{
+    if (atomicCAS(p.ctrl + kCtrlStatus, 0, kStatusTimeout) == 0) {
+        p.ctrl[kCtrlCta] = (int)blockIdx.x;
+        p.ctrl[kCtrlWhere] = where;
+        p.ctrl[kCtrlNb] = (int)nb;
+        p.ctrl[kCtrlStep] = (int)n;
+    }
+    atomicExch(p.ctrl + kCtrlAbort, 1);
+}
+
+static __device__ __noinline__ bool wait_flag3(const Params3 &p, const unsigned long long *fl, long long need,
+                                               unsigned long long *seen, long long n, long long nb)
+{
+    unsigned long long v = ld_acquire(fl);
+    if ((long long)v >= need) { *seen = v; return true; }
+    const unsigned long long t0 = global_ns();
+    unsigned ns = 32;
+    for (;;) {
+        __nanosleep(ns);
+        if (ns < 256) ns <<= 1;
+        v = ld_acquire(fl);
+        if ((long long)v >= need) { *seen = v; return true; }
+        if (ld_relaxed(p.ctrl + kCtrlAbort)) return false;
+        if ((long long)(global_ns() - t0) > p.timeout_ns) {
+            raise_timeout3(p, kWhereFlag, n, nb);
+            return false;
+        }
+    }
+}
+
+// all threads wait (bounded) for the bulk copies into a stage
+static __device__ __noinline__ bool wait_stage3(const Params3 &p, uint64_t *bar, unsigned parity)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    for (;;) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (ld_relaxed(p.ctrl + kCtrlAbort)) return false;
+        if ((long long)(global_ns() - t0) > p.timeout_ns) {
+            raise_timeout3(p, kWhereTile, -1, -1);
+            return false;
+        }
+    }
+}
+
+// grid barrier before level `step` (1-based within the launch), one arrival
+// per CTA; bounded.  Returns false on abort.
+static __device__ __noinline__ bool grid_sync3(const Params3 &p, long long step, int *s_flag)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(p.gbar, 1ull);
+        const unsigned long long target = (unsigned long long)step * (unsigned long long)p.G;
+        const unsigned long long t0 = global_ns();
+        int ok = 1;
+        while (ld_acquire(p.gbar) < target) {
+            if (ld_relaxed(p.ctrl + kCtrlAbort)) { ok = 0; break; }
+            if ((long long)(global_ns() - t0) > p.timeout_ns) { raise_timeout3(p, kWhereGrid, step, -1); ok = 0; break; }
+        }
+        __threadfence();
+        *s_flag = ok;
+    }
+    __syncthreads();
+    return *s_flag != 0;
+}
+
+// neighbour of subdomain (p0, p1, p2) across face f
+__device__ __forceinline__ long long face_neighbour(const Params3 &p, long long q0, long long q1, long long q2, int f)
+{
+    const int a = f >> 1, up = f & 1;
+    if (a == 0) q0 = up ? (q0 + 1 == p.P0 ? 0 : q0 + 1) : (q0 == 0 ? p.P0 - 1 : q0 - 1);
+    else if (a == 1) q1 = up ? (q1 + 1 == p.P1 ? 0 : q1 + 1) : (q1 == 0 ? p.P1 - 1 : q1 - 1);
+    else q2 = up ? (q2 + 1 == p.P2 ? 0 : q2 + 1) : (q2 == 0 ? p.P2 - 1 : q2 - 1);
+    return (q2 * p.P1 + q1) * p.P0 + q0;
+}
+
+template <typename T>
+__device__ __forceinline__ T *ring_entry(const Params3 &p, long long level, long long sub, int face)
+{
+    return reinterpret_cast<T *>(p.ring) +
+           (((size_t)(level & (p.T - 1)) * p.P + sub) * 6 + face) * (size_t)p.face_words;
+}
+
+template <typename T, int TC>
+__global__ void __launch_bounds__(kThreads3, 2) at_stepper3d(const Params3 p)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    const Smem3 sl = smem3_layout(p.m0, p.m1, (int)sizeof(T), p.stages);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + sl.bar_off);
+    unsigned *hist = reinterpret_cast<unsigned *>(smem + sl.hist_off);
+    int *s_k = reinterpret_cast<int *>(smem + sl.face_off);                  // [6] delays of the tile
+    long long *s_q = reinterpret_cast<long long *>(smem + sl.face_off + 32);  // [6] face neighbours
+    int *s_flag = reinterpret_cast<int *>(smem + sl.face_off + 80);          // barrier / abort word
+    unsigned char *stages = smem + sl.stage_off;
+
+    const int tid = threadIdx.x, lane = tid & 31;
+    const long long lo = (long long)blockIdx.x * p.P / p.G, hi = (long long)(blockIdx.x + 1) * p.P / p.G;
+    const long long S = hi - lo;
+    const long long lev0 = *reinterpret_cast<const volatile long long *>(p.ctrl + kCtrlN0);
+    const int NS = p.stages;
+    const int m0 = p.m0, m1 = p.m1, m2 = p.m2;
+    const int PW = m0 * m1;
+    const unsigned plane_bytes = (unsigned)(PW * (int)sizeof(T));
+    const long long Q = p.n_steps * S * m2;                 // planes this CTA sweeps
+    const T cA0 = (T)p.cA[0], cA1 = (T)p.cA[1], cA2 = (T)p.cA[2];
+    const T cB0 = (T)p.cB[0], cB1 = (T)p.cB[1], cB2 = (T)p.cB[2];
+    T *u = reinterpret_cast<T *>(p.u);
+
+    if (tid < NS) mbar_init(&bars[tid], 1);
+    if (tid == 0) { mbar_fence_init(); *s_flag = 0; }
+    for (int i = tid; i <= kMaxL; i += kThreads3) hist[i] = 0u;
+    __syncthreads();
+
+    // plane g -> (level, subdomain, z)
+    auto plane_of = [&](long long g, long long *lv, long long *sub, int *z) {
+        const long long t = g / m2;
+        *z = (int)(g - t * m2);
+        *lv = lev0 + t / S;
+        *sub = lo + t % S;
+    };
+    // warp 0 issues the bulk copies of plane g into stage g % NS
+    auto issue = [&](long long g) {
+        if (tid >= 32) return;
+        long long lv, sub;
+        int z;
+        plane_of(g, &lv, &sub, &z);
+        const long long q0 = sub % p.P0, q1 = (sub / p.P0) % p.P1, q2 = sub / (p.P0 * p.P1);
+        uint64_t *bar = &bars[g % NS];
+        if (lane == 0) mbar_arrive_expect_tx(bar, plane_bytes);
+        __syncwarp();
+        unsigned char *dst = stages + (size_t)(g % NS) * sl.plane_bytes;
+        const long long zg = q2 * m2 + z;
+        for (int y = lane; y < m1; y += 32) {
+            const T *src = u + ((size_t)zg * p.n1 + (size_t)(q1 * m1 + y)) * (size_t)p.n0 + (size_t)(q0 * m0);
+            bulk_load(dst + (size_t)y * m0 * sizeof(T), src, (unsigned)(m0 * sizeof(T)), bar);
+        }
+    };
+
+    // columns of this thread
+    int cx[TC], cy[TC];
+    bool cv[TC];
+#pragma unroll
+    for (int q = 0; q < TC; ++q) {
+        const int c = tid + kThreads3 * q;
+        cv[q] = c < PW;
+        cx[q] = cv[q] ? c % m0 : 0;
+        cy[q] = cv[q] ? c / m0 : 0;
+    }
+    T prev[TC], cur[TC];
+#pragma unroll
+    for (int q = 0; q < TC; ++q) prev[q] = cur[q] = (T)0;
+
+    long long issued = 0;
+    for (; issued < NS && issued < Q; ++issued) issue(issued);
+    // every thread waits (bounded) for the stages it reads; a failed wait is
+    // recorded and acted on by all threads after the next barrier
+    auto wait_plane = [&](long long g) {
+        if (g < Q && !wait_stage3(p, &bars[g % NS], (unsigned)((g / NS) & 1))) atomicExch(s_flag, -1);
+    };
+    wait_plane(0);
+    wait_plane(1);
+    __syncthreads();
+
+    bool ok = *s_flag != -1;
+    long long lv = lev0, sub = lo;
+    int z = 0;
+    long long s0 = 0, s1 = 0, s2 = 0;        // coordinates of the current subdomain
+    for (long long g = 0; g < Q && ok; ++g) {
+        if (z == 0) {
+            // ---- tile start: grid barrier (synchronous mode), delays, halos
+            if (p.mode == kModeSync && sub == lo && lv > lev0) {
+                if (!grid_sync3(p, lv - lev0, s_flag)) { ok = false; break; }
+            }
+            s0 = sub % p.P0; s1 = (sub / p.P0) % p.P1; s2 = sub / (p.P0 * p.P1);
+            if (tid < 6) {
+                const int f = tid;
+                const long long q = face_neighbour(p, s0, s1, s2, f);
+                long long kmax = lv - 2 + 1;           // s = 2 levels per extrapolation
+                if (kmax < 0) kmax = 0;
+                if (kmax > p.L) kmax = p.L;
+                long long k = 0;
+                if (p.mode == kModeSeeded) {
+                    const unsigned long long ctr = ((unsigned long long)lv * (unsigned long long)p.P +
+                                                    (unsigned long long)sub) * 6ull + (unsigned long long)f;
+                    k = (long long)(((splitmix64(p.seed, ctr) >> 32) * (unsigned long long)(p.L + 1)) >> 32);
+                } else if (p.mode == kModeReplay) {
+                    k = p.delays[((size_t)(lv - lev0) * p.P + sub) * 6 + f];
+                }
+                if (k > kmax) k = kmax;
+                if (k < 0) k = 0;
+                int good = 1;
+                if (p.mode != kModeSync) {
+                    const unsigned long long *fl = p.flag + q * 6 + (f ^ 1);
+                    const long long need = (p.mode == kModeFree) ? lv - kmax : lv - k;
+                    unsigned long long seen = ld_acquire(fl);
+                    if ((long long)seen < need && !wait_flag3(p, fl, need, &seen, lv, q)) good = 0;
+                    if (good && p.mode == kModeFree) k = lv - ((long long)seen < lv ? (long long)seen : lv);
+                }
+                if (good) {
+                    atomicAdd(&hist[k], 1u);
+                    if (p.delays && p.mode != kModeReplay) p.delays[((size_t)(lv - lev0) * p.P + sub) * 6 + f] = (int8_t)k;
+                }
+                s_k[f] = (int)k;
+                s_q[f] = q;
+                if (!good) atomicExch(s_flag, -1);
+            }
+            if (tid == 0 && p.mode == kModeSync) __threadfence();
+            __syncthreads();
+            if (*s_flag == -1) { ok = false; break; }
+            // plane z = -1: the -z neighbour's top plane, extrapolated
+            {
+                const int k4 = s_k[4];
+                const T *e0 = ring_entry<T>(p, lv - k4, s_q[4], 5);
+                const T *e1 = ring_entry<T>(p, lv - k4 - 1, s_q[4], 5);
+#pragma unroll
+                for (int q = 0; q < TC; ++q) {
+                    if (!cv[q]) continue;
+                    const int idx = cy[q] * m0 + cx[q];
+                    prev[q] = k4 == 0 ? e0[idx] : (T)(k4 + 1) * e0[idx] - (T)k4 * e1[idx];
+                }
+            }
+            // plane z = 0 of this tile (its stage was waited for two planes ago)
+            const T *st0 = reinterpret_cast<const T *>(stages + (size_t)(g % NS) * sl.plane_bytes);
+#pragma unroll
+            for (int q = 0; q < TC; ++q) cur[q] = cv[q] ? st0[cy[q] * m0 + cx[q]] : (T)0;
+        }
+        // ---- plane z: needs plane z+1 (stage, already waited for) or the +z halo
+        const bool top = (z == m2 - 1);
+        const T *st = reinterpret_cast<const T *>(stages + (size_t)(g % NS) * sl.plane_bytes);
+        const T *stn = reinterpret_cast<const T *>(stages + (size_t)((g + 1) % NS) * sl.plane_bytes);
+        const long long lnew = lv + 1;
+        const size_t zrow = (size_t)(s2 * m2 + z) * (size_t)p.n1;
+#pragma unroll
+        for (int q = 0; q < TC; ++q) {
+            if (!cv[q]) continue;
+            const int x = cx[q], y = cy[q], c = y * m0 + x;
+            const T cc = cur[q], below = prev[q];
+            T above;
+            if (!top) {
+                above = stn[c];
+            } else {
+                const int k5 = s_k[5];
+                const T *e0 = ring_entry<T>(p, lv - k5, s_q[5], 4);
+                above = e0[c];
+                if (k5 != 0) above = (T)(k5 + 1) * above - (T)k5 * ring_entry<T>(p, lv - k5 - 1, s_q[5], 4)[c];
+            }
+            T xm, xp, ym, yp;
+            if (x > 0) xm = st[c - 1];
+            else {
+                const int k = s_k[0];
+                const int e = z * m1 + y;
+                xm = ring_entry<T>(p, lv - k, s_q[0], 1)[e];
+                if (k != 0) xm = (T)(k + 1) * xm - (T)k * ring_entry<T>(p, lv - k - 1, s_q[0], 1)[e];
+            }
+            if (x < m0 - 1) xp = st[c + 1];
+            else {
+                const int k = s_k[1];
+                const int e = z * m1 + y;
+                xp = ring_entry<T>(p, lv - k, s_q[1], 0)[e];
+                if (k != 0) xp = (T)(k + 1) * xp - (T)k * ring_entry<T>(p, lv - k - 1, s_q[1], 0)[e];
+            }
+            if (y > 0) ym = st[c - m0];
+            else {
+                const int k = s_k[2];
+                const int e = z * m0 + x;
+                ym = ring_entry<T>(p, lv - k, s_q[2], 3)[e];
+                if (k != 0) ym = (T)(k + 1) * ym - (T)k * ring_entry<T>(p, lv - k - 1, s_q[2], 3)[e];
+            }
+            if (y < m1 - 1) yp = st[c + m0];
+            else {
+                const int k = s_k[3];
+                const int e = z * m0 + x;
+                yp = ring_entry<T>(p, lv - k, s_q[3], 2)[e];
+                if (k != 0) yp = (T)(k + 1) * yp - (T)k * ring_entry<T>(p, lv - k - 1, s_q[3], 2)[e];
+            }
+            const T d1 = cA0 * (xp - xm) + cA1 * (yp - ym) + cA2 * (above - below);
+            const T d2 = cB0 * ((xp + xm) - (T)2 * cc) + cB1 * ((yp + ym) - (T)2 * cc) + cB2 * ((above + below) - (T)2 * cc);
+            const T un = cc + (d2 - cc * d1);
+            u[(zrow + (size_t)(s1 * m1 + y)) * (size_t)p.n0 + (size_t)(s0 * m0 + x)] = un;
+            // boundary values of the new level into the ring
+            if (x == 0) ring_entry<T>(p, lnew, sub, 0)[z * m1 + y] = un;
+            if (x == m0 - 1) ring_entry<T>(p, lnew, sub, 1)[z * m1 + y] = un;
+            if (y == 0) ring_entry<T>(p, lnew, sub, 2)[z * m0 + x] = un;
+            if (y == m1 - 1) ring_entry<T>(p, lnew, sub, 3)[z * m0 + x] = un;
+            if (z == 0) ring_entry<T>(p, lnew, sub, 4)[c] = un;
+            if (top) ring_entry<T>(p, lnew, sub, 5)[c] = un;
+            prev[q] = cc;
+            cur[q] = above;
+        }
+        // stage g is free once every thread is past it; the next read of a
+        // plane written here is a bulk copy (async proxy)
+        fence_proxy_async_global();
+        wait_plane(g + 2);
+        __syncthreads();
+        if (*s_flag == -1) { ok = false; break; }
+        if (issued < Q) { issue(issued); ++issued; }
+        if (top) {
+            // ---- tile end: release the six faces' flags
+            if (tid == 0) {
+                __threadfence();
+                for (int f = 0; f < 6; ++f) st_release(p.flag + sub * 6 + f, (unsigned long long)lnew);
+            }
+            if (++sub == hi) { sub = lo; ++lv; }
+            z = 0;
+        } else {
+            ++z;
+        }
+    }
+    // let the copies in flight land before leaving
+    if (tid == 0) {
+        for (long long t = (issued > NS ? issued - NS : 0); t < issued; ++t) {
+            const unsigned long long t0 = global_ns();
+            while (!mbar_try_wait(&bars[t % NS], (unsigned)((t / NS) & 1)) &&
+                   (long long)(global_ns() - t0) < p.timeout_ns) {
+            }
+        }
+    }
+    __syncthreads();
+    if (tid <= p.L && tid <= kMaxL && hist[tid]) atomicAdd(p.hist + tid, (unsigned long long)hist[tid]);
+    (void)ok;
+    // the last CTA to finish advances the level and rearms the grid barrier
+    __syncthreads();
+    if (tid == 0) {
+        __threadfence();
+        if (atomicAdd(p.ctrl + kCtrlDone, 1) == p.G - 1) {
+            *reinterpret_cast<volatile long long *>(p.ctrl + kCtrlN0) = lev0 + p.n_steps;
+            *reinterpret_cast<volatile int *>(p.ctrl + kCtrlDone) = 0;
+            *reinterpret_cast<volatile unsigned long long *>(p.gbar) = 0ull;
+            __threadfence();
+        }
+    }
+}
+
+// level-0 ring entries of every face, flags and control block
+template <typename T>
+__global__ void at_init3d(const Params3 p)
+{
+    const int PWmax = (int)p.face_words;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long total = p.P * 6 * PWmax;
+    const T *u = reinterpret_cast<const T *>(p.u);
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += stride) {
+        const long long sub = t / (6 * PWmax);
+        const int f = (int)((t / PWmax) % 6);
+        const int e = (int)(t % PWmax);
+        const long long s0 = sub % p.P0, s1 = (sub / p.P0) % p.P1, s2 = sub / (p.P0 * p.P1);
+        int x, y, z;
+        if (f < 2) {            // [z][y]
+            if (e >= p.m1 * p.m2) continue;
+            z = e / p.m1; y = e % p.m1; x = f == 0 ? 0 : p.m0 - 1;
+        } else if (f < 4) {     // [z][x]
+            if (e >= p.m0 * p.m2) continue;
+            z = e / p.m0; x = e % p.m0; y = f == 2 ? 0 : p.m1 - 1;
+        } else {                // [y][x]
+            if (e >= p.m0 * p.m1) continue;
+            y = e / p.m0; x = e % p.m0; z = f == 4 ? 0 : p.m2 - 1;
+        }
+        const size_t gi = ((size_t)(s2 * p.m2 + z) * p.n1 + (size_t)(s1 * p.m1 + y)) * p.n0 + (size_t)(s0 * p.m0 + x);
+        ring_entry<T>(p, 0, sub, f)[e] = u[gi];
+        if (e == 0) p.flag[sub * 6 + f] = 0ull;
+    }
+    if (blockIdx.x == 0) {
+        if (threadIdx.x < kCtrlWords) p.ctrl[threadIdx.x] = 0;
+        if (threadIdx.x <= p.L) p.hist[threadIdx.x] = 0ull;
+        if (threadIdx.x == 0) *p.gbar = 0ull;
+    }
+}
+
+}  // namespace atk

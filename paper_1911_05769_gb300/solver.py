@@ -53,6 +53,7 @@ class Solver:
             raise B.AtError(rc, "at_create")
         self.h = h
         self.N, self.P, self.order, self.L = N, P, order, L
+        self.faces = 2
 
     def tune(self, n_steps, mode=B.AT_FREE):
         """Runs the launch-shape autotuner (at_tune) and returns its result.
@@ -77,11 +78,11 @@ class Solver:
         self._keep = t     # keep a host source alive until the stream passes the copy
 
     def step(self, n_steps, mode=B.AT_SEEDED, delays=None):
-        """delays: int8 device tensor [n_steps, P, 2] (input for REPLAY, record otherwise)."""
+        """delays: int8 device tensor [n_steps, P, faces] (input for REPLAY, record otherwise)."""
         ptr = None
         if delays is not None:
             assert delays.dtype == self.torch.int8 and delays.is_cuda and delays.is_contiguous()
-            assert delays.numel() == n_steps * self.P * 2
+            assert delays.numel() == n_steps * self.P * self.faces
             ptr = delays.data_ptr()
         rc = B.at_step(self.h, n_steps, mode, ptr)
         if rc != B.AT_OK:
@@ -178,6 +179,7 @@ class EnsembleSolver(Solver):
         if rc != B.AT_OK:
             raise B.AtError(rc, "at_create_batch")
         self.h = h
+        self.faces = 2
         self.N = sum(int(d["n"]) for d in instances)
         self.P = self.N // M
         self.order = order
@@ -185,3 +187,50 @@ class EnsembleSolver(Solver):
         self.offsets = [0]
         for d in instances:
             self.offsets.append(self.offsets[-1] + int(d["n"]))
+
+
+class Solver3D(Solver):
+    """Scalar 3D Burgers on a periodic box of n = (n0, n1, n2) points (x fastest)
+    in subdomains of sub = (m0, m1, m2) points, order 2, six AT faces per
+    subdomain.  The state is a flat tensor of n0 n1 n2 words (or shaped
+    (n2, n1, n0)); delays are [n_steps, P, 6]."""
+
+    def __init__(self, n, sub, L, nu, dt, *, dtype="f32", length=(2 * math.pi,) * 3, seed=0, flags=0,
+                 timeout_ns=0, max_ctas=0, stages=0, stream=None, device=None):
+        import torch
+        self.torch = torch
+        dev = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        self.device = dev
+        self.stream = stream if stream is not None else torch.cuda.current_stream(dev)
+        self.tdtype = torch.float64 if dtype == "f64" else torch.float32
+        g = B.at_grid()
+        g.dim, g.bc = 3, B.AT_BC_PERIODIC
+        g.dtype = B.AT_F64 if dtype == "f64" else B.AT_F32
+        g.flags = flags
+        for a in range(3):
+            g.n[a] = int(n[a])
+            g.sub[a] = int(sub[a])
+            g.length[a] = float(length[a])
+        g.seed = seed & (2 ** 64 - 1)
+        g.timeout_ns = timeout_ns
+        g.max_ctas = max_ctas
+        g.stages = stages
+        P = 1
+        for a in range(3):
+            P *= int(n[a]) // int(sub[a])
+        nbytes = B.at_workspace_bytes(g, P, 2, L)
+        if nbytes == 0:
+            raise B.AtError(B.AT_ERR_ARG, "at_workspace_bytes")
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+        g.workspace = self.workspace.data_ptr()
+        g.workspace_bytes = nbytes
+        g.stream = self.stream.cuda_stream
+        self.grid = g
+        rc, h = B.at_create(g, P, 2, L, nu, dt)
+        if rc != B.AT_OK:
+            raise B.AtError(rc, "at_create")
+        self.h = h
+        self.N = int(n[0]) * int(n[1]) * int(n[2])
+        self.P, self.order, self.L = P, 2, L
+        self.faces = 6
+        self.shape = (int(n[2]), int(n[1]), int(n[0]))

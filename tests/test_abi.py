@@ -57,7 +57,7 @@ int main(void) {
   F(at_grid, dim); F(at_grid, bc); F(at_grid, dtype); F(at_grid, flags); F(at_grid, n); F(at_grid, length);
   F(at_grid, origin); F(at_grid, forcing_amp); F(at_grid, seed); F(at_grid, workspace);
   F(at_grid, workspace_bytes); F(at_grid, stream); F(at_grid, timeout_ns); F(at_grid, max_ctas);
-  F(at_grid, stages); F(at_grid, test_skip_step); F(at_grid, steps_per_pass);
+  F(at_grid, stages); F(at_grid, test_skip_step); F(at_grid, steps_per_pass); F(at_grid, sub);
   printf("at_info size %zu\n", sizeof(at_info));
   F(at_info, N); F(at_info, P); F(at_info, M); F(at_info, order); F(at_info, L); F(at_info, R); F(at_info, s);
   F(at_info, T); F(at_info, ctas); F(at_info, threads); F(at_info, stages); F(at_info, smem_bytes);

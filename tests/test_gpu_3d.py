@@ -1,0 +1,126 @@
+"""The 3D stepper (scalar Burgers, order 2, AT halos on six faces) against the
+3D oracle, element by element, on seeded k^-5/3 fields."""
+import numpy as np
+import pytest
+
+import at_workloads as W
+import oracle
+from gpu_util import TOL, rel_linf
+
+pytestmark = pytest.mark.gpu
+
+
+def gpu_run3d(u0, *, sub, L, nu, dt, steps, dtype="f64", mode=None, seed=0, max_ctas=0, stages=0, delays=None,
+              record=False, calls=None):
+    import torch
+
+    from paper_1911_05769_gb300 import AT_OK, AT_REPLAY, AT_SEEDED, Solver3D, binding
+    mode = AT_SEEDED if mode is None else mode
+    n2, n1, n0 = u0.shape
+    s = Solver3D((n0, n1, n2), sub, L, nu, dt, dtype=dtype, seed=seed, max_ctas=max_ctas, stages=stages)
+    s.set_state(torch.from_numpy(np.ascontiguousarray(u0).ravel()).cuda())
+    calls = calls or [steps]
+    recs, done = [], 0
+    for c in calls:
+        d = None
+        if mode == AT_REPLAY:
+            d = torch.from_numpy(np.ascontiguousarray(delays[done:done + c])).cuda()
+        elif record:
+            d = torch.full((c, s.P, 6), -1, dtype=torch.int8, device="cuda")
+        s.step(c, mode, d)
+        if record and mode != AT_REPLAY:
+            recs.append(d)
+        done += c
+    out = torch.empty(s.N, dtype=s.tdtype, device="cuda")
+    rc = binding.at_state(s.h, out.data_ptr())
+    assert rc == AT_OK, binding.at_last_error()
+    hist, _, _ = s.delay_stats()
+    res = dict(u=out.double().cpu().numpy().reshape(u0.shape), hist=np.array(hist), info=s.info(), P=s.P)
+    if recs:
+        res["rec"] = np.concatenate([r.cpu().numpy() for r in recs], axis=0)
+    s.close()
+    return res
+
+
+# viscosity with a cell Peclet number max|u| dx / nu of about 2 (forward Euler
+# with central advection diverges far above that)
+NU = {24: 0.15, 32: 0.1, 256: 0.0125}
+
+
+def case(n, seed=4, kmax=8):
+    u0 = W.u0_spectral3d(n, seed=seed, kmax=kmax)
+    dx = 2 * np.pi / n
+    return u0, W.dt_rule(u0, dx, NU[n], dim=3)
+
+
+SHAPES = [
+    # (n, sub, max_ctas)
+    (32, (16, 16, 8), 0),
+    (32, (16, 16, 8), 3),            # several subdomains per CTA, uneven split
+    (32, (32, 8, 4), 5),
+    (24, (8, 4, 3), 0),              # 96 subdomains of 96 points; most threads idle
+    (32, (32, 32, 16), 0),           # 4 columns per thread
+]
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("n,sub,max_ctas", SHAPES)
+def test_seeded_3d_matches_oracle(dtype, n, sub, max_ctas):
+    from paper_1911_05769_gb300 import AT_SEEDED
+    u0, dt = case(n)
+    nu, L, steps = NU[n], 2, 40
+    P = tuple(n // m for m in sub)
+    g = gpu_run3d(u0, sub=sub, L=L, nu=nu, dt=dt, steps=steps, dtype=dtype, mode=AT_SEEDED, seed=5,
+                  max_ctas=max_ctas)
+    ref, hist = oracle.run3d(u0, P=P, L=L, nu=nu, dt=dt, n_steps=steps, delay_mode=oracle.SEEDED, seed=5)
+    assert rel_linf(g["u"], ref) <= TOL[dtype]
+    assert np.array_equal(g["hist"], hist)
+
+
+def test_sync_replay_and_free_3d():
+    from paper_1911_05769_gb300 import AT_FREE, AT_REPLAY, AT_SYNC
+    n, sub, L = 32, (16, 8, 8), 3
+    nu = NU[n]
+    u0, dt = case(n, seed=7)
+    P = tuple(n // m for m in sub)
+    NP = P[0] * P[1] * P[2]
+    steps = 36
+    g = gpu_run3d(u0, sub=sub, L=L, nu=nu, dt=dt, steps=steps, mode=AT_SYNC, max_ctas=4)
+    ref, _ = oracle.run3d(u0, P=P, L=L, nu=nu, dt=dt, n_steps=steps, delay_mode=oracle.SYNC)
+    assert rel_linf(g["u"], ref) <= TOL["f64"]
+    d = np.random.default_rng(3).integers(0, L + 1, size=(steps, NP, 6), dtype=np.int8)
+    g = gpu_run3d(u0, sub=sub, L=L, nu=nu, dt=dt, steps=steps, mode=AT_REPLAY, delays=d)
+    ref, _ = oracle.run3d(u0, P=P, L=L, nu=nu, dt=dt, n_steps=steps, delay_mode=oracle.REPLAY, replay=d)
+    assert rel_linf(g["u"], ref) <= TOL["f64"]
+    g = gpu_run3d(u0, sub=sub, L=L, nu=nu, dt=dt, steps=steps, mode=AT_FREE, record=True, max_ctas=5)
+    rec = g["rec"]
+    assert rec.min() >= 0 and rec.max() <= L
+    ref, _ = oracle.run3d(u0, P=P, L=L, nu=nu, dt=dt, n_steps=steps, delay_mode=oracle.REPLAY, replay=rec)
+    assert rel_linf(g["u"], ref) <= TOL["f64"]
+
+
+def test_multiple_calls_and_zero_delay_bound_3d():
+    from paper_1911_05769_gb300 import AT_SEEDED, AT_SYNC
+    n, sub = 32, (16, 16, 8)
+    nu = NU[n]
+    u0, dt = case(n, seed=9)
+    one = gpu_run3d(u0, sub=sub, L=2, nu=nu, dt=dt, steps=30, mode=AT_SEEDED, seed=2, max_ctas=3)
+    two = gpu_run3d(u0, sub=sub, L=2, nu=nu, dt=dt, steps=30, mode=AT_SEEDED, seed=2, max_ctas=3, calls=[11, 19])
+    assert np.array_equal(one["u"], two["u"])
+    a = gpu_run3d(u0, sub=sub, L=0, nu=nu, dt=dt, steps=20, mode=AT_SEEDED, seed=2)
+    b = gpu_run3d(u0, sub=sub, L=0, nu=nu, dt=dt, steps=20, mode=AT_SYNC)
+    assert np.array_equal(a["u"], b["u"])
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_large_box_3d(dtype):
+    """256^3 points in 32^3 subdomains (512 subdomains, the workload's
+    subdomain size, k^-5/3 field with |k| <= 32), seeded L = 2, 6 steps,
+    against the oracle over the whole box."""
+    from paper_1911_05769_gb300 import AT_SEEDED
+    n, sub, L, nu = 256, (32, 32, 32), 2, NU[256]
+    u0 = W.u0_spectral3d(n, seed=4, kmax=32)
+    dt = W.dt_rule(u0, 2 * np.pi / n, nu, dim=3)
+    g = gpu_run3d(u0, sub=sub, L=L, nu=nu, dt=dt, steps=6, dtype=dtype, mode=AT_SEEDED, seed=5)
+    ref, _ = oracle.run3d(u0, P=(8, 8, 8), L=L, nu=nu, dt=dt, n_steps=6, delay_mode=oracle.SEEDED, seed=5)
+    assert rel_linf(g["u"], ref) <= TOL[dtype]

@@ -66,6 +66,8 @@ def parse():
     ap.add_argument("--ens-time-steps", type=int, default=5000, help="time steps per ensemble launch")
     ap.add_argument("--no-tune", action="store_true", help="ensemble leg: keep the default launch shape")
     ap.add_argument("--adjoint-only", action="store_true", help="time only the adjoint leg")
+    ap.add_argument("--only-3d", action="store_true", help="time only the 3D leg")
+    ap.add_argument("--time-steps-3d", type=int, default=500, help="time steps per 3D launch")
     return ap.parse_args()
 
 
@@ -371,6 +373,69 @@ def adjoint_config(args, at, torch, dev):
     return res
 
 
+def config3d(args, at, torch, dev):
+    """3D scalar Burgers, 512^3 FP32 in 32^3 subdomains (4096), order 2, L = 2,
+    nu = 5e-3, k^-5/3 field (seed 4): launches of 500 steps (4 per 2000-step
+    run), free-running vs seeded vs synchronous; the FP32 error against the
+    FP64 oracle on a 128^3 box of the same recipe after 50 steps."""
+    n, sub, L, nu = 512, (32, 32, 32), 2, 5e-3
+    u0 = W.u0_spectral3d(n, seed=4, kmax=32)
+    dt = W.dt_rule(u0, 2 * np.pi / n, nu, dim=3)
+    u0_dev = torch.from_numpy(u0.ravel()).to(device=dev, dtype=torch.float32)
+    del u0
+    S = args.time_steps_3d
+    N = n ** 3
+    res = {"workload": "burgers3d_n512", "n": n, "sub": list(sub), "P": (n // sub[0]) ** 3, "L": L, "nu": nu,
+           "dt": dt, "dtype": "f32", "time_steps_per_launch": S}
+    stream = torch.cuda.Stream(device=dev)
+    for name, mode in (("free", at.AT_FREE), ("seeded", at.AT_SEEDED), ("sync", at.AT_SYNC)):
+        s = at.Solver3D((n, n, n), sub, L, nu, dt, dtype="f32", seed=5, stream=stream, device=dev.index)
+        with torch.cuda.stream(stream):
+            s.set_state(u0_dev)
+            s.step(S, mode)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        reps = max(1, min(args.steps, 4))
+        with torch.cuda.stream(stream):
+            ev[0].record(stream)
+            for _ in range(reps):
+                s.step(S, mode)
+            ev[1].record(stream)
+        torch.cuda.synchronize(dev)
+        ms = ev[0].elapsed_time(ev[1]) / reps
+        rc = s.status()
+        if rc != at.AT_OK:
+            raise RuntimeError(f"3D {name}: device status {rc}: {at.at_last_error()}")
+        fin = s.state()
+        info = s.info()
+        hist, m1, _ = s.delay_stats()
+        res[name] = {"value": N * S / (ms * 1e-3) / 1e9, "unit": UNIT, "ms_per_launch": ms, "mean_k": m1,
+                     "max_abs_u": float(fin.abs().max()), "ctas": info.ctas, "stages": info.stages}
+        s.close()
+    res["speedup_free_over_sync"] = res["free"]["value"] / res["sync"]["value"]
+    # algorithmic bytes per update: state read + write, plus the ring (each
+    # subdomain writes its 6 faces and reads 2 levels of 6 faces per level)
+    bpu = 2 * 4 + 18 * 4 / sub[0]
+    peak, src = hbm_peak()
+    res["roofline"] = {"bound": "hbm", "algorithmic_bytes_per_update": bpu,
+                       "achieved": res["free"]["value"] * bpu, "peak": peak, "unit": "GB/s",
+                       "frac": res["free"]["value"] * bpu / peak, "peak_source": src}
+    # FP32 against the FP64 oracle, 128^3 box in 32^3 subdomains, 50 seeded steps
+    import oracle
+    nb = 128
+    ub = W.u0_spectral3d(nb, seed=4, kmax=32)
+    nub = 0.02
+    dtb = W.dt_rule(ub, 2 * np.pi / nb, nub, dim=3)
+    s = at.Solver3D((nb, nb, nb), sub, L, nub, dtb, dtype="f32", seed=5, device=dev.index)
+    s.set_state(torch.from_numpy(ub.ravel()).to(dev))
+    s.step(50, at.AT_SEEDED)
+    g = s.state().double().cpu().numpy().reshape(ub.shape)
+    s.close()
+    ref, _ = oracle.run3d(ub, P=(4, 4, 4), L=L, nu=nub, dt=dtb, n_steps=50, delay_mode=oracle.SEEDED, seed=5)
+    res["err_vs_fp64_oracle"] = {"rel_linf": float(np.max(np.abs(g - ref)) / np.max(np.abs(ref))),
+                                 "box": [nb, nb, nb], "nu": nub, "steps": 50, "mode": "seeded"}
+    return res
+
+
 def reference_arm(args, ws, rank, pg):
     """--impl reference: the CPU oracle timed on this workload, bounded sample per step."""
     cfg = W.config(WORKLOAD)
@@ -617,6 +682,7 @@ def gpu_arm(args, ws, rank, local, pg):
         if rank == 0 and ws == 1:
             line["ensemble"] = ensemble_config(args, at, torch, dev, stream)
             line["adjoint"] = adjoint_config(args, at, torch, dev)
+            line["burgers3d"] = config3d(args, at, torch, dev)
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -630,6 +696,15 @@ def main():
         reference_arm(args, ws, rank, None)
         return
     ws, rank, local, pg = dist_setup(args)
+    if args.only_3d:
+        import torch
+
+        import paper_1911_05769_gb300 as at
+        from paper_1911_05769_gb300 import build as atbuild
+        atbuild.build()
+        torch.cuda.set_device(local)
+        print(json.dumps(config3d(args, at, torch, torch.device("cuda", local))), flush=True)
+        return
     if args.adjoint_only:
         import torch
 

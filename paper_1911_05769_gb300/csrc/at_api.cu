@@ -5,7 +5,9 @@
 // CTA is resident and the bounded waits between CTAs always make progress),
 // and launches the kernels on the caller's stream.  No device memory is
 // allocated here.
+#include <cuda.h>
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>
 
 #include <cmath>
 #include <cstdarg>
@@ -117,6 +119,7 @@ int check_args3(const at_grid *g, int64_t P, int order, int L, Dims3 *d)
         np *= d->P[a];
     }
     if (d->m[0] % 4 != 0) return fail(AT_ERR_ARG, "sub[0] must be a multiple of 4");
+    if (d->m[0] > 256 || d->m[1] > 256) return fail(AT_ERR_ARG, "sub[0] and sub[1] must be <= 256");
     if ((int64_t)d->m[0] * d->m[1] > 1024) return fail(AT_ERR_ARG, "sub[0] * sub[1] must be <= 1024");
     if (d->m[1] < 2 || d->m[2] < 3) return fail(AT_ERR_ARG, "sub[1] >= 2 and sub[2] >= 3 are required");
     if (P != np) return fail(AT_ERR_ARG, "P=%lld differs from the %lld subdomains of the grid", (long long)P, (long long)np);
@@ -279,6 +282,7 @@ struct at_solver {
     int dim;                   // 1 or 3
     Dims3 d3;                  // 3D: extents, subdomains, ring entry size
     int tc;                    // 3D: columns per thread
+    CUtensorMap tmap;          // 3D: tensor map of the state (planes of a subdomain)
     bool v64;                  // FP32 state with FP64 viscous accumulation
     bool batch;                // ensemble of instances
     int64_t n_inst;
@@ -387,8 +391,8 @@ static int create3d(const at_grid *grid, int64_t P, int L, double nu, double dt,
     int stages = grid->stages > 0 ? grid->stages : 4;
     if (stages < 3) stages = 3;
     if (stages > d.m[2]) stages = d.m[2];
-    atk::Smem3 sl3 = atk::smem3_layout(d.m[0], d.m[1], w, stages);
-    while (sl3.total > smem_optin && stages > 3) sl3 = atk::smem3_layout(d.m[0], d.m[1], w, --stages);
+    atk::Smem3 sl3 = atk::smem3_layout(d.m[0], d.m[1], d.m[2], w, stages);
+    while (sl3.total > smem_optin && stages > 3) sl3 = atk::smem3_layout(d.m[0], d.m[1], d.m[2], w, --stages);
     if (sl3.total > smem_optin) return fail(AT_ERR_RESIDENCY, "shared memory %lld exceeds %d", sl3.total, smem_optin);
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sl3.total);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
@@ -423,6 +427,28 @@ static int create3d(const at_grid *grid, int64_t P, int L, double nu, double dt,
     h->smem = (int)sl3.total;
     h->sb = 1;
     h->lmin = L;
+    // tensor map of the state: boxes of sub[0] x sub[1] x 1 points (one plane
+    // of a subdomain), encoded through the driver entry point of the runtime
+    PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    cudaDriverEntryPointQueryResult qres = cudaDriverEntryPointSymbolNotFound;
+    e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", reinterpret_cast<void **>(&encode), 12000,
+                                         cudaEnableDefault, &qres);
+    if (e != cudaSuccess || qres != cudaDriverEntryPointSuccess || !encode) {
+        delete h;
+        return fail(AT_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
+    }
+    const cuuint64_t gdim[3] = {(cuuint64_t)d.n[0], (cuuint64_t)d.n[1], (cuuint64_t)d.n[2]};
+    const cuuint64_t gstride[2] = {(cuuint64_t)(d.n[0] * w), (cuuint64_t)(d.n[0] * d.n[1] * w)};
+    const cuuint32_t box[3] = {(cuuint32_t)d.m[0], (cuuint32_t)d.m[1], 1u};
+    const cuuint32_t estride[3] = {1u, 1u, 1u};
+    const CUresult cr = encode(&h->tmap, w == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
+                               h->ws + lay.u, gdim, gstride, box, estride, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (cr != CUDA_SUCCESS) {
+        delete h;
+        return fail(AT_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)cr);
+    }
     *out = h;
     return AT_OK;
 }
@@ -616,7 +642,7 @@ static int step_impl(at_solver *h, int64_t n_steps, int delay_mode, int8_t *dela
         attr[0].val.cooperative = 1;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
-        void *args[] = {&p};
+        void *args[] = {&p, &h->tmap};
         const cudaError_t e = cudaLaunchKernelExC(&cfg, h->kernel, args);
         if (e != cudaSuccess) return cuda_fail(e, "cooperative launch of at_stepper3d");
         h->step += n_steps;

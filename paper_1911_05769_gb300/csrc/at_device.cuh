@@ -81,6 +81,17 @@ __device__ __forceinline__ void bulk_load(void *dst_smem, const void *src_gmem, 
                  : "memory");
 }
 
+// Tiled tensor copy (TMA): the box of a 3D tensor map at element coordinates
+// (x, y, z) into shared memory, completion counted on `bar`.  x times the
+// element size must be a multiple of 16 bytes.
+__device__ __forceinline__ void tensor_load_3d(void *dst_smem, const void *tmap, int x, int y, int z, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+        ::"r"(smem_addr(dst_smem)), "l"(tmap), "r"(x), "r"(y), "r"(z), "r"(smem_addr(bar))
+        : "memory");
+}
+
 // Orders this thread's earlier generic-proxy global accesses before later
 // async-proxy accesses (a bulk copy re-reading data written with st.global).
 __device__ __forceinline__ void fence_proxy_async_global()

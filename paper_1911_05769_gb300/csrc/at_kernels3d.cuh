@@ -8,9 +8,10 @@
 // points are numbered (p2 P1 + p1) P0 + p0.  Each CTA is one processing
 // element owning the subdomains [lo, hi) and sweeps them level by level.  A
 // tile (one subdomain at one level) is swept plane by plane along z: every
-// plane (m1 rows of m0 words) is brought into one of `stages` shared-memory
-// buffers by bulk copies (one per row, 16-byte aligned; completion counted on
-// the stage's mbarrier), several planes ahead.  A thread owns up to TC (x, y)
+// plane (an m0 x m1 box) is brought into one of `stages` shared-memory buffers
+// by one TMA tensor copy (3D tensor map over the state; completion counted on
+// the stage's mbarrier), several planes ahead; warps free a stage through a
+// second mbarrier.  A thread owns up to TC (x, y)
 // columns; it keeps the values of its columns at planes z-1, z, z+1 in
 // registers and reads x and y neighbours from the plane in shared memory.
 // Neighbours across a subdomain face come from the ring of face planes:
@@ -27,11 +28,16 @@
 // Every wait is bounded; on expiry the kernel latches the timeout status.
 #pragma once
 
+#include <cuda.h>   // CUtensorMap (the tensor map is encoded on the host)
+
 #include "at_kernels.cuh"
 
 namespace atk {
 
 constexpr int kThreads3 = 256;
+#ifndef AT_MIN_CTAS_3D
+#define AT_MIN_CTAS_3D 2      // resident CTAs per SM the 3D stepper is compiled for
+#endif
 
 struct Params3 {
     void *u;
@@ -53,18 +59,27 @@ struct Params3 {
     long long timeout_ns;
 };
 
-// shared memory: mbarriers, delay counters, per-tile face data, plane stages
+// shared memory: mbarriers, delay counters, per-tile face data, the six
+// extrapolated halo planes of the tile (x faces [z][y], y faces [z][x], z
+// faces [y][x]), plane stages
 struct Smem3 {
-    long long bar_off, hist_off, face_off, stage_off, plane_bytes, total;
+    long long bar_off, hist_off, face_off, halo_off, halo_words[6], halo_at[6], stage_off, plane_bytes, total;
 };
 
-__host__ __device__ inline Smem3 smem3_layout(int m0, int m1, int word, int stages)
+__host__ __device__ inline Smem3 smem3_layout(int m0, int m1, int m2, int word, int stages)
 {
     Smem3 l;
-    l.bar_off = 0;
-    l.hist_off = round_up(8LL * stages, 16);
+    l.bar_off = 0;                                   // full[stages], then empty[stages]
+    l.hist_off = round_up(16LL * stages, 16);
     l.face_off = round_up(l.hist_off + 4LL * (kMaxL + 1), 16);
-    l.stage_off = round_up(l.face_off + 6 * 16 + 16, 128);
+    l.halo_off = round_up(l.face_off + 6 * 16 + 16, 128);
+    long long at = l.halo_off;
+    for (int f = 0; f < 6; ++f) {
+        l.halo_words[f] = f < 2 ? (long long)m1 * m2 : f < 4 ? (long long)m0 * m2 : (long long)m0 * m1;
+        l.halo_at[f] = at;
+        at = round_up(at + l.halo_words[f] * word, 16);
+    }
+    l.stage_off = round_up(at, 128);
     l.plane_bytes = round_up((long long)m0 * m1 * word, 128);
     l.total = l.stage_off + (long long)stages * l.plane_bytes;
     return l;
@@ -156,16 +171,19 @@ __device__ __forceinline__ T *ring_entry(const Params3 &p, long long level, long
 }
 
 template <typename T, int TC>
-__global__ void __launch_bounds__(kThreads3, 2) at_stepper3d(const Params3 p)
+__global__ void __launch_bounds__(kThreads3, AT_MIN_CTAS_3D) at_stepper3d(const Params3 p, const __grid_constant__ CUtensorMap tmap)
 {
     extern __shared__ __align__(128) unsigned char smem[];
-    const Smem3 sl = smem3_layout(p.m0, p.m1, (int)sizeof(T), p.stages);
+    const Smem3 sl = smem3_layout(p.m0, p.m1, p.m2, (int)sizeof(T), p.stages);
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + sl.bar_off);
     unsigned *hist = reinterpret_cast<unsigned *>(smem + sl.hist_off);
     int *s_k = reinterpret_cast<int *>(smem + sl.face_off);                  // [6] delays of the tile
     long long *s_q = reinterpret_cast<long long *>(smem + sl.face_off + 32);  // [6] face neighbours
     int *s_flag = reinterpret_cast<int *>(smem + sl.face_off + 80);          // barrier / abort word
     unsigned char *stages = smem + sl.stage_off;
+    T *hx0 = reinterpret_cast<T *>(smem + sl.halo_at[0]), *hx1 = reinterpret_cast<T *>(smem + sl.halo_at[1]);
+    T *hy0 = reinterpret_cast<T *>(smem + sl.halo_at[2]), *hy1 = reinterpret_cast<T *>(smem + sl.halo_at[3]);
+    T *hz0 = reinterpret_cast<T *>(smem + sl.halo_at[4]), *hz1 = reinterpret_cast<T *>(smem + sl.halo_at[5]);
 
     const int tid = threadIdx.x, lane = tid & 31;
     const long long lo = (long long)blockIdx.x * p.P / p.G, hi = (long long)(blockIdx.x + 1) * p.P / p.G;
@@ -180,38 +198,61 @@ __global__ void __launch_bounds__(kThreads3, 2) at_stepper3d(const Params3 p)
     const T cB0 = (T)p.cB[0], cB1 = (T)p.cB[1], cB2 = (T)p.cB[2];
     T *u = reinterpret_cast<T *>(p.u);
 
-    if (tid < NS) mbar_init(&bars[tid], 1);
+    constexpr int kWarps3 = kThreads3 / 32;
+    uint64_t *empty = bars + NS;           // every warp arrives once it is done with a stage
+    if (tid < NS) {
+        mbar_init(&bars[tid], 1);
+        mbar_init(&empty[tid], kWarps3);
+    }
     if (tid == 0) { mbar_fence_init(); *s_flag = 0; }
     for (int i = tid; i <= kMaxL; i += kThreads3) hist[i] = 0u;
     __syncthreads();
 
-    // plane g -> (level, subdomain, z)
-    auto plane_of = [&](long long g, long long *lv, long long *sub, int *z) {
-        const long long t = g / m2;
-        *z = (int)(g - t * m2);
-        *lv = lev0 + t / S;
-        *sub = lo + t % S;
+    // word offset of the first point of subdomain `sub` in u
+    const long long plane_words = p.n0 * p.n1;
+    auto tile_base = [&](long long sub) -> long long {
+        const long long q01 = p.P0 * p.P1;
+        const long long q2 = sub / q01, r = sub - q2 * q01, q1 = r / p.P0, q0 = r - q1 * p.P0;
+        return (q2 * m2) * plane_words + (q1 * m1) * p.n0 + q0 * m0;
     };
-    // warp 0 issues the bulk copies of plane g into stage g % NS
-    auto issue = [&](long long g) {
-        if (tid >= 32) return;
-        long long lv, sub;
-        int z;
-        plane_of(g, &lv, &sub, &z);
-        const long long q0 = sub % p.P0, q1 = (sub / p.P0) % p.P1, q2 = sub / (p.P0 * p.P1);
-        uint64_t *bar = &bars[g % NS];
-        if (lane == 0) mbar_arrive_expect_tx(bar, plane_bytes);
-        __syncwarp();
-        unsigned char *dst = stages + (size_t)(g % NS) * sl.plane_bytes;
-        const long long zg = q2 * m2 + z;
-        for (int y = lane; y < m1; y += 32) {
-            const T *src = u + ((size_t)zg * p.n1 + (size_t)(q1 * m1 + y)) * (size_t)p.n0 + (size_t)(q0 * m0);
-            bulk_load(dst + (size_t)y * m0 * sizeof(T), src, (unsigned)(m0 * sizeof(T)), bar);
+    // element coordinates of the first point of subdomain `sub`
+    auto tile_coords = [&](long long sub, int *x, int *y, int *z) {
+        const long long q01 = p.P0 * p.P1;
+        const long long q2 = sub / q01, r = sub - q2 * q01, q1 = r / p.P0, q0 = r - q1 * p.P0;
+        *x = (int)(q0 * m0); *y = (int)(q1 * m1); *z = (int)(q2 * m2);
+    };
+    // issue cursor: the next plane to copy (advanced plane by plane, no division)
+    long long i_sub = lo, issued = 0;
+    int i_z = 0, i_stage = 0, i_x0, i_y0, i_z0;
+    tile_coords(lo, &i_x0, &i_y0, &i_z0);
+    // warp 0 issues the bulk copies of the next plane into its stage, once
+    // every warp is done with the plane that stage held (bounded wait)
+    auto issue = [&]() {
+        if (tid < 32) {
+            if (issued >= NS) {
+                int good = 1;
+                if (lane == 0) good = wait_stage3(p, &empty[i_stage], (unsigned)(((issued - NS) / NS) & 1));
+                good = __shfl_sync(0xffffffffu, good, 0);
+                if (!good) atomicExch(s_flag, -1);
+            }
+            if (lane == 0) {
+                uint64_t *bar = &bars[i_stage];
+                mbar_arrive_expect_tx(bar, plane_bytes);
+                tensor_load_3d(stages + (size_t)i_stage * sl.plane_bytes, &tmap, i_x0, i_y0, i_z0 + i_z, bar);
+            }
+            __syncwarp();
+        }
+        ++issued;
+        if (++i_stage == NS) i_stage = 0;
+        if (++i_z == m2) {
+            i_z = 0;
+            if (++i_sub == hi) i_sub = lo;
+            tile_coords(i_sub, &i_x0, &i_y0, &i_z0);
         }
     };
 
-    // columns of this thread
-    int cx[TC], cy[TC];
+    // columns of this thread: position, offset in a plane of u, faces touched
+    int cx[TC], cy[TC], coff[TC], cface[TC];
     bool cv[TC];
 #pragma unroll
     for (int q = 0; q < TC; ++q) {
@@ -219,166 +260,160 @@ __global__ void __launch_bounds__(kThreads3, 2) at_stepper3d(const Params3 p)
         cv[q] = c < PW;
         cx[q] = cv[q] ? c % m0 : 0;
         cy[q] = cv[q] ? c / m0 : 0;
+        coff[q] = cy[q] * (int)p.n0 + cx[q];
+        cface[q] = (cx[q] == 0 ? 1 : 0) | (cx[q] == m0 - 1 ? 2 : 0) | (cy[q] == 0 ? 4 : 0) | (cy[q] == m1 - 1 ? 8 : 0);
     }
     T prev[TC], cur[TC];
 #pragma unroll
     for (int q = 0; q < TC; ++q) prev[q] = cur[q] = (T)0;
 
-    long long issued = 0;
-    for (; issued < NS && issued < Q; ++issued) issue(issued);
-    // every thread waits (bounded) for the stages it reads; a failed wait is
-    // recorded and acted on by all threads after the next barrier
-    auto wait_plane = [&](long long g) {
-        if (g < Q && !wait_stage3(p, &bars[g % NS], (unsigned)((g / NS) & 1))) atomicExch(s_flag, -1);
+    while (issued < NS && issued < Q) issue();
+    // a failed wait is recorded in s_flag; every thread acts on it at the
+    // next CTA barrier (one per tile), so control flow stays uniform there
+    auto wait_plane = [&](long long g) -> bool {
+        if (!wait_stage3(p, &bars[g % NS], (unsigned)((g / NS) & 1))) { atomicExch(s_flag, -1); return false; }
+        return true;
     };
-    wait_plane(0);
-    wait_plane(1);
-    __syncthreads();
 
-    bool ok = *s_flag != -1;
+    // Every warp runs the same number of tiles and meets the same CTA
+    // barriers; a failed wait inside a tile only skips that warp's remaining
+    // planes, and all threads leave together after the next tile-start barrier.
+    bool ok = true;
     long long lv = lev0, sub = lo;
-    int z = 0;
-    long long s0 = 0, s1 = 0, s2 = 0;        // coordinates of the current subdomain
-    for (long long g = 0; g < Q && ok; ++g) {
-        if (z == 0) {
-            // ---- tile start: grid barrier (synchronous mode), delays, halos
-            if (p.mode == kModeSync && sub == lo && lv > lev0) {
-                if (!grid_sync3(p, lv - lev0, s_flag)) { ok = false; break; }
-            }
-            s0 = sub % p.P0; s1 = (sub / p.P0) % p.P1; s2 = sub / (p.P0 * p.P1);
-            if (tid < 6) {
-                const int f = tid;
-                const long long q = face_neighbour(p, s0, s1, s2, f);
-                long long kmax = lv - 2 + 1;           // s = 2 levels per extrapolation
-                if (kmax < 0) kmax = 0;
-                if (kmax > p.L) kmax = p.L;
-                long long k = 0;
-                if (p.mode == kModeSeeded) {
-                    const unsigned long long ctr = ((unsigned long long)lv * (unsigned long long)p.P +
-                                                    (unsigned long long)sub) * 6ull + (unsigned long long)f;
-                    k = (long long)(((splitmix64(p.seed, ctr) >> 32) * (unsigned long long)(p.L + 1)) >> 32);
-                } else if (p.mode == kModeReplay) {
-                    k = p.delays[((size_t)(lv - lev0) * p.P + sub) * 6 + f];
-                }
-                if (k > kmax) k = kmax;
-                if (k < 0) k = 0;
-                int good = 1;
-                if (p.mode != kModeSync) {
-                    const unsigned long long *fl = p.flag + q * 6 + (f ^ 1);
-                    const long long need = (p.mode == kModeFree) ? lv - kmax : lv - k;
-                    unsigned long long seen = ld_acquire(fl);
-                    if ((long long)seen < need && !wait_flag3(p, fl, need, &seen, lv, q)) good = 0;
-                    if (good && p.mode == kModeFree) k = lv - ((long long)seen < lv ? (long long)seen : lv);
-                }
-                if (good) {
-                    atomicAdd(&hist[k], 1u);
-                    if (p.delays && p.mode != kModeReplay) p.delays[((size_t)(lv - lev0) * p.P + sub) * 6 + f] = (int8_t)k;
-                }
-                s_k[f] = (int)k;
-                s_q[f] = q;
-                if (!good) atomicExch(s_flag, -1);
-            }
-            if (tid == 0 && p.mode == kModeSync) __threadfence();
-            __syncthreads();
-            if (*s_flag == -1) { ok = false; break; }
-            // plane z = -1: the -z neighbour's top plane, extrapolated
-            {
-                const int k4 = s_k[4];
-                const T *e0 = ring_entry<T>(p, lv - k4, s_q[4], 5);
-                const T *e1 = ring_entry<T>(p, lv - k4 - 1, s_q[4], 5);
+    long long prev_sub = -1, prev_new = 0;   // the tile whose flags are still to be released
+    T *rf[6];                                // ring entries of the new level of the current tile
+    const long long n_tiles = p.n_steps * S;
+    for (long long t = 0; t < n_tiles; ++t) {
+        long long g = t * m2;                // first plane of the tile
+        // ---- tile start (one CTA barrier): release the previous tile's
+        // flags, grid barrier (synchronous mode), delays, halos
+        __syncthreads();
+        if (*s_flag == -1) { ok = false; break; }
+        if (tid == 0 && prev_sub >= 0) {
+            __threadfence();
+            for (int f = 0; f < 6; ++f) st_release(p.flag + prev_sub * 6 + f, (unsigned long long)prev_new);
+        }
+        if (p.mode == kModeSync && sub == lo && lv > lev0) {
+            if (!grid_sync3(p, lv - lev0, s_flag)) { ok = false; break; }
+        }
+        const long long s0 = sub % p.P0, s1 = (sub / p.P0) % p.P1, s2 = sub / (p.P0 * p.P1);
+        const long long base = tile_base(sub);
 #pragma unroll
-                for (int q = 0; q < TC; ++q) {
-                    if (!cv[q]) continue;
-                    const int idx = cy[q] * m0 + cx[q];
-                    prev[q] = k4 == 0 ? e0[idx] : (T)(k4 + 1) * e0[idx] - (T)k4 * e1[idx];
-                }
+        for (int f = 0; f < 6; ++f) rf[f] = ring_entry<T>(p, lv + 1, sub, f);
+        if (tid < 6) {
+            const int f = tid;
+            const long long q = face_neighbour(p, s0, s1, s2, f);
+            long long kmax = lv - 2 + 1;           // s = 2 levels per extrapolation
+            if (kmax < 0) kmax = 0;
+            if (kmax > p.L) kmax = p.L;
+            long long k = 0;
+            if (p.mode == kModeSeeded) {
+                const unsigned long long ctr = ((unsigned long long)lv * (unsigned long long)p.P +
+                                                (unsigned long long)sub) * 6ull + (unsigned long long)f;
+                k = (long long)(((splitmix64(p.seed, ctr) >> 32) * (unsigned long long)(p.L + 1)) >> 32);
+            } else if (p.mode == kModeReplay) {
+                k = p.delays[((size_t)(lv - lev0) * p.P + sub) * 6 + f];
             }
-            // plane z = 0 of this tile (its stage was waited for two planes ago)
+            if (k > kmax) k = kmax;
+            if (k < 0) k = 0;
+            int good = 1;
+            if (p.mode != kModeSync) {
+                const unsigned long long *fl = p.flag + q * 6 + (f ^ 1);
+                const long long need = (p.mode == kModeFree) ? lv - kmax : lv - k;
+                unsigned long long seen = ld_acquire(fl);
+                if ((long long)seen < need && !wait_flag3(p, fl, need, &seen, lv, q)) good = 0;
+                if (good && p.mode == kModeFree) k = lv - ((long long)seen < lv ? (long long)seen : lv);
+            }
+            if (good) {
+                atomicAdd(&hist[k], 1u);
+                if (p.delays && p.mode != kModeReplay) p.delays[((size_t)(lv - lev0) * p.P + sub) * 6 + f] = (int8_t)k;
+            }
+            s_k[f] = (int)k;
+            s_q[f] = q;
+            if (!good) atomicExch(s_flag, -1);
+        }
+        if (tid == 0 && p.mode == kModeSync) __threadfence();
+        __syncthreads();
+        if (*s_flag == -1) { ok = false; break; }
+        // the six halo planes of the tile: the neighbours' facing ring
+        // entries (coalesced), extrapolated once with the faces' delays
+#pragma unroll
+        for (int f = 0; f < 6; ++f) {
+            const int k = s_k[f];
+            const T *e0 = ring_entry<T>(p, lv - k, s_q[f], f ^ 1);
+            const T *e1 = ring_entry<T>(p, lv - k - 1, s_q[f], f ^ 1);
+            T *h = reinterpret_cast<T *>(smem + sl.halo_at[f]);
+            const int nw = (int)sl.halo_words[f];
+            for (int i = tid; i < nw; i += kThreads3)
+                h[i] = k == 0 ? e0[i] : (T)(k + 1) * e0[i] - (T)k * e1[i];
+        }
+        __syncthreads();
+        // plane z = -1 (the -z halo) and plane 0
+#pragma unroll
+        for (int q = 0; q < TC; ++q) prev[q] = cv[q] ? hz0[cy[q] * m0 + cx[q]] : (T)0;
+        if (!wait_plane(g)) { ok = false; }
+        {
             const T *st0 = reinterpret_cast<const T *>(stages + (size_t)(g % NS) * sl.plane_bytes);
 #pragma unroll
             for (int q = 0; q < TC; ++q) cur[q] = cv[q] ? st0[cy[q] * m0 + cx[q]] : (T)0;
         }
-        // ---- plane z: needs plane z+1 (stage, already waited for) or the +z halo
-        const bool top = (z == m2 - 1);
-        const T *st = reinterpret_cast<const T *>(stages + (size_t)(g % NS) * sl.plane_bytes);
-        const T *stn = reinterpret_cast<const T *>(stages + (size_t)((g + 1) % NS) * sl.plane_bytes);
         const long long lnew = lv + 1;
-        const size_t zrow = (size_t)(s2 * m2 + z) * (size_t)p.n1;
+        // ---- the planes of the tile; warps run independently (stage
+        // barriers only)
+        for (int z = 0; z < m2 && ok; ++z, ++g) {
+            const bool top = (z == m2 - 1);
+            if (!top && !wait_plane(g + 1)) { ok = false; break; }
+            const int sg = (int)(g % NS), sg1 = sg + 1 == NS ? 0 : sg + 1;
+            const T *st = reinterpret_cast<const T *>(stages + (size_t)sg * sl.plane_bytes);
+            const T *stn = reinterpret_cast<const T *>(stages + (size_t)sg1 * sl.plane_bytes);
+            T *up = u + base + (long long)z * plane_words;
+            const int zy = z * m1, zx = z * m0;
 #pragma unroll
-        for (int q = 0; q < TC; ++q) {
-            if (!cv[q]) continue;
-            const int x = cx[q], y = cy[q], c = y * m0 + x;
-            const T cc = cur[q], below = prev[q];
-            T above;
-            if (!top) {
-                above = stn[c];
-            } else {
-                const int k5 = s_k[5];
-                const T *e0 = ring_entry<T>(p, lv - k5, s_q[5], 4);
-                above = e0[c];
-                if (k5 != 0) above = (T)(k5 + 1) * above - (T)k5 * ring_entry<T>(p, lv - k5 - 1, s_q[5], 4)[c];
+            for (int q = 0; q < TC; ++q) {
+                if (!cv[q]) continue;
+                const int x = cx[q], y = cy[q], c = y * m0 + x;
+                const T cc = cur[q], below = prev[q];
+                const T above = top ? hz1[c] : stn[c];
+                const int fc = cface[q];
+                const T xm = (fc & 1) ? hx0[zy + y] : st[c - 1];
+                const T xp = (fc & 2) ? hx1[zy + y] : st[c + 1];
+                const T ym = (fc & 4) ? hy0[zx + x] : st[c - m0];
+                const T yp = (fc & 8) ? hy1[zx + x] : st[c + m0];
+                const T d1 = cA0 * (xp - xm) + cA1 * (yp - ym) + cA2 * (above - below);
+                const T d2 = cB0 * ((xp + xm) - (T)2 * cc) + cB1 * ((yp + ym) - (T)2 * cc) +
+                             cB2 * ((above + below) - (T)2 * cc);
+                const T un = cc + (d2 - cc * d1);
+                up[coff[q]] = un;
+                // boundary values of the new level into the ring
+                if (fc) {
+                    if (fc & 1) rf[0][zy + y] = un;
+                    if (fc & 2) rf[1][zy + y] = un;
+                    if (fc & 4) rf[2][zx + x] = un;
+                    if (fc & 8) rf[3][zx + x] = un;
+                }
+                if (z == 0) rf[4][c] = un;
+                if (top) rf[5][c] = un;
+                prev[q] = cc;
+                cur[q] = above;
             }
-            T xm, xp, ym, yp;
-            if (x > 0) xm = st[c - 1];
-            else {
-                const int k = s_k[0];
-                const int e = z * m1 + y;
-                xm = ring_entry<T>(p, lv - k, s_q[0], 1)[e];
-                if (k != 0) xm = (T)(k + 1) * xm - (T)k * ring_entry<T>(p, lv - k - 1, s_q[0], 1)[e];
-            }
-            if (x < m0 - 1) xp = st[c + 1];
-            else {
-                const int k = s_k[1];
-                const int e = z * m1 + y;
-                xp = ring_entry<T>(p, lv - k, s_q[1], 0)[e];
-                if (k != 0) xp = (T)(k + 1) * xp - (T)k * ring_entry<T>(p, lv - k - 1, s_q[1], 0)[e];
-            }
-            if (y > 0) ym = st[c - m0];
-            else {
-                const int k = s_k[2];
-                const int e = z * m0 + x;
-                ym = ring_entry<T>(p, lv - k, s_q[2], 3)[e];
-                if (k != 0) ym = (T)(k + 1) * ym - (T)k * ring_entry<T>(p, lv - k - 1, s_q[2], 3)[e];
-            }
-            if (y < m1 - 1) yp = st[c + m0];
-            else {
-                const int k = s_k[3];
-                const int e = z * m0 + x;
-                yp = ring_entry<T>(p, lv - k, s_q[3], 2)[e];
-                if (k != 0) yp = (T)(k + 1) * yp - (T)k * ring_entry<T>(p, lv - k - 1, s_q[3], 2)[e];
-            }
-            const T d1 = cA0 * (xp - xm) + cA1 * (yp - ym) + cA2 * (above - below);
-            const T d2 = cB0 * ((xp + xm) - (T)2 * cc) + cB1 * ((yp + ym) - (T)2 * cc) + cB2 * ((above + below) - (T)2 * cc);
-            const T un = cc + (d2 - cc * d1);
-            u[(zrow + (size_t)(s1 * m1 + y)) * (size_t)p.n0 + (size_t)(s0 * m0 + x)] = un;
-            // boundary values of the new level into the ring
-            if (x == 0) ring_entry<T>(p, lnew, sub, 0)[z * m1 + y] = un;
-            if (x == m0 - 1) ring_entry<T>(p, lnew, sub, 1)[z * m1 + y] = un;
-            if (y == 0) ring_entry<T>(p, lnew, sub, 2)[z * m0 + x] = un;
-            if (y == m1 - 1) ring_entry<T>(p, lnew, sub, 3)[z * m0 + x] = un;
-            if (z == 0) ring_entry<T>(p, lnew, sub, 4)[c] = un;
-            if (top) ring_entry<T>(p, lnew, sub, 5)[c] = un;
-            prev[q] = cc;
-            cur[q] = above;
+            // the next read of a plane written here is a bulk copy (async
+            // proxy) at the next level: with two or more subdomains per CTA it
+            // is issued after this tile ends, so one proxy fence per tile (it
+            // waits for this thread's stores) covers every plane; with one
+            // subdomain, fence every plane
+            if (top || S == 1) fence_proxy_async_global();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[sg]);
+            if (issued < Q) issue();
         }
-        // stage g is free once every thread is past it; the next read of a
-        // plane written here is a bulk copy (async proxy)
-        fence_proxy_async_global();
-        wait_plane(g + 2);
-        __syncthreads();
-        if (*s_flag == -1) { ok = false; break; }
-        if (issued < Q) { issue(issued); ++issued; }
-        if (top) {
-            // ---- tile end: release the six faces' flags
-            if (tid == 0) {
-                __threadfence();
-                for (int f = 0; f < 6; ++f) st_release(p.flag + sub * 6 + f, (unsigned long long)lnew);
-            }
-            if (++sub == hi) { sub = lo; ++lv; }
-            z = 0;
-        } else {
-            ++z;
-        }
+        prev_sub = sub;
+        prev_new = lnew;
+        if (++sub == hi) { sub = lo; ++lv; }
+    }
+    __syncthreads();
+    if (tid == 0 && ok && prev_sub >= 0) {
+        __threadfence();
+        for (int f = 0; f < 6; ++f) st_release(p.flag + prev_sub * 6 + f, (unsigned long long)prev_new);
     }
     // let the copies in flight land before leaving
     if (tid == 0) {

@@ -97,6 +97,9 @@ def lib():
             L.at_oracle_run3d.restype = ctypes.c_int
             L.at_oracle_run3d.argtypes = [ctypes.POINTER(Cfg3), ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
                                           ctypes.c_void_p, ctypes.c_void_p]
+            L.at_oracle_run3d_system.restype = ctypes.c_int
+            L.at_oracle_run3d_system.argtypes = [ctypes.POINTER(Cfg3), ctypes.c_int, ctypes.c_void_p, ctypes.c_int64,
+                                                 ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
             L.at_oracle_cfg3_size.restype = ctypes.c_int64
             if L.at_oracle_cfg3_size() != ctypes.sizeof(Cfg3):
                 raise RuntimeError("oracle: 3D configuration struct layout mismatch")
@@ -240,4 +243,37 @@ def run3d(u0, *, P, L, nu, dt, n_steps, dx=None, length=2 * np.pi, delay_mode=SY
     rc = lib().at_oracle_run3d(ctypes.byref(c), n_steps, _dptr(rep), _dptr(u0), _dptr(out), _dptr(hist))
     if rc != 0:
         raise ValueError(f"oracle run3d failed: rc={rc}")
+    return out, hist
+
+
+def run3d_system(q0, *, kappa, P, L, dt, n_steps, dx=None, length=2 * np.pi, delay_mode=SYNC, seed=0, replay=None):
+    """The system of Eq. BS in 3D: q0 shaped (nf, n2, n1, n0) with the velocity
+    components in fields 0, 1, 2 and passive scalars after them; kappa[f] the
+    viscosity (velocity) or diffusivity (scalars) of field f.  Same grid,
+    subdomains, delays and AT halos as ``run3d``.  Returns ``(q, hist)``."""
+    q0 = np.ascontiguousarray(q0, dtype=np.float64)
+    nf, n2, n1, n0 = q0.shape
+    kap = np.ascontiguousarray(kappa, dtype=np.float64)
+    if kap.size != nf:
+        raise ValueError("run3d_system: one kappa per field")
+    if dx is None:
+        dx = (length / n0, length / n1, length / n2)
+    c = Cfg3()
+    c.n[0], c.n[1], c.n[2] = n0, n1, n2
+    c.P[0], c.P[1], c.P[2] = P
+    c.L, c.delay_mode, c.nu, c.dt = L, delay_mode, 0.0, dt
+    c.dx[0], c.dx[1], c.dx[2] = dx
+    c.seed = seed & (2**64 - 1)
+    NP = P[0] * P[1] * P[2]
+    rep = None
+    if delay_mode == REPLAY:
+        rep = np.ascontiguousarray(replay, dtype=np.int8)
+        if rep.size != n_steps * NP * 6:
+            raise ValueError("run3d_system: replay array has the wrong size")
+    out = np.empty_like(q0)
+    hist = np.zeros(L + 1, dtype=np.int64)
+    rc = lib().at_oracle_run3d_system(ctypes.byref(c), nf, _dptr(kap), n_steps, _dptr(rep), _dptr(q0), _dptr(out),
+                                      _dptr(hist))
+    if rc != 0:
+        raise ValueError(f"oracle run3d_system failed: rc={rc}")
     return out, hist

@@ -498,3 +498,87 @@ int at_oracle_run3d(const at_oracle_cfg3 *c, int64_t n_steps, const int8_t *repl
 }
 
 int64_t at_oracle_cfg3_size(void) { return (int64_t)sizeof(at_oracle_cfg3); }
+
+/* ------------------------------------------------------------------------ */
+/* The system of Eq. BS in three dimensions: velocity components q_0, q_1,  */
+/* q_2 (u, v, w) and passive scalars q_3 .. q_{nf-1}, each                  */
+/*     d_t q_f + u d_x q_f + v d_y q_f + w d_z q_f = kappa_f lap q_f         */
+/* (kappa = nu for the velocity components, the scalar's diffusivity alpha  */
+/* for the scalars), same grid, decomposition, stencils and AT halos as     */
+/* at_oracle_run3d; one delay per (level, subdomain, face) serves every      */
+/* field (one message per face carries all of them).  Fields are stored one  */
+/* after another: q[f][k][j][i].                                             */
+/* ------------------------------------------------------------------------ */
+int at_oracle_run3d_system(const at_oracle_cfg3 *c, int nf, const double *kappa, int64_t n_steps,
+                           const int8_t *replay, const double *q0, double *q_out, int64_t *hist)
+{
+    if (!c || nf < 3 || nf > 8 || !kappa || n_steps < 0 || c->L < 0 || c->L > 64) return ORC_EARG;
+    int64_t m[3], NP = 1, N = 1;
+    for (int a = 0; a < 3; ++a) {
+        if (c->n[a] <= 0 || c->P[a] <= 0 || c->n[a] % c->P[a] != 0) return ORC_EARG;
+        m[a] = c->n[a] / c->P[a];
+        if (m[a] < 2) return ORC_EARG;
+        NP *= c->P[a];
+        N *= c->n[a];
+    }
+    const int s = 2;
+    const int depth = c->L + s + 1;
+    const size_t lvl = (size_t)nf * (size_t)N;     /* words per level (all fields) */
+    double *H = (double *)calloc((size_t)depth * lvl, sizeof(double));
+    int8_t *K = (int8_t *)malloc((size_t)NP * 6);
+    if (!H || !K) { free(H); free(K); return ORC_ENOMEM; }
+    memcpy(H, q0, lvl * sizeof(double));
+    if (hist) memset(hist, 0, (size_t)(c->L + 1) * sizeof(int64_t));
+    const int64_t n0 = c->n[0], n1 = c->n[1], n2 = c->n[2];
+    for (int64_t n = 0; n < n_steps; ++n) {
+        const double *cur = H + (size_t)(n % depth) * lvl;
+        double *nxt = H + (size_t)((n + 1) % depth) * lvl;
+        for (int64_t p = 0; p < NP; ++p) {
+            for (int f = 0; f < 6; ++f) {
+                int kr = 0;
+                if (c->delay_mode == 1) kr = at_oracle_seeded_delay(c->seed, n, p, NP, f, 6, c->L);
+                else if (c->delay_mode == 2) kr = replay[((size_t)n * NP + p) * 6 + f];
+                if (kr < 0 || kr > c->L) { free(H); free(K); return ORC_EDELAY; }
+                int64_t kmax = n - s + 1; if (kmax < 0) kmax = 0;
+                K[p * 6 + f] = (int8_t)((kr < kmax) ? kr : kmax);
+                if (hist) hist[K[p * 6 + f]] += 1;
+            }
+        }
+        for (int64_t k = 0; k < n2; ++k)
+            for (int64_t j = 0; j < n1; ++j)
+                for (int64_t i = 0; i < n0; ++i) {
+                    const int64_t idx[3] = {i, j, k};
+                    const int64_t p = ((k / m[2]) * c->P[1] + j / m[1]) * c->P[0] + i / m[0];
+                    const int64_t pt = (k * n1 + j) * n0 + i;
+                    const double vel[3] = {cur[pt], cur[(size_t)N + pt], cur[2 * (size_t)N + pt]};
+                    for (int fld = 0; fld < nf; ++fld) {
+                        const double *cf = cur + (size_t)fld * N;
+                        const double q = cf[pt];
+                        double adv = 0.0, lap = 0.0;
+                        for (int a = 0; a < 3; ++a) {
+                            double v[2];
+                            for (int side = 0; side < 2; ++side) {
+                                int64_t qq[3] = {i, j, k};
+                                qq[a] = wrap(idx[a] + (side ? 1 : -1), c->n[a]);
+                                const int64_t src = (qq[2] * n1 + qq[1]) * n0 + qq[0];
+                                const int64_t loc = idx[a] % m[a] + (side ? 1 : -1);
+                                if (loc >= 0 && loc < m[a]) { v[side] = cf[src]; continue; }
+                                const int kf = K[p * 6 + 2 * a + side];
+                                double lev[2];
+                                for (int t = 0; t < s; ++t) {
+                                    const int64_t lv = n - kf - t;
+                                    lev[t] = (lv >= 0) ? H[(size_t)(lv % depth) * lvl + (size_t)fld * N + src] : 0.0;
+                                }
+                                v[side] = at_oracle_extrapolate(s, kf, 1, lev);
+                            }
+                            adv += vel[a] * (v[1] - v[0]) / (2.0 * c->dx[a]);
+                            lap += (v[1] - 2.0 * q + v[0]) / (c->dx[a] * c->dx[a]);
+                        }
+                        nxt[(size_t)fld * N + pt] = q + c->dt * (-adv + kappa[fld] * lap);
+                    }
+                }
+    }
+    memcpy(q_out, H + (size_t)(n_steps % depth) * lvl, lvl * sizeof(double));
+    free(H); free(K);
+    return ORC_OK;
+}

@@ -67,6 +67,7 @@ def parse():
     ap.add_argument("--no-tune", action="store_true", help="ensemble leg: keep the default launch shape")
     ap.add_argument("--adjoint-only", action="store_true", help="time only the adjoint leg")
     ap.add_argument("--only-3d", action="store_true", help="time only the 3D leg")
+    ap.add_argument("--only-system", action="store_true", help="time only the 3D system leg")
     ap.add_argument("--time-steps-3d", type=int, default=500, help="time steps per 3D launch")
     return ap.parse_args()
 
@@ -436,6 +437,73 @@ def config3d(args, at, torch, dev):
     return res
 
 
+def config_system(args, at, torch, dev):
+    """The 3D system of Eq. BS: velocity (u, v, w) and two passive scalars on
+    256^3 points in 16^3 subdomains (4096), order 2, L = 2, nu = 0.02,
+    alpha = (0.01, 0.05), FP32, k^-5/3 fields (seeds 4..8) at half amplitude:
+    200-step launches free-running vs seeded vs synchronous; the fields' first
+    and second moments before and after; FP32 against the FP64 oracle on a
+    64^3 box after 30 seeded steps."""
+    n, sub, L, nf = 256, (16, 16, 16), 2, 5
+    kappa = [0.02, 0.02, 0.02, 0.01, 0.05]
+    q0 = np.stack([0.5 * W.u0_spectral3d(n, seed=4 + f, kmax=32) for f in range(nf)])
+    dt = W.dt_rule(q0[:3].reshape(-1), 2 * np.pi / n, max(kappa), dim=3)
+    q_dev = torch.from_numpy(q0.ravel()).to(device=dev, dtype=torch.float32)
+    del q0
+    S = 200
+    npts = n ** 3
+    res = {"workload": "system3d_n256_5fields", "n": n, "sub": list(sub), "P": (n // sub[0]) ** 3, "fields": nf,
+           "kappa": kappa, "L": L, "dt": dt, "dtype": "f32", "time_steps_per_launch": S,
+           "unit_note": "GPts/s counts grid points (all fields of a point advanced once = one update)"}
+    stream = torch.cuda.Stream(device=dev)
+    for name, mode in (("free", at.AT_FREE), ("seeded", at.AT_SEEDED), ("sync", at.AT_SYNC)):
+        s = at.System3D((n, n, n), sub, L, kappa, dt, dtype="f32", seed=5, stream=stream, device=dev.index)
+        with torch.cuda.stream(stream):
+            s.set_state(q_dev)
+        if name == "free":
+            res["moments_initial"] = s.moments()
+        with torch.cuda.stream(stream):
+            s.step(S, mode)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        reps = max(1, min(args.steps, 4))
+        with torch.cuda.stream(stream):
+            ev[0].record(stream)
+            for _ in range(reps):
+                s.step(S, mode)
+            ev[1].record(stream)
+        torch.cuda.synchronize(dev)
+        ms = ev[0].elapsed_time(ev[1]) / reps
+        rc = s.status()
+        if rc != at.AT_OK:
+            raise RuntimeError(f"system {name}: device status {rc}: {at.at_last_error()}")
+        info = s.info()
+        res[name] = {"value": npts * S / (ms * 1e-3) / 1e9, "unit": UNIT, "ms_per_launch": ms, "ctas": info.ctas,
+                     "stages": info.stages}
+        if name == "free":
+            res["moments_after"] = s.moments()
+            res["moments_after_steps"] = S * (1 + reps)
+        s.close()
+    res["speedup_free_over_sync"] = res["free"]["value"] / res["sync"]["value"]
+    bpu = nf * (2 * 4 + 18 * 4 / sub[0])
+    peak, src = hbm_peak()
+    res["roofline"] = {"bound": "hbm", "algorithmic_bytes_per_update": bpu, "achieved": res["free"]["value"] * bpu,
+                       "peak": peak, "unit": "GB/s", "frac": res["free"]["value"] * bpu / peak, "peak_source": src}
+    import oracle
+    nb = 64
+    qb = np.stack([0.5 * W.u0_spectral3d(nb, seed=4 + f, kmax=16) for f in range(nf)])
+    kb = [0.1, 0.1, 0.1, 0.05, 0.2]
+    dtb = W.dt_rule(qb[:3].reshape(-1), 2 * np.pi / nb, max(kb), dim=3)
+    s = at.System3D((nb, nb, nb), sub, L, kb, dtb, dtype="f32", seed=5, device=dev.index)
+    s.set_state(torch.from_numpy(qb.ravel()).to(dev))
+    s.step(30, at.AT_SEEDED)
+    g = s.state().double().cpu().numpy().reshape(qb.shape)
+    s.close()
+    ref, _ = oracle.run3d_system(qb, kappa=kb, P=(4, 4, 4), L=L, dt=dtb, n_steps=30, delay_mode=oracle.SEEDED, seed=5)
+    res["err_vs_fp64_oracle"] = {"rel_linf_per_field": [float(np.max(np.abs(g[f] - ref[f])) / np.max(np.abs(ref[f])))
+                                                        for f in range(nf)], "box": [nb] * 3, "steps": 30}
+    return res
+
+
 def reference_arm(args, ws, rank, pg):
     """--impl reference: the CPU oracle timed on this workload, bounded sample per step."""
     cfg = W.config(WORKLOAD)
@@ -683,6 +751,7 @@ def gpu_arm(args, ws, rank, local, pg):
             line["ensemble"] = ensemble_config(args, at, torch, dev, stream)
             line["adjoint"] = adjoint_config(args, at, torch, dev)
             line["burgers3d"] = config3d(args, at, torch, dev)
+            line["system3d"] = config_system(args, at, torch, dev)
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -696,6 +765,15 @@ def main():
         reference_arm(args, ws, rank, None)
         return
     ws, rank, local, pg = dist_setup(args)
+    if args.only_system:
+        import torch
+
+        import paper_1911_05769_gb300 as at
+        from paper_1911_05769_gb300 import build as atbuild
+        atbuild.build()
+        torch.cuda.set_device(local)
+        print(json.dumps(config_system(args, at, torch, torch.device("cuda", local))), flush=True)
+        return
     if args.only_3d:
         import torch
 

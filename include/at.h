@@ -201,6 +201,26 @@ const char *at_last_error(void);
  * temporal blocking, ensembles, adjoint or autotuner in 3D.
  * --------------------------------------------------------------------------- */
 
+/* The full system of Eq. BS in 3D: velocity components u, v, w and 0..2
+ * passive scalars phi_k, nfields = 3..5 fields stored one after another
+ * (field-major, each n[0] x n[1] x n[2] with x fastest):
+ *     d_t q_f + u d_x q_f + v d_y q_f + w d_z q_f = kappa[f] lap q_f
+ * with kappa[0..2] the viscosity nu and kappa[3..] the scalars'
+ * diffusivities alpha_k (Eq. BS).  Same grid, subdomains (sub[0] * sub[1] <=
+ * 512), order-2 stencils, AT halos and delays as the scalar 3D solver; one
+ * delay per (level, subdomain, face) serves every field (one message per face
+ * carries all fields).  The state and at_set_state / at_state buffers hold
+ * nfields x n[0] n[1] n[2] words; at_info reports that as N. */
+size_t at_system_workspace_bytes(const at_grid *grid, int64_t P, int L, int nfields);
+int at_create_system(const at_grid *grid, int64_t P, int L, int nfields, const double *kappa, double dt,
+                     at_solver **out);
+
+/* Mean and mean square of every field of a 3D solver's state (the one-point
+ * moments whose statistics the paper follows): out[2 f] = <q_f>,
+ * out[2 f + 1] = <q_f^2>, summed in FP64.  Synchronises; returns the device
+ * status. */
+int at_moments(at_solver *h, double *out);
+
 /* ---------------------------------------------------------------------------
  * Ensembles: many independent 1D problems advanced by one persistent launch.
  *

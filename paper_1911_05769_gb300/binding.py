@@ -108,6 +108,12 @@ _SIGNATURES = [
      [ctypes.POINTER(at_grid), ctypes.c_int64, ctypes.POINTER(at_instance), ctypes.c_int64, ctypes.c_int,
       ctypes.POINTER(ctypes.c_void_p)]),
     ("at_tune", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.POINTER(at_tune_result)]),
+    ("at_system_workspace_bytes", ctypes.c_size_t,
+     [ctypes.POINTER(at_grid), ctypes.c_int64, ctypes.c_int, ctypes.c_int]),
+    ("at_create_system", ctypes.c_int,
+     [ctypes.POINTER(at_grid), ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+      ctypes.c_double, ctypes.POINTER(ctypes.c_void_p)]),
+    ("at_moments", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
     ("at_step_levels", ctypes.c_int,
      [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64]),
     ("at_set_history", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64]),
@@ -221,6 +227,25 @@ def at_tune(h, n_steps: int, delay_mode: int):
     res = at_tune_result()
     rc = lib().at_tune(h, n_steps, delay_mode, ctypes.byref(res))
     return rc, res
+
+
+def at_system_workspace_bytes(grid: at_grid, P: int, L: int, nfields: int) -> int:
+    return int(lib().at_system_workspace_bytes(ctypes.byref(grid), P, L, nfields))
+
+
+def at_create_system(grid: at_grid, P: int, L: int, kappa, dt: float):
+    """Returns (code, handle); kappa: one viscosity/diffusivity per field (3..5 fields)."""
+    kap = (ctypes.c_double * len(kappa))(*kappa)
+    h = ctypes.c_void_p()
+    rc = lib().at_create_system(ctypes.byref(grid), P, L, len(kappa), kap, dt, ctypes.byref(h))
+    return rc, h
+
+
+def at_moments(h, nfields: int):
+    """Returns (code, [(mean, mean square) per field])."""
+    out = (ctypes.c_double * (2 * nfields))()
+    rc = lib().at_moments(h, out)
+    return rc, [(out[2 * f], out[2 * f + 1]) for f in range(nfields)]
 
 
 def _vp(ptr):

@@ -32,6 +32,7 @@ void *atk_restore_kernel_f32(int order);
 void *atk_restore_kernel_f64(int order);
 void *atk_adjoint_kernel(int w, int order);
 void *atk_stepper3d_kernel(int w, int tc);
+void *atk_system3d_kernel(int w, int tc, int nf);
 void *atk_init3d_kernel(int w);
 
 namespace {
@@ -130,18 +131,19 @@ int check_args3(const at_grid *g, int64_t P, int order, int L, Dims3 *d)
     return AT_OK;
 }
 
-Layout layout3(const Dims3 &d, int64_t P, int w, int L, int T)
+Layout layout3(const Dims3 &d, int64_t P, int w, int L, int T, int nf = 1)
 {
     Layout l{};
     size_t off = 0;
     const int64_t N = d.n[0] * d.n[1] * d.n[2];
-    l.u = off;    off = align_up(off + (size_t)N * w, 256);
-    l.ring = off; off = align_up(off + (size_t)T * P * 6 * d.face_words * w, 256);
+    l.u = off;    off = align_up(off + (size_t)nf * N * w, 256);
+    l.ring = off; off = align_up(off + (size_t)T * P * 6 * nf * d.face_words * w, 256);
     l.flag = off; off = align_up(off + (size_t)P * 6 * 8, 256);
     l.ctrl = off; off = align_up(off + atk::kCtrlWords * 4, 256);
     l.hist = off; off = align_up(off + (size_t)(L + 1) * 8, 256);
     l.gbar = off; off = align_up(off + 8, 256);
-    l.bsub = off; l.binst = off;
+    l.bsub = off; l.binst = off;   // (3D: per-block moment sums of at_moments, 4096 x 2 nf doubles)
+    off = align_up(off + (size_t)4096 * 2 * nf * 8, 256);
     l.total = off;
     return l;
 }
@@ -282,7 +284,9 @@ struct at_solver {
     int dim;                   // 1 or 3
     Dims3 d3;                  // 3D: extents, subdomains, ring entry size
     int tc;                    // 3D: columns per thread
-    CUtensorMap tmap;          // 3D: tensor map of the state (planes of a subdomain)
+    CUtensorMap tmap;          // 3D: tensor map of the state (planes of a subdomain, all fields)
+    int nf;                    // 3D: fields (1: the scalar equation; 3..5: the system)
+    double kappa[atk::kMaxFields3];   // 3D system: viscosity / diffusivities of the fields
     bool v64;                  // FP32 state with FP64 viscous accumulation
     bool batch;                // ensemble of instances
     int64_t n_inst;
@@ -349,28 +353,33 @@ size_t at_workspace_bytes(const at_grid *grid, int64_t P, int scheme_order, int 
     if (grid->dim == 3) {
         Dims3 d;
         check_args3(grid, P, scheme_order, L, &d);
-        return layout3(d, P, w, L, ring_slots(L, s)).total;
+        return layout3(d, P, w, L, ring_slots(L, s), 1).total;
     }
     return layout(grid->n[0], P, w, L, ring_slots(L, s)).total;
 }
 
-static int create3d(const at_grid *grid, int64_t P, int L, double nu, double dt, at_solver **out)
+// nf = 1: the scalar equation with viscosity kappa[0]; nf = 3..5: the system
+static int create3d(const at_grid *grid, int64_t P, int L, int nf, const double *kappa, double dt, at_solver **out)
 {
     Dims3 d;
     int rc = check_args3(grid, P, 2, L, &d);
     if (rc != AT_OK) return rc;
     if (!(dt > 0.0) || !std::isfinite(dt)) return fail(AT_ERR_ARG, "dt must be positive");
-    if (!(nu >= 0.0) || !std::isfinite(nu)) return fail(AT_ERR_ARG, "nu must be >= 0");
+    double kmax = 0.0;
+    for (int f = 0; f < nf; ++f) {
+        if (!(kappa[f] >= 0.0) || !std::isfinite(kappa[f])) return fail(AT_ERR_ARG, "viscosity/diffusivity %d must be >= 0", f);
+        if (kappa[f] > kmax) kmax = kappa[f];
+    }
     double dx[3], sum = 0.0;
     for (int a = 0; a < 3; ++a) {
         dx[a] = grid->length[a] / (double)d.n[a];
         sum += 1.0 / (dx[a] * dx[a]);
     }
-    if (!(grid->flags & AT_FLAG_ALLOW_UNSTABLE) && nu * dt * sum > 0.5)
-        return fail(AT_ERR_UNSTABLE, "nu*dt*(1/dx^2+1/dy^2+1/dz^2) = %g exceeds 1/2", nu * dt * sum);
+    if (!(grid->flags & AT_FLAG_ALLOW_UNSTABLE) && kmax * dt * sum > 0.5)
+        return fail(AT_ERR_UNSTABLE, "kappa*dt*(1/dx^2+1/dy^2+1/dz^2) = %g exceeds 1/2", kmax * dt * sum);
     const int w = grid->dtype == AT_F64 ? 8 : 4;
     const int T = ring_slots(L, 2);
-    const Layout lay = layout3(d, P, w, L, T);
+    const Layout lay = layout3(d, P, w, L, T, nf);
     if (!grid->workspace) return fail(AT_ERR_ARG, "workspace is NULL");
     if (grid->workspace_bytes < lay.total)
         return fail(AT_ERR_ARG, "workspace too small: %zu < %zu", grid->workspace_bytes, lay.total);
@@ -386,13 +395,14 @@ static int create3d(const at_grid *grid, int64_t P, int L, double nu, double dt,
 
     const int pw = d.m[0] * d.m[1];
     const int tc = pw <= atk::kThreads3 ? 1 : pw <= 2 * atk::kThreads3 ? 2 : 4;
-    void *kern = atk_stepper3d_kernel(w, tc);
+    if (nf > 1 && tc > 2) return fail(AT_ERR_ARG, "the 3D system needs sub[0] * sub[1] <= 512");
+    void *kern = nf == 1 ? atk_stepper3d_kernel(w, tc) : atk_system3d_kernel(w, tc, nf);
     // plane buffers: at least 3 (planes z and z+1 in use, one arriving), at most sub[2]
     int stages = grid->stages > 0 ? grid->stages : 4;
     if (stages < 3) stages = 3;
     if (stages > d.m[2]) stages = d.m[2];
-    atk::Smem3 sl3 = atk::smem3_layout(d.m[0], d.m[1], d.m[2], w, stages);
-    while (sl3.total > smem_optin && stages > 3) sl3 = atk::smem3_layout(d.m[0], d.m[1], d.m[2], w, --stages);
+    atk::Smem3 sl3 = atk::smem3_layout(d.m[0], d.m[1], d.m[2], w, stages, nf);
+    while (sl3.total > smem_optin && stages > 3) sl3 = atk::smem3_layout(d.m[0], d.m[1], d.m[2], w, --stages, nf);
     if (sl3.total > smem_optin) return fail(AT_ERR_RESIDENCY, "shared memory %lld exceeds %d", sl3.total, smem_optin);
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sl3.total);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
@@ -411,11 +421,13 @@ static int create3d(const at_grid *grid, int64_t P, int L, double nu, double dt,
     h->dim = 3;
     h->d3 = d;
     h->tc = tc;
-    h->N = d.n[0] * d.n[1] * d.n[2];
+    h->nf = nf;
+    for (int f = 0; f < nf; ++f) h->kappa[f] = kappa[f];
+    h->N = (int64_t)nf * d.n[0] * d.n[1] * d.n[2];   // words of the state (all fields)
     h->P = P;
     h->M = (int64_t)d.m[0] * d.m[1] * d.m[2];
     h->order = 2; h->L = L; h->R = 1; h->s = 2; h->T = T; h->w = w;
-    h->nu = nu; h->dt = dt; h->dx = dx[0];
+    h->nu = kappa[0]; h->dt = dt; h->dx = dx[0];
     h->lay = lay;
     h->ws = static_cast<unsigned char *>(grid->workspace);
     h->stream = static_cast<cudaStream_t>(grid->stream);
@@ -437,11 +449,13 @@ static int create3d(const at_grid *grid, int64_t P, int L, double nu, double dt,
         delete h;
         return fail(AT_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
     }
-    const cuuint64_t gdim[3] = {(cuuint64_t)d.n[0], (cuuint64_t)d.n[1], (cuuint64_t)d.n[2]};
-    const cuuint64_t gstride[2] = {(cuuint64_t)(d.n[0] * w), (cuuint64_t)(d.n[0] * d.n[1] * w)};
-    const cuuint32_t box[3] = {(cuuint32_t)d.m[0], (cuuint32_t)d.m[1], 1u};
-    const cuuint32_t estride[3] = {1u, 1u, 1u};
-    const CUresult cr = encode(&h->tmap, w == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
+    // 4D: x, y, z, field; a box is one plane of a subdomain in every field
+    const cuuint64_t gdim[4] = {(cuuint64_t)d.n[0], (cuuint64_t)d.n[1], (cuuint64_t)d.n[2], (cuuint64_t)nf};
+    const cuuint64_t gstride[3] = {(cuuint64_t)(d.n[0] * w), (cuuint64_t)(d.n[0] * d.n[1] * w),
+                                   (cuuint64_t)(d.n[0] * d.n[1] * d.n[2] * w)};
+    const cuuint32_t box[4] = {(cuuint32_t)d.m[0], (cuuint32_t)d.m[1], 1u, (cuuint32_t)nf};
+    const cuuint32_t estride[4] = {1u, 1u, 1u, 1u};
+    const CUresult cr = encode(&h->tmap, w == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4,
                                h->ws + lay.u, gdim, gstride, box, estride, CU_TENSOR_MAP_INTERLEAVE_NONE,
                                CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -471,7 +485,9 @@ static atk::Params3 make_params3(const at_solver *h)
         const double dxa = h->g.length[a] / (double)h->d3.n[a];
         p.cA[a] = h->dt / (2.0 * dxa);
         p.cB[a] = h->nu * h->dt / (dxa * dxa);
+        for (int f = 0; f < h->nf; ++f) p.cBf[f][a] = h->kappa[f] * h->dt / (dxa * dxa);
     }
+    p.nf = h->nf;
     p.face_words = h->d3.face_words;
     p.G = h->G;
     p.timeout_ns = h->g.timeout_ns;
@@ -483,7 +499,7 @@ int at_create(const at_grid *grid, int64_t P, int scheme_order, int L, double nu
     g_err[0] = 0;
     if (!out) return fail(AT_ERR_ARG, "out is NULL");
     *out = nullptr;
-    if (grid && grid->dim == 3) return create3d(grid, P, L, nu, dt, out);
+    if (grid && grid->dim == 3) return create3d(grid, P, L, 1, &nu, dt, out);
     int rc = check_args(grid, P, scheme_order, L);
     if (rc != AT_OK) return rc;
     if (!(dt > 0.0) || !std::isfinite(dt)) return fail(AT_ERR_ARG, "dt must be positive");
@@ -596,7 +612,7 @@ int at_set_state(at_solver *h, const void *u)
     if (h->dim == 3) {
         atk::Params3 p = make_params3(h);
         void *args[] = {&p};
-        const long long work = h->P * 6 * h->d3.face_words;
+        const long long work = h->P * 6 * h->nf * h->d3.face_words;
         const int blocks = (int)((work + 255) / 256 < 4096 ? (work + 255) / 256 : 4096);
         e = cudaLaunchKernel(h->init_kernel, dim3(blocks), dim3(256), args, 0, h->stream);
         if (e != cudaSuccess) return cuda_fail(e, "launch at_init3d");
@@ -1356,3 +1372,97 @@ extern "C" int at_step_noalloc(const at_grid *grid, int64_t P, int scheme_order,
     }
     return read_status(&h);
 }
+
+// ---------------------------------------------------------------------------
+// The 3D system of Eq. BS and its moments
+// ---------------------------------------------------------------------------
+namespace {
+
+// per-block sums of q and q^2 of every field (FP64), block b at [b][2 nf]
+template <typename T>
+__global__ void at_moments_kernel(const T *q, long long npts, int nf, double *part)
+{
+    __shared__ double red[256];
+    for (int f = 0; f < nf; ++f) {
+        for (int m = 0; m < 2; ++m) {
+            double acc = 0.0;
+            for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < npts;
+                 i += (long long)gridDim.x * blockDim.x) {
+                const double v = (double)q[(size_t)f * npts + i];
+                acc += m == 0 ? v : v * v;
+            }
+            red[threadIdx.x] = acc;
+            __syncthreads();
+            for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+                if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+                __syncthreads();
+            }
+            if (threadIdx.x == 0) part[(size_t)blockIdx.x * 2 * nf + 2 * f + m] = red[0];
+            __syncthreads();
+        }
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t at_system_workspace_bytes(const at_grid *grid, int64_t P, int L, int nfields)
+{
+    if (!grid || grid->dim != 3) { fail(AT_ERR_ARG, "the system needs dim = 3"); return 0; }
+    if (nfields < 3 || nfields > 5) { fail(AT_ERR_ARG, "nfields must be 3, 4 or 5"); return 0; }
+    Dims3 d;
+    if (check_args3(grid, P, 2, L, &d) != AT_OK) return 0;
+    const int w = grid->dtype == AT_F64 ? 8 : 4;
+    return layout3(d, P, w, L, ring_slots(L, 2), nfields).total;
+}
+
+int at_create_system(const at_grid *grid, int64_t P, int L, int nfields, const double *kappa, double dt,
+                     at_solver **out)
+{
+    g_err[0] = 0;
+    if (!out) return fail(AT_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!grid || grid->dim != 3) return fail(AT_ERR_ARG, "the system needs dim = 3");
+    if (nfields < 3 || nfields > 5) return fail(AT_ERR_ARG, "nfields must be 3, 4 or 5");
+    if (!kappa) return fail(AT_ERR_ARG, "kappa is NULL");
+    return create3d(grid, P, L, nfields, kappa, dt, out);
+}
+
+int at_moments(at_solver *h, double *out)
+{
+    g_err[0] = 0;
+    if (!h || !out) return fail(AT_ERR_ARG, "NULL argument");
+    if (h->dim != 3) return fail(AT_ERR_ARG, "at_moments is for 3D solvers");
+    if (!h->has_state) return fail(AT_ERR_STATE, "at_moments before at_set_state");
+    const long long npts = h->d3.n[0] * h->d3.n[1] * h->d3.n[2];
+    const int blocks = (int)((npts + 255) / 256 < 4096 ? (npts + 255) / 256 : 4096);
+    double *part = reinterpret_cast<double *>(h->ws + h->lay.bsub);
+    cudaError_t e;
+    if (h->w == 8) {
+        at_moments_kernel<double><<<blocks, 256, 0, h->stream>>>(reinterpret_cast<const double *>(h->ws + h->lay.u),
+                                                                 npts, h->nf, part);
+    } else {
+        at_moments_kernel<float><<<blocks, 256, 0, h->stream>>>(reinterpret_cast<const float *>(h->ws + h->lay.u),
+                                                                npts, h->nf, part);
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "launch at_moments_kernel");
+    std::vector<double> host((size_t)blocks * 2 * h->nf);
+    e = cudaMemcpyAsync(host.data(), part, host.size() * 8, cudaMemcpyDeviceToHost, h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(moments)");
+    const int rc = read_status(h);
+    if (rc != AT_OK) return rc;
+    for (int f = 0; f < h->nf; ++f) {
+        double s1 = 0.0, s2 = 0.0;
+        for (int b = 0; b < blocks; ++b) {
+            s1 += host[(size_t)b * 2 * h->nf + 2 * f];
+            s2 += host[(size_t)b * 2 * h->nf + 2 * f + 1];
+        }
+        out[2 * f] = s1 / (double)npts;
+        out[2 * f + 1] = s2 / (double)npts;
+    }
+    return AT_OK;
+}
+
+}  // extern "C"

@@ -92,6 +92,16 @@ __device__ __forceinline__ void tensor_load_3d(void *dst_smem, const void *tmap,
         : "memory");
 }
 
+// The same for a 4D tensor map (element coordinates x, y, z, w).
+__device__ __forceinline__ void tensor_load_4d(void *dst_smem, const void *tmap, int x, int y, int z, int w,
+                                               uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];"
+        ::"r"(smem_addr(dst_smem)), "l"(tmap), "r"(x), "r"(y), "r"(z), "r"(w), "r"(smem_addr(bar))
+        : "memory");
+}
+
 // Orders this thread's earlier generic-proxy global accesses before later
 // async-proxy accesses (a bulk copy re-reading data written with st.global).
 __device__ __forceinline__ void fence_proxy_async_global()

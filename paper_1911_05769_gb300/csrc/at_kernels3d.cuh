@@ -35,6 +35,7 @@
 namespace atk {
 
 constexpr int kThreads3 = 256;
+constexpr int kMaxFields3 = 6;          // fields of the system (u, v, w and up to 3 scalars)
 #ifndef AT_MIN_CTAS_3D
 #define AT_MIN_CTAS_3D 2      // resident CTAs per SM the 3D stepper is compiled for
 #endif
@@ -54,7 +55,9 @@ struct Params3 {
     long long n_steps;
     unsigned long long seed;
     double cA[3], cB[3];        // dt / (2 dx_a), nu dt / dx_a^2
-    long long face_words;       // words per ring entry (a multiple of 4)
+    double cBf[kMaxFields3][3]; // the system: kappa_f dt / dx_a^2 per field
+    int nf;                     // fields (1: the scalar equation)
+    long long face_words;       // words per field of a ring entry (a multiple of 4)
     int G;
     long long timeout_ns;
 };
@@ -66,7 +69,7 @@ struct Smem3 {
     long long bar_off, hist_off, face_off, halo_off, halo_words[6], halo_at[6], stage_off, plane_bytes, total;
 };
 
-__host__ __device__ inline Smem3 smem3_layout(int m0, int m1, int m2, int word, int stages)
+__host__ __device__ inline Smem3 smem3_layout(int m0, int m1, int m2, int word, int stages, int nf = 1)
 {
     Smem3 l;
     l.bar_off = 0;                                   // full[stages], then empty[stages]
@@ -74,13 +77,13 @@ __host__ __device__ inline Smem3 smem3_layout(int m0, int m1, int m2, int word, 
     l.face_off = round_up(l.hist_off + 4LL * (kMaxL + 1), 16);
     l.halo_off = round_up(l.face_off + 6 * 16 + 16, 128);
     long long at = l.halo_off;
-    for (int f = 0; f < 6; ++f) {
+    for (int f = 0; f < 6; ++f) {                    // per face: nf fields of halo_words each
         l.halo_words[f] = f < 2 ? (long long)m1 * m2 : f < 4 ? (long long)m0 * m2 : (long long)m0 * m1;
         l.halo_at[f] = at;
-        at = round_up(at + l.halo_words[f] * word, 16);
+        at = round_up(at + (long long)nf * l.halo_words[f] * word, 16);
     }
     l.stage_off = round_up(at, 128);
-    l.plane_bytes = round_up((long long)m0 * m1 * word, 128);
+    l.plane_bytes = round_up((long long)nf * m0 * m1 * word, 128);   // a plane of every field
     l.total = l.stage_off + (long long)stages * l.plane_bytes;
     return l;
 }
@@ -163,27 +166,36 @@ __device__ __forceinline__ long long face_neighbour(const Params3 &p, long long 
     return (q2 * p.P1 + q1) * p.P0 + q0;
 }
 
+// ring entry of (level, subdomain, face): nf arrays of face_words words
 template <typename T>
 __device__ __forceinline__ T *ring_entry(const Params3 &p, long long level, long long sub, int face)
 {
     return reinterpret_cast<T *>(p.ring) +
-           (((size_t)(level & (p.T - 1)) * p.P + sub) * 6 + face) * (size_t)p.face_words;
+           (((size_t)(level & (p.T - 1)) * p.P + sub) * 6 + face) * (size_t)p.face_words * (size_t)p.nf;
 }
 
-template <typename T, int TC>
+// NF fields stored one after another; SYS: the system of Eq. BS (fields 0, 1,
+// 2 are the velocity (u, v, w), each field is advected by it and diffused with
+// its own kappa); otherwise NF = 1 and the scalar equation
+// u_t + u (u_x + u_y + u_z) = nu lap u.  A plane of every field arrives with
+// one copy of a 4D tensor map (x, y, z, field).
+template <typename T, int TC, int NF, bool SYS>
 __global__ void __launch_bounds__(kThreads3, AT_MIN_CTAS_3D) at_stepper3d(const Params3 p, const __grid_constant__ CUtensorMap tmap)
 {
     extern __shared__ __align__(128) unsigned char smem[];
-    const Smem3 sl = smem3_layout(p.m0, p.m1, p.m2, (int)sizeof(T), p.stages);
+    const Smem3 sl = smem3_layout(p.m0, p.m1, p.m2, (int)sizeof(T), p.stages, NF);
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + sl.bar_off);
     unsigned *hist = reinterpret_cast<unsigned *>(smem + sl.hist_off);
     int *s_k = reinterpret_cast<int *>(smem + sl.face_off);                  // [6] delays of the tile
     long long *s_q = reinterpret_cast<long long *>(smem + sl.face_off + 32);  // [6] face neighbours
     int *s_flag = reinterpret_cast<int *>(smem + sl.face_off + 80);          // barrier / abort word
     unsigned char *stages = smem + sl.stage_off;
+    // halo planes of face f, field q: halo_at[f] + q * halo_words[f] words
     T *hx0 = reinterpret_cast<T *>(smem + sl.halo_at[0]), *hx1 = reinterpret_cast<T *>(smem + sl.halo_at[1]);
     T *hy0 = reinterpret_cast<T *>(smem + sl.halo_at[2]), *hy1 = reinterpret_cast<T *>(smem + sl.halo_at[3]);
     T *hz0 = reinterpret_cast<T *>(smem + sl.halo_at[4]), *hz1 = reinterpret_cast<T *>(smem + sl.halo_at[5]);
+    const int hwx = (int)sl.halo_words[0], hwy = (int)sl.halo_words[2], hwz = (int)sl.halo_words[4];
+    const long long fw = p.face_words;
 
     const int tid = threadIdx.x, lane = tid & 31;
     const long long lo = (long long)blockIdx.x * p.P / p.G, hi = (long long)(blockIdx.x + 1) * p.P / p.G;
@@ -192,11 +204,17 @@ __global__ void __launch_bounds__(kThreads3, AT_MIN_CTAS_3D) at_stepper3d(const 
     const int NS = p.stages;
     const int m0 = p.m0, m1 = p.m1, m2 = p.m2;
     const int PW = m0 * m1;
-    const unsigned plane_bytes = (unsigned)(PW * (int)sizeof(T));
+    const unsigned plane_bytes = (unsigned)(NF * PW * (int)sizeof(T));   // one box: a plane of every field
     const long long Q = p.n_steps * S * m2;                 // planes this CTA sweeps
     const T cA0 = (T)p.cA[0], cA1 = (T)p.cA[1], cA2 = (T)p.cA[2];
-    const T cB0 = (T)p.cB[0], cB1 = (T)p.cB[1], cB2 = (T)p.cB[2];
+    T cB[NF][3];
+#pragma unroll
+    for (int q = 0; q < NF; ++q) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) cB[q][a] = (T)(SYS ? p.cBf[q][a] : p.cB[a]);
+    }
     T *u = reinterpret_cast<T *>(p.u);
+    const long long field_words = p.n0 * p.n1 * p.n2;
 
     constexpr int kWarps3 = kThreads3 / 32;
     uint64_t *empty = bars + NS;           // every warp arrives once it is done with a stage
@@ -238,7 +256,7 @@ __global__ void __launch_bounds__(kThreads3, AT_MIN_CTAS_3D) at_stepper3d(const 
             if (lane == 0) {
                 uint64_t *bar = &bars[i_stage];
                 mbar_arrive_expect_tx(bar, plane_bytes);
-                tensor_load_3d(stages + (size_t)i_stage * sl.plane_bytes, &tmap, i_x0, i_y0, i_z0 + i_z, bar);
+                tensor_load_4d(stages + (size_t)i_stage * sl.plane_bytes, &tmap, i_x0, i_y0, i_z0 + i_z, 0, bar);
             }
             __syncwarp();
         }
@@ -263,9 +281,11 @@ __global__ void __launch_bounds__(kThreads3, AT_MIN_CTAS_3D) at_stepper3d(const 
         coff[q] = cy[q] * (int)p.n0 + cx[q];
         cface[q] = (cx[q] == 0 ? 1 : 0) | (cx[q] == m0 - 1 ? 2 : 0) | (cy[q] == 0 ? 4 : 0) | (cy[q] == m1 - 1 ? 8 : 0);
     }
-    T prev[TC], cur[TC];
+    T prev[NF][TC], cur[NF][TC];
 #pragma unroll
-    for (int q = 0; q < TC; ++q) prev[q] = cur[q] = (T)0;
+    for (int f = 0; f < NF; ++f)
+#pragma unroll
+        for (int q = 0; q < TC; ++q) prev[f][q] = cur[f][q] = (T)0;
 
     while (issued < NS && issued < Q) issue();
     // a failed wait is recorded in s_flag; every thread acts on it at the
@@ -344,18 +364,23 @@ __global__ void __launch_bounds__(kThreads3, AT_MIN_CTAS_3D) at_stepper3d(const 
             const T *e1 = ring_entry<T>(p, lv - k - 1, s_q[f], f ^ 1);
             T *h = reinterpret_cast<T *>(smem + sl.halo_at[f]);
             const int nw = (int)sl.halo_words[f];
-            for (int i = tid; i < nw; i += kThreads3)
-                h[i] = k == 0 ? e0[i] : (T)(k + 1) * e0[i] - (T)k * e1[i];
+            for (int fld = 0; fld < NF; ++fld)
+                for (int i = tid; i < nw; i += kThreads3)
+                    h[fld * nw + i] = k == 0 ? e0[fld * fw + i] : (T)(k + 1) * e0[fld * fw + i] - (T)k * e1[fld * fw + i];
         }
         __syncthreads();
         // plane z = -1 (the -z halo) and plane 0
-#pragma unroll
-        for (int q = 0; q < TC; ++q) prev[q] = cv[q] ? hz0[cy[q] * m0 + cx[q]] : (T)0;
         if (!wait_plane(g)) { ok = false; }
         {
             const T *st0 = reinterpret_cast<const T *>(stages + (size_t)(g % NS) * sl.plane_bytes);
 #pragma unroll
-            for (int q = 0; q < TC; ++q) cur[q] = cv[q] ? st0[cy[q] * m0 + cx[q]] : (T)0;
+            for (int f = 0; f < NF; ++f) {
+#pragma unroll
+                for (int q = 0; q < TC; ++q) {
+                    prev[f][q] = cv[q] ? hz0[f * hwz + cy[q] * m0 + cx[q]] : (T)0;
+                    cur[f][q] = cv[q] ? st0[f * PW + cy[q] * m0 + cx[q]] : (T)0;
+                }
+            }
         }
         const long long lnew = lv + 1;
         // ---- the planes of the tile; warps run independently (stage
@@ -372,29 +397,41 @@ __global__ void __launch_bounds__(kThreads3, AT_MIN_CTAS_3D) at_stepper3d(const 
             for (int q = 0; q < TC; ++q) {
                 if (!cv[q]) continue;
                 const int x = cx[q], y = cy[q], c = y * m0 + x;
-                const T cc = cur[q], below = prev[q];
-                const T above = top ? hz1[c] : stn[c];
                 const int fc = cface[q];
-                const T xm = (fc & 1) ? hx0[zy + y] : st[c - 1];
-                const T xp = (fc & 2) ? hx1[zy + y] : st[c + 1];
-                const T ym = (fc & 4) ? hy0[zx + x] : st[c - m0];
-                const T yp = (fc & 8) ? hy1[zx + x] : st[c + m0];
-                const T d1 = cA0 * (xp - xm) + cA1 * (yp - ym) + cA2 * (above - below);
-                const T d2 = cB0 * ((xp + xm) - (T)2 * cc) + cB1 * ((yp + ym) - (T)2 * cc) +
-                             cB2 * ((above + below) - (T)2 * cc);
-                const T un = cc + (d2 - cc * d1);
-                up[coff[q]] = un;
-                // boundary values of the new level into the ring
-                if (fc) {
-                    if (fc & 1) rf[0][zy + y] = un;
-                    if (fc & 2) rf[1][zy + y] = un;
-                    if (fc & 4) rf[2][zx + x] = un;
-                    if (fc & 8) rf[3][zx + x] = un;
+                // advecting velocity at the point, level n (the system)
+                const T U = SYS ? cur[0][q] : (T)0, V = SYS ? cur[1 % NF][q] : (T)0, Wv = SYS ? cur[2 % NF][q] : (T)0;
+#pragma unroll
+                for (int f = 0; f < NF; ++f) {
+                    const T *sf = st + f * PW;
+                    const T cc = cur[f][q], below = prev[f][q];
+                    const T above = top ? hz1[f * hwz + c] : stn[f * PW + c];
+                    const T xm = (fc & 1) ? hx0[f * hwx + zy + y] : sf[c - 1];
+                    const T xp = (fc & 2) ? hx1[f * hwx + zy + y] : sf[c + 1];
+                    const T ym = (fc & 4) ? hy0[f * hwy + zx + x] : sf[c - m0];
+                    const T yp = (fc & 8) ? hy1[f * hwy + zx + x] : sf[c + m0];
+                    const T d2 = cB[f][0] * ((xp + xm) - (T)2 * cc) + cB[f][1] * ((yp + ym) - (T)2 * cc) +
+                                 cB[f][2] * ((above + below) - (T)2 * cc);
+                    T un;
+                    if constexpr (SYS) {
+                        const T adv = cA0 * U * (xp - xm) + cA1 * V * (yp - ym) + cA2 * Wv * (above - below);
+                        un = cc + (d2 - adv);
+                    } else {
+                        const T d1 = cA0 * (xp - xm) + cA1 * (yp - ym) + cA2 * (above - below);
+                        un = cc + (d2 - cc * d1);
+                    }
+                    up[f * field_words + coff[q]] = un;
+                    // boundary values of the new level into the ring
+                    if (fc) {
+                        if (fc & 1) rf[0][f * fw + zy + y] = un;
+                        if (fc & 2) rf[1][f * fw + zy + y] = un;
+                        if (fc & 4) rf[2][f * fw + zx + x] = un;
+                        if (fc & 8) rf[3][f * fw + zx + x] = un;
+                    }
+                    if (z == 0) rf[4][f * fw + c] = un;
+                    if (top) rf[5][f * fw + c] = un;
+                    prev[f][q] = cc;
+                    cur[f][q] = above;
                 }
-                if (z == 0) rf[4][c] = un;
-                if (top) rf[5][c] = un;
-                prev[q] = cc;
-                cur[q] = above;
             }
             // the next read of a plane written here is a bulk copy (async
             // proxy) at the next level: with two or more subdomains per CTA it
@@ -446,12 +483,14 @@ __global__ void at_init3d(const Params3 p)
 {
     const int PWmax = (int)p.face_words;
     const long long stride = (long long)gridDim.x * blockDim.x;
-    const long long total = p.P * 6 * PWmax;
-    const T *u = reinterpret_cast<const T *>(p.u);
+    const long long total = p.P * 6 * p.nf * PWmax;
+    const long long field_words = p.n0 * p.n1 * p.n2;
     for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += stride) {
-        const long long sub = t / (6 * PWmax);
-        const int f = (int)((t / PWmax) % 6);
+        const long long sub = t / (6 * p.nf * PWmax);
+        const int f = (int)((t / ((long long)p.nf * PWmax)) % 6);
+        const int fld = (int)((t / PWmax) % p.nf);
         const int e = (int)(t % PWmax);
+        const T *u = reinterpret_cast<const T *>(p.u) + (size_t)fld * field_words;
         const long long s0 = sub % p.P0, s1 = (sub / p.P0) % p.P1, s2 = sub / (p.P0 * p.P1);
         int x, y, z;
         if (f < 2) {            // [z][y]
@@ -465,8 +504,8 @@ __global__ void at_init3d(const Params3 p)
             y = e / p.m0; x = e % p.m0; z = f == 4 ? 0 : p.m2 - 1;
         }
         const size_t gi = ((size_t)(s2 * p.m2 + z) * p.n1 + (size_t)(s1 * p.m1 + y)) * p.n0 + (size_t)(s0 * p.m0 + x);
-        ring_entry<T>(p, 0, sub, f)[e] = u[gi];
-        if (e == 0) p.flag[sub * 6 + f] = 0ull;
+        ring_entry<T>(p, 0, sub, f)[(size_t)fld * PWmax + e] = u[gi];
+        if (e == 0 && fld == 0) p.flag[sub * 6 + f] = 0ull;
     }
     if (blockIdx.x == 0) {
         if (threadIdx.x < kCtrlWords) p.ctrl[threadIdx.x] = 0;

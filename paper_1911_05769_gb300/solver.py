@@ -234,3 +234,58 @@ class Solver3D(Solver):
         self.P, self.order, self.L = P, 2, L
         self.faces = 6
         self.shape = (int(n[2]), int(n[1]), int(n[0]))
+
+
+class System3D(Solver3D):
+    """The 3D system of Eq. BS: velocity (u, v, w) and 0..2 passive scalars,
+    ``kappa`` = (nu, nu, nu, alpha_1, ...).  The state holds the fields one
+    after another (shape (nfields, n2, n1, n0)); delays are [n_steps, P, 6]."""
+
+    def __init__(self, n, sub, L, kappa, dt, *, dtype="f32", length=(2 * math.pi,) * 3, seed=0, flags=0,
+                 timeout_ns=0, max_ctas=0, stages=0, stream=None, device=None):
+        import torch
+        self.torch = torch
+        dev = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        self.device = dev
+        self.stream = stream if stream is not None else torch.cuda.current_stream(dev)
+        self.tdtype = torch.float64 if dtype == "f64" else torch.float32
+        g = B.at_grid()
+        g.dim, g.bc = 3, B.AT_BC_PERIODIC
+        g.dtype = B.AT_F64 if dtype == "f64" else B.AT_F32
+        g.flags = flags
+        for a in range(3):
+            g.n[a] = int(n[a])
+            g.sub[a] = int(sub[a])
+            g.length[a] = float(length[a])
+        g.seed = seed & (2 ** 64 - 1)
+        g.timeout_ns = timeout_ns
+        g.max_ctas = max_ctas
+        g.stages = stages
+        P = 1
+        for a in range(3):
+            P *= int(n[a]) // int(sub[a])
+        nf = len(kappa)
+        nbytes = B.at_system_workspace_bytes(g, P, L, nf)
+        if nbytes == 0:
+            raise B.AtError(B.AT_ERR_ARG, "at_system_workspace_bytes")
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+        g.workspace = self.workspace.data_ptr()
+        g.workspace_bytes = nbytes
+        g.stream = self.stream.cuda_stream
+        self.grid = g
+        rc, h = B.at_create_system(g, P, L, list(kappa), dt)
+        if rc != B.AT_OK:
+            raise B.AtError(rc, "at_create_system")
+        self.h = h
+        self.nfields = nf
+        self.N = nf * int(n[0]) * int(n[1]) * int(n[2])
+        self.P, self.order, self.L = P, 2, L
+        self.faces = 6
+        self.shape = (nf, int(n[2]), int(n[1]), int(n[0]))
+
+    def moments(self):
+        """[(mean, mean square)] per field (FP64 sums on the device)."""
+        rc, m = B.at_moments(self.h, self.nfields)
+        if rc != B.AT_OK:
+            raise B.AtError(rc, "at_moments")
+        return m

@@ -744,6 +744,33 @@ def gpu_arm(args, ws, rank, local, pg):
             err = float(np.max(np.abs(g[cut:-cut] - ref[cut:-cut])) / np.max(np.abs(ref)))
             line["err_vs_fp64_oracle"] = {"rel_linf": err, "mode": "seeded", "steps": csteps,
                                           "points_compared": int(nsub * M - 2 * cut), "dtype": args.dtype}
+            if args.dtype == "f32":
+                # the compensated state (second FP32 word per point, two-sum
+                # updates): throughput of the headline arm and the same error
+                sc = at.Solver(N, P, order, L, nu, dt, dtype="f32", forcing_amp=A, seed=cfg["seed"], stream=stream,
+                               device=local, steps_per_pass=spp, flags=at.AT_FLAG_COMPENSATED)
+                sc.set_state(u0_dev)
+                for _ in range(2):
+                    sc.step(S, at.AT_FREE)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                with torch.cuda.stream(stream):
+                    e0.record(stream)
+                    for _ in range(3):
+                        sc.step(S, at.AT_FREE)
+                    e1.record(stream)
+                torch.cuda.synchronize(dev)
+                cval = N * S * 3 / (e0.elapsed_time(e1) * 1e-3) / 1e9
+                sc.close()
+                sc = at.Solver(N, P, order, L, nu, dt, dtype="f32", forcing_amp=A, seed=cfg["seed"], stream=stream,
+                               device=local, flags=at.AT_FLAG_COMPENSATED)
+                sc.set_state(u0_dev)
+                sc.step(csteps, at.AT_SEEDED)
+                gc = sc.state().double().cpu().numpy()[:nsub * M]
+                sc.close()
+                line["compensated"] = {
+                    "value": cval, "unit": UNIT, "mode": "free, passes of L+1",
+                    "err_vs_fp64_oracle": float(np.max(np.abs(gc[cut:-cut] - ref[cut:-cut])) / np.max(np.abs(ref))),
+                    "note": "FP32 state + FP32 error word per point (two-sum updates); 2 CTAs per SM"}
         # the latency-bound case: N = 4096, P = 16 subdomains of 256 points,
         # order 2, L = 2, FP64 (one PE per subdomain, four CTAs), AT vs barrier
         line["small_config"] = small_config(args, at, torch, dev, stream)

@@ -78,6 +78,13 @@ extern "C" {
                                           update).  Chosen automatically when
                                           nu dt / dx^2 >= 0.8 x the stability limit */
 #define AT_FLAG_VISCOUS_FP32       16  /* FP32 state: never use FP64 for it */
+#define AT_FLAG_COMPENSATED        32  /* FP32 state (1D single domain): keep the
+                                          rounding error of every stored value in a
+                                          second FP32 word and add each update with an
+                                          error-free two-sum, so that increments far
+                                          below an ulp are not lost; doubles the state
+                                          memory and traffic; not with the adjoint,
+                                          at_set_history or at_step_noalloc */
 
 typedef struct at_solver at_solver;   /* opaque handle */
 

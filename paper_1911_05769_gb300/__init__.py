@@ -13,7 +13,7 @@ missing.
 """
 from .binding import (AT_BC_EXACT_TANH, AT_BC_PERIODIC, AT_ERR_ARG, AT_ERR_CUDA, AT_ERR_RESIDENCY, AT_ERR_STATE,
                       AT_ERR_TIMEOUT, AT_ERR_UNSTABLE, AT_F32, AT_F64, AT_FLAG_ALLOW_UNSTABLE,
-                      AT_FLAG_PER_SUBDOMAIN_DELAY, AT_FLAG_TEST_SKIP_PUBLISH, AT_FLAG_VISCOUS_FP32, AT_FLAG_VISCOUS_FP64, AT_FREE, AT_NOALLOC_SCRATCH_BYTES, AT_OK,
+                      AT_FLAG_COMPENSATED, AT_FLAG_PER_SUBDOMAIN_DELAY, AT_FLAG_TEST_SKIP_PUBLISH, AT_FLAG_VISCOUS_FP32, AT_FLAG_VISCOUS_FP64, AT_FREE, AT_NOALLOC_SCRATCH_BYTES, AT_OK,
                       AT_REPLAY,
                       AT_SEEDED, AT_SYNC, AtError, at_batch_workspace_bytes, at_create, at_create_batch,
                       at_delay_stats, at_destroy, at_get_info, at_grid, at_info, at_instance, at_last_error,

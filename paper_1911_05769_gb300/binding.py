@@ -40,6 +40,7 @@ AT_FLAG_ALLOW_UNSTABLE = 2
 AT_FLAG_TEST_SKIP_PUBLISH = 4
 AT_FLAG_VISCOUS_FP64 = 8
 AT_FLAG_VISCOUS_FP32 = 16
+AT_FLAG_COMPENSATED = 32
 
 AT_NOALLOC_SCRATCH_BYTES = 8 * 1024 * 1024
 

@@ -23,6 +23,7 @@
 
 void *atk_stepper_kernel_f32(int order, int gw, bool forced, bool full);
 void *atk_stepper_kernel_f32v(int order, int gw, bool forced, bool full);
+void *atk_stepper_kernel_f32c(int order, int gw, bool forced, bool full);
 void *atk_stepper_kernel_f64(int order, int gw, bool forced, bool full);
 void *atk_init_kernel_f32(int order);
 void *atk_init_kernel_f64(int order);
@@ -67,17 +68,19 @@ int ring_slots(int L, int s)
 }
 
 struct Layout {
-    size_t u, ring, flag, ctrl, hist, gbar, bsub, binst, total;
+    size_t u, ring, flag, ctrl, hist, gbar, bsub, binst, ur, total;
 };
 
 // Workspace: state, ring buffers [T][P][2], flags [P][2], control block,
 // delay counts, barrier counter; for an ensemble (n_inst > 0) also the
 // subdomain and instance records.
-Layout layout(int64_t N, int64_t P, int w, int L, int T, int64_t n_inst = 0)
+Layout layout(int64_t N, int64_t P, int w, int L, int T, int64_t n_inst = 0, bool comp = false)
 {
     Layout l{};
     size_t off = 0;
     l.u = off;    off = align_up(off + (size_t)N * w, 256);
+    l.ur = off;   // compensated state: the rounding error of every point
+    if (comp) off = align_up(off + (size_t)N * w, 256);
     l.ring = off; off = align_up(off + (size_t)T * P * 2 * atk::kRingEntry, 256);
     l.flag = off; off = align_up(off + (size_t)P * 2 * 8, 256);
     l.ctrl = off; off = align_up(off + atk::kCtrlWords * 4, 256);
@@ -193,9 +196,9 @@ bool viscous_fp64(int w, int order, uint32_t flags, double D)
 }
 
 // The stepper and init kernels for a word size, order, subdomain size,
-// forcing and viscous precision (instantiated in at_kernels_f32.cu,
-// at_kernels_f32v.cu and at_kernels_f64.cu).
-void pick_kernels(int w, int order, int64_t M, bool forced, bool v64, void **stepper, void **init)
+// forcing and precision mode (instantiated in at_kernels_f32.cu,
+// at_kernels_f32v.cu, at_kernels_f32c.cu and at_kernels_f64.cu).
+void pick_kernels(int w, int order, int64_t M, bool forced, bool v64, bool comp, void **stepper, void **init)
 {
     const int gw = groups_per_lane(M);
     const bool full = (M == 128LL * gw);
@@ -203,22 +206,26 @@ void pick_kernels(int w, int order, int64_t M, bool forced, bool v64, void **ste
         *stepper = atk_stepper_kernel_f64(order, gw, forced, full);
         *init = atk_init_kernel_f64(order);
     } else {
-        *stepper = v64 ? atk_stepper_kernel_f32v(order, gw, forced, full) : atk_stepper_kernel_f32(order, gw, forced, full);
+        *stepper = comp  ? atk_stepper_kernel_f32c(order, gw, forced, full)
+                   : v64 ? atk_stepper_kernel_f32v(order, gw, forced, full)
+                         : atk_stepper_kernel_f32(order, gw, forced, full);
         *init = atk_init_kernel_f32(order);
     }
 }
 
 // Shared-memory table of a CTA: `fixed` bytes plus `per_sub` bytes per
-// subdomain of each of its PEs (forcing: sin/cos tables; ensembles: records).
+// subdomain of each of its PEs (forcing: sin/cos tables; ensembles: records);
+// comp: stages hold the error words of a compensated state too.
 struct TabSize {
     long long fixed, per_sub;
+    bool comp;
 };
 
-TabSize tab_size(int64_t M, int w, bool forced, bool batch)
+TabSize tab_size(int64_t M, int w, bool forced, bool batch, bool comp = false)
 {
-    if (batch) return {0, (long long)sizeof(atk::BatchSub)};
-    if (forced) return {2LL * M * w, 2LL * w};
-    return {0, 0};
+    if (batch) return {0, (long long)sizeof(atk::BatchSub), false};
+    if (forced) return {2LL * M * w, 2LL * w, comp};
+    return {0, 0, comp};
 }
 
 // Chooses the CTA count (all co-resident CTAs unless max_ctas is set, at most
@@ -232,7 +239,7 @@ int launch_shape(int64_t M, int w, int64_t P, TabSize tsz, int max_ctas, int sta
         const int64_t E = (int64_t)G * atk::kWarps;
         *smax = (P + E - 1) / E;
         const long long tab = tsz.fixed + (long long)atk::kWarps * *smax * tsz.per_sub;
-        return atk::smem_layout(M, w, st, tab);
+        return atk::smem_layout(M, w, st, tab, tsz.comp);
     };
     // CTAs needed for one PE per subdomain at most
     const int gmax = (int)((P + atk::kWarps - 1) / atk::kWarps);
@@ -288,6 +295,7 @@ struct at_solver {
     int nf;                    // 3D: fields (1: the scalar equation; 3..5: the system)
     double kappa[atk::kMaxFields3];   // 3D system: viscosity / diffusivities of the fields
     bool v64;                  // FP32 state with FP64 viscous accumulation
+    bool comp;                 // FP32 state compensated by a second word per point
     bool batch;                // ensemble of instances
     int64_t n_inst;
     int lmin;                  // smallest delay bound (ensembles), else L
@@ -355,7 +363,7 @@ size_t at_workspace_bytes(const at_grid *grid, int64_t P, int scheme_order, int 
         check_args3(grid, P, scheme_order, L, &d);
         return layout3(d, P, w, L, ring_slots(L, s), 1).total;
     }
-    return layout(grid->n[0], P, w, L, ring_slots(L, s)).total;
+    return layout(grid->n[0], P, w, L, ring_slots(L, s), 0, (grid->flags & AT_FLAG_COMPENSATED) != 0).total;
 }
 
 // nf = 1: the scalar equation with viscosity kappa[0]; nf = 3..5: the system
@@ -512,7 +520,10 @@ int at_create(const at_grid *grid, int64_t P, int scheme_order, int L, double nu
     const int w = grid->dtype == AT_F64 ? 8 : 4;
     const int s = scheme_order / 2 + 1;
     const int T = ring_slots(L, s);
-    const Layout lay = layout(N, P, w, L, T);
+    const bool comp = (grid->flags & AT_FLAG_COMPENSATED) != 0;
+    if (comp && (w != 4 || (grid->flags & AT_FLAG_VISCOUS_FP64)))
+        return fail(AT_ERR_ARG, "AT_FLAG_COMPENSATED needs FP32 state and excludes AT_FLAG_VISCOUS_FP64");
+    const Layout lay = layout(N, P, w, L, T, 0, comp);
     if (!grid->workspace) return fail(AT_ERR_ARG, "workspace is NULL");
     if (grid->workspace_bytes < lay.total)
         return fail(AT_ERR_ARG, "workspace too small: %zu < %zu", grid->workspace_bytes, lay.total);
@@ -539,9 +550,10 @@ int at_create(const at_grid *grid, int64_t P, int scheme_order, int L, double nu
     h->stream = static_cast<cudaStream_t>(grid->stream);
     h->device = dev; h->sm_count = sms; h->smem_optin = smem_optin;
     h->batch = false; h->n_inst = 0; h->lmin = L; h->dim = 1;
-    h->v64 = viscous_fp64(w, scheme_order, (uint32_t)grid->flags, nu * dt / (dx * dx));
+    h->comp = comp;
+    h->v64 = !comp && viscous_fp64(w, scheme_order, (uint32_t)grid->flags, nu * dt / (dx * dx));
 
-    pick_kernels(w, scheme_order, h->M, grid->forcing_amp != 0.0, h->v64, &h->kernel, &h->init_kernel);
+    pick_kernels(w, scheme_order, h->M, grid->forcing_amp != 0.0, h->v64, h->comp, &h->kernel, &h->init_kernel);
 
     // launch shape: by default as many CTAs of kWarps processing elements
     // (warps) as can be resident, at most one PE per subdomain; `stages`
@@ -549,8 +561,8 @@ int at_create(const at_grid *grid, int64_t P, int scheme_order, int L, double nu
     const int sb = grid->steps_per_pass > 0 ? grid->steps_per_pass : 1;
     int stages = grid->stages > 0 ? grid->stages : 3;
     if (stages < atk::kMinStages) stages = atk::kMinStages;
-    int rc2 = launch_shape(h->M, w, P, tab_size(h->M, w, grid->forcing_amp != 0.0, false), grid->max_ctas, stages,
-                           sms, smem_optin, h->kernel, &h->G, &h->stages, &h->sl, &h->smem, &h->smax);
+    int rc2 = launch_shape(h->M, w, P, tab_size(h->M, w, grid->forcing_amp != 0.0, false, comp), grid->max_ctas,
+                           stages, sms, smem_optin, h->kernel, &h->G, &h->stages, &h->sl, &h->smem, &h->smax);
     if (rc2 != AT_OK) { delete h; return rc2; }
     h->sb = sb;
     h->step = 0;
@@ -568,6 +580,7 @@ static atk::Params make_params(const at_solver *h)
     p.ctrl = reinterpret_cast<int *>(h->ws + h->lay.ctrl);
     p.hist = reinterpret_cast<unsigned long long *>(h->ws + h->lay.hist);
     p.gbar = reinterpret_cast<unsigned long long *>(h->ws + h->lay.gbar);
+    if (h->comp) p.ur = h->ws + h->lay.ur;
     if (h->batch) {
         p.bsub = reinterpret_cast<const atk::BatchSub *>(h->ws + h->lay.bsub);
         p.binst = reinterpret_cast<const atk::BatchInst *>(h->ws + h->lay.binst);
@@ -623,6 +636,10 @@ int at_set_state(at_solver *h, const void *u)
     }
     e = cudaMemsetAsync(h->ws + h->lay.ring, 0, (size_t)h->T * h->P * 2 * atk::kRingEntry, h->stream);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(ring)");
+    if (h->comp) {
+        e = cudaMemsetAsync(h->ws + h->lay.ur, 0, (size_t)h->N * h->w, h->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(error words)");
+    }
     atk::Params p = make_params(h);
     void *args[] = {&p};
     const int blocks = (int)((h->P + 255) / 256 < 1024 ? (h->P + 255) / 256 : 1024);
@@ -695,6 +712,7 @@ int at_set_history(at_solver *h, const void *levels, int64_t depth, int64_t leve
     g_err[0] = 0;
     if (!h || !levels) return fail(AT_ERR_ARG, "NULL argument");
     if (h->dim == 3) return fail(AT_ERR_ARG, "at_set_history is for 1D solvers");
+    if (h->comp) return fail(AT_ERR_ARG, "at_set_history does not cover the compensated state");
     if (level < 0) return fail(AT_ERR_ARG, "level < 0");
     const int64_t need = level + 1 < h->L + h->s ? level + 1 : h->L + h->s;
     if (depth < need) return fail(AT_ERR_ARG, "depth %lld holds fewer than the %lld levels needed", (long long)depth,
@@ -984,7 +1002,7 @@ int at_tune(at_solver *h, int64_t n_steps, int delay_mode, at_tune_result *res)
     if (cudaStreamIsCapturing(h->stream, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone)
         return fail(AT_ERR_STATE, "at_tune under stream capture");
     std::memset(res, 0, sizeof(*res));
-    const TabSize tsz = tab_size(h->M, h->w, h->g.forcing_amp != 0.0, h->batch);
+    const TabSize tsz = tab_size(h->M, h->w, h->g.forcing_amp != 0.0, h->batch, h->comp);
     const int gmax = (int)((h->P + atk::kWarps - 1) / atk::kWarps);
 
     cudaEvent_t ev[3];
@@ -1108,6 +1126,7 @@ int check_adjoint_args(const at_solver *h, int64_t n_steps, int64_t interval)
 {
     if (!h) return fail(AT_ERR_ARG, "NULL handle");
     if (h->batch || h->dim == 3) return fail(AT_ERR_ARG, "the adjoint covers single-domain 1D solvers");
+    if (h->comp) return fail(AT_ERR_ARG, "the adjoint does not cover the compensated state");
     if (h->N >= (1LL << 31)) return fail(AT_ERR_ARG, "the adjoint needs N < 2^31");
     if (n_steps < 0) return fail(AT_ERR_ARG, "n_steps < 0");
     if (interval < 1) return fail(AT_ERR_ARG, "interval must be >= 1");
@@ -1343,8 +1362,10 @@ extern "C" int at_step_noalloc(const at_grid *grid, int64_t P, int scheme_order,
     h.stream = static_cast<cudaStream_t>(grid->stream);
     h.device = dev; h.sm_count = sms; h.smem_optin = smem_optin;
     h.batch = false; h.n_inst = 0; h.lmin = L;
+    if (grid->flags & AT_FLAG_COMPENSATED) return fail(AT_ERR_ARG, "at_step_noalloc has no compensated state");
+    h.comp = false;
     h.v64 = viscous_fp64(w, scheme_order, (uint32_t)grid->flags, nu * dt / (dx * dx));
-    pick_kernels(w, scheme_order, h.M, grid->forcing_amp != 0.0, h.v64, &h.kernel, &h.init_kernel);
+    pick_kernels(w, scheme_order, h.M, grid->forcing_amp != 0.0, h.v64, false, &h.kernel, &h.init_kernel);
     int stages = grid->stages > 0 ? grid->stages : 3;
     if (stages < atk::kMinStages) stages = atk::kMinStages;
     rc = launch_shape(h.M, w, P, tab_size(h.M, w, grid->forcing_amp != 0.0, false), grid->max_ctas, stages, sms,

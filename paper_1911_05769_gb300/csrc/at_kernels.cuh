@@ -77,14 +77,14 @@ struct SmemLayout {
 
 __host__ __device__ inline long long round_up(long long x, long long a) { return (x + a - 1) / a * a; }
 
-__host__ __device__ inline SmemLayout smem_layout(long long M, int word, int stages, long long tab_bytes)
+__host__ __device__ inline SmemLayout smem_layout(long long M, int word, int stages, long long tab_bytes, bool comp = false)
 {
     SmemLayout l;
     l.bar_off = 0;
     l.hist_off = round_up(8LL * kWarps * stages, 16);
     l.raw_off = round_up(l.hist_off + 4LL * kWarps * 2 * (kMaxL + 1), 128);
     l.stage_off = round_up(l.raw_off + 2LL * kWarps * kRawBytes, 128);
-    l.stage_bytes = round_up(M * word, 128);
+    l.stage_bytes = round_up(M * word, 128) * (comp ? 2 : 1);     // tile (+ its error words)
     l.tab_off = l.stage_off + (long long)kWarps * stages * l.stage_bytes;
     l.total = l.tab_off + tab_bytes;
     return l;
@@ -122,6 +122,7 @@ struct Params {
     int8_t *delays;            // [n_steps][P][2] replay input / record output
     const BatchSub *bsub;      // ensembles: [P] subdomain records (else NULL)
     const BatchInst *binst;    // ensembles: instance records (else NULL)
+    void *ur;                  // compensated state: the rounding error of every point (N words)
     void *levels;              // optional copy of every level l computed: slot l mod levels_depth of N words
     long long levels_depth;    // (single-level passes only; the adjoint's recomputation)
     long long N, P, M;
@@ -389,10 +390,14 @@ static __device__ __noinline__ T exact_ghost(const BatchInst *binst, const Batch
 // a face whose neighbour is another PE's, or not the next subdomain in the
 // sweep (a periodic instance's wrap-around), goes through the flags.
 //
-// V64 (FP32 state only): the viscous term nu dt D2(u) is formed from the
+// PREC (FP32 state only) 1: the viscous term nu dt D2(u) is formed from the
 // stencil values in FP64 and added to u in FP64, rounded to FP32 once per
-// update (for runs close to the diffusive stability limit).
-template <typename T, int ORDER, int GW, bool FORCED, bool FULL, bool BATCH, bool V64>
+// update (for runs close to the diffusive stability limit).  2: compensated
+// state: every point also keeps the rounding error of its stored value (a
+// second FP32 word, array p.ur); each update adds the increment and that
+// word with an error-free two-sum (Knuth), keeping the new error for the next
+// step, so that small increments are not lost to rounding.
+template <typename T, int ORDER, int GW, bool FORCED, bool FULL, bool BATCH, int PREC>
 __device__ void run_pe(const Params &p, const Sweep &sw, long long lo, long long hi, uint64_t *bars, unsigned *hist,
                        unsigned char *raw, unsigned char *stages, const T *sj, const T *cj, const T *spt,
                        const T *cpt, const BatchSub *btab, int *s_count, volatile long long *s_epoch)
@@ -430,13 +435,19 @@ __device__ void run_pe(const Params &p, const Sweep &sw, long long lo, long long
     Cursor C = L;                                     // tile being processed
 
     // --- state tile copies (lane 0): tile t goes to stage t % NS ------------
+    // (compensated state: the stage holds the tile, then its error words)
+    const size_t err_off = round_up((long long)tile_bytes, 128);
     auto issue_load = [&](long long t, const Cursor &c) {
         if (lane == 0) {
             uint64_t *bar = &bars[t % NS];
-            mbar_arrive_expect_tx(bar, (unsigned)tile_bytes);
+            mbar_arrive_expect_tx(bar, (unsigned)(PREC == 2 ? 2 * tile_bytes : tile_bytes));
             bulk_load(stages + (size_t)(t % NS) * p.stage_bytes,
                       reinterpret_cast<const unsigned char *>(p.u) + (size_t)c.j * tile_bytes,
                       (unsigned)tile_bytes, bar);
+            if constexpr (PREC == 2)
+                bulk_load(stages + (size_t)(t % NS) * p.stage_bytes + err_off,
+                          reinterpret_cast<const unsigned char *>(p.ur) + (size_t)c.j * tile_bytes,
+                          (unsigned)tile_bytes, bar);
         }
     };
 
@@ -617,11 +628,17 @@ __device__ void run_pe(const Params &p, const Sweep &sw, long long lo, long long
         }
 
         T c[GW][4];
+        T er[PREC == 2 ? GW : 1][4];           // compensated state: carried rounding errors
 #pragma unroll
         for (int m = 0; m < GW; ++m) {
             const int g = lane + 32 * m;
             if (FULL || g < NG) lds<T, 4>(stile + 4 * g, c[m]);
             else { c[m][0] = c[m][1] = c[m][2] = c[m][3] = (T)0; }
+            if constexpr (PREC == 2) {
+                const T *se = reinterpret_cast<const T *>(reinterpret_cast<const unsigned char *>(stile) + err_off);
+                if (FULL || g < NG) lds<T, 4>(se + 4 * g, er[m]);
+                else { er[m][0] = er[m][1] = er[m][2] = er[m][3] = (T)0; }
+            }
         }
         // A sin(x) dt = (dt A sin x_j) cos(i dx) + (dt A cos x_j) sin(i dx)
         T fs = (T)0, fc = (T)0;
@@ -699,7 +716,7 @@ __device__ void run_pe(const Params &p, const Sweep &sw, long long lo, long long
                         a = (T)8 * (v[e + 3] - v[e + 1]) - (v[e + 4] - v[e]);
                         b = (T)16 * (v[e + 3] + v[e + 1]) - (v[e + 4] + v[e]) - (T)30 * cc;
                     }
-                    if constexpr (V64) {
+                    if constexpr (PREC == 1) {
                         double b64;
                         if constexpr (ORDER == 2) {
                             b64 = ((double)v[e + 2] + (double)v[e]) - 2.0 * (double)cc;
@@ -711,6 +728,15 @@ __device__ void run_pe(const Params &p, const Sweep &sw, long long lo, long long
                         if constexpr (FORCED) rest = fs * c4[e] + (fc * s4[e] + rest);
                         c[m][e] = (T)((double)cc + (cB64 * b64 + (double)rest));
                         (void)b;
+                    } else if constexpr (PREC == 2) {
+                        T du = cB * b - cA * cc * a;
+                        if constexpr (FORCED) du = fs * c4[e] + (fc * s4[e] + du);
+                        // two-sum of cc and (du + carried error): exact sum s + err
+                        const T y = du + er[m][e];
+                        const T t = cc + y;
+                        const T yy = t - cc;
+                        er[m][e] = (cc - (t - yy)) + (y - yy);
+                        c[m][e] = t;
                     } else {
                         T du = cB * b - cA * cc * a;
                         if constexpr (FORCED) du = fs * c4[e] + (fc * s4[e] + du);   // two fused multiply-adds
@@ -745,6 +771,9 @@ __device__ void run_pe(const Params &p, const Sweep &sw, long long lo, long long
         for (int m = 0; m < GW; ++m) {
             const int g = lane + 32 * m;
             if (FULL || g < NG) stg4<T>(ug + 4 * g, c[m]);
+            if constexpr (PREC == 2) {
+                if (FULL || g < NG) stg4<T>(reinterpret_cast<T *>(p.ur) + (size_t)j * p.M + 4 * g, er[m]);
+            }
         }
         if (p.levels) {
             T *lg = reinterpret_cast<T *>(p.levels) + (size_t)((n + len) % p.levels_depth) * (size_t)p.N +
@@ -783,7 +812,7 @@ __device__ void run_pe(const Params &p, const Sweep &sw, long long lo, long long
 // ---------------------------------------------------------------------------
 // the persistent kernel
 // ---------------------------------------------------------------------------
-template <typename T, int ORDER, int GW, bool FORCED, bool FULL, bool BATCH, bool V64>
+template <typename T, int ORDER, int GW, bool FORCED, bool FULL, bool BATCH, int PREC>
 __global__ void __launch_bounds__(kThreads, AT_MIN_CTAS_PER_SM) at_stepper(const Params p)
 {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -841,7 +870,7 @@ __global__ void __launch_bounds__(kThreads, AT_MIN_CTAS_PER_SM) at_stepper(const
         if (sw.sb > lmin + 1) sw.sb = lmin + 1;
     }
     __syncthreads();
-    run_pe<T, ORDER, GW, FORCED, FULL, BATCH, V64>(p, sw, lo, hi, bars, hist, raw, stages, sj, cj, spt, cpt, btab,
+    run_pe<T, ORDER, GW, FORCED, FULL, BATCH, PREC>(p, sw, lo, hi, bars, hist, raw, stages, sj, cj, spt, cpt, btab,
                                                    &s_count, &s_epoch);
     // the last CTA to finish advances the level of the state and rearms the
     // grid barrier for the next launch (every CTA has read the level by now)
@@ -922,35 +951,35 @@ __global__ void at_restore(const Params p, const T *levels, long long depth, lon
 // ---------------------------------------------------------------------------
 namespace atk {
 
-template <typename T, int ORDER, bool FORCED, bool FULL, bool BATCH, bool V64>
+template <typename T, int ORDER, bool FORCED, bool FULL, bool BATCH, int PREC>
 void *stepper_gw(int gw)
 {
     switch (gw) {
-    case 1: return (void *)at_stepper<T, ORDER, 1, FORCED, FULL, BATCH, V64>;
-    case 2: return (void *)at_stepper<T, ORDER, 2, FORCED, FULL, BATCH, V64>;
-    case 4: return (void *)at_stepper<T, ORDER, 4, FORCED, FULL, BATCH, V64>;
-    default: return (void *)at_stepper<T, ORDER, 8, FORCED, FULL, BATCH, V64>;
+    case 1: return (void *)at_stepper<T, ORDER, 1, FORCED, FULL, BATCH, PREC>;
+    case 2: return (void *)at_stepper<T, ORDER, 2, FORCED, FULL, BATCH, PREC>;
+    case 4: return (void *)at_stepper<T, ORDER, 4, FORCED, FULL, BATCH, PREC>;
+    default: return (void *)at_stepper<T, ORDER, 8, FORCED, FULL, BATCH, PREC>;
     }
 }
 
-template <typename T, int ORDER, bool FORCED, bool BATCH, bool V64>
+template <typename T, int ORDER, bool FORCED, bool BATCH, int PREC>
 void *stepper_full(int gw, bool full)
 {
-    return full ? stepper_gw<T, ORDER, FORCED, true, BATCH, V64>(gw) : stepper_gw<T, ORDER, FORCED, false, BATCH, V64>(gw);
+    return full ? stepper_gw<T, ORDER, FORCED, true, BATCH, PREC>(gw) : stepper_gw<T, ORDER, FORCED, false, BATCH, PREC>(gw);
 }
 
 // Stepper for stencil order 2|4, gw groups of 4 points per lane (1, 2, 4 or
 // 8), with or without forcing (single domain only), full tiles (M = 128 gw)
-// or not; V64: FP64 viscous accumulation.
-template <typename T, bool BATCH, bool V64 = false>
+// or not; PREC 1: FP64 viscous accumulation, 2: compensated state.
+template <typename T, bool BATCH, int PREC = 0>
 void *stepper_kernel(int order, int gw, bool forced, bool full)
 {
     if constexpr (BATCH) {
-        return order == 2 ? stepper_full<T, 2, false, true, V64>(gw, full) : stepper_full<T, 4, false, true, V64>(gw, full);
+        return order == 2 ? stepper_full<T, 2, false, true, PREC>(gw, full) : stepper_full<T, 4, false, true, PREC>(gw, full);
     } else {
         if (order == 2)
-            return forced ? stepper_full<T, 2, true, false, V64>(gw, full) : stepper_full<T, 2, false, false, V64>(gw, full);
-        return forced ? stepper_full<T, 4, true, false, V64>(gw, full) : stepper_full<T, 4, false, false, V64>(gw, full);
+            return forced ? stepper_full<T, 2, true, false, PREC>(gw, full) : stepper_full<T, 2, false, false, PREC>(gw, full);
+        return forced ? stepper_full<T, 4, true, false, PREC>(gw, full) : stepper_full<T, 4, false, false, PREC>(gw, full);
     }
 }
 

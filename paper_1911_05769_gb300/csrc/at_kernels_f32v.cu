@@ -4,5 +4,5 @@
 
 __attribute__((visibility("hidden"))) void *atk_stepper_kernel_f32v(int order, int gw, bool forced, bool full)
 {
-    return atk::stepper_kernel<float, false, true>(order, gw, forced, full);
+    return atk::stepper_kernel<float, false, 1>(order, gw, forced, full);
 }

@@ -610,6 +610,7 @@ static atk::Params make_params(const at_solver *h)
     p.stage_bytes = h->sl.stage_bytes;
     p.tab_off = h->sl.tab_off;
     p.sb = 1;
+    p.alt = 0;
     p.timeout_ns = h->g.timeout_ns;
     p.skip_publish = (h->g.flags & AT_FLAG_TEST_SKIP_PUBLISH) ? 1 : 0;
     p.skip_step = h->g.test_skip_step;
@@ -686,6 +687,7 @@ static int step_impl(at_solver *h, int64_t n_steps, int delay_mode, int8_t *dela
     p.delays = delays;
     p.n_steps = n_steps;
     p.sb = (delay_mode == AT_FREE && !levels) ? h->sb : 1;
+    p.alt = p.sb > 1 ? 1 : 0;
     p.levels = levels;
     p.levels_depth = depth;
     const cudaError_t e = launch_stepper(h, &p);

@@ -129,6 +129,7 @@ struct Params {
     int L, T, mode, per_sub;   // L: largest delay bound (ensembles: of any instance)
     long long n_steps;
     int sb;                    // most levels per pass (temporal blocking, free mode)
+    int alt;                   // sweep direction alternates from pass to pass (blocked free mode)
     unsigned long long seed;
     double cA, cB, dtA;        // dt/(2dx) | dt/(12dx);  nu dt/dx^2 | nu dt/(12dx^2);  dt A
     double x0, dx;
@@ -323,16 +324,26 @@ static __device__ __noinline__ bool cta_grid_sync(const Params &p, int *s_count,
 // shorter).  sb may differ between PEs (in an ensemble each PE takes the
 // smallest delay bound of its subdomains): a PE's halo waits only need its
 // neighbours' per-level flags, whatever their pass boundaries.
+//
+// alt: the sweep direction alternates from pass to pass (lo..hi-1, then
+// hi-1..lo, ...).  A pass of L+1 levels must start from its edge neighbours'
+// level n exactly (delay 0); in a one-way sweep the first tile of a pass
+// needs the left neighbour PE's last tile of the previous pass, so every PE
+// waits on its neighbour at each pass start.  Alternating, each edge tile
+// needs a tile its neighbour finished about a pass earlier; and the tile at
+// the turn is the same subdomain twice in a row, continued in registers.
 struct Sweep {
     long long n0, n_steps;
     int sb;
+    bool alt;
 };
 
-// Position of a tile in a PE's sweep: pass start level n, subdomain j and
-// the pass length.
+// Position of a tile in a PE's sweep: pass start level n, subdomain j, the
+// pass length and (alternating sweeps) the direction of the pass.
 struct Cursor {
     long long n, j;
     int len;
+    bool rev;
 };
 
 __device__ __forceinline__ int pass_len(const Sweep &sw, long long n, int s_lev)
@@ -354,10 +365,19 @@ __device__ __forceinline__ long long count_passes(const Sweep &sw, int s_lev)
 
 __device__ __forceinline__ void advance(const Sweep &sw, Cursor &c, long long lo, long long hi, int s_lev)
 {
-    if (++c.j == hi) {
-        c.j = lo;
+    if (!sw.alt) {
+        if (++c.j == hi) {
+            c.j = lo;
+            c.n += c.len;
+            c.len = pass_len(sw, c.n, s_lev);
+        }
+    } else if (c.rev ? c.j == lo : c.j == hi - 1) {
+        // turn: the next pass starts on the same subdomain
+        c.rev = !c.rev;
         c.n += c.len;
         c.len = pass_len(sw, c.n, s_lev);
+    } else {
+        c.j += c.rev ? -1 : 1;
     }
 }
 
@@ -416,7 +436,10 @@ __device__ void run_pe(const Params &p, const Sweep &sw, long long lo, long long
         return;
     }
     const int NS = p.stages;
-    const int D = (int)((S - 1) < (NS - 1) ? (S - 1) : (NS - 1));   // tiles loaded ahead
+    // tiles loaded ahead; an alternating sweep revisits the subdomain of
+    // position i after a turn 2i+1 tiles later, so at most 2 ahead there
+    int D = (int)((S - 1) < (NS - 1) ? (S - 1) : (NS - 1));
+    if (sw.alt && D > 2) D = 2;
     const long long Q = count_passes(sw, S_LEV) * S;
     const int NG = (int)(p.M / 4);
     // owner of group NG-1 (compile-time when the tile is a multiple of 128 points)
@@ -430,22 +453,24 @@ __device__ void run_pe(const Params &p, const Sweep &sw, long long lo, long long
     const bool edge_pub = !(p.skip_publish && blockIdx.x == 0 && threadIdx.x < 32);
     unsigned *my_hist = hist + (lane & 1) * (kMaxL + 1);
 
-    Cursor L{sw.n0, lo, pass_len(sw, sw.n0, S_LEV)};   // next tile to load
+    Cursor L{sw.n0, lo, pass_len(sw, sw.n0, S_LEV), false};   // next tile to load
     Cursor H = L;                                     // next tile whose halo is prepared
     Cursor C = L;                                     // tile being processed
 
     // --- state tile copies (lane 0): tile t goes to stage t % NS ------------
     // (compensated state: the stage holds the tile, then its error words)
     const size_t err_off = round_up((long long)tile_bytes, 128);
-    auto issue_load = [&](long long t, const Cursor &c) {
+    // (stage indices and phases are kept as running counters: no 64-bit
+    // division per tile)
+    auto issue_load = [&](int st, const Cursor &c) {
         if (lane == 0) {
-            uint64_t *bar = &bars[t % NS];
+            uint64_t *bar = &bars[st];
             mbar_arrive_expect_tx(bar, (unsigned)(PREC == 2 ? 2 * tile_bytes : tile_bytes));
-            bulk_load(stages + (size_t)(t % NS) * p.stage_bytes,
+            bulk_load(stages + (size_t)st * p.stage_bytes,
                       reinterpret_cast<const unsigned char *>(p.u) + (size_t)c.j * tile_bytes,
                       (unsigned)tile_bytes, bar);
             if constexpr (PREC == 2)
-                bulk_load(stages + (size_t)(t % NS) * p.stage_bytes + err_off,
+                bulk_load(stages + (size_t)st * p.stage_bytes + err_off,
                           reinterpret_cast<const unsigned char *>(p.ur) + (size_t)c.j * tile_bytes,
                           (unsigned)tile_bytes, bar);
         }
@@ -558,18 +583,31 @@ __device__ void run_pe(const Params &p, const Sweep &sw, long long lo, long long
 
     // --- prologue -------------------------------------------------------------
     long long tl = 0;                  // next tile index to load
-    for (; tl < D && tl < Q; ++tl) { issue_load(tl, L); advance(sw, L, lo, hi, S_LEV); }
+    long long nl = 0;                  // loads issued
+    int sl = 0;                        // stage of the next load (nl % NS)
+    int sr = 0;                        // stage of the next loaded tile to use and the parity of its fill
+    unsigned ph = 0;
+    // after a load: move to the next tile that is loaded (a turn tile of an
+    // alternating sweep is not: it continues in registers)
+    auto next_load = [&]() {
+        const long long jj = L.j;
+        advance(sw, L, lo, hi, S_LEV);
+        ++tl;
+        while (sw.alt && L.j == jj && tl < Q) { advance(sw, L, lo, hi, S_LEV); ++tl; }
+        sl = (sl + 1 == NS) ? 0 : sl + 1;
+        ++nl;
+    };
+    while (tl < D && tl < Q) { issue_load(sl, L); next_load(); }
     bool ok = true;
     bool pending = true;               // the halo of tile 0 is prepared in the loop
     int k0cur = 0, k1cur = 0;
+    bool turn = false;                 // tile r continues tile r-1 in registers (alternating sweep)
+    T c[GW][4];                        // the tile's words, group g = lane + 32 m
+    T er[PREC == 2 ? GW : 1][4];       // compensated state: carried rounding errors
 
     for (long long r = 0; r < Q && ok; ++r) {
         // state copy of tile r + D (stage of tile r - 1, complete: in order)
-        if (tl < Q && tl <= r + D) {
-            issue_load(tl, L);
-            advance(sw, L, lo, hi, S_LEV);
-            ++tl;
-        }
+        if (tl < Q && tl <= r + D) { issue_load(sl, L); next_load(); }
         const long long step = C.n - sw.n0;
         // synchronous algorithm: before the first tile of a step, all PEs
         // have finished the previous step (grid barrier, Algorithm 1)
@@ -592,7 +630,7 @@ __device__ void run_pe(const Params &p, const Sweep &sw, long long lo, long long
         // internal right neighbour at the pass start was computed by tile
         // r + 2 - S, which is tile r itself when S == 2: no prefetch then.
         pending = true;
-        if (r + 1 < Q && S != 2) {
+        if (r + 1 < Q && (S != 2 || sw.alt)) {
             const bool new_step = (H.j == lo);
             if (!(p.mode == kModeSync && new_step)) {
                 const int st = prep_halo(r + 1, H, buf ^ 1, false);
@@ -603,14 +641,16 @@ __device__ void run_pe(const Params &p, const Sweep &sw, long long lo, long long
                 }
             }
         }
-        // the state tile
-        int good = 1;
-        if (lane == 0) good = wait_stage(p, &bars[r % NS], (unsigned)((r / NS) & 1));
-        good = __shfl_sync(kAll, good, 0);
-        __syncwarp();
-        if (!good) { ok = false; break; }
-
-        const T *stile = reinterpret_cast<const T *>(stages + (size_t)(r % NS) * p.stage_bytes);
+        // the state tile (a turn tile is already in registers)
+        const T *stile = reinterpret_cast<const T *>(stages + (size_t)sr * p.stage_bytes);
+        if (!turn) {
+            int good = 1;
+            if (lane == 0 && !mbar_try_wait(&bars[sr], ph)) good = wait_stage(p, &bars[sr], ph);
+            good = __shfl_sync(kAll, good, 0);
+            __syncwarp();
+            if (!good) { ok = false; break; }
+            if (++sr == NS) { sr = 0; ph ^= 1u; }
+        }
         const unsigned char *rw = raw + (size_t)buf * kRawBytes;
         const long long j = C.j, n = C.n;
         const int len = C.len;
@@ -627,17 +667,18 @@ __device__ void run_pe(const Params &p, const Sweep &sw, long long lo, long long
             bnd1 = b.right < 0;
         }
 
-        T c[GW][4];
-        T er[PREC == 2 ? GW : 1][4];           // compensated state: carried rounding errors
+        if (!turn) {
 #pragma unroll
-        for (int m = 0; m < GW; ++m) {
-            const int g = lane + 32 * m;
-            if (FULL || g < NG) lds<T, 4>(stile + 4 * g, c[m]);
-            else { c[m][0] = c[m][1] = c[m][2] = c[m][3] = (T)0; }
-            if constexpr (PREC == 2) {
-                const T *se = reinterpret_cast<const T *>(reinterpret_cast<const unsigned char *>(stile) + err_off);
-                if (FULL || g < NG) lds<T, 4>(se + 4 * g, er[m]);
-                else { er[m][0] = er[m][1] = er[m][2] = er[m][3] = (T)0; }
+            for (int m = 0; m < GW; ++m) {
+                const int g = lane + 32 * m;
+                if (FULL || g < NG) lds<T, 4>(stile + 4 * g, c[m]);
+                else { c[m][0] = c[m][1] = c[m][2] = c[m][3] = (T)0; }
+                if constexpr (PREC == 2) {
+                    const T *se =
+                        reinterpret_cast<const T *>(reinterpret_cast<const unsigned char *>(stile) + err_off);
+                    if (FULL || g < NG) lds<T, 4>(se + 4 * g, er[m]);
+                    else { er[m][0] = er[m][1] = er[m][2] = er[m][3] = (T)0; }
+                }
             }
         }
         // A sin(x) dt = (dt A sin x_j) cos(i dx) + (dt A cos x_j) sin(i dx)
@@ -659,7 +700,10 @@ __device__ void run_pe(const Params &p, const Sweep &sw, long long lo, long long
             else
                 hv = approx_halo<T, S_LEV>(rw + f * kMaxS * kRingEntry, (f ? k1cur : k0cur) + rem / R, rem % R);
         }
-        for (int i = 0; i < len; ++i) {
+        // one level of the tile: old values in cs, new ones into cd (the
+        // level loop alternates two register arrays, so no moves are needed
+        // between levels)
+        auto level = [&](int i, T (&cs)[GW][4], T (&cd)[GW][4]) {
             const long long lev = n + i + 1;                 // level being computed
             T hl[R], hr[R];
 #pragma unroll
@@ -674,6 +718,48 @@ __device__ void run_pe(const Params &p, const Sweep &sw, long long lo, long long
                                             : approx_halo<T, S_LEV>(rw + kMaxS * kRingEntry, k1cur + i, q);
                 }
             }
+            // One point: w[0 .. 2R] are the values at offsets -R .. R (w[R] the
+            // point itself), sv/cv the forcing table entries; returns the new
+            // value (compensated state: updates the carried error too).
+            auto point = [&](const T *w, T sv, T cv, T &err) -> T {
+                const T cc = w[R];
+                T a, b;
+                if constexpr (ORDER == 2) {
+                    a = w[2] - w[0];
+                    b = (w[2] + w[0]) - (T)2 * cc;
+                } else {
+                    a = (T)8 * (w[3] - w[1]) - (w[4] - w[0]);
+                    b = (T)16 * (w[3] + w[1]) - (w[4] + w[0]) - (T)30 * cc;
+                }
+                if constexpr (PREC == 1) {
+                    double b64;
+                    if constexpr (ORDER == 2) {
+                        b64 = ((double)w[2] + (double)w[0]) - 2.0 * (double)cc;
+                    } else {
+                        b64 = 16.0 * ((double)w[3] + (double)w[1]) - ((double)w[4] + (double)w[0]) - 30.0 * (double)cc;
+                    }
+                    T rest = -cA * cc * a;
+                    if constexpr (FORCED) rest = fs * cv + (fc * sv + rest);
+                    (void)b;
+                    return (T)((double)cc + (cB64 * b64 + (double)rest));
+                } else if constexpr (PREC == 2) {
+                    T du = cB * b - cA * cc * a;
+                    if constexpr (FORCED) du = fs * cv + (fc * sv + du);
+                    // two-sum of cc and (du + carried error): exact sum s + err
+                    const T y = du + err;
+                    const T t = cc + y;
+                    const T yy = t - cc;
+                    err = (cc - (t - yy)) + (y - yy);
+                    return t;
+                } else {
+                    T du = cB * b - cA * cc * a;
+                    if constexpr (FORCED) du = fs * cv + (fc * sv + du);   // two fused multiply-adds
+                    return cc + du;
+                }
+            };
+            // lane l holds groups g = l + 32 m of 4 points; neighbour words come
+            // from the adjacent lanes (lane 0 / 31: the other end of the warp at
+            // the previous / next m, or the halo)
             T tail[R], rb[R];                                // old last words of group m-1; new last words of NG-1
 #pragma unroll
             for (int q = 0; q < R; ++q) { tail[q] = (T)0; rb[q] = (T)0; }
@@ -683,15 +769,15 @@ __device__ void run_pe(const Params &p, const Sweep &sw, long long lo, long long
                 T v[4 + 2 * R];
 #pragma unroll
                 for (int q = 0; q < R; ++q) {
-                    const T to_next = (lane == 31) ? tail[q] : c[m][4 - R + q];
+                    const T to_next = (lane == 31) ? tail[q] : cs[m][4 - R + q];
                     v[q] = __shfl_sync(kAll, to_next, up);
-                    const T to_prev = (lane == 0) ? c[m + 1 < GW ? m + 1 : m][q] : c[m][q];
+                    const T to_prev = (lane == 0) ? cs[m + 1 < GW ? m + 1 : m][q] : cs[m][q];
                     v[R + 4 + q] = __shfl_sync(kAll, to_prev, down);
                 }
 #pragma unroll
-                for (int q = 0; q < R; ++q) tail[q] = c[m][4 - R + q];
+                for (int q = 0; q < R; ++q) tail[q] = cs[m][4 - R + q];
 #pragma unroll
-                for (int e = 0; e < 4; ++e) v[R + e] = c[m][e];
+                for (int e = 0; e < 4; ++e) v[R + e] = cs[m][e];
                 if (m == 0) {
 #pragma unroll
                     for (int q = 0; q < R; ++q) v[q] = (lane == 0) ? hl[q] : v[q];
@@ -701,50 +787,15 @@ __device__ void run_pe(const Params &p, const Sweep &sw, long long lo, long long
                 for (int q = 0; q < R; ++q) v[R + 4 + q] = is_last ? hr[q] : v[R + 4 + q];
                 T s4[4], c4[4];
                 if constexpr (FORCED) {
-                    const int gg = (FULL || g < NG) ? g : NG - 1;
+                    const int gg = g < NG ? g : NG - 1;
                     lds<T, 4>(sj + 4 * gg, s4);
                     lds<T, 4>(cj + 4 * gg, c4);
                 }
 #pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    const T cc = v[e + R];
-                    T a, b;
-                    if constexpr (ORDER == 2) {
-                        a = v[e + 2] - v[e];
-                        b = (v[e + 2] + v[e]) - (T)2 * cc;
-                    } else {
-                        a = (T)8 * (v[e + 3] - v[e + 1]) - (v[e + 4] - v[e]);
-                        b = (T)16 * (v[e + 3] + v[e + 1]) - (v[e + 4] + v[e]) - (T)30 * cc;
-                    }
-                    if constexpr (PREC == 1) {
-                        double b64;
-                        if constexpr (ORDER == 2) {
-                            b64 = ((double)v[e + 2] + (double)v[e]) - 2.0 * (double)cc;
-                        } else {
-                            b64 = 16.0 * ((double)v[e + 3] + (double)v[e + 1]) - ((double)v[e + 4] + (double)v[e]) -
-                                  30.0 * (double)cc;
-                        }
-                        T rest = -cA * cc * a;
-                        if constexpr (FORCED) rest = fs * c4[e] + (fc * s4[e] + rest);
-                        c[m][e] = (T)((double)cc + (cB64 * b64 + (double)rest));
-                        (void)b;
-                    } else if constexpr (PREC == 2) {
-                        T du = cB * b - cA * cc * a;
-                        if constexpr (FORCED) du = fs * c4[e] + (fc * s4[e] + du);
-                        // two-sum of cc and (du + carried error): exact sum s + err
-                        const T y = du + er[m][e];
-                        const T t = cc + y;
-                        const T yy = t - cc;
-                        er[m][e] = (cc - (t - yy)) + (y - yy);
-                        c[m][e] = t;
-                    } else {
-                        T du = cB * b - cA * cc * a;
-                        if constexpr (FORCED) du = fs * c4[e] + (fc * s4[e] + du);   // two fused multiply-adds
-                        c[m][e] = cc + du;
-                    }
-                }
+                for (int e = 0; e < 4; ++e)
+                    cd[m][e] = point(v + e, s4[e], c4[e], er[PREC == 2 ? m : 0][PREC == 2 ? e : 0]);
 #pragma unroll
-                for (int q = 0; q < R; ++q) rb[q] = (m == m_last) ? c[m][4 - R + q] : rb[q];
+                for (int q = 0; q < R; ++q) rb[q] = (m == m_last) ? cd[m][4 - R + q] : rb[q];
             }
             // publish the new boundary values and release the edge flags
             // (face 0 by lane 0, face 1 by the owner of group NG-1)
@@ -754,7 +805,10 @@ __device__ void run_pe(const Params &p, const Sweep &sw, long long lo, long long
                 unsigned char *e0 = p.ring + (size_t)slot * slot_stride + (size_t)j * 2 * kRingEntry;
                 const int f_lo = (lane == 0) ? 0 : 1, f_hi = (lane == lane_last) ? 1 : 0;
                 for (int f = f_lo; f <= f_hi; ++f) {
-                    st_entry<T, R>(e0 + f * kRingEntry, f ? rb : c[0]);
+                    T w[R];                // word by word: no runtime choice between arrays
+#pragma unroll
+                    for (int q = 0; q < R; ++q) w[q] = f ? rb[q] : cd[0][q];
+                    st_entry<T, R>(e0 + f * kRingEntry, w);
                     if (p.mode == kModeSync) __threadfence();
                     bool rel;              // the consumer across face f waits on this flag
                     if constexpr (BATCH) {
@@ -766,13 +820,31 @@ __device__ void run_pe(const Params &p, const Sweep &sw, long long lo, long long
                     if (rel && pub_ok) st_release(p.flag + j * 2 + f, (unsigned long long)lev);
                 }
             }
-        }
+        };
+        T c2[GW][4];
+        for (int i = 0; i < len; i += 2) {
+            level(i, c, c2);
+            if (i + 1 == len) {
 #pragma unroll
-        for (int m = 0; m < GW; ++m) {
-            const int g = lane + 32 * m;
-            if (FULL || g < NG) stg4<T>(ug + 4 * g, c[m]);
-            if constexpr (PREC == 2) {
-                if (FULL || g < NG) stg4<T>(reinterpret_cast<T *>(p.ur) + (size_t)j * p.M + 4 * g, er[m]);
+                for (int m = 0; m < GW; ++m)
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) c[m][e] = c2[m][e];
+                break;
+            }
+            level(i + 1, c2, c);
+        }
+        // the next tile; before a turn the words stay in registers
+        Cursor Cn = C;
+        advance(sw, Cn, lo, hi, S_LEV);
+        const bool keep = sw.alt && Cn.j == j && r + 1 < Q;
+        if (!keep) {
+#pragma unroll
+            for (int m = 0; m < GW; ++m) {
+                const int g = lane + 32 * m;
+                if (FULL || g < NG) stg4<T>(ug + 4 * g, c[m]);
+                if constexpr (PREC == 2) {
+                    if (FULL || g < NG) stg4<T>(reinterpret_cast<T *>(p.ur) + (size_t)j * p.M + 4 * g, er[m]);
+                }
             }
         }
         if (p.levels) {
@@ -788,14 +860,15 @@ __device__ void run_pe(const Params &p, const Sweep &sw, long long lo, long long
         // lane 0 after the warp barrier
         fence_proxy_async_global();
         __syncwarp();
-        advance(sw, C, lo, hi, S_LEV);
+        C = Cn;
+        turn = keep;
     }
     // synchronous algorithm: the last step's arrival at the grid barrier
     if (ok && p.mode == kModeSync) cta_grid_sync(p, s_count, s_epoch, p.n_steps, false);
     // let every copy in flight land before the warp leaves
     if (lane < 2) cp_async_wait_all();
     if (lane == 0) {
-        for (long long t = (tl > NS ? tl - NS : 0); t < tl; ++t) {
+        for (long long t = (nl > NS ? nl - NS : 0); t < nl; ++t) {
             const unsigned long long t0 = global_ns();
             while (!mbar_try_wait(&bars[t % NS], (unsigned)((t / NS) & 1)) &&
                    (long long)(global_ns() - t0) < p.timeout_ns) {
@@ -830,7 +903,7 @@ __global__ void __launch_bounds__(kThreads, AT_MIN_CTAS_PER_SM) at_stepper(const
     T *spt = tab + 2 * p.M + (size_t)w * 2 * p.smax, *cpt = spt + p.smax;
     BatchSub *btab = reinterpret_cast<BatchSub *>(smem + p.tab_off) + (size_t)w * p.smax;
     // time level of the state, advanced at the end of the previous launch
-    Sweep sw{*reinterpret_cast<const volatile long long *>(p.ctrl + kCtrlN0), p.n_steps, p.sb};
+    Sweep sw{*reinterpret_cast<const volatile long long *>(p.ctrl + kCtrlN0), p.n_steps, p.sb, p.alt != 0};
 
     __shared__ int s_count;                   // grid-barrier arrivals of this CTA's warps
     __shared__ long long s_epoch;             // last grid barrier this CTA passed

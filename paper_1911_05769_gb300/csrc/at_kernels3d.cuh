@@ -242,6 +242,7 @@ __global__ void __launch_bounds__(kThreads3, AT_MIN_CTAS_3D) at_stepper3d(const 
     // issue cursor: the next plane to copy (advanced plane by plane, no division)
     long long i_sub = lo, issued = 0;
     int i_z = 0, i_stage = 0, i_x0, i_y0, i_z0;
+    unsigned i_par = 1;                    // parity of the empty-barrier phase the next issue waits for
     tile_coords(lo, &i_x0, &i_y0, &i_z0);
     // warp 0 issues the bulk copies of the next plane into its stage, once
     // every warp is done with the plane that stage held (bounded wait)
@@ -249,7 +250,7 @@ __global__ void __launch_bounds__(kThreads3, AT_MIN_CTAS_3D) at_stepper3d(const 
         if (tid < 32) {
             if (issued >= NS) {
                 int good = 1;
-                if (lane == 0) good = wait_stage3(p, &empty[i_stage], (unsigned)(((issued - NS) / NS) & 1));
+                if (lane == 0 && !mbar_try_wait(&empty[i_stage], i_par)) good = wait_stage3(p, &empty[i_stage], i_par);
                 good = __shfl_sync(0xffffffffu, good, 0);
                 if (!good) atomicExch(s_flag, -1);
             }
@@ -261,7 +262,7 @@ __global__ void __launch_bounds__(kThreads3, AT_MIN_CTAS_3D) at_stepper3d(const 
             __syncwarp();
         }
         ++issued;
-        if (++i_stage == NS) i_stage = 0;
+        if (++i_stage == NS) { i_stage = 0; i_par ^= 1u; }
         if (++i_z == m2) {
             i_z = 0;
             if (++i_sub == hi) i_sub = lo;
@@ -289,9 +290,14 @@ __global__ void __launch_bounds__(kThreads3, AT_MIN_CTAS_3D) at_stepper3d(const 
 
     while (issued < NS && issued < Q) issue();
     // a failed wait is recorded in s_flag; every thread acts on it at the
-    // next CTA barrier (one per tile), so control flow stays uniform there
-    auto wait_plane = [&](long long g) -> bool {
-        if (!wait_stage3(p, &bars[g % NS], (unsigned)((g / NS) & 1))) { atomicExch(s_flag, -1); return false; }
+    // next CTA barrier (one per tile), so control flow stays uniform there.
+    // Planes are consumed in order: gs, gp are the stage and fill parity of
+    // the current plane g (running counters: no division per plane).
+    int gs = 0;
+    unsigned gp = 0;
+    auto wait_plane = [&](int st, unsigned par) -> bool {
+        if (mbar_try_wait(&bars[st], par)) return true;
+        if (!wait_stage3(p, &bars[st], par)) { atomicExch(s_flag, -1); return false; }
         return true;
     };
 
@@ -304,7 +310,6 @@ __global__ void __launch_bounds__(kThreads3, AT_MIN_CTAS_3D) at_stepper3d(const 
     T *rf[6];                                // ring entries of the new level of the current tile
     const long long n_tiles = p.n_steps * S;
     for (long long t = 0; t < n_tiles; ++t) {
-        long long g = t * m2;                // first plane of the tile
         // ---- tile start (one CTA barrier): release the previous tile's
         // flags, grid barrier (synchronous mode), delays, halos
         __syncthreads();
@@ -370,9 +375,9 @@ __global__ void __launch_bounds__(kThreads3, AT_MIN_CTAS_3D) at_stepper3d(const 
         }
         __syncthreads();
         // plane z = -1 (the -z halo) and plane 0
-        if (!wait_plane(g)) { ok = false; }
+        if (!wait_plane(gs, gp)) { ok = false; }
         {
-            const T *st0 = reinterpret_cast<const T *>(stages + (size_t)(g % NS) * sl.plane_bytes);
+            const T *st0 = reinterpret_cast<const T *>(stages + (size_t)gs * sl.plane_bytes);
 #pragma unroll
             for (int f = 0; f < NF; ++f) {
 #pragma unroll
@@ -385,10 +390,11 @@ __global__ void __launch_bounds__(kThreads3, AT_MIN_CTAS_3D) at_stepper3d(const 
         const long long lnew = lv + 1;
         // ---- the planes of the tile; warps run independently (stage
         // barriers only)
-        for (int z = 0; z < m2 && ok; ++z, ++g) {
+        for (int z = 0; z < m2 && ok; ++z) {
             const bool top = (z == m2 - 1);
-            if (!top && !wait_plane(g + 1)) { ok = false; break; }
-            const int sg = (int)(g % NS), sg1 = sg + 1 == NS ? 0 : sg + 1;
+            const int sg = gs, sg1 = gs + 1 == NS ? 0 : gs + 1;
+            const unsigned gp1 = sg1 == 0 ? gp ^ 1u : gp;
+            if (!top && !wait_plane(sg1, gp1)) { ok = false; break; }
             const T *st = reinterpret_cast<const T *>(stages + (size_t)sg * sl.plane_bytes);
             const T *stn = reinterpret_cast<const T *>(stages + (size_t)sg1 * sl.plane_bytes);
             T *up = u + base + (long long)z * plane_words;
@@ -442,6 +448,8 @@ __global__ void __launch_bounds__(kThreads3, AT_MIN_CTAS_3D) at_stepper3d(const 
             __syncwarp();
             if (lane == 0) mbar_arrive(&empty[sg]);
             if (issued < Q) issue();
+            gs = sg1;
+            gp = gp1;
         }
         prev_sub = sub;
         prev_new = lnew;

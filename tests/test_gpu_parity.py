@@ -230,6 +230,25 @@ def test_blocked_passes_of_L_plus_1_are_deterministic(require_gpu):
     assert np.array_equal(g["rec"], np.broadcast_to(want[:, None, None], g["rec"].shape))
 
 
+@pytest.mark.parametrize("stages", [2, 3, 4])
+@pytest.mark.parametrize("per_pe,calls", [(1, None), (2, [37, 83]), (5, None), (9, [1, 119])])
+def test_alternating_sweep_turns(require_gpu, stages, per_pe, calls):
+    """Blocked free-running passes sweep each element's subdomains forth and
+    back; the tile at a turn continues in registers and the tiles after it are
+    loaded no earlier than their last write-back.  Every tile-buffer count
+    and run length (1: every tile a turn; 2: every other tile) replays exactly
+    in the oracle, also across calls of odd lengths."""
+    from paper_1911_05769_gb300 import AT_FREE
+    P, M, L = 8 * per_pe, 256, 3
+    u0, dt = _setup(P * M, 0.02, kind="fourier")
+    kw = dict(P=P, order=4, L=L, nu=0.02, dt=dt, steps=120, forcing=0.1)
+    g = gpu_run(u0, mode=AT_FREE, max_ctas=2, stages=stages, record=True, calls=calls, steps_per_pass=L + 1, **kw)
+    ref, hist = oracle_run(u0, mode="replay", delays=g["rec"], **kw)
+    assert g["info"].ctas == 2
+    assert rel_linf(g["u"], ref) <= TOL["f64"]
+    assert np.array_equal(g["hist"], hist)
+
+
 @pytest.mark.parametrize("per_pe", [1, 2, 3])
 @pytest.mark.parametrize("mode_name", ["seeded", "free", "free_blocked", "sync"])
 def test_subdomains_per_processing_element(require_gpu, per_pe, mode_name):

@@ -214,7 +214,7 @@ const char *at_last_error(void);
  *     d_t q_f + u d_x q_f + v d_y q_f + w d_z q_f = kappa[f] lap q_f
  * with kappa[0..2] the viscosity nu and kappa[3..] the scalars'
  * diffusivities alpha_k (Eq. BS).  Same grid, subdomains (sub[0] * sub[1] <=
- * 512), order-2 stencils, AT halos and delays as the scalar 3D solver; one
+ * 512, or exactly 1024 with FP32 state and sub[0] a multiple of 4), order-2 stencils, AT halos and delays as the scalar 3D solver; one
  * delay per (level, subdomain, face) serves every field (one message per face
  * carries all fields).  The state and at_set_state / at_state buffers hold
  * nfields x n[0] n[1] n[2] words; at_info reports that as N. */

@@ -32,8 +32,8 @@ void *atk_batch_kernel_f64(int order, int gw, bool full);
 void *atk_restore_kernel_f32(int order);
 void *atk_restore_kernel_f64(int order);
 void *atk_adjoint_kernel(int w, int order);
-void *atk_stepper3d_kernel(int w, int tc);
-void *atk_system3d_kernel(int w, int tc, int nf);
+void *atk_stepper3d_kernel(int w, int tc, int vw);
+void *atk_system3d_kernel(int w, int tc, int nf, int vw);
 void *atk_init3d_kernel(int w);
 
 namespace {
@@ -401,10 +401,13 @@ static int create3d(const at_grid *grid, int64_t P, int L, int nf, const double 
     cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (!coop) return fail(AT_ERR_RESIDENCY, "device does not support cooperative launch");
 
+    // a thread takes one group of vw = 4 consecutive columns (FP32 planes of
+    // 1024 points: every thread busy) or 1, 2 or 4 single columns
     const int pw = d.m[0] * d.m[1];
-    const int tc = pw <= atk::kThreads3 ? 1 : pw <= 2 * atk::kThreads3 ? 2 : 4;
-    if (nf > 1 && tc > 2) return fail(AT_ERR_ARG, "the 3D system needs sub[0] * sub[1] <= 512");
-    void *kern = nf == 1 ? atk_stepper3d_kernel(w, tc) : atk_system3d_kernel(w, tc, nf);
+    const int vw = (w == 4 && d.m[0] % 4 == 0 && pw == 4 * atk::kThreads3) ? 4 : 1;
+    const int tc = vw == 4 ? 1 : pw <= atk::kThreads3 ? 1 : pw <= 2 * atk::kThreads3 ? 2 : 4;
+    if (nf > 1 && vw == 1 && tc > 2) return fail(AT_ERR_ARG, "the 3D system needs sub[0] * sub[1] <= 512 (or 1024, FP32)");
+    void *kern = nf == 1 ? atk_stepper3d_kernel(w, tc, vw) : atk_system3d_kernel(w, tc, nf, vw);
     // plane buffers: at least 3 (planes z and z+1 in use, one arriving), at most sub[2]
     int stages = grid->stages > 0 ? grid->stages : 4;
     if (stages < 3) stages = 3;

@@ -11,9 +11,10 @@
 // plane (an m0 x m1 box) is brought into one of `stages` shared-memory buffers
 // by one TMA tensor copy (3D tensor map over the state; completion counted on
 // the stage's mbarrier), several planes ahead; warps free a stage through a
-// second mbarrier.  A thread owns up to TC (x, y)
-// columns; it keeps the values of its columns at planes z-1, z, z+1 in
-// registers and reads x and y neighbours from the plane in shared memory.
+// second mbarrier.  A thread owns up to TC groups of VW consecutive (x, y)
+// columns; it keeps the values of its columns at planes z-1, z in registers,
+// reads the plane z+1 and the y neighbours as VW-word vectors and the two x
+// neighbours beyond its group as single words from shared memory.
 // Neighbours across a subdomain face come from the ring of face planes:
 // entry [slot][subdomain][face] holds the face's boundary values at level
 // slot (faces 0/1: the x = 0 / x = m0-1 planes indexed [z][y]; 2/3: y planes
@@ -179,7 +180,19 @@ __device__ __forceinline__ T *ring_entry(const Params3 &p, long long level, long
 // its own kappa); otherwise NF = 1 and the scalar equation
 // u_t + u (u_x + u_y + u_z) = nu lap u.  A plane of every field arrives with
 // one copy of a 4D tensor map (x, y, z, field).
-template <typename T, int TC, int NF, bool SYS>
+// VW consecutive words (VW = 1 or 4; 16-byte aligned for 4) to global memory
+template <typename T, int VW>
+__device__ __forceinline__ void stv(T *g, const T *v)
+{
+    if constexpr (VW == 4 && sizeof(T) == 4) {
+        *reinterpret_cast<float4 *>(g) = make_float4(v[0], v[1], v[2], v[3]);
+    } else {
+#pragma unroll
+        for (int i = 0; i < VW; ++i) g[i] = v[i];
+    }
+}
+
+template <typename T, int TC, int NF, bool SYS, int VW>
 __global__ void __launch_bounds__(kThreads3, AT_MIN_CTAS_3D) at_stepper3d(const Params3 p, const __grid_constant__ CUtensorMap tmap)
 {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -270,23 +283,27 @@ __global__ void __launch_bounds__(kThreads3, AT_MIN_CTAS_3D) at_stepper3d(const 
         }
     };
 
-    // columns of this thread: position, offset in a plane of u, faces touched
+    // column groups of this thread: first column, offset in a plane of u,
+    // faces touched (x: by the group's first / last column)
     int cx[TC], cy[TC], coff[TC], cface[TC];
     bool cv[TC];
+    const int GR = m0 / VW;                  // groups per row (the host checks VW | m0)
 #pragma unroll
     for (int q = 0; q < TC; ++q) {
         const int c = tid + kThreads3 * q;
-        cv[q] = c < PW;
-        cx[q] = cv[q] ? c % m0 : 0;
-        cy[q] = cv[q] ? c / m0 : 0;
+        cv[q] = c < PW / VW;
+        cx[q] = cv[q] ? (c % GR) * VW : 0;
+        cy[q] = cv[q] ? c / GR : 0;
         coff[q] = cy[q] * (int)p.n0 + cx[q];
-        cface[q] = (cx[q] == 0 ? 1 : 0) | (cx[q] == m0 - 1 ? 2 : 0) | (cy[q] == 0 ? 4 : 0) | (cy[q] == m1 - 1 ? 8 : 0);
+        cface[q] = (cx[q] == 0 ? 1 : 0) | (cx[q] + VW == m0 ? 2 : 0) | (cy[q] == 0 ? 4 : 0) | (cy[q] == m1 - 1 ? 8 : 0);
     }
-    T prev[NF][TC], cur[NF][TC];
+    T prev[NF][TC][VW], cur[NF][TC][VW];
 #pragma unroll
     for (int f = 0; f < NF; ++f)
 #pragma unroll
-        for (int q = 0; q < TC; ++q) prev[f][q] = cur[f][q] = (T)0;
+        for (int q = 0; q < TC; ++q)
+#pragma unroll
+            for (int e = 0; e < VW; ++e) prev[f][q][e] = cur[f][q][e] = (T)0;
 
     while (issued < NS && issued < Q) issue();
     // a failed wait is recorded in s_flag; every thread acts on it at the
@@ -382,8 +399,9 @@ __global__ void __launch_bounds__(kThreads3, AT_MIN_CTAS_3D) at_stepper3d(const 
             for (int f = 0; f < NF; ++f) {
 #pragma unroll
                 for (int q = 0; q < TC; ++q) {
-                    prev[f][q] = cv[q] ? hz0[f * hwz + cy[q] * m0 + cx[q]] : (T)0;
-                    cur[f][q] = cv[q] ? st0[f * PW + cy[q] * m0 + cx[q]] : (T)0;
+                    if (!cv[q]) continue;
+                    lds<T, VW>(hz0 + f * hwz + cy[q] * m0 + cx[q], prev[f][q]);
+                    lds<T, VW>(st0 + f * PW + cy[q] * m0 + cx[q], cur[f][q]);
                 }
             }
         }
@@ -404,39 +422,54 @@ __global__ void __launch_bounds__(kThreads3, AT_MIN_CTAS_3D) at_stepper3d(const 
                 if (!cv[q]) continue;
                 const int x = cx[q], y = cy[q], c = y * m0 + x;
                 const int fc = cface[q];
-                // advecting velocity at the point, level n (the system)
-                const T U = SYS ? cur[0][q] : (T)0, V = SYS ? cur[1 % NF][q] : (T)0, Wv = SYS ? cur[2 % NF][q] : (T)0;
+                // advecting velocity at the points, level n (the system)
+                T Uv[VW], Vv[VW], Wv[VW];
+#pragma unroll
+                for (int e = 0; e < VW; ++e) {
+                    Uv[e] = SYS ? cur[0][q][e] : (T)0;
+                    Vv[e] = SYS ? cur[1 % NF][q][e] : (T)0;
+                    Wv[e] = SYS ? cur[2 % NF][q][e] : (T)0;
+                }
 #pragma unroll
                 for (int f = 0; f < NF; ++f) {
                     const T *sf = st + f * PW;
-                    const T cc = cur[f][q], below = prev[f][q];
-                    const T above = top ? hz1[f * hwz + c] : stn[f * PW + c];
-                    const T xm = (fc & 1) ? hx0[f * hwx + zy + y] : sf[c - 1];
-                    const T xp = (fc & 2) ? hx1[f * hwx + zy + y] : sf[c + 1];
-                    const T ym = (fc & 4) ? hy0[f * hwy + zx + x] : sf[c - m0];
-                    const T yp = (fc & 8) ? hy1[f * hwy + zx + x] : sf[c + m0];
-                    const T d2 = cB[f][0] * ((xp + xm) - (T)2 * cc) + cB[f][1] * ((yp + ym) - (T)2 * cc) +
-                                 cB[f][2] * ((above + below) - (T)2 * cc);
-                    T un;
-                    if constexpr (SYS) {
-                        const T adv = cA0 * U * (xp - xm) + cA1 * V * (yp - ym) + cA2 * Wv * (above - below);
-                        un = cc + (d2 - adv);
-                    } else {
-                        const T d1 = cA0 * (xp - xm) + cA1 * (yp - ym) + cA2 * (above - below);
-                        un = cc + (d2 - cc * d1);
+                    T ab[VW], ym[VW], yp[VW], un[VW];
+                    lds<T, VW>(top ? hz1 + f * hwz + c : stn + f * PW + c, ab);
+                    lds<T, VW>((fc & 4) ? hy0 + f * hwy + zx + x : sf + c - m0, ym);
+                    lds<T, VW>((fc & 8) ? hy1 + f * hwy + zx + x : sf + c + m0, yp);
+                    const T xl = (fc & 1) ? hx0[f * hwx + zy + y] : sf[c - 1];
+                    const T xr = (fc & 2) ? hx1[f * hwx + zy + y] : sf[c + VW];
+#pragma unroll
+                    for (int e = 0; e < VW; ++e) {
+                        const T cc = cur[f][q][e], below = prev[f][q][e], above = ab[e];
+                        const T xm = e == 0 ? xl : cur[f][q][e > 0 ? e - 1 : 0];
+                        const T xp = e == VW - 1 ? xr : cur[f][q][e + 1 < VW ? e + 1 : e];
+                        const T d2 = cB[f][0] * ((xp + xm) - (T)2 * cc) + cB[f][1] * ((yp[e] + ym[e]) - (T)2 * cc) +
+                                     cB[f][2] * ((above + below) - (T)2 * cc);
+                        if constexpr (SYS) {
+                            const T adv = cA0 * Uv[e] * (xp - xm) + cA1 * Vv[e] * (yp[e] - ym[e]) +
+                                          cA2 * Wv[e] * (above - below);
+                            un[e] = cc + (d2 - adv);
+                        } else {
+                            const T d1 = cA0 * (xp - xm) + cA1 * (yp[e] - ym[e]) + cA2 * (above - below);
+                            un[e] = cc + (d2 - cc * d1);
+                        }
                     }
-                    up[f * field_words + coff[q]] = un;
+                    stv<T, VW>(up + f * field_words + coff[q], un);
                     // boundary values of the new level into the ring
                     if (fc) {
-                        if (fc & 1) rf[0][f * fw + zy + y] = un;
-                        if (fc & 2) rf[1][f * fw + zy + y] = un;
-                        if (fc & 4) rf[2][f * fw + zx + x] = un;
-                        if (fc & 8) rf[3][f * fw + zx + x] = un;
+                        if (fc & 1) rf[0][f * fw + zy + y] = un[0];
+                        if (fc & 2) rf[1][f * fw + zy + y] = un[VW - 1];
+                        if (fc & 4) stv<T, VW>(rf[2] + f * fw + zx + x, un);
+                        if (fc & 8) stv<T, VW>(rf[3] + f * fw + zx + x, un);
                     }
-                    if (z == 0) rf[4][f * fw + c] = un;
-                    if (top) rf[5][f * fw + c] = un;
-                    prev[f][q] = cc;
-                    cur[f][q] = above;
+                    if (z == 0) stv<T, VW>(rf[4] + f * fw + c, un);
+                    if (top) stv<T, VW>(rf[5] + f * fw + c, un);
+#pragma unroll
+                    for (int e = 0; e < VW; ++e) {
+                        prev[f][q][e] = cur[f][q][e];
+                        cur[f][q][e] = ab[e];
+                    }
                 }
             }
             // the next read of a plane written here is a bulk copy (async

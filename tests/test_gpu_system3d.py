@@ -58,6 +58,8 @@ CASES = [
     (32, (32, 16, 8), 3, 0),         # two columns per thread
     (24, (8, 4, 3), 4, 5),           # most threads idle, uneven split
 ]
+# FP32 planes of 1024 points: each thread takes a group of 4 consecutive columns
+WIDE = [(64, (32, 32, 8), 5, 7), (64, (32, 32, 4), 3, 0)]
 
 
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
@@ -76,6 +78,19 @@ def test_seeded_system_matches_oracle(dtype, n, sub, nf, max_ctas):
     for f, (m1, m2) in enumerate(g["moments"]):
         assert abs(m1 - g["q"][f].mean()) <= 1e-12 * max(abs(g["q"][f]).max(), 1e-300)
         assert abs(m2 - (g["q"][f] ** 2).mean()) <= 1e-12 * (g["q"][f] ** 2).mean()
+
+
+@pytest.mark.parametrize("n,sub,nf,max_ctas", WIDE)
+def test_wide_planes_fp32_system(n, sub, nf, max_ctas):
+    from paper_1911_05769_gb300 import AT_SEEDED
+    q0, kappa, dt = setup(n, nf)
+    P = tuple(n // m for m in sub)
+    g = gpu_system(q0, sub=sub, L=2, kappa=kappa, dt=dt, steps=30, dtype="f32", mode=AT_SEEDED, seed=5,
+                   max_ctas=max_ctas)
+    ref, hist = oracle.run3d_system(q0, kappa=kappa, P=P, L=2, dt=dt, n_steps=30, delay_mode=oracle.SEEDED, seed=5)
+    for f in range(nf):
+        assert rel_linf(g["q"][f], ref[f]) <= TOL["f32"], f
+    assert np.array_equal(g["hist"], hist)
 
 
 def test_sync_replay_and_free_system():

@@ -404,7 +404,8 @@ static int create3d(const at_grid *grid, int64_t P, int L, int nf, const double 
     // a thread takes one group of vw = 4 consecutive columns (FP32 planes of
     // 1024 points: every thread busy) or 1, 2 or 4 single columns
     const int pw = d.m[0] * d.m[1];
-    const int vw = (w == 4 && d.m[0] % 4 == 0 && pw == 4 * atk::kThreads3) ? 4 : 1;
+    // (a row of sub[0] / 4 groups must lie within one warp: sub[0] <= 128)
+    const int vw = (w == 4 && d.m[0] % 4 == 0 && d.m[0] <= 128 && pw == 4 * atk::kThreads3) ? 4 : 1;
     const int tc = vw == 4 ? 1 : pw <= atk::kThreads3 ? 1 : pw <= 2 * atk::kThreads3 ? 2 : 4;
     if (nf > 1 && vw == 1 && tc > 2) return fail(AT_ERR_ARG, "the 3D system needs sub[0] * sub[1] <= 512 (or 1024, FP32)");
     void *kern = nf == 1 ? atk_stepper3d_kernel(w, tc, vw) : atk_system3d_kernel(w, tc, nf, vw);
@@ -497,6 +498,9 @@ static atk::Params3 make_params3(const at_solver *h)
         p.cA[a] = h->dt / (2.0 * dxa);
         p.cB[a] = h->nu * h->dt / (dxa * dxa);
         for (int f = 0; f < h->nf; ++f) p.cBf[f][a] = h->kappa[f] * h->dt / (dxa * dxa);
+        p.cA32[a] = (float)p.cA[a];
+        for (int f = 0; f < atk::kMaxFields3; ++f)
+            p.cBf32[f][a] = (float)(h->nf > 1 ? (f < h->nf ? p.cBf[f][a] : 0.0) : p.cB[a]);
     }
     p.nf = h->nf;
     p.face_words = h->d3.face_words;

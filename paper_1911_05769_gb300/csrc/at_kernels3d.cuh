@@ -57,6 +57,7 @@ struct Params3 {
     unsigned long long seed;
     double cA[3], cB[3];        // dt / (2 dx_a), nu dt / dx_a^2
     double cBf[kMaxFields3][3]; // the system: kappa_f dt / dx_a^2 per field
+    float cA32[3], cBf32[kMaxFields3][3];   // the same, rounded to FP32 once on the host
     int nf;                     // fields (1: the scalar equation)
     long long face_words;       // words per field of a ring entry (a multiple of 4)
     int G;
@@ -219,12 +220,15 @@ __global__ void __launch_bounds__(kThreads3, AT_MIN_CTAS_3D) at_stepper3d(const 
     const int PW = m0 * m1;
     const unsigned plane_bytes = (unsigned)(NF * PW * (int)sizeof(T));   // one box: a plane of every field
     const long long Q = p.n_steps * S * m2;                 // planes this CTA sweeps
-    const T cA0 = (T)p.cA[0], cA1 = (T)p.cA[1], cA2 = (T)p.cA[2];
+    // (FP32: the host's FP32 copies, so no conversion is ever redone in the loop)
+    constexpr bool F32 = sizeof(T) == 4;
+    const T cA0 = F32 ? (T)p.cA32[0] : (T)p.cA[0], cA1 = F32 ? (T)p.cA32[1] : (T)p.cA[1],
+            cA2 = F32 ? (T)p.cA32[2] : (T)p.cA[2];
     T cB[NF][3];
 #pragma unroll
     for (int q = 0; q < NF; ++q) {
 #pragma unroll
-        for (int a = 0; a < 3; ++a) cB[q][a] = (T)(SYS ? p.cBf[q][a] : p.cB[a]);
+        for (int a = 0; a < 3; ++a) cB[q][a] = F32 ? (T)p.cBf32[SYS ? q : 0][a] : (T)(SYS ? p.cBf[q][a] : p.cB[a]);
     }
     T *u = reinterpret_cast<T *>(p.u);
     const long long field_words = p.n0 * p.n1 * p.n2;
@@ -312,9 +316,14 @@ __global__ void __launch_bounds__(kThreads3, AT_MIN_CTAS_3D) at_stepper3d(const 
     // the current plane g (running counters: no division per plane).
     int gs = 0;
     unsigned gp = 0;
+    // Lane 0 of each warp waits and the warp follows it (warp-uniform
+    // outcome: the plane loop exchanges words by shuffles).
     auto wait_plane = [&](int st, unsigned par) -> bool {
-        if (mbar_try_wait(&bars[st], par)) return true;
-        if (!wait_stage3(p, &bars[st], par)) { atomicExch(s_flag, -1); return false; }
+        int good = 1;
+        if (lane == 0 && !mbar_try_wait(&bars[st], par)) good = wait_stage3(p, &bars[st], par) ? 1 : 0;
+        good = __shfl_sync(0xffffffffu, good, 0);
+        __syncwarp();
+        if (!good) { if (lane == 0) atomicExch(s_flag, -1); return false; }
         return true;
     };
 
@@ -419,7 +428,7 @@ __global__ void __launch_bounds__(kThreads3, AT_MIN_CTAS_3D) at_stepper3d(const 
             const int zy = z * m1, zx = z * m0;
 #pragma unroll
             for (int q = 0; q < TC; ++q) {
-                if (!cv[q]) continue;
+                if (VW == 1 && !cv[q]) continue;            // groups of 4: every thread has one
                 const int x = cx[q], y = cy[q], c = y * m0 + x;
                 const int fc = cface[q];
                 // advecting velocity at the points, level n (the system)
@@ -437,8 +446,18 @@ __global__ void __launch_bounds__(kThreads3, AT_MIN_CTAS_3D) at_stepper3d(const 
                     lds<T, VW>(top ? hz1 + f * hwz + c : stn + f * PW + c, ab);
                     lds<T, VW>((fc & 4) ? hy0 + f * hwy + zx + x : sf + c - m0, ym);
                     lds<T, VW>((fc & 8) ? hy1 + f * hwy + zx + x : sf + c + m0, yp);
-                    const T xl = (fc & 1) ? hx0[f * hwx + zy + y] : sf[c - 1];
-                    const T xr = (fc & 2) ? hx1[f * hwx + zy + y] : sf[c + VW];
+                    T xl, xr;
+                    if constexpr (VW == 4) {
+                        // a row is GR <= 32 consecutive lanes of one warp: the
+                        // words beyond the group are the neighbouring lanes'
+                        const T lft = __shfl_up_sync(0xffffffffu, cur[f][q][VW - 1], 1);
+                        const T rgt = __shfl_down_sync(0xffffffffu, cur[f][q][0], 1);
+                        xl = (fc & 1) ? hx0[f * hwx + zy + y] : lft;
+                        xr = (fc & 2) ? hx1[f * hwx + zy + y] : rgt;
+                    } else {
+                        xl = (fc & 1) ? hx0[f * hwx + zy + y] : sf[c - 1];
+                        xr = (fc & 2) ? hx1[f * hwx + zy + y] : sf[c + VW];
+                    }
 #pragma unroll
                     for (int e = 0; e < VW; ++e) {
                         const T cc = cur[f][q][e], below = prev[f][q][e], above = ab[e];

@@ -10,8 +10,8 @@
 // tile (one subdomain at one level) is swept plane by plane along z: every
 // plane (an m0 x m1 box) is brought into one of `stages` shared-memory buffers
 // by one TMA tensor copy (3D tensor map over the state; completion counted on
-// the stage's mbarrier), several planes ahead; warps free a stage through a
-// second mbarrier.  A thread owns up to TC groups of VW consecutive (x, y)
+// the stage's mbarrier), several planes ahead; the last warp to finish with a
+// stage (a shared counter per stage) refills it.  A thread owns up to TC groups of VW consecutive (x, y)
 // columns; it keeps the values of its columns at planes z-1, z in registers,
 // reads the plane z+1 and the y neighbours as VW-word vectors and the two x
 // neighbours beyond its group as single words from shared memory.
@@ -74,7 +74,7 @@ struct Smem3 {
 __host__ __device__ inline Smem3 smem3_layout(int m0, int m1, int m2, int word, int stages, int nf = 1)
 {
     Smem3 l;
-    l.bar_off = 0;                                   // full[stages], then empty[stages]
+    l.bar_off = 0;                                   // full[stages], then two ints per stage
     l.hist_off = round_up(16LL * stages, 16);
     l.face_off = round_up(l.hist_off + 4LL * (kMaxL + 1), 16);
     l.halo_off = round_up(l.face_off + 6 * 16 + 16, 128);
@@ -234,10 +234,12 @@ __global__ void __launch_bounds__(kThreads3, AT_MIN_CTAS_3D) at_stepper3d(const 
     const long long field_words = p.n0 * p.n1 * p.n2;
 
     constexpr int kWarps3 = kThreads3 / 32;
-    uint64_t *empty = bars + NS;           // every warp arrives once it is done with a stage
+    // per stage: warps done with its plane (the last one refills it), fills issued
+    int *s_done = reinterpret_cast<int *>(bars + NS), *s_fills = s_done + NS;
     if (tid < NS) {
         mbar_init(&bars[tid], 1);
-        mbar_init(&empty[tid], kWarps3);
+        s_done[tid] = 0;
+        s_fills[tid] = 0;
     }
     if (tid == 0) { mbar_fence_init(); *s_flag = 0; }
     for (int i = tid; i <= kMaxL; i += kThreads3) hist[i] = 0u;
@@ -256,36 +258,17 @@ __global__ void __launch_bounds__(kThreads3, AT_MIN_CTAS_3D) at_stepper3d(const 
         const long long q2 = sub / q01, r = sub - q2 * q01, q1 = r / p.P0, q0 = r - q1 * p.P0;
         *x = (int)(q0 * m0); *y = (int)(q1 * m1); *z = (int)(q2 * m2);
     };
-    // issue cursor: the next plane to copy (advanced plane by plane, no division)
-    long long i_sub = lo, issued = 0;
-    int i_z = 0, i_stage = 0, i_x0, i_y0, i_z0;
-    unsigned i_par = 1;                    // parity of the empty-barrier phase the next issue waits for
-    tile_coords(lo, &i_x0, &i_y0, &i_z0);
-    // warp 0 issues the bulk copies of the next plane into its stage, once
-    // every warp is done with the plane that stage held (bounded wait)
-    auto issue = [&]() {
-        if (tid < 32) {
-            if (issued >= NS) {
-                int good = 1;
-                if (lane == 0 && !mbar_try_wait(&empty[i_stage], i_par)) good = wait_stage3(p, &empty[i_stage], i_par);
-                good = __shfl_sync(0xffffffffu, good, 0);
-                if (!good) atomicExch(s_flag, -1);
-            }
-            if (lane == 0) {
-                uint64_t *bar = &bars[i_stage];
-                mbar_arrive_expect_tx(bar, plane_bytes);
-                tensor_load_4d(stages + (size_t)i_stage * sl.plane_bytes, &tmap, i_x0, i_y0, i_z0 + i_z, 0, bar);
-            }
-            __syncwarp();
-        }
-        ++issued;
-        if (++i_stage == NS) { i_stage = 0; i_par ^= 1u; }
-        if (++i_z == m2) {
-            i_z = 0;
-            if (++i_sub == hi) i_sub = lo;
-            tile_coords(i_sub, &i_x0, &i_y0, &i_z0);
-        }
+    // one plane of every field into stage st (lane 0 of the issuing warp)
+    auto issue_plane = [&](int st, int x0, int y0, int z0) {
+        mbar_arrive_expect_tx(&bars[st], plane_bytes);
+        tensor_load_4d(stages + (size_t)st * sl.plane_bytes, &tmap, x0, y0, z0, 0, &bars[st]);
+        ++s_fills[st];
     };
+    // element coordinates of the current tile's subdomain and of the next
+    // tile's (a refill is at most stages <= m2 planes ahead)
+    int tx0, ty0, tz0, nx0, ny0, nz0;
+    tile_coords(lo, &tx0, &ty0, &tz0);
+    tile_coords(lo + 1 == hi ? lo : lo + 1, &nx0, &ny0, &nz0);
 
     // column groups of this thread: first column, offset in a plane of u,
     // faces touched (x: by the group's first / last column)
@@ -309,7 +292,8 @@ __global__ void __launch_bounds__(kThreads3, AT_MIN_CTAS_3D) at_stepper3d(const 
 #pragma unroll
             for (int e = 0; e < VW; ++e) prev[f][q][e] = cur[f][q][e] = (T)0;
 
-    while (issued < NS && issued < Q) issue();
+    if (tid == 0)
+        for (int st = 0; st < NS && st < Q; ++st) issue_plane(st, tx0, ty0, tz0 + st);
     // a failed wait is recorded in s_flag; every thread acts on it at the
     // next CTA barrier (one per tile), so control flow stays uniform there.
     // Planes are consumed in order: gs, gp are the stage and fill parity of
@@ -332,6 +316,7 @@ __global__ void __launch_bounds__(kThreads3, AT_MIN_CTAS_3D) at_stepper3d(const 
     // planes, and all threads leave together after the next tile-start barrier.
     bool ok = true;
     long long lv = lev0, sub = lo;
+    long long g = 0;                         // plane of the sweep being computed (0 .. Q-1)
     long long prev_sub = -1, prev_new = 0;   // the tile whose flags are still to be released
     T *rf[6];                                // ring entries of the new level of the current tile
     const long long n_tiles = p.n_steps * S;
@@ -498,26 +483,43 @@ __global__ void __launch_bounds__(kThreads3, AT_MIN_CTAS_3D) at_stepper3d(const 
             // subdomain, fence every plane
             if (top || S == 1) fence_proxy_async_global();
             __syncwarp();
-            if (lane == 0) mbar_arrive(&empty[sg]);
-            if (issued < Q) issue();
+            // done with stage sg (plane g; plane g - 1 read it as the plane
+            // above): the last warp refills it with plane g + NS
+            if (lane == 0) {
+                __threadfence_block();
+                if (atomicAdd(&s_done[sg], 1) == kWarps3 - 1) {
+                    s_done[sg] = 0;
+                    __threadfence_block();
+                    if (g + NS < Q) {
+                        if (z + NS < m2) issue_plane(sg, tx0, ty0, tz0 + z + NS);
+                        else issue_plane(sg, nx0, ny0, nz0 + z + NS - m2);
+                    }
+                }
+            }
+            ++g;
             gs = sg1;
             gp = gp1;
         }
         prev_sub = sub;
         prev_new = lnew;
         if (++sub == hi) { sub = lo; ++lv; }
+        // coordinates of the new tile and of the one after it
+        tx0 = nx0; ty0 = ny0; tz0 = nz0;
+        tile_coords(sub + 1 == hi ? lo : sub + 1, &nx0, &ny0, &nz0);
     }
     __syncthreads();
     if (tid == 0 && ok && prev_sub >= 0) {
         __threadfence();
         for (int f = 0; f < 6; ++f) st_release(p.flag + prev_sub * 6 + f, (unsigned long long)prev_new);
     }
-    // let the copies in flight land before leaving
+    // let the copies in flight land before leaving (the latest fill of each
+    // stage completes the phase of parity (fills - 1) & 1)
     if (tid == 0) {
-        for (long long t = (issued > NS ? issued - NS : 0); t < issued; ++t) {
+        for (int st = 0; st < NS; ++st) {
+            if (s_fills[st] == 0) continue;
+            const unsigned par = (unsigned)((s_fills[st] - 1) & 1);
             const unsigned long long t0 = global_ns();
-            while (!mbar_try_wait(&bars[t % NS], (unsigned)((t / NS) & 1)) &&
-                   (long long)(global_ns() - t0) < p.timeout_ns) {
+            while (!mbar_try_wait(&bars[st], par) && (long long)(global_ns() - t0) < p.timeout_ns) {
             }
         }
     }

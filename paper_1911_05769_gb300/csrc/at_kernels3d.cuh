@@ -200,8 +200,6 @@ __global__ void __launch_bounds__(kThreads3, AT_MIN_CTAS_3D) at_stepper3d(const 
     const Smem3 sl = smem3_layout(p.m0, p.m1, p.m2, (int)sizeof(T), p.stages, NF);
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + sl.bar_off);
     unsigned *hist = reinterpret_cast<unsigned *>(smem + sl.hist_off);
-    int *s_k = reinterpret_cast<int *>(smem + sl.face_off);                  // [6] delays of the tile
-    long long *s_q = reinterpret_cast<long long *>(smem + sl.face_off + 32);  // [6] face neighbours
     int *s_flag = reinterpret_cast<int *>(smem + sl.face_off + 80);          // barrier / abort word
     unsigned char *stages = smem + sl.stage_off;
     // halo planes of face f, field q: halo_at[f] + q * halo_words[f] words
@@ -336,55 +334,82 @@ __global__ void __launch_bounds__(kThreads3, AT_MIN_CTAS_3D) at_stepper3d(const 
         const long long base = tile_base(sub);
 #pragma unroll
         for (int f = 0; f < 6; ++f) rf[f] = ring_entry<T>(p, lv + 1, sub, f);
-        if (tid < 6) {
-            const int f = tid;
+        // warp f (< 6) takes face f: its lane 0 chooses the delay and checks
+        // (or waits for) the neighbour's flag, then the warp stages the
+        // face's halo plane -- the neighbour's facing ring entries,
+        // extrapolated once with the delay (16-byte loads where aligned)
+        if ((tid >> 5) < 6) {
+            const int f = tid >> 5;
             const long long q = face_neighbour(p, s0, s1, s2, f);
-            long long kmax = lv - 2 + 1;           // s = 2 levels per extrapolation
-            if (kmax < 0) kmax = 0;
-            if (kmax > p.L) kmax = p.L;
             long long k = 0;
-            if (p.mode == kModeSeeded) {
-                const unsigned long long ctr = ((unsigned long long)lv * (unsigned long long)p.P +
-                                                (unsigned long long)sub) * 6ull + (unsigned long long)f;
-                k = (long long)(((splitmix64(p.seed, ctr) >> 32) * (unsigned long long)(p.L + 1)) >> 32);
-            } else if (p.mode == kModeReplay) {
-                k = p.delays[((size_t)(lv - lev0) * p.P + sub) * 6 + f];
-            }
-            if (k > kmax) k = kmax;
-            if (k < 0) k = 0;
             int good = 1;
-            if (p.mode != kModeSync) {
-                const unsigned long long *fl = p.flag + q * 6 + (f ^ 1);
-                const long long need = (p.mode == kModeFree) ? lv - kmax : lv - k;
-                unsigned long long seen = ld_acquire(fl);
-                if ((long long)seen < need && !wait_flag3(p, fl, need, &seen, lv, q)) good = 0;
-                if (good && p.mode == kModeFree) k = lv - ((long long)seen < lv ? (long long)seen : lv);
+            if (lane == 0) {
+                long long kmax = lv - 2 + 1;           // s = 2 levels per extrapolation
+                if (kmax < 0) kmax = 0;
+                if (kmax > p.L) kmax = p.L;
+                if (p.mode == kModeSeeded) {
+                    const unsigned long long ctr = ((unsigned long long)lv * (unsigned long long)p.P +
+                                                    (unsigned long long)sub) * 6ull + (unsigned long long)f;
+                    k = (long long)(((splitmix64(p.seed, ctr) >> 32) * (unsigned long long)(p.L + 1)) >> 32);
+                } else if (p.mode == kModeReplay) {
+                    k = p.delays[((size_t)(lv - lev0) * p.P + sub) * 6 + f];
+                }
+                if (k > kmax) k = kmax;
+                if (k < 0) k = 0;
+                if (p.mode != kModeSync) {
+                    const unsigned long long *fl = p.flag + q * 6 + (f ^ 1);
+                    const long long need = (p.mode == kModeFree) ? lv - kmax : lv - k;
+                    unsigned long long seen = ld_acquire(fl);
+                    if ((long long)seen < need && !wait_flag3(p, fl, need, &seen, lv, q)) good = 0;
+                    if (good && p.mode == kModeFree) k = lv - ((long long)seen < lv ? (long long)seen : lv);
+                }
+                if (good) {
+                    atomicAdd(&hist[k], 1u);
+                    if (p.delays && p.mode != kModeReplay)
+                        p.delays[((size_t)(lv - lev0) * p.P + sub) * 6 + f] = (int8_t)k;
+                } else {
+                    atomicExch(s_flag, -1);
+                }
             }
+            good = __shfl_sync(0xffffffffu, good, 0);
+            const int kk = __shfl_sync(0xffffffffu, (int)k, 0);
             if (good) {
-                atomicAdd(&hist[k], 1u);
-                if (p.delays && p.mode != kModeReplay) p.delays[((size_t)(lv - lev0) * p.P + sub) * 6 + f] = (int8_t)k;
+                const T *e0 = ring_entry<T>(p, lv - kk, q, f ^ 1);
+                const T *e1 = ring_entry<T>(p, lv - kk - 1, q, f ^ 1);
+                // (entries of the layout picked by selects: no local-memory copy)
+                long long hat = sl.halo_at[0], hwd = sl.halo_words[0];
+#pragma unroll
+                for (int i = 1; i < 6; ++i) {
+                    hat = f == i ? sl.halo_at[i] : hat;
+                    hwd = f == i ? sl.halo_words[i] : hwd;
+                }
+                T *h = reinterpret_cast<T *>(smem + hat);
+                const int nw = (int)hwd;
+                const T a = (T)(kk + 1), b = (T)kk;
+                for (int fld = 0; fld < NF; ++fld) {
+                    const T *s0p = e0 + fld * fw, *s1p = e1 + fld * fw;
+                    T *hp = h + fld * nw;
+                    if (sizeof(T) == 4 && (nw & 3) == 0) {
+                        for (int i = 4 * lane; i < nw; i += 128) {
+                            T v0[4], v1[4];
+                            lds<T, 4>(s0p + i, v0);           // (a 16-byte generic load of global memory)
+                            if (kk != 0) {
+                                lds<T, 4>(s1p + i, v1);
+#pragma unroll
+                                for (int e = 0; e < 4; ++e) v0[e] = a * v0[e] - b * v1[e];
+                            }
+                            sts4<T>(hp + i, v0);
+                        }
+                    } else {
+                        for (int i = lane; i < nw; i += 32)
+                            hp[i] = kk == 0 ? s0p[i] : a * s0p[i] - b * s1p[i];
+                    }
+                }
             }
-            s_k[f] = (int)k;
-            s_q[f] = q;
-            if (!good) atomicExch(s_flag, -1);
         }
         if (tid == 0 && p.mode == kModeSync) __threadfence();
         __syncthreads();
         if (*s_flag == -1) { ok = false; break; }
-        // the six halo planes of the tile: the neighbours' facing ring
-        // entries (coalesced), extrapolated once with the faces' delays
-#pragma unroll
-        for (int f = 0; f < 6; ++f) {
-            const int k = s_k[f];
-            const T *e0 = ring_entry<T>(p, lv - k, s_q[f], f ^ 1);
-            const T *e1 = ring_entry<T>(p, lv - k - 1, s_q[f], f ^ 1);
-            T *h = reinterpret_cast<T *>(smem + sl.halo_at[f]);
-            const int nw = (int)sl.halo_words[f];
-            for (int fld = 0; fld < NF; ++fld)
-                for (int i = tid; i < nw; i += kThreads3)
-                    h[fld * nw + i] = k == 0 ? e0[fld * fw + i] : (T)(k + 1) * e0[fld * fw + i] - (T)k * e1[fld * fw + i];
-        }
-        __syncthreads();
         // plane z = -1 (the -z halo) and plane 0
         if (!wait_plane(gs, gp)) { ok = false; }
         {

@@ -700,9 +700,8 @@ __device__ void run_pe(const Params &p, const Sweep &sw, long long lo, long long
             else
                 hv = approx_halo<T, S_LEV>(rw + f * kMaxS * kRingEntry, (f ? k1cur : k0cur) + rem / R, rem % R);
         }
-        // one level of the tile: old values in cs, new ones into cd (the
-        // level loop alternates two register arrays, so no moves are needed
-        // between levels)
+        // one level of the tile, in place (cs and cd are the same array: a
+        // group's old words are copied into its window before it is written)
         auto level = [&](int i, T (&cs)[GW][4], T (&cd)[GW][4]) {
             const long long lev = n + i + 1;                 // level being computed
             T hl[R], hr[R];
@@ -821,18 +820,7 @@ __device__ void run_pe(const Params &p, const Sweep &sw, long long lo, long long
                 }
             }
         };
-        T c2[GW][4];
-        for (int i = 0; i < len; i += 2) {
-            level(i, c, c2);
-            if (i + 1 == len) {
-#pragma unroll
-                for (int m = 0; m < GW; ++m)
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) c[m][e] = c2[m][e];
-                break;
-            }
-            level(i + 1, c2, c);
-        }
+        for (int i = 0; i < len; ++i) level(i, c, c);
         // the next tile; before a turn the words stay in registers
         Cursor Cn = C;
         advance(sw, Cn, lo, hi, S_LEV);

@@ -145,39 +145,51 @@ struct AdjStep {
     }
 };
 
-// Block (x, y) handles points y*256 .. y*256+255 of subdomains x, x + gridDim.x,
-// ...  Each point first computes the 2R+1 terms it contributes to the adjoint
-// of its stencil values (c_j = lambda^{n+1}_r d u^{n+1}_r / d v_j) into shared
-// memory; each point then gathers the terms of its readers from there.
+// Block (x, y) handles the chunk of points y*C .. y*C+C-1 (C = 1024: a thread
+// takes 4 points, 256 apart) of subdomains x, x + gridDim.x, ...  Each point
+// first computes the 2R+1 terms it contributes to the adjoint of its stencil
+// values (c_j = lambda^{n+1}_r d u^{n+1}_r / d v_j) into shared memory; each
+// point then gathers the terms of its readers from there.
 constexpr int kAdjThreads = 256;
+constexpr int kAdjPts = 4;                            // points per thread
+constexpr int kAdjChunk = kAdjThreads * kAdjPts;      // points per block and subdomain
 
 template <typename T, int ORDER>
-__global__ void __launch_bounds__(kAdjThreads) at_adjoint_step(const AdjParams a)
+__global__ void __launch_bounds__(kAdjThreads, ORDER == 2 ? 7 : 3) at_adjoint_step(const AdjParams a)
 {
     constexpr int R = ORDER / 2;
     constexpr int S_LEV = ORDER / 2 + 1;
     const AdjStep<T, ORDER> A(a);
-    __shared__ T s_c[2 * R + 1][kAdjThreads];
+    __shared__ T s_c[2 * R + 1][kAdjChunk];
     T nu_acc = (T)0;          // this thread's sum of lambda^{n+1}_i b_i
     const T dtdx2 = sizeof(T) == 4 ? (T)a.dtdx2f : (T)a.dtdx2;
     const int tid = threadIdx.x, lane = tid & 31;
     const int M = A.M;
-    const int chunk_lo = blockIdx.y * kAdjThreads;
-    const int loc = chunk_lo + tid;
+    const int chunk_lo = blockIdx.y * kAdjChunk;
     T *lam_out = reinterpret_cast<T *>(a.lam_out);
     for (int p = blockIdx.x; p < A.P; p += gridDim.x) {
         const int pl = A.left(p), pr = A.right(p);
+        // loads that need no delay first (lambda^{n+1}; the pending words
+        // addressed to this level), so that their latency overlaps the delays'
+        T gl[kAdjPts], pw[kAdjPts];
+#pragma unroll
+        for (int kp = 0; kp < kAdjPts; ++kp) {
+            const int loc = chunk_lo + tid + kp * kAdjThreads;
+            gl[kp] = loc < M ? A.lam[p * M + loc] : (T)0;
+            pw[kp] = loc < R ? *A.pend(a.n, p, 0, loc) : (loc >= M - R && loc < M) ? *A.pend(a.n, p, 1, loc - (M - R)) : (T)0;
+        }
         // delays (lanes 0..3, then shared across the warp): this subdomain's
         // faces 0, 1; the left neighbour's face 1; the right neighbour's face 0
         int kk = 0;
         if (lane < 4) kk = A.delay(lane < 2 ? p : (lane == 2 ? pl : pr), lane < 2 ? lane : (lane == 2 ? 1 : 0));
         const int k0 = __shfl_sync(0xffffffffu, kk, 0), k1 = __shfl_sync(0xffffffffu, kk, 1);
         const int kl1 = __shfl_sync(0xffffffffu, kk, 2), kr0 = __shfl_sync(0xffffffffu, kk, 3);
-        __syncthreads();   // the previous subdomain's terms have been read
-        const bool live = loc < M;
-        const int i = p * M + loc;
-        T v[2 * R + 1];
-        if (live) {
+        if (p != (int)blockIdx.x) __syncthreads();   // the previous subdomain's terms have been read
+#pragma unroll
+        for (int kp = 0; kp < kAdjPts; ++kp) {
+            const int off = tid + kp * kAdjThreads, loc = chunk_lo + off;
+            if (loc >= M) continue;
+            T v[2 * R + 1];
             A.values(p, loc, k0, k1, v);
             T av = (T)0, bv = (T)0;
 #pragma unroll
@@ -185,25 +197,30 @@ __global__ void __launch_bounds__(kAdjThreads) at_adjoint_step(const AdjParams a
                 av += (T)Coeffs<ORDER>::alpha(q) * v[q + R];
                 bv += (T)Coeffs<ORDER>::beta(q) * v[q + R];
             }
-            const T g = A.lam[i];
+            const T g = gl[kp];
 #pragma unroll
             for (int j = -R; j <= R; ++j) {
                 T d = A.cB * (T)Coeffs<ORDER>::beta(j) - A.cA * v[R] * (T)Coeffs<ORDER>::alpha(j);
                 if (j == 0) d += (T)1 - A.cA * av;
-                s_c[j + R][tid] = g * d;
+                s_c[j + R][off] = g * d;
             }
             nu_acc += g * bv;
         }
         __syncthreads();
-        if (live) {
+#pragma unroll
+        for (int kp = 0; kp < kAdjPts; ++kp) {
+            const int off = tid + kp * kAdjThreads, loc = chunk_lo + off;
+            if (loc >= M) continue;
+            const int i = p * M + loc;
+            T v[2 * R + 1];
             T acc = (T)0;
             // readers r = i + d whose value j = -d is u^n_i
 #pragma unroll
             for (int d = -R; d <= R; ++d) {
                 const int rl = loc + d;
                 if (rl >= 0 && rl < M) {
-                    if (rl >= chunk_lo && rl < chunk_lo + kAdjThreads) {
-                        acc += s_c[-d + R][tid + d];
+                    if (rl >= chunk_lo && rl < chunk_lo + kAdjChunk) {
+                        acc += s_c[-d + R][off + d];
                     } else {
                         A.values(p, rl, k0, k1, v);
                         acc += A.gbar(i + d, -d, v);
@@ -221,21 +238,19 @@ __global__ void __launch_bounds__(kAdjThreads) at_adjoint_step(const AdjParams a
                     acc += A.gbar(pr * M + (rl - M), -d, v);
                 }
             }
-            // delayed reads from later steps addressed to level n
+            // delayed reads from later steps addressed to level n (loaded above)
             if (loc < R) {
-                T *q = A.pend(a.n, p, 0, loc);
-                acc += *q;
-                *q = (T)0;
+                acc += pw[kp];
+                *A.pend(a.n, p, 0, loc) = (T)0;
             } else if (loc >= M - R) {
-                T *q = A.pend(a.n, p, 1, loc - (M - R));
-                acc += *q;
-                *q = (T)0;
+                acc += pw[kp];
+                *A.pend(a.n, p, 1, loc - (M - R)) = (T)0;
             }
             lam_out[i] = acc;
 
             // this subdomain's delayed reads across a face, scattered to older
             // levels of the neighbour's boundary values (one thread per face;
-            // its readers are in its own chunk)
+            // its readers are in its own chunk: the last chunk holds >= 4 points)
             if (loc == 0 || loc == M - 1) {
                 const int f = loc == 0 ? 0 : 1;
                 const int k = f == 0 ? k0 : k1;
@@ -256,7 +271,7 @@ __global__ void __launch_bounds__(kAdjThreads) at_adjoint_step(const AdjParams a
                 for (int r = 0; r < R; ++r) src[r] = (T)0;
 #pragma unroll
                 for (int t = 0; t < R; ++t) {
-                    const int rt = f == 0 ? tid + t : tid - t;         // reader's thread
+                    const int rt = f == 0 ? off + t : off - t;         // reader's place in the chunk
 #pragma unroll
                     for (int j = -R; j <= R; ++j) {
                         const bool crosses = f == 0 ? (j <= -t - 1) : (j >= t + 1);
@@ -290,7 +305,10 @@ __global__ void __launch_bounds__(kAdjThreads) at_adjoint_step(const AdjParams a
     if (tid == 0) {
         double sum = 0.0;
         for (int w = 0; w < kAdjThreads / 32; ++w) sum += (double)red[w] * (double)dtdx2;
-        a.dnu_part[(size_t)blockIdx.y * gridDim.x + blockIdx.x] += sum;
+        // one add per block and launch into the block's own running total: a
+        // reduction without return (no load on the block's critical path);
+        // launches are stream-ordered, so the order of the adds is fixed
+        atomicAdd(a.dnu_part + (size_t)blockIdx.y * gridDim.x + blockIdx.x, sum);
     }
 }
 

@@ -1109,9 +1109,9 @@ int64_t ckpt_levels(const at_solver *h) { return h->L + h->s; }
 
 int64_t n_segments(int64_t n_steps, int64_t interval) { return n_steps <= 0 ? 1 : (n_steps + interval - 1) / interval; }
 
-// adjoint launch: x walks the subdomains, y the 256-point chunks of one
+// adjoint launch: x walks the subdomains, y the 1024-point chunks of one
 int adj_grid_x(const at_solver *h) { return (int)(h->P < 16LL * h->sm_count ? h->P : 16LL * h->sm_count); }
-int adj_grid_y(const at_solver *h) { return (int)((h->M + atk::kAdjThreads - 1) / atk::kAdjThreads); }
+int adj_grid_y(const at_solver *h) { return (int)((h->M + atk::kAdjChunk - 1) / atk::kAdjChunk); }
 int adj_blocks(const at_solver *h) { return adj_grid_x(h) * adj_grid_y(h); }
 
 struct AdjLayout {

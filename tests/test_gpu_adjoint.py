@@ -81,6 +81,22 @@ def test_adjoint_matches_oracle_fp64(order, L, mode, interval, max_ctas):
     assert abs(dnu - odnu) <= TOL["f64"] * abs(odnu)
 
 
+@pytest.mark.parametrize("order,M", [(4, 516), (2, 1020)])
+def test_adjoint_long_subdomains(order, M):
+    """Subdomains of 516 and 1020 points: a thread of the adjoint step takes
+    several points of one subdomain (256 apart), the last ones partly idle."""
+    from paper_1911_05769_gb300 import AT_SEEDED
+    pr = problem(N=6 * M, P=6, order=order, L=2, steps=40, nu=0.02)
+    uT, lam0, dnu, _ = gpu_adjoint(pr, mode=AT_SEEDED, interval=9)
+    ouT, olam0, odnu = oracle_adjoint(pr, mode=oracle.SEEDED)
+    assert rel_linf(uT, ouT) <= TOL["f64"]
+    assert rel_linf(lam0, olam0) <= TOL["f64"]
+    # dJ/dnu sums N * steps (~1e5) terms of both signs, in another order on
+    # each side (per block on the GPU): the FP64 bound K eps sum|t| allows
+    # ~1e-11 of sum|t|, a few times |dJ/dnu| here
+    assert abs(dnu - odnu) <= 1e-10 * abs(odnu)
+
+
 def test_adjoint_of_replayed_and_free_runs():
     from paper_1911_05769_gb300 import AT_FREE, AT_REPLAY
     pr = problem(N=640, P=20, order=2, L=3, steps=80)

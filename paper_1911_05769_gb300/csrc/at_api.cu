@@ -291,6 +291,7 @@ struct at_solver {
     int dim;                   // 1 or 3
     Dims3 d3;                  // 3D: extents, subdomains, ring entry size
     int tc;                    // 3D: columns per thread
+    int nt3;                   // 3D: threads per CTA
     CUtensorMap tmap;          // 3D: tensor map of the state (planes of a subdomain, all fields)
     int nf;                    // 3D: fields (1: the scalar equation; 3..5: the system)
     double kappa[atk::kMaxFields3];   // 3D system: viscosity / diffusivities of the fields
@@ -406,7 +407,10 @@ static int create3d(const at_grid *grid, int64_t P, int L, int nf, const double 
     const int pw = d.m[0] * d.m[1];
     // (a row of sub[0] / 4 groups must lie within one warp: sub[0] <= 128)
     const int vw = (w == 4 && d.m[0] % 4 == 0 && d.m[0] <= 128 && pw == 4 * atk::kThreads3) ? 4 : 1;
-    const int tc = vw == 4 ? 1 : pw <= atk::kThreads3 ? 1 : pw <= 2 * atk::kThreads3 ? 2 : 4;
+    // the scalar equation with groups of 4: CTAs of 128 threads, two groups
+    // each (4 CTAs per SM: one CTA's tile start overlaps the others' planes)
+    const int nt = (vw == 4 && nf == 1) ? 128 : atk::kThreads3;
+    const int tc = vw == 4 ? (nf == 1 ? 2 : 1) : pw <= atk::kThreads3 ? 1 : pw <= 2 * atk::kThreads3 ? 2 : 4;
     if (nf > 1 && vw == 1 && tc > 2) return fail(AT_ERR_ARG, "the 3D system needs sub[0] * sub[1] <= 512 (or 1024, FP32)");
     void *kern = nf == 1 ? atk_stepper3d_kernel(w, tc, vw) : atk_system3d_kernel(w, tc, nf, vw);
     // plane buffers: at least 3 (planes z and z+1 in use, one arriving), at most sub[2]
@@ -419,7 +423,7 @@ static int create3d(const at_grid *grid, int64_t P, int L, int nf, const double 
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sl3.total);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
     int occ = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, atk::kThreads3, (size_t)sl3.total);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, nt, (size_t)sl3.total);
     if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
     int64_t G = grid->max_ctas > 0 ? grid->max_ctas : (int64_t)occ * sms;
     if (G > P) G = P;
@@ -433,6 +437,7 @@ static int create3d(const at_grid *grid, int64_t P, int L, int nf, const double 
     h->dim = 3;
     h->d3 = d;
     h->tc = tc;
+    h->nt3 = nt;
     h->nf = nf;
     for (int f = 0; f < nf; ++f) h->kappa[f] = kappa[f];
     h->N = (int64_t)nf * d.n[0] * d.n[1] * d.n[2];   // words of the state (all fields)
@@ -675,7 +680,7 @@ static int step_impl(at_solver *h, int64_t n_steps, int delay_mode, int8_t *dela
         p.n_steps = n_steps;
         cudaLaunchConfig_t cfg{};
         cfg.gridDim = dim3(h->G);
-        cfg.blockDim = dim3(atk::kThreads3);
+        cfg.blockDim = dim3(h->nt3);
         cfg.dynamicSmemBytes = (size_t)h->smem;
         cfg.stream = h->stream;
         cudaLaunchAttribute attr[1];

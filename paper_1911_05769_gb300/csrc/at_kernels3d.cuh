@@ -35,7 +35,7 @@
 
 namespace atk {
 
-constexpr int kThreads3 = 256;
+constexpr int kThreads3 = 256;          // threads of a CTA (128 for groups of 4 columns)
 constexpr int kMaxFields3 = 6;          // fields of the system (u, v, w and up to 3 scalars)
 #ifndef AT_MIN_CTAS_3D
 #define AT_MIN_CTAS_3D 2      // resident CTAs per SM the 3D stepper is compiled for
@@ -193,8 +193,9 @@ __device__ __forceinline__ void stv(T *g, const T *v)
     }
 }
 
-template <typename T, int TC, int NF, bool SYS, int VW>
-__global__ void __launch_bounds__(kThreads3, AT_MIN_CTAS_3D) at_stepper3d(const Params3 p, const __grid_constant__ CUtensorMap tmap)
+template <typename T, int TC, int NF, bool SYS, int VW, int NT = kThreads3>
+__global__ void __launch_bounds__(NT, NT == kThreads3 ? AT_MIN_CTAS_3D : 2 * AT_MIN_CTAS_3D)
+    at_stepper3d(const Params3 p, const __grid_constant__ CUtensorMap tmap)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     const Smem3 sl = smem3_layout(p.m0, p.m1, p.m2, (int)sizeof(T), p.stages, NF);
@@ -231,7 +232,7 @@ __global__ void __launch_bounds__(kThreads3, AT_MIN_CTAS_3D) at_stepper3d(const 
     T *u = reinterpret_cast<T *>(p.u);
     const long long field_words = p.n0 * p.n1 * p.n2;
 
-    constexpr int kWarps3 = kThreads3 / 32;
+    constexpr int kWarps3 = NT / 32;
     // per stage: warps done with its plane (the last one refills it), fills issued
     int *s_done = reinterpret_cast<int *>(bars + NS), *s_fills = s_done + NS;
     if (tid < NS) {
@@ -240,7 +241,7 @@ __global__ void __launch_bounds__(kThreads3, AT_MIN_CTAS_3D) at_stepper3d(const 
         s_fills[tid] = 0;
     }
     if (tid == 0) { mbar_fence_init(); *s_flag = 0; }
-    for (int i = tid; i <= kMaxL; i += kThreads3) hist[i] = 0u;
+    for (int i = tid; i <= kMaxL; i += NT) hist[i] = 0u;
     __syncthreads();
 
     // word offset of the first point of subdomain `sub` in u
@@ -275,7 +276,7 @@ __global__ void __launch_bounds__(kThreads3, AT_MIN_CTAS_3D) at_stepper3d(const 
     const int GR = m0 / VW;                  // groups per row (the host checks VW | m0)
 #pragma unroll
     for (int q = 0; q < TC; ++q) {
-        const int c = tid + kThreads3 * q;
+        const int c = tid + NT * q;
         cv[q] = c < PW / VW;
         cx[q] = cv[q] ? (c % GR) * VW : 0;
         cy[q] = cv[q] ? c / GR : 0;
@@ -334,12 +335,11 @@ __global__ void __launch_bounds__(kThreads3, AT_MIN_CTAS_3D) at_stepper3d(const 
         const long long base = tile_base(sub);
 #pragma unroll
         for (int f = 0; f < 6; ++f) rf[f] = ring_entry<T>(p, lv + 1, sub, f);
-        // warp f (< 6) takes face f: its lane 0 chooses the delay and checks
-        // (or waits for) the neighbour's flag, then the warp stages the
-        // face's halo plane -- the neighbour's facing ring entries,
-        // extrapolated once with the delay (16-byte loads where aligned)
-        if ((tid >> 5) < 6) {
-            const int f = tid >> 5;
+        // warp w takes faces w, w + NT/32, ... (< 6): its lane 0 chooses the
+        // delay and checks (or waits for) the neighbour's flag, then the warp
+        // stages the face's halo plane -- the neighbour's facing ring
+        // entries, extrapolated once with the delay (16-byte loads where aligned)
+        for (int f = tid >> 5; f < 6; f += kWarps3) {
             const long long q = face_neighbour(p, s0, s1, s2, f);
             long long k = 0;
             int good = 1;

@@ -5,12 +5,12 @@
 #include "at_kernels3d.cuh"
 
 namespace {
-template <typename T, int TC, int VW>
+template <typename T, int TC, int VW, int NT = atk::kThreads3>
 void *system_for(int nf)
 {
-    return nf == 3 ? (void *)atk::at_stepper3d<T, TC, 3, true, VW>
-                   : nf == 4 ? (void *)atk::at_stepper3d<T, TC, 4, true, VW>
-                             : (void *)atk::at_stepper3d<T, TC, 5, true, VW>;
+    return nf == 3 ? (void *)atk::at_stepper3d<T, TC, 3, true, VW, NT>
+                   : nf == 4 ? (void *)atk::at_stepper3d<T, TC, 4, true, VW, NT>
+                             : (void *)atk::at_stepper3d<T, TC, 5, true, VW, NT>;
 }
 }  // namespace
 

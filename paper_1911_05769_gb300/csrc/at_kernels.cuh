@@ -700,6 +700,22 @@ __device__ void run_pe(const Params &p, const Sweep &sw, long long lo, long long
             else
                 hv = approx_halo<T, S_LEV>(rw + f * kMaxS * kRingEntry, (f ? k1cur : k0cur) + rem / R, rem % R);
         }
+        // this lane's ring entry (slot 0) and flag of the face it publishes,
+        // and whether the consumer across that face waits on the flag
+        // (lane_last == 0: lane 0 publishes both faces, face 1 via prel1)
+        const int pf = (lane == 0) ? 0 : 1;
+        unsigned char *const pe0 = p.ring + ((size_t)j * 2 + pf) * kRingEntry;
+        unsigned long long *const pflag = p.flag + j * 2 + pf;
+        bool prel, prel1 = false;
+        if constexpr (BATCH) {
+            const BatchSub &b = btab[j - lo];
+            const long long q0 = pf ? b.right : b.left;
+            prel = q0 >= 0 && (q0 < lo || q0 >= hi || q0 != j + (pf ? 1 : -1));
+            prel1 = b.right >= 0 && (b.right < lo || b.right >= hi || b.right != j + 1);
+        } else {
+            prel = pf ? j == hi - 1 : j == lo;
+            prel1 = j == hi - 1;
+        }
         // one level of the tile, in place (cs and cd are the same array: a
         // group's old words are copied into its window before it is written)
         auto level = [&](int i, T (&cs)[GW][4], T (&cd)[GW][4]) {
@@ -797,26 +813,29 @@ __device__ void run_pe(const Params &p, const Sweep &sw, long long lo, long long
                 for (int q = 0; q < R; ++q) rb[q] = (m == m_last) ? cd[m][4 - R + q] : rb[q];
             }
             // publish the new boundary values and release the edge flags
-            // (face 0 by lane 0, face 1 by the owner of group NG-1)
+            // (face 0 by lane 0, face 1 by the owner of group NG-1; the
+            // tile's entry addresses and release conditions are set above)
             if (lane == 0 || lane == lane_last) {
-                const long long slot = lev & (p.T - 1);
+                const size_t slot_off = (size_t)(lev & (p.T - 1)) * slot_stride;
                 const bool pub_ok = edge_pub || lev <= p.skip_step;
-                unsigned char *e0 = p.ring + (size_t)slot * slot_stride + (size_t)j * 2 * kRingEntry;
-                const int f_lo = (lane == 0) ? 0 : 1, f_hi = (lane == lane_last) ? 1 : 0;
-                for (int f = f_lo; f <= f_hi; ++f) {
-                    T w[R];                // word by word: no runtime choice between arrays
+                if (FULL || lane_last != 0) {
+                    T w[R];                    // word by word: no runtime choice between arrays
 #pragma unroll
-                    for (int q = 0; q < R; ++q) w[q] = f ? rb[q] : cd[0][q];
-                    st_entry<T, R>(e0 + f * kRingEntry, w);
+                    for (int q = 0; q < R; ++q) w[q] = pf ? rb[q] : cd[0][q];
+                    st_entry<T, R>(pe0 + slot_off, w);
                     if (p.mode == kModeSync) __threadfence();
-                    bool rel;              // the consumer across face f waits on this flag
-                    if constexpr (BATCH) {
-                        const long long qf = f ? btab[j - lo].right : btab[j - lo].left;
-                        rel = qf >= 0 && (qf < lo || qf >= hi || qf != j + (f ? 1 : -1));
-                    } else {
-                        rel = f ? j == hi - 1 : j == lo;
+                    if (prel && pub_ok) st_release(pflag, (unsigned long long)lev);
+                } else {
+                    // one group: lane 0 publishes both faces
+#pragma unroll
+                    for (int f = 0; f < 2; ++f) {
+                        T w[R];
+#pragma unroll
+                        for (int q = 0; q < R; ++q) w[q] = f ? rb[q] : cd[0][q];
+                        st_entry<T, R>(pe0 + f * kRingEntry + slot_off, w);
+                        if (p.mode == kModeSync) __threadfence();
+                        if ((f ? prel1 : prel) && pub_ok) st_release(pflag + f, (unsigned long long)lev);
                     }
-                    if (rel && pub_ok) st_release(p.flag + j * 2 + f, (unsigned long long)lev);
                 }
             }
         };

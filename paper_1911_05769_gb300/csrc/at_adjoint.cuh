@@ -19,7 +19,7 @@
 // are scattered into a pending ring [slot][P][2][R] by the one thread that owns
 // the reading face (one writer per slot entry and step) and collected, then
 // cleared, when the sweep reaches that level.  No atomics; dJ/dnu is summed
-// per block in FP64.  Blocks walk the subdomains, one thread per point; the
+// per block in FP64.  Blocks walk the subdomains, 4 points per thread; the
 // word offsets of the levels read are computed on the host.
 #pragma once
 

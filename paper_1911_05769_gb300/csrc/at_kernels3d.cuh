@@ -11,10 +11,12 @@
 // plane (an m0 x m1 box) is brought into one of `stages` shared-memory buffers
 // by one TMA tensor copy (3D tensor map over the state; completion counted on
 // the stage's mbarrier), several planes ahead; the last warp to finish with a
-// stage (a shared counter per stage) refills it.  A thread owns up to TC groups of VW consecutive (x, y)
-// columns; it keeps the values of its columns at planes z-1, z in registers,
-// reads the plane z+1 and the y neighbours as VW-word vectors and the two x
-// neighbours beyond its group as single words from shared memory.
+// stage (a shared counter per stage) refills it.  A thread owns up to TC
+// groups of VW consecutive (x, y) columns; it keeps the values of its columns
+// at planes z-1, z in registers, reads the plane z+1 and the y neighbours as
+// VW-word vectors, and the two x neighbours beyond a group by warp shuffles
+// (VW = 4) or as single words from shared memory (VW = 1).  The halo planes
+// of a tile are staged once at its start, face by face, one warp per face.
 // Neighbours across a subdomain face come from the ring of face planes:
 // entry [slot][subdomain][face] holds the face's boundary values at level
 // slot (faces 0/1: the x = 0 / x = m0-1 planes indexed [z][y]; 2/3: y planes
@@ -294,7 +296,7 @@ __global__ void __launch_bounds__(NT, NT == kThreads3 ? AT_MIN_CTAS_3D : 2 * AT_
     if (tid == 0)
         for (int st = 0; st < NS && st < Q; ++st) issue_plane(st, tx0, ty0, tz0 + st);
     // a failed wait is recorded in s_flag; every thread acts on it at the
-    // next CTA barrier (one per tile), so control flow stays uniform there.
+    // next CTA barrier (at a tile start), so control flow stays uniform there.
     // Planes are consumed in order: gs, gp are the stage and fill parity of
     // the current plane g (running counters: no division per plane).
     int gs = 0;
@@ -320,7 +322,7 @@ __global__ void __launch_bounds__(NT, NT == kThreads3 ? AT_MIN_CTAS_3D : 2 * AT_
     T *rf[6];                                // ring entries of the new level of the current tile
     const long long n_tiles = p.n_steps * S;
     for (long long t = 0; t < n_tiles; ++t) {
-        // ---- tile start (one CTA barrier): release the previous tile's
+        // ---- tile start (two CTA barriers): release the previous tile's
         // flags, grid barrier (synchronous mode), delays, halos
         __syncthreads();
         if (*s_flag == -1) { ok = false; break; }

@@ -18,8 +18,9 @@
 // lambda^{n+1}_r d u^{n+1}_r / d v_{i-r}.  Reads of older levels (k + m >= 1)
 // are scattered into a pending ring [slot][P][2][R] by the one thread that owns
 // the reading face (one writer per slot entry and step) and collected, then
-// cleared, when the sweep reaches that level.  No atomics; dJ/dnu is summed
-// per block in FP64.  Blocks walk the subdomains, 4 points per thread; the
+// cleared, when the sweep reaches that level (no atomics there); dJ/dnu is
+// summed per block in FP64 and added into the block's own slot (one add per
+// block and launch, so the sum's order is fixed).  Blocks walk the subdomains, 4 points per thread; the
 // word offsets of the levels read are computed on the host.
 #pragma once
 

@@ -127,6 +127,7 @@ int check_args3(const at_grid *g, int64_t P, int order, int L, Dims3 *d)
     if ((int64_t)d->m[0] * d->m[1] > 1024) return fail(AT_ERR_ARG, "sub[0] * sub[1] must be <= 1024");
     if (d->m[1] < 2 || d->m[2] < 3) return fail(AT_ERR_ARG, "sub[1] >= 2 and sub[2] >= 3 are required");
     if (P != np) return fail(AT_ERR_ARG, "P=%lld differs from the %lld subdomains of the grid", (long long)P, (long long)np);
+    if (P >= (1LL << 31)) return fail(AT_ERR_ARG, "at most 2^31 - 1 subdomains (P=%lld)", (long long)P);
     int64_t fw = (int64_t)d->m[1] * d->m[2];
     if ((int64_t)d->m[0] * d->m[2] > fw) fw = (int64_t)d->m[0] * d->m[2];
     if ((int64_t)d->m[0] * d->m[1] > fw) fw = (int64_t)d->m[0] * d->m[1];

@@ -248,15 +248,16 @@ __global__ void __launch_bounds__(NT, NT == kThreads3 ? AT_MIN_CTAS_3D : 2 * AT_
 
     // word offset of the first point of subdomain `sub` in u
     const long long plane_words = p.n0 * p.n1;
+    // (subdomain indices in 32 bits: the host keeps P < 2^31, and a 64-bit
+    // division costs tens of instructions on every thread of a tile start)
+    const unsigned uP0 = (unsigned)p.P0, uP01 = (unsigned)(p.P0 * p.P1);
     auto tile_base = [&](long long sub) -> long long {
-        const long long q01 = p.P0 * p.P1;
-        const long long q2 = sub / q01, r = sub - q2 * q01, q1 = r / p.P0, q0 = r - q1 * p.P0;
-        return (q2 * m2) * plane_words + (q1 * m1) * p.n0 + q0 * m0;
+        const unsigned us = (unsigned)sub, q2 = us / uP01, r = us - q2 * uP01, q1 = r / uP0, q0 = r - q1 * uP0;
+        return ((long long)q2 * m2) * plane_words + ((long long)q1 * m1) * p.n0 + (long long)q0 * m0;
     };
     // element coordinates of the first point of subdomain `sub`
     auto tile_coords = [&](long long sub, int *x, int *y, int *z) {
-        const long long q01 = p.P0 * p.P1;
-        const long long q2 = sub / q01, r = sub - q2 * q01, q1 = r / p.P0, q0 = r - q1 * p.P0;
+        const unsigned us = (unsigned)sub, q2 = us / uP01, r = us - q2 * uP01, q1 = r / uP0, q0 = r - q1 * uP0;
         *x = (int)(q0 * m0); *y = (int)(q1 * m1); *z = (int)(q2 * m2);
     };
     // one plane of every field into stage st (lane 0 of the issuing warp)
@@ -333,7 +334,8 @@ __global__ void __launch_bounds__(NT, NT == kThreads3 ? AT_MIN_CTAS_3D : 2 * AT_
         if (p.mode == kModeSync && sub == lo && lv > lev0) {
             if (!grid_sync3(p, lv - lev0, s_flag)) { ok = false; break; }
         }
-        const long long s0 = sub % p.P0, s1 = (sub / p.P0) % p.P1, s2 = sub / (p.P0 * p.P1);
+        const unsigned us = (unsigned)sub, us2 = us / uP01, usr = us - us2 * uP01, us1 = usr / uP0;
+        const long long s0 = usr - us1 * uP0, s1 = us1, s2 = us2;
         const long long base = tile_base(sub);
 #pragma unroll
         for (int f = 0; f < 6; ++f) rf[f] = ring_entry<T>(p, lv + 1, sub, f);

@@ -272,6 +272,17 @@ def ensemble_config(args, at, torch, dev, stream):
     res["sync"] = run(at.AT_SYNC, "sync")
     res["speedup_free_over_sync"] = res["free"]["value"] / res["sync"]["value"]
     res["effective_one_pass_frac"] = res["free"]["value"] * 1e9 * 8 / (hbm_peak()[0] * 1e9)
+    # algorithmic bytes per update with passes of the launch's steps_per_pass
+    # (warps whose smallest L_j is lower take shorter passes and move more:
+    # this is the least the free-running arm can move)
+    spp = max(1, res["free"]["shape"]["steps_per_pass"])
+    w, R, s_lev = 4, order // 2, order // 2 + 1
+    bpu = (2 * w + 2 * R * s_lev * w / M) / spp + 2 * R * w / M
+    peak, src = hbm_peak()
+    res["roofline"] = {"bound": "hbm", "algorithmic_bytes_per_update": bpu,
+                       "achieved": res["free"]["value"] * bpu, "peak": peak, "unit": "GB/s",
+                       "frac": res["free"]["value"] * bpu / peak, "peak_source": src,
+                       "note": "per-tile latency bound (profiles/at_stepper_ensemble_f32_o2_m256.md)"}
     res["gpu_launches_per_replay"] = 1
     # FP32 error against the FP64 oracle after the full 5000 seeded steps, on
     # the four smallest instances and one mid-size one

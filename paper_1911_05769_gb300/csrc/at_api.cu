@@ -811,7 +811,7 @@ int at_get_info(const at_solver *h, at_info *info)
     // (3D: M is the points per subdomain, sub[0] sub[1] sub[2])
     info->N = h->N; info->P = h->P; info->M = h->M;
     info->order = h->order; info->L = h->L; info->R = h->R; info->s = h->s; info->T = h->T;
-    info->ctas = h->G; info->threads = atk::kThreads; info->stages = h->stages;
+    info->ctas = h->G; info->threads = h->dim == 3 ? h->nt3 : atk::kThreads; info->stages = h->stages;
     info->smem_bytes = h->smem; info->step = h->step; info->sm_count = h->sm_count;
     info->dtype = h->g.dtype; info->steps_per_pass = h->sb;
     info->viscous_fp64 = h->v64 ? 1 : 0;

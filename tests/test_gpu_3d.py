@@ -75,6 +75,8 @@ def test_seeded_3d_matches_oracle(dtype, n, sub, max_ctas):
     ref, hist = oracle.run3d(u0, P=P, L=L, nu=nu, dt=dt, n_steps=steps, delay_mode=oracle.SEEDED, seed=5)
     assert rel_linf(g["u"], ref) <= TOL[dtype]
     assert np.array_equal(g["hist"], hist)
+    # FP32 planes of 1024 points run in 128-thread CTAs of 4-column groups
+    assert g["info"].threads == (128 if dtype == "f32" and sub[0] * sub[1] == 1024 else 256)
 
 
 def test_sync_replay_and_free_3d():

@@ -125,7 +125,7 @@ typedef struct at_info {
   int32_t T;                /* ring slots (levels kept per boundary)               */
   int32_t ctas;             /* CTAs of the persistent kernel                       */
   int32_t threads;          /* threads per CTA                                     */
-  int32_t stages;           /* tile buffers per warp                               */
+  int32_t stages;           /* tile buffers per warp (3D: plane buffers per CTA)   */
   int64_t smem_bytes;       /* dynamic shared memory per CTA                       */
   int64_t step;             /* time level of the state (steps taken)               */
   int32_t sm_count;         /* SMs of the device                                   */

@@ -115,6 +115,19 @@ def test_workspace_bytes_and_validation(B):
     assert B.at_workspace_bytes(g, 16, 2, 2) == 0
 
 
+def test_3d_workspace_and_subdomain_count_limit(B):
+    """A 3D grid's workspace is sized on the host; more than 2^31 - 1
+    subdomains are refused (the kernel keeps subdomain indices in 32 bits)."""
+    g = _grid(B, dtype=B.AT_F32)
+    g.dim = 3
+    for a, (n, m) in enumerate([(64, 32), (64, 32), (32, 8)]):
+        g.n[a], g.sub[a], g.length[a] = n, m, 6.283185307179586
+    assert B.at_workspace_bytes(g, 2 * 2 * 4, 2, 2) > 0
+    for a, (n, m) in enumerate([(4 << 11, 4), (2 << 11, 2), (3 << 9, 3)]):
+        g.n[a], g.sub[a] = n, m
+    assert B.at_workspace_bytes(g, 1 << 31, 2, 2) == 0 and "2^31" in B.at_last_error()
+
+
 def test_create_rejects_bad_arguments_on_the_host(B):
     g = _grid(B)
     dx = 6.283185307179586 / 4096

@@ -148,6 +148,23 @@ class Clocks:
 
 
 # ---------------------------------------------------------------------------
+def max_over_ranks(pg, x: float, device) -> float:
+    """The largest x over the ranks of process group module `pg` (None: one
+    process); the job's time is its slowest rank's."""
+    if pg is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(ws: int, units_per_rank: float, seconds: float) -> float:
+    """Whole-job throughput in G units/s: every rank processes the same units
+    (weak scaling), the job takes the slowest rank's time."""
+    return ws * units_per_rank / seconds / 1e9
+
+
 def dist_setup(args):
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -597,12 +614,8 @@ def gpu_arm(args, ws, rank, local, pg):
         if pg is not None:
             pg.barrier()
 
-    def max_over_ranks(x):
-        if pg is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        return float(t.item())
+    def max_over_ranks_here(x):
+        return max_over_ranks(pg, x, dev)
 
     def timed_arm(mode, steps, warmup, time_steps, dtype=args.dtype, clocks=None):
         s = make(dtype, blocked=(mode == at.AT_FREE))
@@ -633,7 +646,7 @@ def gpu_arm(args, ws, rank, local, pg):
         hist, m1, m2 = s.delay_stats()
         final = s.state()
         s.close()
-        return dict(total_ms=max_over_ranks(tot), launch_ms=per, info=info, m1=m1, m2=m2, final=final, clocks=clk)
+        return dict(total_ms=max_over_ranks_here(tot), launch_ms=per, info=info, m1=m1, m2=m2, final=final, clocks=clk)
 
     clocks = Clocks(local)
     arms = args.arms.split(",")
@@ -643,7 +656,7 @@ def gpu_arm(args, ws, rank, local, pg):
 
     upd_per_step = N * S
     def gpts(r, steps=args.steps, per=upd_per_step):
-        return ws * per * steps / (r["total_ms"] * 1e-3) / 1e9
+        return whole_job_rate(ws, per * steps, r["total_ms"] * 1e-3)
 
     value = gpts(head)
     ms_per_step = head["total_ms"] / args.steps
@@ -730,14 +743,14 @@ def gpu_arm(args, ws, rank, local, pg):
                   at.at_state(s.h, host_out.data_ptr()))
             if any(rc):
                 raise RuntimeError(f"e2e: {rc} {at.at_last_error()}")
-        el = max_over_ranks(time.perf_counter() - t0)
+        el = max_over_ranks_here(time.perf_counter() - t0)
         s.close()
-        line["e2e"] = {"value": ws * upd_per_step * e2e_steps / el / 1e9, "unit": UNIT,
+        line["e2e"] = {"value": whole_job_rate(ws, upd_per_step * e2e_steps, el), "unit": UNIT,
                        "h2d_bytes_per_step": N * wbytes, "d2h_bytes_per_step": N * wbytes,
                        "steps": e2e_steps}
         # FP64 state (FP64 arithmetic) on the same workload, fewer time steps
         f64 = timed_arm(at.AT_FREE, 3, 2, max(1, S // 10), dtype="f64")
-        line["f64"] = {"value": ws * N * max(1, S // 10) * 3 / (f64["total_ms"] * 1e-3) / 1e9, "unit": UNIT,
+        line["f64"] = {"value": whole_job_rate(ws, N * max(1, S // 10) * 3, f64["total_ms"] * 1e-3), "unit": UNIT,
                        "time_steps_per_step": max(1, S // 10), "bound": "fp64 alu (see DESIGN)"}
         if rank == 0 and ws == 1:
             cb, ref, nsub, csteps = cpu_baseline(args, u0, dt, cfg)

@@ -35,11 +35,15 @@ BC_PERIODIC, BC_TANH = 0, 1
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle into ``oracle/libat_oracle.so`` (plain gcc)."""
+    """Compile the oracle into ``oracle/libat_oracle.so`` (plain gcc, with
+    OpenMP over subdomains where the compiler has it)."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".{os.getpid()}.tmp"
-        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math",
-                               "-std=c99", "-shared", "-fPIC", _SRC, "-o", tmp, "-lm"])
+        base = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-std=c99", "-shared", "-fPIC"]
+        try:
+            subprocess.check_call(base + ["-fopenmp", _SRC, "-o", tmp, "-lm"], stderr=subprocess.DEVNULL)
+        except subprocess.CalledProcessError:
+            subprocess.check_call(base + [_SRC, "-o", tmp, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -100,6 +104,8 @@ def lib():
             L.at_oracle_run3d_system.restype = ctypes.c_int
             L.at_oracle_run3d_system.argtypes = [ctypes.POINTER(Cfg3), ctypes.c_int, ctypes.c_void_p, ctypes.c_int64,
                                                  ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+            L.at_oracle_threads.restype = ctypes.c_int
+            L.at_oracle_threads.argtypes = [ctypes.c_int]
             L.at_oracle_cfg3_size.restype = ctypes.c_int64
             if L.at_oracle_cfg3_size() != ctypes.sizeof(Cfg3):
                 raise RuntimeError("oracle: 3D configuration struct layout mismatch")
@@ -108,6 +114,13 @@ def lib():
                 raise RuntimeError("oracle: configuration struct layout mismatch")
             _lib = L
     return _lib
+
+
+def threads(n: int = 0) -> int:
+    """Sets the oracle's thread count (n > 0) and returns the count in force.
+    Results do not depend on it: the threads share out whole subdomains (1D)
+    or planes (3D), and every point is computed by the same arithmetic."""
+    return int(lib().at_oracle_threads(int(n)))
 
 
 def _dptr(a):

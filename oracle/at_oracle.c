@@ -43,6 +43,10 @@
 #include <stdlib.h>
 #include <string.h>
 
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
 #define ORC_OK 0
 #define ORC_EARG (-1)
 #define ORC_ENOMEM (-2)
@@ -198,15 +202,16 @@ int at_oracle_run(const at_oracle_cfg *c, int64_t n_steps, const int8_t *replay,
     memcpy(H, u0, (size_t)W * sizeof(double));
     if (hist) memset(hist, 0, (size_t)(c->L + 1) * sizeof(int64_t));
 
-    double v[5], lev[4];
+    int *K = (int *)malloc((size_t)c->p_count * 2 * sizeof(int));
+    if (!K) { free(H); return ORC_ENOMEM; }
     for (int64_t n = 0; n < n_steps; ++n) {
         const double *cur = H + (size_t)(n % depth) * W;
         double *nxt = H + (size_t)((n + 1) % depth) * W;
         const double tn = (double)n * c->dt;
+        /* delays of the two faces of every subdomain at this level
+         * (0: left neighbour p-1, 1: right p+1) */
         for (int64_t pl = 0; pl < c->p_count; ++pl) {
             const int64_t pg = (c->p_lo + pl) % c->P;   /* windows wrap */
-            /* delays of the two faces (0: left neighbour p-1, 1: right p+1) */
-            int k[2];
             for (int f = 0; f < 2; ++f) {
                 int kr = 0;
                 if (c->delay_mode == 1)
@@ -214,13 +219,24 @@ int at_oracle_run(const at_oracle_cfg *c, int64_t n_steps, const int8_t *replay,
                                                 c->per_subdomain ? 0 : f, 2, c->L);
                 else if (c->delay_mode == 2)
                     kr = replay[((size_t)n * c->p_count + pl) * 2 + f];
-                if (kr < 0 || kr > c->L) { free(H); return ORC_EDELAY; }
+                if (kr < 0 || kr > c->L) { free(H); free(K); return ORC_EDELAY; }
                 /* start-up: never read a level below 0 */
                 int64_t kmax = n - s + 1; if (kmax < 0) kmax = 0;
-                k[f] = (kr < kmax) ? kr : (int)kmax;
-                if (hist) hist[k[f]] += 1;
-                if (k_used) k_used[((size_t)n * c->p_count + pl) * 2 + f] = (int8_t)k[f];
+                K[pl * 2 + f] = (kr < kmax) ? kr : (int)kmax;
+                if (hist) hist[K[pl * 2 + f]] += 1;
+                if (k_used) k_used[((size_t)n * c->p_count + pl) * 2 + f] = (int8_t)K[pl * 2 + f];
             }
+        }
+        /* the points of every subdomain (independent of one another: the
+         * subdomains may be taken by several threads, each point's arithmetic
+         * is the same whatever the thread count) */
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static)
+#endif
+        for (int64_t pl = 0; pl < c->p_count; ++pl) {
+            const int64_t pg = (c->p_lo + pl) % c->P;
+            const int *k = K + pl * 2;
+            double v[5], lev[4];
             for (int64_t m = 0; m < M; ++m) {
                 const int64_t il = pl * M + m;   /* index in the window */
                 const int64_t ig = pg * M + m;   /* index in the domain */
@@ -255,9 +271,25 @@ int at_oracle_run(const at_oracle_cfg *c, int64_t n_steps, const int8_t *replay,
             }
         }
     }
+    free(K);
     memcpy(u_out, H + (size_t)(n_steps % depth) * W, (size_t)W * sizeof(double));
     free(H);
     return ORC_OK;
+}
+
+/* Threads the point loops of the runs use (OpenMP over subdomains / planes;
+ * every point's arithmetic is the same whatever the count, so results do not
+ * depend on it).  n <= 0 leaves the setting alone.  Returns the count now in
+ * force (1 when the oracle was built without OpenMP). */
+int at_oracle_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
 }
 
 /* Size of the configuration struct, so the caller can check its layout. */
@@ -460,6 +492,9 @@ int at_oracle_run3d(const at_oracle_cfg3 *c, int64_t n_steps, const int8_t *repl
                 if (hist) hist[K[p * 6 + f]] += 1;
             }
         }
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static)
+#endif
         for (int64_t k = 0; k < n2; ++k)
             for (int64_t j = 0; j < n1; ++j)
                 for (int64_t i = 0; i < n0; ++i) {
@@ -544,6 +579,9 @@ int at_oracle_run3d_system(const at_oracle_cfg3 *c, int nf, const double *kappa,
                 if (hist) hist[K[p * 6 + f]] += 1;
             }
         }
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static)
+#endif
         for (int64_t k = 0; k < n2; ++k)
             for (int64_t j = 0; j < n1; ++j)
                 for (int64_t i = 0; i < n0; ++i) {

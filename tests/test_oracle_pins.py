@@ -244,6 +244,71 @@ def test_oracle_matches_brute_force_eq_at1_at2(P, L):
     assert hist[1:].sum() > 0
 
 
+# --------------------------------------------------------------------------
+# Brute force: the order-4 AT scheme (reading c2), dense history
+# --------------------------------------------------------------------------
+def _brute_force_order4(u0, P, L, nu, dt, dx, delays, n_steps, A=0.0, x0=0.0):
+    """Independent restatement of the fourth-order AT run: every halo value
+    across a face is the quadratic Lagrange extrapolation in time of the
+    neighbour's levels n-k, n-k-1, n-k-2 to level n, weights
+    ((k+1)(k+2)/2, -k(k+2), k(k+1)/2); both halo points of a face (offsets
+    1 and 2 beyond the subdomain) take that face's delay.  Delays are clamped
+    to max(0, n - 2) so that no level below 0 is read (Algorithm 2 start-up).
+    Then the five-point central differences for f_x and f_xx, the right-hand
+    side -u f_x + nu f_xx + A sin x of Eq. BS (forced), forward Euler."""
+    N = len(u0)
+    M = N // P
+    hist = [list(map(float, u0))]
+    for n in range(n_steps):
+        u = hist[n]
+        new = [0.0] * N
+        for p in range(P):
+            k_face = [min(int(delays[n, p, f]), max(0, n - 2)) for f in (0, 1)]
+            for m in range(M):
+                i = p * M + m
+                v = {}
+                for j in (-2, -1, 0, 1, 2):
+                    q = i + j
+                    inside = p * M <= q < (p + 1) * M
+                    qq = q % N
+                    if inside:
+                        v[j] = u[qq]
+                        continue
+                    k = k_face[0] if q < p * M else k_face[1]
+                    lev = [hist[n - k - mm][qq] if n - k - mm >= 0 else 0.0 for mm in range(3)]
+                    w0 = (k + 1) * (k + 2) / 2.0
+                    w1 = -k * (k + 2.0)
+                    w2 = k * (k + 1) / 2.0
+                    v[j] = w0 * lev[0] + w1 * lev[1] + w2 * lev[2]
+                fx = (-v[2] + 8.0 * v[1] - 8.0 * v[-1] + v[-2]) / (12.0 * dx)
+                fxx = (-v[2] + 16.0 * v[1] - 30.0 * v[0] + 16.0 * v[-1] - v[-2]) / (12.0 * dx * dx)
+                x = x0 + i * dx
+                new[i] = u[i] + dt * (-v[0] * fx + nu * fxx + A * math.sin(x))
+        hist.append(new)
+    return np.array(hist[-1])
+
+
+@pytest.mark.parametrize("P,L,M,A", [(6, 2, 8, 0.0), (4, 3, 12, 0.1), (8, 1, 4, 0.1), (3, 3, 16, 0.0)])
+def test_oracle_order4_matches_brute_force_dense_history(P, L, M, A):
+    """The order-4 delayed run as a whole (the scheme of the 2^26-point
+    workload): replayed random delays, every face, start-up clamp, forcing;
+    M = 4 puts both halo points of a face in the neighbour's first/last two."""
+    N = P * M
+    x, dx = W.grid(N)
+    u0 = np.sin(x) + 0.4 * np.cos(2 * x + 0.3) + 0.1 * np.sin(5 * x + 1.0)
+    nu = 0.05
+    dt = W.dt_rule(u0, dx, nu)
+    n_steps = 30
+    delays = W.random_delays(n_steps, P, L, seed=P * 1000 + L * 10 + M)
+    bf = _brute_force_order4(u0, P, L, nu, dt, dx, delays, n_steps, A=A)
+    u, hist = oracle.run(u0, P=P, order=4, L=L, nu=nu, dt=dt, n_steps=n_steps, forcing_amp=A,
+                         delay_mode=oracle.REPLAY, replay=delays)
+    assert np.max(np.abs(u - bf)) <= 1e-13 * np.max(np.abs(bf))
+    assert hist.sum() == n_steps * P * 2
+    # the delays were exercised, up to the bound (k >= 2 weights the third level)
+    assert hist[1:].sum() > 0 and hist[L] > 0
+
+
 def test_k0_is_bitwise_synchronous():
     """Sec. 3.2: with every delay 0 the AT run is the synchronous run,
     bit for bit (replayed zeros, and seeded delays with L = 0)."""

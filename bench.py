@@ -299,7 +299,7 @@ def ensemble_config(args, at, torch, dev, stream):
     res["roofline"] = {"bound": "hbm", "algorithmic_bytes_per_update": bpu,
                        "achieved": res["free"]["value"] * bpu, "peak": peak, "unit": "GB/s",
                        "frac": res["free"]["value"] * bpu / peak, "peak_source": src,
-                       "note": "per-tile latency bound (profiles/at_stepper_ensemble_f32_o2_m256.md)"}
+                       "note": "bound by per-tile latency and control instructions, not by HBM"}
     res["gpu_launches_per_replay"] = 1
     # FP32 error against the FP64 oracle after the full 5000 seeded steps, on
     # the four smallest instances and one mid-size one

@@ -376,12 +376,26 @@ int at_adjoint(at_solver *h, int64_t n_steps, int delay_mode, const int8_t *dela
  * last call left in it; each call clears the parts that must start at zero
  * before it launches.  Calls whose work overlaps on the same GPU (other
  * streams, other host threads) race on the array and corrupt each other's
- * results: issue them one after another.  The call waits for its stream
- * before it returns, and returns the device status (AT_OK or AT_ERR_TIMEOUT).
+ * results: issue them one after another.
  *
- * Set-up.  The first call on each device looks up the device address of the
- * array (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture begins on the device. */
+ * Levels per pass.  One level per pass (no temporal blocking):
+ * grid->steps_per_pass must be 0 or 1, else AT_ERR_ARG.  No compensated
+ * state (AT_FLAG_COMPENSATED gives AT_ERR_ARG).
+ *
+ * Returns.  The call synchronises its stream (it reads the device status
+ * after the run) and returns
+ *   AT_OK;
+ *   AT_ERR_ARG       bad arguments, as at_create and at_step, or a problem too
+ *                    large for the array, or steps_per_pass > 1;
+ *   AT_ERR_UNSTABLE  nu dt / dx^2 above the order's limit (as at_create);
+ *   AT_ERR_RESIDENCY the CTAs cannot be co-resident, or no cooperative launch;
+ *   AT_ERR_CUDA      a CUDA call failed (message from at_last_error());
+ *   AT_ERR_TIMEOUT   a device wait expired.
+ *
+ * Set-up.  Every call looks up the device address of the array
+ * (cudaGetSymbolAddress) with the calling thread's current device; the first
+ * call on a device also loads this library's device code there, so make that
+ * first call before any stream capture begins on the device. */
 int at_step_noalloc(const at_grid *grid, int64_t P, int scheme_order, int L,
                     double nu, double dt, void *u, int64_t n_steps,
                     int delay_mode, int8_t *delays);

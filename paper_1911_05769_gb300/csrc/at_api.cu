@@ -1297,30 +1297,22 @@ int at_adjoint(at_solver *h, int64_t n_steps, int delay_mode, const int8_t *dela
 // exits.  The caller still passes the state (input and output) and, if used,
 // the delay array.
 // ---------------------------------------------------------------------------
-#include <mutex>
-
 namespace {
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[AT_NOALLOC_SCRATCH_BYTES];
 
-constexpr int kNoallocMaxDevices = 64;
-std::mutex g_noalloc_mutex;
-unsigned char *g_noalloc_addr[kNoallocMaxDevices] = {};
-
-// Device address of the scratch array on device `dev` (which must be the
-// current device).  In host code the array's name is only a host-side
-// stand-in, so the address is looked up once per device and cached.
-int noalloc_scratch_address(int dev, unsigned char **out)
+// Device address of the scratch array in the current device's context.  In
+// host code the array's name is only a host-side stand-in, so the address is
+// looked up with the device current -- on every call, not cached: after a
+// context is torn down and created again (cudaDeviceReset, a primary-context
+// reset) the module is loaded anew and the array may sit elsewhere, and a
+// cached address would then point into memory that is no longer the array.
+int noalloc_scratch_address(unsigned char **out)
 {
-    if (dev < 0 || dev >= kNoallocMaxDevices) return fail(AT_ERR_ARG, "device ordinal %d not supported", dev);
-    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-    if (!g_noalloc_addr[dev]) {
-        void *ptr = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(scratch array)");
-        g_noalloc_addr[dev] = static_cast<unsigned char *>(ptr);
-    }
-    *out = g_noalloc_addr[dev];
+    void *ptr = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(scratch array)");
+    *out = static_cast<unsigned char *>(ptr);
     return AT_OK;
 }
 
@@ -1340,6 +1332,10 @@ extern "C" int at_step_noalloc(const at_grid *grid, int64_t P, int scheme_order,
     if (n_steps < 0) return fail(AT_ERR_ARG, "n_steps < 0");
     if (delay_mode < AT_SYNC || delay_mode > AT_REPLAY) return fail(AT_ERR_ARG, "bad delay_mode %d", delay_mode);
     if (delay_mode == AT_REPLAY && !delays) return fail(AT_ERR_ARG, "AT_REPLAY needs a delays array");
+    if (grid->steps_per_pass > 1)
+        return fail(AT_ERR_ARG, "at_step_noalloc runs one level per pass (steps_per_pass must be 0 or 1, got %d)",
+                    grid->steps_per_pass);
+    if (grid->flags & AT_FLAG_COMPENSATED) return fail(AT_ERR_ARG, "at_step_noalloc has no compensated state");
     const int64_t N = grid->n[0];
     const double dx = grid->length[0] / (double)N;
     const double lim = scheme_order == 2 ? 0.5 : 0.375;
@@ -1363,7 +1359,7 @@ extern "C" int at_step_noalloc(const at_grid *grid, int64_t P, int scheme_order,
     cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (!coop) return fail(AT_ERR_RESIDENCY, "device does not support cooperative launch");
     unsigned char *scratch = nullptr;
-    rc = noalloc_scratch_address(dev, &scratch);
+    rc = noalloc_scratch_address(&scratch);
     if (rc != AT_OK) return rc;
 
     at_solver h{};   // on the stack: nothing is allocated, on the host or on the device
@@ -1377,7 +1373,6 @@ extern "C" int at_step_noalloc(const at_grid *grid, int64_t P, int scheme_order,
     h.stream = static_cast<cudaStream_t>(grid->stream);
     h.device = dev; h.sm_count = sms; h.smem_optin = smem_optin;
     h.batch = false; h.n_inst = 0; h.lmin = L;
-    if (grid->flags & AT_FLAG_COMPENSATED) return fail(AT_ERR_ARG, "at_step_noalloc has no compensated state");
     h.comp = false;
     h.v64 = viscous_fp64(w, scheme_order, (uint32_t)grid->flags, nu * dt / (dx * dx));
     pick_kernels(w, scheme_order, h.M, grid->forcing_amp != 0.0, h.v64, false, &h.kernel, &h.init_kernel);

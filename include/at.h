@@ -78,12 +78,17 @@ extern "C" {
                                           update).  Chosen automatically when
                                           nu dt / dx^2 >= 0.8 x the stability limit */
 #define AT_FLAG_VISCOUS_FP32       16  /* FP32 state: never use FP64 for it */
-#define AT_FLAG_COMPENSATED        32  /* FP32 state (1D single domain): keep the
-                                          rounding error of every stored value in a
-                                          second FP32 word and add each update with an
-                                          error-free two-sum, so that increments far
-                                          below an ulp are not lost; doubles the state
-                                          memory and traffic; not with the adjoint,
+#define AT_FLAG_COMPENSATED        32  /* FP32 state (1D: single domain and
+                                          ensembles): every value is a pair hi + lo
+                                          of FP32 words (lo: the rounding error of
+                                          hi); stencil differences and halo values
+                                          are formed word by word, ring entries carry
+                                          both words, and each update is added with
+                                          an error-free two-sum, so that neither
+                                          increments far below an ulp nor the
+                                          quantisation of the stored field are lost;
+                                          doubles the state memory and traffic;
+                                          at_state returns hi; not with the adjoint,
                                           at_set_history or at_step_noalloc */
 
 typedef struct at_solver at_solver;   /* opaque handle */
@@ -173,6 +178,14 @@ int at_step(at_solver *h, int64_t n_steps, int delay_mode, int8_t *delays);
 /* Copies the state (N words) to dst (host or device memory), waits for the
  * stream and returns the device status: AT_OK or AT_ERR_TIMEOUT. */
 int at_state(at_solver *h, void *dst);
+
+/* Compensated state (AT_FLAG_COMPENSATED) only: copies the N lo words -- the
+ * rounding errors of the words at_state() returns, so that hi + lo is the
+ * value the solver carries -- to dst (host or device memory), waits for the
+ * stream and returns the device status.  AT_ERR_ARG without a compensated
+ * state.  (An extension of at_state for the precision variant; the paper
+ * has no counterpart.) */
+int at_state_error(at_solver *h, void *dst);
 
 /* Waits for the stream and returns the device status. */
 int at_status(at_solver *h);

@@ -93,6 +93,7 @@ _SIGNATURES = [
     ("at_set_state", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     ("at_step", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p]),
     ("at_state", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    ("at_state_error", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     ("at_status", ctypes.c_int, [ctypes.c_void_p]),
     ("at_delay_stats", ctypes.c_int,
      [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double),
@@ -178,6 +179,10 @@ def at_step(h, n_steps: int, delay_mode: int, delays_ptr: int | None = None) -> 
 
 def at_state(h, dst_ptr: int) -> int:
     return lib().at_state(h, ctypes.c_void_p(dst_ptr))
+
+
+def at_state_error(h, dst_ptr: int) -> int:
+    return lib().at_state_error(h, ctypes.c_void_p(dst_ptr))
 
 
 def at_status(h) -> int:

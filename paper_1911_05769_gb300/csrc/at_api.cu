@@ -29,6 +29,7 @@ void *atk_init_kernel_f32(int order);
 void *atk_init_kernel_f64(int order);
 void *atk_batch_kernel_f32(int order, int gw, bool full);
 void *atk_batch_kernel_f64(int order, int gw, bool full);
+void *atk_batch_kernel_f32c(int order, int gw, bool full);
 void *atk_restore_kernel_f32(int order);
 void *atk_restore_kernel_f64(int order);
 void *atk_adjoint_kernel(int w, int order);
@@ -224,7 +225,7 @@ struct TabSize {
 
 TabSize tab_size(int64_t M, int w, bool forced, bool batch, bool comp = false)
 {
-    if (batch) return {0, (long long)sizeof(atk::BatchSub), false};
+    if (batch) return {0, (long long)sizeof(atk::BatchSub), comp};
     if (forced) return {2LL * M * w, 2LL * w, comp};
     return {0, 0, comp};
 }
@@ -776,6 +777,17 @@ int at_state(at_solver *h, void *dst)
     return read_status(h);
 }
 
+int at_state_error(at_solver *h, void *dst)
+{
+    g_err[0] = 0;
+    if (!h || !dst) return fail(AT_ERR_ARG, "NULL argument");
+    if (!h->comp) return fail(AT_ERR_ARG, "at_state_error needs a compensated state (AT_FLAG_COMPENSATED)");
+    if (!h->has_state) return fail(AT_ERR_STATE, "at_state_error before at_set_state");
+    cudaError_t e = cudaMemcpyAsync(dst, h->ws + h->lay.ur, (size_t)h->N * h->w, cudaMemcpyDefault, h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(error words out)");
+    return read_status(h);
+}
+
 int at_status(at_solver *h)
 {
     g_err[0] = 0;
@@ -901,7 +913,7 @@ size_t at_batch_workspace_bytes(const at_grid *grid, int64_t n_inst, const at_in
     if (check_batch(grid, n_inst, inst, M, scheme_order, &d) != AT_OK) return 0;
     const int w = grid->dtype == AT_F64 ? 8 : 4;
     const int s = scheme_order / 2 + 1;
-    return layout(d.N, d.P, w, d.Lmax, ring_slots(d.Lmax, s), n_inst).total;
+    return layout(d.N, d.P, w, d.Lmax, ring_slots(d.Lmax, s), n_inst, (grid->flags & AT_FLAG_COMPENSATED) != 0).total;
 }
 
 int at_create_batch(const at_grid *grid, int64_t n_inst, const at_instance *inst, int64_t M, int scheme_order,
@@ -916,7 +928,9 @@ int at_create_batch(const at_grid *grid, int64_t n_inst, const at_instance *inst
     const int w = grid->dtype == AT_F64 ? 8 : 4;
     const int s = scheme_order / 2 + 1;
     const int T = ring_slots(d.Lmax, s);
-    const Layout lay = layout(d.N, d.P, w, d.Lmax, T, n_inst);
+    const bool comp = (grid->flags & AT_FLAG_COMPENSATED) != 0;
+    if (comp && w != 4) return fail(AT_ERR_ARG, "AT_FLAG_COMPENSATED needs FP32 state");
+    const Layout lay = layout(d.N, d.P, w, d.Lmax, T, n_inst, comp);
     if (!grid->workspace) return fail(AT_ERR_ARG, "workspace is NULL");
     if (grid->workspace_bytes < lay.total)
         return fail(AT_ERR_ARG, "workspace too small: %zu < %zu", grid->workspace_bytes, lay.total);
@@ -987,11 +1001,14 @@ int at_create_batch(const at_grid *grid, int64_t n_inst, const at_instance *inst
     h->batch = true; h->n_inst = n_inst; h->lmin = d.Lmin;
     const int gw = groups_per_lane(M);
     const bool full = (M == 128LL * gw);
-    h->kernel = w == 8 ? atk_batch_kernel_f64(scheme_order, gw, full) : atk_batch_kernel_f32(scheme_order, gw, full);
+    h->comp = comp;
+    h->kernel = w == 8 ? atk_batch_kernel_f64(scheme_order, gw, full)
+                : comp ? atk_batch_kernel_f32c(scheme_order, gw, full)
+                       : atk_batch_kernel_f32(scheme_order, gw, full);
     h->init_kernel = w == 8 ? atk_init_kernel_f64(scheme_order) : atk_init_kernel_f32(scheme_order);
     int stages = grid->stages > 0 ? grid->stages : 3;
     if (stages < atk::kMinStages) stages = atk::kMinStages;
-    rc = launch_shape(M, w, d.P, tab_size(M, w, false, true), grid->max_ctas, stages, sms, smem_optin, h->kernel,
+    rc = launch_shape(M, w, d.P, tab_size(M, w, false, true, comp), grid->max_ctas, stages, sms, smem_optin, h->kernel,
                       &h->G, &h->stages, &h->sl, &h->smem, &h->smax);
     if (rc != AT_OK) { delete h; return rc; }
     h->sb = grid->steps_per_pass > 0 ? grid->steps_per_pass : 1;

@@ -273,6 +273,39 @@ __device__ __forceinline__ T approx_halo(const unsigned char *raw, int k, int r)
     }
 }
 
+// Compensated state (PREC 2: a value is the pair hi + lo of FP32 words; ring
+// entries hold the R hi words, then the R lo words): the halo value's hi word
+// is the newest delayed level's hi word f0, and its lo word carries the rest
+// of the same extrapolation in Newton form, f0 + k d1 (+ k(k+1)/2 d2 for
+// s = 3), the backward differences d1, d2 formed word by word (differences of
+// nearby hi words are exact), so that no part of the value is lost to the
+// rounding of a single FP32 word.
+template <typename T, int S_LEV, int R>
+__device__ __forceinline__ T approx_halo_lo(const unsigned char *raw, int k, int r)
+{
+    const T *e0 = reinterpret_cast<const T *>(raw);
+    const T h0 = e0[r], l0 = e0[R + r];
+    if (k == 0) return l0;
+    const T *e1 = reinterpret_cast<const T *>(raw + kRingEntry);
+    const T h1 = e1[r], l1 = e1[R + r];
+    const T d1 = (h0 - h1) + (l0 - l1);
+    if constexpr (S_LEV == 2) {
+        return l0 + (T)k * d1;
+    } else {
+        const T *e2 = reinterpret_cast<const T *>(raw + 2 * kRingEntry);
+        const T h2 = e2[r], l2 = e2[R + r];
+        const T d2 = ((h0 - h1) - (h1 - h2)) + ((l0 - l1) - (l1 - l2));
+        return l0 + (T)k * d1 + (T)(k * (k + 1) / 2) * d2;
+    }
+}
+
+// One 16-byte ring entry of a compensated FP32 state: R hi words, R lo words.
+template <int R>
+__device__ __forceinline__ void st_entry2(unsigned char *e, const float *h, const float *l)
+{
+    if constexpr (R == 2) st_cg16(e, h[0], h[1], l[0], l[1]);
+    else st_cg16(e, h[0], l[0], 0.0f, 0.0f);
+}
 
 // Waits (lane 0) for the bulk copy into a stage; bounded.
 static __device__ __noinline__ bool wait_stage(const Params &p, uint64_t *bar, unsigned parity)
@@ -383,15 +416,33 @@ __device__ __forceinline__ void advance(const Sweep &sw, Cursor &c, long long lo
 
 // Exact boundary value of an ensemble instance (travelling tanh wave) at
 // point `q` of the halo across face f of subdomain record b, at level lev.
-template <typename T, int R>
-static __device__ __noinline__ T exact_ghost(const BatchInst *binst, const BatchSub &b, long long M, int f, int q,
-                                             long long lev)
+template <int R>
+static __device__ __noinline__ double exact_ghost64(const BatchInst *binst, const BatchSub &b, long long M, int f,
+                                                    int q, long long lev)
 {
     const BatchInst &bi = binst[b.inst];
     const long long gi = f ? ((long long)b.lp + 1) * M + q : (long long)b.lp * M - R + q;
     const double x = bi.x0 + (double)gi * bi.dx;
     const double t = (double)lev * bi.dt;
-    return (T)(bi.tc - bi.ta * tanh(bi.ta * (x - bi.txc - bi.tc * t) / (2.0 * bi.nu)));
+    return bi.tc - bi.ta * tanh(bi.ta * (x - bi.txc - bi.tc * t) / (2.0 * bi.nu));
+}
+
+template <typename T, int R>
+__device__ __forceinline__ T exact_ghost(const BatchInst *binst, const BatchSub &b, long long M, int f, int q,
+                                         long long lev)
+{
+    return (T)exact_ghost64<R>(binst, b, M, f, q, lev);
+}
+
+// The exact boundary value as a hi + lo pair of words (compensated state).
+template <typename T, int R>
+__device__ __forceinline__ T exact_ghost2(const BatchInst *binst, const BatchSub &b, long long M, int f, int q,
+                                          long long lev, T &lo)
+{
+    const double g = exact_ghost64<R>(binst, b, M, f, q, lev);
+    const T hi = (T)g;
+    lo = (T)(g - (double)hi);
+    return hi;
 }
 
 // ---------------------------------------------------------------------------
@@ -413,10 +464,13 @@ static __device__ __noinline__ T exact_ghost(const BatchInst *binst, const Batch
 // PREC (FP32 state only) 1: the viscous term nu dt D2(u) is formed from the
 // stencil values in FP64 and added to u in FP64, rounded to FP32 once per
 // update (for runs close to the diffusive stability limit).  2: compensated
-// state: every point also keeps the rounding error of its stored value (a
-// second FP32 word, array p.ur); each update adds the increment and that
-// word with an error-free two-sum (Knuth), keeping the new error for the next
-// step, so that small increments are not lost to rounding.
+// state: every point is the pair hi + lo of FP32 words (lo: array p.ur, the
+// rounding error of hi); the stencil differences are formed word by word
+// (differences of nearby hi words are exact, those of the lo words small),
+// the halo values and ring entries carry both words, and each update adds
+// the increment and lo to hi with an error-free two-sum (Knuth), keeping the
+// new error as lo -- so that neither small increments nor the quantisation
+// of the stored field are lost to FP32 rounding.
 template <typename T, int ORDER, int GW, bool FORCED, bool FULL, bool BATCH, int PREC>
 __device__ void run_pe(const Params &p, const Sweep &sw, long long lo, long long hi, uint64_t *bars, unsigned *hist,
                        unsigned char *raw, unsigned char *stages, const T *sj, const T *cj, const T *spt,
@@ -692,13 +746,24 @@ __device__ void run_pe(const Params &p, const Sweep &sw, long long lo, long long
         // x < 2 R len computes one of them once per tile; each level then
         // takes its 2R values by shuffle
         const bool hv_lanes = 2 * R * len <= 32;
-        T hv = (T)0;
+        T hv = (T)0, hvl = (T)0;       // (hvl: lo word of a compensated state)
         if (hv_lanes && lane < 2 * R * len) {
             const int f = lane / (R * len), rem = lane % (R * len);
-            if (BATCH && (f ? bnd1 : bnd0))
-                hv = exact_ghost<T, R>(p.binst, btab[j - lo], p.M, f, rem % R, n + rem / R);
-            else
-                hv = approx_halo<T, S_LEV>(rw + f * kMaxS * kRingEntry, (f ? k1cur : k0cur) + rem / R, rem % R);
+            const unsigned char *rf = rw + f * kMaxS * kRingEntry;
+            const int kf = (f ? k1cur : k0cur) + rem / R;
+            if constexpr (PREC == 2) {
+                if (BATCH && (f ? bnd1 : bnd0)) {
+                    hv = exact_ghost2<T, R>(p.binst, btab[j - lo], p.M, f, rem % R, n + rem / R, hvl);
+                } else {
+                    hv = reinterpret_cast<const T *>(rf)[rem % R];
+                    hvl = approx_halo_lo<T, S_LEV, R>(rf, kf, rem % R);
+                }
+            } else {
+                if (BATCH && (f ? bnd1 : bnd0))
+                    hv = exact_ghost<T, R>(p.binst, btab[j - lo], p.M, f, rem % R, n + rem / R);
+                else
+                    hv = approx_halo<T, S_LEV>(rf, kf, rem % R);
+            }
         }
         // this lane's ring entry (slot 0) and flag of the face it publishes,
         // and whether the consumer across that face waits on the flag
@@ -721,11 +786,31 @@ __device__ void run_pe(const Params &p, const Sweep &sw, long long lo, long long
         auto level = [&](int i, T (&cs)[GW][4], T (&cd)[GW][4]) {
             const long long lev = n + i + 1;                 // level being computed
             T hl[R], hr[R];
+            T hll[R], hrl[R];                                // lo words (compensated state)
 #pragma unroll
             for (int q = 0; q < R; ++q) {
+                hll[q] = hrl[q] = (T)0;
                 if (hv_lanes) {
                     hl[q] = __shfl_sync(kAll, hv, i * R + q);
                     hr[q] = __shfl_sync(kAll, hv, R * len + i * R + q);
+                    if constexpr (PREC == 2) {
+                        hll[q] = __shfl_sync(kAll, hvl, i * R + q);
+                        hrl[q] = __shfl_sync(kAll, hvl, R * len + i * R + q);
+                    }
+                } else if constexpr (PREC == 2) {
+                    const unsigned char *rr = rw + kMaxS * kRingEntry;
+                    if (BATCH && bnd0) {
+                        hl[q] = exact_ghost2<T, R>(p.binst, btab[j - lo], p.M, 0, q, n + i, hll[q]);
+                    } else {
+                        hl[q] = reinterpret_cast<const T *>(rw)[q];
+                        hll[q] = approx_halo_lo<T, S_LEV, R>(rw, k0cur + i, q);
+                    }
+                    if (BATCH && bnd1) {
+                        hr[q] = exact_ghost2<T, R>(p.binst, btab[j - lo], p.M, 1, q, n + i, hrl[q]);
+                    } else {
+                        hr[q] = reinterpret_cast<const T *>(rr)[q];
+                        hrl[q] = approx_halo_lo<T, S_LEV, R>(rr, k1cur + i, q);
+                    }
                 } else {
                     hl[q] = (BATCH && bnd0) ? exact_ghost<T, R>(p.binst, btab[j - lo], p.M, 0, q, n + i)
                                             : approx_halo<T, S_LEV>(rw, k0cur + i, q);
@@ -736,10 +821,30 @@ __device__ void run_pe(const Params &p, const Sweep &sw, long long lo, long long
             // One point: w[0 .. 2R] are the values at offsets -R .. R (w[R] the
             // point itself), sv/cv the forcing table entries; returns the new
             // value (compensated state: updates the carried error too).
-            auto point = [&](const T *w, T sv, T cv, T &err) -> T {
+            auto point = [&](const T *w, const T *wl, T sv, T cv, T &err) -> T {
                 const T cc = w[R];
                 T a, b;
-                if constexpr (ORDER == 2) {
+                if constexpr (PREC == 2) {
+                    // differences word by word; the second difference as
+                    // differences from the centre point
+                    const T cl = wl[R];
+                    if constexpr (ORDER == 2) {
+                        a = (w[2] - w[0]) + (wl[2] - wl[0]);
+                        b = ((w[2] - cc) + (w[0] - cc)) + ((wl[2] - cl) + (wl[0] - cl));
+                    } else {
+                        a = ((T)8 * (w[3] - w[1]) - (w[4] - w[0])) + ((T)8 * (wl[3] - wl[1]) - (wl[4] - wl[0]));
+                        b = ((T)16 * ((w[3] - cc) + (w[1] - cc)) - ((w[4] - cc) + (w[0] - cc))) +
+                            ((T)16 * ((wl[3] - cl) + (wl[1] - cl)) - ((wl[4] - cl) + (wl[0] - cl)));
+                    }
+                    T du = cB * b - cA * (cc + cl) * a;
+                    if constexpr (FORCED) du = fs * cv + (fc * sv + du);
+                    // two-sum of hi and (du + lo): exact sum t + err
+                    const T y = du + err;
+                    const T t = cc + y;
+                    const T yy = t - cc;
+                    err = (cc - (t - yy)) + (y - yy);
+                    return t;
+                } else if constexpr (ORDER == 2) {
                     a = w[2] - w[0];
                     b = (w[2] + w[0]) - (T)2 * cc;
                 } else {
@@ -756,17 +861,10 @@ __device__ void run_pe(const Params &p, const Sweep &sw, long long lo, long long
                     T rest = -cA * cc * a;
                     if constexpr (FORCED) rest = fs * cv + (fc * sv + rest);
                     (void)b;
+                    (void)wl;
                     return (T)((double)cc + (cB64 * b64 + (double)rest));
-                } else if constexpr (PREC == 2) {
-                    T du = cB * b - cA * cc * a;
-                    if constexpr (FORCED) du = fs * cv + (fc * sv + du);
-                    // two-sum of cc and (du + carried error): exact sum s + err
-                    const T y = du + err;
-                    const T t = cc + y;
-                    const T yy = t - cc;
-                    err = (cc - (t - yy)) + (y - yy);
-                    return t;
                 } else {
+                    (void)wl;
                     T du = cB * b - cA * cc * a;
                     if constexpr (FORCED) du = fs * cv + (fc * sv + du);   // two fused multiply-adds
                     return cc + du;
@@ -776,30 +874,52 @@ __device__ void run_pe(const Params &p, const Sweep &sw, long long lo, long long
             // from the adjacent lanes (lane 0 / 31: the other end of the warp at
             // the previous / next m, or the halo)
             T tail[R], rb[R];                                // old last words of group m-1; new last words of NG-1
+            T tail_l[R], rb_l[R];                            // (the same for the lo words, PREC 2)
 #pragma unroll
-            for (int q = 0; q < R; ++q) { tail[q] = (T)0; rb[q] = (T)0; }
+            for (int q = 0; q < R; ++q) { tail[q] = (T)0; rb[q] = (T)0; tail_l[q] = (T)0; rb_l[q] = (T)0; }
 #pragma unroll
             for (int m = 0; m < GW; ++m) {
                 const int g = lane + 32 * m;
                 T v[4 + 2 * R];
+                T vl[PREC == 2 ? 4 + 2 * R : 1];
 #pragma unroll
                 for (int q = 0; q < R; ++q) {
                     const T to_next = (lane == 31) ? tail[q] : cs[m][4 - R + q];
                     v[q] = __shfl_sync(kAll, to_next, up);
                     const T to_prev = (lane == 0) ? cs[m + 1 < GW ? m + 1 : m][q] : cs[m][q];
                     v[R + 4 + q] = __shfl_sync(kAll, to_prev, down);
+                    if constexpr (PREC == 2) {
+                        const T ln = (lane == 31) ? tail_l[q] : er[m][4 - R + q];
+                        vl[q] = __shfl_sync(kAll, ln, up);
+                        const T lp = (lane == 0) ? er[m + 1 < GW ? m + 1 : m][q] : er[m][q];
+                        vl[R + 4 + q] = __shfl_sync(kAll, lp, down);
+                    }
                 }
 #pragma unroll
                 for (int q = 0; q < R; ++q) tail[q] = cs[m][4 - R + q];
 #pragma unroll
                 for (int e = 0; e < 4; ++e) v[R + e] = cs[m][e];
+                if constexpr (PREC == 2) {
+#pragma unroll
+                    for (int q = 0; q < R; ++q) tail_l[q] = er[m][4 - R + q];
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) vl[R + e] = er[m][e];
+                }
                 if (m == 0) {
 #pragma unroll
                     for (int q = 0; q < R; ++q) v[q] = (lane == 0) ? hl[q] : v[q];
+                    if constexpr (PREC == 2) {
+#pragma unroll
+                        for (int q = 0; q < R; ++q) vl[q] = (lane == 0) ? hll[q] : vl[q];
+                    }
                 }
                 const bool is_last = (m == m_last) && (lane == lane_last);
 #pragma unroll
                 for (int q = 0; q < R; ++q) v[R + 4 + q] = is_last ? hr[q] : v[R + 4 + q];
+                if constexpr (PREC == 2) {
+#pragma unroll
+                    for (int q = 0; q < R; ++q) vl[R + 4 + q] = is_last ? hrl[q] : vl[R + 4 + q];
+                }
                 T s4[4], c4[4];
                 if constexpr (FORCED) {
                     const int gg = g < NG ? g : NG - 1;
@@ -808,9 +928,14 @@ __device__ void run_pe(const Params &p, const Sweep &sw, long long lo, long long
                 }
 #pragma unroll
                 for (int e = 0; e < 4; ++e)
-                    cd[m][e] = point(v + e, s4[e], c4[e], er[PREC == 2 ? m : 0][PREC == 2 ? e : 0]);
+                    cd[m][e] = point(v + e, vl + (PREC == 2 ? e : 0), s4[e], c4[e],
+                                     er[PREC == 2 ? m : 0][PREC == 2 ? e : 0]);
 #pragma unroll
                 for (int q = 0; q < R; ++q) rb[q] = (m == m_last) ? cd[m][4 - R + q] : rb[q];
+                if constexpr (PREC == 2) {
+#pragma unroll
+                    for (int q = 0; q < R; ++q) rb_l[q] = (m == m_last) ? er[m][4 - R + q] : rb_l[q];
+                }
             }
             // publish the new boundary values and release the edge flags
             // (face 0 by lane 0, face 1 by the owner of group NG-1; the
@@ -819,20 +944,32 @@ __device__ void run_pe(const Params &p, const Sweep &sw, long long lo, long long
                 const size_t slot_off = (size_t)(lev & (p.T - 1)) * slot_stride;
                 const bool pub_ok = edge_pub || lev <= p.skip_step;
                 if (FULL || lane_last != 0) {
-                    T w[R];                    // word by word: no runtime choice between arrays
+                    T w[R], wl[R];             // word by word: no runtime choice between arrays
 #pragma unroll
                     for (int q = 0; q < R; ++q) w[q] = pf ? rb[q] : cd[0][q];
-                    st_entry<T, R>(pe0 + slot_off, w);
+                    if constexpr (PREC == 2) {
+#pragma unroll
+                        for (int q = 0; q < R; ++q) wl[q] = pf ? rb_l[q] : er[0][q];
+                        st_entry2<R>(pe0 + slot_off, w, wl);
+                    } else {
+                        st_entry<T, R>(pe0 + slot_off, w);
+                    }
                     if (p.mode == kModeSync) __threadfence();
                     if (prel && pub_ok) st_release(pflag, (unsigned long long)lev);
                 } else {
                     // one group: lane 0 publishes both faces
 #pragma unroll
                     for (int f = 0; f < 2; ++f) {
-                        T w[R];
+                        T w[R], wl[R];
 #pragma unroll
                         for (int q = 0; q < R; ++q) w[q] = f ? rb[q] : cd[0][q];
-                        st_entry<T, R>(pe0 + f * kRingEntry + slot_off, w);
+                        if constexpr (PREC == 2) {
+#pragma unroll
+                            for (int q = 0; q < R; ++q) wl[q] = f ? rb_l[q] : er[0][q];
+                            st_entry2<R>(pe0 + f * kRingEntry + slot_off, w, wl);
+                        } else {
+                            st_entry<T, R>(pe0 + f * kRingEntry + slot_off, w);
+                        }
                         if (p.mode == kModeSync) __threadfence();
                         if ((f ? prel1 : prel) && pub_ok) st_release(pflag + f, (unsigned long long)lev);
                     }

@@ -1,7 +1,7 @@
-// at_kernels_f32c.cu -- single-domain stepper for float state with a
-// compensated state (a second FP32 word per point carries the rounding error
-// of the stored value; updates are error-free two-sums).  The extra registers
-// take it to two CTAs per SM.
+// at_kernels_f32c.cu -- single-domain stepper for a compensated float state
+// (every value a pair hi + lo of FP32 words: stencil differences and halo
+// values word by word, updates by error-free two-sums; see atk::run_pe,
+// PREC 2).  The extra registers take it to two CTAs per SM.
 #define AT_MIN_CTAS_PER_SM 2
 #include "at_kernels.cuh"
 

@@ -97,6 +97,16 @@ class Solver:
             raise B.AtError(rc, "at_state")
         return out
 
+    def state_error(self, out=None):
+        """Compensated state only: the lo words (rounding errors of ``state()``),
+        so that state() + state_error() is the value carried."""
+        if out is None:
+            out = self.torch.empty(self.N, dtype=self.tdtype, device=self.device)
+        rc = B.at_state_error(self.h, out.data_ptr())
+        if rc != B.AT_OK:
+            raise B.AtError(rc, "at_state_error")
+        return out
+
     def status(self):
         return B.at_status(self.h)
 

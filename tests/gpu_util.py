@@ -19,7 +19,7 @@ def gpu_run(u0, *, P, order, L, nu, dt, steps, dtype="f64", mode=None, seed=0, f
     """Runs the CUDA solver; returns dict(u, hist, m1, m2, rec, info, rc)."""
     import torch
 
-    from paper_1911_05769_gb300 import AT_OK, AT_REPLAY, AT_SEEDED, Solver, binding
+    from paper_1911_05769_gb300 import AT_FLAG_COMPENSATED, AT_OK, AT_REPLAY, AT_SEEDED, Solver, binding
     mode = AT_SEEDED if mode is None else mode
     N = len(u0)
     s = Solver(N, P, order, L, nu, dt, dtype=dtype, seed=seed, forcing_amp=forcing, max_ctas=max_ctas,
@@ -47,6 +47,8 @@ def gpu_run(u0, *, P, order, L, nu, dt, steps, dtype="f64", mode=None, seed=0, f
     if rc == AT_OK:
         hist, m1, m2 = s.delay_stats()
         res.update(u=out.cpu().numpy().astype(np.float64), hist=np.array(hist), m1=m1, m2=m2)
+        if flags & AT_FLAG_COMPENSATED:
+            res["lo"] = s.state_error().cpu().numpy().astype(np.float64)
         if recs:
             res["rec"] = np.concatenate([r.cpu().numpy() for r in recs], axis=0)
     s.close()
@@ -63,15 +65,15 @@ def oracle_run(u0, *, P, order, L, nu, dt, steps, mode, seed=0, forcing=0.0, del
 
 
 def gpu_ensemble_run(instances, *, M, order, steps, dtype="f64", mode=None, record=False, calls=None,
-                     max_ctas=0, stages=0, steps_per_pass=0, delays=None, tune=0):
+                     max_ctas=0, stages=0, steps_per_pass=0, delays=None, tune=0, flags=0):
     """Runs an ensemble through the C ABI (at_create_batch); returns dict(u, hist, rec, info, solver)."""
     import torch
 
     import at_workloads as W
-    from paper_1911_05769_gb300 import AT_FREE, AT_OK, AT_REPLAY, AT_SEEDED, EnsembleSolver, binding
+    from paper_1911_05769_gb300 import AT_FLAG_COMPENSATED, AT_FREE, AT_OK, AT_REPLAY, AT_SEEDED, EnsembleSolver, binding
     mode = AT_SEEDED if mode is None else mode
     s = EnsembleSolver(instances, M, order, dtype=dtype, max_ctas=max_ctas, stages=stages,
-                       steps_per_pass=steps_per_pass)
+                       steps_per_pass=steps_per_pass, flags=flags)
     u0 = torch.from_numpy(W.ensemble_field(instances)).cuda()
     res = {}
     if tune:
@@ -97,6 +99,9 @@ def gpu_ensemble_run(instances, *, M, order, steps, dtype="f64", mode=None, reco
         raise AssertionError(f"at_state returned {rc}: {binding.at_last_error()}")
     hist, m1, m2 = s.delay_stats()
     res.update(u=out.cpu().numpy().astype(np.float64), hist=np.array(hist), info=s.info(), offsets=s.offsets)
+    if flags & AT_FLAG_COMPENSATED:
+        # the value carried: hi + lo
+        res["lo"] = s.state_error().cpu().numpy().astype(np.float64)
     if recs:
         res["rec"] = np.concatenate([r.cpu().numpy() for r in recs], axis=0)
     s.close()

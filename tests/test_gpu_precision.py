@@ -102,21 +102,28 @@ def test_compensated_state_keeps_increments_below_an_ulp():
 
 
 def test_compensated_state_at_full_size():
-    """The forced N = 2^26 workload, 10^4 seeded steps: the compensated state
-    within the FP32 bar of the FP64 oracle.  Here it is not closer than plain
-    FP32 (both a few 1e-7 of max|u0|): the field moves by less than the FP32
-    rounding noise of the order-4 stencil sums, which compensation keeps."""
+    """The forced N = 2^26 workload, all 10^4 seeded steps (dt = 8.8e-13).  The
+    field moves by ~1e-6 of max|u| over the run, less than an FP32 ulp at most
+    points, and neighbouring values differ by a few ulps (dx = 9.4e-8).  The
+    compensated state (hi + lo words, stencil differences formed word by word,
+    two-sum updates) follows the FP64 oracle's run from the same initial field
+    (its FP32 rounding): the carried value hi + lo differs from it by less than
+    1e-3 of the change the oracle computes, on sampled windows; the public hi
+    words stay within the FP32 bar of max|u0|.  Plain FP32 cannot: most of its
+    updates are rounded away."""
     import math
 
     from paper_1911_05769_gb300 import AT_FLAG_COMPENSATED, AT_SEEDED
     cfg = W.config("burgers1d_forced_n2p26")
-    u0 = W.initial_field(cfg)
+    u0 = W.initial_field(cfg).astype(np.float32).astype(np.float64)
     N, P, order, L = cfg["N"], cfg["P"], cfg["order"], cfg["L"]
     _, dx = W.grid(N)
     dt = W.dt_rule(u0, dx, cfg["nu"])
     steps = cfg["n_steps"]
-    comp = gpu_run(u0, P=P, order=order, L=L, nu=cfg["nu"], dt=dt, steps=steps, dtype="f32", mode=AT_SEEDED,
-                   seed=cfg["seed"], forcing=cfg["forcing_amp"], flags=AT_FLAG_COMPENSATED)["u"]
+    kw = dict(P=P, order=order, L=L, nu=cfg["nu"], dt=dt, steps=steps, dtype="f32", mode=AT_SEEDED,
+              seed=cfg["seed"], forcing=cfg["forcing_amp"])
+    comp = gpu_run(u0, flags=AT_FLAG_COMPENSATED, **kw)
+    plain = gpu_run(u0, **kw)["u"]
     M, R = N // P, order // 2
     m = math.ceil(R * steps / M) + 1
     scale = np.max(np.abs(u0))
@@ -127,4 +134,11 @@ def test_compensated_state_at_full_size():
                             forcing_amp=cfg["forcing_amp"], p_lo=idx[0], p_count=2 * m + 1,
                             delay_mode=oracle.SEEDED, seed=cfg["seed"])
         want = ref[m * M:(m + 1) * M]
-        assert np.max(np.abs(comp[p * M:(p + 1) * M] - want)) / scale <= TOL["f32"]
+        start = u0[p * M:(p + 1) * M]
+        change = np.max(np.abs(want - start))
+        hi, lo = comp["u"][p * M:(p + 1) * M], comp["lo"][p * M:(p + 1) * M]
+        assert np.max(np.abs(hi - want)) / scale <= TOL["f32"]
+        e_pair = np.max(np.abs(hi + lo - want))
+        e_plain = np.max(np.abs(plain[p * M:(p + 1) * M] - want))
+        assert e_pair <= 1e-3 * change, (p, e_pair, change)
+        assert e_plain > 10 * e_pair, (p, e_plain, e_pair)

@@ -69,13 +69,13 @@ int ring_slots(int L, int s)
 }
 
 struct Layout {
-    size_t u, ring, flag, ctrl, hist, gbar, bsub, binst, ur, total;
+    size_t u, ring, flag, ctrl, hist, gbar, bsub, binst, ur, strip, total;
 };
 
 // Workspace: state, ring buffers [T][P][2], flags [P][2], control block,
 // delay counts, barrier counter; for an ensemble (n_inst > 0) also the
 // subdomain and instance records.
-Layout layout(int64_t N, int64_t P, int w, int L, int T, int64_t n_inst = 0, bool comp = false)
+Layout layout(int64_t N, int64_t P, int w, int L, int T, int64_t n_inst = 0, bool comp = false, bool strips = true)
 {
     Layout l{};
     size_t off = 0;
@@ -87,6 +87,8 @@ Layout layout(int64_t N, int64_t P, int w, int L, int T, int64_t n_inst = 0, boo
     l.ctrl = off; off = align_up(off + atk::kCtrlWords * 4, 256);
     l.hist = off; off = align_up(off + (size_t)(L + 1) * 8, 256);
     l.gbar = off; off = align_up(off + 8, 256);
+    l.strip = off;   // blocked synchronous mode: edge strips [2][P][2]
+    if (strips) off = align_up(off + (size_t)2 * P * 2 * atk::kStripBytes, 256);
     l.bsub = off; l.binst = off;
     if (n_inst > 0) {
         off = align_up(off + (size_t)P * sizeof(atk::BatchSub), 256);
@@ -216,18 +218,20 @@ void pick_kernels(int w, int order, int64_t M, bool forced, bool v64, bool comp,
 }
 
 // Shared-memory table of a CTA: `fixed` bytes plus `per_sub` bytes per
-// subdomain of each of its PEs (forcing: sin/cos tables; ensembles: records);
-// comp: stages hold the error words of a compensated state too.
+// subdomain of each of its PEs and `extra` more subdomains per PE (forcing:
+// sin/cos tables, which also cover the PE's two outer neighbours; ensembles:
+// records); comp: stages hold the error words of a compensated state too.
 struct TabSize {
     long long fixed, per_sub;
     bool comp;
+    int extra;
 };
 
 TabSize tab_size(int64_t M, int w, bool forced, bool batch, bool comp = false)
 {
-    if (batch) return {0, (long long)sizeof(atk::BatchSub), comp};
-    if (forced) return {2LL * M * w, 2LL * w, comp};
-    return {0, 0, comp};
+    if (batch) return {0, (long long)sizeof(atk::BatchSub), comp, 0};
+    if (forced) return {2LL * M * w, 2LL * w, comp, 2};
+    return {0, 0, comp, 0};
 }
 
 // Chooses the CTA count (all co-resident CTAs unless max_ctas is set, at most
@@ -240,7 +244,7 @@ int launch_shape(int64_t M, int w, int64_t P, TabSize tsz, int max_ctas, int sta
     auto layout_for = [&](int G, int st, long long *smax) {
         const int64_t E = (int64_t)G * atk::kWarps;
         *smax = (P + E - 1) / E;
-        const long long tab = tsz.fixed + (long long)atk::kWarps * *smax * tsz.per_sub;
+        const long long tab = tsz.fixed + (long long)atk::kWarps * (*smax + tsz.extra) * tsz.per_sub;
         return atk::smem_layout(M, w, st, tab, tsz.comp);
     };
     // CTAs needed for one PE per subdomain at most
@@ -595,6 +599,7 @@ static atk::Params make_params(const at_solver *h)
     p.hist = reinterpret_cast<unsigned long long *>(h->ws + h->lay.hist);
     p.gbar = reinterpret_cast<unsigned long long *>(h->ws + h->lay.gbar);
     if (h->comp) p.ur = h->ws + h->lay.ur;
+    p.strip = h->ws + h->lay.strip;
     if (h->batch) {
         p.bsub = reinterpret_cast<const atk::BatchSub *>(h->ws + h->lay.bsub);
         p.binst = reinterpret_cast<const atk::BatchInst *>(h->ws + h->lay.binst);
@@ -666,6 +671,25 @@ int at_set_state(at_solver *h, const void *u)
     return AT_OK;
 }
 
+// Levels per pass of the blocked synchronous mode (AT_SYNC with
+// steps_per_pass > 1): the largest count up to the solver's steps_per_pass
+// whose edge strips (R x count points, rounded up to a multiple of 4) fit the
+// strip entry (16 words and 64 bytes) and lie within one subdomain.  The
+// compensated state is stepped one level per pass.
+static int sync_pass_len(const at_solver *h)
+{
+    if (h->comp) return 1;
+    int sb = h->sb;
+    while (sb > 1) {
+        const int64_t words = (int64_t)(h->R * sb + 3) / 4 * 4;
+        if (words <= 16 && words * h->w <= atk::kStripBytes && words <= h->M) break;
+        --sb;
+    }
+    return sb < 1 ? 1 : sb;
+}
+
+static int strip_words(const at_solver *h, int sb) { return (h->R * sb + 3) / 4 * 4; }
+
 static int step_impl(at_solver *h, int64_t n_steps, int delay_mode, int8_t *delays, void *levels, int64_t depth)
 {
     if (!h) return fail(AT_ERR_ARG, "NULL handle");
@@ -700,8 +724,11 @@ static int step_impl(at_solver *h, int64_t n_steps, int delay_mode, int8_t *dela
     p.mode = delay_mode;
     p.delays = delays;
     p.n_steps = n_steps;
-    p.sb = (delay_mode == AT_FREE && !levels) ? h->sb : 1;
-    p.alt = p.sb > 1 ? 1 : 0;
+    p.sb = levels ? 1 : delay_mode == AT_FREE ? h->sb : delay_mode == AT_SYNC ? sync_pass_len(h) : 1;
+    // blocked free-running passes alternate their sweep direction; the
+    // blocked synchronous passes (a grid barrier before each) need not
+    p.alt = (p.sb > 1 && delay_mode == AT_FREE) ? 1 : 0;
+    p.strip_words = strip_words(h, p.sb);
     p.levels = levels;
     p.levels_depth = depth;
     const cudaError_t e = launch_stepper(h, &p);
@@ -1089,7 +1116,7 @@ int at_tune(at_solver *h, int64_t n_steps, int delay_mode, at_tune_result *res)
     res->first_ms = best_ms;
     // levels per pass: up to the largest delay bound + 1 (an ensemble's PEs
     // clamp it to their own smallest bound + 1)
-    const int sb_hi = delay_mode == AT_FREE ? h->L + 1 : 1;
+    const int sb_hi = (delay_mode == AT_FREE || delay_mode == AT_SYNC) ? h->L + 1 : 1;
     for (int st = atk::kMinStages; rc == AT_OK && st <= 4; ++st) {
         int lastG = -1;
         for (int per_sm = 1; rc == AT_OK && per_sm <= 4; ++per_sm) {
@@ -1361,7 +1388,7 @@ extern "C" int at_step_noalloc(const at_grid *grid, int64_t P, int scheme_order,
     const int w = grid->dtype == AT_F64 ? 8 : 4;
     const int s = scheme_order / 2 + 1;
     const int T = ring_slots(L, s);
-    const Layout lay = layout(0, P, w, L, T);   // scratch only: the state is the caller's
+    const Layout lay = layout(0, P, w, L, T, 0, false, false);   // scratch only: the state is the caller's
     if (lay.total > (size_t)AT_NOALLOC_SCRATCH_BYTES)
         return fail(AT_ERR_ARG,
                     "at_step_noalloc: P=%lld, L=%d, order %d need %zu bytes of scratch, more than the "

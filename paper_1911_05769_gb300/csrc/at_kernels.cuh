@@ -49,7 +49,9 @@ constexpr int kWarps = 4;                         // PEs (warps) per CTA
 constexpr int kThreads = 32 * kWarps;
 constexpr int kRingEntry = 16;                    // bytes per (slot, subdomain, face)
 constexpr int kMaxS = 3;                          // levels per halo approximation
-constexpr int kRawBytes = 2 * kMaxS * kRingEntry; // one tile's delayed levels [face][m]
+constexpr int kStripBytes = 64;                  // blocked synchronous mode: edge strip per (subdomain, face)
+constexpr int kRawFace = 64;                      // raw bytes per face: kMaxS ring entries or one edge strip
+constexpr int kRawBytes = 2 * kRawFace;           // one tile's delayed levels [face][m] (or edge strips)
 constexpr int kMaxM = 1024;                       // points per subdomain (one warp's tile)
 constexpr int kMaxL = 16;
 constexpr int kMinStages = 2;                     // stages per PE (tile in use + one ahead)
@@ -123,12 +125,15 @@ struct Params {
     const BatchSub *bsub;      // ensembles: [P] subdomain records (else NULL)
     const BatchInst *binst;    // ensembles: instance records (else NULL)
     void *ur;                  // compensated state: the rounding error of every point (N words)
+    unsigned char *strip;      // blocked synchronous mode: edge strips [2][P][2] of kStripBytes (pass parity)
+    int strip_words;           // words per strip (R x levels per pass, rounded up to a multiple of 4)
     void *levels;              // optional copy of every level l computed: slot l mod levels_depth of N words
     long long levels_depth;    // (single-level passes only; the adjoint's recomputation)
     long long N, P, M;
     int L, T, mode, per_sub;   // L: largest delay bound (ensembles: of any instance)
     long long n_steps;
-    int sb;                    // most levels per pass (temporal blocking, free mode)
+    int sb;                    // most levels per pass (temporal blocking: free mode, and the blocked
+                               // synchronous mode, where k = 0 and the ghost cells are recomputed)
     int alt;                   // sweep direction alternates from pass to pass (blocked free mode)
     unsigned long long seed;
     double cA, cB, dtA;        // dt/(2dx) | dt/(12dx);  nu dt/dx^2 | nu dt/(12dx^2);  dt A
@@ -307,6 +312,71 @@ __device__ __forceinline__ void st_entry2(unsigned char *e, const float *h, cons
     else st_cg16(e, h[0], l[0], 0.0f, 0.0f);
 }
 
+// One point of the forward-Euler update: w[0 .. 2R] are the values at offsets
+// -R .. R (w[R] the point itself; wl the lo words of a compensated state),
+// cA = dt/(2dx) | dt/(12dx), cB = nu dt/dx^2 | nu dt/(12dx^2) (cB64 the
+// same in FP64), fs/fc and sv/cv the forcing factors of the subdomain and of
+// the point's offset (A dt sin x = fs cv + fc sv); returns the new value
+// (compensated state: updates the carried error too).  The stepper's tiles
+// and the ghost cells of the blocked synchronous mode both call it, so a
+// point computed twice is computed the same way twice.
+template <typename T, int ORDER, bool FORCED, int PREC>
+__device__ __forceinline__ T stencil_point(const T *w, const T *wl, T cA, T cB, double cB64, T fs, T fc, T sv, T cv,
+                                           T &err)
+{
+    constexpr int R = ORDER / 2;
+    const T cc = w[R];
+    T a, b;
+    if constexpr (PREC == 2) {
+        // differences word by word; the second difference as differences
+        // from the centre point
+        const T cl = wl[R];
+        if constexpr (ORDER == 2) {
+            a = (w[2] - w[0]) + (wl[2] - wl[0]);
+            b = ((w[2] - cc) + (w[0] - cc)) + ((wl[2] - cl) + (wl[0] - cl));
+        } else {
+            a = ((T)8 * (w[3] - w[1]) - (w[4] - w[0])) + ((T)8 * (wl[3] - wl[1]) - (wl[4] - wl[0]));
+            b = ((T)16 * ((w[3] - cc) + (w[1] - cc)) - ((w[4] - cc) + (w[0] - cc))) +
+                ((T)16 * ((wl[3] - cl) + (wl[1] - cl)) - ((wl[4] - cl) + (wl[0] - cl)));
+        }
+        T du = cB * b - cA * (cc + cl) * a;
+        if constexpr (FORCED) du = fs * cv + (fc * sv + du);
+        // two-sum of hi and (du + lo): exact sum t + err
+        const T y = du + err;
+        const T t = cc + y;
+        const T yy = t - cc;
+        err = (cc - (t - yy)) + (y - yy);
+        return t;
+    } else {
+        (void)wl;
+        (void)err;
+        if constexpr (ORDER == 2) {
+            a = w[2] - w[0];
+            b = (w[2] + w[0]) - (T)2 * cc;
+        } else {
+            a = (T)8 * (w[3] - w[1]) - (w[4] - w[0]);
+            b = (T)16 * (w[3] + w[1]) - (w[4] + w[0]) - (T)30 * cc;
+        }
+        if constexpr (PREC == 1) {
+            double b64;
+            if constexpr (ORDER == 2) {
+                b64 = ((double)w[2] + (double)w[0]) - 2.0 * (double)cc;
+            } else {
+                b64 = 16.0 * ((double)w[3] + (double)w[1]) - ((double)w[4] + (double)w[0]) - 30.0 * (double)cc;
+            }
+            T rest = -cA * cc * a;
+            if constexpr (FORCED) rest = fs * cv + (fc * sv + rest);
+            (void)b;
+            return (T)((double)cc + (cB64 * b64 + (double)rest));
+        } else {
+            (void)cB64;
+            T du = cB * b - cA * cc * a;
+            if constexpr (FORCED) du = fs * cv + (fc * sv + du);   // two fused multiply-adds
+            return cc + du;
+        }
+    }
+}
+
 // Waits (lane 0) for the bulk copy into a stage; bounded.
 static __device__ __noinline__ bool wait_stage(const Params &p, uint64_t *bar, unsigned parity)
 {
@@ -365,30 +435,37 @@ static __device__ __noinline__ bool cta_grid_sync(const Params &p, int *s_count,
 // waits on its neighbour at each pass start.  Alternating, each edge tile
 // needs a tile its neighbour finished about a pass earlier; and the tile at
 // the turn is the same subdomain twice in a row, continued in registers.
+//
+// startup: passes of one level while the level is below s-1 (the AT halos
+// need s levels); the synchronous modes read level n only and have none.
 struct Sweep {
     long long n0, n_steps;
     int sb;
     bool alt;
+    bool startup;
 };
 
 // Position of a tile in a PE's sweep: pass start level n, subdomain j, the
-// pass length and (alternating sweeps) the direction of the pass.
+// pass length, (alternating sweeps) the direction of the pass, and the
+// index of the pass within the launch.
 struct Cursor {
     long long n, j;
     int len;
     bool rev;
+    long long pass;
 };
 
 __device__ __forceinline__ int pass_len(const Sweep &sw, long long n, int s_lev)
 {
     const long long left = sw.n0 + sw.n_steps - n;
     int len = (int)(left < sw.sb ? left : sw.sb);
-    if (n < s_lev - 1) len = 1;
+    if (sw.startup && n < s_lev - 1) len = 1;
     return len;
 }
 
 __device__ __forceinline__ long long count_passes(const Sweep &sw, int s_lev)
 {
+    if (!sw.startup) return (sw.n_steps + sw.sb - 1) / sw.sb;
     long long single = (s_lev - 1) - sw.n0;
     if (single < 0) single = 0;
     if (single > sw.n_steps) single = sw.n_steps;
@@ -403,12 +480,14 @@ __device__ __forceinline__ void advance(const Sweep &sw, Cursor &c, long long lo
             c.j = lo;
             c.n += c.len;
             c.len = pass_len(sw, c.n, s_lev);
+            ++c.pass;
         }
     } else if (c.rev ? c.j == lo : c.j == hi - 1) {
         // turn: the next pass starts on the same subdomain
         c.rev = !c.rev;
         c.n += c.len;
         c.len = pass_len(sw, c.n, s_lev);
+        ++c.pass;
     } else {
         c.j += c.rev ? -1 : 1;
     }
@@ -481,11 +560,23 @@ __device__ void run_pe(const Params &p, const Sweep &sw, long long lo, long long
     constexpr unsigned kAll = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const long long S = hi - lo;
+    // Blocked synchronous mode (AT_SYNC in passes of sb > 1 levels): every
+    // delay is 0, a grid barrier precedes each pass, and a tile takes, instead
+    // of the ring's per-level halo, its neighbours' edge strips of R sb points
+    // at the pass's first level; the halo of each later level of the pass is
+    // recomputed from them (ghost cells, the same arithmetic as the
+    // neighbour's own update), so the result equals the unblocked AT_SYNC run
+    // bit for bit.  Strips are written at the end of each pass (parity of the
+    // pass index) and, at the launch start, from the state itself; barrier 1
+    // follows that.
+    const bool bsync = p.mode == kModeSync && sw.sb > 1;
+    const long long ep_off = bsync ? 1 : 0;                 // grid barriers before the first pass
+    const long long n_ep = count_passes(sw, S_LEV) + ep_off; // arrivals of this launch
     if (S <= 0) {
         // a PE without subdomains still takes part in every grid barrier
         if (p.mode == kModeSync) {
-            for (long long st = 1; st <= p.n_steps; ++st)
-                if (!cta_grid_sync(p, s_count, s_epoch, st, st < p.n_steps)) break;
+            for (long long st = 1; st <= n_ep; ++st)
+                if (!cta_grid_sync(p, s_count, s_epoch, st, st < n_ep)) break;
         }
         return;
     }
@@ -507,7 +598,7 @@ __device__ void run_pe(const Params &p, const Sweep &sw, long long lo, long long
     const bool edge_pub = !(p.skip_publish && blockIdx.x == 0 && threadIdx.x < 32);
     unsigned *my_hist = hist + (lane & 1) * (kMaxL + 1);
 
-    Cursor L{sw.n0, lo, pass_len(sw, sw.n0, S_LEV), false};   // next tile to load
+    Cursor L{sw.n0, lo, pass_len(sw, sw.n0, S_LEV), false, 0};   // next tile to load
     Cursor H = L;                                     // next tile whose halo is prepared
     Cursor C = L;                                     // tile being processed
 
@@ -618,18 +709,29 @@ __device__ void run_pe(const Params &p, const Sweep &sw, long long lo, long long
         // phase 2: both faces ready -- count, record and copy the levels
         if (lane < 2) {
             const int f = lane;
+            // (the synchronous modes use level n itself at every level: k = 0)
+            const int kstep = p.mode == kModeSync ? 0 : 1;
             for (int i = 0; i < c.len; ++i) {
-                my_hist[k + i] += 1u;
+                my_hist[k + kstep * i] += 1u;
                 if (p.delays && p.mode != kModeReplay)
-                    p.delays[((c.n - sw.n0 + i) * p.P + c.j) * 2 + f] = (int8_t)(k + i);
+                    p.delays[((c.n - sw.n0 + i) * p.P + c.j) * 2 + f] = (int8_t)(k + kstep * i);
             }
             hk = (int)k;
-            const unsigned char *rbase = p.ring + ((size_t)(bnd ? 0 : q) * 2 + (1 - f)) * kRingEntry;
-            const int levels = bnd ? 0 : (k == 0 && c.len == 1) ? 1 : S_LEV;
-            for (int m = 0; m < levels; ++m) {
-                const long long lv = c.n - k - m;
-                cp_async16(raw + (size_t)buf * kRawBytes + (f * kMaxS + m) * kRingEntry,
-                           rbase + (size_t)(lv & (p.T - 1)) * slot_stride);
+            if (bsync) {
+                // the neighbour's edge strip at the pass's first level
+                const unsigned char *sb0 = p.strip +
+                    ((size_t)((c.pass & 1) * p.P + (bnd ? 0 : q)) * 2 + (1 - f)) * kStripBytes;
+                const int chunks = bnd ? 0 : p.strip_words * (int)sizeof(T) / 16;
+                for (int ch = 0; ch < chunks; ++ch)
+                    cp_async16(raw + (size_t)buf * kRawBytes + f * kRawFace + ch * 16, sb0 + ch * 16);
+            } else {
+                const unsigned char *rbase = p.ring + ((size_t)(bnd ? 0 : q) * 2 + (1 - f)) * kRingEntry;
+                const int levels = bnd ? 0 : (k == 0 && c.len == 1) ? 1 : S_LEV;
+                for (int m = 0; m < levels; ++m) {
+                    const long long lv = c.n - k - m;
+                    cp_async16(raw + (size_t)buf * kRawBytes + f * kRawFace + m * kRingEntry,
+                               rbase + (size_t)(lv & (p.T - 1)) * slot_stride);
+                }
             }
         }
         return 1;
@@ -651,8 +753,21 @@ __device__ void run_pe(const Params &p, const Sweep &sw, long long lo, long long
         sl = (sl + 1 == NS) ? 0 : sl + 1;
         ++nl;
     };
-    while (tl < D && tl < Q) { issue_load(sl, L); next_load(); }
     bool ok = true;
+    if (bsync) {
+        // edge strips of the state at the launch's first level (parity 0),
+        // then the first grid barrier
+        const int sw4 = p.strip_words;
+        const T *ust = reinterpret_cast<const T *>(p.u);
+        for (long long t = lane; t < S * 2 * sw4; t += 32) {
+            const long long jj = lo + t / (2 * sw4);
+            const int f = (int)((t / sw4) & 1), wd = (int)(t % sw4);
+            const long long src = jj * p.M + (f ? p.M - sw4 : 0) + wd;
+            reinterpret_cast<T *>(p.strip + ((size_t)jj * 2 + f) * kStripBytes)[wd] = ust[src];
+        }
+        if (!cta_grid_sync(p, s_count, s_epoch, 1, true)) ok = false;
+    }
+    while (tl < D && tl < Q) { issue_load(sl, L); next_load(); }
     bool pending = true;               // the halo of tile 0 is prepared in the loop
     int k0cur = 0, k1cur = 0;
     bool turn = false;                 // tile r continues tile r-1 in registers (alternating sweep)
@@ -662,11 +777,11 @@ __device__ void run_pe(const Params &p, const Sweep &sw, long long lo, long long
     for (long long r = 0; r < Q && ok; ++r) {
         // state copy of tile r + D (stage of tile r - 1, complete: in order)
         if (tl < Q && tl <= r + D) { issue_load(sl, L); next_load(); }
-        const long long step = C.n - sw.n0;
-        // synchronous algorithm: before the first tile of a step, all PEs
-        // have finished the previous step (grid barrier, Algorithm 1)
-        if (p.mode == kModeSync && step > 0 && C.j == lo) {
-            if (!cta_grid_sync(p, s_count, s_epoch, step, true)) { ok = false; break; }
+        // synchronous algorithm: before the first tile of a pass (a step when
+        // unblocked), all PEs have finished the previous pass (grid barrier,
+        // Algorithm 1)
+        if (p.mode == kModeSync && C.pass > 0 && C.j == lo) {
+            if (!cta_grid_sync(p, s_count, s_epoch, C.pass + ep_off, true)) { ok = false; break; }
         }
         // halo of tile r: prepared one tile ahead unless it was pending
         const int buf = (int)(r & 1);
@@ -736,20 +851,41 @@ __device__ void run_pe(const Params &p, const Sweep &sw, long long lo, long long
             }
         }
         // A sin(x) dt = (dt A sin x_j) cos(i dx) + (dt A cos x_j) sin(i dx)
+        // (the tables hold subdomains lo-1 .. hi: entry j - lo + 1)
         T fs = (T)0, fc = (T)0;
         if constexpr (FORCED) {
-            fs = (T)(p.dtA * (double)spt[j - lo]);
-            fc = (T)(p.dtA * (double)cpt[j - lo]);
+            fs = (T)(p.dtA * (double)spt[j - lo + 1]);
+            fc = (T)(p.dtA * (double)cpt[j - lo + 1]);
+        }
+
+        // blocked synchronous mode: ghost cells.  Lanes 0 .. G-1 hold the left
+        // neighbour's points x = -G .. -1 (relative to the tile), lanes
+        // 16 .. 16+G-1 the right neighbour's points M .. M+G-1, at the level
+        // being advanced (G = R len; at the pass start, the strips)
+        const int G = R * len;
+        T gv = (T)0;
+        T fsl = (T)0, fcl = (T)0, fsr = (T)0, fcr = (T)0;    // forcing factors of the neighbours
+        if (bsync) {
+            const T *stl = reinterpret_cast<const T *>(rw);
+            const T *str = reinterpret_cast<const T *>(rw + kRawFace);
+            if (lane < G) gv = stl[p.strip_words - G + lane];
+            else if (lane >= 16 && lane < 16 + G) gv = str[lane - 16];
+            if constexpr (FORCED) {
+                fsl = (T)(p.dtA * (double)spt[j - lo]);
+                fcl = (T)(p.dtA * (double)cpt[j - lo]);
+                fsr = (T)(p.dtA * (double)spt[j - lo + 2]);
+                fcr = (T)(p.dtA * (double)cpt[j - lo + 2]);
+            }
         }
 
         // halo values of every inner level (delays k0 + i, k1 + i): lane
         // x < 2 R len computes one of them once per tile; each level then
         // takes its 2R values by shuffle
-        const bool hv_lanes = 2 * R * len <= 32;
+        const bool hv_lanes = !bsync && 2 * R * len <= 32;
         T hv = (T)0, hvl = (T)0;       // (hvl: lo word of a compensated state)
         if (hv_lanes && lane < 2 * R * len) {
             const int f = lane / (R * len), rem = lane % (R * len);
-            const unsigned char *rf = rw + f * kMaxS * kRingEntry;
+            const unsigned char *rf = rw + f * kRawFace;
             const int kf = (f ? k1cur : k0cur) + rem / R;
             if constexpr (PREC == 2) {
                 if (BATCH && (f ? bnd1 : bnd0)) {
@@ -787,6 +923,61 @@ __device__ void run_pe(const Params &p, const Sweep &sw, long long lo, long long
             const long long lev = n + i + 1;                 // level being computed
             T hl[R], hr[R];
             T hll[R], hrl[R];                                // lo words (compensated state)
+            if (bsync) {
+                // the halo of level n+i from the ghost lanes (an ensemble's
+                // domain ends: the exact values)
+#pragma unroll
+                for (int q = 0; q < R; ++q) {
+                    hll[q] = hrl[q] = (T)0;
+                    hl[q] = __shfl_sync(kAll, gv, G - R + q);
+                    hr[q] = __shfl_sync(kAll, gv, 16 + q);
+                    if constexpr (BATCH) {
+                        if (bnd0) hl[q] = exact_ghost<T, R>(p.binst, btab[j - lo], p.M, 0, q, n + i);
+                        if (bnd1) hr[q] = exact_ghost<T, R>(p.binst, btab[j - lo], p.M, 1, q, n + i);
+                    }
+                }
+                if (i + 1 < len) {
+                    // the ghost cells of level n+i+1 from level n+i: ghost
+                    // lanes and the tile's own edge words (not yet updated)
+                    T el[R];
+#pragma unroll
+                    for (int q = 0; q < R; ++q) el[q] = (T)0;
+#pragma unroll
+                    for (int m = 0; m < GW; ++m) {
+#pragma unroll
+                        for (int q = 0; q < R; ++q) el[q] = (m == m_last) ? cs[m][4 - R + q] : el[q];
+                    }
+                    T ownl[R], ownr[R];
+#pragma unroll
+                    for (int q = 0; q < R; ++q) {
+                        ownl[q] = __shfl_sync(kAll, cs[0][q], 0);
+                        ownr[q] = __shfl_sync(kAll, el[q], lane_last);
+                    }
+                    const bool left = lane < 16;
+                    const int xo = left ? lane - G : lane - 16;      // x, or x - M on the right
+                    T w[2 * R + 1];
+#pragma unroll
+                    for (int jj = -R; jj <= R; ++jj) {
+                        const T gq = __shfl_sync(kAll, gv, (lane + jj) & 31);
+                        const int y = xo + jj;
+                        T v;
+                        if (left) v = (y < 0) ? gq : ((R == 1 || y == 0) ? ownl[0] : ownl[R - 1]);
+                        else v = (y >= 0) ? gq : ((R == 1 || y == -1) ? ownr[R - 1] : ownr[0]);
+                        w[jj + R] = v;
+                    }
+                    T sv = (T)0, cv = (T)0;
+                    if constexpr (FORCED) {
+                        if (left ? lane < G : lane - 16 < G) {
+                            const int off = left ? (int)p.M + xo : xo;
+                            sv = sj[off];
+                            cv = cj[off];
+                        }
+                    }
+                    T unused = (T)0;
+                    gv = stencil_point<T, ORDER, FORCED, PREC>(w, w, cA, cB, cB64, left ? fsl : fsr, left ? fcl : fcr,
+                                                               sv, cv, unused);
+                }
+            } else {
 #pragma unroll
             for (int q = 0; q < R; ++q) {
                 hll[q] = hrl[q] = (T)0;
@@ -798,7 +989,7 @@ __device__ void run_pe(const Params &p, const Sweep &sw, long long lo, long long
                         hrl[q] = __shfl_sync(kAll, hvl, R * len + i * R + q);
                     }
                 } else if constexpr (PREC == 2) {
-                    const unsigned char *rr = rw + kMaxS * kRingEntry;
+                    const unsigned char *rr = rw + kRawFace;
                     if (BATCH && bnd0) {
                         hl[q] = exact_ghost2<T, R>(p.binst, btab[j - lo], p.M, 0, q, n + i, hll[q]);
                     } else {
@@ -815,60 +1006,15 @@ __device__ void run_pe(const Params &p, const Sweep &sw, long long lo, long long
                     hl[q] = (BATCH && bnd0) ? exact_ghost<T, R>(p.binst, btab[j - lo], p.M, 0, q, n + i)
                                             : approx_halo<T, S_LEV>(rw, k0cur + i, q);
                     hr[q] = (BATCH && bnd1) ? exact_ghost<T, R>(p.binst, btab[j - lo], p.M, 1, q, n + i)
-                                            : approx_halo<T, S_LEV>(rw + kMaxS * kRingEntry, k1cur + i, q);
+                                            : approx_halo<T, S_LEV>(rw + kRawFace, k1cur + i, q);
                 }
+            }
             }
             // One point: w[0 .. 2R] are the values at offsets -R .. R (w[R] the
             // point itself), sv/cv the forcing table entries; returns the new
             // value (compensated state: updates the carried error too).
             auto point = [&](const T *w, const T *wl, T sv, T cv, T &err) -> T {
-                const T cc = w[R];
-                T a, b;
-                if constexpr (PREC == 2) {
-                    // differences word by word; the second difference as
-                    // differences from the centre point
-                    const T cl = wl[R];
-                    if constexpr (ORDER == 2) {
-                        a = (w[2] - w[0]) + (wl[2] - wl[0]);
-                        b = ((w[2] - cc) + (w[0] - cc)) + ((wl[2] - cl) + (wl[0] - cl));
-                    } else {
-                        a = ((T)8 * (w[3] - w[1]) - (w[4] - w[0])) + ((T)8 * (wl[3] - wl[1]) - (wl[4] - wl[0]));
-                        b = ((T)16 * ((w[3] - cc) + (w[1] - cc)) - ((w[4] - cc) + (w[0] - cc))) +
-                            ((T)16 * ((wl[3] - cl) + (wl[1] - cl)) - ((wl[4] - cl) + (wl[0] - cl)));
-                    }
-                    T du = cB * b - cA * (cc + cl) * a;
-                    if constexpr (FORCED) du = fs * cv + (fc * sv + du);
-                    // two-sum of hi and (du + lo): exact sum t + err
-                    const T y = du + err;
-                    const T t = cc + y;
-                    const T yy = t - cc;
-                    err = (cc - (t - yy)) + (y - yy);
-                    return t;
-                } else if constexpr (ORDER == 2) {
-                    a = w[2] - w[0];
-                    b = (w[2] + w[0]) - (T)2 * cc;
-                } else {
-                    a = (T)8 * (w[3] - w[1]) - (w[4] - w[0]);
-                    b = (T)16 * (w[3] + w[1]) - (w[4] + w[0]) - (T)30 * cc;
-                }
-                if constexpr (PREC == 1) {
-                    double b64;
-                    if constexpr (ORDER == 2) {
-                        b64 = ((double)w[2] + (double)w[0]) - 2.0 * (double)cc;
-                    } else {
-                        b64 = 16.0 * ((double)w[3] + (double)w[1]) - ((double)w[4] + (double)w[0]) - 30.0 * (double)cc;
-                    }
-                    T rest = -cA * cc * a;
-                    if constexpr (FORCED) rest = fs * cv + (fc * sv + rest);
-                    (void)b;
-                    (void)wl;
-                    return (T)((double)cc + (cB64 * b64 + (double)rest));
-                } else {
-                    (void)wl;
-                    T du = cB * b - cA * cc * a;
-                    if constexpr (FORCED) du = fs * cv + (fc * sv + du);   // two fused multiply-adds
-                    return cc + du;
-                }
+                return stencil_point<T, ORDER, FORCED, PREC>(w, wl, cA, cB, cB64, fs, fc, sv, cv, err);
             };
             // lane l holds groups g = l + 32 m of 4 points; neighbour words come
             // from the adjacent lanes (lane 0 / 31: the other end of the warp at
@@ -977,6 +1123,20 @@ __device__ void run_pe(const Params &p, const Sweep &sw, long long lo, long long
             }
         };
         for (int i = 0; i < len; ++i) level(i, c, c);
+        if (bsync) {
+            // edge strips of the pass's last level for the next pass
+            const int gq = p.strip_words / 4;
+            T *s0 = reinterpret_cast<T *>(p.strip + ((size_t)(((C.pass + 1) & 1) * p.P + j) * 2) * kStripBytes);
+            T *s1 = reinterpret_cast<T *>(reinterpret_cast<unsigned char *>(s0) + kStripBytes);
+            bool wrote = false;
+#pragma unroll
+            for (int m = 0; m < GW; ++m) {
+                const int g = lane + 32 * m;
+                if (g < gq) { stg4<T>(s0 + 4 * g, c[m]); wrote = true; }
+                if (g >= NG - gq && g < NG) { stg4<T>(s1 + 4 * (g - (NG - gq)), c[m]); wrote = true; }
+            }
+            if (wrote) __threadfence();
+        }
         // the next tile; before a turn the words stay in registers
         Cursor Cn = C;
         advance(sw, Cn, lo, hi, S_LEV);
@@ -1007,8 +1167,8 @@ __device__ void run_pe(const Params &p, const Sweep &sw, long long lo, long long
         C = Cn;
         turn = keep;
     }
-    // synchronous algorithm: the last step's arrival at the grid barrier
-    if (ok && p.mode == kModeSync) cta_grid_sync(p, s_count, s_epoch, p.n_steps, false);
+    // synchronous algorithm: the last pass's arrival at the grid barrier
+    if (ok && p.mode == kModeSync) cta_grid_sync(p, s_count, s_epoch, n_ep, false);
     // let every copy in flight land before the warp leaves
     if (lane < 2) cp_async_wait_all();
     if (lane == 0) {
@@ -1044,10 +1204,11 @@ __global__ void __launch_bounds__(kThreads, AT_MIN_CTAS_PER_SM) at_stepper(const
     unsigned char *stages = smem + p.stage_off + (size_t)w * p.stages * p.stage_bytes;
     T *tab = reinterpret_cast<T *>(smem + p.tab_off);
     T *sj = tab, *cj = tab + p.M;
-    T *spt = tab + 2 * p.M + (size_t)w * 2 * p.smax, *cpt = spt + p.smax;
+    T *spt = tab + 2 * p.M + (size_t)w * 2 * (p.smax + 2), *cpt = spt + p.smax + 2;
     BatchSub *btab = reinterpret_cast<BatchSub *>(smem + p.tab_off) + (size_t)w * p.smax;
     // time level of the state, advanced at the end of the previous launch
-    Sweep sw{*reinterpret_cast<const volatile long long *>(p.ctrl + kCtrlN0), p.n_steps, p.sb, p.alt != 0};
+    Sweep sw{*reinterpret_cast<const volatile long long *>(p.ctrl + kCtrlN0), p.n_steps, p.sb, p.alt != 0,
+             p.mode != kModeSync};
 
     __shared__ int s_count;                   // grid-barrier arrivals of this CTA's warps
     __shared__ long long s_epoch;             // last grid barrier this CTA passed
@@ -1066,9 +1227,13 @@ __global__ void __launch_bounds__(kThreads, AT_MIN_CTAS_PER_SM) at_stepper(const
             sj[i] = (T)sv;
             cj[i] = (T)cv;
         }
-        for (long long i = lane; i < S; i += 32) {
+        // entry i: subdomain lo - 1 + i (wrapped), i = 0 .. S + 1
+        for (long long i = lane; i < S + 2; i += 32) {
+            long long q = lo - 1 + i;
+            if (q < 0) q += p.P;
+            if (q >= p.P) q -= p.P;
             double sv, cv;
-            sincos(p.x0 + (double)((lo + i) * p.M) * p.dx, &sv, &cv);
+            sincos(p.x0 + (double)(q * p.M) * p.dx, &sv, &cv);
             spt[i] = (T)sv;
             cpt[i] = (T)cv;
         }
@@ -1084,7 +1249,7 @@ __global__ void __launch_bounds__(kThreads, AT_MIN_CTAS_PER_SM) at_stepper(const
         for (long long i = lane; i < S; i += 32) lmin = min(lmin, p.bsub[lo + i].L);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) lmin = min(lmin, __shfl_xor_sync(0xffffffffu, lmin, o));
-        if (sw.sb > lmin + 1) sw.sb = lmin + 1;
+        if (p.mode != kModeSync && sw.sb > lmin + 1) sw.sb = lmin + 1;
     }
     __syncthreads();
     run_pe<T, ORDER, GW, FORCED, FULL, BATCH, PREC>(p, sw, lo, hi, bars, hist, raw, stages, sj, cj, spt, cpt, btab,

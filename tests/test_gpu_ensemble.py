@@ -99,6 +99,30 @@ def test_replayed_ensemble_delays_match_oracle():
     check_against_oracle(inst, res, M=M, order=2, steps=steps, mode="replay", dtype="f64", delays=delays)
 
 
+@pytest.mark.parametrize("order", [2, 4])
+def test_blocked_sync_ensemble_is_bitwise_synchronous(order):
+    """Blocked synchronous passes in an ensemble (exact-boundary and periodic
+    instances, one- and two-subdomain instances, uneven L_j): equal to the
+    unblocked AT_SYNC run bit for bit; every PE takes the same passes
+    whatever its L_j (the grid barrier before each pass needs that)."""
+    from paper_1911_05769_gb300 import AT_SYNC
+    M = 256
+    inst = small_ensemble(M=M, seed=41 + order, log2_n=(8.0, 10.5), periodic=(0, 3))
+    inst[0]["n"] = 256
+    inst[3]["n"] = 512
+    for j in (0, 3):
+        d = inst[j]
+        x, dx = W.grid(d["n"], d["length"], d["origin"])
+        d["u0"] = 0.3 + 0.2 * np.sin(x) + 0.1 * np.sin(3 * x + 1)
+        d["dt"] = W.dt_rule(d["u0"], dx, d["nu"])
+    blk = gpu_ensemble_run(inst, M=M, order=order, steps=130, dtype="f64", mode=AT_SYNC, max_ctas=2,
+                           steps_per_pass=4, calls=[70, 60])
+    one = gpu_ensemble_run(inst, M=M, order=order, steps=130, dtype="f64", mode=AT_SYNC, max_ctas=2)
+    assert blk["info"].steps_per_pass == 4
+    assert np.array_equal(blk["u"], one["u"])
+    check_against_oracle(inst, blk, M=M, order=order, steps=130, mode="sync", dtype="f64")
+
+
 def test_sync_ensemble_matches_oracle():
     from paper_1911_05769_gb300 import AT_SYNC
     M = 256

@@ -273,3 +273,67 @@ def test_subdomains_per_processing_element(require_gpu, per_pe, mode_name):
     assert g["info"].ctas == 2
     assert rel_linf(g["u"], ref) <= TOL["f64"]
     assert np.array_equal(g["hist"], hist)
+
+
+BLOCKED_SYNC = [
+    # dtype, order, L, steps_per_pass, P, M, max_ctas, steps, calls, forcing, flags
+    ("f64", 4, 3, 4, 96, 256, 7, 301, None, 0.1, 0),
+    ("f32", 4, 3, 4, 256, 1024, 0, 200, [150, 50], 0.1, 0),
+    ("f64", 2, 2, 3, 64, 128, 5, 200, [100, 1, 99], 0.0, 0),
+    ("f32", 2, 7, 8, 48, 16, 4, 161, None, 0.1, 0),        # strips of 8 words, tiles of 16 points
+    ("f64", 4, 3, 2, 40, 1020, 3, 150, None, 0.1, 0),      # ragged tiles (groups beyond 32 lanes)
+    ("f64", 2, 1, 2, 1, 256, 0, 120, None, 0.0, 0),        # one subdomain, its own neighbour
+    ("f64", 2, 2, 3, 3, 256, 0, 90, None, 0.1, 0),         # three subdomains on three PEs
+    ("f64", 4, 3, 4, 40, 8, 6, 100, [3, 97], 0.1, 0),      # strips as wide as the tile
+    ("f32", 4, 3, 4, 64, 256, 2, 120, None, 0.1, "v64"),   # FP64 viscous accumulation
+]
+
+
+@pytest.mark.parametrize("dtype,order,L,spp,P,M,max_ctas,steps,calls,forcing,flags", BLOCKED_SYNC)
+def test_blocked_sync_is_bitwise_synchronous(require_gpu, dtype, order, L, spp, P, M, max_ctas, steps, calls,
+                                             forcing, flags):
+    """The blocked synchronous mode (AT_SYNC in passes of steps_per_pass
+    levels, a grid barrier before each pass, every delay 0, the halo of each
+    inner level recomputed from the neighbours' edge strips as ghost cells)
+    equals the unblocked AT_SYNC run (a barrier every step) bit for bit, and
+    the synchronous oracle to the bar."""
+    from paper_1911_05769_gb300 import AT_FLAG_VISCOUS_FP64, AT_SYNC
+    N = P * M
+    u0, dt = _setup(N, 0.02, kind="fourier" if N >= 256 else "two_modes")
+    fl = AT_FLAG_VISCOUS_FP64 if flags == "v64" else 0
+    kw = dict(P=P, order=order, L=L, nu=0.02, dt=dt, steps=steps, forcing=forcing, flags=fl)
+    blk = gpu_run(u0, dtype=dtype, mode=AT_SYNC, max_ctas=max_ctas, record=True, calls=calls, steps_per_pass=spp,
+                  **kw)
+    one = gpu_run(u0, dtype=dtype, mode=AT_SYNC, max_ctas=max_ctas, **kw)
+    assert blk["info"].steps_per_pass == spp
+    assert np.array_equal(blk["u"], one["u"]), rel_linf(blk["u"], one["u"])
+    assert np.all(blk["rec"] == 0) and np.array_equal(blk["hist"], one["hist"])
+    ref, _ = oracle_run(u0, mode="sync", P=P, order=order, L=L, nu=0.02, dt=dt, steps=steps, forcing=forcing)
+    assert rel_linf(blk["u"], ref) <= TOL[dtype]
+
+
+def test_blocked_sync_follows_other_modes(require_gpu):
+    """A blocked synchronous launch takes its edge strips from the state it
+    starts from, whatever ran before it: seeded, then blocked sync, then
+    free-running blocked, then blocked sync again, against the oracle
+    replaying the same delay sequence (zeros for the synchronous parts)."""
+    import torch
+
+    from paper_1911_05769_gb300 import AT_FREE, AT_SEEDED, AT_SYNC, Solver
+    N, P, L, order = 64 * 256, 64, 3, 4
+    u0, dt = _setup(N, 0.02, kind="fourier")
+    s = Solver(N, P, order, L, 0.02, dt, dtype="f64", seed=9, forcing_amp=0.1, max_ctas=5, steps_per_pass=L + 1)
+    s.set_state(torch.from_numpy(u0).cuda())
+    parts = [(AT_SEEDED, 37), (AT_SYNC, 41), (AT_FREE, 30), (AT_SYNC, 22)]
+    rec = []
+    for mode, n in parts:
+        d = torch.full((n, P, 2), -1, dtype=torch.int8, device="cuda")
+        s.step(n, mode, d)
+        rec.append(d.cpu().numpy())
+    got = s.state().cpu().numpy()
+    s.close()
+    rec = np.concatenate(rec, axis=0)
+    assert rec[37:78].max() == 0 and rec[108:].max() == 0
+    ref, _ = oracle_run(u0, mode="replay", delays=rec, P=P, order=order, L=L, nu=0.02, dt=dt, steps=130,
+                        forcing=0.1)
+    assert rel_linf(got, ref) <= TOL["f64"]

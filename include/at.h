@@ -62,7 +62,8 @@ extern "C" {
                                undelayed (see at_instance)                        */
 
 /* delay modes of at_step (Sec. 2 delay model; Algorithms 1 and 2) */
-#define AT_SYNC   0  /* k = 0 everywhere, grid barrier every step (Alg. 1)     */
+#define AT_SYNC   0  /* k = 0 everywhere, grid barrier every step (Alg. 1);    */
+                     /* with steps_per_pass > 1: every pass (ghost cells)     */
 #define AT_SEEDED 1  /* k prescribed by SplitMix64(seed) per (n, p, face)      */
 #define AT_FREE   2  /* k = how far the neighbour lags, waiting only if > L    */
 #define AT_REPLAY 3  /* k read from a caller array                             */
@@ -115,8 +116,16 @@ typedef struct at_grid {
   int32_t  stages;          /* tile buffers per warp: 0 = 3; at least 2; fewer if */
                             /* shared memory cannot hold them                     */
   int64_t  test_skip_step;  /* level after which AT_FLAG_TEST_SKIP_PUBLISH acts    */
-  int32_t  steps_per_pass;  /* AT_FREE only: levels advanced per pass over a tile  */
-                            /* (temporal blocking), 0 or 1 = none, at most L+1    */
+  int32_t  steps_per_pass;  /* levels advanced per pass over a tile (temporal      */
+                            /* blocking), 0 or 1 = none, at most L+1.  AT_FREE:   */
+                            /* halos of inner levels extrapolated with delay     */
+                            /* k0 + i.  AT_SYNC: a grid barrier per pass, every  */
+                            /* delay 0, the halos of inner levels recomputed     */
+                            /* from the neighbours' edge strips of R x levels     */
+                            /* points (ghost cells), bit for bit the result of    */
+                            /* a barrier every step; the count is reduced until  */
+                            /* a strip fits 16 words, 64 bytes and one subdomain */
+                            /* (one level per pass with AT_FLAG_COMPENSATED)      */
   int32_t  reserved;
   int64_t  sub[3];          /* dim 3: points per subdomain along x, y, z; n[a] a  */
                             /* multiple of sub[a]; P = product of n[a] / sub[a]   */
@@ -135,7 +144,7 @@ typedef struct at_info {
   int64_t step;             /* time level of the state (steps taken)               */
   int32_t sm_count;         /* SMs of the device                                   */
   int32_t dtype;            /* AT_F64 or AT_F32                                    */
-  int32_t steps_per_pass;   /* levels per pass in AT_FREE                          */
+  int32_t steps_per_pass;   /* levels per pass (AT_FREE; AT_SYNC as reduced above) */
   int32_t viscous_fp64;     /* 1 if the viscous term is accumulated in FP64        */
 } at_info;
 

@@ -55,7 +55,9 @@ def parse():
     ap.add_argument("--cpu-sample-subdomains", type=int, default=4096)
     ap.add_argument("--ctas", type=int, default=0, help="CTAs of the persistent kernel (0 = one per SM)")
     ap.add_argument("--stages", type=int, default=0, help="tiles in flight per CTA (0 = default)")
-    ap.add_argument("--arms", default="free,sync,seeded", help="timed arms (free first is the headline)")
+    ap.add_argument("--arms", default="all",
+                    help="timed arms besides the headline free_blocked: all or a comma list of "
+                         "sync,sync_blocked,seeded,free")
     ap.add_argument("--N", type=int, default=0, help="smaller N for profiling runs (P scales, M stays 1024)")
     ap.add_argument("--spp", type=int, default=-1,
                     help="levels per pass of the free-running arm (temporal blocking); -1 = L+1")
@@ -178,26 +180,72 @@ def dist_setup(args):
     return ws, rank, local, pg
 
 
+def compiler_version() -> str:
+    try:
+        return subprocess.check_output(["gcc", "--version"], text=True).splitlines()[0]
+    except Exception:
+        return "gcc (version unknown)"
+
+
 def cpu_baseline(args, u0, dt, cfg):
-    """The oracle (single thread, as it stands) on a bounded sample: a window of
-    the workload's subdomains advanced a few steps with seeded delays.  Also
-    returns the window's result for the FP64-oracle error of the GPU run."""
+    """The oracle as it stands, timed on the host cores: single-threaded on a
+    window of 512 subdomains and with OpenMP over subdomains on every core on
+    a window of 4096 subdomains, both over 100 seeded steps of the workload,
+    median of 5 repetitions (after one untimed run)."""
     import oracle
     oracle.build()
+    N, P, M = cfg["N"], cfg["P"], cfg["N"] // cfg["P"]
+    steps = args.cpu_sample_steps
+    ncores = os.cpu_count() or 1
+
+    def timed(nsub, threads, reps=5):
+        oracle.threads(threads)
+        u0w = np.ascontiguousarray(u0[:nsub * M], dtype=np.float64)
+        kw = dict(N=N, P=P, order=cfg["order"], L=cfg["L"], nu=cfg["nu"], dt=dt, n_steps=steps,
+                  forcing_amp=cfg["forcing_amp"], delay_mode=oracle.SEEDED, seed=cfg["seed"], p_lo=0, p_count=nsub)
+        oracle.run(u0w, **kw)
+        ts = []
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            oracle.run(u0w, **kw)
+            ts.append(time.perf_counter() - t0)
+        med = statistics.median(ts)
+        return nsub * M * steps / med / 1e9, med, ts
+
+    one, one_s, _ = timed(min(512, P), 1)
+    nsub = min(args.cpu_sample_subdomains, P)
+    used = oracle.threads(ncores)
+    allc, all_s, _ = timed(nsub, used)
+    out = {"value": allc, "unit": UNIT, "cores": used, "kind": "oracle",
+           "sample": f"{nsub} subdomains x {M} points of the N=2^26 workload, {steps} seeded-delay steps, FP64, "
+                     f"OpenMP over subdomains on {used} threads (nproc {ncores}): median of 5 runs {all_s:.3f} s",
+           "nproc": ncores, "compiler": compiler_version(), "repetitions": 5,
+           "single_thread": {"value": one, "unit": UNIT, "cores": 1,
+                             "sample": f"{min(512, P)} subdomains x {M} points, {steps} seeded steps: "
+                                       f"median of 5 runs {one_s:.3f} s"}}
+    return out
+
+
+def window_oracles(args, u0, dt, cfg, recs):
+    """FP64 oracle runs of a window of the workload's subdomains (all host
+    cores): synchronous, seeded, every delay at L (the c15 envelope's
+    reference), and the recorded delays of each free-running arm replayed."""
+    import oracle
+    oracle.build()
+    oracle.threads(os.cpu_count() or 1)
     N, P, M = cfg["N"], cfg["P"], cfg["N"] // cfg["P"]
     nsub = min(args.cpu_sample_subdomains, P)
     steps = args.cpu_sample_steps
     u0w = np.ascontiguousarray(u0[:nsub * M], dtype=np.float64)
-    t0 = time.perf_counter()
-    ref, _ = oracle.run(u0w, N=N, P=P, order=cfg["order"], L=cfg["L"], nu=cfg["nu"], dt=dt, n_steps=steps,
-                        forcing_amp=cfg["forcing_amp"], delay_mode=oracle.SEEDED, seed=cfg["seed"], p_lo=0,
-                        p_count=nsub)
-    el = time.perf_counter() - t0
-    upd = nsub * M * steps
-    out = {"value": upd / el / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
-           "sample": f"{nsub} subdomains x {M} points ({nsub * M} points) of the N=2^26 workload, "
-                     f"{steps} seeded-delay steps, FP64, single thread: {upd:.3e} updates in {el:.2f} s"}
-    return out, ref, nsub, steps
+    kw = dict(N=N, P=P, order=cfg["order"], L=cfg["L"], nu=cfg["nu"], dt=dt, n_steps=steps,
+              forcing_amp=cfg["forcing_amp"], p_lo=0, p_count=nsub)
+    out = {"sync": oracle.run(u0w, delay_mode=oracle.SYNC, **kw)[0],
+           "seeded": oracle.run(u0w, delay_mode=oracle.SEEDED, seed=cfg["seed"], **kw)[0],
+           "k_eq_L": oracle.run(u0w, delay_mode=oracle.REPLAY,
+                                replay=np.full((steps, nsub, 2), cfg["L"], np.int8), **kw)[0]}
+    for name, rec in recs.items():
+        out[name] = oracle.run(u0w, delay_mode=oracle.REPLAY, replay=np.ascontiguousarray(rec[:, :nsub, :]), **kw)[0]
+    return out, nsub, steps
 
 
 def small_config(args, at, torch, dev, stream):
@@ -212,7 +260,7 @@ def small_config(args, at, torch, dev, stream):
     res = {"workload": "burgers1d_n4096", "N": cfg["N"], "P": cfg["P"], "order": cfg["order"], "L": cfg["L"],
            "dtype": "f64", "time_steps_per_launch": cfg["n_steps"]}
     arms = (("free", at.AT_FREE, 0), ("free_blocked", at.AT_FREE, cfg["L"] + 1), ("seeded", at.AT_SEEDED, 0),
-            ("sync", at.AT_SYNC, 0))
+            ("sync", at.AT_SYNC, 0), ("sync_blocked", at.AT_SYNC, cfg["L"] + 1))
     for name, mode, spp in arms:
         s = at.Solver(cfg["N"], cfg["P"], cfg["order"], cfg["L"], cfg["nu"], dt, dtype="f64", seed=cfg["seed"],
                       stream=stream, device=dev.index, steps_per_pass=spp)
@@ -232,6 +280,7 @@ def small_config(args, at, torch, dev, stream):
         res[name] = {"us_per_step": us_step, "value": cfg["N"] / (us_step * 1e-6) / 1e9, "unit": UNIT}
         s.close()
     res["speedup_free_over_sync"] = res["sync"]["us_per_step"] / res["free"]["us_per_step"]
+    res["speedup_free_blocked_over_sync_blocked"] = res["sync_blocked"]["us_per_step"] / res["free_blocked"]["us_per_step"]
     return res
 
 
@@ -251,9 +300,9 @@ def ensemble_config(args, at, torch, dev, stream):
            "l2": f"state {Ntot * 4 / 2**20:.0f} MiB: close to the 126 MiB L2 (replays continue in place)"}
     Lmax = max(d["L"] for d in inst)
 
-    def run(mode, name):
-        s = at.EnsembleSolver(inst, M, order, dtype="f32", stream=stream, device=dev.index,
-                              steps_per_pass=Lmax + 1 if mode == at.AT_FREE else 0)
+    def run(mode, name, spp=None, flags=0):
+        s = at.EnsembleSolver(inst, M, order, dtype="f32", stream=stream, device=dev.index, flags=flags,
+                              steps_per_pass=(Lmax + 1 if mode == at.AT_FREE else 0) if spp is None else spp)
         with torch.cuda.stream(stream):
             s.set_state(u0)
         t = None if args.no_tune else s.tune(200, mode)
@@ -287,7 +336,10 @@ def ensemble_config(args, at, torch, dev, stream):
 
     res["free"] = run(at.AT_FREE, "free")
     res["sync"] = run(at.AT_SYNC, "sync")
+    res["sync_blocked"] = run(at.AT_SYNC, "sync_blocked", spp=Lmax + 1)
+    res["free_compensated"] = run(at.AT_FREE, "free_compensated", flags=at.AT_FLAG_COMPENSATED)
     res["speedup_free_over_sync"] = res["free"]["value"] / res["sync"]["value"]
+    res["speedup_free_over_sync_blocked"] = res["free"]["value"] / res["sync_blocked"]["value"]
     res["effective_one_pass_frac"] = res["free"]["value"] * 1e9 * 8 / (hbm_peak()[0] * 1e9)
     # algorithmic bytes per update with passes of the launch's steps_per_pass
     # (warps whose smallest L_j is lower take shorter passes and move more:
@@ -302,27 +354,37 @@ def ensemble_config(args, at, torch, dev, stream):
                        "note": "bound by per-tile latency and control instructions, not by HBM"}
     res["gpu_launches_per_replay"] = 1
     # FP32 error against the FP64 oracle after the full 5000 seeded steps, on
-    # the four smallest instances and one mid-size one
-    s = at.EnsembleSolver(inst, M, order, dtype="f32", stream=stream, device=dev.index)
-    with torch.cuda.stream(stream):
-        s.set_state(u0)
-        s.step(time_steps, at.AT_SEEDED)
-        g = s.state().double().cpu().numpy()
-    s.close()
+    # the four smallest instances (the largest dt), one mid-size one and the
+    # largest: plain FP32 state and the compensated state (hi + lo)
     n = np.array([d["n"] for d in inst])
-    which = list(np.argsort(n)[:4]) + [int(np.argsort(n)[len(n) // 2])]
+    which = list(np.argsort(n)[:4]) + [int(np.argsort(n)[len(n) // 2]), int(np.argmax(n))]
+    finals = {}
+    for key, fl in (("plain", 0), ("compensated", at.AT_FLAG_COMPENSATED)):
+        s = at.EnsembleSolver(inst, M, order, dtype="f32", stream=stream, device=dev.index, flags=fl)
+        with torch.cuda.stream(stream):
+            s.set_state(u0)
+            s.step(time_steps, at.AT_SEEDED)
+            g = s.state().double().cpu().numpy()
+            if fl:
+                g = g + s.state_error().double().cpu().numpy()
+        s.close()
+        finals[key] = g
     import oracle
+    oracle.build()
+    oracle.threads(os.cpu_count() or 1)
     offs = np.concatenate([[0], np.cumsum(n)])
-    worst = 0.0
+    worst = {"plain": 0.0, "compensated": 0.0}
     for j in which:
         d = inst[j]
         ref, _ = oracle.run(W.instance_field(d), N=d["n"], P=d["n"] // M, order=order, L=d["L"], nu=d["nu"],
                             dt=d["dt"], n_steps=time_steps, x0=d["origin"], dx=d["length"] / d["n"],
                             bc=oracle.BC_TANH, tanh=(d["tanh_a"], d["tanh_c"], d["tanh_xc"]),
                             delay_mode=oracle.SEEDED, seed=d["seed"])
-        part = g[offs[j]:offs[j + 1]]
-        worst = max(worst, float(np.max(np.abs(part - ref)) / np.max(np.abs(ref))))
-    res["err_vs_fp64_oracle"] = {"rel_linf": worst, "mode": "seeded", "steps": time_steps,
+        for key, g in finals.items():
+            part = g[offs[j]:offs[j + 1]]
+            worst[key] = max(worst[key], float(np.max(np.abs(part - ref)) / np.max(np.abs(ref))))
+    res["err_vs_fp64_oracle"] = {"rel_linf": worst["compensated"], "state": "compensated (hi + lo)",
+                                 "rel_linf_plain_fp32": worst["plain"], "mode": "seeded", "steps": time_steps,
                                  "instances": [int(j) for j in which]}
     return res
 
@@ -406,7 +468,8 @@ def config3d(args, at, torch, dev):
     """3D scalar Burgers, 512^3 FP32 in 32^3 subdomains (4096), order 2, L = 2,
     nu = 5e-3, k^-5/3 field (seed 4): launches of 500 steps (4 per 2000-step
     run), free-running vs seeded vs synchronous; the FP32 error against the
-    FP64 oracle on a 128^3 box of the same recipe after 50 steps."""
+    FP64 oracle over all 2000 steps on a 128^3 box at the workload's dx, nu
+    and dt."""
     n, sub, L, nu = 512, (32, 32, 32), 2, 5e-3
     u0 = W.u0_spectral3d(n, seed=4, kmax=32)
     dt = W.dt_rule(u0, 2 * np.pi / n, nu, dim=3)
@@ -448,20 +511,25 @@ def config3d(args, at, torch, dev):
     res["roofline"] = {"bound": "hbm", "algorithmic_bytes_per_update": bpu,
                        "achieved": res["free"]["value"] * bpu, "peak": peak, "unit": "GB/s",
                        "frac": res["free"]["value"] * bpu / peak, "peak_source": src}
-    # FP32 against the FP64 oracle, 128^3 box in 32^3 subdomains, 50 seeded steps
+    # FP32 against the FP64 oracle over all 2000 steps at the workload's dx,
+    # nu and dt: a periodic 128^3 box of length pi/2 (32^3 subdomains, the
+    # k^-5/3 recipe at the workload's wavenumbers), seeded delays
     import oracle
-    nb = 128
-    ub = W.u0_spectral3d(nb, seed=4, kmax=32)
-    nub = 0.02
-    dtb = W.dt_rule(ub, 2 * np.pi / nb, nub, dim=3)
-    s = at.Solver3D((nb, nb, nb), sub, L, nub, dtb, dtype="f32", seed=5, device=dev.index)
+    oracle.build()
+    oracle.threads(os.cpu_count() or 1)
+    nb, box, nsteps = 128, np.pi / 2, 2000
+    ub = W.u0_spectral3d(nb, seed=4, kmax=8)
+    dtb = W.dt_rule(ub, box / nb, nu, dim=3)
+    s = at.Solver3D((nb, nb, nb), sub, L, nu, dtb, dtype="f32", seed=5, device=dev.index, length=(box,) * 3)
     s.set_state(torch.from_numpy(ub.ravel()).to(dev))
-    s.step(50, at.AT_SEEDED)
+    s.step(nsteps, at.AT_SEEDED)
     g = s.state().double().cpu().numpy().reshape(ub.shape)
     s.close()
-    ref, _ = oracle.run3d(ub, P=(4, 4, 4), L=L, nu=nub, dt=dtb, n_steps=50, delay_mode=oracle.SEEDED, seed=5)
+    ref, _ = oracle.run3d(ub, P=(4, 4, 4), L=L, nu=nu, dt=dtb, n_steps=nsteps, length=box, delay_mode=oracle.SEEDED,
+                          seed=5)
     res["err_vs_fp64_oracle"] = {"rel_linf": float(np.max(np.abs(g - ref)) / np.max(np.abs(ref))),
-                                 "box": [nb, nb, nb], "nu": nub, "steps": 50, "mode": "seeded"}
+                                 "box": [nb, nb, nb], "box_length": box, "nu": nu, "dt": dtb, "steps": nsteps,
+                                 "mode": "seeded"}
     return res
 
 
@@ -533,14 +601,16 @@ def config_system(args, at, torch, dev):
 
 
 def reference_arm(args, ws, rank, pg):
-    """--impl reference: the CPU oracle timed on this workload, bounded sample per step."""
+    """--impl reference: the CPU oracle timed on this workload on every host
+    core (OpenMP over subdomains), bounded sample per step."""
     cfg = W.config(WORKLOAD)
     if rank != 0:
         return
     import oracle
     oracle.build()
+    cores = oracle.threads(os.cpu_count() or 1)
     N, P, M = cfg["N"], cfg["P"], cfg["N"] // cfg["P"]
-    nsub = 1024
+    nsub = 4096
     full = W.initial_field(cfg)
     _, dx = W.grid(N)
     dt = W.dt_rule(full, dx, cfg["nu"])
@@ -565,14 +635,25 @@ def reference_arm(args, ws, rank, pg):
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "N": N, "P": P, "order": cfg["order"], "L": cfg["L"],
                    "sample": f"{nsub} subdomains ({nsub * M} points) x {steps_per} steps per bench step"},
-        "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"{nsub * M} points x {steps_per} seeded steps per bench step, single thread"},
+        "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{nsub * M} points x {steps_per} seeded steps per bench step, "
+                                   f"OpenMP over subdomains on {cores} threads"},
         "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 
 
 # ---------------------------------------------------------------------------
+def fma_peaks(at):
+    """Measured FMA rates of this GPU (FP64 and FP32), FMAs per second."""
+    return {"f64": at.at_fma_peak(at.AT_F64, 1500), "f32": at.at_fma_peak(at.AT_F32, 100000)}
+
+
+def timing_stats(per_ms):
+    q = statistics.quantiles(per_ms, n=4) if len(per_ms) >= 2 else [per_ms[0]] * 3
+    return {"median": statistics.median(per_ms), "q1": q[0], "q3": q[2], "launches": len(per_ms)}
+
+
 def gpu_arm(args, ws, rank, local, pg):
     import torch
 
@@ -605,10 +686,9 @@ def gpu_arm(args, ws, rank, local, pg):
 
     spp = L + 1 if args.spp < 0 else args.spp
 
-    def make(dtype=args.dtype, blocked=True):
-        s = at.Solver(N, P, order, L, nu, dt, dtype=dtype, forcing_amp=A, seed=cfg["seed"], stream=stream,
-                      device=local, max_ctas=args.ctas, stages=args.stages, steps_per_pass=spp if blocked else 0)
-        return s
+    def make(dtype=args.dtype, sb=spp, flags=0):
+        return at.Solver(N, P, order, L, nu, dt, dtype=dtype, forcing_amp=A, seed=cfg["seed"], stream=stream,
+                         device=local, max_ctas=args.ctas, stages=args.stages, steps_per_pass=sb, flags=flags)
 
     def barrier():
         if pg is not None:
@@ -617,8 +697,8 @@ def gpu_arm(args, ws, rank, local, pg):
     def max_over_ranks_here(x):
         return max_over_ranks(pg, x, dev)
 
-    def timed_arm(mode, steps, warmup, time_steps, dtype=args.dtype, clocks=None):
-        s = make(dtype, blocked=(mode == at.AT_FREE))
+    def timed_arm(mode, sb, steps, warmup, time_steps, dtype=args.dtype, clocks=None, flags=0):
+        s = make(dtype, sb, flags)
         s.set_state(u0_dev if dtype == args.dtype else u0_dev.to(torch.float64 if dtype == "f64" else torch.float32))
         for _ in range(warmup):
             s.step(time_steps, mode)
@@ -644,29 +724,29 @@ def gpu_arm(args, ws, rank, local, pg):
             raise RuntimeError(f"{mode}: device status {rc}: {at.at_last_error()}")
         info = s.info()
         hist, m1, m2 = s.delay_stats()
-        final = s.state()
         s.close()
-        return dict(total_ms=max_over_ranks_here(tot), launch_ms=per, info=info, m1=m1, m2=m2, final=final, clocks=clk)
+        return dict(total_ms=max_over_ranks_here(tot), launch_ms=per, info=info, m1=m1, m2=m2, clocks=clk)
 
     clocks = Clocks(local)
-    arms = args.arms.split(",")
-    head = timed_arm(at.AT_FREE, args.steps, args.warmup, S, clocks=clocks)
-    sync = timed_arm(at.AT_SYNC, args.steps, args.warmup, S) if "sync" in arms else None
-    seed = timed_arm(at.AT_SEEDED, args.steps, args.warmup, S) if "seeded" in arms else None
+    # the arms, timed back to back: free-running in passes of L+1 levels (the
+    # headline), synchronous with a barrier every step, synchronous in passes
+    # of L+1 levels (ghost cells), seeded delays, free-running one level per pass
+    arm_defs = [("free_blocked", at.AT_FREE, spp), ("sync", at.AT_SYNC, 0), ("sync_blocked", at.AT_SYNC, spp),
+                ("seeded", at.AT_SEEDED, 0), ("free", at.AT_FREE, 0)]
+    want = set(args.arms.split(","))
+    runs = {}
+    for name, mode, sb in arm_defs:
+        if name == "free_blocked" or name in want or "all" in want:
+            runs[name] = timed_arm(mode, sb, args.steps, args.warmup, S, clocks=clocks if name == "free_blocked" else None)
+    head = runs["free_blocked"]
 
     upd_per_step = N * S
+
     def gpts(r, steps=args.steps, per=upd_per_step):
         return whole_job_rate(ws, per * steps, r["total_ms"] * 1e-3)
 
     value = gpts(head)
     ms_per_step = head["total_ms"] / args.steps
-    # equal error: AT results against the synchronous result after the same steps
-    def err_vs_sync(r):
-        if sync is None or r is None:
-            return None
-        ref = sync["final"].double()
-        return float((r["final"].double() - ref).abs().max()) / float(ref.abs().max())
-    err_free, err_seed = err_vs_sync(head), err_vs_sync(seed)
 
     # roofline of the stepper kernel: algorithmic bytes per launch / launch time
     M, R, s_lev = N // P, order // 2, order // 2 + 1
@@ -682,11 +762,12 @@ def gpu_arm(args, ws, rank, local, pg):
         traffic = traffic * S / traffic_steps
     # FP32 operations per update of the order-4 forced stencil (FMA = one op):
     # first difference 3, second difference 4, viscous/advective terms 3,
-    # forcing 2, Euler update 1; against 128 FP32 lanes per SM per clock
+    # forcing 2, Euler update 1
     ops_per_update = 13
+    peaks = fma_peaks(at)
     clk = (head["clocks"] or {}).get("sm_mhz") or 2070.0
     sms = head["info"].sm_count
-    alu_peak = sms * 128 * clk * 1e6 / 1e12
+    alu_peak = peaks["f32"] / 1e12
     alu_achieved = ops_per_update * upd_per_step / launch_s / 1e12
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": traffic, "peak_source": peak_src,
@@ -696,13 +777,34 @@ def gpu_arm(args, ws, rank, local, pg):
                                    "frac": upd_per_step * 2 * wbytes / launch_s / 1e9 / peak,
                                    "note": "updates/s x 2 words: the HBM bytes a one-pass-per-step kernel would need"},
             "alu": None if wbytes != 4 else {
-                "achieved": alu_achieved, "peak": alu_peak, "unit": "TOP/s (FP32, FMA = 1 op)",
+                "achieved": alu_achieved, "peak": alu_peak, "unit": "T FMA-pipe ops/s (FP32, FMA = 1 op)",
                 "frac": alu_achieved / alu_peak, "ops_per_update": ops_per_update,
-                "peak_note": f"{sms} SMs x 128 FP32 lanes x {clk:.0f} MHz (median SM clock under load)"}}
+                "peak_source": "measured: at_fma_peak (FP32 FMA chains, all SMs)"}}
+
+    def arm_line(name):
+        r = runs.get(name)
+        if r is None:
+            return None
+        return {"value": gpts(r), "ms_per_step": r["total_ms"] / args.steps, "ms_per_launch": timing_stats(r["launch_ms"]),
+                "mean_k": r["m1"], "mean_k2": r["m2"], "steps_per_pass": r["info"].steps_per_pass if name in (
+                    "free_blocked", "sync_blocked") else 1}
+
+    at_vs_sync = {n: arm_line(n) for n, _, _ in arm_defs}
+    if runs.get("sync"):
+        at_vs_sync["speedup_free_over_sync"] = value / gpts(runs["sync"])
+    if runs.get("sync_blocked"):
+        at_vs_sync["speedup_free_over_sync_blocked"] = value / gpts(runs["sync_blocked"])
+    if runs.get("free") and runs.get("sync"):
+        at_vs_sync["speedup_free_unblocked_over_sync"] = gpts(runs["free"]) / gpts(runs["sync"])
+    at_vs_sync["baselines"] = ("sync: a grid barrier every step, one HBM pass per step; sync_blocked: a grid barrier "
+                               "every L+1 steps, one HBM pass per L+1 steps (ghost cells recomputed, bit for bit the "
+                               "sync result); free_blocked: the headline, no barrier, passes of L+1 levels")
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "ms_per_step": ms_per_step, "ms_per_step_median": timing_stats(head["launch_ms"])["median"],
+        "ms_per_step_q1": timing_stats(head["launch_ms"])["q1"], "ms_per_step_q3": timing_stats(head["launch_ms"])["q3"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": args.dtype, "data": "synthetic",
         "config": {"workload": WORKLOAD, "N": N, "P": P, "M": M, "order": order, "L": L, "nu": nu,
                    "forcing_amp": A, "dt": dt, "time_steps_per_step": S, "mode": "free",
@@ -714,15 +816,9 @@ def gpu_arm(args, ws, rank, local, pg):
         "gpu_launches_note": "one at_stepper launch per bench step in the headline arm",
         "roofline": roof,
         "clocks": head["clocks"],
-        "at_vs_sync": {
-            "free": {"value": value, "ms_per_step": ms_per_step, "mean_k": head["m1"], "mean_k2": head["m2"],
-                     "rel_linf_vs_sync": err_free},
-            "seeded": None if seed is None else {
-                "value": gpts(seed), "ms_per_step": seed["total_ms"] / args.steps, "mean_k": seed["m1"],
-                "mean_k2": seed["m2"], "rel_linf_vs_sync": err_seed},
-            "sync": None if sync is None else {"value": gpts(sync), "ms_per_step": sync["total_ms"] / args.steps},
-            "speedup_free_over_sync": None if sync is None else value / gpts(sync),
-        },
+        "fma_peak": {"f64_tfma_per_s": peaks["f64"] / 1e12, "f32_tfma_per_s": peaks["f32"] / 1e12,
+                     "sm_mhz_bench": clk, "note": "at_fma_peak: independent FMA chains on every SM, CUDA events"},
+        "at_vs_sync": at_vs_sync,
     }
 
     if not args.no_extra:
@@ -748,78 +844,33 @@ def gpu_arm(args, ws, rank, local, pg):
         line["e2e"] = {"value": whole_job_rate(ws, upd_per_step * e2e_steps, el), "unit": UNIT,
                        "h2d_bytes_per_step": N * wbytes, "d2h_bytes_per_step": N * wbytes,
                        "steps": e2e_steps}
-        # FP64 state (FP64 arithmetic) on the same workload, fewer time steps
-        f64 = timed_arm(at.AT_FREE, 3, 2, max(1, S // 10), dtype="f64")
-        line["f64"] = {"value": whole_job_rate(ws, N * max(1, S // 10) * 3, f64["total_ms"] * 1e-3), "unit": UNIT,
-                       "time_steps_per_step": max(1, S // 10), "bound": "fp64 alu (see DESIGN)"}
+        # FP64 state (FP64 arithmetic) on the same workload, fewer time steps;
+        # bound by the FP64 FMA rate
+        S64 = max(1, S // 10)
+        f64 = timed_arm(at.AT_FREE, spp, 3, 2, S64, dtype="f64")
+        v64 = whole_job_rate(ws, N * S64 * 3, f64["total_ms"] * 1e-3)
+        ops64 = ops_per_update * v64 * 1e9 / 1e12
+        line["f64"] = {"value": v64, "unit": UNIT, "time_steps_per_step": S64,
+                       "roofline": {"bound": "fp64 alu", "achieved": ops64, "peak": peaks["f64"] / 1e12,
+                                    "unit": "T FP64 FMA-pipe ops/s (FMA = 1 op)", "frac": ops64 / (peaks["f64"] / 1e12),
+                                    "ops_per_update": ops_per_update,
+                                    "peak_source": "measured: at_fma_peak (FP64 FMA chains, all SMs)",
+                                    "hbm_frac": v64 * (2 * 8 / max(1, spp)) / peak}}
+        if args.dtype == "f32":
+            # the FP32 precision variants in the headline configuration
+            for key, fl, note in (
+                    ("compensated", at.AT_FLAG_COMPENSATED,
+                     "FP32 hi + lo words per point, word-by-word stencil differences, two-sum updates; 2 CTAs per SM"),
+                    ("viscous_fp64", at.AT_FLAG_VISCOUS_FP64,
+                     "FP32 state, viscous term nu dt D2 formed and added in FP64 (forced on)")):
+                r = timed_arm(at.AT_FREE, spp, 3, 2, S, flags=fl)
+                line[key] = {"value": gpts(r, steps=3), "unit": UNIT, "mode": "free, passes of L+1", "note": note}
         if rank == 0 and ws == 1:
-            cb, ref, nsub, csteps = cpu_baseline(args, u0, dt, cfg)
-            line["cpu_baseline"] = cb
-            # error of the GPU result against the FP64 oracle: the same seeded
-            # run on the GPU, compared away from the window's ends (values
-            # within R*steps points of them depend on the window's wrap)
-            s2 = at.Solver(N, P, order, L, nu, dt, dtype=args.dtype, forcing_amp=A, seed=cfg["seed"],
-                           stream=stream, device=local)
-            s2.set_state(u0_dev)
-            s2.step(csteps, at.AT_SEEDED)
-            g = s2.state().double().cpu().numpy()[:nsub * M]
-            s2.close()
-            cut = (order // 2) * csteps + M
-            err = float(np.max(np.abs(g[cut:-cut] - ref[cut:-cut])) / np.max(np.abs(ref)))
-            line["err_vs_fp64_oracle"] = {"rel_linf": err, "mode": "seeded", "steps": csteps,
-                                          "points_compared": int(nsub * M - 2 * cut), "dtype": args.dtype}
-            if args.dtype == "f32":
-                # the compensated state (second FP32 word per point, two-sum
-                # updates): throughput of the headline arm and the same error
-                sc = at.Solver(N, P, order, L, nu, dt, dtype="f32", forcing_amp=A, seed=cfg["seed"], stream=stream,
-                               device=local, steps_per_pass=spp, flags=at.AT_FLAG_COMPENSATED)
-                sc.set_state(u0_dev)
-                for _ in range(2):
-                    sc.step(S, at.AT_FREE)
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                with torch.cuda.stream(stream):
-                    e0.record(stream)
-                    for _ in range(3):
-                        sc.step(S, at.AT_FREE)
-                    e1.record(stream)
-                torch.cuda.synchronize(dev)
-                cval = N * S * 3 / (e0.elapsed_time(e1) * 1e-3) / 1e9
-                sc.close()
-                sc = at.Solver(N, P, order, L, nu, dt, dtype="f32", forcing_amp=A, seed=cfg["seed"], stream=stream,
-                               device=local, flags=at.AT_FLAG_COMPENSATED)
-                sc.set_state(u0_dev)
-                sc.step(csteps, at.AT_SEEDED)
-                gc = sc.state().double().cpu().numpy()[:nsub * M]
-                sc.close()
-                # FP64 viscous accumulation forced on the same workload
-                sv = at.Solver(N, P, order, L, nu, dt, dtype="f32", forcing_amp=A, seed=cfg["seed"], stream=stream,
-                               device=local, steps_per_pass=spp, flags=at.AT_FLAG_VISCOUS_FP64)
-                sv.set_state(u0_dev)
-                for _ in range(2):
-                    sv.step(S, at.AT_FREE)
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                with torch.cuda.stream(stream):
-                    e0.record(stream)
-                    for _ in range(3):
-                        sv.step(S, at.AT_FREE)
-                    e1.record(stream)
-                torch.cuda.synchronize(dev)
-                vval = N * S * 3 / (e0.elapsed_time(e1) * 1e-3) / 1e9
-                sv.close()
-                sv = at.Solver(N, P, order, L, nu, dt, dtype="f32", forcing_amp=A, seed=cfg["seed"], stream=stream,
-                               device=local, flags=at.AT_FLAG_VISCOUS_FP64)
-                sv.set_state(u0_dev)
-                sv.step(csteps, at.AT_SEEDED)
-                gv = sv.state().double().cpu().numpy()[:nsub * M]
-                sv.close()
-                line["viscous_fp64"] = {
-                    "value": vval, "unit": UNIT, "mode": "free, passes of L+1",
-                    "err_vs_fp64_oracle": float(np.max(np.abs(gv[cut:-cut] - ref[cut:-cut])) / np.max(np.abs(ref))),
-                    "note": "FP32 state, viscous term nu dt D2 formed and added in FP64 (forced on)"}
-                line["compensated"] = {
-                    "value": cval, "unit": UNIT, "mode": "free, passes of L+1",
-                    "err_vs_fp64_oracle": float(np.max(np.abs(gc[cut:-cut] - ref[cut:-cut])) / np.max(np.abs(ref))),
-                    "note": "FP32 state + FP32 error word per point (two-sum updates); 2 CTAs per SM"}
+            line["cpu_baseline"] = cpu_baseline(args, u0, dt, cfg)
+            line["accuracy"] = accuracy_legs(args, at, torch, stream, local, cfg, u0, u0_dev, dt, spp)
+            for key, arm in (("compensated", "free_blocked_compensated"), ("viscous_fp64", "free_blocked_viscous_fp64")):
+                if key in line and arm in line["accuracy"]:
+                    line[key]["err_vs_fp64_oracle"] = line["accuracy"][arm]["rel_linf_vs_oracle_same_delays"]
         # the latency-bound case: N = 4096, P = 16 subdomains of 256 points,
         # order 2, L = 2, FP64 (one PE per subdomain, four CTAs), AT vs barrier
         line["small_config"] = small_config(args, at, torch, dev, stream)
@@ -830,6 +881,53 @@ def gpu_arm(args, ws, rank, local, pg):
             line["system3d"] = config_system(args, at, torch, dev)
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def accuracy_legs(args, at, torch, stream, local, cfg, u0, u0_dev, dt, spp):
+    """Equal error: every arm advanced 100 steps from the same state on the
+    GPU, compared on a window of the workload's subdomains (away from its
+    ends) with the FP64 oracle -- with the arm's own delays (parity) and with
+    the synchronous run (accuracy), and the AT arms against the envelope
+    2 |u(k=L) - u_sync| + 10 eps max|u_sync| (any admissible delay pattern)."""
+    N, P, order, L, nu, A = cfg["N"], cfg["P"], cfg["order"], cfg["L"], cfg["nu"], cfg["forcing_amp"]
+    M = N // P
+    steps = args.cpu_sample_steps
+    nsub = min(args.cpu_sample_subdomains, P)
+    arms = [("free_blocked", at.AT_FREE, spp, 0), ("free", at.AT_FREE, 0, 0), ("seeded", at.AT_SEEDED, 0, 0),
+            ("sync", at.AT_SYNC, 0, 0), ("sync_blocked", at.AT_SYNC, spp, 0)]
+    if args.dtype == "f32":
+        arms += [("free_blocked_compensated", at.AT_FREE, spp, at.AT_FLAG_COMPENSATED),
+                 ("free_blocked_viscous_fp64", at.AT_FREE, spp, at.AT_FLAG_VISCOUS_FP64)]
+    got, recs = {}, {}
+    for name, mode, sb, flags in arms:
+        s = at.Solver(N, P, order, L, nu, dt, dtype=args.dtype, forcing_amp=A, seed=cfg["seed"], stream=stream,
+                      device=local, steps_per_pass=sb, flags=flags)
+        s.set_state(u0_dev)
+        d = torch.full((steps, P, 2), -1, dtype=torch.int8, device=u0_dev.device)
+        s.step(steps, mode, d)
+        u = s.state().double().cpu().numpy()[:nsub * M]
+        if flags & at.AT_FLAG_COMPENSATED:
+            u = u + s.state_error().double().cpu().numpy()[:nsub * M]
+        got[name] = u
+        if mode == at.AT_FREE:
+            recs[name] = d.cpu().numpy()
+        s.close()
+    ref, nsub, steps = window_oracles(args, u0, dt, cfg, recs)
+    cut = (order // 2) * steps + M
+    sl = slice(cut, nsub * M - cut)
+    scale = float(np.max(np.abs(ref["sync"][sl])))
+    eps = float(np.finfo(np.float32 if args.dtype == "f32" else np.float64).eps)
+    env = 2.0 * float(np.max(np.abs(ref["k_eq_L"][sl] - ref["sync"][sl]))) + 10.0 * eps * scale
+    out = {"window": f"{nsub} subdomains ({nsub * M} points), {steps} steps from the same state, "
+                     f"{nsub * M - 2 * cut} points compared", "dtype": args.dtype,
+           "envelope_abs": env, "k_eq_L_vs_sync_rel_linf": float(np.max(np.abs(ref["k_eq_L"][sl] - ref["sync"][sl]))) / scale}
+    for name, mode, sb, flags in arms:
+        own = ref[name] if name in recs else (ref["sync"] if mode == at.AT_SYNC else ref["seeded"])
+        e_own = float(np.max(np.abs(got[name][sl] - own[sl]))) / scale
+        d_sync = float(np.max(np.abs(got[name][sl] - ref["sync"][sl])))
+        out[name] = {"rel_linf_vs_oracle_same_delays": e_own, "rel_linf_vs_fp64_sync": d_sync / scale,
+                     "within_envelope": bool(d_sync <= env)}
+    return out
 
 
 def main():

@@ -298,9 +298,10 @@ int at_create_batch(const at_grid *grid, int64_t n_inst, const at_instance *inst
 /* ---------------------------------------------------------------------------
  * Autotuner.  Launch shapes of the persistent kernel: CTAs (1 up to the
  * resident limit per SM, times the SM count: so the processing elements per
- * subdomain), tile buffers per warp (2..4) and, for AT_FREE, levels per pass
- * (1 .. L + 1; in an ensemble each processing element then takes at most its
- * own smallest delay bound + 1).
+ * subdomain), tile buffers per warp (2..4) and levels per pass: for AT_FREE
+ * 1 .. L + 1 (in an ensemble each processing element then takes at most its
+ * own smallest delay bound + 1); for AT_SYNC 1 .. L + 1 only if the solver
+ * was created with steps_per_pass > 1 (the blocked synchronous mode), else 1.
  * --------------------------------------------------------------------------- */
 typedef struct at_tune_result {
   int32_t ctas, stages, steps_per_pass;   /* the fastest shape                     */
@@ -369,6 +370,15 @@ size_t at_adjoint_workspace_bytes(const at_solver *h, int64_t interval);
  * stepping.  Synchronises and returns the device status. */
 int at_adjoint(at_solver *h, int64_t n_steps, int delay_mode, const int8_t *delays, int64_t interval,
                const void *ckpt, void *adj_ws, size_t adj_ws_bytes, void *lam, double *dnu);
+
+/* Measured FMA throughput of the current device for dtype AT_F64 or AT_F32:
+ * fused multiply-adds per second (2 flops each) over the whole GPU, from one
+ * timed launch (after one warm-up launch) of a kernel whose threads run
+ * independent FMA chains, `trips` x 64 FMAs per thread (8 CTAs of 256 threads
+ * per SM).  The roofline of the arithmetic-bound variants (FP64 state) is
+ * taken against it.  Synchronises the legacy default stream.  A measurement
+ * utility; the paper has no counterpart. */
+int at_fma_peak(int dtype, int64_t trips, double *fma_per_s);
 
 /* Size in bytes of the fixed scratch array used by at_step_noalloc(). */
 #define AT_NOALLOC_SCRATCH_BYTES (8u * 1024u * 1024u)

@@ -17,7 +17,7 @@ from .binding import (AT_BC_EXACT_TANH, AT_BC_PERIODIC, AT_ERR_ARG, AT_ERR_CUDA,
                       AT_REPLAY,
                       AT_SEEDED, AT_SYNC, AtError, at_batch_workspace_bytes, at_create, at_create_batch,
                       at_delay_stats, at_destroy, at_get_info, at_grid, at_info, at_instance, at_last_error,
-                      at_set_state, at_state, at_state_error, at_status, at_step, at_step_noalloc, at_tune,
+                      at_fma_peak, at_set_state, at_state, at_state_error, at_status, at_step, at_step_noalloc, at_tune,
                       at_tune_result,
                       at_workspace_bytes, library_path, at_adjoint, at_adjoint_workspace_bytes,
                       at_checkpoint_bytes, at_set_history, at_step_checkpointed, at_step_levels,

@@ -94,6 +94,7 @@ _SIGNATURES = [
     ("at_step", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p]),
     ("at_state", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     ("at_state_error", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    ("at_fma_peak", ctypes.c_int, [ctypes.c_int, ctypes.c_int64, ctypes.POINTER(ctypes.c_double)]),
     ("at_status", ctypes.c_int, [ctypes.c_void_p]),
     ("at_delay_stats", ctypes.c_int,
      [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double),
@@ -183,6 +184,15 @@ def at_state(h, dst_ptr: int) -> int:
 
 def at_state_error(h, dst_ptr: int) -> int:
     return lib().at_state_error(h, ctypes.c_void_p(dst_ptr))
+
+
+def at_fma_peak(dtype: int, trips: int) -> float:
+    """FMAs per second of the current GPU for AT_F64 / AT_F32 (raises on error)."""
+    out = ctypes.c_double()
+    rc = lib().at_fma_peak(dtype, trips, ctypes.byref(out))
+    if rc != AT_OK:
+        raise AtError(rc, "at_fma_peak")
+    return out.value
 
 
 def at_status(h) -> int:

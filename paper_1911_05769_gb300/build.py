@@ -1,9 +1,11 @@
 """Builds the CUDA library ``libat.so`` in-tree for sm_103a with nvcc.
 
-Eleven translation units (host ABI; FP32 and FP64 single-domain kernels;
+Fifteen translation units (host ABI; FP32 and FP64 single-domain kernels;
 FP32 and FP64 ensemble kernels; adjoint kernels; FP32 kernels with FP64
 viscous accumulation; single-domain and ensemble FP32 kernels with a
-compensated state; scalar 3D kernels; 3D system kernels) compiled in parallel, one ``-gencode``; static CUDA runtime.
+compensated state; blocked synchronous kernels for FP32, FP32 with FP64
+viscous accumulation, FP32 ensembles and FP64; scalar 3D kernels; 3D system
+kernels) compiled in parallel, one ``-gencode``; static CUDA runtime.
 Run as
 ``python -m paper_1911_05769_gb300.build`` or through ``__graft_entry__.build()``.
 """
@@ -20,7 +22,8 @@ INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libat.so")
 SOURCES = [os.path.join(CSRC, f) for f in (
     "at_api.cu", "at_kernels_f32.cu", "at_kernels_f64.cu", "at_batch_f32.cu", "at_batch_f64.cu", "at_adjoint.cu",
-    "at_kernels_f32v.cu", "at_kernels_f32c.cu", "at_batch_f32c.cu", "at_kernels3d.cu", "at_system3d.cu")]
+    "at_kernels_f32v.cu", "at_kernels_f32c.cu", "at_batch_f32c.cu", "at_sync_f32.cu", "at_sync_f32v.cu", "at_sync_batch_f32.cu",
+    "at_sync_f64.cu", "at_kernels3d.cu", "at_system3d.cu")]
 DEPS = SOURCES + [os.path.join(CSRC, f) for f in ("at_kernels.cuh", "at_device.cuh", "at_adjoint.cuh",
                                                  "at_kernels3d.cuh")] + [
     os.path.join(INCLUDE, "at.h")]

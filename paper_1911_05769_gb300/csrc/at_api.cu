@@ -25,6 +25,11 @@ void *atk_stepper_kernel_f32(int order, int gw, bool forced, bool full);
 void *atk_stepper_kernel_f32v(int order, int gw, bool forced, bool full);
 void *atk_stepper_kernel_f32c(int order, int gw, bool forced, bool full);
 void *atk_stepper_kernel_f64(int order, int gw, bool forced, bool full);
+void *atk_sync_kernel_f32(int order, int gw, bool forced, bool full);
+void *atk_sync_kernel_f32v(int order, int gw, bool forced, bool full);
+void *atk_sync_kernel_f64(int order, int gw, bool forced, bool full);
+void *atk_sync_batch_kernel_f32(int order, int gw, bool full);
+void *atk_sync_batch_kernel_f64(int order, int gw, bool full);
 void *atk_init_kernel_f32(int order);
 void *atk_init_kernel_f64(int order);
 void *atk_batch_kernel_f32(int order, int gw, bool full);
@@ -202,19 +207,25 @@ bool viscous_fp64(int w, int order, uint32_t flags, double D)
 // The stepper and init kernels for a word size, order, subdomain size,
 // forcing and precision mode (instantiated in at_kernels_f32.cu,
 // at_kernels_f32v.cu, at_kernels_f32c.cu and at_kernels_f64.cu).
-void pick_kernels(int w, int order, int64_t M, bool forced, bool v64, bool comp, void **stepper, void **init)
+void pick_kernels(int w, int order, int64_t M, bool forced, bool v64, bool comp, void **stepper, void **init,
+                  void **stepper_bs = nullptr)
 {
     const int gw = groups_per_lane(M);
     const bool full = (M == 128LL * gw);
+    void *bs = nullptr;
     if (w == 8) {
         *stepper = atk_stepper_kernel_f64(order, gw, forced, full);
+        bs = atk_sync_kernel_f64(order, gw, forced, full);
         *init = atk_init_kernel_f64(order);
     } else {
         *stepper = comp  ? atk_stepper_kernel_f32c(order, gw, forced, full)
                    : v64 ? atk_stepper_kernel_f32v(order, gw, forced, full)
                          : atk_stepper_kernel_f32(order, gw, forced, full);
+        bs = comp ? nullptr : v64 ? atk_sync_kernel_f32v(order, gw, forced, full)
+                                  : atk_sync_kernel_f32(order, gw, forced, full);
         *init = atk_init_kernel_f32(order);
     }
+    if (stepper_bs) *stepper_bs = bs;
 }
 
 // Shared-memory table of a CTA: `fixed` bytes plus `per_sub` bytes per
@@ -307,6 +318,8 @@ struct at_solver {
     int64_t n_inst;
     int lmin;                  // smallest delay bound (ensembles), else L
     void *kernel;
+    void *kernel_bs;           // the blocked synchronous mode's kernel (NULL: none)
+    bool bs_ok;                // it can run in the launch shape chosen for `kernel`
     void *init_kernel;
 };
 
@@ -329,7 +342,7 @@ __global__ void at_flags_to_level(unsigned long long *flag, const int *ctrl, lon
 // resident; cudaLaunchKernelExC with the cooperative attribute may be
 // captured into a CUDA graph.  Brings the flags up to date first when the
 // partition into PEs differs from the previous launch's.
-cudaError_t launch_stepper(at_solver *h, atk::Params *p)
+cudaError_t launch_stepper(at_solver *h, atk::Params *p, void *kernel)
 {
     const int64_t E = (int64_t)h->G * atk::kWarps;
     if (h->flags_E != 0 && h->flags_E != E) {
@@ -351,7 +364,26 @@ cudaError_t launch_stepper(at_solver *h, atk::Params *p)
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     void *args[] = {p};
-    return cudaLaunchKernelExC(&cfg, h->kernel, args);
+    return cudaLaunchKernelExC(&cfg, kernel, args);
+}
+
+// The blocked synchronous kernel runs in the launch shape chosen for the
+// solver's kernel: the same dynamic shared memory, and only if as many of its
+// CTAs can be resident (else AT_SYNC keeps one level per pass).
+void prepare_bs(at_solver *h)
+{
+    h->bs_ok = false;
+    if (!h->kernel_bs) return;
+    if (cudaFuncSetAttribute(h->kernel_bs, cudaFuncAttributeMaxDynamicSharedMemorySize, h->smem) != cudaSuccess) {
+        cudaGetLastError();
+        return;
+    }
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, h->kernel_bs, atk::kThreads, (size_t)h->smem) != cudaSuccess) {
+        cudaGetLastError();
+        return;
+    }
+    h->bs_ok = (int64_t)occ * h->sm_count >= h->G;
 }
 
 }  // namespace
@@ -571,7 +603,8 @@ int at_create(const at_grid *grid, int64_t P, int scheme_order, int L, double nu
     h->comp = comp;
     h->v64 = !comp && viscous_fp64(w, scheme_order, (uint32_t)grid->flags, nu * dt / (dx * dx));
 
-    pick_kernels(w, scheme_order, h->M, grid->forcing_amp != 0.0, h->v64, h->comp, &h->kernel, &h->init_kernel);
+    pick_kernels(w, scheme_order, h->M, grid->forcing_amp != 0.0, h->v64, h->comp, &h->kernel, &h->init_kernel,
+                 &h->kernel_bs);
 
     // launch shape: by default as many CTAs of kWarps processing elements
     // (warps) as can be resident, at most one PE per subdomain; `stages`
@@ -582,6 +615,7 @@ int at_create(const at_grid *grid, int64_t P, int scheme_order, int L, double nu
     int rc2 = launch_shape(h->M, w, P, tab_size(h->M, w, grid->forcing_amp != 0.0, false, comp), grid->max_ctas,
                            stages, sms, smem_optin, h->kernel, &h->G, &h->stages, &h->sl, &h->smem, &h->smax);
     if (rc2 != AT_OK) { delete h; return rc2; }
+    prepare_bs(h);
     h->sb = sb;
     h->step = 0;
     h->has_state = false;
@@ -724,14 +758,14 @@ static int step_impl(at_solver *h, int64_t n_steps, int delay_mode, int8_t *dela
     p.mode = delay_mode;
     p.delays = delays;
     p.n_steps = n_steps;
-    p.sb = levels ? 1 : delay_mode == AT_FREE ? h->sb : delay_mode == AT_SYNC ? sync_pass_len(h) : 1;
+    p.sb = levels ? 1 : delay_mode == AT_FREE ? h->sb : (delay_mode == AT_SYNC && h->bs_ok) ? sync_pass_len(h) : 1;
     // blocked free-running passes alternate their sweep direction; the
     // blocked synchronous passes (a grid barrier before each) need not
     p.alt = (p.sb > 1 && delay_mode == AT_FREE) ? 1 : 0;
     p.strip_words = strip_words(h, p.sb);
     p.levels = levels;
     p.levels_depth = depth;
-    const cudaError_t e = launch_stepper(h, &p);
+    const cudaError_t e = launch_stepper(h, &p, (delay_mode == AT_SYNC && p.sb > 1) ? h->kernel_bs : h->kernel);
     if (e != cudaSuccess) return cuda_fail(e, "cooperative launch of at_stepper");
     h->step += n_steps;
     return AT_OK;
@@ -1032,12 +1066,16 @@ int at_create_batch(const at_grid *grid, int64_t n_inst, const at_instance *inst
     h->kernel = w == 8 ? atk_batch_kernel_f64(scheme_order, gw, full)
                 : comp ? atk_batch_kernel_f32c(scheme_order, gw, full)
                        : atk_batch_kernel_f32(scheme_order, gw, full);
+    h->kernel_bs = w == 8 ? atk_sync_batch_kernel_f64(scheme_order, gw, full)
+                   : comp ? nullptr
+                          : atk_sync_batch_kernel_f32(scheme_order, gw, full);
     h->init_kernel = w == 8 ? atk_init_kernel_f64(scheme_order) : atk_init_kernel_f32(scheme_order);
     int stages = grid->stages > 0 ? grid->stages : 3;
     if (stages < atk::kMinStages) stages = atk::kMinStages;
     rc = launch_shape(M, w, d.P, tab_size(M, w, false, true, comp), grid->max_ctas, stages, sms, smem_optin, h->kernel,
                       &h->G, &h->stages, &h->sl, &h->smem, &h->smax);
     if (rc != AT_OK) { delete h; return rc; }
+    prepare_bs(h);
     h->sb = grid->steps_per_pass > 0 ? grid->steps_per_pass : 1;
     h->step = 0;
     h->has_state = false;
@@ -1084,6 +1122,7 @@ int at_tune(at_solver *h, int64_t n_steps, int delay_mode, at_tune_result *res)
         if (r != AT_OK) return r;
         if (st != sh.stages) return AT_ERR_RESIDENCY;   // did not fit as asked
         h->G = G; h->stages = st; h->sl = sl; h->smem = smem; h->smax = smax; h->sb = sh.sb;
+        prepare_bs(h);
         return AT_OK;
     };
     // time of one at_step(n_steps): one untimed launch, best of two timed
@@ -1115,8 +1154,9 @@ int at_tune(at_solver *h, int64_t n_steps, int delay_mode, at_tune_result *res)
     int tried = 1;
     res->first_ms = best_ms;
     // levels per pass: up to the largest delay bound + 1 (an ensemble's PEs
-    // clamp it to their own smallest bound + 1)
-    const int sb_hi = (delay_mode == AT_FREE || delay_mode == AT_SYNC) ? h->L + 1 : 1;
+    // clamp it to their own smallest bound + 1); the synchronous mode keeps
+    // one level per pass unless the solver was made for blocked passes
+    const int sb_hi = (delay_mode == AT_FREE || (delay_mode == AT_SYNC && h->sb > 1)) ? h->L + 1 : 1;
     for (int st = atk::kMinStages; rc == AT_OK && st <= 4; ++st) {
         int lastG = -1;
         for (int per_sm = 1; rc == AT_OK && per_sm <= 4; ++per_sm) {
@@ -1442,7 +1482,7 @@ extern "C" int at_step_noalloc(const at_grid *grid, int64_t P, int scheme_order,
         p.delays = delays;
         p.n_steps = n_steps;
         p.sb = 1;
-        e = launch_stepper(&h, &p);
+        e = launch_stepper(&h, &p, h.kernel);
         if (e != cudaSuccess) return cuda_fail(e, "cooperative launch of at_stepper");
     }
     return read_status(&h);
@@ -1541,3 +1581,74 @@ int at_moments(at_solver *h, double *out)
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Arithmetic throughput probe (at_fma_peak): the measured FMA rate of this
+// GPU for the roofline of ALU-bound variants (the FP64 state).
+// ---------------------------------------------------------------------------
+namespace {
+
+static __device__ double g_probe_sink;
+
+// kChains independent FMA chains per thread, kUnroll FMAs of each per trip:
+// enough independent work to keep the FMA pipe of every SM issuing.
+constexpr int kProbeChains = 8, kProbeUnroll = 8, kProbeThreads = 256, kProbeCtasPerSm = 8;
+
+template <typename T>
+__global__ void __launch_bounds__(kProbeThreads) at_fma_probe(long long trips, T a, T b, double *sink)
+{
+    T x[kProbeChains];
+#pragma unroll
+    for (int c = 0; c < kProbeChains; ++c) x[c] = (T)(threadIdx.x + c) * (T)1e-3;
+    for (long long t = 0; t < trips; ++t) {
+#pragma unroll
+        for (int u = 0; u < kProbeUnroll; ++u) {
+#pragma unroll
+            for (int c = 0; c < kProbeChains; ++c) x[c] = fma(x[c], a, b);
+        }
+    }
+    T acc = (T)0;
+#pragma unroll
+    for (int c = 0; c < kProbeChains; ++c) acc += x[c];
+    if (acc == (T)-1.2345e30) *sink = (double)acc;   // never true; keeps the chains live
+}
+
+}  // namespace
+
+extern "C" int at_fma_peak(int dtype, int64_t trips, double *fma_per_s)
+{
+    g_err[0] = 0;
+    if (!fma_per_s) return fail(AT_ERR_ARG, "fma_per_s is NULL");
+    if (dtype != AT_F64 && dtype != AT_F32) return fail(AT_ERR_ARG, "dtype must be AT_F64 or AT_F32");
+    if (trips <= 0) return fail(AT_ERR_ARG, "trips must be positive");
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute");
+    void *sink = nullptr;
+    e = cudaGetSymbolAddress(&sink, g_probe_sink);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(probe sink)");
+    cudaEvent_t ev[2];
+    if ((e = cudaEventCreate(&ev[0])) != cudaSuccess) return cuda_fail(e, "cudaEventCreate");
+    if ((e = cudaEventCreate(&ev[1])) != cudaSuccess) { cudaEventDestroy(ev[0]); return cuda_fail(e, "cudaEventCreate"); }
+    const dim3 grid((unsigned)(sms * kProbeCtasPerSm)), block(kProbeThreads);
+    float ms = 0.f;
+    for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {   // the first launch warms up
+        cudaEventRecord(ev[0], 0);
+        if (dtype == AT_F64)
+            at_fma_probe<double><<<grid, block>>>(trips, 0.9999999, 1e-7, static_cast<double *>(sink));
+        else
+            at_fma_probe<float><<<grid, block>>>(trips, 0.9999999f, 1e-7f, static_cast<double *>(sink));
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaEventRecord(ev[1], 0);
+        if (e == cudaSuccess) e = cudaEventSynchronize(ev[1]);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ev[0], ev[1]);
+    }
+    cudaEventDestroy(ev[0]);
+    cudaEventDestroy(ev[1]);
+    if (e != cudaSuccess) return cuda_fail(e, "at_fma_probe");
+    const double fmas = (double)grid.x * kProbeThreads * (double)trips * kProbeUnroll * kProbeChains;
+    *fma_per_s = fmas / (ms * 1e-3);
+    return AT_OK;
+}

@@ -550,7 +550,7 @@ __device__ __forceinline__ T exact_ghost2(const BatchInst *binst, const BatchSub
 // the increment and lo to hi with an error-free two-sum (Knuth), keeping the
 // new error as lo -- so that neither small increments nor the quantisation
 // of the stored field are lost to FP32 rounding.
-template <typename T, int ORDER, int GW, bool FORCED, bool FULL, bool BATCH, int PREC>
+template <typename T, int ORDER, int GW, bool FORCED, bool FULL, bool BATCH, int PREC, bool BS>
 __device__ void run_pe(const Params &p, const Sweep &sw, long long lo, long long hi, uint64_t *bars, unsigned *hist,
                        unsigned char *raw, unsigned char *stages, const T *sj, const T *cj, const T *spt,
                        const T *cpt, const BatchSub *btab, int *s_count, volatile long long *s_epoch)
@@ -569,7 +569,9 @@ __device__ void run_pe(const Params &p, const Sweep &sw, long long lo, long long
     // bit for bit.  Strips are written at the end of each pass (parity of the
     // pass index) and, at the launch start, from the state itself; barrier 1
     // follows that.
-    const bool bsync = p.mode == kModeSync && sw.sb > 1;
+    // (a separate instantiation, BS: the host launches it for AT_SYNC with
+    // passes of more than one level only)
+    constexpr bool bsync = BS;
     const long long ep_off = bsync ? 1 : 0;                 // grid barriers before the first pass
     const long long n_ep = count_passes(sw, S_LEV) + ep_off; // arrivals of this launch
     if (S <= 0) {
@@ -717,7 +719,7 @@ __device__ void run_pe(const Params &p, const Sweep &sw, long long lo, long long
                     p.delays[((c.n - sw.n0 + i) * p.P + c.j) * 2 + f] = (int8_t)(k + kstep * i);
             }
             hk = (int)k;
-            if (bsync) {
+            if constexpr (bsync) {
                 // the neighbour's edge strip at the pass's first level
                 const unsigned char *sb0 = p.strip +
                     ((size_t)((c.pass & 1) * p.P + (bnd ? 0 : q)) * 2 + (1 - f)) * kStripBytes;
@@ -754,7 +756,7 @@ __device__ void run_pe(const Params &p, const Sweep &sw, long long lo, long long
         ++nl;
     };
     bool ok = true;
-    if (bsync) {
+    if constexpr (bsync) {
         // edge strips of the state at the launch's first level (parity 0),
         // then the first grid barrier
         const int sw4 = p.strip_words;
@@ -865,7 +867,7 @@ __device__ void run_pe(const Params &p, const Sweep &sw, long long lo, long long
         const int G = R * len;
         T gv = (T)0;
         T fsl = (T)0, fcl = (T)0, fsr = (T)0, fcr = (T)0;    // forcing factors of the neighbours
-        if (bsync) {
+        if constexpr (bsync) {
             const T *stl = reinterpret_cast<const T *>(rw);
             const T *str = reinterpret_cast<const T *>(rw + kRawFace);
             if (lane < G) gv = stl[p.strip_words - G + lane];
@@ -923,7 +925,7 @@ __device__ void run_pe(const Params &p, const Sweep &sw, long long lo, long long
             const long long lev = n + i + 1;                 // level being computed
             T hl[R], hr[R];
             T hll[R], hrl[R];                                // lo words (compensated state)
-            if (bsync) {
+            if constexpr (bsync) {
                 // the halo of level n+i from the ghost lanes (an ensemble's
                 // domain ends: the exact values)
 #pragma unroll
@@ -1123,19 +1125,19 @@ __device__ void run_pe(const Params &p, const Sweep &sw, long long lo, long long
             }
         };
         for (int i = 0; i < len; ++i) level(i, c, c);
-        if (bsync) {
+        if constexpr (bsync) {
             // edge strips of the pass's last level for the next pass
             const int gq = p.strip_words / 4;
             T *s0 = reinterpret_cast<T *>(p.strip + ((size_t)(((C.pass + 1) & 1) * p.P + j) * 2) * kStripBytes);
             T *s1 = reinterpret_cast<T *>(reinterpret_cast<unsigned char *>(s0) + kStripBytes);
-            bool wrote = false;
+            // (read after the next grid barrier: the warp barrier at the end
+            // of this tile and the fence of the arrival order them before it)
 #pragma unroll
             for (int m = 0; m < GW; ++m) {
                 const int g = lane + 32 * m;
-                if (g < gq) { stg4<T>(s0 + 4 * g, c[m]); wrote = true; }
-                if (g >= NG - gq && g < NG) { stg4<T>(s1 + 4 * (g - (NG - gq)), c[m]); wrote = true; }
+                if (g < gq) stg4<T>(s0 + 4 * g, c[m]);
+                if (g >= NG - gq && g < NG) stg4<T>(s1 + 4 * (g - (NG - gq)), c[m]);
             }
-            if (wrote) __threadfence();
         }
         // the next tile; before a turn the words stay in registers
         Cursor Cn = C;
@@ -1189,7 +1191,7 @@ __device__ void run_pe(const Params &p, const Sweep &sw, long long lo, long long
 // ---------------------------------------------------------------------------
 // the persistent kernel
 // ---------------------------------------------------------------------------
-template <typename T, int ORDER, int GW, bool FORCED, bool FULL, bool BATCH, int PREC>
+template <typename T, int ORDER, int GW, bool FORCED, bool FULL, bool BATCH, int PREC, bool BS>
 __global__ void __launch_bounds__(kThreads, AT_MIN_CTAS_PER_SM) at_stepper(const Params p)
 {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -1252,8 +1254,8 @@ __global__ void __launch_bounds__(kThreads, AT_MIN_CTAS_PER_SM) at_stepper(const
         if (p.mode != kModeSync && sw.sb > lmin + 1) sw.sb = lmin + 1;
     }
     __syncthreads();
-    run_pe<T, ORDER, GW, FORCED, FULL, BATCH, PREC>(p, sw, lo, hi, bars, hist, raw, stages, sj, cj, spt, cpt, btab,
-                                                   &s_count, &s_epoch);
+    run_pe<T, ORDER, GW, FORCED, FULL, BATCH, PREC, BS>(p, sw, lo, hi, bars, hist, raw, stages, sj, cj, spt, cpt,
+                                                       btab, &s_count, &s_epoch);
     // the last CTA to finish advances the level of the state and rearms the
     // grid barrier for the next launch (every CTA has read the level by now)
     __syncthreads();
@@ -1333,35 +1335,40 @@ __global__ void at_restore(const Params p, const T *levels, long long depth, lon
 // ---------------------------------------------------------------------------
 namespace atk {
 
-template <typename T, int ORDER, bool FORCED, bool FULL, bool BATCH, int PREC>
+template <typename T, int ORDER, bool FORCED, bool FULL, bool BATCH, int PREC, bool BS>
 void *stepper_gw(int gw)
 {
     switch (gw) {
-    case 1: return (void *)at_stepper<T, ORDER, 1, FORCED, FULL, BATCH, PREC>;
-    case 2: return (void *)at_stepper<T, ORDER, 2, FORCED, FULL, BATCH, PREC>;
-    case 4: return (void *)at_stepper<T, ORDER, 4, FORCED, FULL, BATCH, PREC>;
-    default: return (void *)at_stepper<T, ORDER, 8, FORCED, FULL, BATCH, PREC>;
+    case 1: return (void *)at_stepper<T, ORDER, 1, FORCED, FULL, BATCH, PREC, BS>;
+    case 2: return (void *)at_stepper<T, ORDER, 2, FORCED, FULL, BATCH, PREC, BS>;
+    case 4: return (void *)at_stepper<T, ORDER, 4, FORCED, FULL, BATCH, PREC, BS>;
+    default: return (void *)at_stepper<T, ORDER, 8, FORCED, FULL, BATCH, PREC, BS>;
     }
 }
 
-template <typename T, int ORDER, bool FORCED, bool BATCH, int PREC>
+template <typename T, int ORDER, bool FORCED, bool BATCH, int PREC, bool BS>
 void *stepper_full(int gw, bool full)
 {
-    return full ? stepper_gw<T, ORDER, FORCED, true, BATCH, PREC>(gw) : stepper_gw<T, ORDER, FORCED, false, BATCH, PREC>(gw);
+    return full ? stepper_gw<T, ORDER, FORCED, true, BATCH, PREC, BS>(gw)
+                : stepper_gw<T, ORDER, FORCED, false, BATCH, PREC, BS>(gw);
 }
 
 // Stepper for stencil order 2|4, gw groups of 4 points per lane (1, 2, 4 or
 // 8), with or without forcing (single domain only), full tiles (M = 128 gw)
-// or not; PREC 1: FP64 viscous accumulation, 2: compensated state.
-template <typename T, bool BATCH, int PREC = 0>
+// or not; PREC 1: FP64 viscous accumulation, 2: compensated state; BS: the
+// blocked synchronous mode (AT_SYNC in passes of more than one level).
+template <typename T, bool BATCH, int PREC = 0, bool BS = false>
 void *stepper_kernel(int order, int gw, bool forced, bool full)
 {
     if constexpr (BATCH) {
-        return order == 2 ? stepper_full<T, 2, false, true, PREC>(gw, full) : stepper_full<T, 4, false, true, PREC>(gw, full);
+        return order == 2 ? stepper_full<T, 2, false, true, PREC, BS>(gw, full)
+                          : stepper_full<T, 4, false, true, PREC, BS>(gw, full);
     } else {
         if (order == 2)
-            return forced ? stepper_full<T, 2, true, false, PREC>(gw, full) : stepper_full<T, 2, false, false, PREC>(gw, full);
-        return forced ? stepper_full<T, 4, true, false, PREC>(gw, full) : stepper_full<T, 4, false, false, PREC>(gw, full);
+            return forced ? stepper_full<T, 2, true, false, PREC, BS>(gw, full)
+                          : stepper_full<T, 2, false, false, PREC, BS>(gw, full);
+        return forced ? stepper_full<T, 4, true, false, PREC, BS>(gw, full)
+                      : stepper_full<T, 4, false, false, PREC, BS>(gw, full);
     }
 }
 

@@ -6,3 +6,4 @@ __attribute__((visibility("hidden"))) void *atk_stepper_kernel_f32v(int order, i
 {
     return atk::stepper_kernel<float, false, 1>(order, gw, forced, full);
 }
+

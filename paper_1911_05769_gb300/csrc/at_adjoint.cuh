@@ -1,8 +1,10 @@
 // at_adjoint.cuh -- discrete adjoint of the AT time step (reverse mode).
 //
-// One launch takes lambda^{n+1} = dJ/du^{n+1} to lambda^n = dJ/du^n for a
+// One step takes lambda^{n+1} = dJ/du^{n+1} to lambda^n = dJ/du^n for a
 // scalar J of the final level, given the stored level u^n, the levels the
 // delayed halos of level n were extrapolated from, and the delays of level n.
+// One cooperative launch takes the steps of a whole checkpoint interval,
+// n_hi - 1 down to n_lo, with a grid barrier (bounded) between steps.
 //
 // The forward step (Sec. 3.2, Eq. BS, AT halos of Eq. AT1/AT2 in split form)
 // writes u^{n+1}_i = v_0 + cB b(v) - cA v_0 a(v) (+ forcing, independent of u
@@ -31,19 +33,21 @@ namespace atk {
 constexpr int kAdjMaxLevels = 20;   // levels n .. n-L-s+1 a step reads (L <= 16, s <= 3)
 
 struct AdjParams {
-    const void *levels;        // full fields of the stored levels, N words each
-    long long lvl_off[kAdjMaxLevels];   // word offset of level n - q in `levels` (q = 0 .. L+s-1)
-    const void *lam_in;        // lambda^{n+1}, N words
-    void *lam_out;             // lambda^n, N words
+    const void *levels;        // full fields of the stored levels, N words each: level l in slot l mod Dl
+    long long Dl;
+    void *lam_a, *lam_b;       // lambda, N words each: lambda^{n_hi} in lam_a, then alternating
     void *pend;                // [Tp][P][2][R] words: adjoint of boundary values at older levels
-    double *dnu_part;          // [gridDim.x] running FP64 sums of dJ/dnu
+    double *dnu_part;          // [gridDim.x * gridDim.y] running FP64 sums of dJ/dnu
     const int8_t *delays;      // delays of level n at delays[(n - k_level) * P * 2 + p * 2 + face]
     long long k_level;         // level of the delays' first row
     long long N, P, M;
     int L, Tp;                 // Tp: a power of two
     double cA, cB, dtdx2;      // as the stepper's; dtdx2 = cB / nu
     float cAf, cBf, dtdx2f;    // the same in FP32 (FP32 kernels convert nothing per point)
-    long long n;               // level of lambda_out
+    long long n_hi, n_lo;      // this launch: lambda^{n_hi} -> lambda^{n_lo}, n_hi > n_lo
+    unsigned long long *bar;   // grid-barrier arrivals, zero at the launch
+    int *ctrl;                 // the solver's control block (status, abort word)
+    long long timeout_ns;      // bound of each grid-barrier wait
 };
 
 template <int ORDER>
@@ -60,22 +64,25 @@ struct Coeffs<4> {
     static __device__ __forceinline__ int beta(int j) { return j == 0 ? -30 : (j == 1 || j == -1) ? 16 : -1; }
 };
 
-// Per-launch view of the stored levels and the adjoint fields, with 32-bit
-// indices within a level (the host checks N < 2^31).
+// Per-step view of the stored levels and the adjoint fields, with 32-bit
+// indices within a level (the host checks N < 2^31); off[q] is the word
+// offset of level n - q in the stored levels (in shared memory).
 template <typename T, int ORDER>
 struct AdjStep {
     static constexpr int R = ORDER / 2;
     static constexpr int S_LEV = ORDER / 2 + 1;
     const AdjParams &a;
+    long long n;               // level of the lambda being computed
+    const long long *off;
     const T *lev;              // stored levels
     const T *un;               // level n
     const T *lam;              // lambda^{n+1}
     int M, P;
     T cA, cB;
 
-    __device__ explicit AdjStep(const AdjParams &p)
-        : a(p), lev(reinterpret_cast<const T *>(p.levels)), un(reinterpret_cast<const T *>(p.levels) + p.lvl_off[0]),
-          lam(reinterpret_cast<const T *>(p.lam_in)), M((int)p.M), P((int)p.P)
+    __device__ AdjStep(const AdjParams &p, long long n_, const long long *off_, const T *lam_)
+        : a(p), n(n_), off(off_), lev(reinterpret_cast<const T *>(p.levels)),
+          un(reinterpret_cast<const T *>(p.levels) + off_[0]), lam(lam_), M((int)p.M), P((int)p.P)
     {
         if constexpr (sizeof(T) == 4) { cA = p.cAf; cB = p.cBf; }
         else { cA = (T)p.cA; cB = (T)p.cB; }
@@ -86,8 +93,8 @@ struct AdjStep {
     // forward run clamps it (no level below 0, at most L)
     __device__ int delay(int p, int f) const
     {
-        int k = a.delays[((size_t)(a.n - a.k_level) * a.P + p) * 2 + f];
-        long long kmax = a.n - S_LEV + 1;
+        int k = a.delays[((size_t)(n - a.k_level) * a.P + p) * 2 + f];
+        long long kmax = n - S_LEV + 1;
         if (kmax < 0) kmax = 0;
         if (kmax > a.L) kmax = a.L;
         if (k > kmax) k = (int)kmax;
@@ -99,13 +106,13 @@ struct AdjStep {
     // the stepper's halo approximation)
     __device__ T halo(int src, int k) const
     {
-        const T r0 = lev[a.lvl_off[k] + src];
+        const T r0 = lev[off[k] + src];
         if (k == 0) return r0;
-        const T r1 = lev[a.lvl_off[k + 1] + src];
+        const T r1 = lev[off[k + 1] + src];
         if constexpr (S_LEV == 2) {
             return (T)(k + 1) * r0 - (T)k * r1;
         } else {
-            const T r2 = lev[a.lvl_off[k + 2] + src];
+            const T r2 = lev[off[k + 2] + src];
             const T w0 = (T)((k + 1) * (k + 2) / 2);
             const T w1 = (T)(-k * (k + 2));
             const T w2 = (T)(k * (k + 1) / 2);
@@ -155,19 +162,20 @@ constexpr int kAdjThreads = 256;
 constexpr int kAdjPts = 4;                            // points per thread
 constexpr int kAdjChunk = kAdjThreads * kAdjPts;      // points per block and subdomain
 
+// One step, lambda^{n+1} (lam_in) -> lambda^n (lam_out), by this block;
+// returns the block's FP64 contribution to dJ/dnu (thread 0).
 template <typename T, int ORDER>
-__global__ void __launch_bounds__(kAdjThreads, ORDER == 2 ? 7 : 3) at_adjoint_step(const AdjParams a)
+__device__ double adjoint_level(const AdjParams &a, long long n, const long long *s_off, const T *lam_in, T *lam_out,
+                                T (*s_c)[kAdjChunk], T *red)
 {
     constexpr int R = ORDER / 2;
     constexpr int S_LEV = ORDER / 2 + 1;
-    const AdjStep<T, ORDER> A(a);
-    __shared__ T s_c[2 * R + 1][kAdjChunk];
+    const AdjStep<T, ORDER> A(a, n, s_off, lam_in);
     T nu_acc = (T)0;          // this thread's sum of lambda^{n+1}_i b_i
     const T dtdx2 = sizeof(T) == 4 ? (T)a.dtdx2f : (T)a.dtdx2;
     const int tid = threadIdx.x, lane = tid & 31;
     const int M = A.M;
     const int chunk_lo = blockIdx.y * kAdjChunk;
-    T *lam_out = reinterpret_cast<T *>(a.lam_out);
     for (int p = blockIdx.x; p < A.P; p += gridDim.x) {
         const int pl = A.left(p), pr = A.right(p);
         // loads that need no delay first (lambda^{n+1}; the pending words
@@ -177,7 +185,7 @@ __global__ void __launch_bounds__(kAdjThreads, ORDER == 2 ? 7 : 3) at_adjoint_st
         for (int kp = 0; kp < kAdjPts; ++kp) {
             const int loc = chunk_lo + tid + kp * kAdjThreads;
             gl[kp] = loc < M ? A.lam[p * M + loc] : (T)0;
-            pw[kp] = loc < R ? *A.pend(a.n, p, 0, loc) : (loc >= M - R && loc < M) ? *A.pend(a.n, p, 1, loc - (M - R)) : (T)0;
+            pw[kp] = loc < R ? *A.pend(n, p, 0, loc) : (loc >= M - R && loc < M) ? *A.pend(n, p, 1, loc - (M - R)) : (T)0;
         }
         // delays (lanes 0..3, then shared across the warp): this subdomain's
         // faces 0, 1; the left neighbour's face 1; the right neighbour's face 0
@@ -242,10 +250,10 @@ __global__ void __launch_bounds__(kAdjThreads, ORDER == 2 ? 7 : 3) at_adjoint_st
             // delayed reads from later steps addressed to level n (loaded above)
             if (loc < R) {
                 acc += pw[kp];
-                *A.pend(a.n, p, 0, loc) = (T)0;
+                *A.pend(n, p, 0, loc) = (T)0;
             } else if (loc >= M - R) {
                 acc += pw[kp];
-                *A.pend(a.n, p, 1, loc - (M - R)) = (T)0;
+                *A.pend(n, p, 1, loc - (M - R)) = (T)0;
             }
             lam_out[i] = acc;
 
@@ -287,29 +295,95 @@ __global__ void __launch_bounds__(kAdjThreads, ORDER == 2 ? 7 : 3) at_adjoint_st
                 for (int m = 0; m < S_LEV; ++m)
 #pragma unroll
                     for (int r = 0; r < R; ++r)
-                        old[m][r] = (k + m == 0 || w[m] == (T)0) ? (T)0 : *A.pend(a.n - k - m, q, side, r);
+                        old[m][r] = (k + m == 0 || w[m] == (T)0) ? (T)0 : *A.pend(n - k - m, q, side, r);
 #pragma unroll
                 for (int m = 0; m < S_LEV; ++m) {
                     if (k + m == 0 || w[m] == (T)0) continue;     // level n: gathered above
 #pragma unroll
-                    for (int r = 0; r < R; ++r) *A.pend(a.n - k - m, q, side, r) = old[m][r] + w[m] * src[r];
+                    for (int r = 0; r < R; ++r) *A.pend(n - k - m, q, side, r) = old[m][r] + w[m] * src[r];
                 }
             }
         }
     }
     // dJ/dnu of this block: warp sums in the state's precision, then the
-    // block's FP64 running total (one FP64 add per warp: FP64 is slow here)
+    // block's FP64 sum (one FP64 add per warp: FP64 is slow here)
     for (int o = 16; o > 0; o >>= 1) nu_acc += __shfl_xor_sync(0xffffffffu, nu_acc, o);
-    __shared__ T red[kAdjThreads / 32];
     if (lane == 0) red[tid >> 5] = nu_acc;
     __syncthreads();
-    if (tid == 0) {
-        double sum = 0.0;
+    double sum = 0.0;
+    if (tid == 0)
         for (int w = 0; w < kAdjThreads / 32; ++w) sum += (double)red[w] * (double)dtdx2;
-        // one add per block and launch into the block's own running total: a
-        // reduction without return (no load on the block's critical path);
-        // launches are stream-ordered, so the order of the adds is fixed
-        atomicAdd(a.dnu_part + (size_t)blockIdx.y * gridDim.x + blockIdx.x, sum);
+    return sum;
+}
+
+// Grid barrier between the steps of an interval: every block arrives once
+// per step (thread 0, after a block barrier and a fence) and waits for all;
+// bounded by timeout_ns, after which the status and abort words are set and
+// every block leaves.  Returns false on abort.
+static __device__ __noinline__ bool adjoint_grid_sync(const AdjParams &a, unsigned long long target, long long n,
+                                               int *s_ok)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(a.bar, 1ull);
+        bool ok = true;
+        if (ld_acquire(a.bar) < target) {
+            const unsigned long long t0 = global_ns();
+            for (;;) {
+                __nanosleep(32);
+                if (ld_acquire(a.bar) >= target) break;
+                if (ld_relaxed(a.ctrl + kCtrlAbort)) { ok = false; break; }
+                if ((long long)(global_ns() - t0) > a.timeout_ns) {
+                    if (atomicCAS(a.ctrl + kCtrlStatus, 0, kStatusTimeout) == 0) {
+                        a.ctrl[kCtrlCta] = (int)(blockIdx.y * gridDim.x + blockIdx.x);
+                        a.ctrl[kCtrlWhere] = kWhereAdjoint;
+                        a.ctrl[kCtrlNb] = -1;
+                        a.ctrl[kCtrlStep] = (int)n;
+                    }
+                    atomicExch(a.ctrl + kCtrlAbort, 1);
+                    ok = false;
+                    break;
+                }
+            }
+        }
+        __threadfence();
+        *s_ok = ok ? 1 : 0;
+    }
+    __syncthreads();
+    return *s_ok != 0;
+}
+
+// The steps n_hi - 1 .. n_lo of one checkpoint interval in one cooperative
+// launch (every block resident): lambda^{n_hi} in lam_a, lambda^{n_lo} in
+// lam_a or lam_b after an even or odd number of steps.  Each block adds its
+// dJ/dnu contribution of every step into its own FP64 running total, in the
+// order of the steps.
+template <typename T, int ORDER>
+__global__ void __launch_bounds__(kAdjThreads, ORDER == 2 ? 7 : 3) at_adjoint_interval(const AdjParams a)
+{
+    constexpr int R = ORDER / 2;
+    __shared__ T s_c[2 * R + 1][kAdjChunk];
+    __shared__ T red[kAdjThreads / 32];
+    __shared__ long long s_off[kAdjMaxLevels];
+    __shared__ int s_ok;
+    const int tid = threadIdx.x;
+    unsigned long long arrivals = 0;
+    const unsigned long long nblocks = (unsigned long long)gridDim.x * gridDim.y;
+    for (long long n = a.n_hi - 1, it = 0; n >= a.n_lo; --n, ++it) {
+        // word offsets of the levels n, n-1, ..., n-L-s+1 in the stored ring
+        if (tid < kAdjMaxLevels) s_off[tid] = (n - tid >= 0) ? ((n - tid) % a.Dl) * a.N : 0;
+        __syncthreads();
+        const T *lam_in = reinterpret_cast<const T *>((it & 1) ? a.lam_b : a.lam_a);
+        T *lam_out = reinterpret_cast<T *>((it & 1) ? a.lam_a : a.lam_b);
+        const double sum = adjoint_level<T, ORDER>(a, n, s_off, lam_in, lam_out, s_c, red);
+        // one add per block and step into the block's own running total: a
+        // reduction without return (no load on the block's critical path)
+        if (tid == 0) atomicAdd(a.dnu_part + (size_t)blockIdx.y * gridDim.x + blockIdx.x, sum);
+        if (n > a.n_lo) {
+            arrivals += nblocks;
+            if (!adjoint_grid_sync(a, arrivals, n, &s_ok)) return;
+        }
     }
 }
 

@@ -1205,7 +1205,7 @@ int adj_grid_y(const at_solver *h) { return (int)((h->M + atk::kAdjChunk - 1) / 
 int adj_blocks(const at_solver *h) { return adj_grid_x(h) * adj_grid_y(h); }
 
 struct AdjLayout {
-    size_t levels, lam, pend, dnu, kbuf, total;
+    size_t levels, lam, pend, dnu, bar, kbuf, total;
 };
 
 AdjLayout adj_layout(const at_solver *h, int64_t interval)
@@ -1216,6 +1216,7 @@ AdjLayout adj_layout(const at_solver *h, int64_t interval)
     l.lam = off;    off = align_up(off + (size_t)h->N * h->w, 256);
     l.pend = off;   off = align_up(off + (size_t)h->T * h->P * 2 * h->R * h->w, 256);
     l.dnu = off;    off = align_up(off + (size_t)adj_blocks(h) * 8, 256);
+    l.bar = off;    off = align_up(off + 8, 256);
     l.kbuf = off;   off = align_up(off + (size_t)interval * h->P * 2, 256);
     l.total = off;
     return l;
@@ -1304,8 +1305,12 @@ int at_adjoint(at_solver *h, int64_t n_steps, int delay_mode, const int8_t *dela
 
     atk::AdjParams a{};
     a.levels = ws + al.levels;
+    a.Dl = Dl;
     a.pend = ws + al.pend;
     a.dnu_part = reinterpret_cast<double *>(ws + al.dnu);
+    a.bar = reinterpret_cast<unsigned long long *>(ws + al.bar);
+    a.ctrl = reinterpret_cast<int *>(h->ws + h->lay.ctrl);
+    a.timeout_ns = h->g.timeout_ns;
     a.N = h->N; a.P = h->P; a.M = h->M;
     a.L = h->L; a.Tp = h->T;
     if (h->order == 2) {
@@ -1319,6 +1324,14 @@ int at_adjoint(at_solver *h, int64_t n_steps, int delay_mode, const int8_t *dela
     }
     a.cAf = (float)a.cA; a.cBf = (float)a.cB; a.dtdx2f = (float)a.dtdx2;
     void *kern = atk_adjoint_kernel(h->w, h->order);
+    // one cooperative launch per interval: every block resident
+    int occ = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, atk::kAdjThreads, 0);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor(adjoint)");
+    const int gy = adj_grid_y(h);
+    int gx = adj_grid_x(h);
+    if ((int64_t)gx * gy > (int64_t)occ * h->sm_count) gx = (int)((int64_t)occ * h->sm_count / gy);
+    if (gx < 1) return fail(AT_ERR_RESIDENCY, "adjoint: %d blocks per subdomain cannot be co-resident", gy);
     unsigned char *cur = static_cast<unsigned char *>(lam), *other = ws + al.lam;
     for (int64_t seg = nseg - 1; seg >= 0; --seg) {
         const int64_t c = seg * interval;
@@ -1337,19 +1350,28 @@ int at_adjoint(at_solver *h, int64_t n_steps, int delay_mode, const int8_t *dela
                                             : reinterpret_cast<int8_t *>(ws + al.kbuf);
         rc = step_impl(h, end - c, delay_mode, d, ws + al.levels, Dl);
         if (rc != AT_OK) return rc;
+        if (end == c) continue;
         a.delays = d;
         a.k_level = c;
-        for (int64_t n = end - 1; n >= c; --n) {
-            a.n = n;
-            for (int q = 0; q < atk::kAdjMaxLevels; ++q)
-                a.lvl_off[q] = n - q >= 0 ? (long long)((n - q) % Dl) * h->N : 0;
-            a.lam_in = cur;
-            a.lam_out = other;
-            void *args[] = {&a};
-            e = cudaLaunchKernel(kern, dim3(adj_grid_x(h), adj_grid_y(h)), dim3(atk::kAdjThreads), args, 0, h->stream);
-            if (e != cudaSuccess) return cuda_fail(e, "launch at_adjoint_step");
-            unsigned char *t = cur; cur = other; other = t;
-        }
+        a.n_hi = end;
+        a.n_lo = c;
+        a.lam_a = cur;
+        a.lam_b = other;
+        e = cudaMemsetAsync(a.bar, 0, 8, h->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(adjoint barrier)");
+        cudaLaunchConfig_t cfg{};
+        cfg.gridDim = dim3(gx, gy);
+        cfg.blockDim = dim3(atk::kAdjThreads);
+        cfg.stream = h->stream;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeCooperative;
+        attr[0].val.cooperative = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        void *args[] = {&a};
+        e = cudaLaunchKernelExC(&cfg, kern, args);
+        if (e != cudaSuccess) return cuda_fail(e, "cooperative launch of at_adjoint_interval");
+        if ((end - c) & 1) { unsigned char *t = cur; cur = other; other = t; }
     }
     if (cur != lam) {
         e = cudaMemcpyAsync(lam, cur, lvl, cudaMemcpyDeviceToDevice, h->stream);

@@ -12,6 +12,19 @@
 
 namespace atk {
 
+// Control block words (the solver's workspace).  kCtrlN0 (64-bit, words 8-9)
+// is the time level of the state: every launch reads it at its start and the
+// last CTA to finish advances it, so that a launch replayed from a captured
+// graph continues where the previous one stopped.  kCtrlDone counts finished
+// CTAs.  A bounded wait that expires latches kStatusTimeout with where it
+// happened and raises the abort word that every other wait polls.
+enum : int {
+    kCtrlStatus = 0, kCtrlAbort = 1, kCtrlCta = 2, kCtrlWhere = 3, kCtrlNb = 4, kCtrlStep = 5,
+    kCtrlN0 = 8, kCtrlDone = 10, kCtrlWords = 16
+};
+enum : int { kWhereTile = 1, kWhereRing = 2, kWhereFlag = 3, kWhereGrid = 4, kWhereAdjoint = 5 };
+constexpr int kStatusTimeout = -5;
+
 __device__ __forceinline__ unsigned smem_addr(const void *p)
 {
     return static_cast<unsigned>(__cvta_generic_to_shared(p));

@@ -57,16 +57,6 @@ constexpr int kMaxL = 16;
 constexpr int kMinStages = 2;                     // stages per PE (tile in use + one ahead)
 
 enum : int { kModeSync = 0, kModeSeeded = 1, kModeFree = 2, kModeReplay = 3 };
-// Control block words.  kCtrlN0 (64-bit, words 8-9) is the time level of the
-// state: every launch reads it at its start and the last CTA to finish
-// advances it, so that a launch replayed from a captured graph continues
-// where the previous one stopped.  kCtrlDone counts finished CTAs.
-enum : int {
-    kCtrlStatus = 0, kCtrlAbort = 1, kCtrlCta = 2, kCtrlWhere = 3, kCtrlNb = 4, kCtrlStep = 5,
-    kCtrlN0 = 8, kCtrlDone = 10, kCtrlWords = 16
-};
-enum : int { kWhereTile = 1, kWhereRing = 2, kWhereFlag = 3, kWhereGrid = 4 };
-constexpr int kStatusTimeout = -5;
 
 // Shared-memory layout of one CTA, shared by the host (launch set-up) and the
 // kernel: per PE `stages` mbarriers, delay counters, two raw-level buffers and

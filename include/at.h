@@ -126,7 +126,13 @@ typedef struct at_grid {
                             /* a barrier every step; the count is reduced until  */
                             /* a strip fits 16 words, 64 bytes and one subdomain */
                             /* (one level per pass with AT_FLAG_COMPENSATED)      */
-  int32_t  reserved;
+  int32_t  tile_subdomains;  /* ensembles: subdomains per tile (0 or 1: one; 2 or  */
+                            /* 4 with M of 128, 256 or 512 and K M <= 1024): in   */
+                            /* AT_FREE and AT_SYNC a tile advances K consecutive  */
+                            /* subdomains of an instance together, the faces      */
+                            /* between them at delay 0 (recorded as such);        */
+                            /* AT_SEEDED and AT_REPLAY take one subdomain per     */
+                            /* tile.  Single domain: must be 0                    */
   int64_t  sub[3];          /* dim 3: points per subdomain along x, y, z; n[a] a  */
                             /* multiple of sub[a]; P = product of n[a] / sub[a]   */
 } at_grid;
@@ -146,6 +152,7 @@ typedef struct at_info {
   int32_t dtype;            /* AT_F64 or AT_F32                                    */
   int32_t steps_per_pass;   /* levels per pass (AT_FREE; AT_SYNC as reduced above) */
   int32_t viscous_fp64;     /* 1 if the viscous term is accumulated in FP64        */
+  int32_t tile_subdomains;  /* ensembles: subdomains per tile in AT_FREE / AT_SYNC  */
 } at_info;
 
 /* Bytes of workspace needed for this problem, or 0 if the arguments are
@@ -308,6 +315,8 @@ typedef struct at_tune_result {
   int32_t n_tried;                        /* shapes timed                          */
   double  best_ms;                        /* its time for at_step(n_steps)          */
   double  first_ms;                       /* time of the shape the solver had      */
+  int32_t tile_subdomains;                /* ensembles: subdomains per tile        */
+  int32_t pad_;
 } at_tune_result;
 
 /* Times at_step(h, n_steps, delay_mode, NULL) for every launch shape above

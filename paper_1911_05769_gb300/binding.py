@@ -52,7 +52,7 @@ class at_grid(ctypes.Structure):
         ("forcing_amp", ctypes.c_double), ("seed", ctypes.c_uint64),
         ("workspace", ctypes.c_void_p), ("workspace_bytes", ctypes.c_size_t), ("stream", ctypes.c_void_p),
         ("timeout_ns", ctypes.c_int64), ("max_ctas", ctypes.c_int32), ("stages", ctypes.c_int32),
-        ("test_skip_step", ctypes.c_int64), ("steps_per_pass", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("test_skip_step", ctypes.c_int64), ("steps_per_pass", ctypes.c_int32), ("tile_subdomains", ctypes.c_int32),
         ("sub", ctypes.c_int64 * 3),
     ]
 
@@ -64,6 +64,7 @@ class at_info(ctypes.Structure):
         ("T", ctypes.c_int32), ("ctas", ctypes.c_int32), ("threads", ctypes.c_int32), ("stages", ctypes.c_int32),
         ("smem_bytes", ctypes.c_int64), ("step", ctypes.c_int64), ("sm_count", ctypes.c_int32),
         ("dtype", ctypes.c_int32), ("steps_per_pass", ctypes.c_int32), ("viscous_fp64", ctypes.c_int32),
+        ("tile_subdomains", ctypes.c_int32),
     ]
 
 
@@ -80,6 +81,7 @@ class at_tune_result(ctypes.Structure):
     _fields_ = [
         ("ctas", ctypes.c_int32), ("stages", ctypes.c_int32), ("steps_per_pass", ctypes.c_int32),
         ("n_tried", ctypes.c_int32), ("best_ms", ctypes.c_double), ("first_ms", ctypes.c_double),
+        ("tile_subdomains", ctypes.c_int32), ("pad_", ctypes.c_int32),
     ]
 
 

@@ -14,6 +14,7 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <algorithm>
 #include <vector>
 
 #include "at.h"
@@ -74,7 +75,7 @@ int ring_slots(int L, int s)
 }
 
 struct Layout {
-    size_t u, ring, flag, ctrl, hist, gbar, bsub, binst, ur, strip, total;
+    size_t u, ring, flag, ctrl, hist, gbar, bsub, binst, ur, strip, tiles, order, total;
 };
 
 // Workspace: state, ring buffers [T][P][2], flags [P][2], control block,
@@ -95,10 +96,15 @@ Layout layout(int64_t N, int64_t P, int w, int L, int T, int64_t n_inst = 0, boo
     l.strip = off;   // blocked synchronous mode: edge strips [2][P][2]
     if (strips) off = align_up(off + (size_t)2 * P * 2 * atk::kStripBytes, 256);
     l.bsub = off; l.binst = off;
+    l.tiles = off; l.order = off;
     if (n_inst > 0) {
         off = align_up(off + (size_t)P * sizeof(atk::BatchSub), 256);
         l.binst = off;
         off = align_up(off + (size_t)n_inst * sizeof(atk::BatchInst), 256);
+        l.tiles = off;   // two tile lists [2][P] (one subdomain per tile; K per tile)
+        off = align_up(off + (size_t)2 * P * sizeof(int4), 256);
+        l.order = off;   // the lists' enumeration of the subdomains [P]
+        off = align_up(off + (size_t)P * sizeof(int), 256);
     }
     l.total = off;
     return l;
@@ -181,6 +187,8 @@ int check_args(const at_grid *g, int64_t P, int order, int L)
     if (!(g->length[0] > 0.0)) return fail(AT_ERR_ARG, "length[0] must be positive");
     if (g->steps_per_pass < 0 || g->steps_per_pass > L + 1)
         return fail(AT_ERR_ARG, "steps_per_pass must be in 0..L+1 (the delay bound), got %d", g->steps_per_pass);
+    if (g->tile_subdomains > 1 || g->tile_subdomains < 0)
+        return fail(AT_ERR_ARG, "tile_subdomains is for ensembles (0 or 1 for a single domain)");
     return AT_OK;
 }
 
@@ -236,13 +244,15 @@ struct TabSize {
     long long fixed, per_sub;
     bool comp;
     int extra;
+    int64_t ntk;     // ensembles: tiles of the multi-subdomain list (0: single domain)
+    int k;           // ensembles: most subdomains per tile
 };
 
-TabSize tab_size(int64_t M, int w, bool forced, bool batch, bool comp = false)
+TabSize tab_size(int64_t M, int w, bool forced, bool batch, bool comp = false, int64_t ntk = 0, int k = 1)
 {
-    if (batch) return {0, (long long)sizeof(atk::BatchSub), comp, 0};
-    if (forced) return {2LL * M * w, 2LL * w, comp, 2};
-    return {0, 0, comp, 0};
+    if (batch) return {0, (long long)sizeof(atk::BatchSub), comp, 0, ntk, k};
+    if (forced) return {2LL * M * w, 2LL * w, comp, 2, 0, 1};
+    return {0, 0, comp, 0, 0, 1};
 }
 
 // Chooses the CTA count (all co-resident CTAs unless max_ctas is set, at most
@@ -252,9 +262,16 @@ int launch_shape(int64_t M, int w, int64_t P, TabSize tsz, int max_ctas, int sta
                  void *kernel, int *G_out, int *stages_out, atk::SmemLayout *sl_out, int *smem_out,
                  long long *smax_out)
 {
+    if (M < 4 || M > atk::kMaxM) return fail(AT_ERR_ARG, "tile of %lld points (4..%d)", (long long)M, atk::kMaxM);
     auto layout_for = [&](int G, int st, long long *smax) {
         const int64_t E = (int64_t)G * atk::kWarps;
+        // records per PE: the most tiles of one PE times the subdomains a tile
+        // may have, over both tile lists of an ensemble
         *smax = (P + E - 1) / E;
+        if (tsz.ntk > 0 && tsz.k > 1) {
+            const long long sk = (tsz.ntk + E - 1) / E * tsz.k;
+            if (sk > *smax) *smax = sk;
+        }
         const long long tab = tsz.fixed + (long long)atk::kWarps * (*smax + tsz.extra) * tsz.per_sub;
         return atk::smem_layout(M, w, st, tab, tsz.comp);
     };
@@ -317,6 +334,11 @@ struct at_solver {
     bool batch;                // ensemble of instances
     int64_t n_inst;
     int lmin;                  // smallest delay bound (ensembles), else L
+    int K;                     // ensembles: subdomains per tile of the AT_FREE / AT_SYNC list
+    int64_t ntiles_k;          // ensembles: tiles of that list
+    std::vector<atk::BatchSub> bsub_host;   // ensembles: the subdomain records (tile planning)
+    std::vector<at_instance> inst_host;     // ensembles: the instances
+    const void *flags_list;    // tile list of the launch that last released flags
     void *kernel;
     void *kernel_bs;           // the blocked synchronous mode's kernel (NULL: none)
     bool bs_ok;                // it can run in the launch shape chosen for `kernel`
@@ -345,7 +367,7 @@ __global__ void at_flags_to_level(unsigned long long *flag, const int *ctrl, lon
 cudaError_t launch_stepper(at_solver *h, atk::Params *p, void *kernel)
 {
     const int64_t E = (int64_t)h->G * atk::kWarps;
-    if (h->flags_E != 0 && h->flags_E != E) {
+    if (h->flags_E != 0 && (h->flags_E != E || h->flags_list != (const void *)p->tiles)) {
         const long long nflags = h->P * 2;
         const int blocks = (int)((nflags + 255) / 256 < 1024 ? (nflags + 255) / 256 : 1024);
         at_flags_to_level<<<blocks, 256, 0, h->stream>>>(p->flag, p->ctrl, nflags);
@@ -353,6 +375,7 @@ cudaError_t launch_stepper(at_solver *h, atk::Params *p, void *kernel)
         if (e != cudaSuccess) return e;
     }
     h->flags_E = E;
+    h->flags_list = p->tiles;
     cudaLaunchConfig_t cfg{};
     cfg.gridDim = dim3(h->G);
     cfg.blockDim = dim3(atk::kThreads);
@@ -384,6 +407,92 @@ void prepare_bs(at_solver *h)
         return;
     }
     h->bs_ok = (int64_t)occ * h->sm_count >= h->G;
+}
+
+// The tile lists of an ensemble.  Instances are taken in order of their
+// delay bound (stable), so that the processing elements, which take
+// contiguous runs of the lists, mostly hold instances of one bound and can
+// make their passes L + 1 levels long; within an instance the subdomains are
+// in order.  `order` enumerates the subdomains in that sequence; list 1 has
+// one subdomain per tile, list K up to K consecutive subdomains of an
+// instance per tile; both as atk::TileInfo int4s.
+struct TilePlan {
+    std::vector<int> order;
+    std::vector<int4> list1, listk;
+};
+
+void plan_tiles(const std::vector<atk::BatchSub> &sub, int64_t n_inst, const at_instance *inst, int64_t M, int K,
+                TilePlan *tp)
+{
+    std::vector<int64_t> first((size_t)n_inst);
+    int64_t p0 = 0;
+    for (int64_t j = 0; j < n_inst; ++j) { first[(size_t)j] = p0; p0 += inst[j].n / M; }
+    std::vector<int64_t> idx((size_t)n_inst);
+    for (int64_t j = 0; j < n_inst; ++j) idx[(size_t)j] = j;
+    std::stable_sort(idx.begin(), idx.end(), [&](int64_t a, int64_t b) { return inst[a].L < inst[b].L; });
+    tp->order.clear();
+    tp->list1.clear();
+    tp->listk.clear();
+    for (int64_t j : idx) {
+        const int64_t Pi = inst[j].n / M, f0 = first[(size_t)j];
+        const int64_t r0 = (int64_t)tp->order.size();
+        for (int64_t lp = 0; lp < Pi; ++lp) {
+            tp->order.push_back((int)(f0 + lp));
+            tp->list1.push_back(make_int4((int)(f0 + lp), (int)(r0 + lp), 1, 0));
+        }
+        for (int64_t lp = 0; lp < Pi; lp += K) {
+            const int cnt = (int)(Pi - lp < K ? Pi - lp : K);
+            tp->listk.push_back(make_int4((int)(f0 + lp), (int)(r0 + lp), cnt, 0));
+        }
+    }
+    // link bits: the neighbour across the tile's face is in the adjacent tile
+    for (std::vector<int4> *l : {&tp->list1, &tp->listk}) {
+        const int64_t n = (int64_t)l->size();
+        for (int64_t t = 0; t < n; ++t) {
+            int4 &d = (*l)[(size_t)t];
+            const int cnt = d.z & 0xffff;
+            int link = 0;
+            if (t > 0) {
+                const int4 &pv = (*l)[(size_t)(t - 1)];
+                if (sub[(size_t)d.x].left == (long long)pv.x + (pv.z & 0xffff) - 1) link |= 1;
+            }
+            if (t + 1 < n && sub[(size_t)d.x + cnt - 1].right == (long long)(*l)[(size_t)(t + 1)].x) link |= 2;
+            d.z = cnt | (link << 16);
+        }
+    }
+}
+
+// Ensembles: plans the tile lists for K subdomains per tile, copies them to
+// the workspace (waits for the stream) and picks the kernels for tiles of up
+// to K M points.
+int set_tile_plan(at_solver *h, int K)
+{
+    TilePlan tp;
+    plan_tiles(h->bsub_host, h->n_inst, h->inst_host.data(), h->M, K, &tp);
+    unsigned char *tl = h->ws + h->lay.tiles;
+    cudaError_t e = cudaMemcpyAsync(tl, tp.list1.data(), tp.list1.size() * sizeof(int4), cudaMemcpyHostToDevice,
+                                    h->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(tl + (size_t)h->P * sizeof(int4), tp.listk.data(), tp.listk.size() * sizeof(int4),
+                            cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h->ws + h->lay.order, tp.order.data(), tp.order.size() * sizeof(int),
+                            cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "copying the tile lists");
+    h->K = K;
+    h->ntiles_k = (int64_t)tp.listk.size();
+    const int gw = groups_per_lane((int64_t)K * h->M);
+    const bool full = K == 1 && h->M == 128LL * gw;
+    const int order = h->order;
+    h->kernel = h->w == 8 ? atk_batch_kernel_f64(order, gw, full)
+                : h->comp ? atk_batch_kernel_f32c(order, gw, full)
+                          : atk_batch_kernel_f32(order, gw, full);
+    h->kernel_bs = h->w == 8 ? atk_sync_batch_kernel_f64(order, gw, full)
+                   : h->comp ? nullptr
+                             : atk_sync_batch_kernel_f32(order, gw, full);
+    h->flags_list = nullptr;
+    return AT_OK;
 }
 
 }  // namespace
@@ -599,7 +708,7 @@ int at_create(const at_grid *grid, int64_t P, int scheme_order, int L, double nu
     h->ws = static_cast<unsigned char *>(grid->workspace);
     h->stream = static_cast<cudaStream_t>(grid->stream);
     h->device = dev; h->sm_count = sms; h->smem_optin = smem_optin;
-    h->batch = false; h->n_inst = 0; h->lmin = L; h->dim = 1;
+    h->batch = false; h->n_inst = 0; h->lmin = L; h->dim = 1; h->K = 1;
     h->comp = comp;
     h->v64 = !comp && viscous_fp64(w, scheme_order, (uint32_t)grid->flags, nu * dt / (dx * dx));
 
@@ -634,7 +743,12 @@ static atk::Params make_params(const at_solver *h)
     p.gbar = reinterpret_cast<unsigned long long *>(h->ws + h->lay.gbar);
     if (h->comp) p.ur = h->ws + h->lay.ur;
     p.strip = h->ws + h->lay.strip;
+    p.ntiles = h->P;
+    p.ktile = 1;
     if (h->batch) {
+        p.tiles = reinterpret_cast<const int4 *>(h->ws + h->lay.tiles);   // one subdomain per tile
+        p.sub_order = reinterpret_cast<const int *>(h->ws + h->lay.order);
+        p.ktile = h->K;
         p.bsub = reinterpret_cast<const atk::BatchSub *>(h->ws + h->lay.bsub);
         p.binst = reinterpret_cast<const atk::BatchInst *>(h->ws + h->lay.binst);
     }
@@ -763,6 +877,11 @@ static int step_impl(at_solver *h, int64_t n_steps, int delay_mode, int8_t *dela
     // blocked synchronous passes (a grid barrier before each) need not
     p.alt = (p.sb > 1 && delay_mode == AT_FREE) ? 1 : 0;
     p.strip_words = strip_words(h, p.sb);
+    if (h->batch && h->K > 1 && (delay_mode == AT_FREE || delay_mode == AT_SYNC)) {
+        // multi-subdomain tiles (the faces between a tile's subdomains at delay 0)
+        p.tiles = reinterpret_cast<const int4 *>(h->ws + h->lay.tiles) + h->P;
+        p.ntiles = h->ntiles_k;
+    }
     p.levels = levels;
     p.levels_depth = depth;
     const cudaError_t e = launch_stepper(h, &p, (delay_mode == AT_SYNC && p.sb > 1) ? h->kernel_bs : h->kernel);
@@ -888,6 +1007,7 @@ int at_get_info(const at_solver *h, at_info *info)
     info->smem_bytes = h->smem; info->step = h->step; info->sm_count = h->sm_count;
     info->dtype = h->g.dtype; info->steps_per_pass = h->sb;
     info->viscous_fp64 = h->v64 ? 1 : 0;
+    info->tile_subdomains = h->batch ? h->K : 1;
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     if (h->has_state && cudaStreamIsCapturing(h->stream, &cap) == cudaSuccess && cap == cudaStreamCaptureStatusNone) {
         long long n0 = 0;
@@ -958,8 +1078,16 @@ int check_batch(const at_grid *g, int64_t n_inst, const at_instance *inst, int64
         if (a.L < d->Lmin) d->Lmin = a.L;
     }
     d->P = d->N / M;
+    if (d->P >= (1LL << 31)) return fail(AT_ERR_ARG, "at most 2^31 - 1 subdomains");
     if (g->steps_per_pass < 0 || g->steps_per_pass > d->Lmax + 1)
         return fail(AT_ERR_ARG, "steps_per_pass must be in 0..max L + 1, got %d", g->steps_per_pass);
+    const int K = g->tile_subdomains > 1 ? g->tile_subdomains : 1;
+    if (g->tile_subdomains < 0 || (K != 1 && K != 2 && K != 4))
+        return fail(AT_ERR_ARG, "tile_subdomains must be 0, 1, 2 or 4, got %d", g->tile_subdomains);
+    if (K > 1 && (M != 128 && M != 256 && M != 512))
+        return fail(AT_ERR_ARG, "tile_subdomains > 1 needs M = 128, 256 or 512 (M=%lld)", (long long)M);
+    if ((int64_t)K * M > atk::kMaxM)
+        return fail(AT_ERR_ARG, "tile_subdomains x M must be <= %d", atk::kMaxM);
     return AT_OK;
 }
 
@@ -1060,20 +1188,16 @@ int at_create_batch(const at_grid *grid, int64_t n_inst, const at_instance *inst
     h->stream = st;
     h->device = dev; h->sm_count = sms; h->smem_optin = smem_optin;
     h->batch = true; h->n_inst = n_inst; h->lmin = d.Lmin;
-    const int gw = groups_per_lane(M);
-    const bool full = (M == 128LL * gw);
     h->comp = comp;
-    h->kernel = w == 8 ? atk_batch_kernel_f64(scheme_order, gw, full)
-                : comp ? atk_batch_kernel_f32c(scheme_order, gw, full)
-                       : atk_batch_kernel_f32(scheme_order, gw, full);
-    h->kernel_bs = w == 8 ? atk_sync_batch_kernel_f64(scheme_order, gw, full)
-                   : comp ? nullptr
-                          : atk_sync_batch_kernel_f32(scheme_order, gw, full);
+    h->bsub_host = std::move(sub);
+    h->inst_host.assign(inst, inst + n_inst);
+    rc = set_tile_plan(h, grid->tile_subdomains > 1 ? grid->tile_subdomains : 1);
+    if (rc != AT_OK) { delete h; return rc; }
     h->init_kernel = w == 8 ? atk_init_kernel_f64(scheme_order) : atk_init_kernel_f32(scheme_order);
     int stages = grid->stages > 0 ? grid->stages : 3;
     if (stages < atk::kMinStages) stages = atk::kMinStages;
-    rc = launch_shape(M, w, d.P, tab_size(M, w, false, true, comp), grid->max_ctas, stages, sms, smem_optin, h->kernel,
-                      &h->G, &h->stages, &h->sl, &h->smem, &h->smax);
+    rc = launch_shape((int64_t)h->K * M, w, d.P, tab_size(M, w, false, true, comp, h->ntiles_k, h->K), grid->max_ctas,
+                      stages, sms, smem_optin, h->kernel, &h->G, &h->stages, &h->sl, &h->smem, &h->smax);
     if (rc != AT_OK) { delete h; return rc; }
     prepare_bs(h);
     h->sb = grid->steps_per_pass > 0 ? grid->steps_per_pass : 1;
@@ -1099,7 +1223,6 @@ int at_tune(at_solver *h, int64_t n_steps, int delay_mode, at_tune_result *res)
     if (cudaStreamIsCapturing(h->stream, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone)
         return fail(AT_ERR_STATE, "at_tune under stream capture");
     std::memset(res, 0, sizeof(*res));
-    const TabSize tsz = tab_size(h->M, h->w, h->g.forcing_amp != 0.0, h->batch, h->comp);
     const int gmax = (int)((h->P + atk::kWarps - 1) / atk::kWarps);
 
     cudaEvent_t ev[3];
@@ -1111,14 +1234,21 @@ int at_tune(at_solver *h, int64_t n_steps, int delay_mode, at_tune_result *res)
         }
     }
     struct Shape {
-        int G, stages, sb;
+        int G, stages, sb, K;
     };
     auto apply = [&](const Shape &sh) -> int {
+        if (h->batch && sh.K != h->K) {
+            const int r = set_tile_plan(h, sh.K);
+            if (r != AT_OK) return r;
+        }
+        // (a tile is one subdomain, except in an ensemble of K-subdomain tiles)
+        const int kt = h->batch ? h->K : 1;
+        const TabSize tsz = tab_size(h->M, h->w, h->g.forcing_amp != 0.0, h->batch, h->comp, h->ntiles_k, kt);
         int G = 0, st = 0, smem = 0;
         long long smax = 0;
         atk::SmemLayout sl{};
-        const int r = launch_shape(h->M, h->w, h->P, tsz, sh.G, sh.stages, h->sm_count, h->smem_optin, h->kernel,
-                                   &G, &st, &sl, &smem, &smax);
+        const int r = launch_shape((int64_t)kt * h->M, h->w, h->P, tsz, sh.G, sh.stages, h->sm_count,
+                                   h->smem_optin, h->kernel, &G, &st, &sl, &smem, &smax);
         if (r != AT_OK) return r;
         if (st != sh.stages) return AT_ERR_RESIDENCY;   // did not fit as asked
         h->G = G; h->stages = st; h->sl = sl; h->smem = smem; h->smax = smax; h->sb = sh.sb;
@@ -1147,7 +1277,7 @@ int at_tune(at_solver *h, int64_t n_steps, int delay_mode, at_tune_result *res)
         return AT_OK;
     };
 
-    const Shape orig{h->G, h->stages, h->sb};
+    const Shape orig{h->G, h->stages, h->sb, h->batch ? h->K : 1};
     Shape best = orig;
     double best_ms = 0.0;
     int rc = time_shape(&best_ms);
@@ -1157,20 +1287,30 @@ int at_tune(at_solver *h, int64_t n_steps, int delay_mode, at_tune_result *res)
     // clamp it to their own smallest bound + 1); the synchronous mode keeps
     // one level per pass unless the solver was made for blocked passes
     const int sb_hi = (delay_mode == AT_FREE || (delay_mode == AT_SYNC && h->sb > 1)) ? h->L + 1 : 1;
-    for (int st = atk::kMinStages; rc == AT_OK && st <= 4; ++st) {
-        int lastG = -1;
-        for (int per_sm = 1; rc == AT_OK && per_sm <= 4; ++per_sm) {
-            const int G = per_sm * h->sm_count < gmax ? per_sm * h->sm_count : gmax;
-            if (G == lastG) break;
-            lastG = G;
-            for (int sb = 1; rc == AT_OK && sb <= sb_hi; ++sb) {
-                const Shape sh{G, st, sb};
-                if (sh.G == orig.G && sh.stages == orig.stages && sh.sb == orig.sb) continue;
-                if (apply(sh) != AT_OK) { g_err[0] = 0; continue; }   // not resident: skip
-                double ms = 0.0;
-                rc = time_shape(&ms);
-                ++tried;
-                if (rc == AT_OK && ms < best_ms) { best_ms = ms; best = sh; }
+    // ensembles in AT_FREE / AT_SYNC: subdomains per tile 1, 2, 4 (as the
+    // subdomain size allows)
+    int k_hi = 1;
+    if (h->batch && (delay_mode == AT_FREE || delay_mode == AT_SYNC) &&
+        (h->M == 128 || h->M == 256 || h->M == 512))
+        k_hi = (int)(atk::kMaxM / h->M) < 4 ? (int)(atk::kMaxM / h->M) : 4;
+    for (int K = 1; rc == AT_OK && K <= k_hi; K *= 2) {
+        for (int st = atk::kMinStages; rc == AT_OK && st <= 4; ++st) {
+            int lastG = -1;
+            for (int per_sm = 1; rc == AT_OK && per_sm <= 4; ++per_sm) {
+                const int G = per_sm * h->sm_count < gmax ? per_sm * h->sm_count : gmax;
+                if (G == lastG) break;
+                lastG = G;
+                for (int sb = 1; rc == AT_OK && sb <= sb_hi; ++sb) {
+                    const Shape sh{G, st, sb, h->batch ? K : 1};
+                    if (sh.G == orig.G && sh.stages == orig.stages && sh.sb == orig.sb && sh.K == orig.K) continue;
+                    const int ra = apply(sh);
+                    if (ra == AT_ERR_CUDA) { rc = ra; break; }
+                    if (ra != AT_OK) { g_err[0] = 0; continue; }   // not resident: skip
+                    double ms = 0.0;
+                    rc = time_shape(&ms);
+                    ++tried;
+                    if (rc == AT_OK && ms < best_ms) { best_ms = ms; best = sh; }
+                }
             }
         }
     }
@@ -1181,6 +1321,7 @@ int at_tune(at_solver *h, int64_t n_steps, int delay_mode, at_tune_result *res)
     res->ctas = h->G;
     res->stages = h->stages;
     res->steps_per_pass = h->sb;
+    res->tile_subdomains = h->batch ? h->K : 1;
     res->n_tried = tried;
     res->best_ms = best_ms;
     return AT_OK;
@@ -1478,7 +1619,7 @@ extern "C" int at_step_noalloc(const at_grid *grid, int64_t P, int scheme_order,
     h.ws = scratch;
     h.stream = static_cast<cudaStream_t>(grid->stream);
     h.device = dev; h.sm_count = sms; h.smem_optin = smem_optin;
-    h.batch = false; h.n_inst = 0; h.lmin = L;
+    h.batch = false; h.n_inst = 0; h.lmin = L; h.K = 1;
     h.comp = false;
     h.v64 = viscous_fp64(w, scheme_order, (uint32_t)grid->flags, nu * dt / (dx * dx));
     pick_kernels(w, scheme_order, h.M, grid->forcing_amp != 0.0, h.v64, false, &h.kernel, &h.init_kernel);

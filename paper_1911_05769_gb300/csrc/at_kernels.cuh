@@ -104,6 +104,20 @@ struct BatchInst {
 };
 static_assert(sizeof(BatchInst) == 64, "BatchInst is 64 bytes");
 
+// A tile of an ensemble launch: cnt (1..ktile) consecutive subdomains s0 ..
+// s0+cnt-1 of one instance, advanced together (the faces between them at
+// delay 0: the neighbour's level itself).  Tiles are listed in the order the
+// processing elements sweep them (instances grouped by delay bound); rec is
+// the place of s0 in the list's enumeration of subdomains, which orders the
+// subdomain records in shared memory.  link bit 0: the left neighbour of s0
+// is the last subdomain of the previous tile of the list; bit 1: the right
+// neighbour of the last subdomain is s0 of the next tile.  Stored as an int4
+// (s0, rec, cnt | link << 16, 0).
+struct TileInfo {
+    long long s0, rec;
+    int cnt, link;
+};
+
 struct Params {
     void *u;                   // state, N words, updated in place
     unsigned char *ring;       // [T][P][2] entries of 16 bytes
@@ -114,6 +128,10 @@ struct Params {
     int8_t *delays;            // [n_steps][P][2] replay input / record output
     const BatchSub *bsub;      // ensembles: [P] subdomain records (else NULL)
     const BatchInst *binst;    // ensembles: instance records (else NULL)
+    const int4 *tiles;         // ensembles: the launch's tile list [ntiles] (see TileInfo)
+    const int *sub_order;      // ensembles: subdomain at each place of the tile lists' enumeration [P]
+    long long ntiles;          // tiles of the launch (single domain: P, tile j = subdomain j)
+    int ktile;                 // most subdomains per tile
     void *ur;                  // compensated state: the rounding error of every point (N words)
     unsigned char *strip;      // blocked synchronous mode: edge strips [2][P][2] of kStripBytes (pass parity)
     int strip_words;           // words per strip (R x levels per pass, rounded up to a multiple of 4)
@@ -524,11 +542,13 @@ __device__ __forceinline__ T exact_ghost2(const BatchInst *binst, const BatchSub
 // of group g+1 (lane l+1, same m; for lane 31, lane 0 at m+1): one shuffle
 // per word, no barrier.  Groups 0 and NG-1 take the approximated halo instead.
 //
-// In an ensemble (BATCH) the stencil factors, delay bound and seed come from
-// the subdomain's record in shared memory (btab[j - lo]); a face whose record
-// names no neighbour takes the instance's exact boundary values, undelayed;
-// a face whose neighbour is another PE's, or not the next subdomain in the
-// sweep (a periodic instance's wrap-around), goes through the flags.
+// In an ensemble (BATCH) a tile is cnt consecutive subdomains of one instance
+// (see TileInfo; the faces between them at delay 0); the stencil factors,
+// delay bound and seed come from its records in shared memory; a face whose
+// record names no neighbour takes the instance's exact boundary values,
+// undelayed; a face whose neighbour is another PE's, or not in the adjacent
+// tile of the sweep (a periodic instance's wrap-around), goes through the
+// flags.
 //
 // PREC (FP32 state only) 1: the viscous term nu dt D2(u) is formed from the
 // stencil values in FP64 and added to u in FP64, rounded to FP32 once per
@@ -572,19 +592,40 @@ __device__ void run_pe(const Params &p, const Sweep &sw, long long lo, long long
         }
         return;
     }
+    // the subdomains of tile t (single domain: tile t is subdomain t)
+    auto tile_info = [&](long long t) -> TileInfo {
+        if constexpr (BATCH) {
+            const int4 d = __ldg(p.tiles + t);
+            return TileInfo{(long long)d.x, (long long)d.y, d.z & 0xffff, d.z >> 16};
+        } else {
+            return TileInfo{t, t, 1, 0};
+        }
+    };
+    long long rec_lo = 0;                // place of this PE's first record
+    if constexpr (BATCH) rec_lo = tile_info(lo).rec;
+    // the first and last subdomain records of a tile (ensembles)
+    auto rec_first = [&](const TileInfo &ti) -> const BatchSub & { return btab[ti.rec - rec_lo]; };
+    auto rec_last = [&](const TileInfo &ti) -> const BatchSub & { return btab[ti.rec - rec_lo + ti.cnt - 1]; };
+    // whether face f of tile t takes its halo through the flags: its
+    // neighbour is not the adjacent tile of this PE's sweep (ensembles; the
+    // single domain: the PE's first and last tile)
+    auto link_edge = [&](long long t, const TileInfo &ti, int f) -> bool {
+        return f == 0 ? !(t - 1 >= lo && (ti.link & 1)) : !(t + 1 < hi && (ti.link & 2));
+    };
     const int NS = p.stages;
     // tiles loaded ahead; an alternating sweep revisits the subdomain of
     // position i after a turn 2i+1 tiles later, so at most 2 ahead there
     int D = (int)((S - 1) < (NS - 1) ? (S - 1) : (NS - 1));
     if (sw.alt && D > 2) D = 2;
     const long long Q = count_passes(sw, S_LEV) * S;
-    const int NG = (int)(p.M / 4);
+    // groups of 4 points in the tile (an ensemble's tiles: cnt subdomains)
+    int NG = (int)(p.M / 4);
     // owner of group NG-1 (compile-time when the tile is a multiple of 128 points)
-    const int m_last = FULL ? GW - 1 : (NG - 1) >> 5;
-    const int lane_last = FULL ? 31 : (NG - 1) & 31;
+    int m_last = FULL ? GW - 1 : (NG - 1) >> 5;
+    int lane_last = FULL ? 31 : (NG - 1) & 31;
     const T cA0 = (T)p.cA, cB0 = (T)p.cB;
     const double cB64_0 = p.cB;
-    const size_t tile_bytes = (size_t)p.M * sizeof(T);
+    const size_t tile_bytes = (size_t)p.M * sizeof(T);                 // one subdomain
     const size_t slot_stride = (size_t)p.P * 2 * kRingEntry;
     const int up = (lane + 31) & 31, down = (lane + 1) & 31;
     const bool edge_pub = !(p.skip_publish && blockIdx.x == 0 && threadIdx.x < 32);
@@ -596,20 +637,21 @@ __device__ void run_pe(const Params &p, const Sweep &sw, long long lo, long long
 
     // --- state tile copies (lane 0): tile t goes to stage t % NS ------------
     // (compensated state: the stage holds the tile, then its error words)
-    const size_t err_off = round_up((long long)tile_bytes, 128);
+    const size_t err_off = round_up((long long)tile_bytes * p.ktile, 128);
     // (stage indices and phases are kept as running counters: no 64-bit
     // division per tile)
     auto issue_load = [&](int st, const Cursor &c) {
         if (lane == 0) {
+            const TileInfo ti = tile_info(c.j);
+            const size_t bytes = tile_bytes * (size_t)ti.cnt;
             uint64_t *bar = &bars[st];
-            mbar_arrive_expect_tx(bar, (unsigned)(PREC == 2 ? 2 * tile_bytes : tile_bytes));
+            mbar_arrive_expect_tx(bar, (unsigned)(PREC == 2 ? 2 * bytes : bytes));
             bulk_load(stages + (size_t)st * p.stage_bytes,
-                      reinterpret_cast<const unsigned char *>(p.u) + (size_t)c.j * tile_bytes,
-                      (unsigned)tile_bytes, bar);
+                      reinterpret_cast<const unsigned char *>(p.u) + (size_t)ti.s0 * tile_bytes, (unsigned)bytes, bar);
             if constexpr (PREC == 2)
                 bulk_load(stages + (size_t)st * p.stage_bytes + err_off,
-                          reinterpret_cast<const unsigned char *>(p.ur) + (size_t)c.j * tile_bytes,
-                          (unsigned)tile_bytes, bar);
+                          reinterpret_cast<const unsigned char *>(p.ur) + (size_t)ti.s0 * tile_bytes, (unsigned)bytes,
+                          bar);
         }
     };
 
@@ -630,15 +672,17 @@ __device__ void run_pe(const Params &p, const Sweep &sw, long long lo, long long
             while (jj >= hi) { jj -= S; ++nn; }
             int k = 0;
             if (t0 + (lane >> 1) < Q && nn >= sw.n0 && nn < sw.n0 + sw.n_steps) {
+                // (prescribed delays: tiles of one subdomain)
+                const TileInfo tj = tile_info(jj);
                 if (p.mode == kModeSeeded) {
                     if constexpr (BATCH) {
-                        const BatchSub &b = btab[jj - lo];
+                        const BatchSub &b = rec_first(tj);
                         k = seeded_delay(b.seed, nn, b.lp, b.Pi, p.per_sub ? 0 : (lane & 1), b.L);
                     } else {
                         k = seeded_delay(p.seed, nn, jj, p.P, p.per_sub ? 0 : (lane & 1), p.L);
                     }
                 } else if (p.mode == kModeReplay) {
-                    k = p.delays[((nn - sw.n0) * p.P + jj) * 2 + (lane & 1)];
+                    k = p.delays[((nn - sw.n0) * p.P + tj.s0) * 2 + (lane & 1)];
                 }
             }
             kb = k;
@@ -656,6 +700,7 @@ __device__ void run_pe(const Params &p, const Sweep &sw, long long lo, long long
         int state = 1;
         long long k = 0, q = 0;
         bool bnd = false;              // exact boundary face (ensembles)
+        const TileInfo ti = tile_info(c.j);
         if (lane < 2) {
             const int f = lane;
             const long long n = c.n;
@@ -663,11 +708,11 @@ __device__ void run_pe(const Params &p, const Sweep &sw, long long lo, long long
             bool edge;
             int Lj = p.L;
             if constexpr (BATCH) {
-                const BatchSub &b = btab[c.j - lo];
-                q = f ? b.right : b.left;
+                const BatchSub &bf = rec_first(ti), &bl = rec_last(ti);
+                q = f ? bl.right : bf.left;
                 bnd = q < 0;
-                edge = !bnd && (q < lo || q >= hi || q != c.j + (f ? 1 : -1));
-                Lj = b.L;
+                edge = !bnd && link_edge(c.j, ti, f);
+                Lj = bf.L;
             } else {
                 q = (f == 0) ? (c.j == 0 ? p.P - 1 : c.j - 1) : (c.j == p.P - 1 ? 0 : c.j + 1);
                 edge = (f == 0) ? (c.j == lo) : (c.j == hi - 1);
@@ -703,10 +748,22 @@ __device__ void run_pe(const Params &p, const Sweep &sw, long long lo, long long
             const int f = lane;
             // (the synchronous modes use level n itself at every level: k = 0)
             const int kstep = p.mode == kModeSync ? 0 : 1;
+            const long long sf = f ? ti.s0 + ti.cnt - 1 : ti.s0;      // the subdomain of face f
             for (int i = 0; i < c.len; ++i) {
                 my_hist[k + kstep * i] += 1u;
                 if (p.delays && p.mode != kModeReplay)
-                    p.delays[((c.n - sw.n0 + i) * p.P + c.j) * 2 + f] = (int8_t)(k + kstep * i);
+                    p.delays[((c.n - sw.n0 + i) * p.P + sf) * 2 + f] = (int8_t)(k + kstep * i);
+            }
+            if (BATCH && f == 0 && ti.cnt > 1) {
+                // the faces between the tile's subdomains: delay 0
+                for (int i = 0; i < c.len; ++i) {
+                    my_hist[0] += 2u * (unsigned)(ti.cnt - 1);
+                    if (p.delays && p.mode != kModeReplay)
+                        for (int s = 0; s + 1 < ti.cnt; ++s) {
+                            p.delays[((c.n - sw.n0 + i) * p.P + ti.s0 + s) * 2 + 1] = 0;
+                            p.delays[((c.n - sw.n0 + i) * p.P + ti.s0 + s + 1) * 2 + 0] = 0;
+                        }
+                }
             }
             hk = (int)k;
             if constexpr (bsync) {
@@ -749,10 +806,18 @@ __device__ void run_pe(const Params &p, const Sweep &sw, long long lo, long long
     if constexpr (bsync) {
         // edge strips of the state at the launch's first level (parity 0),
         // then the first grid barrier
+        // (every subdomain of this PE's tiles: records rec_lo .. rec_hi-1)
         const int sw4 = p.strip_words;
         const T *ust = reinterpret_cast<const T *>(p.u);
-        for (long long t = lane; t < S * 2 * sw4; t += 32) {
-            const long long jj = lo + t / (2 * sw4);
+        long long nrec = S;
+        if constexpr (BATCH) {
+            const TileInfo tl_ = tile_info(hi - 1);
+            nrec = tl_.rec + tl_.cnt - rec_lo;
+        }
+        for (long long t = lane; t < nrec * 2 * sw4; t += 32) {
+            const long long r = t / (2 * sw4);
+            long long jj = lo + r;
+            if constexpr (BATCH) jj = p.sub_order[rec_lo + r];
             const int f = (int)((t / sw4) & 1), wd = (int)(t % sw4);
             const long long src = jj * p.M + (f ? p.M - sw4 : 0) + wd;
             reinterpret_cast<T *>(p.strip + ((size_t)jj * 2 + f) * kStripBytes)[wd] = ust[src];
@@ -813,19 +878,26 @@ __device__ void run_pe(const Params &p, const Sweep &sw, long long lo, long long
             if (++sr == NS) { sr = 0; ph ^= 1u; }
         }
         const unsigned char *rw = raw + (size_t)buf * kRawBytes;
-        const long long j = C.j, n = C.n;
+        const long long j = C.j, n = C.n;                 // tile, level at the pass start
         const int len = C.len;
-        T *ug = reinterpret_cast<T *>(p.u) + (size_t)j * p.M;
+        const TileInfo ti = tile_info(j);
+        const long long s0 = ti.s0, s1 = ti.s0 + ti.cnt - 1;   // its first and last subdomain
+        T *ug = reinterpret_cast<T *>(p.u) + (size_t)s0 * p.M;
         T cA = cA0, cB = cB0;
         double cB64 = cB64_0;
         bool bnd0 = false, bnd1 = false;
         if constexpr (BATCH) {
-            const BatchSub &b = btab[j - lo];
-            cA = (T)b.cA;
-            cB = (T)b.cB;
-            cB64 = b.cB;
-            bnd0 = b.left < 0;
-            bnd1 = b.right < 0;
+            const BatchSub &bf = rec_first(ti), &bl = rec_last(ti);
+            cA = (T)bf.cA;
+            cB = (T)bf.cB;
+            cB64 = bf.cB;
+            bnd0 = bf.left < 0;
+            bnd1 = bl.right < 0;
+            if constexpr (!FULL) {
+                NG = (int)(ti.cnt * p.M / 4);
+                m_last = (NG - 1) >> 5;
+                lane_last = (NG - 1) & 31;
+            }
         }
 
         if (!turn) {
@@ -881,14 +953,15 @@ __device__ void run_pe(const Params &p, const Sweep &sw, long long lo, long long
             const int kf = (f ? k1cur : k0cur) + rem / R;
             if constexpr (PREC == 2) {
                 if (BATCH && (f ? bnd1 : bnd0)) {
-                    hv = exact_ghost2<T, R>(p.binst, btab[j - lo], p.M, f, rem % R, n + rem / R, hvl);
+                    hv = exact_ghost2<T, R>(p.binst, f ? rec_last(ti) : rec_first(ti), p.M, f, rem % R, n + rem / R,
+                                            hvl);
                 } else {
                     hv = reinterpret_cast<const T *>(rf)[rem % R];
                     hvl = approx_halo_lo<T, S_LEV, R>(rf, kf, rem % R);
                 }
             } else {
                 if (BATCH && (f ? bnd1 : bnd0))
-                    hv = exact_ghost<T, R>(p.binst, btab[j - lo], p.M, f, rem % R, n + rem / R);
+                    hv = exact_ghost<T, R>(p.binst, f ? rec_last(ti) : rec_first(ti), p.M, f, rem % R, n + rem / R);
                 else
                     hv = approx_halo<T, S_LEV>(rf, kf, rem % R);
             }
@@ -897,14 +970,15 @@ __device__ void run_pe(const Params &p, const Sweep &sw, long long lo, long long
         // and whether the consumer across that face waits on the flag
         // (lane_last == 0: lane 0 publishes both faces, face 1 via prel1)
         const int pf = (lane == 0) ? 0 : 1;
-        unsigned char *const pe0 = p.ring + ((size_t)j * 2 + pf) * kRingEntry;
-        unsigned long long *const pflag = p.flag + j * 2 + pf;
+        const long long sp = pf ? s1 : s0;                  // the subdomain of that face
+        unsigned char *const pe0 = p.ring + ((size_t)sp * 2 + pf) * kRingEntry;
+        unsigned long long *const pflag = p.flag + sp * 2 + pf;
         bool prel, prel1 = false;
         if constexpr (BATCH) {
-            const BatchSub &b = btab[j - lo];
-            const long long q0 = pf ? b.right : b.left;
-            prel = q0 >= 0 && (q0 < lo || q0 >= hi || q0 != j + (pf ? 1 : -1));
-            prel1 = b.right >= 0 && (b.right < lo || b.right >= hi || b.right != j + 1);
+            const BatchSub &bf = rec_first(ti), &bl = rec_last(ti);
+            const long long q0 = pf ? bl.right : bf.left;
+            prel = q0 >= 0 && link_edge(j, ti, pf);
+            prel1 = bl.right >= 0 && link_edge(j, ti, 1);
         } else {
             prel = pf ? j == hi - 1 : j == lo;
             prel1 = j == hi - 1;
@@ -924,8 +998,8 @@ __device__ void run_pe(const Params &p, const Sweep &sw, long long lo, long long
                     hl[q] = __shfl_sync(kAll, gv, G - R + q);
                     hr[q] = __shfl_sync(kAll, gv, 16 + q);
                     if constexpr (BATCH) {
-                        if (bnd0) hl[q] = exact_ghost<T, R>(p.binst, btab[j - lo], p.M, 0, q, n + i);
-                        if (bnd1) hr[q] = exact_ghost<T, R>(p.binst, btab[j - lo], p.M, 1, q, n + i);
+                        if (bnd0) hl[q] = exact_ghost<T, R>(p.binst, rec_first(ti), p.M, 0, q, n + i);
+                        if (bnd1) hr[q] = exact_ghost<T, R>(p.binst, rec_last(ti), p.M, 1, q, n + i);
                     }
                 }
                 if (i + 1 < len) {
@@ -983,21 +1057,21 @@ __device__ void run_pe(const Params &p, const Sweep &sw, long long lo, long long
                 } else if constexpr (PREC == 2) {
                     const unsigned char *rr = rw + kRawFace;
                     if (BATCH && bnd0) {
-                        hl[q] = exact_ghost2<T, R>(p.binst, btab[j - lo], p.M, 0, q, n + i, hll[q]);
+                        hl[q] = exact_ghost2<T, R>(p.binst, rec_first(ti), p.M, 0, q, n + i, hll[q]);
                     } else {
                         hl[q] = reinterpret_cast<const T *>(rw)[q];
                         hll[q] = approx_halo_lo<T, S_LEV, R>(rw, k0cur + i, q);
                     }
                     if (BATCH && bnd1) {
-                        hr[q] = exact_ghost2<T, R>(p.binst, btab[j - lo], p.M, 1, q, n + i, hrl[q]);
+                        hr[q] = exact_ghost2<T, R>(p.binst, rec_last(ti), p.M, 1, q, n + i, hrl[q]);
                     } else {
                         hr[q] = reinterpret_cast<const T *>(rr)[q];
                         hrl[q] = approx_halo_lo<T, S_LEV, R>(rr, k1cur + i, q);
                     }
                 } else {
-                    hl[q] = (BATCH && bnd0) ? exact_ghost<T, R>(p.binst, btab[j - lo], p.M, 0, q, n + i)
+                    hl[q] = (BATCH && bnd0) ? exact_ghost<T, R>(p.binst, rec_first(ti), p.M, 0, q, n + i)
                                             : approx_halo<T, S_LEV>(rw, k0cur + i, q);
-                    hr[q] = (BATCH && bnd1) ? exact_ghost<T, R>(p.binst, btab[j - lo], p.M, 1, q, n + i)
+                    hr[q] = (BATCH && bnd1) ? exact_ghost<T, R>(p.binst, rec_last(ti), p.M, 1, q, n + i)
                                             : approx_halo<T, S_LEV>(rw + kRawFace, k1cur + i, q);
                 }
             }
@@ -1113,20 +1187,49 @@ __device__ void run_pe(const Params &p, const Sweep &sw, long long lo, long long
                     }
                 }
             }
+            if constexpr (BATCH) {
+                // the faces between the subdomains of a multi-subdomain tile
+                // (subdomains of 128, 256 or 512 points: a subdomain's first
+                // group is lane 0's, its last lane 31's): ring entries only
+                if (ti.cnt > 1 && (lane == 0 || lane == 31)) {
+                    const size_t slot_off = (size_t)(lev & (p.T - 1)) * slot_stride;
+                    const int gsh = p.M == 128 ? 0 : p.M == 256 ? 1 : 2;      // m slots per subdomain: 1 << gsh
+                    const int gmask = (1 << gsh) - 1;
+#pragma unroll
+                    for (int m = 0; m < GW; ++m) {
+                        const int sidx = m >> gsh;
+                        const bool fst = lane == 0 && (m & gmask) == 0 && sidx >= 1 && sidx < ti.cnt;
+                        const bool lst = lane == 31 && (m & gmask) == gmask && sidx + 1 < ti.cnt;
+                        if (!(fst || lst)) continue;
+                        const int fi = fst ? 0 : 1;
+                        T w[R], wl[R];
+#pragma unroll
+                        for (int q = 0; q < R; ++q) {
+                            w[q] = fst ? cd[m][q] : cd[m][4 - R + q];
+                            wl[q] = (T)0;
+                            if constexpr (PREC == 2) wl[q] = fst ? er[m][q] : er[m][4 - R + q];
+                        }
+                        unsigned char *e = p.ring + slot_off + ((size_t)(s0 + sidx) * 2 + fi) * kRingEntry;
+                        if constexpr (PREC == 2) st_entry2<R>(e, w, wl);
+                        else st_entry<T, R>(e, w);
+                    }
+                }
+            }
         };
         for (int i = 0; i < len; ++i) level(i, c, c);
         if constexpr (bsync) {
             // edge strips of the pass's last level for the next pass
             const int gq = p.strip_words / 4;
-            T *s0 = reinterpret_cast<T *>(p.strip + ((size_t)(((C.pass + 1) & 1) * p.P + j) * 2) * kStripBytes);
-            T *s1 = reinterpret_cast<T *>(reinterpret_cast<unsigned char *>(s0) + kStripBytes);
+            const size_t par_off = (size_t)((C.pass + 1) & 1) * p.P;
+            T *st0 = reinterpret_cast<T *>(p.strip + ((par_off + s0) * 2 + 0) * kStripBytes);
+            T *st1 = reinterpret_cast<T *>(p.strip + ((par_off + s1) * 2 + 1) * kStripBytes);
             // (read after the next grid barrier: the warp barrier at the end
             // of this tile and the fence of the arrival order them before it)
 #pragma unroll
             for (int m = 0; m < GW; ++m) {
                 const int g = lane + 32 * m;
-                if (g < gq) stg4<T>(s0 + 4 * g, c[m]);
-                if (g >= NG - gq && g < NG) stg4<T>(s1 + 4 * (g - (NG - gq)), c[m]);
+                if (g < gq) stg4<T>(st0 + 4 * g, c[m]);
+                if (g >= NG - gq && g < NG) stg4<T>(st1 + 4 * (g - (NG - gq)), c[m]);
             }
         }
         // the next tile; before a turn the words stay in registers
@@ -1139,13 +1242,13 @@ __device__ void run_pe(const Params &p, const Sweep &sw, long long lo, long long
                 const int g = lane + 32 * m;
                 if (FULL || g < NG) stg4<T>(ug + 4 * g, c[m]);
                 if constexpr (PREC == 2) {
-                    if (FULL || g < NG) stg4<T>(reinterpret_cast<T *>(p.ur) + (size_t)j * p.M + 4 * g, er[m]);
+                    if (FULL || g < NG) stg4<T>(reinterpret_cast<T *>(p.ur) + (size_t)s0 * p.M + 4 * g, er[m]);
                 }
             }
         }
         if (p.levels) {
             T *lg = reinterpret_cast<T *>(p.levels) + (size_t)((n + len) % p.levels_depth) * (size_t)p.N +
-                    (size_t)j * p.M;
+                    (size_t)s0 * p.M;
 #pragma unroll
             for (int m = 0; m < GW; ++m) {
                 const int g = lane + 32 * m;
@@ -1187,8 +1290,8 @@ __global__ void __launch_bounds__(kThreads, AT_MIN_CTAS_PER_SM) at_stepper(const
     extern __shared__ __align__(128) unsigned char smem[];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const long long e = (long long)blockIdx.x * kWarps + w;     // this warp's PE
-    const long long lo = e * p.P / p.E;
-    const long long hi = (e + 1) * p.P / p.E;
+    const long long lo = e * p.ntiles / p.E;                  // this PE's tiles
+    const long long hi = (e + 1) * p.ntiles / p.E;
     const long long S = hi - lo;
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + p.bar_off) + (size_t)w * p.stages;
     unsigned *hist = reinterpret_cast<unsigned *>(smem + p.hist_off) + (size_t)w * 2 * (kMaxL + 1);
@@ -1231,14 +1334,21 @@ __global__ void __launch_bounds__(kThreads, AT_MIN_CTAS_PER_SM) at_stepper(const
         }
     }
     if constexpr (BATCH) {
-        // this PE's subdomain records; passes no longer than the smallest
-        // delay bound among them allows (k0 + len - 1 <= L)
-        const uint4 *src = reinterpret_cast<const uint4 *>(p.bsub + lo);
+        // this PE's subdomain records, in the order of its tiles; passes no
+        // longer than the smallest delay bound among them allows
+        // (k0 + len - 1 <= L), except in the synchronous modes
+        long long r_lo = 0, r_hi = 0;
+        if (S > 0) {
+            const int4 a = p.tiles[lo], b = p.tiles[hi - 1];
+            r_lo = a.y;
+            r_hi = (long long)b.y + (b.z & 0xffff);
+        }
         uint4 *dst = reinterpret_cast<uint4 *>(btab);
         constexpr int kVec = (int)(sizeof(BatchSub) / sizeof(uint4));
-        for (long long i = lane; i < S * kVec; i += 32) dst[i] = src[i];
+        for (long long i = lane; i < (r_hi - r_lo) * kVec; i += 32)
+            dst[i] = reinterpret_cast<const uint4 *>(p.bsub + p.sub_order[r_lo + i / kVec])[i % kVec];
         int lmin = kMaxL;
-        for (long long i = lane; i < S; i += 32) lmin = min(lmin, p.bsub[lo + i].L);
+        for (long long i = lane; i < r_hi - r_lo; i += 32) lmin = min(lmin, p.bsub[p.sub_order[r_lo + i]].L);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) lmin = min(lmin, __shfl_xor_sync(0xffffffffu, lmin, o));
         if (p.mode != kModeSync && sw.sb > lmin + 1) sw.sb = lmin + 1;

@@ -150,7 +150,7 @@ class EnsembleSolver(Solver):
     """
 
     def __init__(self, instances, M, order, *, dtype="f32", flags=0, timeout_ns=0, max_ctas=0, stages=0,
-                 steps_per_pass=0, stream=None, device=None):
+                 steps_per_pass=0, tile_subdomains=0, stream=None, device=None):
         import torch
         self.torch = torch
         dev = torch.device("cuda", torch.cuda.current_device() if device is None else device)
@@ -176,6 +176,7 @@ class EnsembleSolver(Solver):
         g.max_ctas = max_ctas
         g.stages = stages
         g.steps_per_pass = steps_per_pass
+        g.tile_subdomains = tile_subdomains
         nbytes = B.at_batch_workspace_bytes(g, arr, M, order)
         if nbytes == 0:
             raise B.AtError(B.AT_ERR_ARG, "at_batch_workspace_bytes")

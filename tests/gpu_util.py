@@ -65,7 +65,8 @@ def oracle_run(u0, *, P, order, L, nu, dt, steps, mode, seed=0, forcing=0.0, del
 
 
 def gpu_ensemble_run(instances, *, M, order, steps, dtype="f64", mode=None, record=False, calls=None,
-                     max_ctas=0, stages=0, steps_per_pass=0, delays=None, tune=0, flags=0):
+                     max_ctas=0, stages=0, steps_per_pass=0, delays=None, tune=0, flags=0, tile_subdomains=0,
+                     modes=None):
     """Runs an ensemble through the C ABI (at_create_batch); returns dict(u, hist, rec, info, solver)."""
     import torch
 
@@ -73,7 +74,7 @@ def gpu_ensemble_run(instances, *, M, order, steps, dtype="f64", mode=None, reco
     from paper_1911_05769_gb300 import AT_FLAG_COMPENSATED, AT_FREE, AT_OK, AT_REPLAY, AT_SEEDED, EnsembleSolver, binding
     mode = AT_SEEDED if mode is None else mode
     s = EnsembleSolver(instances, M, order, dtype=dtype, max_ctas=max_ctas, stages=stages,
-                       steps_per_pass=steps_per_pass, flags=flags)
+                       steps_per_pass=steps_per_pass, flags=flags, tile_subdomains=tile_subdomains)
     u0 = torch.from_numpy(W.ensemble_field(instances)).cuda()
     res = {}
     if tune:
@@ -82,15 +83,16 @@ def gpu_ensemble_run(instances, *, M, order, steps, dtype="f64", mode=None, reco
     s.set_state(u0)
     calls = calls or [steps]
     assert sum(calls) == steps
+    modes = modes or [mode] * len(calls)      # a mode per call (delays recorded in every call)
     recs, done = [], 0
-    for c in calls:
+    for c, md in zip(calls, modes):
         d = None
-        if mode == AT_REPLAY:
+        if md == AT_REPLAY:
             d = torch.from_numpy(np.ascontiguousarray(delays[done:done + c])).cuda()
         elif record:
             d = torch.full((c, s.P, 2), -1, dtype=torch.int8, device="cuda")
-        s.step(c, mode, d)
-        if record and mode != AT_REPLAY:
+        s.step(c, md, d)
+        if record:
             recs.append(d)
         done += c
     out = torch.empty(s.N, dtype=s.tdtype, device="cuda")

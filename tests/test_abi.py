@@ -57,17 +57,20 @@ int main(void) {
   F(at_grid, dim); F(at_grid, bc); F(at_grid, dtype); F(at_grid, flags); F(at_grid, n); F(at_grid, length);
   F(at_grid, origin); F(at_grid, forcing_amp); F(at_grid, seed); F(at_grid, workspace);
   F(at_grid, workspace_bytes); F(at_grid, stream); F(at_grid, timeout_ns); F(at_grid, max_ctas);
-  F(at_grid, stages); F(at_grid, test_skip_step); F(at_grid, steps_per_pass); F(at_grid, sub);
+  F(at_grid, stages); F(at_grid, test_skip_step); F(at_grid, steps_per_pass); F(at_grid, tile_subdomains);
+  F(at_grid, sub);
   printf("at_info size %zu\n", sizeof(at_info));
   F(at_info, N); F(at_info, P); F(at_info, M); F(at_info, order); F(at_info, L); F(at_info, R); F(at_info, s);
   F(at_info, T); F(at_info, ctas); F(at_info, threads); F(at_info, stages); F(at_info, smem_bytes);
   F(at_info, step); F(at_info, sm_count); F(at_info, dtype); F(at_info, steps_per_pass); F(at_info, viscous_fp64);
+  F(at_info, tile_subdomains);
   printf("at_instance size %zu\n", sizeof(at_instance));
   F(at_instance, n); F(at_instance, L); F(at_instance, bc); F(at_instance, length); F(at_instance, origin);
   F(at_instance, nu); F(at_instance, dt); F(at_instance, tanh_a); F(at_instance, tanh_c); F(at_instance, tanh_xc);
   F(at_instance, seed);
   printf("at_tune_result size %zu\n", sizeof(at_tune_result));
   F(at_tune_result, ctas); F(at_tune_result, stages); F(at_tune_result, steps_per_pass);
+  F(at_tune_result, tile_subdomains);
   F(at_tune_result, n_tried); F(at_tune_result, best_ms); F(at_tune_result, first_ms);
   return 0;
 }

@@ -196,6 +196,93 @@ def test_autotuner_free_mode_shapes():
     s.close()
 
 
+# ---- multi-subdomain tiles (tile_subdomains K > 1, AT_FREE and AT_SYNC) ----
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("K,spp,order", [(2, 0, 2), (4, 4, 2), (4, 2, 4), (2, 4, 4)])
+def test_multi_subdomain_tiles_free_replays(dtype, K, spp, order):
+    """A tile advances K consecutive subdomains of an instance together; the
+    faces between them are at delay 0 and recorded so; every recorded delay
+    pattern replays in the oracle (periodic, one- and two-subdomain and
+    exact-boundary instances, tiles cut short at an instance end)."""
+    from paper_1911_05769_gb300 import AT_FREE
+    M = 256
+    inst = small_ensemble(M=M, seed=51 + K + order, log2_n=(8.0, 11.0), periodic=(0, 2))
+    inst[0]["n"] = 256
+    inst[2]["n"] = 768
+    for j in (0, 2):
+        d = inst[j]
+        x, dx = W.grid(d["n"], d["length"], d["origin"])
+        d["u0"] = 0.3 + 0.2 * np.sin(x) + 0.1 * np.sin(3 * x + 1)
+        d["dt"] = W.dt_rule(d["u0"], dx, d["nu"])
+    steps = 160
+    res = gpu_ensemble_run(inst, M=M, order=order, steps=steps, dtype=dtype, mode=AT_FREE, record=True, max_ctas=2,
+                           steps_per_pass=spp, tile_subdomains=K, calls=[61, 99])
+    assert res["info"].tile_subdomains == K
+    rec = res["rec"]
+    p0 = 0
+    for d in inst:
+        Pj = d["n"] // M
+        r = rec[:, p0:p0 + Pj, :]
+        assert r.min() >= 0 and r.max() <= d["L"]
+        p0 += Pj
+    check_against_oracle(inst, res, M=M, order=order, steps=steps, mode="replay", dtype=dtype, delays=rec)
+
+
+@pytest.mark.parametrize("spp", [0, 4])
+def test_multi_subdomain_tiles_sync_is_bitwise(spp):
+    """AT_SYNC with tiles of 4 subdomains (unblocked, and blocked in passes
+    of 4 levels with ghost cells) equals the one-subdomain-per-tile run bit
+    for bit."""
+    from paper_1911_05769_gb300 import AT_SYNC
+    M = 256
+    inst = small_ensemble(M=M, seed=61, log2_n=(8.0, 11.0), periodic=(1,))
+    one = gpu_ensemble_run(inst, M=M, order=2, steps=120, dtype="f64", mode=AT_SYNC, max_ctas=2, steps_per_pass=spp)
+    four = gpu_ensemble_run(inst, M=M, order=2, steps=120, dtype="f64", mode=AT_SYNC, max_ctas=2, steps_per_pass=spp,
+                            tile_subdomains=4)
+    assert np.array_equal(one["u"], four["u"])
+    assert np.array_equal(one["hist"], four["hist"])
+
+
+def test_multi_subdomain_tiles_across_modes():
+    """Seeded steps (one subdomain per tile), then free-running steps (tiles
+    of 4), then seeded again, then synchronous: the flags are brought to the
+    state's level whenever the tiling changes; the recorded delays replay."""
+    from paper_1911_05769_gb300 import AT_FREE, AT_SEEDED, AT_SYNC
+    M = 256
+    inst = small_ensemble(n_inst=12, M=M, seed=62, log2_n=(9.0, 11.5))
+    calls, modes = [30, 50, 40, 20], [AT_SEEDED, AT_FREE, AT_SEEDED, AT_SYNC]
+    res = gpu_ensemble_run(inst, M=M, order=2, steps=140, dtype="f64", mode=AT_FREE, record=True, max_ctas=3,
+                           steps_per_pass=3, tile_subdomains=4, calls=calls, modes=modes)
+    check_against_oracle(inst, res, M=M, order=2, steps=140, mode="replay", dtype="f64", delays=res["rec"])
+
+
+def test_multi_subdomain_tiles_compensated():
+    from paper_1911_05769_gb300 import AT_FLAG_COMPENSATED, AT_FREE
+    M = 256
+    inst = small_ensemble(M=M, seed=63, log2_n=(8.5, 11.0))
+    res = gpu_ensemble_run(inst, M=M, order=2, steps=200, dtype="f32", mode=AT_FREE, record=True, max_ctas=2,
+                           steps_per_pass=4, tile_subdomains=4, flags=AT_FLAG_COMPENSATED)
+    ref = oracle_ensemble(inst, M=M, order=2, steps=200, mode="replay", delays=res["rec"])
+    ph, pl = split(res["u"], res["offsets"]), split(res["lo"], res["offsets"])
+    for j, (u_ref, _) in ref.items():
+        assert rel_linf(ph[j] + pl[j], u_ref) <= 1e-6, j
+
+
+def test_autotuner_chooses_tile_subdomains():
+    """In free-running mode the tuner also tries 1, 2 and 4 subdomains per
+    tile and keeps the fastest shape; the run stays replayable."""
+    from paper_1911_05769_gb300 import AT_FREE
+    M = 256
+    inst = small_ensemble(n_inst=40, seed=64, M=M, log2_n=(10.0, 12.5))
+    res = gpu_ensemble_run(inst, M=M, order=2, steps=100, dtype="f64", mode=AT_FREE, record=True, tune=10,
+                           steps_per_pass=1)
+    t = res["tune"]
+    assert t.tile_subdomains in (1, 2, 4) and res["info"].tile_subdomains == t.tile_subdomains
+    assert t.n_tried >= 3
+    check_against_oracle(inst, res, M=M, order=2, steps=100, mode="replay", dtype="f64", delays=res["rec"])
+
+
 @pytest.mark.parametrize("kind", ["ensemble", "single"])
 def test_captured_graph_replays_continue(kind):
     """at_step captured once into a CUDA graph and replayed three times equals
@@ -321,12 +408,13 @@ def test_compensated_ensemble_matches_oracle(mode, order):
         assert rel_linf(ph[j] + pl[j], u_ref) <= 1e-6, (j, rel_linf(ph[j] + pl[j], u_ref))
 
 
-def test_full_ensemble_free_blocked_replay_sampled():
+@pytest.mark.parametrize("K", [1, 4])
+def test_full_ensemble_free_blocked_replay_sampled(K):
     from paper_1911_05769_gb300 import AT_FREE
     inst = W.ensemble()
     steps = 200
     res = gpu_ensemble_run(inst, M=256, order=2, steps=steps, dtype="f64", mode=AT_FREE, record=True,
-                           steps_per_pass=4)
+                           steps_per_pass=4, tile_subdomains=K)
     n = np.array([d["n"] for d in inst])
     which = set(np.argsort(n)[:3].tolist()) | {int(np.argmax(n))}
     check_against_oracle(inst, res, M=256, order=2, steps=steps, mode="replay", dtype="f64", delays=res["rec"],

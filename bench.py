@@ -330,7 +330,8 @@ def ensemble_config(args, at, torch, dev, stream):
         s.close()
         del g
         return {"value": Ntot * time_steps / (ms * 1e-3) / 1e9, "unit": UNIT, "ms_per_launch": ms,
-                "shape": {"ctas": info.ctas, "stages": info.stages, "steps_per_pass": info.steps_per_pass},
+                "shape": {"ctas": info.ctas, "stages": info.stages, "steps_per_pass": info.steps_per_pass,
+                          "tile_subdomains": info.tile_subdomains},
                 "tuned": None if t is None else {
                     "shapes_tried": t.n_tried, "ms_200_steps_first": t.first_ms, "ms_200_steps_best": t.best_ms}}
 

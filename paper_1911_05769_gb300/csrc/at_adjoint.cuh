@@ -103,20 +103,19 @@ struct AdjStep {
     }
 
     // halo value of point src extrapolated with delay k (same operations as
-    // the stepper's halo approximation)
+    // the stepper's halo approximation: Newton form)
     __device__ T halo(int src, int k) const
     {
         const T r0 = lev[off[k] + src];
         if (k == 0) return r0;
         const T r1 = lev[off[k + 1] + src];
+        const T d1 = r0 - r1;
         if constexpr (S_LEV == 2) {
-            return (T)(k + 1) * r0 - (T)k * r1;
+            return r0 + (T)k * d1;
         } else {
             const T r2 = lev[off[k + 2] + src];
-            const T w0 = (T)((k + 1) * (k + 2) / 2);
-            const T w1 = (T)(-k * (k + 2));
-            const T w2 = (T)(k * (k + 1) / 2);
-            return w0 * r0 + w1 * r1 + w2 * r2;
+            const T d2 = d1 - (r1 - r2);
+            return r0 + ((T)k * d1 + (T)(k * (k + 1) / 2) * d2);
         }
     }
 

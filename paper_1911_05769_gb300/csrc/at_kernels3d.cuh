@@ -389,7 +389,9 @@ __global__ void __launch_bounds__(NT, NT == kThreads3 ? AT_MIN_CTAS_3D : 2 * AT_
                 }
                 T *h = reinterpret_cast<T *>(smem + hat);
                 const int nw = (int)hwd;
-                const T a = (T)(kk + 1), b = (T)kk;
+                // (k+1) f0 - k f1 in Newton form f0 + k (f0 - f1): the difference
+                // of nearby levels is exact, so the rounding stays about an ulp
+                const T b = (T)kk;
                 for (int fld = 0; fld < NF; ++fld) {
                     const T *s0p = e0 + fld * fw, *s1p = e1 + fld * fw;
                     T *hp = h + fld * nw;
@@ -400,13 +402,13 @@ __global__ void __launch_bounds__(NT, NT == kThreads3 ? AT_MIN_CTAS_3D : 2 * AT_
                             if (kk != 0) {
                                 lds<T, 4>(s1p + i, v1);
 #pragma unroll
-                                for (int e = 0; e < 4; ++e) v0[e] = a * v0[e] - b * v1[e];
+                                for (int e = 0; e < 4; ++e) v0[e] = v0[e] + b * (v0[e] - v1[e]);
                             }
                             sts4<T>(hp + i, v0);
                         }
                     } else {
                         for (int i = lane; i < nw; i += 32)
-                            hp[i] = kk == 0 ? s0p[i] : a * s0p[i] - b * s1p[i];
+                            hp[i] = kk == 0 ? s0p[i] : s0p[i] + b * (s0p[i] - s1p[i]);
                     }
                 }
             }

@@ -42,6 +42,9 @@
 #ifndef AT_MIN_CTAS_PER_SM
 #define AT_MIN_CTAS_PER_SM 3
 #endif
+#ifndef AT_VGROUP
+#define AT_VGROUP 2
+#endif
 
 namespace atk {
 
@@ -68,6 +71,16 @@ struct SmemLayout {
 };
 
 __host__ __device__ inline long long round_up(long long x, long long a) { return (x + a - 1) / a * a; }
+
+// Groups of 4 points a lane of the stepper holds consecutively (see run_pe).
+template <int GW, bool FULL, bool BATCH, int PREC>
+__host__ __device__ constexpr int group_run() { return (!BATCH && FULL && PREC != 2 && GW % AT_VGROUP == 0) ? AT_VGROUP : 1; }
+
+// Place of group g of a subdomain in the forcing tables: with runs of VG
+// groups per lane the tables are stored run-slot-major, so that the lanes of
+// a warp, reading slot i of their runs, read consecutive 16-byte words.
+template <int VG>
+__host__ __device__ inline int table_group(int g, int NG) { return VG == 1 ? g : (g % VG) * (NG / VG) + g / VG; }
 
 __host__ __device__ inline SmemLayout smem_layout(long long M, int word, int stages, long long tab_bytes, bool comp = false)
 {
@@ -574,6 +587,13 @@ __device__ void run_pe(const Params &p, const Sweep &sw, long long lo, long long
     constexpr unsigned kAll = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const long long S = hi - lo;
+    // Groups of 4 points a lane holds consecutively (full single-domain
+    // tiles; else 1): register slot m of lane l is group
+    // VG l + m mod VG + 32 VG (m div VG), so that a lane updates runs of VG
+    // groups with register neighbours and exchanges words with its
+    // neighbour lanes once per run instead of once per group.
+    constexpr int VG = group_run<GW, FULL, BATCH, PREC>();
+    auto gidx = [&](int m) -> int { return VG * lane + (m % VG) + 32 * VG * (m / VG); };
     // Blocked synchronous mode (AT_SYNC in passes of sb > 1 levels): every
     // delay is 0, a grid barrier precedes each pass, and a tile takes, instead
     // of the ring's per-level halo, its neighbours' edge strips of R sb points
@@ -907,7 +927,7 @@ __device__ void run_pe(const Params &p, const Sweep &sw, long long lo, long long
         if (!turn) {
 #pragma unroll
             for (int m = 0; m < GW; ++m) {
-                const int g = lane + 32 * m;
+                const int g = gidx(m);
                 if (FULL || g < NG) lds<T, 4>(stile + 4 * g, c[m]);
                 else { c[m][0] = c[m][1] = c[m][2] = c[m][3] = (T)0; }
                 if constexpr (PREC == 2) {
@@ -1039,8 +1059,9 @@ __device__ void run_pe(const Params &p, const Sweep &sw, long long lo, long long
                     if constexpr (FORCED) {
                         if (left ? lane < G : lane - 16 < G) {
                             const int off = left ? (int)p.M + xo : xo;
-                            sv = sj[off];
-                            cv = cj[off];
+                            const int tp = 4 * table_group<VG>(off >> 2, (int)(p.M / 4)) + (off & 3);
+                            sv = sj[tp];
+                            cv = cj[tp];
                         }
                     }
                     T unused = (T)0;
@@ -1086,71 +1107,92 @@ __device__ void run_pe(const Params &p, const Sweep &sw, long long lo, long long
             auto point = [&](const T *w, const T *wl, T sv, T cv, T &err) -> T {
                 return stencil_point<T, ORDER, FORCED, PREC>(w, wl, cA, cB, cB64, fs, fc, sv, cv, err);
             };
-            // lane l holds groups g = l + 32 m of 4 points; neighbour words come
-            // from the adjacent lanes (lane 0 / 31: the other end of the warp at
-            // the previous / next m, or the halo)
-            T tail[R], rb[R];                                // old last words of group m-1; new last words of NG-1
+            // lane l holds runs of VG groups of 4 points (group gidx(m) in
+            // slot m); the neighbour words of a run come from the adjacent
+            // lanes (lane 0 / 31: the other end of the warp at the previous /
+            // next run, or the halo), those within a run from the lane's own
+            // registers
+            T tail[R], rb[R];                                // old last words of the previous run; new last words of NG-1
             T tail_l[R], rb_l[R];                            // (the same for the lo words, PREC 2)
 #pragma unroll
             for (int q = 0; q < R; ++q) { tail[q] = (T)0; rb[q] = (T)0; tail_l[q] = (T)0; rb_l[q] = (T)0; }
 #pragma unroll
-            for (int m = 0; m < GW; ++m) {
-                const int g = lane + 32 * m;
-                T v[4 + 2 * R];
-                T vl[PREC == 2 ? 4 + 2 * R : 1];
+            for (int b = 0; b < GW / VG; ++b) {
+                const int mf = b * VG, ml = mf + VG - 1;     // the run's first and last slot
+                T lh[R], rh[R];                              // words left of the run's first group, right of its last
+                T lhl[R], rhl[R];
 #pragma unroll
                 for (int q = 0; q < R; ++q) {
-                    const T to_next = (lane == 31) ? tail[q] : cs[m][4 - R + q];
-                    v[q] = __shfl_sync(kAll, to_next, up);
-                    const T to_prev = (lane == 0) ? cs[m + 1 < GW ? m + 1 : m][q] : cs[m][q];
-                    v[R + 4 + q] = __shfl_sync(kAll, to_prev, down);
+                    const T to_next = (lane == 31) ? tail[q] : cs[ml][4 - R + q];
+                    lh[q] = __shfl_sync(kAll, to_next, up);
+                    const T to_prev = (lane == 0) ? cs[b + 1 < GW / VG ? mf + VG : mf][q] : cs[mf][q];
+                    rh[q] = __shfl_sync(kAll, to_prev, down);
+                    lhl[q] = rhl[q] = (T)0;
                     if constexpr (PREC == 2) {
-                        const T ln = (lane == 31) ? tail_l[q] : er[m][4 - R + q];
-                        vl[q] = __shfl_sync(kAll, ln, up);
-                        const T lp = (lane == 0) ? er[m + 1 < GW ? m + 1 : m][q] : er[m][q];
-                        vl[R + 4 + q] = __shfl_sync(kAll, lp, down);
+                        const T ln = (lane == 31) ? tail_l[q] : er[ml][4 - R + q];
+                        lhl[q] = __shfl_sync(kAll, ln, up);
+                        const T lp = (lane == 0) ? er[b + 1 < GW / VG ? mf + VG : mf][q] : er[mf][q];
+                        rhl[q] = __shfl_sync(kAll, lp, down);
                     }
                 }
 #pragma unroll
-                for (int q = 0; q < R; ++q) tail[q] = cs[m][4 - R + q];
-#pragma unroll
-                for (int e = 0; e < 4; ++e) v[R + e] = cs[m][e];
-                if constexpr (PREC == 2) {
-#pragma unroll
-                    for (int q = 0; q < R; ++q) tail_l[q] = er[m][4 - R + q];
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) vl[R + e] = er[m][e];
+                for (int q = 0; q < R; ++q) {
+                    tail[q] = cs[ml][4 - R + q];
+                    if constexpr (PREC == 2) tail_l[q] = er[ml][4 - R + q];
                 }
-                if (m == 0) {
+                if (b == 0) {
 #pragma unroll
-                    for (int q = 0; q < R; ++q) v[q] = (lane == 0) ? hl[q] : v[q];
-                    if constexpr (PREC == 2) {
-#pragma unroll
-                        for (int q = 0; q < R; ++q) vl[q] = (lane == 0) ? hll[q] : vl[q];
+                    for (int q = 0; q < R; ++q) {
+                        lh[q] = (lane == 0) ? hl[q] : lh[q];
+                        if constexpr (PREC == 2) lhl[q] = (lane == 0) ? hll[q] : lhl[q];
                     }
                 }
-                const bool is_last = (m == m_last) && (lane == lane_last);
+                const bool is_last = (ml == m_last) && (lane == lane_last);
 #pragma unroll
-                for (int q = 0; q < R; ++q) v[R + 4 + q] = is_last ? hr[q] : v[R + 4 + q];
-                if constexpr (PREC == 2) {
-#pragma unroll
-                    for (int q = 0; q < R; ++q) vl[R + 4 + q] = is_last ? hrl[q] : vl[R + 4 + q];
-                }
-                T s4[4], c4[4];
-                if constexpr (FORCED) {
-                    const int gg = g < NG ? g : NG - 1;
-                    lds<T, 4>(sj + 4 * gg, s4);
-                    lds<T, 4>(cj + 4 * gg, c4);
+                for (int q = 0; q < R; ++q) {
+                    rh[q] = is_last ? hr[q] : rh[q];
+                    if constexpr (PREC == 2) rhl[q] = is_last ? hrl[q] : rhl[q];
                 }
 #pragma unroll
-                for (int e = 0; e < 4; ++e)
-                    cd[m][e] = point(v + e, vl + (PREC == 2 ? e : 0), s4[e], c4[e],
-                                     er[PREC == 2 ? m : 0][PREC == 2 ? e : 0]);
+                for (int i = 0; i < VG; ++i) {
+                    const int m = mf + i;
+                    const int g = gidx(m);
+                    T v[4 + 2 * R];
+                    T vl[PREC == 2 ? 4 + 2 * R : 1];
 #pragma unroll
-                for (int q = 0; q < R; ++q) rb[q] = (m == m_last) ? cd[m][4 - R + q] : rb[q];
-                if constexpr (PREC == 2) {
+                    for (int q = 0; q < R; ++q) {
+                        v[q] = lh[q];
+                        v[R + 4 + q] = (i == VG - 1) ? rh[q] : cs[m + 1 < GW ? m + 1 : m][q];
+                        lh[q] = cs[m][4 - R + q];            // old words: the next group's left neighbours
+                        if constexpr (PREC == 2) {
+                            vl[q] = lhl[q];
+                            vl[R + 4 + q] = (i == VG - 1) ? rhl[q] : er[m + 1 < GW ? m + 1 : m][q];
+                            lhl[q] = er[m][4 - R + q];
+                        }
+                    }
 #pragma unroll
-                    for (int q = 0; q < R; ++q) rb_l[q] = (m == m_last) ? er[m][4 - R + q] : rb_l[q];
+                    for (int e = 0; e < 4; ++e) {
+                        v[R + e] = cs[m][e];
+                        if constexpr (PREC == 2) vl[R + e] = er[m][e];
+                    }
+                    T s4[4], c4[4];
+                    if constexpr (FORCED) {
+                        // (full tiles: offsets known at compile time)
+                        const int gg = (FULL || g < NG) ? g : NG - 1;
+                        const int tg = table_group<VG>(gg, FULL ? 32 * GW : NG);
+                        lds<T, 4>(sj + 4 * tg, s4);
+                        lds<T, 4>(cj + 4 * tg, c4);
+                    }
+#pragma unroll
+                    for (int e = 0; e < 4; ++e)
+                        cd[m][e] = point(v + e, vl + (PREC == 2 ? e : 0), s4[e], c4[e],
+                                         er[PREC == 2 ? m : 0][PREC == 2 ? e : 0]);
+#pragma unroll
+                    for (int q = 0; q < R; ++q) rb[q] = (m == m_last) ? cd[m][4 - R + q] : rb[q];
+                    if constexpr (PREC == 2) {
+#pragma unroll
+                        for (int q = 0; q < R; ++q) rb_l[q] = (m == m_last) ? er[m][4 - R + q] : rb_l[q];
+                    }
                 }
             }
             // publish the new boundary values and release the edge flags
@@ -1231,7 +1273,7 @@ __device__ void run_pe(const Params &p, const Sweep &sw, long long lo, long long
             // of this tile and the fence of the arrival order them before it)
 #pragma unroll
             for (int m = 0; m < GW; ++m) {
-                const int g = lane + 32 * m;
+                const int g = gidx(m);
                 if (g < gq) stg4<T>(st0 + 4 * g, c[m]);
                 if (g >= NG - gq && g < NG) stg4<T>(st1 + 4 * (g - (NG - gq)), c[m]);
             }
@@ -1243,7 +1285,7 @@ __device__ void run_pe(const Params &p, const Sweep &sw, long long lo, long long
         if (!keep) {
 #pragma unroll
             for (int m = 0; m < GW; ++m) {
-                const int g = lane + 32 * m;
+                const int g = gidx(m);
                 if (FULL || g < NG) stg4<T>(ug + 4 * g, c[m]);
                 if constexpr (PREC == 2) {
                     if (FULL || g < NG) stg4<T>(reinterpret_cast<T *>(p.ur) + (size_t)s0 * p.M + 4 * g, er[m]);
@@ -1255,7 +1297,7 @@ __device__ void run_pe(const Params &p, const Sweep &sw, long long lo, long long
                     (size_t)s0 * p.M;
 #pragma unroll
             for (int m = 0; m < GW; ++m) {
-                const int g = lane + 32 * m;
+                const int g = gidx(m);
                 if (FULL || g < NG) stg4<T>(lg + 4 * g, c[m]);
             }
         }
@@ -1323,8 +1365,10 @@ __global__ void __launch_bounds__(kThreads, AT_MIN_CTAS_PER_SM) at_stepper(const
         for (long long i = threadIdx.x; i < p.M; i += blockDim.x) {
             double sv, cv;
             sincos((double)i * p.dx, &sv, &cv);
-            sj[i] = (T)sv;
-            cj[i] = (T)cv;
+            constexpr int VG = group_run<GW, FULL, BATCH, PREC>();
+            const long long tp = 4LL * table_group<VG>((int)(i >> 2), (int)(p.M / 4)) + (i & 3);
+            sj[tp] = (T)sv;
+            cj[tp] = (T)cv;
         }
         // entry i: subdomain lo - 1 + i (wrapped), i = 0 .. S + 1
         for (long long i = lane; i < S + 2; i += 32) {

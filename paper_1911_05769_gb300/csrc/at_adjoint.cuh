@@ -386,4 +386,278 @@ __global__ void __launch_bounds__(kAdjThreads, ORDER == 2 ? 7 : 3) at_adjoint_in
     }
 }
 
+// ---------------------------------------------------------------------------
+// The interval kernel for one subdomain per block (M <= kAdjOwnChunk points,
+// every subdomain's block resident): a block keeps its own lambda in
+// registers from level to level, and loads everything a level needs that does
+// not depend on lambda -- the delays, its points' stencil values, the pending
+// words its face threads will add to -- before the grid barrier that ends the
+// previous level, so that after the barrier a level waits for one round trip
+// at most (the neighbours' boundary lambdas and values, the pending words
+// addressed to this level; edge threads only).  Same arithmetic, in the same
+// order, as at_adjoint_interval.
+constexpr int kAdjOwnThreads = 128;
+constexpr int kAdjOwnPts = 8;                               // points per thread, kAdjOwnThreads apart
+constexpr int kAdjOwnChunk = kAdjOwnThreads * kAdjOwnPts;
+
+template <typename T, int ORDER>
+__global__ void __launch_bounds__(kAdjOwnThreads, 7) at_adjoint_own(const AdjParams a)
+{
+    constexpr int R = ORDER / 2;
+    constexpr int S_LEV = ORDER / 2 + 1;
+    constexpr int NT = kAdjOwnThreads, PTS = kAdjOwnPts;
+    __shared__ T s_c[2 * R + 1][kAdjOwnChunk];
+    __shared__ T red[NT / 32];
+    __shared__ long long s_off[2][kAdjMaxLevels];
+    __shared__ int s_ok;
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int M = (int)a.M, P = (int)a.P;
+    const int p = blockIdx.x;
+    const int pl = p == 0 ? P - 1 : p - 1, pr = p == P - 1 ? 0 : p + 1;
+    const T dtdx2 = sizeof(T) == 4 ? (T)a.dtdx2f : (T)a.dtdx2;
+    // the face threads: point 0 (face 0) and point M-1 (face 1)
+    const bool own_f0 = tid == 0, own_f1 = tid == (M - 1) % NT;
+    const int kp_f1 = (M - 1) / NT;
+
+    auto set_off = [&](long long n, int b) {
+        if (tid < kAdjMaxLevels) s_off[b][tid] = (n - tid >= 0) ? ((n - tid) % a.Dl) * a.N : 0;
+    };
+    // extrapolation weights of a face with delay k
+    auto weights = [&](int k, T *w) {
+        if constexpr (S_LEV == 2) {
+            w[0] = (T)(k + 1);
+            w[1] = (T)(-k);
+        } else {
+            w[0] = (T)((k + 1) * (k + 2) / 2);
+            w[1] = (T)(-k * (k + 2));
+            w[2] = (T)(k * (k + 1) / 2);
+        }
+    };
+
+    // what a level needs that does not depend on lambda
+    T v[PTS][2 * R + 1];          // stencil values of this thread's points
+    int k0 = 0, k1 = 0, kl1 = 0, kr0 = 0;
+    T pold[2][S_LEV][R];          // face threads: current pending words of the levels they add to
+    // (lanes 0..3: the raw delays of level n: this subdomain's faces 0, 1,
+    // the left neighbour's face 1, the right neighbour's face 0 -- loaded a
+    // level ahead, so that the prefetch below does not wait for them)
+    auto load_delays = [&](long long n) -> int {
+        const AdjStep<T, ORDER> A(a, n, s_off[0], nullptr);
+        return lane < 4 ? A.delay(lane < 2 ? p : (lane == 2 ? pl : pr), lane < 2 ? lane : (lane == 2 ? 1 : 0)) : 0;
+    };
+    auto prefetch = [&](long long n, int b, int kk) {
+        const AdjStep<T, ORDER> A(a, n, s_off[b], nullptr);
+        k0 = __shfl_sync(0xffffffffu, kk, 0);
+        k1 = __shfl_sync(0xffffffffu, kk, 1);
+        kl1 = __shfl_sync(0xffffffffu, kk, 2);
+        kr0 = __shfl_sync(0xffffffffu, kk, 3);
+#pragma unroll
+        for (int kp = 0; kp < PTS; ++kp) {
+            const int loc = tid + kp * NT;
+            if (loc < M) A.values(p, loc, k0, k1, v[kp]);
+        }
+#pragma unroll
+        for (int f = 0; f < 2; ++f) {
+            const bool mine = f == 0 ? own_f0 : own_f1;
+            const int k = f == 0 ? k0 : k1;
+            const int q = f == 0 ? pl : pr;
+            T w[S_LEV];
+            weights(k, w);
+#pragma unroll
+            for (int m = 0; m < S_LEV; ++m)
+#pragma unroll
+                for (int r = 0; r < R; ++r)
+                    pold[f][m][r] = (mine && k + m != 0 && w[m] != (T)0) ? *A.pend(n - k - m, q, f == 0 ? 1 : 0, r)
+                                                                         : (T)0;
+        }
+    };
+
+    // lambda^{n_hi} of this block's points
+    T lamr[PTS];
+    {
+        const T *l0 = reinterpret_cast<const T *>(a.lam_a);
+#pragma unroll
+        for (int kp = 0; kp < PTS; ++kp) {
+            const int loc = tid + kp * NT;
+            lamr[kp] = loc < M ? l0[(size_t)p * M + loc] : (T)0;
+        }
+    }
+    set_off(a.n_hi - 1, 0);
+    __syncthreads();
+    prefetch(a.n_hi - 1, 0, load_delays(a.n_hi - 1));
+    unsigned long long arrivals = 0;
+    for (long long n = a.n_hi - 1, it = 0; n >= a.n_lo; --n, ++it) {
+        const int b = (int)(it & 1);
+        // the next level's delays and level offsets, early
+        int kk_next = 0;
+        if (n > a.n_lo) {
+            kk_next = load_delays(n - 1);
+            set_off(n - 1, b ^ 1);
+        }
+        const T *lam_in = reinterpret_cast<const T *>((it & 1) ? a.lam_b : a.lam_a);
+        T *lam_out = reinterpret_cast<T *>((it & 1) ? a.lam_a : a.lam_b);
+        const AdjStep<T, ORDER> A(a, n, s_off[b], lam_in);
+        // the pending words addressed to this level (written by the
+        // neighbours' face threads at later levels), loaded before any store
+        // of the level: a thread holds at most one point within R of each face
+        // The neighbours' readers across the faces (their lambda^{n+1} and
+        // level-n values: an undelayed read lands on level n) likewise.
+        T pwL = (T)0, pwR = (T)0, eL = (T)0, eR = (T)0;
+        if (tid < R && tid < M) {
+            pwL = *A.pend(n, p, 0, tid);
+            if (kl1 == 0) {
+#pragma unroll
+                for (int d = -R; d < 0; ++d) {
+                    const int rl = tid + d;
+                    if (rl >= 0) continue;
+                    T vv[2 * R + 1];
+                    A.values(pl, M + rl, -1, kl1, vv);
+                    eL += A.gbar(pl * M + M + rl, -d, vv);
+                }
+            }
+        }
+        {
+            const int locR = tid + NT * ((M - 1 - tid) / NT);   // this thread's last point
+            if (tid <= M - 1 && locR >= M - R && locR >= R) {
+                pwR = *A.pend(n, p, 1, locR - (M - R));
+                if (kr0 == 0) {
+#pragma unroll
+                    for (int d = 1; d <= R; ++d) {
+                        const int rl = locR + d;
+                        if (rl < M) continue;
+                        T vv[2 * R + 1];
+                        A.values(pr, rl - M, kr0, -1, vv);
+                        eR += A.gbar(pr * M + (rl - M), -d, vv);
+                    }
+                }
+            }
+        }
+        // terms c_j = lambda^{n+1}_r d u^{n+1}_r / d v_j of this block's points
+        T nu_acc = (T)0;
+#pragma unroll
+        for (int kp = 0; kp < PTS; ++kp) {
+            const int loc = tid + kp * NT;
+            if (loc >= M) continue;
+            T av = (T)0, bv = (T)0;
+#pragma unroll
+            for (int q = -R; q <= R; ++q) {
+                av += (T)Coeffs<ORDER>::alpha(q) * v[kp][q + R];
+                bv += (T)Coeffs<ORDER>::beta(q) * v[kp][q + R];
+            }
+            const T g = lamr[kp];
+#pragma unroll
+            for (int j = -R; j <= R; ++j) {
+                T d = A.cB * (T)Coeffs<ORDER>::beta(j) - A.cA * v[kp][R] * (T)Coeffs<ORDER>::alpha(j);
+                if (j == 0) d += (T)1 - A.cA * av;
+                s_c[j + R][loc] = g * d;
+            }
+            nu_acc += g * bv;
+        }
+        __syncthreads();
+        // gather lambda^n_i; the neighbours' readers across the faces from
+        // their lambda^{n+1} and values (edge threads)
+#pragma unroll
+        for (int kp = 0; kp < PTS; ++kp) {
+            const int loc = tid + kp * NT;
+            if (loc >= M) continue;
+            const int i = p * M + loc;
+            T acc = (T)0;
+#pragma unroll
+            for (int d = -R; d <= R; ++d) {
+                const int rl = loc + d;
+                if (rl >= 0 && rl < M) acc += s_c[-d + R][rl];
+            }
+            // (the readers across the faces and the pending words, loaded
+            // above; the words are then cleared)
+            if (loc < R) acc += eL;
+            if (loc >= M - R && loc >= R) acc += eR;
+            if (loc < R) {
+                acc += pwL;
+                *A.pend(n, p, 0, loc) = (T)0;
+            } else if (loc >= M - R) {
+                acc += pwR;
+                *A.pend(n, p, 1, loc - (M - R)) = (T)0;
+            }
+            lam_out[i] = acc;
+            lamr[kp] = acc;
+        }
+        // this block's delayed reads across its faces, added to the
+        // neighbours' boundary words at older levels (the face threads)
+#pragma unroll
+        for (int f = 0; f < 2; ++f) {
+            if (!(f == 0 ? own_f0 : own_f1)) continue;
+            const int k = f == 0 ? k0 : k1;
+            const int q = f == 0 ? pl : pr;
+            const int off = f == 0 ? 0 : M - 1;
+            T w[S_LEV];
+            weights(k, w);
+            T src[R];
+#pragma unroll
+            for (int r = 0; r < R; ++r) src[r] = (T)0;
+#pragma unroll
+            for (int t = 0; t < R; ++t) {
+                const int rt = f == 0 ? off + t : off - t;
+#pragma unroll
+                for (int j = -R; j <= R; ++j) {
+                    const bool crosses = f == 0 ? (j <= -t - 1) : (j >= t + 1);
+                    if (!crosses) continue;
+                    src[f == 0 ? R + t + j : j - t - 1] += s_c[j + R][rt];
+                }
+            }
+#pragma unroll
+            for (int m = 0; m < S_LEV; ++m) {
+                if (k + m == 0 || w[m] == (T)0) continue;     // level n: gathered above
+#pragma unroll
+                for (int r = 0; r < R; ++r) *A.pend(n - k - m, q, f == 0 ? 1 : 0, r) = pold[f][m][r] + w[m] * src[r];
+            }
+        }
+        (void)kp_f1;
+        // dJ/dnu: warp sums in the state's precision; thread 0 adds the
+        // block's FP64 sum after the next block barrier
+        for (int o = 16; o > 0; o >>= 1) nu_acc += __shfl_xor_sync(0xffffffffu, nu_acc, o);
+        if (lane == 0) red[tid >> 5] = nu_acc;
+        // the next level's lambda-free data (its loads land during the barrier)
+        if (n > a.n_lo) prefetch(n - 1, b ^ 1, kk_next);
+        __syncthreads();
+        bool go = n > a.n_lo;
+        if (tid == 0) {
+            double sum = 0.0;
+            for (int w = 0; w < NT / 32; ++w) sum += (double)red[w] * (double)dtdx2;
+            atomicAdd(a.dnu_part + blockIdx.x, sum);
+            if (go) {
+                // grid barrier (bounded), as adjoint_grid_sync after its block barrier
+                arrivals += gridDim.x;
+                __threadfence();
+                atomicAdd(a.bar, 1ull);
+                bool ok = true;
+                if (ld_acquire(a.bar) < arrivals) {
+                    const unsigned long long t0 = global_ns();
+                    for (;;) {
+                        __nanosleep(32);
+                        if (ld_acquire(a.bar) >= arrivals) break;
+                        if (ld_relaxed(a.ctrl + kCtrlAbort)) { ok = false; break; }
+                        if ((long long)(global_ns() - t0) > a.timeout_ns) {
+                            if (atomicCAS(a.ctrl + kCtrlStatus, 0, kStatusTimeout) == 0) {
+                                a.ctrl[kCtrlCta] = (int)blockIdx.x;
+                                a.ctrl[kCtrlWhere] = kWhereAdjoint;
+                                a.ctrl[kCtrlNb] = -1;
+                                a.ctrl[kCtrlStep] = (int)n;
+                            }
+                            atomicExch(a.ctrl + kCtrlAbort, 1);
+                            ok = false;
+                            break;
+                        }
+                    }
+                }
+                __threadfence();
+                s_ok = ok ? 1 : 0;
+            }
+        }
+        if (go) {
+            __syncthreads();
+            if (!s_ok) return;
+        }
+    }
+}
+
 }  // namespace atk

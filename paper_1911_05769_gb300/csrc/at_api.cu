@@ -39,6 +39,7 @@ void *atk_batch_kernel_f32c(int order, int gw, bool full);
 void *atk_restore_kernel_f32(int order);
 void *atk_restore_kernel_f64(int order);
 void *atk_adjoint_kernel(int w, int order);
+void *atk_adjoint_own_kernel(int w, int order);
 void *atk_stepper3d_kernel(int w, int tc, int vw);
 void *atk_system3d_kernel(int w, int tc, int nf, int vw);
 void *atk_init3d_kernel(int w);
@@ -1464,15 +1465,30 @@ int at_adjoint(at_solver *h, int64_t n_steps, int delay_mode, const int8_t *dela
         a.dtdx2 = h->dt / (12.0 * h->dx * h->dx);
     }
     a.cAf = (float)a.cA; a.cBf = (float)a.cB; a.dtdx2f = (float)a.dtdx2;
-    void *kern = atk_adjoint_kernel(h->w, h->order);
-    // one cooperative launch per interval: every block resident
+    // one cooperative launch per interval: every block resident.  With one
+    // block per subdomain (M <= 1024 points, every subdomain's block
+    // resident) the variant that keeps lambda in registers and loads the next
+    // level's lambda-free data before the grid barrier; else blocks walk the
+    // subdomains
+    void *kern = atk_adjoint_own_kernel(h->w, h->order);
+    int threads = atk::kAdjOwnThreads;
     int occ = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, atk::kAdjThreads, 0);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, 0);
     if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor(adjoint)");
-    const int gy = adj_grid_y(h);
-    int gx = adj_grid_x(h);
-    if ((int64_t)gx * gy > (int64_t)occ * h->sm_count) gx = (int)((int64_t)occ * h->sm_count / gy);
-    if (gx < 1) return fail(AT_ERR_RESIDENCY, "adjoint: %d blocks per subdomain cannot be co-resident", gy);
+    int gy = 1, gx = (int)h->P;
+    // (FP32, order 2: the variant's per-thread data fits its registers there)
+    const bool own = h->w == 4 && h->order == 2 && h->M <= atk::kAdjOwnChunk &&
+                     h->P <= (int64_t)occ * h->sm_count && h->P <= adj_blocks(h);
+    if (!own) {
+        kern = atk_adjoint_kernel(h->w, h->order);
+        threads = atk::kAdjThreads;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, 0);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor(adjoint)");
+        gy = adj_grid_y(h);
+        gx = adj_grid_x(h);
+        if ((int64_t)gx * gy > (int64_t)occ * h->sm_count) gx = (int)((int64_t)occ * h->sm_count / gy);
+        if (gx < 1) return fail(AT_ERR_RESIDENCY, "adjoint: %d blocks per subdomain cannot be co-resident", gy);
+    }
     unsigned char *cur = static_cast<unsigned char *>(lam), *other = ws + al.lam;
     for (int64_t seg = nseg - 1; seg >= 0; --seg) {
         const int64_t c = seg * interval;
@@ -1502,7 +1518,7 @@ int at_adjoint(at_solver *h, int64_t n_steps, int delay_mode, const int8_t *dela
         if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(adjoint barrier)");
         cudaLaunchConfig_t cfg{};
         cfg.gridDim = dim3(gx, gy);
-        cfg.blockDim = dim3(atk::kAdjThreads);
+        cfg.blockDim = dim3(threads);
         cfg.stream = h->stream;
         cudaLaunchAttribute attr[1];
         attr[0].id = cudaLaunchAttributeCooperative;

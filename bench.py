@@ -67,6 +67,9 @@ def parse():
     ap.add_argument("--ensemble-only", action="store_true", help="time only the 2048-instance ensemble leg")
     ap.add_argument("--ens-time-steps", type=int, default=5000, help="time steps per ensemble launch")
     ap.add_argument("--no-tune", action="store_true", help="ensemble leg: keep the default launch shape")
+    ap.add_argument("--ens-shape", default="",
+                    help="ensemble leg without tuning, shape K,spp,stages,ctas (subdomains per tile, levels per "
+                         "pass of the free arm, tile buffers, CTAs), for profiling runs")
     ap.add_argument("--adjoint-only", action="store_true", help="time only the adjoint leg")
     ap.add_argument("--only-3d", action="store_true", help="time only the 3D leg")
     ap.add_argument("--only-system", action="store_true", help="time only the 3D system leg")
@@ -300,12 +303,21 @@ def ensemble_config(args, at, torch, dev, stream):
            "l2": f"state {Ntot * 4 / 2**20:.0f} MiB: close to the 126 MiB L2 (replays continue in place)"}
     Lmax = max(d["L"] for d in inst)
 
+    shape = [int(x) for x in args.ens_shape.split(",")] if args.ens_shape else None
+
     def run(mode, name, spp=None, flags=0):
+        kw = {}
+        if shape:
+            # (the compensated kernels hold fewer CTAs per SM: all that fit)
+            kw = dict(tile_subdomains=shape[0], stages=shape[2],
+                      max_ctas=0 if flags & at.AT_FLAG_COMPENSATED else shape[3])
+            if mode == at.AT_FREE and spp is None:
+                spp = shape[1]
         s = at.EnsembleSolver(inst, M, order, dtype="f32", stream=stream, device=dev.index, flags=flags,
-                              steps_per_pass=(Lmax + 1 if mode == at.AT_FREE else 0) if spp is None else spp)
+                              steps_per_pass=(Lmax + 1 if mode == at.AT_FREE else 0) if spp is None else spp, **kw)
         with torch.cuda.stream(stream):
             s.set_state(u0)
-        t = None if args.no_tune else s.tune(200, mode)
+        t = None if (args.no_tune or shape) else s.tune(200, mode)
         with torch.cuda.stream(stream):
             s.set_state(u0)
         torch.cuda.synchronize(dev)

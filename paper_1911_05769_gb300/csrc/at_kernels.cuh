@@ -1236,8 +1236,11 @@ __device__ void run_pe(const Params &p, const Sweep &sw, long long lo, long long
             if constexpr (BATCH) {
                 // the faces between the subdomains of a multi-subdomain tile
                 // (subdomains of 128, 256 or 512 points: a subdomain's first
-                // group is lane 0's, its last lane 31's): ring entries only
-                if (ti.cnt > 1 && (lane == 0 || lane == 31)) {
+                // group is lane 0's, its last lane 31's): ring entries only,
+                // and only of the launch's last L + s levels -- no tile of this
+                // launch reads them, and a later launch with other tiles reads
+                // back to its first level - L - s + 1 at most
+                if (ti.cnt > 1 && (lane == 0 || lane == 31) && lev > sw.n0 + sw.n_steps - (p.L + S_LEV)) {
                     const size_t slot_off = (size_t)(lev & (p.T - 1)) * slot_stride;
                     const int gsh = p.M == 128 ? 0 : p.M == 256 ? 1 : 2;      // m slots per subdomain: 1 << gsh
                     const int gmask = (1 << gsh) - 1;

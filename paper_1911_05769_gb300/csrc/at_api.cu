@@ -20,7 +20,7 @@
 #include "at.h"
 #include "at_adjoint.cuh"
 #include "at_kernels.cuh"
-#include "at_kernels3d.cuh"
+#include "at_kernels3d_blk.cuh"
 
 void *atk_stepper_kernel_f32(int order, int gw, bool forced, bool full);
 void *atk_stepper_kernel_f32v(int order, int gw, bool forced, bool full);
@@ -43,6 +43,7 @@ void *atk_adjoint_own_kernel(int w, int order);
 void *atk_stepper3d_kernel(int w, int tc, int vw);
 void *atk_system3d_kernel(int w, int tc, int nf, int vw);
 void *atk_init3d_kernel(int w);
+void *atk_stepper3d_blk_kernel(int w, int sb);
 
 namespace {
 
@@ -125,7 +126,9 @@ int check_args3(const at_grid *g, int64_t P, int order, int L, Dims3 *d)
     if (order != 2) return fail(AT_ERR_ARG, "3D solvers use scheme_order 2");
     if (L < 0 || L > atk::kMaxL) return fail(AT_ERR_ARG, "L must be in 0..%d", atk::kMaxL);
     if (g->forcing_amp != 0.0) return fail(AT_ERR_ARG, "3D solvers are unforced");
-    if (g->steps_per_pass > 1) return fail(AT_ERR_ARG, "3D solvers take one level per pass");
+    if (g->steps_per_pass < 0 || g->steps_per_pass > L + 1 || g->steps_per_pass > atk::kMaxPass3)
+        return fail(AT_ERR_ARG, "3D steps_per_pass must be in 0..min(L+1, %d), got %d", atk::kMaxPass3,
+                    g->steps_per_pass);
     int64_t np = 1;
     for (int a = 0; a < 3; ++a) {
         if (g->n[a] <= 0 || g->sub[a] <= 0 || g->n[a] % g->sub[a] != 0)
@@ -141,6 +144,9 @@ int check_args3(const at_grid *g, int64_t P, int order, int L, Dims3 *d)
     if (d->m[0] > 256 || d->m[1] > 256) return fail(AT_ERR_ARG, "sub[0] and sub[1] must be <= 256");
     if ((int64_t)d->m[0] * d->m[1] > 1024) return fail(AT_ERR_ARG, "sub[0] * sub[1] must be <= 1024");
     if (d->m[1] < 2 || d->m[2] < 3) return fail(AT_ERR_ARG, "sub[1] >= 2 and sub[2] >= 3 are required");
+    // blocked passes: a row of sub[0] / 4 groups of 4 columns lies within one warp
+    if (g->steps_per_pass > 1 && (d->m[0] > 128 || (d->m[0] & (d->m[0] - 1)) != 0))
+        return fail(AT_ERR_ARG, "3D steps_per_pass > 1 needs sub[0] a power of two in 4..128");
     if (P != np) return fail(AT_ERR_ARG, "P=%lld differs from the %lld subdomains of the grid", (long long)P, (long long)np);
     if (P >= (1LL << 31)) return fail(AT_ERR_ARG, "at most 2^31 - 1 subdomains (P=%lld)", (long long)P);
     int64_t fw = (int64_t)d->m[1] * d->m[2];
@@ -342,6 +348,8 @@ struct at_solver {
     const void *flags_list;    // tile list of the launch that last released flags
     void *kernel;
     void *kernel_bs;           // the blocked synchronous mode's kernel (NULL: none)
+    void *kernel_b3;           // 3D: the blocked free-running kernel (NULL: none)
+    int G_b3, stages_b3, smem_b3;   // 3D: its CTAs, plane stages and shared memory
     bool bs_ok;                // it can run in the launch shape chosen for `kernel`
     void *init_kernel;
 };
@@ -560,6 +568,8 @@ static int create3d(const at_grid *grid, int64_t P, int L, int nf, const double 
     const int nt = (vw == 4 && nf == 1) ? 128 : atk::kThreads3;
     const int tc = vw == 4 ? (nf == 1 ? 2 : 1) : pw <= atk::kThreads3 ? 1 : pw <= 2 * atk::kThreads3 ? 2 : 4;
     if (nf > 1 && vw == 1 && tc > 2) return fail(AT_ERR_ARG, "the 3D system needs sub[0] * sub[1] <= 512 (or 1024, FP32)");
+    const int sb = grid->steps_per_pass > 0 ? grid->steps_per_pass : 1;
+    if (nf > 1 && sb > 1) return fail(AT_ERR_ARG, "the 3D system takes one level per pass");
     void *kern = nf == 1 ? atk_stepper3d_kernel(w, tc, vw) : atk_system3d_kernel(w, tc, nf, vw);
     // plane buffers: at least 3 (planes z and z+1 in use, one arriving), at most sub[2]
     int stages = grid->stages > 0 ? grid->stages : 4;
@@ -602,8 +612,39 @@ static int create3d(const at_grid *grid, int64_t P, int L, int nf, const double 
     h->G = (int)G;
     h->stages = stages;
     h->smem = (int)sl3.total;
-    h->sb = 1;
+    h->sb = sb;
     h->lmin = L;
+    h->kernel_b3 = nullptr;
+    if (sb > 1) {
+        // the blocked free-running kernel: 256 threads (a group of 4 columns
+        // each), its own plane stages (2 in use, the rest arriving) and grid
+        void *kb = atk_stepper3d_blk_kernel(w, sb);
+        int st = grid->stages > 0 ? grid->stages : 4;
+        if (st < 3) st = 3;
+        if (st > d.m[2]) st = d.m[2];
+        atk::Smem3b sb3 = atk::smem3b_layout(d.m[0], d.m[1], d.face_words, w, st, sb);
+        while (sb3.total > smem_optin && st > 3) sb3 = atk::smem3b_layout(d.m[0], d.m[1], d.face_words, w, --st, sb);
+        if (sb3.total > smem_optin) {
+            delete h;
+            return fail(AT_ERR_RESIDENCY, "blocked 3D passes: shared memory %lld exceeds %d", sb3.total, smem_optin);
+        }
+        e = cudaFuncSetAttribute(kb, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb3.total);
+        if (e != cudaSuccess) { delete h; return cuda_fail(e, "cudaFuncSetAttribute"); }
+        int occb = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occb, kb, atk::kThreads3b, (size_t)sb3.total);
+        if (e != cudaSuccess) { delete h; return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor"); }
+        int64_t Gb = grid->max_ctas > 0 ? grid->max_ctas : (int64_t)occb * sms;
+        if (Gb > P) Gb = P;
+        if (occb < 1 || (int64_t)occb * sms < Gb) {
+            delete h;
+            return fail(AT_ERR_RESIDENCY, "blocked 3D passes: %lld CTAs cannot be co-resident (occupancy %d per SM)",
+                        (long long)Gb, occb);
+        }
+        h->kernel_b3 = kb;
+        h->G_b3 = (int)Gb;
+        h->stages_b3 = st;
+        h->smem_b3 = (int)sb3.total;
+    }
     // tensor map of the state: boxes of sub[0] x sub[1] x 1 points (one plane
     // of a subdomain), encoded through the driver entry point of the runtime
     PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
@@ -853,10 +894,14 @@ static int step_impl(at_solver *h, int64_t n_steps, int delay_mode, int8_t *dela
         p.mode = delay_mode;
         p.delays = delays;
         p.n_steps = n_steps;
+        // free-running passes of several levels: the blocked kernel
+        const bool blk = delay_mode == AT_FREE && h->kernel_b3 != nullptr;
+        p.sb = blk ? h->sb : 1;
+        if (blk) { p.G = h->G_b3; p.stages = h->stages_b3; }
         cudaLaunchConfig_t cfg{};
-        cfg.gridDim = dim3(h->G);
-        cfg.blockDim = dim3(h->nt3);
-        cfg.dynamicSmemBytes = (size_t)h->smem;
+        cfg.gridDim = dim3(blk ? h->G_b3 : h->G);
+        cfg.blockDim = dim3(blk ? atk::kThreads3b : h->nt3);
+        cfg.dynamicSmemBytes = (size_t)(blk ? h->smem_b3 : h->smem);
         cfg.stream = h->stream;
         cudaLaunchAttribute attr[1];
         attr[0].id = cudaLaunchAttributeCooperative;
@@ -864,7 +909,7 @@ static int step_impl(at_solver *h, int64_t n_steps, int delay_mode, int8_t *dela
         cfg.attrs = attr;
         cfg.numAttrs = 1;
         void *args[] = {&p, &h->tmap};
-        const cudaError_t e = cudaLaunchKernelExC(&cfg, h->kernel, args);
+        const cudaError_t e = cudaLaunchKernelExC(&cfg, blk ? h->kernel_b3 : h->kernel, args);
         if (e != cudaSuccess) return cuda_fail(e, "cooperative launch of at_stepper3d");
         h->step += n_steps;
         return AT_OK;

@@ -55,6 +55,7 @@ struct Params3 {
     int m0, m1, m2;             // points per subdomain per axis
     long long P0, P1, P2, P;
     int L, T, mode, stages;
+    int sb;                     // levels per pass (the blocked free-running stepper)
     long long n_steps;
     unsigned long long seed;
     double cA[3], cB[3];        // dt / (2 dx_a), nu dt / dx_a^2

@@ -204,10 +204,11 @@ class Solver3D(Solver):
     """Scalar 3D Burgers on a periodic box of n = (n0, n1, n2) points (x fastest)
     in subdomains of sub = (m0, m1, m2) points, order 2, six AT faces per
     subdomain.  The state is a flat tensor of n0 n1 n2 words (or shaped
-    (n2, n1, n0)); delays are [n_steps, P, 6]."""
+    (n2, n1, n0)); delays are [n_steps, P, 6].  steps_per_pass > 1: AT_FREE
+    steps advance each subdomain that many levels per pass (at most L + 1)."""
 
     def __init__(self, n, sub, L, nu, dt, *, dtype="f32", length=(2 * math.pi,) * 3, seed=0, flags=0,
-                 timeout_ns=0, max_ctas=0, stages=0, stream=None, device=None):
+                 timeout_ns=0, max_ctas=0, stages=0, steps_per_pass=0, stream=None, device=None):
         import torch
         self.torch = torch
         dev = torch.device("cuda", torch.cuda.current_device() if device is None else device)
@@ -226,6 +227,7 @@ class Solver3D(Solver):
         g.timeout_ns = timeout_ns
         g.max_ctas = max_ctas
         g.stages = stages
+        g.steps_per_pass = steps_per_pass
         P = 1
         for a in range(3):
             P *= int(n[a]) // int(sub[a])

@@ -131,6 +131,29 @@ def test_3d_workspace_and_subdomain_count_limit(B):
     assert B.at_workspace_bytes(g, 1 << 31, 2, 2) == 0 and "2^31" in B.at_last_error()
 
 
+def test_3d_steps_per_pass_validation(B):
+    """3D passes of several levels: at most L + 1 (and 4) levels, and rows of
+    a power-of-two sub[0] (4 .. 128) so a row's column groups lie in one warp."""
+    g = _grid(B, dtype=B.AT_F32)
+    g.dim = 3
+    for a, (n, m) in enumerate([(64, 32), (64, 32), (32, 8)]):
+        g.n[a], g.sub[a], g.length[a] = n, m, 6.283185307179586
+    for spp in (0, 1, 2, 3):
+        g.steps_per_pass = spp
+        assert B.at_workspace_bytes(g, 2 * 2 * 4, 2, 2) > 0
+    g.steps_per_pass = 4                                   # > L + 1
+    assert B.at_workspace_bytes(g, 2 * 2 * 4, 2, 2) == 0 and "steps_per_pass" in B.at_last_error()
+    assert B.at_workspace_bytes(g, 2 * 2 * 4, 2, 3) > 0
+    g.steps_per_pass = 5                                   # > 4 levels of registers
+    assert B.at_workspace_bytes(g, 2 * 2 * 4, 2, 6) == 0 and "steps_per_pass" in B.at_last_error()
+    g.steps_per_pass = 2
+    for a, (n, m) in enumerate([(48, 12), (64, 32), (32, 8)]):   # sub[0] = 12: not a power of two
+        g.n[a], g.sub[a] = n, m
+    assert B.at_workspace_bytes(g, 4 * 2 * 4, 2, 2) == 0 and "power of two" in B.at_last_error()
+    g.steps_per_pass = 1
+    assert B.at_workspace_bytes(g, 4 * 2 * 4, 2, 2) > 0
+
+
 def test_create_rejects_bad_arguments_on_the_host(B):
     g = _grid(B)
     dx = 6.283185307179586 / 4096

@@ -11,14 +11,14 @@ pytestmark = pytest.mark.gpu
 
 
 def gpu_run3d(u0, *, sub, L, nu, dt, steps, dtype="f64", mode=None, seed=0, max_ctas=0, stages=0, delays=None,
-              record=False, calls=None, length=(2 * np.pi,) * 3):
+              record=False, calls=None, length=(2 * np.pi,) * 3, steps_per_pass=0):
     import torch
 
     from paper_1911_05769_gb300 import AT_OK, AT_REPLAY, AT_SEEDED, Solver3D, binding
     mode = AT_SEEDED if mode is None else mode
     n2, n1, n0 = u0.shape
     s = Solver3D((n0, n1, n2), sub, L, nu, dt, dtype=dtype, seed=seed, max_ctas=max_ctas, stages=stages,
-                 length=length)
+                 length=length, steps_per_pass=steps_per_pass)
     s.set_state(torch.from_numpy(np.ascontiguousarray(u0).ravel()).cuda())
     calls = calls or [steps]
     recs, done = [], 0
@@ -152,3 +152,86 @@ def test_workload_parameters_all_2000_steps_3d():
                       length=(box,) * 3)
         assert rel_linf(g["u"], ref) <= TOL[dtype], (dtype, rel_linf(g["u"], ref))
         assert np.array_equal(g["hist"], hist)
+
+
+def check_pass_structure(rec, spp, starts):
+    """Delays of blocked passes: a pass from level lv > 0 of b levels gives
+    level lv + j the delay k0 + j on every face (the halo of the pass is
+    extrapolated from one pair of levels); the pass from level 0 has one level
+    at delay 0."""
+    n = rec.shape[0]
+    assert np.all(rec[0] == 0) if starts[0] == 0 else True
+    for lv in starts:
+        if lv == 0:
+            continue
+        b = min(spp, n - lv)
+        for j in range(1, b):
+            assert np.array_equal(rec[lv + j].astype(int) - rec[lv].astype(int), np.full(rec[lv].shape, j))
+
+
+BLOCKED = [
+    # (n, sub, L, steps_per_pass, max_ctas, calls)
+    (32, (16, 8, 8), 3, 2, 5, None),          # several subdomains per CTA
+    (32, (16, 8, 8), 3, 4, 0, None),          # L + 1 levels per pass, one subdomain per CTA
+    (32, (32, 32, 16), 2, 3, 3, None),        # planes of 1024 points (every thread busy)
+    (24, (8, 4, 3), 2, 3, 7, None),           # planes of 32 points, 3 planes per subdomain
+    (32, (16, 16, 8), 2, 3, 0, [7, 12, 17]),  # several calls: passes restart at each call's first level
+]
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("n,sub,L,spp,max_ctas,calls", BLOCKED)
+def test_blocked_free_3d_replays_in_oracle(dtype, n, sub, L, spp, max_ctas, calls):
+    """Free-running passes of steps_per_pass levels: the recorded delays
+    (within L, k0 + j over a pass) replayed by the oracle give the kernel's
+    result, and the delay histogram is theirs."""
+    from paper_1911_05769_gb300 import AT_FREE
+    nu = NU[n]
+    u0, dt = case(n, seed=11)
+    P = tuple(n // m for m in sub)
+    steps = sum(calls) if calls else 36
+    g = gpu_run3d(u0, sub=sub, L=L, nu=nu, dt=dt, steps=steps, dtype=dtype, mode=AT_FREE, record=True,
+                  max_ctas=max_ctas, steps_per_pass=spp, calls=calls)
+    assert g["info"].steps_per_pass == spp
+    rec = g["rec"]
+    assert rec.min() >= 0 and rec.max() <= L
+    starts, lv = [], 0
+    for c in (calls or [steps]):
+        end, lv = lv + c, lv
+        while lv < end:
+            starts.append(lv)
+            lv += 1 if lv == 0 else min(spp, end - lv)
+    check_pass_structure(rec, spp, starts)
+    ref, hist = oracle.run3d(u0, P=P, L=L, nu=nu, dt=dt, n_steps=steps, delay_mode=oracle.REPLAY, replay=rec)
+    assert rel_linf(g["u"], ref) <= TOL[dtype], rel_linf(g["u"], ref)
+    assert np.array_equal(g["hist"], hist)
+    assert np.array_equal(np.bincount(rec.ravel(), minlength=L + 1), hist)
+
+
+def test_blocked_free_3d_mixed_with_other_modes():
+    """Blocked free-running calls between seeded and synchronous calls: each
+    call finds the ring levels it reads, whatever the previous call's mode."""
+    import torch
+
+    from paper_1911_05769_gb300 import AT_FREE, AT_OK, AT_SEEDED, AT_SYNC, Solver3D, binding
+    n, sub, L = 32, (16, 8, 8), 3
+    nu = NU[n]
+    u0, dt = case(n, seed=12)
+    P = tuple(n // m for m in sub)
+    s = Solver3D((n, n, n), sub, L, nu, dt, dtype="f64", seed=3, max_ctas=6, steps_per_pass=3)
+    s.set_state(torch.from_numpy(np.ascontiguousarray(u0).ravel()).cuda())
+    recs = []
+    for c, mode in ((10, AT_FREE), (7, AT_SEEDED), (9, AT_FREE), (3, AT_SYNC), (8, AT_FREE)):
+        d = torch.full((c, s.P, 6), -1, dtype=torch.int8, device="cuda")
+        s.step(c, mode, d)
+        rec = d.cpu().numpy()
+        if mode == AT_SYNC:
+            rec[:] = 0
+        recs.append(rec)
+    rec = np.concatenate(recs, axis=0)
+    assert rec.min() >= 0 and rec.max() <= L
+    out = torch.empty(s.N, dtype=s.tdtype, device="cuda")
+    assert binding.at_state(s.h, out.data_ptr()) == AT_OK, binding.at_last_error()
+    s.close()
+    ref, _ = oracle.run3d(u0, P=P, L=L, nu=nu, dt=dt, n_steps=rec.shape[0], delay_mode=oracle.REPLAY, replay=rec)
+    assert rel_linf(out.double().cpu().numpy().reshape(u0.shape), ref) <= TOL["f64"]

@@ -61,6 +61,11 @@ __host__ __device__ inline Smem3b smem3b_layout(int m0, int m1, long long face_w
     return l;
 }
 
+template <int V>
+struct IntC {
+    static constexpr int value = V;
+};
+
 // levels of the pass that starts at level lv (the launch ends at level lev_end)
 __host__ __device__ inline long long pass_len3(long long lv, long long lev_end, int sb)
 {
@@ -218,6 +223,8 @@ __global__ void __launch_bounds__(kThreads3b, sizeof(T) == 4 ? 2 : 1)
                 const T *e1 = ring_entry<T>(p, lv - k0 - 1, q, f ^ 1);
                 const int nw = f < 2 ? m1 * m2 : f < 4 ? m0 * m2 : m0 * m1;
                 if ((nw & 3) == 0) {
+                    // (several rows in flight: the tile start waits for these loads)
+#pragma unroll 4
                     for (int i = 4 * lane; i < nw; i += 128) {
                         T v0[4], v1[4];
                         lds<T, 4>(e0 + i, v0);               // (a 16-byte generic load of global memory)
@@ -246,87 +253,101 @@ __global__ void __launch_bounds__(kThreads3b, sizeof(T) == 4 ? 2 : 1)
         }
         if (__syncthreads_or(bad)) { ok = false; break; }
         T *uz = reinterpret_cast<T *>(p.u) + (((long long)tz0 * plane_words + (long long)ty0 * p.n0) + tx0) + coff;
+        // ring entries of the pass's last two levels; levels from `ring_from`
+        // on are published too (a later call of any mode may read the
+        // launch's last L + 2 levels)
+        T *const rbB = ring_entry<T>(p, lv + b, sub, 0);
+        T *const rbA = ring_entry<T>(p, lv + b - 1, sub, 0);
+        const long long rf64 = lev_end - p.L - 1 - lv;
+        const int ring_from = rf64 < 1 ? 1 : rf64 > BM + 1 ? BM + 1 : (int)rf64;
         // plane 0 of level lv
         int sc = ws;                                         // stage of plane t
         bad = wait_next() ? 0 : 1;
         if (!bad) lds<T, VW>(stage_at(sc) + c, Cw[0]);
-        // ---- steps of the wavefront
-        const int nst = m2 + b - 1;
-        for (int t = 0; t < nst; ++t) {
+
+        // level i (1 .. BM) of the pass at plane z = t - i + 1.  ST: a step
+        // of the steady state (every level of a full pass at an interior
+        // plane: no guards, no z faces)
+        auto level = [&](auto I, auto STEADY, int t, int sn, T *up) {
+            constexpr int i = decltype(I)::value, j = i - 1;
+            constexpr bool ST = decltype(STEADY)::value != 0;
+            const int z = t - i + 1;
+            if (!ST && (i > b || z < 0 || z >= m2)) return;   // (uniform over the CTA)
+            const bool top = !ST && z == m2 - 1, bot = !ST && z == 0;
+            // level j at plane z: the stage (j = 0) or the level's plane buffer
+            const T *pl = j == 0 ? stage_at(sc)
+                                 : reinterpret_cast<const T *>(smem + o_lvl + (2 * (j > 0 ? j - 1 : 0) + (z & 1)) * pbytes);
+            T ab[VW], bl[VW], ym[VW], yp[VW], un[VW];
+            if (top) lds<T, VW>(halo_at(5, j) + c, ab);
+            else if (j == 0) lds<T, VW>(stage_at(sn) + c, ab);
+            else {
+#pragma unroll
+                for (int e = 0; e < VW; ++e) ab[e] = up[e];
+            }
+            if (bot) lds<T, VW>(halo_at(4, j) + c, bl);
+            else {
+#pragma unroll
+                for (int e = 0; e < VW; ++e) bl[e] = Pw[j][e];
+            }
+            lds<T, VW>(fy0 ? halo_at(2, j) + z * m0 + cx : pl + c - m0, ym);
+            lds<T, VW>(fy1 ? halo_at(3, j) + z * m0 + cx : pl + c + m0, yp);
+            // x neighbours beyond the group: the neighbouring lanes' words,
+            // or the x halos at a row's ends
+            T xl = __shfl_up_sync(0xffffffffu, Cw[j][VW - 1], 1);
+            T xr = __shfl_down_sync(0xffffffffu, Cw[j][0], 1);
+            if (fx0) xl = halo_at(0, j)[z * m1 + cy];
+            if (fx1) xr = halo_at(1, j)[z * m1 + cy];
+#pragma unroll
+            for (int e = 0; e < VW; ++e) {
+                const T cc = Cw[j][e];
+                const T xm = e == 0 ? xl : Cw[j][e > 0 ? e - 1 : 0];
+                const T xp = e == VW - 1 ? xr : Cw[j][e + 1 < VW ? e + 1 : e];
+                const T d2 = cB0 * ((xp + xm) - (T)2 * cc) + cB1 * ((yp[e] + ym[e]) - (T)2 * cc) +
+                             cB2 * ((ab[e] + bl[e]) - (T)2 * cc);
+                const T d1 = cA0 * (xp - xm) + cA1 * (yp[e] - ym[e]) + cA2 * (ab[e] - bl[e]);
+                un[e] = cc + (d2 - cc * d1);
+            }
+            const bool last = ST ? i == BM : i == b;
+            if (cv) {
+                if (!last) sts4<T>(reinterpret_cast<T *>(smem + o_lvl + (2 * (i - 1) + (z & 1)) * pbytes) + c, un);
+                else stv<T, VW>(uz + (long long)z * plane_words, un);
+            }
+            // the last two levels of the pass (and the launch's last L + 2)
+            // go to the ring
+            const bool ring = ST ? (i + 1 >= BM || i >= ring_from) : (i + 1 >= b || i >= ring_from);
+            if (ring && cv) {
+                T *rb = last ? rbB : (ST ? i + 1 == BM : i + 1 == b) ? rbA : ring_entry<T>(p, lv + i, sub, 0);
+                if (fx0) rb[z * m1 + cy] = un[0];
+                if (fx1) rb[fw + z * m1 + cy] = un[VW - 1];
+                if (fy0) stv<T, VW>(rb + 2 * fw + z * m0 + cx, un);
+                if (fy1) stv<T, VW>(rb + 3 * fw + z * m0 + cx, un);
+                if (bot) stv<T, VW>(rb + 4 * fw + c, un);
+                if (top) stv<T, VW>(rb + 5 * fw + c, un);
+            }
+            // level j's planes move up by one; level i starts its own
+            // window at plane 0; level i + 1 takes un as its plane above
+#pragma unroll
+            for (int e = 0; e < VW; ++e) {
+                Pw[j][e] = Cw[j][e];
+                Cw[j][e] = ab[e];
+                if (i < BM && bot) Cw[i < BM ? i : 0][e] = un[e];
+                up[e] = un[e];
+            }
+        };
+        // one step of the wavefront: levels 1 .. BM, a CTA barrier (the
+        // plane buffers written now are read at the next step; the stage of
+        // plane t is free after it), the refill of that stage
+        auto step = [&](int t, auto STEADY) -> bool {
             const int sn = ws;                               // stage of plane t + 1
             if (t + 1 < m2 && !bad) bad = wait_next() ? 0 : 1;
             if (!bad) {
                 T up[VW];                                    // level i - 1 at plane z + 1 (this step)
-#pragma unroll
-                for (int i = 1; i <= BM; ++i) {
-                    const int j = i - 1;
-                    const int z = t - i + 1;
-                    if (i > b || z < 0 || z >= m2) continue;   // (uniform over the CTA)
-                    // level j at plane z: the stage (j = 0) or the level's plane buffer
-                    const T *pl = j == 0 ? stage_at(sc)
-                                         : reinterpret_cast<const T *>(smem + o_lvl + (2 * (j - 1) + (z & 1)) * pbytes);
-                    T ab[VW], bl[VW], ym[VW], yp[VW], un[VW];
-                    if (z == m2 - 1) lds<T, VW>(halo_at(5, j) + c, ab);
-                    else if (j == 0) lds<T, VW>(stage_at(sn) + c, ab);
-                    else {
-#pragma unroll
-                        for (int e = 0; e < VW; ++e) ab[e] = up[e];
-                    }
-                    if (z == 0) lds<T, VW>(halo_at(4, j) + c, bl);
-                    else {
-#pragma unroll
-                        for (int e = 0; e < VW; ++e) bl[e] = Pw[j][e];
-                    }
-                    lds<T, VW>(fy0 ? halo_at(2, j) + z * m0 + cx : pl + c - m0, ym);
-                    lds<T, VW>(fy1 ? halo_at(3, j) + z * m0 + cx : pl + c + m0, yp);
-                    // x neighbours beyond the group: the neighbouring lanes'
-                    // words, or the x halos at a row's ends
-                    T xl = __shfl_up_sync(0xffffffffu, Cw[j][VW - 1], 1);
-                    T xr = __shfl_down_sync(0xffffffffu, Cw[j][0], 1);
-                    if (fx0) xl = halo_at(0, j)[z * m1 + cy];
-                    if (fx1) xr = halo_at(1, j)[z * m1 + cy];
-#pragma unroll
-                    for (int e = 0; e < VW; ++e) {
-                        const T cc = Cw[j][e];
-                        const T xm = e == 0 ? xl : Cw[j][e > 0 ? e - 1 : 0];
-                        const T xp = e == VW - 1 ? xr : Cw[j][e + 1 < VW ? e + 1 : e];
-                        const T d2 = cB0 * ((xp + xm) - (T)2 * cc) + cB1 * ((yp[e] + ym[e]) - (T)2 * cc) +
-                                     cB2 * ((ab[e] + bl[e]) - (T)2 * cc);
-                        const T d1 = cA0 * (xp - xm) + cA1 * (yp[e] - ym[e]) + cA2 * (ab[e] - bl[e]);
-                        un[e] = cc + (d2 - cc * d1);
-                    }
-                    if (cv) {
-                        if (i < b) sts4<T>(reinterpret_cast<T *>(smem + o_lvl + (2 * (i - 1) + (z & 1)) * pbytes) + c, un);
-                        else stv<T, VW>(uz + (long long)z * plane_words, un);
-                    }
-                    // the last two levels of the pass go to the ring, and
-                    // every level a later call of any mode may read
-                    // (levels >= the launch's last level - L - 1)
-                    if (i + 1 >= b || lv + i >= lev_end - p.L - 1) {
-                        T *rb = ring_entry<T>(p, lv + i, sub, 0);
-                        if (cv) {
-                            if (fx0) rb[z * m1 + cy] = un[0];
-                            if (fx1) rb[fw + z * m1 + cy] = un[VW - 1];
-                            if (fy0) stv<T, VW>(rb + 2 * fw + z * m0 + cx, un);
-                            if (fy1) stv<T, VW>(rb + 3 * fw + z * m0 + cx, un);
-                            if (z == 0) stv<T, VW>(rb + 4 * fw + c, un);
-                            if (z == m2 - 1) stv<T, VW>(rb + 5 * fw + c, un);
-                        }
-                    }
-                    // level j's planes move up by one; level i starts its own
-                    // window at plane 0; level i + 1 takes un as its plane above
-#pragma unroll
-                    for (int e = 0; e < VW; ++e) {
-                        Pw[j][e] = Cw[j][e];
-                        Cw[j][e] = ab[e];
-                        if (i < BM && z == 0) Cw[i < BM ? i : 0][e] = un[e];
-                        up[e] = un[e];
-                    }
-                }
+                level(IntC<1>{}, STEADY, t, sn, up);
+                if constexpr (BM >= 2) level(IntC<2>{}, STEADY, t, sn, up);
+                if constexpr (BM >= 3) level(IntC<3>{}, STEADY, t, sn, up);
+                if constexpr (BM >= 4) level(IntC<4>{}, STEADY, t, sn, up);
             }
-            // the plane buffers written this step are read at the next one;
-            // the stage of plane t is free after this barrier
-            if (__syncthreads_or(bad)) { ok = false; break; }
+            if (__syncthreads_or(bad)) return false;
             if (tid == 0 && t < m2) {
                 const long long gq = g0 + t + NS;
                 if (gq < Q) {
@@ -335,7 +356,18 @@ __global__ void __launch_bounds__(kThreads3b, sizeof(T) == 4 ? 2 : 1)
                 }
             }
             sc = sn;
+            return true;
+        };
+        // ---- steps of the wavefront: a full pass runs its interior steps
+        // (t = BM .. m2 - 2) in the steady form
+        const int nst = m2 + b - 1;
+        int t = 0;
+        if (b == BM) {
+            for (; t < BM && ok; ++t) ok = step(t, IntC<0>{});
+#pragma unroll 2
+            for (; t <= m2 - 2 && ok; ++t) ok = step(t, IntC<1>{});
         }
+        for (; t < nst && ok; ++t) ok = step(t, IntC<0>{});
         if (!ok) break;
         // the next bulk read of this tile's output (its next pass) follows
         // a later barrier

@@ -43,7 +43,7 @@ void *atk_adjoint_own_kernel(int w, int order);
 void *atk_stepper3d_kernel(int w, int tc, int vw);
 void *atk_system3d_kernel(int w, int tc, int nf, int vw);
 void *atk_init3d_kernel(int w);
-void *atk_stepper3d_blk_kernel(int w, int sb);
+void *atk_stepper3d_blk_kernel(int w, int sb, int iso);
 
 namespace {
 
@@ -618,7 +618,10 @@ static int create3d(const at_grid *grid, int64_t P, int L, int nf, const double 
     if (sb > 1) {
         // the blocked free-running kernel: 256 threads (a group of 4 columns
         // each), its own plane stages (2 in use, the rest arriving) and grid
-        void *kb = atk_stepper3d_blk_kernel(w, sb);
+        // (equal spacing on the three axes: one coefficient pair, the
+        // neighbours summed first)
+        const int iso = dx[0] == dx[1] && dx[1] == dx[2];
+        void *kb = atk_stepper3d_blk_kernel(w, sb, iso);
         int st = grid->stages > 0 ? grid->stages : 4;
         if (st < 3) st = 3;
         if (st > d.m[2]) st = d.m[2];

@@ -1,13 +1,17 @@
 // at_kernels3d_blk.cu -- instantiations of the temporally blocked free-running
-// scalar 3D stepper (float and double state; 2, 3 or 4 levels per pass).
+// scalar 3D stepper (float and double state; 2, 3 or 4 levels per pass;
+// equal or unequal spacing on the three axes).
 #include "at_kernels3d_blk.cuh"
 
-__attribute__((visibility("hidden"))) void *atk_stepper3d_blk_kernel(int w, int sb)
+template <typename T, bool ISO>
+static void *blk_kernel(int sb)
 {
-    if (w == 8) {
-        return sb == 2 ? (void *)atk::at_stepper3d_blk<double, 2>
-                       : sb == 3 ? (void *)atk::at_stepper3d_blk<double, 3> : (void *)atk::at_stepper3d_blk<double, 4>;
-    }
-    return sb == 2 ? (void *)atk::at_stepper3d_blk<float, 2>
-                   : sb == 3 ? (void *)atk::at_stepper3d_blk<float, 3> : (void *)atk::at_stepper3d_blk<float, 4>;
+    return sb == 2 ? (void *)atk::at_stepper3d_blk<T, 2, ISO>
+                   : sb == 3 ? (void *)atk::at_stepper3d_blk<T, 3, ISO> : (void *)atk::at_stepper3d_blk<T, 4, ISO>;
+}
+
+__attribute__((visibility("hidden"))) void *atk_stepper3d_blk_kernel(int w, int sb, int iso)
+{
+    if (w == 8) return iso ? blk_kernel<double, true>(sb) : blk_kernel<double, false>(sb);
+    return iso ? blk_kernel<float, true>(sb) : blk_kernel<float, false>(sb);
 }

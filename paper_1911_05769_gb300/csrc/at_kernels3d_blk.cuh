@@ -74,8 +74,9 @@ __host__ __device__ inline long long pass_len3(long long lv, long long lev_end, 
     return r < sb ? r : sb;
 }
 
-// BM: levels of a full pass (p.sb == BM)
-template <typename T, int BM>
+// BM: levels of a full pass (p.sb == BM); ISO: equal spacing on the three
+// axes (one coefficient pair: the six neighbours summed before scaling)
+template <typename T, int BM, bool ISO>
 __global__ void __launch_bounds__(kThreads3b, sizeof(T) == 4 ? 2 : 1)
     at_stepper3d_blk(const Params3 p, const __grid_constant__ CUtensorMap tmap)
 {
@@ -159,12 +160,13 @@ __global__ void __launch_bounds__(kThreads3b, sizeof(T) == 4 ? 2 : 1)
     const bool fx0 = cx == 0, fx1 = cx + VW == m0, fy0 = cy == 0, fy1 = cy == m1 - 1;
 
     // level j of the pass (j = 0: the state read; j < b): planes z - 1, z of
-    // this thread's columns while level j + 1 is at plane z
-    T Pw[BM][VW], Cw[BM][VW];
+    // this thread's columns while level j + 1 is at plane z, plane z in slot
+    // z & 1 and plane z - 1 in the other
+    T W[BM][2][VW];
 #pragma unroll
     for (int j = 0; j < BM; ++j)
 #pragma unroll
-        for (int e = 0; e < VW; ++e) Pw[j][e] = Cw[j][e] = (T)0;
+        for (int e = 0; e < VW; ++e) W[j][0][e] = W[j][1][e] = (T)0;
 
     if (tid == 0)
         for (int k = 0; k < NS && k < Q; ++k) issue_plane(k, tx0, ty0, tz0 + k);
@@ -263,14 +265,16 @@ __global__ void __launch_bounds__(kThreads3b, sizeof(T) == 4 ? 2 : 1)
         // plane 0 of level lv
         int sc = ws;                                         // stage of plane t
         bad = wait_next() ? 0 : 1;
-        if (!bad) lds<T, VW>(stage_at(sc) + c, Cw[0]);
+        if (!bad) lds<T, VW>(stage_at(sc) + c, W[0][0]);
 
-        // level i (1 .. BM) of the pass at plane z = t - i + 1.  ST: a step
-        // of the steady state (every level of a full pass at an interior
-        // plane: no guards, no z faces)
+        // level i (1 .. BM) of the pass at plane z = t - i + 1.  STEADY 1 / 2:
+        // a step of the steady state (every level of a full pass at an
+        // interior plane: no guards, no z faces) with t even / odd, so that
+        // the window slots are known at compile time; 0: any step
         auto level = [&](auto I, auto STEADY, int t, int sn, T *up) {
             constexpr int i = decltype(I)::value, j = i - 1;
             constexpr bool ST = decltype(STEADY)::value != 0;
+            constexpr int ZP = ((decltype(STEADY)::value - 1 - i + 1) % 2 + 2) % 2;   // z & 1 (steady)
             const int z = t - i + 1;
             if (!ST && (i > b || z < 0 || z >= m2)) return;   // (uniform over the CTA)
             const bool top = !ST && z == m2 - 1, bot = !ST && z == 0;
@@ -284,28 +288,39 @@ __global__ void __launch_bounds__(kThreads3b, sizeof(T) == 4 ? 2 : 1)
 #pragma unroll
                 for (int e = 0; e < VW; ++e) ab[e] = up[e];
             }
-            if (bot) lds<T, VW>(halo_at(4, j) + c, bl);
-            else {
+            // level j at planes z (cw) and z - 1 from the window
+            const bool odd = ST ? ZP != 0 : (z & 1) != 0;
+            T cw[VW];
 #pragma unroll
-                for (int e = 0; e < VW; ++e) bl[e] = Pw[j][e];
+            for (int e = 0; e < VW; ++e) {
+                cw[e] = odd ? W[j][1][e] : W[j][0][e];
+                bl[e] = odd ? W[j][0][e] : W[j][1][e];
             }
+            if (bot) lds<T, VW>(halo_at(4, j) + c, bl);
             lds<T, VW>(fy0 ? halo_at(2, j) + z * m0 + cx : pl + c - m0, ym);
             lds<T, VW>(fy1 ? halo_at(3, j) + z * m0 + cx : pl + c + m0, yp);
             // x neighbours beyond the group: the neighbouring lanes' words,
             // or the x halos at a row's ends
-            T xl = __shfl_up_sync(0xffffffffu, Cw[j][VW - 1], 1);
-            T xr = __shfl_down_sync(0xffffffffu, Cw[j][0], 1);
+            T xl = __shfl_up_sync(0xffffffffu, cw[VW - 1], 1);
+            T xr = __shfl_down_sync(0xffffffffu, cw[0], 1);
             if (fx0) xl = halo_at(0, j)[z * m1 + cy];
             if (fx1) xr = halo_at(1, j)[z * m1 + cy];
 #pragma unroll
             for (int e = 0; e < VW; ++e) {
-                const T cc = Cw[j][e];
-                const T xm = e == 0 ? xl : Cw[j][e > 0 ? e - 1 : 0];
-                const T xp = e == VW - 1 ? xr : Cw[j][e + 1 < VW ? e + 1 : e];
-                const T d2 = cB0 * ((xp + xm) - (T)2 * cc) + cB1 * ((yp[e] + ym[e]) - (T)2 * cc) +
-                             cB2 * ((ab[e] + bl[e]) - (T)2 * cc);
-                const T d1 = cA0 * (xp - xm) + cA1 * (yp[e] - ym[e]) + cA2 * (ab[e] - bl[e]);
-                un[e] = cc + (d2 - cc * d1);
+                const T cc = cw[e];
+                const T xm = e == 0 ? xl : cw[e > 0 ? e - 1 : 0];
+                const T xp = e == VW - 1 ? xr : cw[e + 1 < VW ? e + 1 : e];
+                if constexpr (ISO) {
+                    const T sum = ((xp + xm) + (yp[e] + ym[e])) + (ab[e] + bl[e]);
+                    const T dif = ((xp - xm) + (yp[e] - ym[e])) + (ab[e] - bl[e]);
+                    const T d2 = cB0 * (sum - (T)6 * cc);
+                    un[e] = cc + (d2 - cc * (cA0 * dif));
+                } else {
+                    const T d2 = cB0 * ((xp + xm) - (T)2 * cc) + cB1 * ((yp[e] + ym[e]) - (T)2 * cc) +
+                                 cB2 * ((ab[e] + bl[e]) - (T)2 * cc);
+                    const T d1 = cA0 * (xp - xm) + cA1 * (yp[e] - ym[e]) + cA2 * (ab[e] - bl[e]);
+                    un[e] = cc + (d2 - cc * d1);
+                }
             }
             const bool last = ST ? i == BM : i == b;
             if (cv) {
@@ -324,13 +339,14 @@ __global__ void __launch_bounds__(kThreads3b, sizeof(T) == 4 ? 2 : 1)
                 if (bot) stv<T, VW>(rb + 4 * fw + c, un);
                 if (top) stv<T, VW>(rb + 5 * fw + c, un);
             }
-            // level j's planes move up by one; level i starts its own
-            // window at plane 0; level i + 1 takes un as its plane above
+            // level j's planes move up by one (plane z + 1 replaces plane
+            // z - 1); level i starts its own window at plane 0; level i + 1
+            // takes un as its plane above
 #pragma unroll
             for (int e = 0; e < VW; ++e) {
-                Pw[j][e] = Cw[j][e];
-                Cw[j][e] = ab[e];
-                if (i < BM && bot) Cw[i < BM ? i : 0][e] = un[e];
+                if (odd) W[j][0][e] = ab[e];
+                else W[j][1][e] = ab[e];
+                if (i < BM && bot) W[i < BM ? i : 0][0][e] = un[e];
                 up[e] = un[e];
             }
         };
@@ -364,8 +380,12 @@ __global__ void __launch_bounds__(kThreads3b, sizeof(T) == 4 ? 2 : 1)
         int t = 0;
         if (b == BM) {
             for (; t < BM && ok; ++t) ok = step(t, IntC<0>{});
-#pragma unroll 2
-            for (; t <= m2 - 2 && ok; ++t) ok = step(t, IntC<1>{});
+            // (t = BM, BM + 1, ...: parities known at compile time)
+            for (; t + 1 <= m2 - 2 && ok; t += 2) {
+                ok = step(t, IntC<1 + (BM & 1)>{});
+                if (ok) ok = step(t + 1, IntC<1 + ((BM + 1) & 1)>{});
+            }
+            if (t <= m2 - 2 && ok) ok = step(t++, IntC<1 + (BM & 1)>{});
         }
         for (; t < nst && ok; ++t) ok = step(t, IntC<0>{});
         if (!ok) break;

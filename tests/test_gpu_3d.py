@@ -235,3 +235,25 @@ def test_blocked_free_3d_mixed_with_other_modes():
     s.close()
     ref, _ = oracle.run3d(u0, P=P, L=L, nu=nu, dt=dt, n_steps=rec.shape[0], delay_mode=oracle.REPLAY, replay=rec)
     assert rel_linf(out.double().cpu().numpy().reshape(u0.shape), ref) <= TOL["f64"]
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_blocked_free_3d_unequal_spacing(dtype):
+    """Blocked free-running passes on a box with unequal spacing (z half as
+    long: the stepper's per-axis coefficients rather than its equal-spacing
+    form), recorded delays replayed by the oracle."""
+    from paper_1911_05769_gb300 import AT_FREE
+    n, sub, L, spp = 32, (16, 8, 8), 2, 3
+    nu = NU[n]
+    u0 = W.u0_spectral3d(n, seed=13, kmax=8)
+    length = (2 * np.pi, 2 * np.pi, np.pi)
+    dx = tuple(a / n for a in length)
+    dt = W.dt_rule(u0, min(dx), nu, dim=3)
+    P = tuple(n // m for m in sub)
+    g = gpu_run3d(u0, sub=sub, L=L, nu=nu, dt=dt, steps=30, dtype=dtype, mode=AT_FREE, record=True, max_ctas=5,
+                  steps_per_pass=spp, length=length)
+    rec = g["rec"]
+    assert rec.min() >= 0 and rec.max() <= L
+    ref, hist = oracle.run3d(u0, P=P, L=L, nu=nu, dt=dt, n_steps=30, dx=dx, delay_mode=oracle.REPLAY, replay=rec)
+    assert rel_linf(g["u"], ref) <= TOL[dtype], rel_linf(g["u"], ref)
+    assert np.array_equal(g["hist"], hist)

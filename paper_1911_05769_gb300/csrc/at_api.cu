@@ -41,6 +41,7 @@ void *atk_restore_kernel_f64(int order);
 void *atk_adjoint_kernel(int w, int order);
 void *atk_adjoint_own_kernel(int w, int order);
 void *atk_stepper3d_kernel(int w, int tc, int vw);
+void *atk_stepper3d_iso_kernel(int w, int tc, int vw);
 void *atk_system3d_kernel(int w, int tc, int nf, int vw);
 void *atk_init3d_kernel(int w);
 void *atk_stepper3d_blk_kernel(int w, int sb, int iso);
@@ -570,7 +571,11 @@ static int create3d(const at_grid *grid, int64_t P, int L, int nf, const double 
     if (nf > 1 && vw == 1 && tc > 2) return fail(AT_ERR_ARG, "the 3D system needs sub[0] * sub[1] <= 512 (or 1024, FP32)");
     const int sb = grid->steps_per_pass > 0 ? grid->steps_per_pass : 1;
     if (nf > 1 && sb > 1) return fail(AT_ERR_ARG, "the 3D system takes one level per pass");
-    void *kern = nf == 1 ? atk_stepper3d_kernel(w, tc, vw) : atk_system3d_kernel(w, tc, nf, vw);
+    // (the scalar equation with equal spacing on the three axes: one
+    // coefficient pair, the neighbours summed first)
+    const int iso = dx[0] == dx[1] && dx[1] == dx[2];
+    void *kern = nf == 1 ? (iso ? atk_stepper3d_iso_kernel(w, tc, vw) : atk_stepper3d_kernel(w, tc, vw))
+                         : atk_system3d_kernel(w, tc, nf, vw);
     // plane buffers: at least 3 (planes z and z+1 in use, one arriving), at most sub[2]
     int stages = grid->stages > 0 ? grid->stages : 4;
     if (stages < 3) stages = 3;
@@ -618,9 +623,6 @@ static int create3d(const at_grid *grid, int64_t P, int L, int nf, const double 
     if (sb > 1) {
         // the blocked free-running kernel: 256 threads (a group of 4 columns
         // each), its own plane stages (2 in use, the rest arriving) and grid
-        // (equal spacing on the three axes: one coefficient pair, the
-        // neighbours summed first)
-        const int iso = dx[0] == dx[1] && dx[1] == dx[2];
         void *kb = atk_stepper3d_blk_kernel(w, sb, iso);
         int st = grid->stages > 0 ? grid->stages : 4;
         if (st < 3) st = 3;

@@ -1,6 +1,7 @@
 // at_kernels3d.cu -- instantiations of the scalar 3D stepper (float and double
 // state; 1, 2 or 4 columns per thread, or for float two groups of 4
-// consecutive columns in 128-thread CTAs) and the 3D init kernel.
+// consecutive columns in 128-thread CTAs; unequal spacing on the axes, the
+// equal-spacing instances are in at_kernels3d_iso.cu) and the 3D init kernel.
 #include "at_kernels3d.cuh"
 
 // Scalar 3D stepper for word size w (4 or 8), tc column groups per thread

@@ -196,7 +196,9 @@ __device__ __forceinline__ void stv(T *g, const T *v)
     }
 }
 
-template <typename T, int TC, int NF, bool SYS, int VW, int NT = kThreads3>
+// ISO (the scalar equation): equal spacing on the three axes, one
+// coefficient pair, the six neighbours summed before scaling
+template <typename T, int TC, int NF, bool SYS, int VW, int NT = kThreads3, bool ISO = false>
 __global__ void __launch_bounds__(NT, NT == kThreads3 ? AT_MIN_CTAS_3D : 2 * AT_MIN_CTAS_3D)
     at_stepper3d(const Params3 p, const __grid_constant__ CUtensorMap tmap)
 {
@@ -486,6 +488,10 @@ __global__ void __launch_bounds__(NT, NT == kThreads3 ? AT_MIN_CTAS_3D : 2 * AT_
                             const T adv = cA0 * Uv[e] * (xp - xm) + cA1 * Vv[e] * (yp[e] - ym[e]) +
                                           cA2 * Wv[e] * (above - below);
                             un[e] = cc + (d2 - adv);
+                        } else if constexpr (ISO) {
+                            const T sum = ((xp + xm) + (yp[e] + ym[e])) + (above + below);
+                            const T dif = ((xp - xm) + (yp[e] - ym[e])) + (above - below);
+                            un[e] = cc + (cB[f][0] * (sum - (T)6 * cc) - cc * (cA0 * dif));
                         } else {
                             const T d1 = cA0 * (xp - xm) + cA1 * (yp[e] - ym[e]) + cA2 * (above - below);
                             un[e] = cc + (d2 - cc * d1);

@@ -125,7 +125,8 @@ typedef struct at_grid {
                             /* points (ghost cells), bit for bit the result of    */
                             /* a barrier every step; the count is reduced until  */
                             /* a strip fits 16 words, 64 bytes and one subdomain */
-                            /* (one level per pass with AT_FLAG_COMPENSATED)      */
+                            /* (one level per pass with AT_FLAG_COMPENSATED).  3D:*/
+                            /* AT_FREE only, see the 3D section below             */
   int32_t  tile_subdomains;  /* ensembles: subdomains per tile (0 or 1: one; 2 or  */
                             /* 4 with M of 128, 256 or 512 and K M <= 1024): in   */
                             /* AT_FREE and AT_SYNC a tile advances K consecutive  */
@@ -143,7 +144,9 @@ typedef struct at_info {
   int32_t order, L;         /* stencil order, maximal delay                        */
   int32_t R, s;             /* stencil radius, levels per halo approximation       */
   int32_t T;                /* ring slots (levels kept per boundary)               */
-  int32_t ctas;             /* CTAs of the persistent kernel                       */
+  int32_t ctas;             /* CTAs of the persistent kernel (3D with              */
+                            /* steps_per_pass > 1: those of the blocked AT_FREE   */
+                            /* kernel, as threads, stages and smem_bytes)         */
   int32_t threads;          /* threads per CTA                                     */
   int32_t stages;           /* tile buffers per warp (3D: plane buffers per CTA)   */
   int64_t smem_bytes;       /* dynamic shared memory per CTA                       */
@@ -233,8 +236,18 @@ const char *at_last_error(void);
  * per (level, subdomain, face); AT_SEEDED draws it at counter (n P + p) 6 +
  * face.  at_create's P must equal the number of subdomains; scheme_order must
  * be 2.  The delay arrays of at_step are [n_steps][P][6].  Stability limit
- * for at_create: nu dt (1/dx^2 + 1/dy^2 + 1/dz^2) <= 1/2.  No forcing,
- * temporal blocking, ensembles, adjoint or autotuner in 3D.
+ * for at_create: nu dt (1/dx^2 + 1/dy^2 + 1/dz^2) <= 1/2.
+ * Temporal blocking (scalar equation, AT_FREE): grid->steps_per_pass b in
+ * 2 .. min(L+1, 4) with sub[0] a power of two in 4..128 advances each
+ * subdomain b levels per pass (the pass from level 0: one level) in a
+ * wavefront along z; the halo of level n + j of a pass is extrapolated from
+ * the neighbour's newest published level s <= n and s - 1 with delay
+ * n + j - s, so a pass waits only until that delay stays within L.  Delays
+ * are recorded per level as for one level per pass; AT_SEEDED, AT_REPLAY and
+ * AT_SYNC calls of the same solver take one level per pass.  Its shared
+ * memory (6 b halo faces, 2 (b - 1) planes, the plane stages) must fit one
+ * CTA, else at_create fails with AT_ERR_RESIDENCY.  No forcing, ensembles,
+ * adjoint or autotuner in 3D; the system below takes one level per pass.
  * --------------------------------------------------------------------------- */
 
 /* The full system of Eq. BS in 3D: velocity components u, v, w and 0..2

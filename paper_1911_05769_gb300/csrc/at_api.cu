@@ -1059,6 +1059,11 @@ int at_get_info(const at_solver *h, at_info *info)
     info->dtype = h->g.dtype; info->steps_per_pass = h->sb;
     info->viscous_fp64 = h->v64 ? 1 : 0;
     info->tile_subdomains = h->batch ? h->K : 1;
+    if (h->dim == 3 && h->kernel_b3) {
+        // 3D with several levels per pass: the blocked AT_FREE kernel's shape
+        info->ctas = h->G_b3; info->threads = atk::kThreads3b; info->stages = h->stages_b3;
+        info->smem_bytes = h->smem_b3;
+    }
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     if (h->has_state && cudaStreamIsCapturing(h->stream, &cap) == cudaSuccess && cap == cudaStreamCaptureStatusNone) {
         long long n0 = 0;

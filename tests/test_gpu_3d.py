@@ -193,6 +193,7 @@ def test_blocked_free_3d_replays_in_oracle(dtype, n, sub, L, spp, max_ctas, call
     g = gpu_run3d(u0, sub=sub, L=L, nu=nu, dt=dt, steps=steps, dtype=dtype, mode=AT_FREE, record=True,
                   max_ctas=max_ctas, steps_per_pass=spp, calls=calls)
     assert g["info"].steps_per_pass == spp
+    assert g["info"].threads == 256              # the blocked kernel's CTAs
     rec = g["rec"]
     assert rec.min() >= 0 and rec.max() <= L
     starts, lv = [], 0

@@ -73,7 +73,8 @@ extern "C" {
 #define AT_FLAG_ALLOW_UNSTABLE      2  /* skip the stability check of at_create */
 #define AT_FLAG_TEST_SKIP_PUBLISH   4  /* test only: CTA 0 stops publishing its
                                           progress flags after level test_skip_step,
-                                          so that its neighbours' waits time out */
+                                          so that its neighbours' waits time out
+                                          (1D: its first warp; 3D: its subdomains) */
 #define AT_FLAG_VISCOUS_FP64        8  /* FP32 state: form the viscous term nu dt D2 u
                                           and add it to u in FP64 (one rounding per
                                           update).  Chosen automatically when

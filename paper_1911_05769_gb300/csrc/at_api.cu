@@ -702,6 +702,8 @@ static atk::Params3 make_params3(const at_solver *h)
             p.cBf32[f][a] = (float)(h->nf > 1 ? (f < h->nf ? p.cBf[f][a] : 0.0) : p.cB[a]);
     }
     p.nf = h->nf;
+    p.skip_publish = (h->g.flags & AT_FLAG_TEST_SKIP_PUBLISH) ? 1 : 0;
+    p.skip_step = h->g.test_skip_step;
     p.face_words = h->d3.face_words;
     p.G = h->G;
     p.timeout_ns = h->g.timeout_ns;

@@ -56,6 +56,8 @@ struct Params3 {
     long long P0, P1, P2, P;
     int L, T, mode, stages;
     int sb;                     // levels per pass (the blocked free-running stepper)
+    int skip_publish;           // test knob: CTA 0 stops releasing flags beyond level skip_step
+    long long skip_step;
     long long n_steps;
     unsigned long long seed;
     double cA[3], cB[3];        // dt / (2 dx_a), nu dt / dx_a^2
@@ -330,7 +332,7 @@ __global__ void __launch_bounds__(NT, NT == kThreads3 ? AT_MIN_CTAS_3D : 2 * AT_
         // flags, grid barrier (synchronous mode), delays, halos
         __syncthreads();
         if (*s_flag == -1) { ok = false; break; }
-        if (tid == 0 && prev_sub >= 0) {
+        if (tid == 0 && prev_sub >= 0 && !(p.skip_publish && blockIdx.x == 0 && prev_new > p.skip_step)) {
             __threadfence();
             for (int f = 0; f < 6; ++f) st_release(p.flag + prev_sub * 6 + f, (unsigned long long)prev_new);
         }
@@ -546,7 +548,7 @@ __global__ void __launch_bounds__(NT, NT == kThreads3 ? AT_MIN_CTAS_3D : 2 * AT_
         tile_coords(sub + 1 == hi ? lo : sub + 1, &nx0, &ny0, &nz0);
     }
     __syncthreads();
-    if (tid == 0 && ok && prev_sub >= 0) {
+    if (tid == 0 && ok && prev_sub >= 0 && !(p.skip_publish && blockIdx.x == 0 && prev_new > p.skip_step)) {
         __threadfence();
         for (int f = 0; f < 6; ++f) st_release(p.flag + prev_sub * 6 + f, (unsigned long long)prev_new);
     }

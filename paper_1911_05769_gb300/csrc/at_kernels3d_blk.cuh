@@ -179,7 +179,7 @@ __global__ void __launch_bounds__(kThreads3b, sizeof(T) == 4 ? 2 : 1)
         const long long g0 = tt * m2;                        // this tile's first plane
         // ---- tile start: release the previous tile's flags, delays, halos
         __syncthreads();
-        if (tid == 0 && prev_sub >= 0) {
+        if (tid == 0 && prev_sub >= 0 && !(p.skip_publish && blockIdx.x == 0 && prev_new > p.skip_step)) {
             __threadfence();
             for (int f = 0; f < 6; ++f) st_release(p.flag + prev_sub * 6 + f, (unsigned long long)prev_new);
         }
@@ -403,7 +403,7 @@ __global__ void __launch_bounds__(kThreads3b, sizeof(T) == 4 ? 2 : 1)
         tile_coords(sub + 1 == hi ? lo : sub + 1, &nx0, &ny0, &nz0);
     }
     __syncthreads();
-    if (tid == 0 && ok && prev_sub >= 0) {
+    if (tid == 0 && ok && prev_sub >= 0 && !(p.skip_publish && blockIdx.x == 0 && prev_new > p.skip_step)) {
         __threadfence();
         for (int f = 0; f < 6; ++f) st_release(p.flag + prev_sub * 6 + f, (unsigned long long)prev_new);
     }

@@ -208,7 +208,7 @@ class Solver3D(Solver):
     steps advance each subdomain that many levels per pass (at most L + 1)."""
 
     def __init__(self, n, sub, L, nu, dt, *, dtype="f32", length=(2 * math.pi,) * 3, seed=0, flags=0,
-                 timeout_ns=0, max_ctas=0, stages=0, steps_per_pass=0, stream=None, device=None):
+                 timeout_ns=0, max_ctas=0, stages=0, steps_per_pass=0, test_skip_step=0, stream=None, device=None):
         import torch
         self.torch = torch
         dev = torch.device("cuda", torch.cuda.current_device() if device is None else device)
@@ -228,6 +228,7 @@ class Solver3D(Solver):
         g.max_ctas = max_ctas
         g.stages = stages
         g.steps_per_pass = steps_per_pass
+        g.test_skip_step = test_skip_step
         P = 1
         for a in range(3):
             P *= int(n[a]) // int(sub[a])

@@ -50,3 +50,36 @@ def test_timeout_status_is_sticky_until_reset(require_gpu):
     s.step(2, at.AT_SEEDED)          # within the published levels: no wait runs out
     assert s.status() == at.AT_OK
     s.close()
+
+
+@pytest.mark.parametrize("mode_name,spp", [("seeded", 1), ("free", 1), ("free", 3)])
+def test_stalled_neighbour_times_out_3d(require_gpu, mode_name, spp):
+    """3D (one level per pass, and the blocked free-running passes): CTA 0
+    stops releasing its subdomains' flags after level 4, its neighbours'
+    bounded flag waits run out, the kernel latches AT_ERR_TIMEOUT and every
+    CTA returns (the others see the abort word in their flag and plane
+    waits); a fresh solver on the same context then runs normally."""
+    import torch
+
+    import oracle
+    import paper_1911_05769_gb300 as at
+    mode = at.AT_SEEDED if mode_name == "seeded" else at.AT_FREE
+    n, sub, L, nu = 32, (16, 8, 8), 2, 0.1
+    u0 = W.u0_spectral3d(n, seed=4, kmax=8)
+    dt = W.dt_rule(u0, 2 * np.pi / n, nu, dim=3)
+    s = at.Solver3D((n, n, n), sub, L, nu, dt, dtype="f64", seed=3, max_ctas=4, steps_per_pass=spp,
+                    flags=at.AT_FLAG_TEST_SKIP_PUBLISH, test_skip_step=4, timeout_ns=20_000_000)
+    s.set_state(torch.from_numpy(np.ascontiguousarray(u0).ravel()).cuda())
+    s.step(40, mode)
+    assert s.status() == at.AT_ERR_TIMEOUT
+    assert "timed out" in at.at_last_error()
+    s.close()
+    # a fresh solver on the same context
+    s = at.Solver3D((n, n, n), sub, L, nu, dt, dtype="f64", seed=3, max_ctas=4)
+    s.set_state(torch.from_numpy(np.ascontiguousarray(u0).ravel()).cuda())
+    s.step(10, at.AT_SEEDED)
+    assert s.status() == at.AT_OK
+    out = s.state().double().cpu().numpy().reshape(u0.shape)
+    s.close()
+    ref, _ = oracle.run3d(u0, P=(2, 4, 4), L=L, nu=nu, dt=dt, n_steps=10, delay_mode=oracle.SEEDED, seed=3)
+    assert rel_linf(out, ref) <= TOL["f64"]

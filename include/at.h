@@ -449,8 +449,7 @@ int at_fma_peak(int dtype, int64_t trips, double *fma_per_s);
  *
  * Set-up.  Every call looks up the device address of the array
  * (cudaGetSymbolAddress) with the calling thread's current device; the first
- * call on a device also loads this library's device code there, so make that
- * first call before any stream capture begins on the device. */
+ * call on a device also loads this library's device code there. */
 int at_step_noalloc(const at_grid *grid, int64_t P, int scheme_order, int L,
                     double nu, double dt, void *u, int64_t n_steps,
                     int delay_mode, int8_t *delays);

@@ -276,3 +276,26 @@ def test_seeded_3d_unequal_spacing(dtype):
                              seed=6)
     assert rel_linf(g["u"], ref) <= TOL[dtype], rel_linf(g["u"], ref)
     assert np.array_equal(g["hist"], hist)
+
+
+def test_workload_parameters_blocked_free_2000_steps_3d():
+    """The 3D workload's parameters (as in the seeded test above: dx = 2 pi /
+    512, nu = 5e-3, the CFL dt, 32^3 subdomains, L = 2, a 128^3 box of length
+    pi / 2) over all 2000 steps, free-running in passes of L + 1 = 3 levels:
+    the oracle replaying the recorded delays matches within 1e-5 (FP32) and
+    1e-12 (FP64)."""
+    from paper_1911_05769_gb300 import AT_FREE
+    n, sub, L, nu, steps = 128, (32, 32, 32), 2, 5e-3, 2000
+    box = np.pi / 2
+    u0 = W.u0_spectral3d(n, seed=4, kmax=8)
+    dt = W.dt_rule(u0, box / n, nu, dim=3)
+    for dtype in ("f32", "f64"):
+        g = gpu_run3d(u0, sub=sub, L=L, nu=nu, dt=dt, steps=steps, dtype=dtype, mode=AT_FREE, record=True,
+                      length=(box,) * 3, steps_per_pass=L + 1)
+        rec = g["rec"]
+        assert rec.min() >= 0 and rec.max() <= L
+        ref, hist = oracle.run3d(u0, P=(4, 4, 4), L=L, nu=nu, dt=dt, n_steps=steps, length=box,
+                                 delay_mode=oracle.REPLAY, replay=rec)
+        assert np.max(np.abs(ref)) > 0.05
+        assert rel_linf(g["u"], ref) <= TOL[dtype], (dtype, rel_linf(g["u"], ref))
+        assert np.array_equal(g["hist"], hist)

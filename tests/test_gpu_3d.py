@@ -154,17 +154,15 @@ def test_workload_parameters_all_2000_steps_3d():
         assert np.array_equal(g["hist"], hist)
 
 
-def check_pass_structure(rec, spp, starts):
-    """Delays of blocked passes: a pass from level lv > 0 of b levels gives
-    level lv + j the delay k0 + j on every face (the halo of the pass is
+def check_pass_structure(rec, passes):
+    """Delays of blocked passes: a pass (lv, b) from level lv > 0 of b levels
+    gives level lv + j the delay k0 + j on every face (the halo of the pass is
     extrapolated from one pair of levels); the pass from level 0 has one level
     at delay 0."""
-    n = rec.shape[0]
-    assert np.all(rec[0] == 0) if starts[0] == 0 else True
-    for lv in starts:
+    for lv, b in passes:
         if lv == 0:
+            assert b == 1 and np.all(rec[0] == 0)
             continue
-        b = min(spp, n - lv)
         for j in range(1, b):
             assert np.array_equal(rec[lv + j].astype(int) - rec[lv].astype(int), np.full(rec[lv].shape, j))
 
@@ -176,6 +174,7 @@ BLOCKED = [
     (32, (32, 32, 16), 2, 3, 3, None),        # planes of 1024 points (every thread busy)
     (24, (8, 4, 3), 2, 3, 7, None),           # planes of 32 points, 3 planes per subdomain
     (32, (16, 16, 8), 2, 3, 0, [7, 12, 17]),  # several calls: passes restart at each call's first level
+    (32, (16, 8, 8), 2, 3, 5, [1, 1, 2, 3, 5]),  # calls shorter than a pass (the start-up pass: one level)
 ]
 
 
@@ -196,13 +195,15 @@ def test_blocked_free_3d_replays_in_oracle(dtype, n, sub, L, spp, max_ctas, call
     assert g["info"].threads == 256              # the blocked kernel's CTAs
     rec = g["rec"]
     assert rec.min() >= 0 and rec.max() <= L
-    starts, lv = [], 0
+    # passes restart at each call's first level; the pass from level 0 has one level
+    passes, lv = [], 0
     for c in (calls or [steps]):
-        end, lv = lv + c, lv
+        end = lv + c
         while lv < end:
-            starts.append(lv)
-            lv += 1 if lv == 0 else min(spp, end - lv)
-    check_pass_structure(rec, spp, starts)
+            b = 1 if lv == 0 else min(spp, end - lv)
+            passes.append((lv, b))
+            lv += b
+    check_pass_structure(rec, passes)
     ref, hist = oracle.run3d(u0, P=P, L=L, nu=nu, dt=dt, n_steps=steps, delay_mode=oracle.REPLAY, replay=rec)
     assert rel_linf(g["u"], ref) <= TOL[dtype], rel_linf(g["u"], ref)
     assert np.array_equal(g["hist"], hist)

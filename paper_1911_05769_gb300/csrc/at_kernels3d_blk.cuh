@@ -255,11 +255,9 @@ __global__ void __launch_bounds__(kThreads3b, sizeof(T) == 4 ? 2 : 1)
         }
         if (__syncthreads_or(bad)) { ok = false; break; }
         T *uz = reinterpret_cast<T *>(p.u) + (((long long)tz0 * plane_words + (long long)ty0 * p.n0) + tx0) + coff;
-        // ring entries of the pass's last two levels; levels from `ring_from`
+        // the pass's last two levels go to the ring; levels from `ring_from`
         // on are published too (a later call of any mode may read the
         // launch's last L + 2 levels)
-        T *const rbB = ring_entry<T>(p, lv + b, sub, 0);
-        T *const rbA = ring_entry<T>(p, lv + b - 1, sub, 0);
         const long long rf64 = lev_end - p.L - 1 - lv;
         const int ring_from = rf64 < 1 ? 1 : rf64 > BM + 1 ? BM + 1 : (int)rf64;
         // plane 0 of level lv
@@ -328,16 +326,18 @@ __global__ void __launch_bounds__(kThreads3b, sizeof(T) == 4 ? 2 : 1)
                 else stv<T, VW>(uz + (long long)z * plane_words, un);
             }
             // the last two levels of the pass (and the launch's last L + 2)
-            // go to the ring
+            // go to the ring: their face values are kept in this level's
+            // own halo arrays (level i read its halos of level lv + j at
+            // these words above and reads them no more), and copied to the
+            // ring by the whole CTA after the tile's last step
             const bool ring = ST ? (i + 1 >= BM || i >= ring_from) : (i + 1 >= b || i >= ring_from);
             if (ring && cv) {
-                T *rb = last ? rbB : (ST ? i + 1 == BM : i + 1 == b) ? rbA : ring_entry<T>(p, lv + i, sub, 0);
-                if (fx0) rb[z * m1 + cy] = un[0];
-                if (fx1) rb[fw + z * m1 + cy] = un[VW - 1];
-                if (fy0) stv<T, VW>(rb + 2 * fw + z * m0 + cx, un);
-                if (fy1) stv<T, VW>(rb + 3 * fw + z * m0 + cx, un);
-                if (bot) stv<T, VW>(rb + 4 * fw + c, un);
-                if (top) stv<T, VW>(rb + 5 * fw + c, un);
+                if (fx0) halo_at(0, j)[z * m1 + cy] = un[0];
+                if (fx1) halo_at(1, j)[z * m1 + cy] = un[VW - 1];
+                if (fy0) sts4<T>(halo_at(2, j) + z * m0 + cx, un);
+                if (fy1) sts4<T>(halo_at(3, j) + z * m0 + cx, un);
+                if (bot) sts4<T>(halo_at(4, j) + c, un);
+                if (top) sts4<T>(halo_at(5, j) + c, un);
             }
             // level j's planes move up by one (plane z + 1 replaces plane
             // z - 1); level i starts its own window at plane 0; level i + 1
@@ -389,6 +389,30 @@ __global__ void __launch_bounds__(kThreads3b, sizeof(T) == 4 ? 2 : 1)
         }
         for (; t < nst && ok; ++t) ok = step(t, IntC<0>{});
         if (!ok) break;
+        // the faces of the levels published (in the halo arrays of the level
+        // below them) to the ring: 16-byte copies spread over the CTA
+        __syncthreads();
+        {
+            const int i_lo = (b - 1 < ring_from ? b - 1 : ring_from) < 1 ? 1 : (b - 1 < ring_from ? b - 1 : ring_from);
+            for (int i = i_lo; i <= b; ++i) {
+                T *rb = ring_entry<T>(p, lv + i, sub, 0);
+#pragma unroll
+                for (int f = 0; f < 6; ++f) {
+                    const int nw = f < 2 ? m1 * m2 : f < 4 ? m0 * m2 : m0 * m1;
+                    const T *h = halo_at(f, i - 1);
+                    T *r = rb + (size_t)f * fw;
+                    if ((nw & 3) == 0) {
+                        for (int q = 4 * tid; q < nw; q += 4 * NT) {
+                            T v[4];
+                            lds<T, 4>(h + q, v);
+                            stv<T, 4>(r + q, v);
+                        }
+                    } else {
+                        for (int q = tid; q < nw; q += NT) r[q] = h[q];
+                    }
+                }
+            }
+        }
         // the next bulk read of this tile's output (its next pass) follows
         // a later barrier
         fence_proxy_async_global();

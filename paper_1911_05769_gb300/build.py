@@ -23,7 +23,7 @@ LIB = os.path.join(HERE, "libat.so")
 SOURCES = [os.path.join(CSRC, f) for f in (
     "at_api.cu", "at_kernels_f32.cu", "at_kernels_f64.cu", "at_batch_f32.cu", "at_batch_f64.cu", "at_adjoint.cu",
     "at_kernels_f32v.cu", "at_kernels_f32c.cu", "at_batch_f32c.cu", "at_sync_f32.cu", "at_sync_f32v.cu", "at_sync_batch_f32.cu",
-    "at_sync_f64.cu", "at_kernels3d.cu", "at_kernels3d_iso.cu", "at_kernels3d_blk.cu", "at_system3d.cu")]
+    "at_sync_f64.cu", "at_kernels3d.cu", "at_kernels3d_iso.cu", "at_kernels3d_blk.cu", "at_kernels3d_blk32.cu", "at_system3d.cu")]
 DEPS = SOURCES + [os.path.join(CSRC, f) for f in ("at_kernels.cuh", "at_device.cuh", "at_adjoint.cuh",
                                                  "at_kernels3d.cuh", "at_kernels3d_blk.cuh")] + [
     os.path.join(INCLUDE, "at.h")]

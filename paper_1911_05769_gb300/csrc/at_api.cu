@@ -45,6 +45,7 @@ void *atk_stepper3d_iso_kernel(int w, int tc, int vw);
 void *atk_system3d_kernel(int w, int tc, int nf, int vw);
 void *atk_init3d_kernel(int w);
 void *atk_stepper3d_blk_kernel(int w, int sb, int iso);
+void *atk_stepper3d_blk32_kernel(int w, int sb, int iso);
 
 namespace {
 
@@ -623,9 +624,12 @@ static int create3d(const at_grid *grid, int64_t P, int L, int nf, const double 
     if (sb > 1) {
         // the blocked free-running kernel: 256 threads (a group of 4 columns
         // each), its own plane stages (2 in use, the rest arriving) and grid
-        void *kb = atk_stepper3d_blk_kernel(w, sb, iso);
+        // (32^3 subdomains: the instances with the sizes known at compile time)
+        const bool cube32 = d.m[0] == 32 && d.m[1] == 32 && d.m[2] == 32;
+        void *kb = cube32 ? atk_stepper3d_blk32_kernel(w, sb, iso) : atk_stepper3d_blk_kernel(w, sb, iso);
         int st = grid->stages > 0 ? grid->stages : 4;
         if (st < 3) st = 3;
+        if (st > atk::kMaxStages3b) st = atk::kMaxStages3b;
         if (st > d.m[2]) st = d.m[2];
         atk::Smem3b sb3 = atk::smem3b_layout(d.m[0], d.m[1], d.face_words, w, st, sb);
         while (sb3.total > smem_optin && st > 3) sb3 = atk::smem3b_layout(d.m[0], d.m[1], d.face_words, w, --st, sb);

@@ -1,6 +1,7 @@
 // at_kernels3d_blk.cu -- instantiations of the temporally blocked free-running
 // scalar 3D stepper (float and double state; 2, 3 or 4 levels per pass;
-// equal or unequal spacing on the three axes).
+// equal or unequal spacing on the three axes; any subdomain shape).  The
+// instances for 32^3 subdomains are in at_kernels3d_blk32.cu.
 #include "at_kernels3d_blk.cuh"
 
 template <typename T, bool ISO>

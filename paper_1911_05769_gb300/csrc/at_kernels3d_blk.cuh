@@ -38,6 +38,7 @@ namespace atk {
 
 constexpr int kThreads3b = 256;    // threads of a CTA: one group of 4 columns each (planes <= 1024 points)
 constexpr int kMaxPass3 = 4;       // levels per pass of the blocked stepper (2 .. 4, one instance each)
+constexpr int kMaxStages3b = 8;    // plane stages at most (their barriers' space is fixed)
 
 // shared memory: mbarriers and fill counts, delay counters, the halos of the
 // pass (face f, level j: array f * sb + j of `face_words` words; x faces
@@ -51,7 +52,7 @@ __host__ __device__ inline Smem3b smem3b_layout(int m0, int m1, long long face_w
 {
     Smem3b l;
     l.bar_off = 0;                                   // full[stages], then one int per stage
-    l.hist_off = round_up(16LL * stages, 16);
+    l.hist_off = 16LL * kMaxStages3b;               // (fixed: the offsets below do not depend on stages)
     l.halo_off = round_up(l.hist_off + 4LL * (kMaxL + 1), 128);
     l.halo_bytes = round_up(face_words * word, 16);
     l.lvl_off = round_up(l.halo_off + 6LL * sb * l.halo_bytes, 128);
@@ -75,23 +76,25 @@ __host__ __device__ inline long long pass_len3(long long lv, long long lev_end, 
 }
 
 // BM: levels of a full pass (p.sb == BM); ISO: equal spacing on the three
-// axes (one coefficient pair: the six neighbours summed before scaling)
-template <typename T, int BM, bool ISO>
+// axes (one coefficient pair: the six neighbours summed before scaling); MS:
+// 0, or the subdomain edge MS of cubic MS^3 subdomains known at compile time
+// (every shared-memory offset and plane index then folds into constants)
+template <typename T, int BM, bool ISO, int MS = 0>
 __global__ void __launch_bounds__(kThreads3b, sizeof(T) == 4 ? 2 : 1)
     at_stepper3d_blk(const Params3 p, const __grid_constant__ CUtensorMap tmap)
 {
     constexpr int NT = kThreads3b, VW = 4;
     extern __shared__ __align__(128) unsigned char smem[];
     const int NS = p.stages;
-    const int m0 = p.m0, m1 = p.m1, m2 = p.m2;
-    const Smem3b sl = smem3b_layout(m0, m1, p.face_words, (int)sizeof(T), NS, BM);
+    const int m0 = MS ? MS : p.m0, m1 = MS ? MS : p.m1, m2 = MS ? MS : p.m2;
+    const Smem3b sl = smem3b_layout(m0, m1, MS ? (long long)MS * MS : p.face_words, (int)sizeof(T), NS, BM);
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + sl.bar_off);
     int *s_fills = reinterpret_cast<int *>(bars + NS);
     unsigned *hist = reinterpret_cast<unsigned *>(smem + sl.hist_off);
     // (32-bit offsets into shared memory)
     const int o_halo = (int)sl.halo_off, hb = (int)sl.halo_bytes, o_lvl = (int)sl.lvl_off,
               pbytes = (int)sl.plane_bytes, o_stage = (int)sl.stage_off;
-    const int fw = (int)p.face_words;
+    const int fw = MS ? MS * MS : (int)p.face_words;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const long long lo = (long long)blockIdx.x * p.P / p.G, hi = (long long)(blockIdx.x + 1) * p.P / p.G;

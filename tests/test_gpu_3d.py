@@ -240,20 +240,22 @@ def test_blocked_free_3d_mixed_with_other_modes():
 
 
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
-def test_blocked_free_3d_unequal_spacing(dtype):
+@pytest.mark.parametrize("n,sub", [(32, (16, 8, 8)), (64, (32, 32, 32))])
+def test_blocked_free_3d_unequal_spacing(dtype, n, sub):
     """Blocked free-running passes on a box with unequal spacing (z half as
     long: the stepper's per-axis coefficients rather than its equal-spacing
-    form), recorded delays replayed by the oracle."""
+    form; 32^3 subdomains take the instances with compile-time sizes),
+    recorded delays replayed by the oracle."""
     from paper_1911_05769_gb300 import AT_FREE
-    n, sub, L, spp = 32, (16, 8, 8), 2, 3
-    nu = NU[n]
+    L, spp = 2, 3
+    nu = NU.get(n, 0.05)
     u0 = W.u0_spectral3d(n, seed=13, kmax=8)
     length = (2 * np.pi, 2 * np.pi, np.pi)
     dx = tuple(a / n for a in length)
     dt = W.dt_rule(u0, min(dx), nu, dim=3)
     P = tuple(n // m for m in sub)
-    g = gpu_run3d(u0, sub=sub, L=L, nu=nu, dt=dt, steps=30, dtype=dtype, mode=AT_FREE, record=True, max_ctas=5,
-                  steps_per_pass=spp, length=length)
+    g = gpu_run3d(u0, sub=sub, L=L, nu=nu, dt=dt, steps=30, dtype=dtype, mode=AT_FREE, record=True,
+                  max_ctas=5 if P[0] * P[1] * P[2] > 8 else 3, steps_per_pass=spp, length=length)
     rec = g["rec"]
     assert rec.min() >= 0 and rec.max() <= L
     ref, hist = oracle.run3d(u0, P=P, L=L, nu=nu, dt=dt, n_steps=30, dx=dx, delay_mode=oracle.REPLAY, replay=rec)

@@ -27,9 +27,13 @@
 //
 // Neighbours only ever read levels that end a pass (a flag is released as the
 // level a pass ends at, and passes of all subdomains start at the same
-// levels), so a pass writes ring entries for its last two levels only.
-// Delays are recorded per (level, subdomain, face) as in the unblocked
-// stepper and replay exactly in the oracle.
+// levels), so a pass writes ring entries for its last two levels only (and
+// for the launch's last L + 2 levels, which a later call of another mode may
+// read).  A level collects the face values it publishes in its own halo
+// arrays, at the words it has just read, and the whole CTA copies them to
+// the ring after the tile's last step.  Delays are recorded per (level,
+// subdomain, face) as in the unblocked stepper and replay exactly in the
+// oracle.
 #pragma once
 
 #include "at_kernels3d.cuh"
@@ -40,10 +44,11 @@ constexpr int kThreads3b = 256;    // threads of a CTA: one group of 4 columns e
 constexpr int kMaxPass3 = 4;       // levels per pass of the blocked stepper (2 .. 4, one instance each)
 constexpr int kMaxStages3b = 8;    // plane stages at most (their barriers' space is fixed)
 
-// shared memory: mbarriers and fill counts, delay counters, the halos of the
-// pass (face f, level j: array f * sb + j of `face_words` words; x faces
-// [z][y], y faces [z][x], z faces [y][x]), two planes per inner level, plane
-// stages
+// shared memory: mbarriers and fill counts (space for kMaxStages3b stages),
+// delay counters, the halos of the pass (face f, level j: array f * sb + j of
+// `face_words` words; x faces [z][y], y faces [z][x], z faces [y][x]; after
+// level j + 1 has read them, the faces it publishes), two planes per inner
+// level, plane stages
 struct Smem3b {
     long long bar_off, hist_off, halo_off, halo_bytes, lvl_off, plane_bytes, stage_off, total;
 };

@@ -304,3 +304,59 @@ def test_workload_parameters_blocked_free_2000_steps_3d():
         assert np.max(np.abs(ref)) > 0.05
         assert rel_linf(g["u"], ref) <= TOL[dtype], (dtype, rel_linf(g["u"], ref))
         assert np.array_equal(g["hist"], hist)
+
+
+def _smooth_box(shape, seed):
+    """A seeded smooth periodic field on a box of shape (n2, n1, n0): a few
+    low Fourier modes with random phases, max |u| = 1 (inputs only)."""
+    rng = np.random.default_rng(seed)
+    n2, n1, n0 = shape
+    z, y, x = np.meshgrid(np.arange(n2) / n2, np.arange(n1) / n1, np.arange(n0) / n0, indexing="ij")
+    u = np.zeros(shape)
+    for _ in range(6):
+        k = rng.integers(0, 3, size=3)
+        u += rng.uniform(0.5, 1.0) * np.sin(2 * np.pi * (k[0] * x + k[1] * y + k[2] * z) + rng.uniform(0, 2 * np.pi))
+    return u / np.max(np.abs(u))
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("shape,sub", [((16, 32, 128), (128, 8, 4)),    # rows of 128 points: a row is a warp
+                                       ((6, 8, 8), (4, 4, 3))])          # the smallest subdomain
+def test_blocked_free_3d_edge_shapes(dtype, shape, sub):
+    """Blocked free-running passes on the extreme subdomain shapes the blocked
+    stepper takes (sub[0] = 128 and 4), against the oracle replaying the
+    recorded delays."""
+    from paper_1911_05769_gb300 import AT_FREE
+    L, spp = 2, 3
+    u0 = _smooth_box(shape, seed=15)
+    n2, n1, n0 = shape
+    dx = tuple(2 * np.pi / n for n in (n0, n1, n2))
+    nu = max(dx) / 2                  # a cell Peclet number of about 2 on the coarsest axis (max |u0| = 1)
+    dt = W.dt_rule(u0.ravel(), min(dx), nu, dim=3)
+    P = (n0 // sub[0], n1 // sub[1], n2 // sub[2])
+    g = gpu_run3d(u0, sub=sub, L=L, nu=nu, dt=dt, steps=24, dtype=dtype, mode=AT_FREE, record=True,
+                  max_ctas=3, steps_per_pass=spp)
+    rec = g["rec"]
+    assert rec.min() >= 0 and rec.max() <= L
+    ref, hist = oracle.run3d(u0, P=P, L=L, nu=nu, dt=dt, n_steps=24, dx=dx, delay_mode=oracle.REPLAY, replay=rec)
+    assert np.all(np.isfinite(ref)) and np.max(np.abs(ref)) > 0.01
+    assert rel_linf(g["u"], ref) <= TOL[dtype], rel_linf(g["u"], ref)
+    assert np.array_equal(g["hist"], hist)
+
+
+def test_blocked_free_3d_four_levels_on_32_cubes():
+    """Passes of 4 levels (L = 3) on 32^3 subdomains: FP32 fits one CTA per
+    SM and replays in the oracle; FP64 (24 halo planes of 8 KiB) does not fit
+    a CTA's shared memory and at_create refuses it with AT_ERR_RESIDENCY."""
+    import paper_1911_05769_gb300 as at
+    n, sub, L = 64, (32, 32, 32), 3
+    nu = 0.05
+    u0 = W.u0_spectral3d(n, seed=16, kmax=8)
+    dt = W.dt_rule(u0, 2 * np.pi / n, nu, dim=3)
+    g = gpu_run3d(u0, sub=sub, L=L, nu=nu, dt=dt, steps=21, dtype="f32", mode=at.AT_FREE, record=True,
+                  steps_per_pass=L + 1)
+    ref, _ = oracle.run3d(u0, P=(2, 2, 2), L=L, nu=nu, dt=dt, n_steps=21, delay_mode=oracle.REPLAY, replay=g["rec"])
+    assert rel_linf(g["u"], ref) <= TOL["f32"]
+    with pytest.raises(at.AtError) as e:
+        at.Solver3D((n, n, n), sub, L, nu, dt, dtype="f64", steps_per_pass=L + 1)
+    assert e.value.code == at.AT_ERR_RESIDENCY and "shared memory" in str(e.value)

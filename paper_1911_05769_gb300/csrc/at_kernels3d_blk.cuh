@@ -277,7 +277,7 @@ __global__ void __launch_bounds__(kThreads3b, sizeof(T) == 4 ? 2 : 1)
         // a step of the steady state (every level of a full pass at an
         // interior plane: no guards, no z faces) with t even / odd, so that
         // the window slots are known at compile time; 0: any step
-        auto level = [&](auto I, auto STEADY, int t, int sn, T *up) {
+        auto level = [&](auto I, auto STEADY, int t, int sn, T *up, const T *xh) {
             constexpr int i = decltype(I)::value, j = i - 1;
             constexpr bool ST = decltype(STEADY)::value != 0;
             constexpr int ZP = ((decltype(STEADY)::value - 1 - i + 1) % 2 + 2) % 2;   // z & 1 (steady)
@@ -309,8 +309,8 @@ __global__ void __launch_bounds__(kThreads3b, sizeof(T) == 4 ? 2 : 1)
             // or the x halos at a row's ends
             T xl = __shfl_up_sync(0xffffffffu, cw[VW - 1], 1);
             T xr = __shfl_down_sync(0xffffffffu, cw[0], 1);
-            if (fx0) xl = halo_at(0, j)[z * m1 + cy];
-            if (fx1) xr = halo_at(1, j)[z * m1 + cy];
+            if (fx0) xl = xh[2 * j];
+            if (fx1) xr = xh[2 * j + 1];
 #pragma unroll
             for (int e = 0; e < VW; ++e) {
                 const T cc = cw[e];
@@ -365,11 +365,21 @@ __global__ void __launch_bounds__(kThreads3b, sizeof(T) == 4 ? 2 : 1)
             const int sn = ws;                               // stage of plane t + 1
             if (t + 1 < m2 && !bad) bad = wait_next() ? 0 : 1;
             if (!bad) {
+                // the x halos of every level of the step, loaded first (their
+                // latency then overlaps level 1 instead of each level's chain)
+                T xh[2 * BM];
+#pragma unroll
+                for (int j = 0; j < BM; ++j) {
+                    const int z = t - j;                     // plane of level j + 1
+                    const bool act = decltype(STEADY)::value != 0 || (j < b && z >= 0 && z < m2);
+                    xh[2 * j] = (act && fx0) ? halo_at(0, j)[z * m1 + cy] : (T)0;
+                    xh[2 * j + 1] = (act && fx1) ? halo_at(1, j)[z * m1 + cy] : (T)0;
+                }
                 T up[VW];                                    // level i - 1 at plane z + 1 (this step)
-                level(IntC<1>{}, STEADY, t, sn, up);
-                if constexpr (BM >= 2) level(IntC<2>{}, STEADY, t, sn, up);
-                if constexpr (BM >= 3) level(IntC<3>{}, STEADY, t, sn, up);
-                if constexpr (BM >= 4) level(IntC<4>{}, STEADY, t, sn, up);
+                level(IntC<1>{}, STEADY, t, sn, up, xh);
+                if constexpr (BM >= 2) level(IntC<2>{}, STEADY, t, sn, up, xh);
+                if constexpr (BM >= 3) level(IntC<3>{}, STEADY, t, sn, up, xh);
+                if constexpr (BM >= 4) level(IntC<4>{}, STEADY, t, sn, up, xh);
             }
             if (__syncthreads_or(bad)) return false;
             if (tid == 0 && t < m2) {
